@@ -1,0 +1,132 @@
+/*
+ * qcl_oracle.h -- plain FP64 CPU oracle for momentum-jump-free mixed
+ * quantum-classical Liouville (QCL) dynamics.
+ *
+ * TEST INFRASTRUCTURE ONLY.  Nothing in the product path may include, link or
+ * call this code; only the tests, the smoke check and the benchmark's CPU
+ * baseline leg use it.  It shares no code, header, table or constant with the
+ * CUDA library: everything here (the Philox generator included) is written
+ * out again from its published definition.
+ *
+ * Method (paper, Sec. II A, Eq. 1): the partially Wigner-transformed density
+ * matrix element rho_ab(R,P) obeys
+ *   d/dt rho_ab = -i w_ab rho_ab - (P/M) sum_g (d_ag rho_gb - rho_ag d_gb)
+ *                 - (P/M) d rho_ab/dR - 1/2 (F_a + F_b) d rho_ab/dP .
+ * It is estimated by a fixed ensemble of walkers (Sec. II B: no spawning, the
+ * walker count is fixed).  Each walker carries (R, P), an index pair (a, b) and
+ * a complex weight m exp(-i phi).  The walker layout in this oracle is
+ * walker-major: R[i*N + j].
+ */
+#ifndef QCL_ORACLE_H
+#define QCL_ORACLE_H
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define ORC_MAX_NS 8
+#define ORC_MAX_N 256
+
+/* Philox counter word 3 ("purpose") values.  They are part of the random
+ * stream definition that the GPU library follows too. */
+#define ORC_PURPOSE_INIT 1u
+#define ORC_PURPOSE_HOP 2u
+
+/* Linear vibronic-coupling model: V(R) = 1/2 sum_j k_j R_j^2 + W(R),
+ * W(R) = E + sum_j R_j K_j, with k_j = M_j w_j^2 and E, K_j real symmetric
+ * n_states x n_states (row-major).  K is [n_modes][n_states*n_states]. */
+typedef struct {
+  int32_t n_states;
+  int32_t n_modes;
+  double hbar;
+  const double* mass;
+  const double* omega;
+  const double* E;
+  const double* K;
+  double hop_scale; /* kappa: p_e = min(kappa |A_e|, p_max) */
+  double p_max;
+} orc_model;
+
+/* Initial condition: diabatic electronic density rho_el0 (real symmetric),
+ * Wigner distribution of harmonic modes centred at (R0, P0) at inverse
+ * temperature beta (INFINITY = ground state).  wigner = 0 puts every walker
+ * exactly at (R0, P0). */
+typedef struct {
+  const double* rho_el0;
+  const double* R0;
+  const double* P0;
+  double beta;
+  int32_t wigner;
+} orc_init;
+
+/* Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11). */
+void orc_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]);
+
+/* Symmetric eigen-decomposition by cyclic Jacobi rotations, eigenvalues
+ * ascending, eigenvectors in the columns of V (row-major n x n). */
+void orc_jacobi_eigh(int32_t n, const double* A, double* w, double* V);
+
+/* Adiabatic energies e[a] (ascending) and eigenvectors U[i*NS + a] of W(R).
+ * Two states: closed form theta = atan2(b, a)/2.  More states: Jacobi, with
+ * each eigenvector's sign aligned to U_ref (parallel transport) when U_ref is
+ * given, else its largest-magnitude component made positive.  Returns 1 if two
+ * energies are closer than the degeneracy threshold, else 0. */
+int32_t orc_adiabatic(const orc_model* md, const double* R, const double* U_ref, double* e,
+                      double* U);
+
+/* Nonadiabatic coupling d[(mu*NS + nu)*N + j] = <mu|d_j nu> (Hellmann-Feynman
+ * form) at R, from the decomposition (e, U).  Degenerate pairs give 0. */
+void orc_nac(const orc_model* md, const double* e, const double* U, double* d);
+
+/* Mean force of pair (a, b): F_j = -k_j R_j - 1/2 (dE_a/dR_j + dE_b/dR_j). */
+void orc_mean_force(const orc_model* md, const double* R, const double* U, int32_t a, int32_t b,
+                    double* F);
+
+/* Transition events of walker (a, b) at (R, P) with decomposition (e, U):
+ * writes, in the fixed event order, the target pair, amplitude A_e and the
+ * quantised probability threshold T_e (p_hat = T_e 2^-24).  Returns the event
+ * count 2 (NS - 1). */
+int32_t orc_events(const orc_model* md, const double* P, const double* e, const double* U,
+                   int32_t a, int32_t b, double dt, int32_t* tgt_a, int32_t* tgt_b, double* A,
+                   uint32_t* T);
+
+/* Deterministic part of one step (velocity Verlet on the pair's mean force and
+ * trapezoid phase); U (NS > 2 only) carries the gauge in and out. */
+void orc_step_deterministic(const orc_model* md, double* R, double* P, double* phi, int32_t a,
+                            int32_t b, double* U, double dt);
+
+/* Sample n_traj walkers with global ids traj_offset + i. */
+int32_t orc_sample(const orc_model* md, const orc_init* in, uint64_t seed, uint64_t traj_offset,
+                   int64_t n_traj, double* R, double* P, double* m, double* phi, int32_t* alpha,
+                   int32_t* beta, double* U);
+
+/* Advance n_traj walkers from absolute step step0 by n_steps.  n_deg (may be
+ * NULL) accumulates the count of degenerate-gap events. */
+int32_t orc_advance(const orc_model* md, uint64_t seed, uint64_t traj_offset, int64_t n_traj,
+                    double* R, double* P, double* m, double* phi, int32_t* alpha, int32_t* beta,
+                    double* U, int64_t step0, int64_t n_steps, double dt, int64_t* n_deg);
+
+/* Per-walker observable contributions q[i*4NS^2 + k]:
+ *   k = 2(i*NS+j)+c          diabatic rho_ij,  c = 0 real, 1 imaginary
+ *   k = 2NS^2 + 2(a*NS+b)+c  adiabatic rho_ab  */
+void orc_contrib(const orc_model* md, int64_t n_traj, const double* R, const double* m,
+                 const double* phi, const int32_t* alpha, const int32_t* beta, const double* U,
+                 double* q);
+
+/* Sum over walkers (pairwise) of each contribution and of its square:
+ * row[k] = sum q_k, row[4NS^2 + k] = sum q_k^2. */
+void orc_observe(const orc_model* md, int64_t n_traj, const double* R, const double* m,
+                 const double* phi, const int32_t* alpha, const int32_t* beta, const double* U,
+                 double* row);
+
+/* Whole run: sample, then n_steps steps with an observation row at every
+ * absolute step s = k * out_stride (k = 0 .. n_steps / out_stride). */
+int32_t orc_run(const orc_model* md, const orc_init* in, uint64_t seed, uint64_t traj_offset,
+                int64_t n_traj, double dt, int64_t n_steps, int64_t out_stride, double* rows,
+                int64_t* n_deg);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

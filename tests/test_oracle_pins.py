@@ -1,0 +1,503 @@
+"""Pins of the FP64 oracle against what the paper and mathematics fix.
+
+Each test compares the oracle with something other than itself: published
+known-answer vectors, numpy.linalg.eigh, finite differences, closed forms of
+the harmonic/pure-dephasing case, physical limits of the Wigner distribution,
+exact branch enumeration, and exact invariants of Eq. 1.
+"""
+import math
+import os
+
+import numpy as np
+import pytest
+from scipy import stats
+
+from paper_2608_14544_gb300 import workloads as wl
+from tests import indep
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _gauge_signs(U_or, U_np):
+    s = np.sign(np.sum(U_or * U_np, axis=0))
+    s[s == 0] = 1.0
+    return s
+
+
+def _models():
+    m2 = wl.config(2)["model"]
+    m3 = wl.config(3)["model"]
+    m4 = wl.random_lvc4(7)
+    return [m2, m3, m4]
+
+
+def _random_R(model, rng):
+    k = model["mass"] * model["omega"] ** 2
+    return rng.normal(size=model["n_modes"]) * np.sqrt(1.0 / k) * 1.5
+
+
+def _random_P(model, rng):
+    return rng.normal(size=model["n_modes"]) * np.sqrt(model["mass"] * model["omega"] ** 2) * 1.5
+
+
+# ------------------------------------------------------------------ Philox --
+def test_philox_known_answers(oracle_lib):
+    n = 0
+    with open(os.path.join(GOLDEN, "philox4x32_10_kat.txt")) as f:
+        for line in f:
+            if line.startswith("#") or not line.strip():
+                continue
+            v = [int(x, 16) for x in line.split()]
+            out = oracle_lib.philox4x32_10(v[0:4], v[4:6])
+            assert list(out) == v[6:10]
+            n += 1
+    assert n == 3
+
+
+# ----------------------------------------------------------- eigen + NAC --
+@pytest.mark.parametrize("n", [2, 3, 4, 5, 8])
+def test_jacobi_matches_numpy(oracle_lib, n):
+    rng = np.random.default_rng(n)
+    for _ in range(20):
+        A = rng.normal(size=(n, n))
+        A = A + A.T
+        w, V = oracle_lib.jacobi_eigh(A)
+        w_np = np.linalg.eigvalsh(A)
+        assert np.allclose(w, w_np, rtol=0, atol=1e-12 * np.abs(w_np).max())
+        assert np.allclose(A @ V, V * w, atol=1e-12 * np.abs(w_np).max())
+        assert np.allclose(V.T @ V, np.eye(n), atol=1e-13)
+
+
+def test_adiabatic_matches_numpy(oracle_lib):
+    rng = np.random.default_rng(1)
+    for model in _models():
+        om = oracle_lib.OracleModel(model)
+        for _ in range(10):
+            R = _random_R(model, rng)
+            e, U, _ = oracle_lib.adiabatic(om, R)
+            e_np, U_np = indep.eigh_aligned(model, R)
+            assert np.allclose(e, e_np, atol=1e-12)
+            s = _gauge_signs(U, U_np)
+            assert np.allclose(U, U_np * s, atol=1e-10)
+
+
+def test_nac_matches_finite_differences(oracle_lib):
+    rng = np.random.default_rng(2)
+    for model in _models():
+        om = oracle_lib.OracleModel(model)
+        for _ in range(5):
+            R = _random_R(model, rng)
+            e, U, _ = oracle_lib.adiabatic(om, R)
+            d = oracle_lib.nac(om, e, U)
+            _, U_np, d_fd = indep.nac_fd(model, R)
+            s = _gauge_signs(U, U_np)
+            d_fd = d_fd * s[:, None, None] * s[None, :, None]
+            scale = max(1.0, np.abs(d_fd).max())
+            assert np.allclose(d, d_fd, atol=2e-6 * scale), (model["name"], np.abs(d - d_fd).max())
+            # antisymmetry of the real first-order coupling
+            assert np.allclose(d, -np.transpose(d, (1, 0, 2)), atol=1e-12 * scale)
+
+
+def test_mean_force_matches_finite_differences(oracle_lib):
+    rng = np.random.default_rng(3)
+    for model in _models():
+        om = oracle_lib.OracleModel(model)
+        ns = model["n_states"]
+        for _ in range(4):
+            R = _random_R(model, rng)
+            _, U, _ = oracle_lib.adiabatic(om, R)
+            for a in range(ns):
+                for b in range(ns):
+                    F = oracle_lib.mean_force(om, R, U, a, b)
+                    F_fd = indep.mean_force_fd(model, R, a, b)
+                    assert np.allclose(F, F_fd, atol=1e-6 * max(1.0, np.abs(F_fd).max()))
+
+
+def test_events_are_the_coupling_term_of_eq1(oracle_lib):
+    """One step's expectation (1 + dt L) column: each event amplitude equals
+    dt L[target, source] with L built from finite-difference couplings."""
+    rng = np.random.default_rng(4)
+    dt = 0.01
+    for model in _models():
+        om = oracle_lib.OracleModel(model)
+        ns = model["n_states"]
+        for _ in range(4):
+            R = _random_R(model, rng)
+            P = _random_P(model, rng)
+            e, U, _ = oracle_lib.adiabatic(om, R)
+            _, U_np, d_fd = indep.nac_fd(model, R)
+            s = _gauge_signs(U, U_np)
+            d_fd = d_fd * s[:, None, None] * s[None, :, None]
+            L = indep.coupling_operator(model, P, d_fd)
+            scale = max(1e-3, np.abs(dt * L).max())
+            for a in range(ns):
+                for b in range(ns):
+                    src = a * ns + b
+                    ta, tb, A, T = oracle_lib.events(om, P, e, U, a, b, dt)
+                    assert len(A) == 2 * (ns - 1)
+                    col = dt * L[:, src].copy()
+                    assert abs(col[src]) < 1e-6 * scale  # no self term
+                    col[src] = 0.0
+                    got = np.zeros(ns * ns)
+                    for k in range(len(A)):
+                        got[ta[k] * ns + tb[k]] += A[k]
+                    assert np.allclose(got, col, atol=2e-6 * scale)
+                    # quantised probabilities: never above p_max, monotone in |A|
+                    assert T.sum() <= model["p_max"] * 2**24 + len(T)
+                    order = np.argsort(np.abs(A))
+                    assert np.all(np.diff(T[order].astype(np.int64)) >= 0)
+
+
+def test_gauge_transport_is_continuous(oracle_lib):
+    model = wl.random_lvc4(3)
+    om = oracle_lib.OracleModel(model)
+    rng = np.random.default_rng(5)
+    R0 = _random_R(model, rng)
+    dR = _random_R(model, rng) * 1e-3
+    _, U, _ = oracle_lib.adiabatic(om, R0)
+    for i in range(1, 200):
+        _, U1, _ = oracle_lib.adiabatic(om, R0 + i * dR, U)
+        assert np.abs(U1 - U).max() < 0.05
+        U = U1
+
+
+# --------------------------------------------------- harmonic closed form --
+def _dephasing_model(eps=5.0, omega=(1.0, 1.7), c=(0.3, 0.5)):
+    return wl.spin_boson(eps, 0.0, np.array(omega), np.array(c), name="pure-dephasing")
+
+
+def _plus_init(model, beta):
+    init = wl.sb_init(model, beta=beta)
+    init["rho_el0"] = np.full((2, 2), 0.5)
+    return init
+
+
+def test_verlet_and_phase_match_discrete_closed_form(oracle_lib):
+    """Delta = 0, no crossing: no transition can fire, every pair moves on an
+    exactly harmonic surface, and the phase is linear in (R0, P0)."""
+    model = _dephasing_model()
+    om = oracle_lib.OracleModel(model)
+    init = _plus_init(model, beta=2.0)
+    oi = oracle_lib.OracleInit(om, init)
+    dt, n_steps = 0.01, 300
+    st = oracle_lib.sample(om, oi, 11, 0, 64)
+    s0 = st.copy()
+    oracle_lib.advance(om, st, 11, 0, 0, n_steps, dt)
+    eps, hbar = 5.0, 1.0
+    c = np.array([0.3, 0.5])
+    k = model["mass"] * model["omega"] ** 2
+    mats = [indep.verlet_matrix(model["omega"][j], model["mass"][j], dt) for j in range(2)]
+    for i in range(64):
+        a, b = s0.alpha[i], s0.beta[i]
+        assert (st.alpha[i], st.beta[i]) == (a, b)
+        assert st.m[i] == s0.m[i]
+        # adiabatic state 0 is diabatic 1 (energy -(eps + cR)), state 1 is diabatic 0
+        sig = {0: -1.0, 1: 1.0}
+        f = -0.5 * (sig[a] + sig[b]) * c  # constant force part of the pair
+        x = np.zeros((2, n_steps + 1))
+        for j in range(2):
+            Rs = f[j] / k[j]
+            v = np.array([s0.R[i, j] - Rs, s0.P[i, j]])
+            x[j, 0] = v[0] + Rs
+            for n in range(n_steps):
+                v = mats[j] @ v
+                x[j, n + 1] = v[0] + Rs
+            assert np.isclose(st.R[i, j], v[0] + Rs, rtol=1e-11, atol=1e-12)
+            assert np.isclose(st.P[i, j], v[1], rtol=1e-11, atol=1e-12)
+        gap = 2.0 * (eps + c @ x) / hbar  # (e_1 - e_0)/hbar along the path
+        w = (sig[a] - sig[b]) / 2.0 * gap
+        phi = np.sum(0.5 * dt * (w[:-1] + w[1:]))
+        assert np.isclose(st.phi[i], phi, rtol=1e-11, atol=1e-11)
+
+
+def _dephasing_closed_form(model, init, dt, steps, eps):
+    """<exp(-i Phi)> for Phi = (2/hbar)(eps t + sum_j c_j int R_j dt) with Gaussian
+    (R0, P0): exact for the discrete Verlet/trapezoid map and for the exact
+    flow."""
+    hbar = model["hbar"]
+    w, M = model["omega"], model["mass"]
+    c = model["K"][:, 0, 0]
+    beta = init["beta"]
+    cth = 1.0 / np.tanh(0.5 * beta * hbar * w)
+    varR = hbar / (2 * M * w) * cth
+    varP = hbar * M * w / 2 * cth
+    muR, muP = init["R0"], init["P0"]
+    out_disc, out_exact = [], []
+    for n in steps:
+        t = n * dt
+        mean, var = 2 / hbar * eps * t, 0.0
+        mean_e, var_e = 2 / hbar * eps * t, 0.0
+        for j in range(len(w)):
+            Mv = indep.verlet_matrix(w[j], M[j], dt)
+            # int R dt by the trapezoid rule as a linear functional of (R0, P0)
+            acc = np.zeros(2)
+            A = np.eye(2)
+            for _ in range(n):
+                A1 = Mv @ A
+                acc += 0.5 * dt * (A[0] + A1[0])
+                A = A1
+            lin = 2 / hbar * c[j] * acc
+            mean += lin[0] * muR[j] + lin[1] * muP[j]
+            var += lin[0] ** 2 * varR[j] + lin[1] ** 2 * varP[j]
+            le = 2 / hbar * c[j] * np.array([np.sin(w[j] * t) / w[j],
+                                             (1 - np.cos(w[j] * t)) / (M[j] * w[j] ** 2)])
+            mean_e += le[0] * muR[j] + le[1] * muP[j]
+            var_e += le[0] ** 2 * varR[j] + le[1] ** 2 * varP[j]
+        out_disc.append(np.exp(-1j * mean - 0.5 * var))
+        out_exact.append(np.exp(-1j * mean_e - 0.5 * var_e))
+    return np.array(out_disc), np.array(out_exact)
+
+
+def test_pure_dephasing_coherence_closed_form(oracle_lib):
+    model = _dephasing_model()
+    init = _plus_init(model, beta=2.0)
+    om = oracle_lib.OracleModel(model)
+    oi = oracle_lib.OracleInit(om, init)
+    dt, n_steps, stride, n_traj = 0.01, 400, 40, 40_000
+    rows, _ = oracle_lib.run(om, oi, 5, 0, n_traj, dt, n_steps, stride)
+    mean, se = oracle_lib.finalize(rows, n_traj)
+    steps = np.arange(0, n_steps + 1, stride)
+    disc, exact = _dephasing_closed_form(model, init, dt, steps, 5.0)
+    # the discrete map tracks the exact flow to O(dt^2)
+    assert np.abs(disc - exact).max() < 1e-3
+    r01 = mean[:, 2 * 1] + 1j * mean[:, 2 * 1 + 1]
+    s01 = se[:, 2 * 1] + 1j * se[:, 2 * 1 + 1]
+    r10 = mean[:, 2 * 2] + 1j * mean[:, 2 * 2 + 1]
+    assert np.all(np.abs(r01.real - 0.5 * disc.real) < 4 * s01.real + 1e-12)
+    assert np.all(np.abs(r01.imag - 0.5 * disc.imag) < 4 * s01.imag + 1e-12)
+    assert np.all(np.abs(r10 - np.conj(0.5 * disc)) < 4 * (s01.real + s01.imag) + 1e-12)
+    # populations are exactly constant: no transition can fire
+    assert np.all(rows[:, 0] == rows[0, 0]) and np.all(rows[:, 6] == rows[0, 6])
+    # the decay is visible: the test is not trivially satisfied
+    assert abs(disc[-1]) < 0.9
+
+
+@pytest.mark.parametrize("kind", ["sb", "vibronic"])
+def test_zero_coupling_populations_bitwise_constant(oracle_lib, kind):
+    if kind == "sb":
+        model = _dephasing_model()
+        init = wl.sb_init(model, beta=2.0)
+    else:
+        model = wl.vibronic_ci()
+        model["K"][2] = 0.0  # lambda = 0
+        init = wl.vibronic_init(model)
+    om = oracle_lib.OracleModel(model)
+    oi = oracle_lib.OracleInit(om, init)
+    rows, _ = oracle_lib.run(om, oi, 3, 0, 2000, 0.01 if kind == "sb" else 0.05, 200, 20)
+    nn = 4
+    for a in range(2):
+        k = 2 * nn + 2 * (a * 2 + a)
+        assert np.all(rows[:, k] == rows[0, k])
+        assert np.all(rows[:, k + 1] == rows[0, k + 1])
+
+
+# ---------------------------------------------------- integrator invariants --
+def test_verlet_time_reversible(oracle_lib):
+    model = wl.vibronic_ci()
+    om = oracle_lib.OracleModel(model)
+    rng = np.random.default_rng(6)
+    for a, b in [(0, 0), (1, 1), (0, 1)]:
+        R0 = _random_R(model, rng)
+        P0 = _random_P(model, rng)
+        R, P, phi = R0.copy(), P0.copy(), 0.0
+        for _ in range(500):
+            R, P, phi, _ = oracle_lib.step_deterministic(om, R, P, phi, a, b, None, 0.05)
+        P = -P
+        for _ in range(500):
+            R, P, phi, _ = oracle_lib.step_deterministic(om, R, P, phi, a, b, None, 0.05)
+        assert np.allclose(R, R0, rtol=1e-12, atol=1e-12 * np.abs(R0).max())
+        assert np.allclose(-P, P0, rtol=1e-12, atol=1e-12 * np.abs(P0).max())
+
+
+def test_energy_error_scales_as_dt_squared(oracle_lib):
+    model = wl.vibronic_ci()
+    om = oracle_lib.OracleModel(model)
+    k = model["mass"] * model["omega"] ** 2
+    R0 = np.array([0.5, -0.8, 0.3])
+    P0 = np.array([3.0, -2.0, 4.0])
+
+    def h(R, P, a, b):
+        e = np.linalg.eigvalsh(indep.elec(model, R))
+        return np.sum(P**2 / (2 * model["mass"])) + 0.5 * np.sum(k * R**2) + 0.5 * (e[a] + e[b])
+
+    for a, b in [(0, 0), (1, 1)]:
+        errs = []
+        for dt in (0.1, 0.05):
+            R, P, phi = R0.copy(), P0.copy(), 0.0
+            H0 = h(R, P, a, b)
+            mx = 0.0
+            for _ in range(int(round(100.0 / dt))):
+                R, P, phi, _ = oracle_lib.step_deterministic(om, R, P, phi, a, b, None, dt)
+                mx = max(mx, abs(h(R, P, a, b) - H0))
+            errs.append(mx)
+        assert 3.2 < errs[0] / errs[1] < 4.8, errs
+
+
+# --------------------------------------------------------- Wigner sampling --
+@pytest.mark.parametrize("beta", [math.inf, 1e-2])
+def test_wigner_moments_physical_limits(oracle_lib, beta):
+    """Ground state: <k dR^2/2> = <P^2/2M> = hbar w / 4.  High temperature:
+    classical equipartition, 1/(2 beta) each."""
+    w, c = wl.ohmic_modes(3, 0.5, 2.5)
+    model = wl.spin_boson(0.5, 0.5, w, c)
+    om = oracle_lib.OracleModel(model)
+    init = wl.sb_init(model, beta=beta)
+    oi = oracle_lib.OracleInit(om, init)
+    n = 200_000
+    st = oracle_lib.sample(om, oi, 9, 0, n)
+    k = model["mass"] * w**2
+    for j in range(3):
+        dR = st.R[:, j] - init["R0"][j]
+        ev = 0.5 * k[j] * dR**2
+        ek = st.P[:, j] ** 2 / (2 * model["mass"][j])
+        target = w[j] / 4 if math.isinf(beta) else 1.0 / (2 * beta)
+        for x in (ev, ek):
+            assert abs(x.mean() - target) < 4 * x.std() / math.sqrt(n) + (
+                0 if math.isinf(beta) else 2e-4 * target)
+        # Box-Muller gives Gaussian marginals
+        z = dR / dR.std()
+        assert stats.kstest(z, "norm").pvalue > 1e-3
+
+
+def test_initial_pair_sampling_is_unbiased(oracle_lib):
+    model = wl.random_lvc4(2)
+    om = oracle_lib.OracleModel(model)
+    rng = np.random.default_rng(8)
+    B = rng.normal(size=(4, 4))
+    rho = B @ B.T
+    rho /= np.trace(rho)
+    R0 = _random_R(model, rng)
+    init = {"rho_el0": rho, "R0": R0, "P0": np.zeros(model["n_modes"]), "beta": math.inf,
+            "wigner": 0}
+    oi = oracle_lib.OracleInit(om, init)
+    n = 200_000
+    st = oracle_lib.sample(om, oi, 4, 0, n)
+    _, U, _ = oracle_lib.adiabatic(om, R0)
+    _, U_np = indep.eigh_aligned(model, R0)
+    U_np = U_np * _gauge_signs(U, U_np)
+    rho_ad = U_np.T @ rho @ U_np
+    est = np.zeros((4, 4))
+    est2 = np.zeros((4, 4))
+    np.add.at(est, (st.alpha, st.beta), st.m)
+    np.add.at(est2, (st.alpha, st.beta), st.m**2)
+    mean = est / n
+    se = np.sqrt(np.maximum(est2 / n - mean**2, 0) / n)
+    assert np.all(np.abs(mean - rho_ad) < 4 * se + 1e-9)
+
+
+# ------------------------------------------------------ branch enumeration --
+def _enumerate(oracle_lib, om, model, R0, P0, rho_el0, dt, k):
+    """Exact expectation of every observable after 0..k steps from one
+    phase-space point: every branch (stay, or each event with p_hat > 0)
+    carries its own trajectory and weight (product of event amplitudes)."""
+    ns = model["n_states"]
+    nq = 4 * ns * ns
+    e, U, _ = oracle_lib.adiabatic(om, R0)
+    rho_ad = U.T @ rho_el0 @ U
+    tot = np.abs(rho_ad).sum()
+    T0 = np.floor(np.abs(rho_ad) / tot * 2**24)
+    exp_rows = np.zeros((k + 1, nq))
+    branches = []
+    for a in range(ns):
+        for b in range(ns):
+            if rho_ad[a, b] != 0 and T0[a, b] > 0:
+                branches.append((R0.copy(), P0.copy(), 0.0, a, b, rho_ad[a, b]))
+
+    def obs(R, a, b, w, phi):
+        _, Uo, _ = oracle_lib.adiabatic(om, R)
+        z = w * np.exp(-1j * phi)
+        q = np.zeros(nq)
+        for i in range(ns):
+            for j in range(ns):
+                v = z * Uo[i, a] * Uo[j, b]
+                q[2 * (i * ns + j)] = v.real
+                q[2 * (i * ns + j) + 1] = v.imag
+        q[2 * ns * ns + 2 * (a * ns + b)] = z.real
+        q[2 * ns * ns + 2 * (a * ns + b) + 1] = z.imag
+        return q
+
+    for br in branches:
+        exp_rows[0] += obs(br[0], br[3], br[4], br[5], br[2])
+    for n in range(1, k + 1):
+        nxt = []
+        for R, P, phi, a, b, w in branches:
+            R1, P1, phi1, _ = oracle_lib.step_deterministic(om, R, P, phi, a, b, None, dt)
+            e1, U1, _ = oracle_lib.adiabatic(om, R1)
+            ta, tb, A, T = oracle_lib.events(om, P1, e1, U1, a, b, dt)
+            nxt.append((R1, P1, phi1, a, b, w))
+            for t in range(len(A)):
+                if T[t] > 0:
+                    nxt.append((R1, P1, phi1, int(ta[t]), int(tb[t]), w * A[t]))
+        branches = nxt
+        for R, P, phi, a, b, w in branches:
+            exp_rows[n] += obs(R, a, b, w, phi)
+    return exp_rows
+
+
+def test_stochastic_walkers_match_branch_enumeration(oracle_lib):
+    model = wl.spin_boson(0.0, 0.5, [1.0], [1.0])
+    model["hop_scale"] = 1.0
+    om = oracle_lib.OracleModel(model)
+    R0, P0 = np.array([0.1]), np.array([2.0])
+    rho = np.array([[1.0, 0.0], [0.0, 0.0]])
+    init = {"rho_el0": rho, "R0": R0, "P0": P0, "beta": math.inf, "wigner": 0}
+    oi = oracle_lib.OracleInit(om, init)
+    dt, k, n = 0.05, 6, 400_000
+    exact = _enumerate(oracle_lib, om, model, R0, P0, rho, dt, k)
+    rows, _ = oracle_lib.run(om, oi, 21, 0, n, dt, k, 1)
+    mean, se = oracle_lib.finalize(rows, n)
+    z = np.abs(mean - exact) / np.maximum(se, 1e-15)
+    assert np.all((z < 4.5) | (np.abs(mean - exact) < 1e-12)), z.max()
+    # hops really happened: some branch weights moved into the coherences
+    assert np.abs(exact[k, 2 * 4 + 2:2 * 4 + 4]).max() > 1e-3
+
+
+# ---------------------------------------------- ensemble-level invariants --
+def test_trace_and_hermiticity_config1(oracle_lib):
+    cfg = wl.config(1)
+    om = oracle_lib.OracleModel(cfg["model"])
+    oi = oracle_lib.OracleInit(om, cfg["init"])
+    rows, ndeg = oracle_lib.run(om, oi, cfg["seed"], 0, cfg["n_traj"], cfg["dt"], cfg["n_steps"],
+                                cfg["out_stride"])
+    mean, se = oracle_lib.finalize(rows, cfg["n_traj"])
+    assert ndeg == 0
+    tr = mean[:, 0] + mean[:, 6]
+    tr_se = se[:, 0] + se[:, 6]
+    assert np.all(np.abs(tr - 1.0) < 4 * tr_se + 1e-12)
+    assert abs(tr[0] - 1.0) < 0.05
+    tri = mean[:, 1] + mean[:, 7]
+    assert np.all(np.abs(tri) < 4 * (se[:, 1] + se[:, 7]) + 1e-12)
+    d_re = mean[:, 2] - mean[:, 4]
+    d_im = mean[:, 3] + mean[:, 5]
+    assert np.all(np.abs(d_re) < 4 * (se[:, 2] + se[:, 4]) + 1e-12)
+    assert np.all(np.abs(d_im) < 4 * (se[:, 3] + se[:, 5]) + 1e-12)
+
+
+def test_standard_error_falls_as_inverse_sqrt_n(oracle_lib):
+    cfg = wl.config(1)
+    om = oracle_lib.OracleModel(cfg["model"])
+    oi = oracle_lib.OracleInit(om, cfg["init"])
+    ns = [1000, 4000, 16000, 64000]
+    ses = []
+    for n in ns:
+        rows, _ = oracle_lib.run(om, oi, 1, 0, n, 0.01, 100, 100)
+        _, se = oracle_lib.finalize(rows, n)
+        ses.append(se[-1])
+    ses = np.array(ses)
+    good = np.all(ses > 0, axis=0)
+    slopes = [np.polyfit(np.log(ns), np.log(ses[:, q]), 1)[0] for q in np.where(good)[0]]
+    assert abs(np.median(slopes) + 0.5) < 0.05, slopes
+
+
+def test_run_equals_sample_advance_observe(oracle_lib):
+    cfg = wl.config(2)
+    om = oracle_lib.OracleModel(cfg["model"])
+    oi = oracle_lib.OracleInit(om, cfg["init"])
+    rows, _ = oracle_lib.run(om, oi, 2, 100, 300, 0.01, 50, 25)
+    st = oracle_lib.sample(om, oi, 2, 100, 300)
+    r0 = oracle_lib.observe(om, st)
+    oracle_lib.advance(om, st, 2, 100, 0, 25, 0.01)
+    r1 = oracle_lib.observe(om, st)
+    oracle_lib.advance(om, st, 2, 100, 25, 25, 0.01)
+    r2 = oracle_lib.observe(om, st)
+    assert np.array_equal(rows, np.stack([r0, r1, r2]))
