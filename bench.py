@@ -1,0 +1,357 @@
+"""Benchmark: trajectory-steps/s of the FP32-bulk QCL ensemble propagation on
+the 3-mode ohmic spin-boson workload (1e7 walkers, 2000 steps), beside the
+FP64 one-launch-per-step comparator and the CPU FP64 oracle.
+
+One timed step = one complete solve: initial Wigner sample, 2000 propagation
+steps with in-kernel observation every 10 steps, and the ensemble reduction.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun (N > 1) every rank propagates its own 1e7 walkers (global ids
+offset by rank), so the per-GPU work is fixed (weak scaling); rank 0 prints
+one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2608_14544_gb300 import workloads as wl  # noqa: E402
+
+WORKLOAD = 2
+METRIC = "trajectory-steps/s (FP32-bulk, served form) at stated error"
+
+
+def _workload_desc(cfg):
+    return (f"3-mode ohmic spin-boson (eps=0.5, Delta=0.5, xi=0.5, wc=2.5, beta=5), "
+            f"{cfg['n_traj']:.0e} walkers, dt={cfg['dt']}, {cfg['n_steps']} steps, "
+            f"output every {cfg['out_stride']} steps")
+
+
+def flops_per_traj_step(model: dict) -> float:
+    """Algorithmic FP32 flops of one walker step of a two-state model: per mode
+    two half kicks, a drift and the collective sums (7 FMA for the spin-boson
+    form, 11 FMA + 2 ADD for the general two-state form), plus 20 scalar flops."""
+    K = model["K"]
+    s = 0.5 * (K[:, 0, 0] + K[:, 1, 1])
+    b = K[:, 0, 1]
+    general = bool(np.any(s != 0) or np.any(b != 0))
+    per_mode = 24.0 if general else 14.0
+    return per_mode * model["n_modes"] + 20.0
+
+
+# ------------------------------------------------------------------- clocks --
+class ClockSampler:
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            p = [x.strip() for x in ln.split(",")]
+            if len(p) < 8:
+                continue
+            try:
+                sm.append(float(p[0]))
+                mx.append(float(p[1]))
+            except ValueError:
+                continue
+            for k, nm in enumerate(names):
+                if p[4 + k].lower() in ("active", "0x1", "1"):
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(mx)),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ------------------------------------------------------------- CPU oracle --
+def cpu_oracle_rate(cfg, target_s: float, threads: int):
+    """The FP64 oracle as it stands on the host cores: a bounded sample of the
+    same workload (all steps, fewer walkers), trajectory-steps/s."""
+    import oracle
+
+    oracle.build()
+    om = oracle.OracleModel(cfg["model"])
+    oi = oracle.OracleInit(om, cfg["init"])
+    steps = cfg["n_steps"]
+    t0 = time.perf_counter()
+    probe = 64
+    oracle.run(om, oi, cfg["seed"], 0, probe, cfg["dt"], steps, cfg["out_stride"])
+    per_walker = (time.perf_counter() - t0) / probe
+    n = max(threads, int(target_s * threads / max(per_walker, 1e-9)))
+    t0 = time.perf_counter()
+    oracle.run_threaded(om, oi, cfg["seed"], n, cfg["dt"], steps, cfg["out_stride"], threads)
+    el = time.perf_counter() - t0
+    return n * steps / el, n, el
+
+
+# ---------------------------------------------------------------- reference --
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    cfg = wl.config(WORKLOAD)
+    threads = os.cpu_count() or 1
+    import oracle
+
+    oracle.build()
+    om = oracle.OracleModel(cfg["model"])
+    oi = oracle.OracleInit(om, cfg["init"])
+    steps = cfg["n_steps"]
+    # size one step to about 4 s of host work
+    t0 = time.perf_counter()
+    oracle.run(om, oi, 0, 0, 32, cfg["dt"], steps, cfg["out_stride"])
+    per_walker = (time.perf_counter() - t0) / 32
+    n = max(threads, int(4.0 * threads / max(per_walker, 1e-9)))
+    for _ in range(args.warmup):
+        oracle.run_threaded(om, oi, cfg["seed"], n, cfg["dt"], steps, cfg["out_stride"], threads)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        oracle.run_threaded(om, oi, cfg["seed"], n, cfg["dt"], steps, cfg["out_stride"], threads)
+    el = time.perf_counter() - t0
+    value = n * steps * args.steps / el
+    sample = f"{n} walkers x {steps} steps per timed step (of {cfg['n_traj']:.0e} walkers)"
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "traj-steps/s",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * el / max(args.steps, 1), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": _workload_desc(cfg), "n_traj_sampled": n},
+        "cpu_baseline": {"value": value, "unit": "traj-steps/s", "cores": threads,
+                         "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": "traj-steps/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }), flush=True)
+
+
+# ---------------------------------------------------------------------- ours --
+def run_ours(args):
+    import torch
+
+    from paper_2608_14544_gb300 import build as qbuild
+    from paper_2608_14544_gb300 import qcl
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(0)
+    if rank == 0 or world == 1:
+        qbuild.build()
+    if dist:
+        dist.barrier()
+    qcl.load()
+
+    cfg = wl.config(WORKLOAD)
+    n, steps, stride, dt = cfg["n_traj"], cfg["n_steps"], cfg["out_stride"], cfg["dt"]
+    n_out = steps // stride + 1
+    model = qcl.Model(cfg["model"])
+    run = qcl.Run(model, n, cfg["seed"], qcl.PREC_FP32_BULK, n_out, traj_id_offset=rank * n)
+    stream = torch.cuda.current_stream()
+
+    def solve():
+        run.sample(cfg["init"])
+        run.propagate(steps, dt, stride)
+        # ensemble reduction into the device rows is part of propagate; the
+        # finalisation of means/SE runs on the device and is read back here
+        return run.observables()
+
+    for _ in range(max(args.warmup, 0)):
+        solve()
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    qcl.launch_count(reset=True)
+    qcl.kernel_time(qcl.KERNEL_BULK)
+    qcl.set_option(qcl.OPT_TIMING, 1)
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        torch.cuda.synchronize()
+        ev0.record(stream)
+        for _ in range(args.steps):
+            obs = solve()
+        ev1.record(stream)
+        torch.cuda.synchronize()
+    qcl.set_option(qcl.OPT_TIMING, 0)
+    launches = qcl.launch_count()
+    bulk_ms, bulk_n = qcl.kernel_time(qcl.KERNEL_BULK)
+    el_ms = ev0.elapsed_time(ev1)
+    if dist:
+        t = torch.tensor([el_ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        el_ms = float(t.item())
+    traj_steps = float(n) * steps * args.steps * world
+    value = traj_steps / (el_ms / 1e3)
+    status = run.status()
+
+    # FP64 comparator: the paper's structure (one launch per step, SoA in HBM),
+    # same walkers, a bounded number of steps
+    fp64_steps = 100
+    run64 = qcl.Run(model, n, cfg["seed"], qcl.PREC_FP64, fp64_steps // stride + 1,
+                    traj_id_offset=rank * n)
+    run64.sample(cfg["init"])
+    run64.propagate(stride, dt, stride)
+    torch.cuda.synchronize()
+    qcl.kernel_time(qcl.KERNEL_FP64_STEP)
+    qcl.set_option(qcl.OPT_TIMING, 1)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    run64.propagate(fp64_steps - stride, dt, stride)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    qcl.set_option(qcl.OPT_TIMING, 0)
+    f64_ms, f64_n = qcl.kernel_time(qcl.KERNEL_FP64_STEP)
+    fp64_rate = float(n) * (fp64_steps - stride) / (e0.elapsed_time(e1) / 1e3)
+    del run64
+
+    # end to end through the C ABI with host buffers: model upload, sample,
+    # propagate, device reduction and the copy of the observables to the host
+    m = cfg["model"]
+    h2d = sum(np.asarray(m[k], dtype=np.float64).nbytes for k in ("mass", "omega", "E", "K"))
+    h2d += sum(np.asarray(cfg["init"][k], dtype=np.float64).nbytes for k in ("rho_el0", "R0", "P0"))
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        mm = qcl.Model(m)
+        rr = qcl.Run(mm, n, cfg["seed"], qcl.PREC_FP32_BULK, n_out, traj_id_offset=rank * n)
+        rr.sample(cfg["init"])
+        rr.propagate(steps, dt, stride)
+        host_obs = rr.observables()
+        del rr
+        mm.close()
+    torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t0
+    if dist:
+        t = torch.tensor([e2e_s], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    e2e = {"value": traj_steps / e2e_s, "unit": "traj-steps/s", "h2d_bytes_per_step": int(h2d),
+           "d2h_bytes_per_step": int(host_obs.nbytes)}
+
+    if rank != 0:
+        if dist:
+            dist.destroy_process_group()
+        return
+
+    # roofline of the dominant kernel (FP32 ALU bound)
+    props = torch.cuda.get_device_properties(0)
+    n_sm = props.multi_processor_count
+    peaks_path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    max_mhz = 2070.0
+    if os.path.exists(peaks_path):
+        max_mhz = float(json.load(open(peaks_path)).get("sm_max_mhz", max_mhz))
+    clocks = clk.summary()
+    if clocks and clocks.get("sm_max_mhz"):
+        max_mhz = clocks["sm_max_mhz"]
+    peak_tflops = n_sm * 128 * 2 * max_mhz * 1e6 / 1e12
+    fl = flops_per_traj_step(m)
+    achieved = float(n) * steps * args.steps * fl / (bulk_ms / 1e3) / 1e12 if bulk_ms > 0 else None
+    cpu_threads = os.cpu_count() or 1
+    cpu_rate, cpu_n, cpu_s = cpu_oracle_rate(cfg, args.cpu_seconds, cpu_threads)
+
+    mean = obs[:, :16]
+    out = {
+        "metric": METRIC, "value": value, "unit": "traj-steps/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": el_ms / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic",
+        "config": {"workload": _workload_desc(cfg), "n_traj_per_gpu": n, "n_steps": steps,
+                   "out_stride": stride, "precision": "FP32 bulk, compensated phase/weight, "
+                   "FP64 reduction", "l2": "inputs larger than L2 (walker state "
+                   f"{qcl.ensemble_bytes(model, run.ens) / 1e6:.0f} MB resident in HBM)",
+                   "parallelism": f"walkers sharded over {world} GPU(s)"},
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_tflops,
+                     "unit": "TFLOP/s", "frac": (achieved / peak_tflops) if achieved else None,
+                     "traffic": None,
+                     "kernel": "k_bulk2 (persistent FP32-bulk walker kernel)",
+                     "flops_per_traj_step": fl,
+                     "peak_basis": f"{n_sm} SMs x 128 FP32 lanes x 2 flop x {max_mhz:.0f} MHz",
+                     "kernel_ms_per_launch": bulk_ms / max(bulk_n, 1),
+                     "launches": bulk_n},
+        "cpu_baseline": {"value": cpu_rate, "unit": "traj-steps/s", "cores": cpu_threads,
+                         "kind": "oracle",
+                         "sample": f"{cpu_n} walkers x {steps} steps of the same workload "
+                                   f"({cpu_s:.1f} s)"},
+        "e2e": e2e,
+        "gpu_launches": launches,
+        "fp64_comparator": {"value": fp64_rate, "unit": "traj-steps/s",
+                            "sample": f"{n:.0e} walkers x {fp64_steps - stride} steps, one "
+                                      "launch per step", "step_kernel_ms": f64_ms / max(f64_n, 1),
+                            "speedup_of_fp32_bulk": value / world / fp64_rate},
+        "clocks": clocks,
+        "result": {"P_ad_upper_t_end": float(mean[-1, 14]),
+                   "rho11_minus_rho22_t_end": float(mean[-1, 0] - mean[-1, 6]),
+                   "trace_t_end": float(obs[-1, 32]), "status_flags": status["flags"]},
+    }
+    print(json.dumps(out), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

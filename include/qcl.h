@@ -1,0 +1,232 @@
+/*
+ * qcl.h -- C ABI of the GB300 engine for momentum-jump-free mixed
+ * quantum-classical Liouville (QCL) dynamics.
+ *
+ * The engine estimates the density matrix of Eq. 1 (paper Sec. II A),
+ *   d/dt rho_ab = -i w_ab rho_ab - (P/M) sum_g (d_ag rho_gb - rho_ag d_gb)
+ *                 - (P/M) d rho_ab/dR - 1/2 (F_a + F_b) d rho_ab/dP ,
+ * with a fixed, pre-allocated ensemble of walkers (Sec. II B: no spawning).
+ * Each walker carries nuclear (R, P), an adiabatic index pair (a, b) and a
+ * complex weight m exp(-i phi).  One step is: velocity Verlet on the mean force
+ * -1/2 (F_a + F_b) (no momentum jump), the phase -i w_ab by the trapezoid rule,
+ * and one stochastic index transition drawn from the coupling term of Eq. 1
+ * with weight correction.  Outputs are ensemble averages of the diabatic and
+ * adiabatic density matrices (the adiabatic excited-state population P_ad of
+ * Sec. III is one of them).
+ *
+ * Conventions shared by every call:
+ *  - Every call returns a qcl_status; QCL_OK is 0.  No C++ exception crosses
+ *    the boundary.  qcl_last_error() gives a message for the calling thread.
+ *  - "Device" pointers are CUDA global-memory addresses on the current device;
+ *    "host" pointers are ordinary CPU memory.  The caller owns every device
+ *    buffer passed in (ensemble and observation buffers); the library owns only
+ *    the model's constant block (allocated by qcl_create_model).
+ *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *    stream).  Calls that take a stream only enqueue work and return; results
+ *    are valid after the stream is synchronised.  Calls without a stream that
+ *    return data to the host (qcl_reduce_observables, qcl_ensemble_status)
+ *    synchronise the stream they are given.
+ *  - Random numbers: Philox4x32-10 (Salmon et al., SC'11), key = (seed low
+ *    word, seed high word), counter = (c0, traj low word, traj high word,
+ *    purpose), traj = traj_id_offset + walker index.  Purpose 1 (initial
+ *    sample): c0 = j gives the Box-Muller pair of mode j, c0 = N gives word 0
+ *    for the index pair.  Purpose 2 (transition of step n): c0 = n >> 2, word
+ *    n & 3.  A walker's stream depends only on (seed, traj, step), so results
+ *    do not depend on launch shape, chunking or sharding.
+ */
+#ifndef QCL_H
+#define QCL_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int32_t qcl_status;
+#define QCL_OK 0
+#define QCL_ERR_INVALID_ARG 1  /* a size, pointer or parameter is out of range */
+#define QCL_ERR_UNSUPPORTED 2  /* valid but not built: n_states > 8, n_modes > 256, ... */
+#define QCL_ERR_OUT_OF_MEMORY 3 /* a buffer is smaller than the size query asks for,
+                                   or the server's arena is full */
+#define QCL_ERR_CUDA 4         /* a CUDA runtime call failed (message has the name) */
+#define QCL_ERR_TIMEOUT 5      /* a bounded wait ran out */
+#define QCL_ERR_NUMERICAL 6    /* a non-finite value or a degenerate gap was seen */
+#define QCL_ERR_BUSY 7         /* the server queue is full */
+#define QCL_ERR_NOT_FOUND 8    /* unknown request id */
+
+/* Working precision of an ensemble. */
+#define QCL_PREC_FP64 0        /* everything in FP64: one kernel launch per step (comparator) */
+#define QCL_PREC_FP32_BULK 1   /* FP32 Verlet/force/coupling, phase and weight carried as
+                                  compensated FP32 pairs, FP64 ensemble reduction;
+                                  persistent register-resident kernel */
+
+#define QCL_MAX_STATES 8
+#define QCL_MAX_MODES 256
+
+/* Linear vibronic-coupling model (the spin-boson and vibronic systems of Sec.
+ * II C are instances): V(R) = 1/2 sum_j M_j w_j^2 R_j^2 + W(R),
+ * W(R) = E + sum_j R_j K_j; E and each K_j are real symmetric
+ * n_states x n_states, row-major; K is [n_modes][n_states * n_states].  All
+ * arrays are host memory, copied by qcl_create_model.  hop_scale (kappa, > 0)
+ * and p_max (in (0, 1)) shape the transition probabilities
+ * p_e = min(kappa |A_e|, p_max), scaled down together when their sum exceeds
+ * p_max; 0 selects the defaults 1 and 0.5. */
+typedef struct {
+  int32_t n_states;
+  int32_t n_modes;
+  double hbar;
+  const double* mass;
+  const double* omega;
+  const double* E;
+  const double* K;
+  double hop_scale;
+  double p_max;
+} qcl_model_desc;
+
+typedef struct qcl_model qcl_model; /* opaque */
+
+/* Identity of an ensemble: walker count, Philox seed, global id of walker 0
+ * (for sharding) and working precision.  The same descriptor must be given to
+ * every call on the same ensemble buffer. */
+typedef struct {
+  int64_t n_traj;
+  uint64_t seed;
+  uint64_t traj_id_offset;
+  int32_t precision;
+  int32_t reserved;
+} qcl_ensemble_desc;
+
+/* Initial condition (host memory): diabatic electronic density rho_el0
+ * (real symmetric [n_states * n_states], not all zero); each mode's Wigner
+ * distribution of the harmonic thermal state at inverse temperature beta
+ * (INFINITY = ground state), centred at (R0_j, P0_j):
+ *   var R_j = hbar/(2 M_j w_j) coth(beta hbar w_j/2), var P_j = hbar M_j w_j/2 coth(...).
+ * wigner = 0 starts every walker exactly at (R0, P0).  The index pair is drawn
+ * from |rho_ad_ab| / sum |rho_ad| with rho_ad = U(R)^T rho_el0 U(R) at the
+ * walker's own R (probabilities quantised to 2^-24), and m0 = rho_ad_ab / p_ab. */
+typedef struct {
+  const double* rho_el0;
+  const double* R0;
+  const double* P0;
+  double beta;
+  int32_t wigner;
+  int32_t reserved;
+} qcl_init_desc;
+
+/* Status words kept in the ensemble buffer's header. */
+typedef struct {
+  int64_t step;          /* absolute step the ensemble has reached */
+  uint32_t flags;        /* bit 0: non-finite value, bit 1: degenerate gap,
+                            bit 2: step0 did not match the ensemble's step */
+  uint32_t reserved;
+  uint64_t n_degenerate; /* walker-steps that met a degenerate gap (coupling set to 0) */
+  uint64_t n_nonfinite;  /* walkers that produced a non-finite value */
+} qcl_ens_status;
+
+#define QCL_FLAG_NONFINITE 1u
+#define QCL_FLAG_DEGENERATE 2u
+#define QCL_FLAG_STEP_MISMATCH 4u
+
+/* Message for the last failing call on this thread ("" if none). */
+const char* qcl_last_error(void);
+
+/* Library version string. */
+const char* qcl_version(void);
+
+/* Validates the model (sizes, symmetry, finiteness, positive masses and
+ * frequencies), derives its constants and copies them to a device block owned
+ * by the returned handle (on the current device).  *out is NULL on failure. */
+qcl_status qcl_create_model(const qcl_model_desc* d, qcl_model** out);
+
+/* Frees the handle and its device block.  NULL is accepted. */
+qcl_status qcl_destroy_model(qcl_model* model);
+
+/* Bytes of device memory the ensemble buffer needs (256-byte aligned SoA:
+ * header, R and P as [n_modes][n_traj], weight, phase, index pair). */
+qcl_status qcl_ensemble_bytes(const qcl_model* model, const qcl_ensemble_desc* ens,
+                              size_t* bytes);
+
+/* Bytes of device memory an observation buffer for n_out output times needs
+ * (FP64 rows of sums, per-tile FP64 partials, finalised means). */
+qcl_status qcl_obs_bytes(const qcl_model* model, const qcl_ensemble_desc* ens, int64_t n_out,
+                         size_t* bytes);
+
+/* Initial sample (Sec. II B: walkers pre-allocated, state in contiguous
+ * arrays).  Writes every walker and the header (step 0) of ens_buf. */
+qcl_status qcl_sample_initial(const qcl_model* model, const qcl_ensemble_desc* ens,
+                              const qcl_init_desc* init, void* ens_buf, size_t ens_bytes,
+                              void* stream);
+
+/* Advances every walker from absolute step step0 (must equal the ensemble's
+ * step, else QCL_FLAG_STEP_MISMATCH is set and nothing moves) by n_steps of
+ * length dt.  At each absolute step s with s % out_stride == 0 and
+ * step0 < s <= step0 + n_steps (and at s = 0 when step0 == 0) it writes output
+ * row k = s / out_stride (k < n_out) of obs_buf: the FP64 sums over walkers of
+ * every observable contribution and of its square, added in a fixed tree
+ * (32-walker groups, 256-walker tiles, tiles in index order), so that results
+ * do not depend on the launch shape and two calls give the same bits as one.
+ * FP64 ensembles launch one kernel per step; FP32-bulk ensembles run a
+ * persistent kernel over 256-walker tiles with state held in registers. */
+qcl_status qcl_propagate(const qcl_model* model, const qcl_ensemble_desc* ens, void* ens_buf,
+                         size_t ens_bytes, int64_t step0, int64_t n_steps, double dt,
+                         int32_t out_stride, void* obs_buf, size_t obs_bytes, int64_t n_out,
+                         void* stream);
+
+/* Ensemble averages (divide by n_traj) of the output rows [k0, k0 + n_rows),
+ * computed on the device and copied to host_out (synchronises `stream`).
+ * Per row, with NS = n_states and Q = 4 NS^2 quantities:
+ *   [0, Q)      means: q = 2(i NS + j) + c, diabatic rho_ij (c = 0 real, 1 imag);
+ *               q = 2 NS^2 + 2(a NS + b) + c, adiabatic rho_ab
+ *   [Q, 2Q)     standard errors sqrt((S2 - S^2/N) / (N (N - 1))) of the same
+ *   2Q, 2Q+1    trace of the diabatic matrix (real, imaginary)
+ *   2Q + 2      walker count N
+ * host_len must be at least n_rows * (2Q + 3). */
+qcl_status qcl_reduce_observables(const qcl_model* model, const qcl_ensemble_desc* ens,
+                                  const void* obs_buf, size_t obs_bytes, int64_t n_out,
+                                  int64_t k0, int64_t n_rows, double* host_out, size_t host_len,
+                                  void* stream);
+
+/* Copies the raw FP64 sum rows [k0, k0 + n_rows) (2Q doubles each: sums, then
+ * sums of squares) to host memory (synchronises `stream`); used to combine
+ * shards. */
+qcl_status qcl_read_sums(const qcl_model* model, const qcl_ensemble_desc* ens,
+                         const void* obs_buf, size_t obs_bytes, int64_t n_out, int64_t k0,
+                         int64_t n_rows, double* host_out, size_t host_len, void* stream);
+
+/* Byte offsets of the ensemble buffer's arrays: [0] R, [1] P, [2] weight
+ * (FP64 value, or FP32 high part), [3] FP32 weight low part, [4] phase (FP64, or
+ * FP32 high part), [5] FP32 phase low part, [6] index pair (uint16: a | b << 8),
+ * [7] total bytes.  R and P are [n_modes][n_traj]; element size 8 (FP64) or 4. */
+qcl_status qcl_ensemble_layout(const qcl_model* model, const qcl_ensemble_desc* ens,
+                               size_t offsets[8]);
+
+/* Reads the ensemble header's status words (synchronises `stream`). */
+qcl_status qcl_ensemble_status(const qcl_model* model, const qcl_ensemble_desc* ens,
+                               const void* ens_buf, size_t ens_bytes, qcl_ens_status* out,
+                               void* stream);
+
+/* ----------------------------------------------------------- instrumentation
+ * Process-wide options:
+ *   QCL_OPT_GRID_CAP  cap on the persistent grid (0: SMs x resident blocks);
+ *                     results do not depend on it (fixed reduction tree)
+ *   QCL_OPT_TIMING    1: record a CUDA event pair on the launching stream around
+ *                     every persistent-kernel and FP64 step-kernel launch */
+#define QCL_OPT_GRID_CAP 1
+#define QCL_OPT_TIMING 2
+qcl_status qcl_set_option(int32_t key, int64_t value);
+
+/* Kernel launches made by the library since the last reset; resets the counter
+ * when reset != 0. */
+qcl_status qcl_launch_count(int64_t* count, int32_t reset);
+
+/* Device time recorded under QCL_OPT_TIMING for kernel class `which`
+ * (0: FP32-bulk persistent kernel, 1: FP64 step kernel): total milliseconds and
+ * launch count.  Synchronises the recorded events, then clears them. */
+qcl_status qcl_kernel_time(int32_t which, double* total_ms, int64_t* launches);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* QCL_H */

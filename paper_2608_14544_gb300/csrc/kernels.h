@@ -1,0 +1,75 @@
+// kernels.h -- host-side declarations of the kernel launchers and their
+// parameter blocks (passed by value as kernel parameters).
+#pragma once
+#include <cuda_runtime.h>
+
+#include "qcl_common.cuh"
+
+namespace qcl {
+
+struct SampleParams {
+  int64_t n_traj;
+  uint64_t traj_offset;
+  uint64_t seed;
+  int32_t n, ns;
+  int32_t wigner;
+  int32_t pad;
+  double R0[kMaxN], P0[kMaxN], sR[kMaxN], sP[kMaxN];
+  double rho[kMaxNS * kMaxNS];
+};
+
+// FP32 per-mode coefficients of a two-state model for one time step dt.
+struct Coef2 {
+  float hk[kMaxN];   // dt/2 * k_j
+  float hs[kMaxN];   // dt/2 * s_j
+  float dtm[kMaxN];  // dt / M_j
+  float a[kMaxN];    // d a / d R_j
+  float b[kMaxN];    // d b / d R_j
+  float am[kMaxN];   // a_j / M_j
+  float bm[kMaxN];   // b_j / M_j
+};
+
+struct BulkParams {
+  int64_t n_traj;
+  int64_t n_tiles;
+  uint64_t traj_offset;
+  uint64_t seed;
+  int64_t step0;       // ensemble step expected at the start of the call
+  int64_t cs, ce;      // absolute steps [cs, ce) advanced by this launch
+  int64_t k_first;     // absolute output index of slot 0
+  int32_t stride;      // output stride
+  int32_t obs_first;   // observe at cs before stepping (only at s = 0)
+  int32_t n;           // modes
+  int32_t kind;        // 0: a_j only (spin-boson form), 1: general two-state
+  float a0, b0;
+  float dt, hdt;       // dt, dt/2
+  float hdt_hbar;      // dt / (2 hbar)
+  float kdt;           // hop_scale * dt
+  float p_max;
+  float pad;
+};
+
+// Kernel launches issued by the library (instrumentation).
+void launches_add(int64_t k);
+int64_t launches_read(bool reset);
+
+void launch_sample_f64(const DevModel* dm, const SampleParams& sp, void* buf, cudaStream_t st);
+void launch_step_f64(const DevModel* dm, void* buf, int64_t nt, int n, int64_t step0,
+                     int64_t step, double dt, uint64_t seed, uint64_t traj_off, cudaStream_t st);
+void launch_observe_f64(const DevModel* dm, const void* buf, int64_t nt, int n, double* part,
+                        cudaStream_t st);
+
+void launch_sample_f32(const DevModel* dm, const SampleParams& sp, void* buf, cudaStream_t st);
+// Returns the persistent grid size used (0 on launch failure).
+int launch_bulk2(const BulkParams& bp, const Coef2& cf, void* buf, double* part, int grid_cap,
+                 cudaStream_t st);
+// Kernel-selection description of the bulk kernel chosen for (n, kind).
+const char* bulk2_variant(int n, int kind);
+
+void launch_fold(const double* part, double* rows_out, double* scratch, int64_t n_tiles,
+                 int q2, int n_slots, cudaStream_t st);
+void launch_finalize(const double* rows, double* fin, int nq, int64_t k0, int64_t nrows,
+                     int64_t n_traj, int ns, cudaStream_t st);
+void launch_header_finish(void* buf, int64_t step0, int64_t step1, cudaStream_t st);
+
+}  // namespace qcl

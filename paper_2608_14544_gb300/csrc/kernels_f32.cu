@@ -1,0 +1,420 @@
+// kernels_f32.cu -- FP32-bulk path: a persistent kernel in which each thread
+// owns one walker for a whole chunk of steps with its state in registers.
+// Verlet, forces and couplings run in FP32; the phase and the weight are
+// carried as compensated FP32 pairs (about 46 significant bits) so that no
+// FP64 instruction sits in the step loop; observations are reduced per tile in
+// FP64.  Random numbers: one Philox4x32-10 call per four steps.
+#include <atomic>
+#include <cstdio>
+
+#include "kernels.h"
+#include "reduce.cuh"
+
+namespace qcl {
+
+namespace {
+
+// 2 pi = C1 + C2 + C3 with C1, C2 of 14 significant bits (k * C exact for |k| < 2^10)
+constexpr float kTwoPi1 = 6.283203125f;
+constexpr float kTwoPi2 = -1.7818063497543335e-05f;
+constexpr float kTwoPi3 = 2.430840251310684e-10f;
+constexpr float kInvTwoPi = 0.15915494309189535f;
+constexpr float kDegTol32 = 1e-6f;  // |e_b - e_a| below this: coupling set to 0
+
+struct W32 {
+  float* R;
+  float* P;
+  float* mh;
+  float* ml;
+  float* ph;
+  float* pl;
+  uint16_t* ab;
+  EnsHeader* hdr;
+};
+
+__device__ __forceinline__ W32 view32(void* buf, int64_t nt, int ns, int n) {
+  const EnsLayout L = EnsLayout::make(nt, ns, n, QCL_PREC_FP32_BULK);
+  char* b = (char*)buf;
+  return {(float*)(b + L.off_R),   (float*)(b + L.off_P),     (float*)(b + L.off_m),
+          (float*)(b + L.off_mlo), (float*)(b + L.off_phi),   (float*)(b + L.off_philo),
+          (uint16_t*)(b + L.off_ab), (EnsHeader*)b};
+}
+
+__device__ __forceinline__ float sgn(int idx) { return idx ? 1.0f : -1.0f; }
+
+}  // namespace
+
+// ---------------------------------------------------------------- sampling --
+// FP32 initial sample from the same Philox words as the FP64 path.
+__global__ void __launch_bounds__(256) k_sample_f32(const DevModel* __restrict__ M,
+                                                    SampleParams sp, void* buf) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t nt = sp.n_traj;
+  const int n = sp.n;
+  W32 w = view32(buf, nt, 2, n);
+  if (i == 0) {
+    w.hdr->magic = kEnsMagic;
+    w.hdr->n_traj = nt;
+    w.hdr->precision = QCL_PREC_FP32_BULK;
+    w.hdr->ns = 2;
+    w.hdr->n = n;
+    w.hdr->step = 0;
+    w.hdr->flags = 0;
+    w.hdr->n_degenerate = 0;
+    w.hdr->n_nonfinite = 0;
+  }
+  if (i >= nt) return;
+  const uint64_t traj = sp.traj_offset + (uint64_t)i;
+  float a = (float)M->a0, b = (float)M->b0;
+  for (int j = 0; j < n; ++j) {
+    float R = (float)sp.R0[j], P = (float)sp.P0[j];
+    if (sp.wigner) {
+      const u4 wd = philox_draw(sp.seed, (uint32_t)j, traj, kPurposeInit);
+      const float u0 = __fmaf_rn(__uint2float_rn(wd.x), 0x1p-32f, 0x1p-33f);
+      const float u1 = __fmaf_rn(__uint2float_rn(wd.y), 0x1p-32f, 0x1p-33f);
+      const float rad = sqrtf(-2.0f * logf(u0));
+      float sn, cs;
+      sincospif(2.0f * u1, &sn, &cs);
+      R = __fmaf_rn((float)sp.sR[j] * rad, cs, R);
+      P = __fmaf_rn((float)sp.sP[j] * rad, sn, P);
+    }
+    w.R[(int64_t)j * nt + i] = R;
+    w.P[(int64_t)j * nt + i] = P;
+    a = __fmaf_rn((float)M->a[j], R, a);
+    b = __fmaf_rn((float)M->b[j], R, b);
+  }
+  const float r2 = a * a + b * b;
+  float c = 1.0f, s = 0.0f;
+  if (r2 > 0.0f) {
+    const float ir = rsqrtf(r2);
+    const float c2 = a * ir, s2 = b * ir;
+    if (a >= 0.0f) {
+      c = sqrtf(0.5f + 0.5f * c2);
+      s = 0.5f * s2 / c;
+    } else {
+      s = copysignf(sqrtf(0.5f - 0.5f * c2), b);
+      c = 0.5f * s2 / s;
+    }
+  }
+  const float U[4] = {-s, c, c, s};
+  double rho_ad[4];
+  double tot = 0.0;
+  for (int al = 0; al < 2; ++al)
+    for (int be = 0; be < 2; ++be) {
+      float acc = 0.0f;
+      for (int k = 0; k < 2; ++k)
+        for (int l = 0; l < 2; ++l)
+          acc = __fmaf_rn(U[k * 2 + al] * (float)sp.rho[k * 2 + l], U[l * 2 + be], acc);
+      rho_ad[al * 2 + be] = acc;
+      tot += fabsf(acc);
+    }
+  // index pair from |rho_ad| with 2^-24 quantised probabilities (remainder to the
+  // last nonzero pair), m0 = rho_ad / p_hat
+  uint32_t Tk[4];
+  uint32_t sumT = 0;
+  int last = 0;
+  for (int k = 0; k < 4; ++k) {
+    Tk[k] = (uint32_t)floorf((float)(fabs(rho_ad[k]) / tot) * kP24f);
+    sumT += Tk[k];
+    if (rho_ad[k] != 0.0) last = k;
+  }
+  Tk[last] += 16777216u - sumT;
+  const u4 wd = philox_draw(sp.seed, (uint32_t)n, traj, kPurposeInit);
+  const uint32_t y = wd.x >> 8;
+  uint32_t cum = 0;
+  int pick = last;
+  for (int k = 0; k < 4; ++k) {
+    cum += Tk[k];
+    if (y < cum) {
+      pick = k;
+      break;
+    }
+  }
+  w.mh[i] = (float)rho_ad[pick] * (kP24f / (float)Tk[pick]);
+  w.ml[i] = 0.0f;
+  w.ph[i] = 0.0f;
+  w.pl[i] = 0.0f;
+  w.ab[i] = (uint16_t)((pick >> 1) | ((pick & 1) << 8));
+}
+
+// ------------------------------------------------------- persistent step --
+template <int NPL, int KIND>
+struct Walker {
+  float R[NPL], P[NPL];
+};
+
+template <int NPL, int KIND>
+__device__ __forceinline__ void decomp(const Walker<NPL, KIND>& w, const BulkParams& bp,
+                                       const Coef2& cf, float& A, float& B) {
+  A = bp.a0;
+  B = bp.b0;
+#pragma unroll
+  for (int j = 0; j < NPL; ++j) {
+    A = __fmaf_rn(cf.a[j], w.R[j], A);
+    if (KIND == 1) B = __fmaf_rn(cf.b[j], w.R[j], B);
+  }
+}
+
+// P += dt/2 F_ab(R),  F_j = -k_j R_j - s_j - sab (a_j cos2t + b_j sin2t)
+template <int NPL, int KIND>
+__device__ __forceinline__ void kick(Walker<NPL, KIND>& w, const Coef2& cf, float hu, float hv) {
+#pragma unroll
+  for (int j = 0; j < NPL; ++j) {
+    float p = __fmaf_rn(-cf.hk[j], w.R[j], w.P[j]);
+    if (KIND == 1) p -= cf.hs[j];
+    p = __fmaf_rn(-hu, cf.a[j], p);
+    if (KIND == 1) p = __fmaf_rn(-hv, cf.b[j], p);
+    w.P[j] = p;
+  }
+}
+
+template <int NPL, int KIND>
+__global__ void __launch_bounds__(256, 3)
+    k_bulk2(const BulkParams bp, const Coef2 cf, void* buf, double* __restrict__ part) {
+  __shared__ double red[8][32];
+  W32 ws = view32(buf, bp.n_traj, 2, bp.n);
+  if (ws.hdr->step != bp.step0) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) atomicOr(&ws.hdr->flags, QCL_FLAG_STEP_MISMATCH);
+    return;
+  }
+  const int64_t nt = bp.n_traj;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  unsigned long long n_deg = 0;
+
+  for (int64_t tile = blockIdx.x; tile < bp.n_tiles; tile += gridDim.x) {
+    const int64_t i = tile * kTile + threadIdx.x;
+    const bool active = i < nt;
+    const int64_t ii = active ? i : 0;
+    Walker<NPL, KIND> w;
+#pragma unroll
+    for (int j = 0; j < NPL; ++j) {
+      const bool on = active && j < bp.n;
+      w.R[j] = on ? ws.R[(int64_t)j * nt + ii] : 0.0f;
+      w.P[j] = on ? ws.P[(int64_t)j * nt + ii] : 0.0f;
+    }
+    f2 m = {active ? ws.mh[ii] : 0.0f, active ? ws.ml[ii] : 0.0f};
+    f2 ph = {active ? ws.ph[ii] : 0.0f, active ? ws.pl[ii] : 0.0f};
+    const uint32_t ab = active ? ws.ab[ii] : 0u;
+    int al = ab & 0xff, be = (ab >> 8) & 0xff;
+    const uint64_t traj = bp.traj_offset + (uint64_t)ii;
+
+    float A, B;
+    decomp<NPL, KIND>(w, bp, cf, A, B);
+    float r2 = __fmaf_rn(A, A, B * B);
+    float ir = rsqrtf(r2);
+    float r = r2 * ir;
+
+    // observation into slot `slot` of the tile partials
+    auto observe = [&](int slot) {
+      // phase reduced to [-pi, pi] in compensated arithmetic
+      const float kq = rintf(ph.hi * kInvTwoPi);
+      ph = df_add(ph, -kq * kTwoPi1);
+      ph = df_add(ph, -kq * kTwoPi2);
+      ph = df_add(ph, -kq * kTwoPi3);
+      float sh, chh;
+      sincosf(ph.hi, &sh, &chh);
+      const float cphi = __fmaf_rn(-ph.lo, sh, chh);
+      const float sphi = __fmaf_rn(ph.lo, chh, sh);
+      float c = 1.0f, s = 0.0f;
+      if (r2 > 0.0f) {
+        const float c2 = A * ir, s2 = B * ir;
+        if (A >= 0.0f) {
+          c = sqrtf(0.5f + 0.5f * c2);
+          s = 0.5f * s2 / c;
+        } else {
+          s = copysignf(sqrtf(0.5f - 0.5f * c2), B);
+          c = 0.5f * s2 / s;
+        }
+      }
+      const float ua0 = al ? c : -s, ua1 = al ? s : c;  // column alpha of U
+      const float ub0 = be ? c : -s, ub1 = be ? s : c;  // column beta of U
+      const float mm = active ? m.hi : 0.0f;
+      const float zr = mm * cphi, zi = -mm * sphi;
+      float v[32];
+      const float f00 = ua0 * ub0, f01 = ua0 * ub1, f10 = ua1 * ub0, f11 = ua1 * ub1;
+      v[0] = zr * f00;
+      v[1] = zi * f00;
+      v[2] = zr * f01;
+      v[3] = zi * f01;
+      v[4] = zr * f10;
+      v[5] = zi * f10;
+      v[6] = zr * f11;
+      v[7] = zi * f11;
+      const int k = al * 2 + be;
+#pragma unroll
+      for (int kk = 0; kk < 4; ++kk) {
+        v[8 + 2 * kk] = (kk == k) ? zr : 0.0f;
+        v[9 + 2 * kk] = (kk == k) ? zi : 0.0f;
+      }
+#pragma unroll
+      for (int q = 0; q < 16; ++q) v[16 + q] = v[q] * v[q];
+      const float x = warp_transpose_sum<float>(v);
+      red[warp][lane] = (double)x;
+      __syncthreads();
+      if (threadIdx.x < 32)
+        part[((int64_t)slot * bp.n_tiles + tile) * 32 + threadIdx.x] =
+            tile_tree8(&red[0][0], 32, threadIdx.x);
+      __syncthreads();
+    };
+
+    if (bp.obs_first) observe(0);
+
+    u4 wd = philox_draw(bp.seed, (uint32_t)(bp.cs >> 2), traj, kPurposeHop);
+    for (int64_t s = bp.cs; s < bp.ce; ++s) {
+      if ((s & 3) == 0 && s != bp.cs) wd = philox_draw(bp.seed, (uint32_t)(s >> 2), traj, kPurposeHop);
+      const float sab = 0.5f * (sgn(al) + sgn(be));
+      const float sd = sgn(al) - sgn(be);
+      // first half kick at R_n
+      {
+        const float u = (r2 > 0.0f) ? A * ir : 1.0f;
+        const float v = (r2 > 0.0f) ? B * ir : 0.0f;
+        kick<NPL, KIND>(w, cf, bp.hdt * sab * u, bp.hdt * sab * v);
+      }
+      // drift
+#pragma unroll
+      for (int j = 0; j < NPL; ++j) w.R[j] = __fmaf_rn(cf.dtm[j], w.P[j], w.R[j]);
+      const float r_old = r;
+      decomp<NPL, KIND>(w, bp, cf, A, B);
+      r2 = __fmaf_rn(A, A, B * B);
+      ir = rsqrtf(r2);
+      r = r2 * ir;
+      // second half kick at R_{n+1}
+      {
+        const float u = (r2 > 0.0f) ? A * ir : 1.0f;
+        const float v = (r2 > 0.0f) ? B * ir : 0.0f;
+        kick<NPL, KIND>(w, cf, bp.hdt * sab * u, bp.hdt * sab * v);
+      }
+      // phase (trapezoid): dt/2 (w_ab(R_n) + w_ab(R_{n+1})), hbar w_ab = (sig_a - sig_b) r
+      ph = df_add(ph, bp.hdt_hbar * sd * (r_old + r));
+      // coupling contracted with P/M: g = (a Bv - b Av) / (2 r^2)
+      float Av = 0.0f, Bv = 0.0f;
+#pragma unroll
+      for (int j = 0; j < NPL; ++j) {
+        Av = __fmaf_rn(cf.am[j], w.P[j], Av);
+        if (KIND == 1) Bv = __fmaf_rn(cf.bm[j], w.P[j], Bv);
+      }
+      const bool degen = 2.0f * r < kDegTol32;
+      n_deg += (degen && active) ? 1ull : 0ull;
+      const float g = degen ? 0.0f : (A * Bv - B * Av) * (0.5f * ir * ir);
+      // both events have |A_e| = dt |g|: p = min(kappa dt |g|, p_max), halved
+      // together when their sum exceeds p_max; thresholds quantised to 2^-24
+      float p = fminf(bp.kdt * fabsf(g), bp.p_max);
+      if (2.0f * p > bp.p_max) p = 0.5f * bp.p_max;
+      const uint32_t T = __float2uint_rz(p * kP24f);
+      const uint32_t y = word_of(wd, (int)(s & 3)) >> 8;
+      const bool hop1 = y < T;
+      const bool hop2 = !hop1 && (y < 2u * T);
+      const float dtg = bp.dt * g;
+      // weight factor: A_e / p_hat on a hop, 1 / (1 - sum p_hat) otherwise
+      const float num = hop1 ? -sgn(al) * dtg * kP24f : (hop2 ? -sgn(be) * dtg * kP24f : kP24f);
+      const float den = (hop1 || hop2) ? (float)T : (float)(16777216u - 2u * T);
+      float q0, q1;
+      df_div(num, den, q0, q1);
+      m = df_mul(m, q0, q1);
+      al ^= hop1 ? 1 : 0;
+      be ^= hop2 ? 1 : 0;
+      if ((s + 1) % bp.stride == 0) observe((int)((s + 1) / bp.stride - bp.k_first));
+    }
+    if (active) {
+#pragma unroll
+      for (int j = 0; j < NPL; ++j)
+        if (j < bp.n) {
+          ws.R[(int64_t)j * nt + i] = w.R[j];
+          ws.P[(int64_t)j * nt + i] = w.P[j];
+        }
+      ws.mh[i] = m.hi;
+      ws.ml[i] = m.lo;
+      ws.ph[i] = ph.hi;
+      ws.pl[i] = ph.lo;
+      ws.ab[i] = (uint16_t)(al | (be << 8));
+      if (!isfinite(m.hi) || !isfinite(ph.hi)) {
+        atomicAdd(&ws.hdr->n_nonfinite, 1ull);
+        atomicOr(&ws.hdr->flags, QCL_FLAG_NONFINITE);
+      }
+    }
+  }
+  if (n_deg) {
+    atomicAdd(&ws.hdr->n_degenerate, n_deg);
+    atomicOr(&ws.hdr->flags, QCL_FLAG_DEGENERATE);
+  }
+}
+
+// ------------------------------------------------------------------ launch --
+namespace {
+std::atomic<int64_t> g_launches{0};
+}
+void launches_add(int64_t k) { g_launches.fetch_add(k, std::memory_order_relaxed); }
+int64_t launches_read(bool reset) {
+  return reset ? g_launches.exchange(0) : g_launches.load();
+}
+
+void launch_sample_f32(const DevModel* dm, const SampleParams& sp, void* buf, cudaStream_t st) {
+  const int64_t nb = (sp.n_traj + 255) / 256;
+  k_sample_f32<<<(unsigned)(nb > 0 ? nb : 1), 256, 0, st>>>(dm, sp, buf);
+  launches_add(1);
+}
+
+namespace {
+using BulkFn = void (*)(const BulkParams, const Coef2, void*, double*);
+
+template <int NPL, int KIND>
+int run_bulk(const BulkParams& bp, const Coef2& cf, void* buf, double* part, int grid_cap,
+             cudaStream_t st) {
+  static int per_sm = -1, n_sm = 0;
+  BulkFn fn = k_bulk2<NPL, KIND>;
+  if (per_sm < 0) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, 256, 0) != cudaSuccess ||
+        per_sm < 1)
+      per_sm = 1;
+  }
+  int64_t grid = (int64_t)per_sm * n_sm;
+  if (grid_cap > 0 && grid > grid_cap) grid = grid_cap;
+  if (grid > bp.n_tiles) grid = bp.n_tiles;
+  if (grid < 1) grid = 1;
+  fn<<<(unsigned)grid, 256, 0, st>>>(bp, cf, buf, part);
+  launches_add(1);
+  return (int)grid;
+}
+
+template <int KIND>
+int dispatch_n(const BulkParams& bp, const Coef2& cf, void* buf, double* part, int cap,
+               cudaStream_t st) {
+  const int n = bp.n;
+  if (n <= 1) return run_bulk<1, KIND>(bp, cf, buf, part, cap, st);
+  if (n <= 2) return run_bulk<2, KIND>(bp, cf, buf, part, cap, st);
+  if (n <= 3) return run_bulk<3, KIND>(bp, cf, buf, part, cap, st);
+  if (n <= 4) return run_bulk<4, KIND>(bp, cf, buf, part, cap, st);
+  if (n <= 6) return run_bulk<6, KIND>(bp, cf, buf, part, cap, st);
+  if (n <= 8) return run_bulk<8, KIND>(bp, cf, buf, part, cap, st);
+  if (n <= 12) return run_bulk<12, KIND>(bp, cf, buf, part, cap, st);
+  if (n <= 16) return run_bulk<16, KIND>(bp, cf, buf, part, cap, st);
+  if (n <= 24) return run_bulk<24, KIND>(bp, cf, buf, part, cap, st);
+  if (n <= 32) return run_bulk<32, KIND>(bp, cf, buf, part, cap, st);
+  return 0;
+}
+}  // namespace
+
+int launch_bulk2(const BulkParams& bp, const Coef2& cf, void* buf, double* part, int grid_cap,
+                 cudaStream_t st) {
+  return bp.kind == 0 ? dispatch_n<0>(bp, cf, buf, part, grid_cap, st)
+                      : dispatch_n<1>(bp, cf, buf, part, grid_cap, st);
+}
+
+const char* bulk2_variant(int n, int kind) {
+  (void)kind;
+  return n <= 32 ? "k_bulk2<register-resident, 1 thread per walker>" : "unsupported";
+}
+
+__global__ void k_header_finish(EnsHeader* h, int64_t step0, int64_t step1) {
+  if (h->step == step0) h->step = step1;
+}
+
+void launch_header_finish(void* buf, int64_t step0, int64_t step1, cudaStream_t st) {
+  k_header_finish<<<1, 1, 0, st>>>((EnsHeader*)buf, step0, step1);
+  launches_add(1);
+}
+
+}  // namespace qcl

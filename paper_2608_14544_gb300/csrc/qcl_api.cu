@@ -1,0 +1,503 @@
+// qcl_api.cu -- host implementation of the C ABI declared in include/qcl.h:
+// argument validation, buffer sizing, model constants, and the launch
+// sequences of the FP64 comparator and the FP32-bulk persistent path.
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "kernels.h"
+
+using namespace qcl;
+
+struct qcl_model {
+  int ns = 0, n = 0;
+  double hbar = 1.0, hop_scale = 1.0, p_max = 0.5;
+  std::vector<double> mass, omega, E, K;
+  DevModel host{};
+  DevModel* dev = nullptr;  // device block: DevModel followed by K
+  int device = 0;
+};
+
+namespace {
+
+thread_local std::string g_err;
+int64_t g_opt_grid_cap = 0;
+bool g_opt_timing = false;
+std::mutex g_tmu;
+std::vector<std::pair<cudaEvent_t, cudaEvent_t>> g_events[2];
+
+// Event pair around one launch of kernel class `which` when timing is on.
+struct TimedLaunch {
+  int which;
+  cudaStream_t s;
+  cudaEvent_t a = nullptr, b = nullptr;
+  TimedLaunch(int w, cudaStream_t st) : which(w), s(st) {
+    if (!g_opt_timing) return;
+    cudaEventCreate(&a);
+    cudaEventCreate(&b);
+    cudaEventRecord(a, s);
+  }
+  ~TimedLaunch() {
+    if (!a) return;
+    cudaEventRecord(b, s);
+    std::lock_guard<std::mutex> lk(g_tmu);
+    g_events[which].push_back({a, b});
+  }
+};
+
+qcl_status fail(qcl_status st, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  g_err = buf;
+  return st;
+}
+
+qcl_status ok() {
+  g_err.clear();
+  return QCL_OK;
+}
+
+#define CUDA_TRY(call)                                                                  \
+  do {                                                                                  \
+    cudaError_t e_ = (call);                                                            \
+    if (e_ != cudaSuccess)                                                              \
+      return fail(QCL_ERR_CUDA, "%s failed: %s", #call, cudaGetErrorString(e_));        \
+  } while (0)
+
+qcl_status check_launch(const char* what) {
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return fail(QCL_ERR_CUDA, "%s launch failed: %s", what, cudaGetErrorString(e));
+  return QCL_OK;
+}
+
+bool finite_all(const double* p, size_t n) {
+  for (size_t i = 0; i < n; ++i)
+    if (!std::isfinite(p[i])) return false;
+  return true;
+}
+
+bool symmetric(const double* A, int ns) {
+  for (int i = 0; i < ns; ++i)
+    for (int j = 0; j < i; ++j) {
+      const double x = A[i * ns + j], y = A[j * ns + i];
+      if (std::fabs(x - y) > 1e-12 * (1.0 + std::fabs(x) + std::fabs(y))) return false;
+    }
+  return true;
+}
+
+qcl_status check_ens(const qcl_model* m, const qcl_ensemble_desc* e) {
+  if (!m) return fail(QCL_ERR_INVALID_ARG, "model is NULL");
+  if (!e) return fail(QCL_ERR_INVALID_ARG, "ensemble descriptor is NULL");
+  if (e->n_traj < 1) return fail(QCL_ERR_INVALID_ARG, "n_traj must be >= 1 (got %lld)", (long long)e->n_traj);
+  if (e->n_traj > (int64_t)1 << 40) return fail(QCL_ERR_INVALID_ARG, "n_traj too large");
+  if (e->precision != QCL_PREC_FP64 && e->precision != QCL_PREC_FP32_BULK)
+    return fail(QCL_ERR_INVALID_ARG, "unknown precision %d", e->precision);
+  if (m->ns != 2) return fail(QCL_ERR_UNSUPPORTED, "only two-state models are built (n_states = %d)", m->ns);
+  if (e->precision == QCL_PREC_FP32_BULK && m->n > 32)
+    return fail(QCL_ERR_UNSUPPORTED, "FP32-bulk path supports n_modes <= 32 (got %d)", m->n);
+  return QCL_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* qcl_last_error(void) { return g_err.c_str(); }
+
+const char* qcl_version(void) { return "qcl-gb300 0.1 (sm_103a)"; }
+
+qcl_status qcl_set_option(int32_t key, int64_t value) {
+  if (key == QCL_OPT_GRID_CAP) {
+    if (value < 0) return fail(QCL_ERR_INVALID_ARG, "grid cap must be >= 0");
+    g_opt_grid_cap = value;
+    return ok();
+  }
+  if (key == QCL_OPT_TIMING) {
+    g_opt_timing = value != 0;
+    return ok();
+  }
+  return fail(QCL_ERR_INVALID_ARG, "unknown option %d", key);
+}
+
+qcl_status qcl_launch_count(int64_t* count, int32_t reset) {
+  if (!count) return fail(QCL_ERR_INVALID_ARG, "count is NULL");
+  *count = launches_read(reset != 0);
+  return ok();
+}
+
+qcl_status qcl_kernel_time(int32_t which, double* total_ms, int64_t* launches) {
+  if (which < 0 || which > 1) return fail(QCL_ERR_INVALID_ARG, "unknown kernel class %d", which);
+  if (!total_ms || !launches) return fail(QCL_ERR_INVALID_ARG, "NULL output");
+  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev;
+  {
+    std::lock_guard<std::mutex> lk(g_tmu);
+    ev.swap(g_events[which]);
+  }
+  double tot = 0.0;
+  qcl_status st = QCL_OK;
+  for (auto& p : ev) {
+    float ms = 0.f;
+    cudaError_t e = cudaEventSynchronize(p.second);
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, p.first, p.second);
+    if (e != cudaSuccess && st == QCL_OK) st = fail(QCL_ERR_CUDA, "event timing failed: %s", cudaGetErrorString(e));
+    tot += ms;
+    cudaEventDestroy(p.first);
+    cudaEventDestroy(p.second);
+  }
+  *total_ms = tot;
+  *launches = (int64_t)ev.size();
+  return st ? st : ok();
+}
+
+qcl_status qcl_ensemble_layout(const qcl_model* model, const qcl_ensemble_desc* ens, size_t offsets[8]) {
+  if (!offsets) return fail(QCL_ERR_INVALID_ARG, "offsets is NULL");
+  qcl_status st = check_ens(model, ens);
+  if (st) return st;
+  const EnsLayout L = EnsLayout::make(ens->n_traj, model->ns, model->n, ens->precision);
+  offsets[0] = L.off_R;
+  offsets[1] = L.off_P;
+  offsets[2] = L.off_m;
+  offsets[3] = L.off_mlo;
+  offsets[4] = L.off_phi;
+  offsets[5] = L.off_philo;
+  offsets[6] = L.off_ab;
+  offsets[7] = L.total;
+  return ok();
+}
+
+qcl_status qcl_create_model(const qcl_model_desc* d, qcl_model** out) {
+  if (!out) return fail(QCL_ERR_INVALID_ARG, "out is NULL");
+  *out = nullptr;
+  if (!d) return fail(QCL_ERR_INVALID_ARG, "model descriptor is NULL");
+  const int ns = d->n_states, n = d->n_modes;
+  if (ns < 2 || ns > QCL_MAX_STATES) return fail(ns < 2 ? QCL_ERR_INVALID_ARG : QCL_ERR_UNSUPPORTED, "n_states = %d outside [2, %d]", ns, QCL_MAX_STATES);
+  if (n < 1 || n > QCL_MAX_MODES) return fail(n < 1 ? QCL_ERR_INVALID_ARG : QCL_ERR_UNSUPPORTED, "n_modes = %d outside [1, %d]", n, QCL_MAX_MODES);
+  if (!d->mass || !d->omega || !d->E || !d->K) return fail(QCL_ERR_INVALID_ARG, "a model array is NULL");
+  if (!(d->hbar > 0.0) || !std::isfinite(d->hbar)) return fail(QCL_ERR_INVALID_ARG, "hbar must be positive");
+  const double hop = d->hop_scale == 0.0 ? 1.0 : d->hop_scale;
+  const double pmax = d->p_max == 0.0 ? 0.5 : d->p_max;
+  if (!(hop > 0.0) || !std::isfinite(hop)) return fail(QCL_ERR_INVALID_ARG, "hop_scale must be positive");
+  if (!(pmax > 0.0 && pmax < 1.0)) return fail(QCL_ERR_INVALID_ARG, "p_max must lie in (0, 1)");
+  for (int j = 0; j < n; ++j) {
+    if (!(d->mass[j] > 0.0) || !std::isfinite(d->mass[j])) return fail(QCL_ERR_INVALID_ARG, "mass[%d] must be positive", j);
+    if (!(d->omega[j] > 0.0) || !std::isfinite(d->omega[j])) return fail(QCL_ERR_INVALID_ARG, "omega[%d] must be positive", j);
+  }
+  const size_t nn = (size_t)ns * ns;
+  if (!finite_all(d->E, nn) || !finite_all(d->K, nn * n)) return fail(QCL_ERR_INVALID_ARG, "E or K has a non-finite entry");
+  if (!symmetric(d->E, ns)) return fail(QCL_ERR_INVALID_ARG, "E is not symmetric");
+  for (int j = 0; j < n; ++j)
+    if (!symmetric(d->K + nn * j, ns)) return fail(QCL_ERR_INVALID_ARG, "K[%d] is not symmetric", j);
+
+  qcl_model* m = new (std::nothrow) qcl_model();
+  if (!m) return fail(QCL_ERR_OUT_OF_MEMORY, "host allocation failed");
+  m->ns = ns;
+  m->n = n;
+  m->hbar = d->hbar;
+  m->hop_scale = hop;
+  m->p_max = pmax;
+  m->mass.assign(d->mass, d->mass + n);
+  m->omega.assign(d->omega, d->omega + n);
+  m->E.assign(d->E, d->E + nn);
+  m->K.assign(d->K, d->K + nn * n);
+  DevModel& h = m->host;
+  h.ns = ns;
+  h.n = n;
+  h.hbar = d->hbar;
+  h.hop_scale = hop;
+  h.p_max = pmax;
+  bool general = false;
+  if (ns == 2) {
+    // W = s 1 + a sigma_z + b sigma_x,  a = (W00 - W11)/2, b = W01, s = (W00 + W11)/2
+    h.a0 = 0.5 * (d->E[0] - d->E[3]);
+    h.b0 = d->E[1];
+    h.s0 = 0.5 * (d->E[0] + d->E[3]);
+  }
+  for (int j = 0; j < n; ++j) {
+    h.mass[j] = d->mass[j];
+    h.omega[j] = d->omega[j];
+    h.k[j] = d->mass[j] * d->omega[j] * d->omega[j];
+    if (ns == 2) {
+      const double* Kj = d->K + 4 * j;
+      h.a[j] = 0.5 * (Kj[0] - Kj[3]);
+      h.b[j] = Kj[1];
+      h.s[j] = 0.5 * (Kj[0] + Kj[3]);
+      if (h.b[j] != 0.0 || h.s[j] != 0.0) general = true;
+    }
+  }
+  for (size_t k = 0; k < nn; ++k) h.E[k] = d->E[k];
+  h.kind = general ? 1 : 0;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  m->device = dev;
+  char* blk = nullptr;
+  const size_t bytes = sizeof(DevModel) + sizeof(double) * nn * n;
+  cudaError_t e = cudaMalloc((void**)&blk, bytes);
+  if (e != cudaSuccess) {
+    delete m;
+    return fail(e == cudaErrorMemoryAllocation ? QCL_ERR_OUT_OF_MEMORY : QCL_ERR_CUDA, "cudaMalloc of the model block failed: %s", cudaGetErrorString(e));
+  }
+  h.K = (const double*)(blk + sizeof(DevModel));
+  e = cudaMemcpy(blk, &h, sizeof(DevModel), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(blk + sizeof(DevModel), d->K, sizeof(double) * nn * n, cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) {
+    cudaFree(blk);
+    delete m;
+    return fail(QCL_ERR_CUDA, "copy of the model block failed: %s", cudaGetErrorString(e));
+  }
+  m->dev = (DevModel*)blk;
+  *out = m;
+  return ok();
+}
+
+qcl_status qcl_destroy_model(qcl_model* model) {
+  if (!model) return ok();
+  if (model->dev) cudaFree(model->dev);
+  delete model;
+  return ok();
+}
+
+qcl_status qcl_ensemble_bytes(const qcl_model* model, const qcl_ensemble_desc* ens, size_t* bytes) {
+  if (!bytes) return fail(QCL_ERR_INVALID_ARG, "bytes is NULL");
+  qcl_status st = check_ens(model, ens);
+  if (st) return st;
+  *bytes = EnsLayout::make(ens->n_traj, model->ns, model->n, ens->precision).total;
+  return ok();
+}
+
+qcl_status qcl_obs_bytes(const qcl_model* model, const qcl_ensemble_desc* ens, int64_t n_out, size_t* bytes) {
+  if (!bytes) return fail(QCL_ERR_INVALID_ARG, "bytes is NULL");
+  qcl_status st = check_ens(model, ens);
+  if (st) return st;
+  if (n_out < 1) return fail(QCL_ERR_INVALID_ARG, "n_out must be >= 1");
+  *bytes = ObsLayout::make(ens->n_traj, model->ns, n_out).total;
+  return ok();
+}
+
+qcl_status qcl_sample_initial(const qcl_model* model, const qcl_ensemble_desc* ens, const qcl_init_desc* init,
+                              void* ens_buf, size_t ens_bytes, void* stream) {
+  qcl_status st = check_ens(model, ens);
+  if (st) return st;
+  if (!init || !init->rho_el0 || !init->R0 || !init->P0) return fail(QCL_ERR_INVALID_ARG, "init descriptor or one of its arrays is NULL");
+  if (!ens_buf) return fail(QCL_ERR_INVALID_ARG, "ens_buf is NULL");
+  if (((uintptr_t)ens_buf & 255) != 0) return fail(QCL_ERR_INVALID_ARG, "ens_buf must be 256-byte aligned");
+  const size_t need = EnsLayout::make(ens->n_traj, model->ns, model->n, ens->precision).total;
+  if (ens_bytes < need) return fail(QCL_ERR_OUT_OF_MEMORY, "ens_buf has %zu bytes, needs %zu", ens_bytes, need);
+  const int ns = model->ns, n = model->n;
+  if (!finite_all(init->rho_el0, (size_t)ns * ns) || !symmetric(init->rho_el0, ns)) return fail(QCL_ERR_INVALID_ARG, "rho_el0 must be finite and symmetric");
+  bool nz = false;
+  for (int k = 0; k < ns * ns; ++k) nz |= init->rho_el0[k] != 0.0;
+  if (!nz) return fail(QCL_ERR_INVALID_ARG, "rho_el0 is zero");
+  if (!finite_all(init->R0, n) || !finite_all(init->P0, n)) return fail(QCL_ERR_INVALID_ARG, "R0 or P0 has a non-finite entry");
+  if (init->wigner && !(init->beta > 0.0)) return fail(QCL_ERR_INVALID_ARG, "beta must be positive (INFINITY for the ground state)");
+  SampleParams* sp = new (std::nothrow) SampleParams();
+  if (!sp) return fail(QCL_ERR_OUT_OF_MEMORY, "host allocation failed");
+  sp->n_traj = ens->n_traj;
+  sp->traj_offset = ens->traj_id_offset;
+  sp->seed = ens->seed;
+  sp->n = n;
+  sp->ns = ns;
+  sp->wigner = init->wigner ? 1 : 0;
+  for (int j = 0; j < n; ++j) {
+    const double M = model->mass[j], w = model->omega[j], hb = model->hbar;
+    const double cth = std::isinf(init->beta) ? 1.0 : 1.0 / std::tanh(0.5 * init->beta * hb * w);
+    sp->R0[j] = init->R0[j];
+    sp->P0[j] = init->P0[j];
+    sp->sR[j] = std::sqrt(hb / (2.0 * M * w) * cth);
+    sp->sP[j] = std::sqrt(0.5 * hb * M * w * cth);
+  }
+  for (int k = 0; k < ns * ns; ++k) sp->rho[k] = init->rho_el0[k];
+  cudaStream_t s = (cudaStream_t)stream;
+  if (ens->precision == QCL_PREC_FP64)
+    launch_sample_f64(model->dev, *sp, ens_buf, s);
+  else
+    launch_sample_f32(model->dev, *sp, ens_buf, s);
+  delete sp;
+  st = check_launch("sample");
+  return st ? st : ok();
+}
+
+qcl_status qcl_propagate(const qcl_model* model, const qcl_ensemble_desc* ens, void* ens_buf, size_t ens_bytes,
+                         int64_t step0, int64_t n_steps, double dt, int32_t out_stride, void* obs_buf,
+                         size_t obs_bytes, int64_t n_out, void* stream) {
+  qcl_status st = check_ens(model, ens);
+  if (st) return st;
+  if (!ens_buf || !obs_buf) return fail(QCL_ERR_INVALID_ARG, "ens_buf or obs_buf is NULL");
+  if (((uintptr_t)ens_buf & 255) != 0 || ((uintptr_t)obs_buf & 255) != 0) return fail(QCL_ERR_INVALID_ARG, "buffers must be 256-byte aligned");
+  if (step0 < 0 || n_steps < 0) return fail(QCL_ERR_INVALID_ARG, "step0 and n_steps must be >= 0");
+  if (step0 + n_steps >= ((int64_t)1 << 34)) return fail(QCL_ERR_INVALID_ARG, "absolute step beyond 2^34");
+  if (!(dt > 0.0) || !std::isfinite(dt)) return fail(QCL_ERR_INVALID_ARG, "dt must be positive");
+  if (out_stride < 1) return fail(QCL_ERR_INVALID_ARG, "out_stride must be >= 1");
+  if (n_out < 1) return fail(QCL_ERR_INVALID_ARG, "n_out must be >= 1");
+  const int64_t k_last = (step0 + n_steps) / out_stride;
+  if (k_last >= n_out) return fail(QCL_ERR_INVALID_ARG, "output row %lld beyond n_out = %lld", (long long)k_last, (long long)n_out);
+  const EnsLayout EL = EnsLayout::make(ens->n_traj, model->ns, model->n, ens->precision);
+  if (ens_bytes < EL.total) return fail(QCL_ERR_OUT_OF_MEMORY, "ens_buf has %zu bytes, needs %zu", ens_bytes, EL.total);
+  const ObsLayout OL = ObsLayout::make(ens->n_traj, model->ns, n_out);
+  if (obs_bytes < OL.total) return fail(QCL_ERR_OUT_OF_MEMORY, "obs_buf has %zu bytes, needs %zu", obs_bytes, OL.total);
+  cudaStream_t s = (cudaStream_t)stream;
+  char* ob = (char*)obs_buf;
+  double* rows = (double*)(ob + OL.off_rows);
+  double* part = (double*)(ob + OL.off_part);
+  double* fold = (double*)(ob + OL.off_fold);
+  const int q2 = OL.q2;
+  const int64_t nt = ens->n_traj;
+
+  if (ens->precision == QCL_PREC_FP64) {
+    if (step0 == 0) {
+      launch_observe_f64(model->dev, ens_buf, nt, model->n, part, s);
+      launch_fold(part, rows, fold, OL.n_tiles, q2, 1, s);
+    }
+    for (int64_t t = step0; t < step0 + n_steps; ++t) {
+      TimedLaunch tl(1, s);
+      launch_step_f64(model->dev, ens_buf, nt, model->n, step0, t, dt, ens->seed, ens->traj_id_offset, s);
+      if ((t + 1) % out_stride == 0) {
+        launch_observe_f64(model->dev, ens_buf, nt, model->n, part, s);
+        launch_fold(part, rows + (size_t)((t + 1) / out_stride) * q2, fold, OL.n_tiles, q2, 1, s);
+      }
+    }
+    st = check_launch("FP64 step");
+    if (st) return st;
+  } else {
+    Coef2* cf = new (std::nothrow) Coef2();
+    if (!cf) return fail(QCL_ERR_OUT_OF_MEMORY, "host allocation failed");
+    const DevModel& h = model->host;
+    for (int j = 0; j < model->n; ++j) {
+      cf->hk[j] = (float)(0.5 * dt * h.k[j]);
+      cf->hs[j] = (float)(0.5 * dt * h.s[j]);
+      cf->dtm[j] = (float)(dt / h.mass[j]);
+      cf->a[j] = (float)h.a[j];
+      cf->b[j] = (float)h.b[j];
+      cf->am[j] = (float)(h.a[j] / h.mass[j]);
+      cf->bm[j] = (float)(h.b[j] / h.mass[j]);
+    }
+    BulkParams bp{};
+    bp.n_traj = nt;
+    bp.n_tiles = OL.n_tiles;
+    bp.traj_offset = ens->traj_id_offset;
+    bp.seed = ens->seed;
+    bp.step0 = step0;
+    bp.stride = out_stride;
+    bp.n = model->n;
+    bp.kind = h.kind;
+    bp.a0 = (float)h.a0;
+    bp.b0 = (float)h.b0;
+    bp.dt = (float)dt;
+    bp.hdt = (float)(0.5 * dt);
+    bp.hdt_hbar = (float)(0.5 * dt / model->hbar);
+    bp.kdt = (float)(model->hop_scale * dt);
+    bp.p_max = (float)model->p_max;
+    // chunks of at most kChunkOut output times
+    int64_t cs = step0;
+    bool first = (step0 == 0);
+    const int64_t end = step0 + n_steps;
+    do {
+      int64_t k_first = first ? 0 : cs / out_stride + 1;
+      int n_slots = first ? 1 : 0;
+      int64_t ce = cs;
+      // extend to the (kChunkOut - n_slots)-th output step after cs, or to end
+      const int64_t next_out = (cs / out_stride + 1) * out_stride;
+      const int64_t room = kChunkOut - n_slots;
+      int64_t last_out = next_out + (room - 1) * out_stride;
+      if (last_out <= end) {
+        ce = last_out;
+        n_slots += (int)room;
+      } else {
+        ce = end;
+        if (end >= next_out) n_slots += (int)((end - next_out) / out_stride + 1);
+      }
+      if (!first && n_slots > 0) k_first = next_out / out_stride;
+      bp.cs = cs;
+      bp.ce = ce;
+      bp.k_first = k_first;
+      bp.obs_first = first ? 1 : 0;
+      int grid = 0;
+      {
+        TimedLaunch tl(0, s);
+        grid = launch_bulk2(bp, *cf, ens_buf, part, (int)g_opt_grid_cap, s);
+      }
+      if (grid == 0) {
+        delete cf;
+        return fail(QCL_ERR_UNSUPPORTED, "no FP32-bulk kernel for n_modes = %d", model->n);
+      }
+      if (n_slots > 0) launch_fold(part, rows + (size_t)k_first * q2, fold, OL.n_tiles, q2, n_slots, s);
+      first = false;
+      cs = ce;
+    } while (cs < end);
+    delete cf;
+    st = check_launch("FP32-bulk propagate");
+    if (st) return st;
+  }
+  launch_header_finish(ens_buf, step0, step0 + n_steps, s);
+  st = check_launch("header");
+  return st ? st : ok();
+}
+
+qcl_status qcl_reduce_observables(const qcl_model* model, const qcl_ensemble_desc* ens, const void* obs_buf,
+                                  size_t obs_bytes, int64_t n_out, int64_t k0, int64_t n_rows, double* host_out,
+                                  size_t host_len, void* stream) {
+  qcl_status st = check_ens(model, ens);
+  if (st) return st;
+  if (!obs_buf || !host_out) return fail(QCL_ERR_INVALID_ARG, "obs_buf or host_out is NULL");
+  if (n_out < 1 || k0 < 0 || n_rows < 0 || k0 + n_rows > n_out) return fail(QCL_ERR_INVALID_ARG, "rows [%lld, %lld) outside [0, %lld)", (long long)k0, (long long)(k0 + n_rows), (long long)n_out);
+  const ObsLayout OL = ObsLayout::make(ens->n_traj, model->ns, n_out);
+  if (obs_bytes < OL.total) return fail(QCL_ERR_OUT_OF_MEMORY, "obs_buf has %zu bytes, needs %zu", obs_bytes, OL.total);
+  const int nq = OL.q2 / 2;
+  const size_t per = (size_t)(2 * nq + 3);
+  if (host_len < per * (size_t)n_rows) return fail(QCL_ERR_INVALID_ARG, "host_out holds %zu doubles, needs %zu", host_len, per * (size_t)n_rows);
+  if (n_rows == 0) return ok();
+  cudaStream_t s = (cudaStream_t)stream;
+  const char* ob = (const char*)obs_buf;
+  double* fin = (double*)(ob + OL.off_fin);
+  launch_finalize((const double*)(ob + OL.off_rows), fin, nq, k0, n_rows, ens->n_traj, model->ns, s);
+  st = check_launch("finalize");
+  if (st) return st;
+  CUDA_TRY(cudaMemcpyAsync(host_out, fin, sizeof(double) * per * n_rows, cudaMemcpyDeviceToHost, s));
+  CUDA_TRY(cudaStreamSynchronize(s));
+  return ok();
+}
+
+qcl_status qcl_read_sums(const qcl_model* model, const qcl_ensemble_desc* ens, const void* obs_buf, size_t obs_bytes,
+                         int64_t n_out, int64_t k0, int64_t n_rows, double* host_out, size_t host_len, void* stream) {
+  qcl_status st = check_ens(model, ens);
+  if (st) return st;
+  if (!obs_buf || !host_out) return fail(QCL_ERR_INVALID_ARG, "obs_buf or host_out is NULL");
+  if (n_out < 1 || k0 < 0 || n_rows < 0 || k0 + n_rows > n_out) return fail(QCL_ERR_INVALID_ARG, "rows outside [0, n_out)");
+  const ObsLayout OL = ObsLayout::make(ens->n_traj, model->ns, n_out);
+  if (obs_bytes < OL.total) return fail(QCL_ERR_OUT_OF_MEMORY, "obs_buf has %zu bytes, needs %zu", obs_bytes, OL.total);
+  if (host_len < (size_t)OL.q2 * n_rows) return fail(QCL_ERR_INVALID_ARG, "host_out too small");
+  if (n_rows == 0) return ok();
+  cudaStream_t s = (cudaStream_t)stream;
+  const double* rows = (const double*)((const char*)obs_buf + OL.off_rows);
+  CUDA_TRY(cudaMemcpyAsync(host_out, rows + (size_t)k0 * OL.q2, sizeof(double) * OL.q2 * n_rows, cudaMemcpyDeviceToHost, s));
+  CUDA_TRY(cudaStreamSynchronize(s));
+  return ok();
+}
+
+qcl_status qcl_ensemble_status(const qcl_model* model, const qcl_ensemble_desc* ens, const void* ens_buf,
+                               size_t ens_bytes, qcl_ens_status* out, void* stream) {
+  qcl_status st = check_ens(model, ens);
+  if (st) return st;
+  if (!ens_buf || !out) return fail(QCL_ERR_INVALID_ARG, "ens_buf or out is NULL");
+  if (ens_bytes < sizeof(EnsHeader)) return fail(QCL_ERR_OUT_OF_MEMORY, "ens_buf too small");
+  EnsHeader h;
+  cudaStream_t s = (cudaStream_t)stream;
+  CUDA_TRY(cudaMemcpyAsync(&h, ens_buf, sizeof(h), cudaMemcpyDeviceToHost, s));
+  CUDA_TRY(cudaStreamSynchronize(s));
+  if (h.magic != kEnsMagic) return fail(QCL_ERR_INVALID_ARG, "ens_buf holds no sampled ensemble");
+  out->step = h.step;
+  out->flags = h.flags;
+  out->reserved = 0;
+  out->n_degenerate = h.n_degenerate;
+  out->n_nonfinite = h.n_nonfinite;
+  return ok();
+}
+
+}  // extern "C"

@@ -1,0 +1,93 @@
+// reduce.cu -- tile fold and finalisation kernels of the fixed-order ensemble
+// reduction (see reduce.cuh for the tree).
+#include "kernels.h"
+#include "reduce.cuh"
+
+namespace qcl {
+
+// One level of the tile fold: in[row][n][nq] -> out[row][ceil(n/1024)][nq].
+// Grid (ceil(n/1024), nq, rows), 32 threads: lane l reduces 32 consecutive
+// entries by a binary tree, then the warp combines lanes by a butterfly.
+__global__ void k_fold_level(const double* __restrict__ in, double* __restrict__ out, int64_t n,
+                             int nq, int64_t in_row_stride, int64_t out_row_stride) {
+  const int64_t blk = blockIdx.x;
+  const int q = blockIdx.y;
+  const int row = blockIdx.z;
+  const int lane = threadIdx.x;
+  const double* src = in + (int64_t)row * in_row_stride;
+  double v[32];
+  const int64_t base = blk * 1024 + (int64_t)lane * 32;
+#pragma unroll
+  for (int i = 0; i < 32; ++i) {
+    const int64_t t = base + i;
+    v[i] = (t < n) ? src[t * nq + q] : 0.0;
+  }
+#pragma unroll
+  for (int s = 1; s < 32; s *= 2) {
+#pragma unroll
+    for (int i = 0; i < 32; i += 2 * s) v[i] += v[i + s];
+  }
+  double x = v[0];
+#pragma unroll
+  for (int off = 1; off < 32; off *= 2) x += __shfl_xor_sync(0xffffffffu, x, off);
+  if (lane == 0) out[(int64_t)row * out_row_stride + blk * nq + q] = x;
+}
+
+// Means and standard errors of rows [k0, k0 + nrows) of sums (divide by N).
+__global__ void k_finalize(const double* __restrict__ rows, double* __restrict__ fin, int nq,
+                           int64_t k0, int64_t nrows, int64_t n_traj, int ns) {
+  const int64_t r = blockIdx.x;
+  if (r >= nrows) return;
+  const double* s = rows + (k0 + r) * 2 * nq;
+  double* o = fin + r * (2 * nq + 3);
+  const double N = (double)n_traj;
+  for (int q = threadIdx.x; q < nq; q += blockDim.x) {
+    const double S = s[q], S2 = s[nq + q];
+    o[q] = S / N;
+    const double var = fmax(S2 - S * S / N, 0.0) / fmax(N - 1.0, 1.0);
+    o[nq + q] = sqrt(var / N);
+  }
+  if (threadIdx.x == 0) {
+    double tr = 0.0, ti = 0.0;
+    for (int i = 0; i < ns; ++i) {
+      tr += s[2 * (i * ns + i)];
+      ti += s[2 * (i * ns + i) + 1];
+    }
+    o[2 * nq] = tr / N;
+    o[2 * nq + 1] = ti / N;
+    o[2 * nq + 2] = N;
+  }
+}
+
+// ------------------------------------------------------------ fold/finalize --
+void launch_fold(const double* part, double* rows_out, double* scratch, int64_t n_tiles, int q2,
+                 int n_slots, cudaStream_t st) {
+  // level 1: tiles -> 1024-tile blocks; repeat until one value per row
+  const double* in = part;
+  int64_t n = n_tiles;
+  int64_t in_stride = n_tiles * q2;
+  double* bufs[2] = {scratch, scratch + (size_t)n_slots * ((n_tiles + 1023) / 1024) * q2};
+  int which = 0;
+  while (true) {
+    const int64_t nb = (n + 1023) / 1024;
+    double* out = (nb == 1) ? rows_out : bufs[which];
+    const int64_t out_stride = (nb == 1) ? q2 : nb * q2;
+    dim3 grid((unsigned)nb, (unsigned)q2, (unsigned)n_slots);
+    k_fold_level<<<grid, 32, 0, st>>>(in, out, n, q2, in_stride, out_stride);
+    launches_add(1);
+    if (nb == 1) break;
+    in = out;
+    in_stride = out_stride;
+    n = nb;
+    which ^= 1;
+  }
+}
+
+void launch_finalize(const double* rows, double* fin, int nq, int64_t k0, int64_t nrows,
+                     int64_t n_traj, int ns, cudaStream_t st) {
+  if (nrows <= 0) return;
+  k_finalize<<<(unsigned)nrows, 64, 0, st>>>(rows, fin, nq, k0, nrows, n_traj, ns);
+  launches_add(1);
+}
+
+}  // namespace qcl

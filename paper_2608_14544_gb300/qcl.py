@@ -1,0 +1,313 @@
+"""Python binding of libqcl.so: the C ABI of include/qcl.h, one function per
+entry point with the same name.  Argument marshalling only: every step of the
+propagation runs in the library's CUDA kernels.  Device buffers are torch
+tensors (torch provides device memory and streams); host arrays are numpy.
+
+The binding fails loudly if the library is missing: there is no fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import math
+import os
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libqcl.so")
+
+QCL_OK = 0
+STATUS_NAMES = {0: "OK", 1: "INVALID_ARG", 2: "UNSUPPORTED", 3: "OUT_OF_MEMORY", 4: "CUDA",
+                5: "TIMEOUT", 6: "NUMERICAL", 7: "BUSY", 8: "NOT_FOUND"}
+PREC_FP64 = 0
+PREC_FP32_BULK = 1
+OPT_GRID_CAP = 1
+OPT_TIMING = 2
+KERNEL_BULK, KERNEL_FP64_STEP = 0, 1
+FLAG_NONFINITE, FLAG_DEGENERATE, FLAG_STEP_MISMATCH = 1, 2, 4
+
+# every entry point declared in include/qcl.h (checked by the CPU test suite)
+EXPORTS = [
+    "qcl_last_error", "qcl_version", "qcl_set_option", "qcl_launch_count", "qcl_kernel_time",
+    "qcl_create_model", "qcl_destroy_model", "qcl_ensemble_bytes", "qcl_obs_bytes",
+    "qcl_ensemble_layout", "qcl_sample_initial", "qcl_propagate", "qcl_reduce_observables",
+    "qcl_read_sums", "qcl_ensemble_status",
+]
+
+
+class QclError(RuntimeError):
+    def __init__(self, status: int, fn: str, msg: str):
+        super().__init__(f"{fn}: {STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+class ModelDesc(C.Structure):
+    _fields_ = [("n_states", C.c_int32), ("n_modes", C.c_int32), ("hbar", C.c_double),
+                ("mass", C.c_void_p), ("omega", C.c_void_p), ("E", C.c_void_p),
+                ("K", C.c_void_p), ("hop_scale", C.c_double), ("p_max", C.c_double)]
+
+
+class EnsembleDesc(C.Structure):
+    _fields_ = [("n_traj", C.c_int64), ("seed", C.c_uint64), ("traj_id_offset", C.c_uint64),
+                ("precision", C.c_int32), ("reserved", C.c_int32)]
+
+
+class InitDesc(C.Structure):
+    _fields_ = [("rho_el0", C.c_void_p), ("R0", C.c_void_p), ("P0", C.c_void_p),
+                ("beta", C.c_double), ("wigner", C.c_int32), ("reserved", C.c_int32)]
+
+
+class EnsStatus(C.Structure):
+    _fields_ = [("step", C.c_int64), ("flags", C.c_uint32), ("reserved", C.c_uint32),
+                ("n_degenerate", C.c_uint64), ("n_nonfinite", C.c_uint64)]
+
+
+_lib = None
+
+
+def load(path: str = LIB_PATH):
+    """Loads libqcl.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise ImportError(f"libqcl.so not built at {path}: run __graft_entry__.build() "
+                          "(the CUDA library is required; there is no CPU fallback)")
+    lib = C.CDLL(path)
+    vp, i32, i64, sz = C.c_void_p, C.c_int32, C.c_int64, C.c_size_t
+    lib.qcl_last_error.restype = C.c_char_p
+    lib.qcl_version.restype = C.c_char_p
+    lib.qcl_set_option.argtypes = [i32, i64]
+    lib.qcl_launch_count.argtypes = [vp, i32]
+    lib.qcl_kernel_time.argtypes = [i32, vp, vp]
+    lib.qcl_ensemble_layout.argtypes = [vp, vp, vp]
+    lib.qcl_create_model.argtypes = [vp, vp]
+    lib.qcl_destroy_model.argtypes = [vp]
+    lib.qcl_ensemble_bytes.argtypes = [vp, vp, vp]
+    lib.qcl_obs_bytes.argtypes = [vp, vp, i64, vp]
+    lib.qcl_sample_initial.argtypes = [vp, vp, vp, vp, sz, vp]
+    lib.qcl_propagate.argtypes = [vp, vp, vp, sz, i64, i64, C.c_double, i32, vp, sz, i64, vp]
+    lib.qcl_reduce_observables.argtypes = [vp, vp, vp, sz, i64, i64, i64, vp, sz, vp]
+    lib.qcl_read_sums.argtypes = [vp, vp, vp, sz, i64, i64, i64, vp, sz, vp]
+    lib.qcl_ensemble_status.argtypes = [vp, vp, vp, sz, vp, vp]
+    for name in EXPORTS:
+        f = getattr(lib, name)
+        if name not in ("qcl_last_error", "qcl_version"):
+            f.restype = i32
+    _lib = lib
+    return lib
+
+
+def _check(st: int, fn: str):
+    if st != QCL_OK:
+        raise QclError(st, fn, load().qcl_last_error().decode())
+
+
+def _f64(x):
+    return np.ascontiguousarray(np.asarray(x, dtype=np.float64))
+
+
+def _stream_ptr(stream):
+    if stream is None:
+        import torch
+
+        return torch.cuda.current_stream().cuda_stream
+    return getattr(stream, "cuda_stream", stream)
+
+
+def _dptr(t) -> int:
+    return t.data_ptr() if hasattr(t, "data_ptr") else int(t)
+
+
+def last_error() -> str:
+    return load().qcl_last_error().decode()
+
+
+def version() -> str:
+    return load().qcl_version().decode()
+
+
+def set_option(key: int, value: int):
+    _check(load().qcl_set_option(key, value), "qcl_set_option")
+
+
+def launch_count(reset: bool = False) -> int:
+    c = C.c_int64()
+    _check(load().qcl_launch_count(C.byref(c), 1 if reset else 0), "qcl_launch_count")
+    return c.value
+
+
+def kernel_time(which: int):
+    """(total ms, launches) recorded under OPT_TIMING for a kernel class."""
+    ms, n = C.c_double(), C.c_int64()
+    _check(load().qcl_kernel_time(which, C.byref(ms), C.byref(n)), "qcl_kernel_time")
+    return ms.value, n.value
+
+
+def ensemble_layout(model, ens) -> list:
+    off = (C.c_size_t * 8)()
+    _check(load().qcl_ensemble_layout(model.handle, C.byref(ens), off), "qcl_ensemble_layout")
+    return list(off)
+
+
+class Model:
+    """Owns a qcl_model handle (create_model / destroy_model)."""
+
+    def __init__(self, m: dict):
+        self.ns = int(m["n_states"])
+        self.n = int(m["n_modes"])
+        self._arrs = [_f64(m["mass"]), _f64(m["omega"]), _f64(m["E"]).reshape(-1),
+                      _f64(m["K"]).reshape(-1)]
+        d = ModelDesc(self.ns, self.n, float(m["hbar"]), *[a.ctypes.data for a in self._arrs],
+                      float(m.get("hop_scale", 1.0)), float(m.get("p_max", 0.5)))
+        h = C.c_void_p()
+        _check(load().qcl_create_model(C.byref(d), C.byref(h)), "qcl_create_model")
+        self.handle = h
+
+    def close(self):
+        if self.handle:
+            load().qcl_destroy_model(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def create_model(m: dict) -> Model:
+    return Model(m)
+
+
+def destroy_model(model: Model):
+    model.close()
+
+
+def ens_desc(n_traj: int, seed: int, precision: int, traj_id_offset: int = 0) -> EnsembleDesc:
+    return EnsembleDesc(int(n_traj), int(seed), int(traj_id_offset), int(precision), 0)
+
+
+def ensemble_bytes(model: Model, ens: EnsembleDesc) -> int:
+    b = C.c_size_t()
+    _check(load().qcl_ensemble_bytes(model.handle, C.byref(ens), C.byref(b)),
+           "qcl_ensemble_bytes")
+    return b.value
+
+
+def obs_bytes(model: Model, ens: EnsembleDesc, n_out: int) -> int:
+    b = C.c_size_t()
+    _check(load().qcl_obs_bytes(model.handle, C.byref(ens), n_out, C.byref(b)), "qcl_obs_bytes")
+    return b.value
+
+
+def sample_initial(model: Model, ens: EnsembleDesc, init: dict, ens_buf, stream=None):
+    arrs = [_f64(init["rho_el0"]).reshape(-1), _f64(init["R0"]), _f64(init["P0"])]
+    d = InitDesc(*[a.ctypes.data for a in arrs], float(init.get("beta", math.inf)),
+                 int(init.get("wigner", 1)), 0)
+    _check(load().qcl_sample_initial(model.handle, C.byref(ens), C.byref(d), _dptr(ens_buf),
+                                     ens_buf.numel() * ens_buf.element_size(),
+                                     _stream_ptr(stream)), "qcl_sample_initial")
+
+
+def propagate(model: Model, ens: EnsembleDesc, ens_buf, step0: int, n_steps: int, dt: float,
+              out_stride: int, obs_buf, n_out: int, stream=None):
+    _check(load().qcl_propagate(model.handle, C.byref(ens), _dptr(ens_buf),
+                                ens_buf.numel() * ens_buf.element_size(), step0, n_steps, dt,
+                                out_stride, _dptr(obs_buf), obs_buf.numel() * obs_buf.element_size(),
+                                n_out, _stream_ptr(stream)), "qcl_propagate")
+
+
+def reduce_observables(model: Model, ens: EnsembleDesc, obs_buf, n_out: int, k0: int = 0,
+                       n_rows: int | None = None, stream=None) -> np.ndarray:
+    n_rows = n_out - k0 if n_rows is None else n_rows
+    q = 4 * model.ns * model.ns
+    out = np.zeros((n_rows, 2 * q + 3))
+    _check(load().qcl_reduce_observables(model.handle, C.byref(ens), _dptr(obs_buf),
+                                         obs_buf.numel() * obs_buf.element_size(), n_out, k0,
+                                         n_rows, out.ctypes.data, out.size,
+                                         _stream_ptr(stream)), "qcl_reduce_observables")
+    return out
+
+
+def read_sums(model: Model, ens: EnsembleDesc, obs_buf, n_out: int, k0: int = 0,
+              n_rows: int | None = None, stream=None) -> np.ndarray:
+    n_rows = n_out - k0 if n_rows is None else n_rows
+    out = np.zeros((n_rows, 8 * model.ns * model.ns))
+    _check(load().qcl_read_sums(model.handle, C.byref(ens), _dptr(obs_buf),
+                                obs_buf.numel() * obs_buf.element_size(), n_out, k0, n_rows,
+                                out.ctypes.data, out.size, _stream_ptr(stream)), "qcl_read_sums")
+    return out
+
+
+def ensemble_status(model: Model, ens: EnsembleDesc, ens_buf, stream=None) -> dict:
+    s = EnsStatus()
+    _check(load().qcl_ensemble_status(model.handle, C.byref(ens), _dptr(ens_buf),
+                                      ens_buf.numel() * ens_buf.element_size(), C.byref(s),
+                                      _stream_ptr(stream)), "qcl_ensemble_status")
+    return {"step": s.step, "flags": s.flags, "n_degenerate": s.n_degenerate,
+            "n_nonfinite": s.n_nonfinite}
+
+
+# ------------------------------------------------------------- conveniences --
+def device_buffer(nbytes: int, device="cuda"):
+    """Caller-owned device memory from torch (256-byte aligned)."""
+    import torch
+
+    t = torch.empty(max(int(nbytes), 1), dtype=torch.uint8, device=device)
+    if t.data_ptr() % 256:
+        raise RuntimeError("torch returned a buffer that is not 256-byte aligned")
+    return t
+
+
+class Run:
+    """One ensemble with its device buffers: sample, propagate, observe."""
+
+    def __init__(self, model: Model, n_traj: int, seed: int, precision: int, n_out: int,
+                 traj_id_offset: int = 0, device="cuda"):
+        self.model = model
+        self.ens = ens_desc(n_traj, seed, precision, traj_id_offset)
+        self.n_out = n_out
+        self.ens_buf = device_buffer(ensemble_bytes(model, self.ens), device)
+        self.obs_buf = device_buffer(obs_bytes(model, self.ens, n_out), device)
+        self.step = 0
+
+    def sample(self, init: dict, stream=None):
+        sample_initial(self.model, self.ens, init, self.ens_buf, stream)
+        self.step = 0
+
+    def propagate(self, n_steps: int, dt: float, out_stride: int, stream=None):
+        propagate(self.model, self.ens, self.ens_buf, self.step, n_steps, dt, out_stride,
+                  self.obs_buf, self.n_out, stream)
+        self.step += n_steps
+
+    def observables(self, stream=None) -> np.ndarray:
+        return reduce_observables(self.model, self.ens, self.obs_buf, self.n_out, stream=stream)
+
+    def sums(self, stream=None) -> np.ndarray:
+        return read_sums(self.model, self.ens, self.obs_buf, self.n_out, stream=stream)
+
+    def status(self, stream=None) -> dict:
+        return ensemble_status(self.model, self.ens, self.ens_buf, stream)
+
+    def state(self):
+        """Host copy of the SoA walker state (for checkpoints and parity tests)."""
+        import torch
+
+        torch.cuda.synchronize()
+        nt, n = self.ens.n_traj, self.model.n
+        off = ensemble_layout(self.model, self.ens)
+        raw = self.ens_buf.cpu().numpy()
+        fp64 = self.ens.precision == PREC_FP64
+        dt = np.float64 if fp64 else np.float32
+        w = 8 if fp64 else 4
+
+        def arr(o, count, dtype, width):
+            return np.frombuffer(raw[o:o + width * count].tobytes(), dtype=dtype).copy()
+
+        return {"R": arr(off[0], nt * n, dt, w).reshape(n, nt).T.copy(),
+                "P": arr(off[1], nt * n, dt, w).reshape(n, nt).T.copy(),
+                "m": arr(off[2], nt, dt, w), "m_lo": arr(off[3], nt, dt, w),
+                "phi": arr(off[4], nt, dt, w), "phi_lo": arr(off[5], nt, dt, w),
+                "alpha": (arr(off[6], nt, np.uint16, 2) & 0xFF).astype(np.int32),
+                "beta": (arr(off[6], nt, np.uint16, 2) >> 8).astype(np.int32)}

@@ -1,0 +1,90 @@
+"""CPU checks of the C ABI: the library builds for sm_103a, loads without a
+GPU, and exports every entry point include/qcl.h declares.  Argument
+validation that happens before any CUDA call is exercised too."""
+import ctypes as C
+import os
+import re
+import subprocess
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2608_14544_gb300 import build, qcl
+
+    build.build()
+    return qcl.load()
+
+
+def _declared():
+    names = set()
+    inc = os.path.join(ROOT, "include")
+    for f in os.listdir(inc):
+        if f.endswith(".h"):
+            txt = open(os.path.join(inc, f)).read()
+            names |= set(re.findall(r"^\s*(?:const\s+)?\w+\**\s+\**(qcl_\w+)\s*\(", txt, re.M))
+    return names
+
+
+def test_every_declared_symbol_is_exported(lib):
+    from paper_2608_14544_gb300 import qcl
+
+    declared = _declared()
+    assert len(declared) >= 15
+    out = subprocess.run(["nm", "-D", "--defined-only", qcl.LIB_PATH], capture_output=True,
+                         text=True, check=True).stdout
+    exported = set(re.findall(r"\sT\s(qcl_\w+)", out))
+    assert declared <= exported, declared - exported
+    assert set(qcl.EXPORTS) == declared
+    for name in declared:
+        assert hasattr(lib, name)
+
+
+def test_library_targets_sm_103a(lib):
+    from paper_2608_14544_gb300 import build
+
+    assert "arch=compute_103a,code=sm_103a" in " ".join(build.ARCH)
+
+
+def test_model_validation_without_gpu(lib):
+    from paper_2608_14544_gb300 import qcl
+
+    def desc(ns, n, E, K, mass=None, omega=None, hbar=1.0, pmax=0.5):
+        arrs = [np.ones(n) if mass is None else np.asarray(mass, float),
+                np.ones(n) if omega is None else np.asarray(omega, float),
+                np.ascontiguousarray(E, dtype=float), np.ascontiguousarray(K, dtype=float)]
+        d = qcl.ModelDesc(ns, n, hbar, *[a.ctypes.data for a in arrs], 1.0, pmax)
+        return d, arrs
+
+    h = C.c_void_p()
+    E = np.array([[0.0, 0.5], [0.5, 0.0]])
+    K = np.array([[[1.0, 0.0], [0.0, -1.0]]])
+    d, keep = desc(1, 1, E, K)
+    assert lib.qcl_create_model(C.byref(d), C.byref(h)) == 1 and not h.value
+    d, keep = desc(2, 1, np.array([[0.0, 0.5], [0.4, 0.0]]), K)
+    assert lib.qcl_create_model(C.byref(d), C.byref(h)) == 1
+    assert b"symmetric" in lib.qcl_last_error()
+    d, keep = desc(2, 1, E, K, mass=[-1.0])
+    assert lib.qcl_create_model(C.byref(d), C.byref(h)) == 1
+    d, keep = desc(2, 1, E, K, pmax=1.5)
+    assert lib.qcl_create_model(C.byref(d), C.byref(h)) == 1
+    d, keep = desc(9, 1, np.eye(9), np.zeros((1, 9, 9)))
+    assert lib.qcl_create_model(C.byref(d), C.byref(h)) == 2
+    assert lib.qcl_create_model(None, C.byref(h)) == 1
+    assert lib.qcl_destroy_model(None) == 0
+
+
+def test_option_and_null_checks_without_gpu(lib):
+    assert lib.qcl_set_option(99, 0) == 1
+    assert lib.qcl_set_option(1, -1) == 1
+    assert lib.qcl_set_option(1, 0) == 0
+    assert lib.qcl_launch_count(None, 0) == 1
+    c = C.c_int64()
+    assert lib.qcl_launch_count(C.byref(c), 0) == 0
+    assert lib.qcl_kernel_time(7, None, None) == 1
+    b = C.c_size_t()
+    assert lib.qcl_ensemble_bytes(None, None, C.byref(b)) == 1
