@@ -215,8 +215,9 @@ void orc_mean_force(const orc_model* md, const double* R, const double* U, int32
  *     amplitude A = -dt sum_j (P_j/M_j) d_{a' g, j}
  *   rho_ab receives +(P/M) rho_ag d_{g b}  => walker (a,g) -> (a,b') with
  *     amplitude A = +dt sum_j (P_j/M_j) d_{g b', j}
- * Probabilities p_e = min(kappa |A_e|, p_max), scaled down together when their
- * sum exceeds p_max, quantised to T_e = floor(p_e 2^24). */
+ * Probabilities p_e = min(kappa |A_e|, p_max) are quantised to 24-bit integer
+ * thresholds T_e = floor(p_e 2^24); when their sum exceeds Tmax = floor(p_max
+ * 2^24) they are scaled down together, T_e <- floor(T_e Tmax / sum T). */
 static int32_t events_impl(const orc_model* md, const double* P, const double* e, const double* U,
                            int32_t a, int32_t b, double dt, int32_t* ta, int32_t* tb, double* A,
                            uint32_t* T, int* deg) {
@@ -237,17 +238,18 @@ static int32_t events_impl(const orc_model* md, const double* P, const double* e
       ++ne;
     }
   }
-  double sum = 0.0;
+  /* quantise first, then scale the integer thresholds down proportionally:
+   * floor(T_e Tmax / sum T) is exact, so equal events stay exactly equal */
+  uint64_t sumT = 0;
+  const uint64_t Tmax = (uint64_t)floor(md->p_max * P24);
   for (int k = 0; k < ne; ++k) {
     p[k] = md->hop_scale * fabs(A[k]);
     if (p[k] > md->p_max) p[k] = md->p_max;
-    sum += p[k];
+    T[k] = (uint32_t)floor(p[k] * P24);
+    sumT += T[k];
   }
-  if (sum > md->p_max) {
-    double scale = md->p_max / sum;
-    for (int k = 0; k < ne; ++k) p[k] = p[k] * scale;
-  }
-  for (int k = 0; k < ne; ++k) T[k] = (uint32_t)floor(p[k] * P24);
+  if (sumT > Tmax)
+    for (int k = 0; k < ne; ++k) T[k] = (uint32_t)(((uint64_t)T[k] * Tmax) / sumT);
   return ne;
 }
 
