@@ -46,7 +46,7 @@ struct BulkParams {
   float hdt_hbar;      // dt / (2 hbar)
   float kdt;           // hop_scale * dt
   float p_max;
-  float pad;
+  uint32_t tmax;       // floor(p_max 2^24)
 };
 
 // Kernel launches issued by the library (instrumentation).

@@ -26,6 +26,7 @@ struct W32 {
   float* P;
   float* mh;
   float* ml;
+  int32_t* me;
   float* ph;
   float* pl;
   uint16_t* ab;
@@ -35,12 +36,33 @@ struct W32 {
 __device__ __forceinline__ W32 view32(void* buf, int64_t nt, int ns, int n) {
   const EnsLayout L = EnsLayout::make(nt, ns, n, QCL_PREC_FP32_BULK);
   char* b = (char*)buf;
-  return {(float*)(b + L.off_R),   (float*)(b + L.off_P),     (float*)(b + L.off_m),
-          (float*)(b + L.off_mlo), (float*)(b + L.off_phi),   (float*)(b + L.off_philo),
-          (uint16_t*)(b + L.off_ab), (EnsHeader*)b};
+  return {(float*)(b + L.off_R),    (float*)(b + L.off_P),     (float*)(b + L.off_m),
+          (float*)(b + L.off_mlo),  (int32_t*)(b + L.off_mexp), (float*)(b + L.off_phi),
+          (float*)(b + L.off_philo), (uint16_t*)(b + L.off_ab),  (EnsHeader*)b};
 }
 
 __device__ __forceinline__ float sgn(int idx) { return idx ? 1.0f : -1.0f; }
+
+// Unbiased exponent of a float (normal numbers), -127 for zero/denormals.
+__device__ __forceinline__ int fexp(float x) {
+  return (int)((__float_as_uint(x) >> 23) & 0xffu) - 127;
+}
+
+// 2^d for -126 <= d <= 127 (0 below)
+__device__ __forceinline__ float pow2i(int d) {
+  return d < -126 ? 0.0f : __uint_as_float((uint32_t)(127 + d) << 23);
+}
+
+// The weight is carried as (hi + lo) * 2^e: move hi's exponent into e so that
+// hi stays in [1, 2) and the FP32 range never limits the weight.
+__device__ __forceinline__ void renorm(f2& m, int& e) {
+  if (m.hi == 0.0f) return;
+  const int k = fexp(m.hi);
+  const float sc = (k == -127) ? 0x1p+126f : (k >= 127 ? 0x1p-127f : pow2i(-k));
+  m.hi *= sc;
+  m.lo *= sc;
+  e += (k == -127) ? -126 : k;
+}
 
 }  // namespace
 
@@ -132,6 +154,7 @@ __global__ void __launch_bounds__(256) k_sample_f32(const DevModel* __restrict__
   }
   w.mh[i] = (float)rho_ad[pick] * (kP24f / (float)Tk[pick]);
   w.ml[i] = 0.0f;
+  w.me[i] = 0;
   w.ph[i] = 0.0f;
   w.pl[i] = 0.0f;
   w.ab[i] = (uint16_t)((pick >> 1) | ((pick & 1) << 8));
@@ -193,6 +216,7 @@ __global__ void __launch_bounds__(256, 3)
       w.P[j] = on ? ws.P[(int64_t)j * nt + ii] : 0.0f;
     }
     f2 m = {active ? ws.mh[ii] : 0.0f, active ? ws.ml[ii] : 0.0f};
+    int mexp = active ? ws.me[ii] : 0;
     f2 ph = {active ? ws.ph[ii] : 0.0f, active ? ws.pl[ii] : 0.0f};
     const uint32_t ab = active ? ws.ab[ii] : 0u;
     int al = ab & 0xff, be = (ab >> 8) & 0xff;
@@ -228,7 +252,14 @@ __global__ void __launch_bounds__(256, 3)
       }
       const float ua0 = al ? c : -s, ua1 = al ? s : c;  // column alpha of U
       const float ub0 = be ? c : -s, ub1 = be ? s : c;  // column beta of U
-      const float mm = active ? m.hi : 0.0f;
+      // common power of two over the warp: FP32 sums of scaled weights, the
+      // exponent restored exactly in FP64
+      renorm(m, mexp);
+      const bool live = active && m.hi != 0.0f;
+      int ew = live ? mexp : -(1 << 28);
+#pragma unroll
+      for (int off = 16; off > 0; off >>= 1) ew = max(ew, __shfl_xor_sync(0xffffffffu, ew, off));
+      const float mm = live ? m.hi * pow2i(mexp - ew) : 0.0f;
       const float zr = mm * cphi, zi = -mm * sphi;
       float v[32];
       const float f00 = ua0 * ub0, f01 = ua0 * ub1, f10 = ua1 * ub0, f11 = ua1 * ub1;
@@ -249,7 +280,8 @@ __global__ void __launch_bounds__(256, 3)
 #pragma unroll
       for (int q = 0; q < 16; ++q) v[16 + q] = v[q] * v[q];
       const float x = warp_transpose_sum<float>(v);
-      red[warp][lane] = (double)x;
+      const int ex = (ew < -(1 << 27)) ? 0 : ((lane < 16) ? ew : 2 * ew);
+      red[warp][lane] = ldexp((double)x, ex);
       __syncthreads();
       if (threadIdx.x < 32)
         part[((int64_t)slot * bp.n_tiles + tile) * 32 + threadIdx.x] =
@@ -296,11 +328,10 @@ __global__ void __launch_bounds__(256, 3)
       const bool degen = 2.0f * r < kDegTol32;
       n_deg += (degen && active) ? 1ull : 0ull;
       const float g = degen ? 0.0f : (A * Bv - B * Av) * (0.5f * ir * ir);
-      // both events have |A_e| = dt |g|: p = min(kappa dt |g|, p_max), halved
-      // together when their sum exceeds p_max; thresholds quantised to 2^-24
-      float p = fminf(bp.kdt * fabsf(g), bp.p_max);
-      if (2.0f * p > bp.p_max) p = 0.5f * bp.p_max;
-      const uint32_t T = __float2uint_rz(p * kP24f);
+      // both events have |A_e| = dt |g|: p = min(kappa dt |g|, p_max)
+      // equal events; quantised thresholds scaled down together in integers
+      uint32_t T = min(__float2uint_rz(fminf(bp.kdt * fabsf(g) * kP24f, 33554432.0f)), bp.tmax);
+      if (2u * T > bp.tmax) T = bp.tmax >> 1;
       const uint32_t y = word_of(wd, (int)(s & 3)) >> 8;
       const bool hop1 = y < T;
       const bool hop2 = !hop1 && (y < 2u * T);
@@ -311,6 +342,7 @@ __global__ void __launch_bounds__(256, 3)
       float q0, q1;
       df_div(num, den, q0, q1);
       m = df_mul(m, q0, q1);
+      if (abs(fexp(m.hi)) > 32) renorm(m, mexp);
       al ^= hop1 ? 1 : 0;
       be ^= hop2 ? 1 : 0;
       if ((s + 1) % bp.stride == 0) observe((int)((s + 1) / bp.stride - bp.k_first));
@@ -324,6 +356,7 @@ __global__ void __launch_bounds__(256, 3)
         }
       ws.mh[i] = m.hi;
       ws.ml[i] = m.lo;
+      ws.me[i] = mexp;
       ws.ph[i] = ph.hi;
       ws.pl[i] = ph.lo;
       ws.ab[i] = (uint16_t)(al | (be << 8));

@@ -284,21 +284,23 @@ __global__ void __launch_bounds__(256) k_step_f64(const DevModel* __restrict__ M
   // events: (first index flips) then (second index flips)
   const double A1 = (al == 0) ? dt * g : -(dt * g);
   const double A2 = (be == 0) ? dt * g : -(dt * g);
-  double p1 = fmin(M->hop_scale * fabs(A1), M->p_max);
-  double p2 = fmin(M->hop_scale * fabs(A2), M->p_max);
-  const double sum = p1 + p2;
-  if (sum > M->p_max) {
-    const double sc = M->p_max / sum;
-    p1 = p1 * sc;
-    p2 = p2 * sc;
+  // probabilities min(kappa |A_e|, p_max) quantised to 24-bit thresholds, then
+  // scaled down together in exact integer arithmetic when their sum exceeds Tmax
+  const double p1 = fmin(M->hop_scale * fabs(A1), M->p_max);
+  const double p2 = fmin(M->hop_scale * fabs(A2), M->p_max);
+  uint64_t T1 = (uint64_t)floor(p1 * kP24), T2 = (uint64_t)floor(p2 * kP24);
+  const uint64_t Tmax = (uint64_t)floor(M->p_max * kP24);
+  if (T1 + T2 > Tmax) {
+    const uint64_t sT = T1 + T2;
+    T1 = T1 * Tmax / sT;
+    T2 = T2 * Tmax / sT;
   }
-  const uint32_t T1 = (uint32_t)floor(p1 * kP24), T2 = (uint32_t)floor(p2 * kP24);
   const u4 wd = philox_draw(seed, (uint32_t)(step >> 2), traj_off + (uint64_t)i, kPurposeHop);
   const uint32_t y = word_of(wd, (int)(step & 3)) >> 8;
-  if (y < T1) {
+  if ((uint64_t)y < T1) {
     m = m * A1 / ((double)T1 / kP24);
     al ^= 1;
-  } else if ((uint64_t)y < (uint64_t)T1 + T2) {
+  } else if ((uint64_t)y < T1 + T2) {
     m = m * A2 / ((double)T2 / kP24);
     be ^= 1;
   } else {

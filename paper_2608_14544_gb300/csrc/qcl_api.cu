@@ -157,7 +157,7 @@ qcl_status qcl_kernel_time(int32_t which, double* total_ms, int64_t* launches) {
   return st ? st : ok();
 }
 
-qcl_status qcl_ensemble_layout(const qcl_model* model, const qcl_ensemble_desc* ens, size_t offsets[8]) {
+qcl_status qcl_ensemble_layout(const qcl_model* model, const qcl_ensemble_desc* ens, size_t offsets[9]) {
   if (!offsets) return fail(QCL_ERR_INVALID_ARG, "offsets is NULL");
   qcl_status st = check_ens(model, ens);
   if (st) return st;
@@ -170,6 +170,7 @@ qcl_status qcl_ensemble_layout(const qcl_model* model, const qcl_ensemble_desc* 
   offsets[5] = L.off_philo;
   offsets[6] = L.off_ab;
   offsets[7] = L.total;
+  offsets[8] = L.off_mexp;
   return ok();
 }
 
@@ -394,6 +395,7 @@ qcl_status qcl_propagate(const qcl_model* model, const qcl_ensemble_desc* ens, v
     bp.hdt_hbar = (float)(0.5 * dt / model->hbar);
     bp.kdt = (float)(model->hop_scale * dt);
     bp.p_max = (float)model->p_max;
+    bp.tmax = (uint32_t)std::floor(model->p_max * kP24);
     // chunks of at most kChunkOut output times
     int64_t cs = step0;
     bool first = (step0 == 0);

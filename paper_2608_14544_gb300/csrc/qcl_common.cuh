@@ -106,7 +106,7 @@ struct DevModel {
   int32_t pad;
   double hbar, hop_scale, p_max;
   double a0, b0, s0;
-  // per-mode FP64 arrays [n] at these offsets (in doubles from `base`)
+  // per-mode arrays [n]
   double mass[kMaxN], omega[kMaxN], k[kMaxN];
   double a[kMaxN], b[kMaxN], s[kMaxN];
   double E[kMaxNS * kMaxNS];
@@ -132,7 +132,7 @@ __host__ __device__ inline size_t align256(size_t x) { return (x + 255) & ~size_
 
 // SoA ensemble layout.  Every array starts on a 256-byte boundary.
 struct EnsLayout {
-  size_t off_R, off_P, off_m, off_mlo, off_phi, off_philo, off_ab, off_U, total;
+  size_t off_R, off_P, off_m, off_mlo, off_mexp, off_phi, off_philo, off_ab, off_U, total;
   __host__ __device__ static EnsLayout make(int64_t n_traj, int ns, int n, int precision) {
     EnsLayout L{};
     const size_t nt = (size_t)n_traj;
@@ -146,6 +146,8 @@ struct EnsLayout {
     o = align256(o + w * nt);
     L.off_mlo = o;
     o = align256(o + w * nt);
+    L.off_mexp = o;
+    o = align256(o + 4 * nt);
     L.off_phi = o;
     o = align256(o + w * nt);
     L.off_philo = o;

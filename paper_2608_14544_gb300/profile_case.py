@@ -1,0 +1,50 @@
+"""One solve of a workload through the C ABI, for profilers (ncu): sample,
+propagate, reduce.  Prints the wall time; use bench.py for measurements.
+
+  python -m paper_2608_14544_gb300.profile_case --config 2 --n-traj 1048576 --steps 160
+"""
+from __future__ import annotations
+
+import argparse
+import time
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--config", type=int, default=2)
+    ap.add_argument("--n-traj", type=int, default=None)
+    ap.add_argument("--steps", type=int, default=None)
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
+    ap.add_argument("--repeat", type=int, default=1)
+    args = ap.parse_args()
+
+    import torch
+
+    from . import build, qcl
+    from . import workloads as wl
+
+    build.build()
+    torch.cuda.set_device(0)
+    cfg = wl.config(args.config)
+    n = args.n_traj or cfg["n_traj"]
+    steps = args.steps or cfg["n_steps"]
+    stride = cfg["out_stride"]
+    prec = qcl.PREC_FP32_BULK if args.precision == "fp32" else qcl.PREC_FP64
+    model = qcl.Model(cfg["model"])
+    run = qcl.Run(model, n, cfg["seed"], prec, steps // stride + 1)
+    for _ in range(args.repeat):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        run.sample(cfg["init"])
+        run.propagate(steps, cfg["dt"], stride)
+        obs = run.observables()
+        torch.cuda.synchronize()
+        el = time.perf_counter() - t0
+        print(f"config {args.config} n_traj {n} steps {steps} {args.precision}: {el * 1e3:.2f} ms, "
+              f"{n * steps / el:.3e} traj-steps/s, trace(t_end) {obs[-1, 32]:.4f}")
+    st = run.status()
+    assert st["flags"] == 0, st
+
+
+if __name__ == "__main__":
+    main()

@@ -145,7 +145,7 @@ def kernel_time(which: int):
 
 
 def ensemble_layout(model, ens) -> list:
-    off = (C.c_size_t * 8)()
+    off = (C.c_size_t * 9)()
     _check(load().qcl_ensemble_layout(model.handle, C.byref(ens), off), "qcl_ensemble_layout")
     return list(off)
 
@@ -305,7 +305,8 @@ class Run:
         def arr(o, count, dtype, width):
             return np.frombuffer(raw[o:o + width * count].tobytes(), dtype=dtype).copy()
 
-        return {"R": arr(off[0], nt * n, dt, w).reshape(n, nt).T.copy(),
+        mexp = np.zeros(nt, dtype=np.int32) if fp64 else arr(off[8], nt, np.int32, 4)
+        return {"R": arr(off[0], nt * n, dt, w).reshape(n, nt).T.copy(), "m_exp": mexp,
                 "P": arr(off[1], nt * n, dt, w).reshape(n, nt).T.copy(),
                 "m": arr(off[2], nt, dt, w), "m_lo": arr(off[3], nt, dt, w),
                 "phi": arr(off[4], nt, dt, w), "phi_lo": arr(off[5], nt, dt, w),
