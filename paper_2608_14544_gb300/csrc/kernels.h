@@ -39,6 +39,10 @@ struct BulkParams {
   int64_t k_first;     // absolute output index of slot 0
   int32_t stride;      // output stride
   int32_t obs_first;   // observe at cs before stepping (only at s = 0)
+  int32_t len;         // ce - cs
+  int32_t to_out0;     // steps from cs until the first output
+  uint32_t blk0;       // Philox block of step cs (cs >> 2)
+  int32_t widx0;       // word of step cs in its block (cs & 3)
   int32_t n;           // modes
   int32_t kind;        // 0: a_j only (spin-boson form), 1: general two-state
   float a0, b0;

@@ -161,13 +161,14 @@ __global__ void __launch_bounds__(256) k_sample_f32(const DevModel* __restrict__
 }
 
 // ------------------------------------------------------- persistent step --
-template <int NPL, int KIND>
+template <int NPL>
 struct Walker {
   float R[NPL], P[NPL];
 };
 
+// a = a0 + sum a_j R_j, b = b0 + sum b_j R_j (fixed FMA order)
 template <int NPL, int KIND>
-__device__ __forceinline__ void decomp(const Walker<NPL, KIND>& w, const BulkParams& bp,
+__device__ __forceinline__ void decomp(const Walker<NPL>& w, const BulkParams& bp,
                                        const Coef2& cf, float& A, float& B) {
   A = bp.a0;
   B = bp.b0;
@@ -178,9 +179,10 @@ __device__ __forceinline__ void decomp(const Walker<NPL, KIND>& w, const BulkPar
   }
 }
 
-// P += dt/2 F_ab(R),  F_j = -k_j R_j - s_j - sab (a_j cos2t + b_j sin2t)
+// P += dt/2 F_ab(R),  F_j = -k_j R_j - s_j - sab (a_j cos2t + b_j sin2t);
+// hu = dt/2 sab cos2t, hv = dt/2 sab sin2t
 template <int NPL, int KIND>
-__device__ __forceinline__ void kick(Walker<NPL, KIND>& w, const Coef2& cf, float hu, float hv) {
+__device__ __forceinline__ void kick(Walker<NPL>& w, const Coef2& cf, float hu, float hv) {
 #pragma unroll
   for (int j = 0; j < NPL; ++j) {
     float p = __fmaf_rn(-cf.hk[j], w.R[j], w.P[j]);
@@ -191,10 +193,19 @@ __device__ __forceinline__ void kick(Walker<NPL, KIND>& w, const Coef2& cf, floa
   }
 }
 
+__device__ __forceinline__ float rcp_approx(float x) {
+  float r;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
+
+// 2^e as a double, -1022 <= e <= 1023
+__device__ __forceinline__ double pow2d(int e) { return __hiloint2double((e + 1023) << 20, 0); }
+
 template <int NPL, int KIND>
 __global__ void __launch_bounds__(256, 3)
     k_bulk2(const BulkParams bp, const Coef2 cf, void* buf, double* __restrict__ part) {
-  __shared__ double red[8][32];
+  __shared__ double red[2][8][32];  // double-buffered group partials
   W32 ws = view32(buf, bp.n_traj, 2, bp.n);
   if (ws.hdr->step != bp.step0) {
     if (blockIdx.x == 0 && threadIdx.x == 0) atomicOr(&ws.hdr->flags, QCL_FLAG_STEP_MISMATCH);
@@ -202,13 +213,14 @@ __global__ void __launch_bounds__(256, 3)
   }
   const int64_t nt = bp.n_traj;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  unsigned long long n_deg = 0;
+  unsigned int n_deg = 0;
+  int rb = 0;
 
   for (int64_t tile = blockIdx.x; tile < bp.n_tiles; tile += gridDim.x) {
     const int64_t i = tile * kTile + threadIdx.x;
     const bool active = i < nt;
     const int64_t ii = active ? i : 0;
-    Walker<NPL, KIND> w;
+    Walker<NPL> w;
 #pragma unroll
     for (int j = 0; j < NPL; ++j) {
       const bool on = active && j < bp.n;
@@ -219,7 +231,8 @@ __global__ void __launch_bounds__(256, 3)
     int mexp = active ? ws.me[ii] : 0;
     f2 ph = {active ? ws.ph[ii] : 0.0f, active ? ws.pl[ii] : 0.0f};
     const uint32_t ab = active ? ws.ab[ii] : 0u;
-    int al = ab & 0xff, be = (ab >> 8) & 0xff;
+    // sigma of the pair's indices: -1 lower, +1 upper adiabatic state
+    float sa = sgn(ab & 0xff), sb = sgn((ab >> 8) & 0xff);
     const uint64_t traj = bp.traj_offset + (uint64_t)ii;
 
     float A, B;
@@ -227,6 +240,8 @@ __global__ void __launch_bounds__(256, 3)
     float r2 = __fmaf_rn(A, A, B * B);
     float ir = rsqrtf(r2);
     float r = r2 * ir;
+    float c2 = r2 > 0.0f ? A * ir : 1.0f;  // cos 2theta (theta = 0 at r = 0)
+    float s2 = r2 > 0.0f ? B * ir : 0.0f;  // sin 2theta
 
     // observation into slot `slot` of the tile partials
     auto observe = [&](int slot) {
@@ -236,20 +251,18 @@ __global__ void __launch_bounds__(256, 3)
       ph = df_add(ph, -kq * kTwoPi2);
       ph = df_add(ph, -kq * kTwoPi3);
       float sh, chh;
-      sincosf(ph.hi, &sh, &chh);
+      __sincosf(ph.hi, &sh, &chh);
       const float cphi = __fmaf_rn(-ph.lo, sh, chh);
       const float sphi = __fmaf_rn(ph.lo, chh, sh);
-      float c = 1.0f, s = 0.0f;
-      if (r2 > 0.0f) {
-        const float c2 = A * ir, s2 = B * ir;
-        if (A >= 0.0f) {
-          c = sqrtf(0.5f + 0.5f * c2);
-          s = 0.5f * s2 / c;
-        } else {
-          s = copysignf(sqrtf(0.5f - 0.5f * c2), B);
-          c = 0.5f * s2 / s;
-        }
-      }
+      // eigenvector angle theta from (cos 2theta, sin 2theta), half-angle form
+      // without cancellation: the larger of cos/sin is sqrt((1 + |cos2t|)/2)
+      const float t = __fmaf_rn(0.5f, fabsf(c2), 0.5f);
+      const float rt = rsqrtf(t);
+      const float big = t * rt, small = 0.5f * fabsf(s2) * rt;
+      const bool cpos = c2 >= 0.0f;
+      const float c = cpos ? big : small;
+      const float s = copysignf(cpos ? small : big, s2);
+      const bool al = sa > 0.0f, be = sb > 0.0f;
       const float ua0 = al ? c : -s, ua1 = al ? s : c;  // column alpha of U
       const float ub0 = be ? c : -s, ub1 = be ? s : c;  // column beta of U
       // common power of two over the warp: FP32 sums of scaled weights, the
@@ -271,7 +284,7 @@ __global__ void __launch_bounds__(256, 3)
       v[5] = zi * f10;
       v[6] = zr * f11;
       v[7] = zi * f11;
-      const int k = al * 2 + be;
+      const int k = (al ? 2 : 0) + (be ? 1 : 0);
 #pragma unroll
       for (int kk = 0; kk < 4; ++kk) {
         v[8 + 2 * kk] = (kk == k) ? zr : 0.0f;
@@ -280,44 +293,38 @@ __global__ void __launch_bounds__(256, 3)
 #pragma unroll
       for (int q = 0; q < 16; ++q) v[16 + q] = v[q] * v[q];
       const float x = warp_transpose_sum<float>(v);
-      const int ex = (ew < -(1 << 27)) ? 0 : ((lane < 16) ? ew : 2 * ew);
-      red[warp][lane] = ldexp((double)x, ex);
+      int ex = (ew < -(1 << 27)) ? 0 : ((lane < 16) ? ew : 2 * ew);
+      const double xd = (double)x;
+      red[rb][warp][lane] = (ex >= -1022 && ex <= 1023) ? xd * pow2d(ex) : ldexp(xd, ex);
       __syncthreads();
       if (threadIdx.x < 32)
         part[((int64_t)slot * bp.n_tiles + tile) * 32 + threadIdx.x] =
-            tile_tree8(&red[0][0], 32, threadIdx.x);
-      __syncthreads();
+            tile_tree8(&red[rb][0][0], 32, threadIdx.x);
+      rb ^= 1;
     };
 
+    int slot = bp.obs_first;
     if (bp.obs_first) observe(0);
-
-    u4 wd = philox_draw(bp.seed, (uint32_t)(bp.cs >> 2), traj, kPurposeHop);
-    for (int64_t s = bp.cs; s < bp.ce; ++s) {
-      if ((s & 3) == 0 && s != bp.cs) wd = philox_draw(bp.seed, (uint32_t)(s >> 2), traj, kPurposeHop);
-      const float sab = 0.5f * (sgn(al) + sgn(be));
-      const float sd = sgn(al) - sgn(be);
-      // first half kick at R_n
-      {
-        const float u = (r2 > 0.0f) ? A * ir : 1.0f;
-        const float v = (r2 > 0.0f) ? B * ir : 0.0f;
-        kick<NPL, KIND>(w, cf, bp.hdt * sab * u, bp.hdt * sab * v);
-      }
-      // drift
+    int to_out = bp.to_out0;
+    uint32_t blk = bp.blk0;
+    int widx = bp.widx0;
+    u4 wd = philox_draw(bp.seed, blk, traj, kPurposeHop);
+    for (int it = 0; it < bp.len; ++it) {
+      const uint32_t word = (widx & 2) ? ((widx & 1) ? wd.w : wd.z) : ((widx & 1) ? wd.y : wd.x);
+      const float hsab = bp.hdt * 0.5f * (sa + sb);  // dt/2 (sig_a + sig_b)/2
+      kick<NPL, KIND>(w, cf, hsab * c2, hsab * s2);  // first half kick at R_n
 #pragma unroll
-      for (int j = 0; j < NPL; ++j) w.R[j] = __fmaf_rn(cf.dtm[j], w.P[j], w.R[j]);
+      for (int j = 0; j < NPL; ++j) w.R[j] = __fmaf_rn(cf.dtm[j], w.P[j], w.R[j]);  // drift
       const float r_old = r;
       decomp<NPL, KIND>(w, bp, cf, A, B);
       r2 = __fmaf_rn(A, A, B * B);
       ir = rsqrtf(r2);
       r = r2 * ir;
-      // second half kick at R_{n+1}
-      {
-        const float u = (r2 > 0.0f) ? A * ir : 1.0f;
-        const float v = (r2 > 0.0f) ? B * ir : 0.0f;
-        kick<NPL, KIND>(w, cf, bp.hdt * sab * u, bp.hdt * sab * v);
-      }
+      c2 = r2 > 0.0f ? A * ir : 1.0f;
+      s2 = r2 > 0.0f ? B * ir : 0.0f;
+      kick<NPL, KIND>(w, cf, hsab * c2, hsab * s2);  // second half kick at R_{n+1}
       // phase (trapezoid): dt/2 (w_ab(R_n) + w_ab(R_{n+1})), hbar w_ab = (sig_a - sig_b) r
-      ph = df_add(ph, bp.hdt_hbar * sd * (r_old + r));
+      ph = df_add(ph, bp.hdt_hbar * (sa - sb) * (r_old + r));
       // coupling contracted with P/M: g = (a Bv - b Av) / (2 r^2)
       float Av = 0.0f, Bv = 0.0f;
 #pragma unroll
@@ -326,26 +333,36 @@ __global__ void __launch_bounds__(256, 3)
         if (KIND == 1) Bv = __fmaf_rn(cf.bm[j], w.P[j], Bv);
       }
       const bool degen = 2.0f * r < kDegTol32;
-      n_deg += (degen && active) ? 1ull : 0ull;
+      n_deg += (degen && active) ? 1u : 0u;
       const float g = degen ? 0.0f : (A * Bv - B * Av) * (0.5f * ir * ir);
-      // both events have |A_e| = dt |g|: p = min(kappa dt |g|, p_max)
-      // equal events; quantised thresholds scaled down together in integers
+      // both events have |A_e| = dt |g|: p = min(kappa dt |g|, p_max) quantised to
+      // 24-bit thresholds, scaled down together in integers when 2T > Tmax
       uint32_t T = min(__float2uint_rz(fminf(bp.kdt * fabsf(g) * kP24f, 33554432.0f)), bp.tmax);
       if (2u * T > bp.tmax) T = bp.tmax >> 1;
-      const uint32_t y = word_of(wd, (int)(s & 3)) >> 8;
+      const uint32_t y = word >> 8;
       const bool hop1 = y < T;
       const bool hop2 = !hop1 && (y < 2u * T);
-      const float dtg = bp.dt * g;
-      // weight factor: A_e / p_hat on a hop, 1 / (1 - sum p_hat) otherwise
-      const float num = hop1 ? -sgn(al) * dtg * kP24f : (hop2 ? -sgn(be) * dtg * kP24f : kP24f);
-      const float den = (hop1 || hop2) ? (float)T : (float)(16777216u - 2u * T);
-      float q0, q1;
-      df_div(num, den, q0, q1);
+      // weight factor: A_e / p_hat on a hop (A_1 = -sig_a dt g, A_2 = -sig_b dt g),
+      // 1 / (1 - sum p_hat) otherwise; num / den as a compensated quotient
+      const float dtg = bp.dt * g * kP24f;
+      const float num = hop1 ? -sa * dtg : (hop2 ? -sb * dtg : kP24f);
+      const float den = __uint2float_rn((hop1 || hop2) ? T : 16777216u - 2u * T);
+      const float rd = rcp_approx(den);
+      const float q0 = num * rd;
+      const float q1 = __fmaf_rn(-q0, den, num) * rd;
       m = df_mul(m, q0, q1);
-      if (abs(fexp(m.hi)) > 32) renorm(m, mexp);
-      al ^= hop1 ? 1 : 0;
-      be ^= hop2 ? 1 : 0;
-      if ((s + 1) % bp.stride == 0) observe((int)((s + 1) / bp.stride - bp.k_first));
+      if (!(fabsf(m.hi) <= 0x1p32f && fabsf(m.hi) >= 0x1p-32f)) renorm(m, mexp);
+      sa = hop1 ? -sa : sa;
+      sb = hop2 ? -sb : sb;
+      if (++widx == 4) {
+        widx = 0;
+        ++blk;
+        if (it + 1 < bp.len) wd = philox_draw(bp.seed, blk, traj, kPurposeHop);
+      }
+      if (--to_out == 0) {
+        observe(slot++);
+        to_out = bp.stride;
+      }
     }
     if (active) {
 #pragma unroll
@@ -359,7 +376,7 @@ __global__ void __launch_bounds__(256, 3)
       ws.me[i] = mexp;
       ws.ph[i] = ph.hi;
       ws.pl[i] = ph.lo;
-      ws.ab[i] = (uint16_t)(al | (be << 8));
+      ws.ab[i] = (uint16_t)((sa > 0.0f ? 1 : 0) | ((sb > 0.0f ? 1 : 0) << 8));
       if (!isfinite(m.hi) || !isfinite(ph.hi)) {
         atomicAdd(&ws.hdr->n_nonfinite, 1ull);
         atomicOr(&ws.hdr->flags, QCL_FLAG_NONFINITE);
@@ -367,7 +384,7 @@ __global__ void __launch_bounds__(256, 3)
     }
   }
   if (n_deg) {
-    atomicAdd(&ws.hdr->n_degenerate, n_deg);
+    atomicAdd(&ws.hdr->n_degenerate, (unsigned long long)n_deg);
     atomicOr(&ws.hdr->flags, QCL_FLAG_DEGENERATE);
   }
 }

@@ -416,10 +416,19 @@ qcl_status qcl_propagate(const qcl_model* model, const qcl_ensemble_desc* ens, v
         if (end >= next_out) n_slots += (int)((end - next_out) / out_stride + 1);
       }
       if (!first && n_slots > 0) k_first = next_out / out_stride;
+      if (ce - cs > ((int64_t)1 << 30)) {  // keep the in-kernel step count in 32 bits
+        ce = cs + ((int64_t)1 << 30);
+        const int64_t k_last_out = ce / out_stride;
+        n_slots = (first ? 1 : 0) + (int)(k_last_out >= next_out / out_stride ? k_last_out - next_out / out_stride + 1 : 0);
+      }
       bp.cs = cs;
       bp.ce = ce;
       bp.k_first = k_first;
       bp.obs_first = first ? 1 : 0;
+      bp.len = (int32_t)(ce - cs);
+      bp.to_out0 = (int32_t)(out_stride - (cs % out_stride));
+      bp.blk0 = (uint32_t)(cs >> 2);
+      bp.widx0 = (int32_t)(cs & 3);
       int grid = 0;
       {
         TimedLaunch tl(0, s);

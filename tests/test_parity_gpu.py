@@ -169,7 +169,9 @@ def test_fp32_bulk_vs_fp64_large_ensemble(q):
     assert np.all(diff <= 3 * se + 1e-9), (diff / (se + 1e-300)).max()
     # the absolute bound applies where the estimator itself resolves 1e-3: the
     # weights of the no-spawn estimator grow like exp(2 int |P d/M| dt)
-    resolved = se.max(axis=1) < 2e-4
+    # (the walkers are matched: same Philox streams, so early on the two paths
+    # differ by far less than one standard error)
+    resolved = se.max(axis=1) < 1e-2
     assert resolved.sum() >= 10
     assert diff[resolved].max() < 1e-3
 
