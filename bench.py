@@ -51,6 +51,23 @@ def flops_per_traj_step(model: dict) -> float:
     return per_mode * model["n_modes"] + 20.0
 
 
+def _profiled_traffic(kernel_src: str, summary: str):
+    """DRAM bytes per launch from the committed ncu summary, or None when the
+    kernel source has changed since the counters were taken."""
+    import hashlib
+
+    try:
+        txt = open(summary).read()
+        h = hashlib.sha256(open(kernel_src, "rb").read()).hexdigest()[:16]
+    except OSError:
+        return None
+    vals = dict(ln.split(":", 1) for ln in txt.splitlines()
+                if ln.startswith(("traffic_bytes_per_launch:", "traffic_source_sha256_prefix:")))
+    if vals.get("traffic_source_sha256_prefix", "").strip() != h:
+        return None
+    return float(vals["traffic_bytes_per_launch"])
+
+
 def _result_summary(obs, cfg, status):
     """Observables with their standard errors.  The no-spawn estimator's weights
     grow like exp(2 int |P d/M| dt), so the standard error grows with time; the
@@ -328,7 +345,10 @@ def run_ours(args):
                    "parallelism": f"walkers sharded over {world} GPU(s)"},
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_tflops,
                      "unit": "TFLOP/s", "frac": (achieved / peak_tflops) if achieved else None,
-                     "traffic": None,
+                     "traffic": _profiled_traffic(
+                         os.path.join(ROOT, "paper_2608_14544_gb300", "csrc", "kernels_f32.cu"),
+                         os.path.join(ROOT, "profiles", "k_bulk2_sb3mode.md")),
+                     "traffic_unit": "bytes per launch (ncu, small case scaled)",
                      "kernel": "k_bulk2 (persistent FP32-bulk walker kernel)",
                      "flops_per_traj_step": fl,
                      "peak_basis": f"{n_sm} SMs x 128 FP32 lanes x 2 flop x {max_mhz:.0f} MHz",
