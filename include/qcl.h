@@ -208,6 +208,40 @@ qcl_status qcl_ensemble_status(const qcl_model* model, const qcl_ensemble_desc* 
                                const void* ens_buf, size_t ens_bytes, qcl_ens_status* out,
                                void* stream);
 
+/* ------------------------------------------- propagation without allocation
+ * The paper has no counterpart to this entry point.  It is qcl_propagate for
+ * FP32-bulk ensembles, for callers that cannot allocate device memory when
+ * they propagate: for example a service that reserved all of its device memory
+ * at start-up and may not call cudaMalloc or cudaFree afterwards (those calls
+ * can wait on the whole device), or a plug-in that is only handed buffers by
+ * its host application.  The caller still passes the ensemble (input and
+ * output) and `rows`, a device array of n_out x 8 NS^2 doubles that receives
+ * the same FP64 output rows as qcl_propagate writes into its observation
+ * buffer (sums, then sums of squares; the same bits).  The per-tile partial
+ * sums that qcl_propagate keeps in the observation buffer live instead in one
+ * static device array of QCL_NOALLOC_SCRATCH_BYTES inside the library: every
+ * GPU that loads the library holds it until the process exits.
+ *  - The call allocates nothing (no cudaMalloc, no cudaFree, no host heap).
+ *  - The first call on each device looks up the array's device address with
+ *    that device current (cudaGetSymbolAddress); make that first call before
+ *    any stream capture on the device.
+ *  - All calls share the one array and it keeps the last call's contents; no
+ *    part of it needs to start at zero (every value a call reads, the same
+ *    call wrote first).  Calls that overlap on the GPU (other streams or other
+ *    host threads) race on the array: serialise them.
+ *  - One output time of a two-state model needs ceil(n_traj / 256) x 256
+ *    bytes of the array; a walker count that does not fit even one output
+ *    time (about 33 million walkers) is rejected with QCL_ERR_UNSUPPORTED and
+ *    a message giving the limit.  Larger counts fit more output times per
+ *    launch.
+ *  - Only FP32-bulk ensembles of two-state models are accepted
+ *    (QCL_ERR_UNSUPPORTED otherwise); other errors as for qcl_propagate. */
+#define QCL_NOALLOC_SCRATCH_BYTES ((size_t)32 << 20)
+qcl_status qcl_propagate_noalloc(const qcl_model* model, const qcl_ensemble_desc* ens,
+                                 void* ens_buf, size_t ens_bytes, int64_t step0, int64_t n_steps,
+                                 double dt, int32_t out_stride, double* rows, size_t rows_bytes,
+                                 int64_t n_out, void* stream);
+
 /* ----------------------------------------------------------- instrumentation
  * Process-wide options:
  *   QCL_OPT_GRID_CAP  cap on the persistent grid (0: SMs x resident blocks);

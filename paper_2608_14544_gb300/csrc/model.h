@@ -1,0 +1,21 @@
+// model.h -- the opaque qcl_model handle (host copy of the model and its
+// device constant block), shared by the translation units of the C ABI.
+#pragma once
+#include <string>
+#include <vector>
+
+#include "qcl_common.cuh"
+
+struct qcl_model {
+  int ns = 0, n = 0;
+  double hbar = 1.0, hop_scale = 1.0, p_max = 0.5;
+  std::vector<double> mass, omega, E, K;
+  qcl::DevModel host{};
+  qcl::DevModel* dev = nullptr;  // device block: DevModel followed by K
+  int device = 0;
+};
+
+namespace qcl {
+// Records `msg` as the calling thread's last error and returns `st`.
+qcl_status set_error(qcl_status st, const char* msg);
+}  // namespace qcl

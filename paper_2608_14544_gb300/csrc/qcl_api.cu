@@ -11,17 +11,10 @@
 #include <vector>
 
 #include "kernels.h"
+#include "model.h"
 
 using namespace qcl;
 
-struct qcl_model {
-  int ns = 0, n = 0;
-  double hbar = 1.0, hop_scale = 1.0, p_max = 0.5;
-  std::vector<double> mass, omega, E, K;
-  DevModel host{};
-  DevModel* dev = nullptr;  // device block: DevModel followed by K
-  int device = 0;
-};
 
 namespace {
 
@@ -107,6 +100,13 @@ qcl_status check_ens(const qcl_model* m, const qcl_ensemble_desc* e) {
 }
 
 }  // namespace
+
+namespace qcl {
+qcl_status set_error(qcl_status st, const char* msg) {
+  g_err = msg ? msg : "";
+  return st;
+}
+}  // namespace qcl
 
 extern "C" {
 

@@ -31,7 +31,7 @@ EXPORTS = [
     "qcl_last_error", "qcl_version", "qcl_set_option", "qcl_launch_count", "qcl_kernel_time",
     "qcl_create_model", "qcl_destroy_model", "qcl_ensemble_bytes", "qcl_obs_bytes",
     "qcl_ensemble_layout", "qcl_sample_initial", "qcl_propagate", "qcl_reduce_observables",
-    "qcl_read_sums", "qcl_ensemble_status",
+    "qcl_read_sums", "qcl_ensemble_status", "qcl_propagate_noalloc",
 ]
 
 
@@ -90,6 +90,8 @@ def load(path: str = LIB_PATH):
     lib.qcl_reduce_observables.argtypes = [vp, vp, vp, sz, i64, i64, i64, vp, sz, vp]
     lib.qcl_read_sums.argtypes = [vp, vp, vp, sz, i64, i64, i64, vp, sz, vp]
     lib.qcl_ensemble_status.argtypes = [vp, vp, vp, sz, vp, vp]
+    lib.qcl_propagate_noalloc.argtypes = [vp, vp, vp, sz, i64, i64, C.c_double, i32, vp, sz, i64,
+                                          vp]
     for name in EXPORTS:
         f = getattr(lib, name)
         if name not in ("qcl_last_error", "qcl_version"):
@@ -216,6 +218,18 @@ def propagate(model: Model, ens: EnsembleDesc, ens_buf, step0: int, n_steps: int
                                 ens_buf.numel() * ens_buf.element_size(), step0, n_steps, dt,
                                 out_stride, _dptr(obs_buf), obs_buf.numel() * obs_buf.element_size(),
                                 n_out, _stream_ptr(stream)), "qcl_propagate")
+
+
+def propagate_noalloc(model: Model, ens: EnsembleDesc, ens_buf, step0: int, n_steps: int,
+                      dt: float, out_stride: int, rows, n_out: int, stream=None):
+    """qcl_propagate_noalloc: FP32-bulk propagation whose scratch lives in the
+    library's static device array; `rows` is a caller-owned device tensor of
+    n_out x 8 NS^2 float64 that receives the output rows."""
+    _check(load().qcl_propagate_noalloc(model.handle, C.byref(ens), _dptr(ens_buf),
+                                        ens_buf.numel() * ens_buf.element_size(), step0, n_steps,
+                                        dt, out_stride, _dptr(rows),
+                                        rows.numel() * rows.element_size(), n_out,
+                                        _stream_ptr(stream)), "qcl_propagate_noalloc")
 
 
 def reduce_observables(model: Model, ens: EnsembleDesc, obs_buf, n_out: int, k0: int = 0,
