@@ -66,12 +66,13 @@ extern "C" qcl_status qcl_propagate_noalloc(const qcl_model* model, const qcl_en
   if (!model || !ens) return fail(QCL_ERR_INVALID_ARG, "model or ensemble descriptor is NULL");
   if (ens->precision != QCL_PREC_FP32_BULK)
     return fail(QCL_ERR_UNSUPPORTED, "qcl_propagate_noalloc runs FP32-bulk ensembles only");
-  if (model->ns != 2 || model->n > 32)
-    return fail(QCL_ERR_UNSUPPORTED, "qcl_propagate_noalloc supports two-state models with <= 32 modes");
+  if (model->ns != 2)
+    return fail(QCL_ERR_UNSUPPORTED, "qcl_propagate_noalloc supports two-state models");
   if (ens->n_traj < 1) return fail(QCL_ERR_INVALID_ARG, "n_traj must be >= 1");
   // static-scratch capacity: per output time n_tiles x q2 partials plus fold scratch
   const int q2 = 8 * model->ns * model->ns;
-  const int64_t n_tiles = (ens->n_traj + kTile - 1) / kTile;
+  const int tile = tile_walkers(ens->precision, model->n);
+  const int64_t n_tiles = (ens->n_traj + tile - 1) / tile;
   const int64_t nb1 = (n_tiles + kFoldBlock - 1) / kFoldBlock;
   const int64_t per_slot = n_tiles * q2 + (nb1 + (nb1 + kFoldBlock - 1) / kFoldBlock + 1) * q2;
   int64_t slots = (int64_t)kScratchDoubles / per_slot;
@@ -80,7 +81,7 @@ extern "C" qcl_status qcl_propagate_noalloc(const qcl_model* model, const qcl_en
                 "n_traj = %lld needs %lld bytes of scratch per output time; the static scratch holds "
                 "%zu bytes (at most about %lld walkers)",
                 (long long)ens->n_traj, (long long)(per_slot * 8), kScratchBytes,
-                (long long)((int64_t)kScratchDoubles / (q2 + 1) * kTile * 99 / 100));
+                (long long)((int64_t)kScratchDoubles / (q2 + 1) * tile * 99 / 100));
   if (slots > kChunkOut) slots = kChunkOut;
   if (!ens_buf || !rows) return fail(QCL_ERR_INVALID_ARG, "ens_buf or rows is NULL");
   if (((uintptr_t)ens_buf & 255) != 0 || ((uintptr_t)rows & 7) != 0)

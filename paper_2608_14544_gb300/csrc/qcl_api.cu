@@ -94,8 +94,6 @@ qcl_status check_ens(const qcl_model* m, const qcl_ensemble_desc* e) {
   if (e->precision != QCL_PREC_FP64 && e->precision != QCL_PREC_FP32_BULK)
     return fail(QCL_ERR_INVALID_ARG, "unknown precision %d", e->precision);
   if (m->ns != 2) return fail(QCL_ERR_UNSUPPORTED, "only two-state models are built (n_states = %d)", m->ns);
-  if (e->precision == QCL_PREC_FP32_BULK && m->n > 32)
-    return fail(QCL_ERR_UNSUPPORTED, "FP32-bulk path supports n_modes <= 32 (got %d)", m->n);
   return QCL_OK;
 }
 
@@ -278,7 +276,7 @@ qcl_status qcl_obs_bytes(const qcl_model* model, const qcl_ensemble_desc* ens, i
   qcl_status st = check_ens(model, ens);
   if (st) return st;
   if (n_out < 1) return fail(QCL_ERR_INVALID_ARG, "n_out must be >= 1");
-  *bytes = ObsLayout::make(ens->n_traj, model->ns, n_out).total;
+  *bytes = ObsLayout::make(ens->n_traj, model->ns, n_out, tile_walkers(ens->precision, model->n)).total;
   return ok();
 }
 
@@ -341,7 +339,7 @@ qcl_status qcl_propagate(const qcl_model* model, const qcl_ensemble_desc* ens, v
   if (k_last >= n_out) return fail(QCL_ERR_INVALID_ARG, "output row %lld beyond n_out = %lld", (long long)k_last, (long long)n_out);
   const EnsLayout EL = EnsLayout::make(ens->n_traj, model->ns, model->n, ens->precision);
   if (ens_bytes < EL.total) return fail(QCL_ERR_OUT_OF_MEMORY, "ens_buf has %zu bytes, needs %zu", ens_bytes, EL.total);
-  const ObsLayout OL = ObsLayout::make(ens->n_traj, model->ns, n_out);
+  const ObsLayout OL = ObsLayout::make(ens->n_traj, model->ns, n_out, tile_walkers(ens->precision, model->n));
   if (obs_bytes < OL.total) return fail(QCL_ERR_OUT_OF_MEMORY, "obs_buf has %zu bytes, needs %zu", obs_bytes, OL.total);
   cudaStream_t s = (cudaStream_t)stream;
   char* ob = (char*)obs_buf;
@@ -458,7 +456,7 @@ qcl_status qcl_reduce_observables(const qcl_model* model, const qcl_ensemble_des
   if (st) return st;
   if (!obs_buf || !host_out) return fail(QCL_ERR_INVALID_ARG, "obs_buf or host_out is NULL");
   if (n_out < 1 || k0 < 0 || n_rows < 0 || k0 + n_rows > n_out) return fail(QCL_ERR_INVALID_ARG, "rows [%lld, %lld) outside [0, %lld)", (long long)k0, (long long)(k0 + n_rows), (long long)n_out);
-  const ObsLayout OL = ObsLayout::make(ens->n_traj, model->ns, n_out);
+  const ObsLayout OL = ObsLayout::make(ens->n_traj, model->ns, n_out, tile_walkers(ens->precision, model->n));
   if (obs_bytes < OL.total) return fail(QCL_ERR_OUT_OF_MEMORY, "obs_buf has %zu bytes, needs %zu", obs_bytes, OL.total);
   const int nq = OL.q2 / 2;
   const size_t per = (size_t)(2 * nq + 3);
@@ -481,7 +479,7 @@ qcl_status qcl_read_sums(const qcl_model* model, const qcl_ensemble_desc* ens, c
   if (st) return st;
   if (!obs_buf || !host_out) return fail(QCL_ERR_INVALID_ARG, "obs_buf or host_out is NULL");
   if (n_out < 1 || k0 < 0 || n_rows < 0 || k0 + n_rows > n_out) return fail(QCL_ERR_INVALID_ARG, "rows outside [0, n_out)");
-  const ObsLayout OL = ObsLayout::make(ens->n_traj, model->ns, n_out);
+  const ObsLayout OL = ObsLayout::make(ens->n_traj, model->ns, n_out, tile_walkers(ens->precision, model->n));
   if (obs_bytes < OL.total) return fail(QCL_ERR_OUT_OF_MEMORY, "obs_buf has %zu bytes, needs %zu", obs_bytes, OL.total);
   if (host_len < (size_t)OL.q2 * n_rows) return fail(QCL_ERR_INVALID_ARG, "host_out too small");
   if (n_rows == 0) return ok();

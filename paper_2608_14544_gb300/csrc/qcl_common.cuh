@@ -167,14 +167,24 @@ struct EnsLayout {
 constexpr int kChunkOut = 16;      // output times per persistent launch
 constexpr int kFoldBlock = 1024;   // tiles per first-level fold block (power of two)
 
+// Threads per walker of the FP32-bulk kernel for a model of n modes: up to 32
+// modes a thread holds a whole walker in registers; beyond that the walker's
+// modes are split over 2 or 4 warps (one thread of each).  A tile (the unit of
+// the fixed reduction tree) is one block of 256 threads: 256 / that walkers.
+__host__ __device__ inline int bulk_lanes(int n) { return n <= 32 ? 1 : (n <= 100 ? 2 : 4); }
+__host__ __device__ inline int tile_walkers(int precision, int n) {
+  return precision == QCL_PREC_FP64 ? kTile : kTile / bulk_lanes(n);
+}
+
 struct ObsLayout {
   size_t off_rows, off_part, off_fin, off_fold, total;
   int64_t n_tiles, n_fold_blocks;
   int q2;
-  __host__ __device__ static ObsLayout make(int64_t n_traj, int ns, int64_t n_out) {
+  __host__ __device__ static ObsLayout make(int64_t n_traj, int ns, int64_t n_out,
+                                            int tile = kTile) {
     ObsLayout L{};
     L.q2 = 8 * ns * ns;
-    L.n_tiles = (n_traj + kTile - 1) / kTile;
+    L.n_tiles = (n_traj + tile - 1) / tile;
     L.n_fold_blocks = (L.n_tiles + kFoldBlock - 1) / kFoldBlock;
     size_t o = 0;
     L.off_rows = o;

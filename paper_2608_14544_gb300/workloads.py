@@ -118,6 +118,19 @@ def random_lvc4(request_id: int, n_modes: int = 6):
     return _model(E, K, np.ones(n_modes), omega, name=f"random-lvc4-{request_id}")
 
 
+def random_lvc2(n_modes: int, seed: int, scale: float = 0.3):
+    """Random two-state LVC model with every gradient (s_j, a_j, b_j) nonzero:
+    unit masses, frequencies ~ U(0.5, 2), E = [[0.3, 0.2], [0.2, -0.3]]."""
+    rng = np.random.default_rng(seed)
+    omega = rng.uniform(0.5, 2.0, size=n_modes)
+    E = np.array([[0.3, 0.2], [0.2, -0.3]])
+    K = np.zeros((n_modes, 2, 2))
+    for j in range(n_modes):
+        a, b, s = rng.normal(size=3) * scale / np.sqrt(n_modes) * omega[j]
+        K[j] = np.array([[s + a, b], [b, s - a]])
+    return _model(E, K, np.ones(n_modes), omega, name=f"random-lvc2-{n_modes}")
+
+
 # --------------------------------------------------------------------- configs
 def config(idx: int):
     """Returns dict(model, init, n_traj, dt, n_steps, out_stride, seed, precision)."""

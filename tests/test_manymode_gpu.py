@@ -1,0 +1,88 @@
+"""Many-mode FP32-bulk kernels (a walker's modes split over 2 or 4 warps)
+against the FP64 path on matched walkers and against the oracle, and the
+bitwise invariance of their results under chunking and launch shape."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2608_14544_gb300 import workloads as wl
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def q():
+    import torch
+
+    from paper_2608_14544_gb300 import build, qcl
+
+    build.build()
+    oracle.build()
+    torch.cuda.set_device(0)
+    return qcl
+
+
+def _run(q, model, init, n, prec, steps, stride, dt, seed, splits=None, cap=0):
+    q.set_option(q.OPT_GRID_CAP, cap)
+    m = q.Model(model)
+    run = q.Run(m, n, seed, prec, steps // stride + 1)
+    run.sample(init)
+    for k in (splits or (steps,)):
+        run.propagate(k, dt, stride)
+    q.set_option(q.OPT_GRID_CAP, 0)
+    return run
+
+
+def _compare(a, b, n_rows_needed=5):
+    se = np.sqrt(a[:, 16:32] ** 2 + b[:, 16:32] ** 2)
+    diff = np.abs(a[:, :16] - b[:, :16])
+    assert np.all(np.isfinite(b[:, :32]))
+    assert np.all(diff <= 3 * se + 1e-9), (diff / (se + 1e-300)).max()
+    resolved = se.max(axis=1) < 1e-2
+    assert resolved.sum() >= n_rows_needed
+    assert diff[resolved].max() < 1e-3
+
+
+@pytest.mark.parametrize("n_modes,kind", [(100, "sb"), (40, "lvc"), (100, "lvc"), (120, "lvc"),
+                                          (200, "sb")])
+def test_manymode_fp32_matches_fp64(q, n_modes, kind):
+    if kind == "sb":
+        w, c = wl.ohmic_modes(n_modes, 0.25, 5.0)
+        model = wl.spin_boson(1.0, 1.0, w, c)
+        init = wl.sb_init(model, beta=1.0)
+        dt, steps, stride = 0.005, 400, 20
+    else:
+        model = wl.random_lvc2(n_modes, seed=n_modes)
+        init = wl.sb_init(model, beta=2.0)
+        dt, steps, stride = 0.01, 300, 10
+    n = 60_000
+    a = _run(q, model, init, n, q.PREC_FP64, steps, stride, dt, 3).observables()
+    b = _run(q, model, init, n, q.PREC_FP32_BULK, steps, stride, dt, 3)
+    assert b.status()["flags"] == 0
+    _compare(a, b.observables())
+
+
+def test_config4_fp32_matches_oracle(q):
+    cfg = wl.config(4)
+    n, steps, stride = 1500, 400, 20
+    b = _run(q, cfg["model"], cfg["init"], n, q.PREC_FP32_BULK, steps, stride, cfg["dt"], 7)
+    obs = b.observables()
+    om = oracle.OracleModel(cfg["model"])
+    ref, _ = oracle.run(om, oracle.OracleInit(om, cfg["init"]), 7, 0, n, cfg["dt"], steps, stride)
+    mean, se = oracle.finalize(ref, n)
+    diff = np.abs(obs[:, :16] - mean)
+    assert np.all(diff <= 3 * se + 1e-9), (diff / (se + 1e-300)).max()
+
+
+@pytest.mark.parametrize("n_modes", [64, 100, 128])
+def test_split_kernel_chunking_and_launch_shape_bitwise(q, n_modes):
+    model = wl.random_lvc2(n_modes, seed=1)
+    init = wl.sb_init(model, beta=2.0)
+    outs = []
+    for splits, cap in (((200,), 0), ((70, 130), 0), ((200,), 5)):
+        r = _run(q, model, init, 20_000, q.PREC_FP32_BULK, 200, 10, 0.01, 2, splits, cap)
+        outs.append((r.sums(), r.state()))
+    for sums, st in outs[1:]:
+        assert np.array_equal(sums, outs[0][0])
+        for k in st:
+            assert np.array_equal(st[k], outs[0][1][k]), k
