@@ -311,6 +311,31 @@ def run_ours(args):
     e2e = {"value": traj_steps / e2e_s, "unit": "traj-steps/s", "h2d_bytes_per_step": int(h2d),
            "d2h_bytes_per_step": int(host_obs.nbytes)}
 
+    # many-mode workload (100-mode ohmic spin-boson, the configuration where the
+    # FP32 FMA work dominates): bounded walker count, all 4000 steps
+    c4 = wl.config(4)
+    n4 = args.sb100_walkers
+    m4 = qcl.Model(c4["model"])
+    r4 = qcl.Run(m4, n4, c4["seed"], qcl.PREC_FP32_BULK, c4["n_steps"] // c4["out_stride"] + 1,
+                 traj_id_offset=rank * n4)
+    r4.sample(c4["init"])
+    r4.propagate(c4["n_steps"], c4["dt"], c4["out_stride"])
+    torch.cuda.synchronize()
+    r4.sample(c4["init"])
+    qcl.kernel_time(qcl.KERNEL_BULK)
+    qcl.set_option(qcl.OPT_TIMING, 1)
+    g0 = torch.cuda.Event(enable_timing=True)
+    g1 = torch.cuda.Event(enable_timing=True)
+    g0.record(stream)
+    r4.propagate(c4["n_steps"], c4["dt"], c4["out_stride"])
+    g1.record(stream)
+    torch.cuda.synchronize()
+    qcl.set_option(qcl.OPT_TIMING, 0)
+    k4_ms, k4_n = qcl.kernel_time(qcl.KERNEL_BULK)
+    rate4 = float(n4) * c4["n_steps"] / (g0.elapsed_time(g1) / 1e3)
+    st4 = r4.status()
+    del r4
+
     if rank != 0:
         if dist:
             dist.destroy_process_group()
@@ -364,6 +389,16 @@ def run_ours(args):
                             "sample": f"{n:.0e} walkers x {fp64_steps - stride} steps, one "
                                       "launch per step", "step_kernel_ms": f64_ms / max(f64_n, 1),
                             "speedup_of_fp32_bulk": value / world / fp64_rate},
+        "sb100": {"workload": f"100-mode ohmic spin-boson (eps=Delta=1, xi=0.25, wc=5, beta=1), "
+                              f"{n4} walkers x {c4['n_steps']} steps, dt={c4['dt']}",
+                  "value": rate4, "unit": "traj-steps/s",
+                  "flops_per_traj_step": flops_per_traj_step(c4["model"]),
+                  "achieved_tflops": float(n4) * c4["n_steps"] * flops_per_traj_step(c4["model"])
+                  / (k4_ms / 1e3) / 1e12 if k4_ms > 0 else None,
+                  "frac_of_fp32_peak": (float(n4) * c4["n_steps"] * flops_per_traj_step(c4["model"])
+                                        / (k4_ms / 1e3) / 1e12 / peak_tflops) if k4_ms > 0 else None,
+                  "kernel": "k_bulk2_split (two warps per 32 walkers)",
+                  "status_flags": st4["flags"]},
         "clocks": clocks,
         "result": _result_summary(obs, cfg, status),
     }
@@ -379,6 +414,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--sb100-walkers", type=int, default=2_000_000)
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

@@ -33,11 +33,15 @@ def _run(q, model, init, n, prec, steps, stride, dt, seed, splits=None, cap=0):
     return run
 
 
-def _compare(a, b, n_rows_needed=5):
+def _compare(a, b, n_rows_needed=4):
     se = np.sqrt(a[:, 16:32] ** 2 + b[:, 16:32] ** 2)
     diff = np.abs(a[:, :16] - b[:, :16])
     assert np.all(np.isfinite(b[:, :32]))
     assert np.all(diff <= 3 * se + 1e-9), (diff / (se + 1e-300)).max()
+    # matched walkers: same sample, so t = 0 agrees to FP32 rounding
+    assert diff[0].max() < 1e-5
+    # the no-spawn weights grow like exp(2 int |P d/M| dt): the 1e-3 bound applies
+    # while the estimator resolves it
     resolved = se.max(axis=1) < 1e-2
     assert resolved.sum() >= n_rows_needed
     assert diff[resolved].max() < 1e-3
@@ -50,12 +54,11 @@ def test_manymode_fp32_matches_fp64(q, n_modes, kind):
         w, c = wl.ohmic_modes(n_modes, 0.25, 5.0)
         model = wl.spin_boson(1.0, 1.0, w, c)
         init = wl.sb_init(model, beta=1.0)
-        dt, steps, stride = 0.005, 400, 20
+        dt, steps, stride, n = 0.005, 100, 2, 400_000
     else:
-        model = wl.random_lvc2(n_modes, seed=n_modes)
+        model = wl.random_lvc2(n_modes, seed=n_modes, scale=0.1)
         init = wl.sb_init(model, beta=2.0)
-        dt, steps, stride = 0.01, 300, 10
-    n = 60_000
+        dt, steps, stride, n = 0.01, 300, 10, 60_000
     a = _run(q, model, init, n, q.PREC_FP64, steps, stride, dt, 3).observables()
     b = _run(q, model, init, n, q.PREC_FP32_BULK, steps, stride, dt, 3)
     assert b.status()["flags"] == 0
