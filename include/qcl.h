@@ -198,10 +198,13 @@ qcl_status qcl_read_sums(const qcl_model* model, const qcl_ensemble_desc* ens,
 /* Byte offsets of the ensemble buffer's arrays: [0] R, [1] P, [2] weight
  * (FP64 value, or FP32 high part), [3] FP32 weight low part, [4] phase (FP64, or
  * FP32 high part), [5] FP32 phase low part, [6] index pair (uint16: a | b << 8),
- * [7] total bytes, [8] FP32 weight exponent (int32: weight = (hi + lo) 2^e).
- * R and P are [n_modes][n_traj]; element size 8 (FP64) or 4 (FP32 bulk). */
+ * [7] total bytes, [8] FP32 weight exponent (int32: weight = (hi + lo) 2^e),
+ * [9] eigenvectors U [n_states^2][n_traj] (U[i][a] at row i*NS + a; models with
+ * more than two states), [10] FP32 eigenvalues [n_states][n_traj] (FP32-bulk
+ * models with more than two states).  R and P are [n_modes][n_traj]; element
+ * size 8 (FP64) or 4 (FP32 bulk). */
 qcl_status qcl_ensemble_layout(const qcl_model* model, const qcl_ensemble_desc* ens,
-                               size_t offsets[9]);
+                               size_t offsets[11]);
 
 /* Reads the ensemble header's status words (synchronises `stream`). */
 qcl_status qcl_ensemble_status(const qcl_model* model, const qcl_ensemble_desc* ens,

@@ -56,7 +56,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
     newest = max(os.path.getmtime(p) for p in srcs + _headers())
     if not force and os.path.exists(LIB) and os.path.getmtime(LIB) >= newest:
         return LIB
-    with cf.ThreadPoolExecutor(max_workers=min(8, len(srcs))) as ex:
+    with cf.ThreadPoolExecutor(max_workers=min(16, len(srcs))) as ex:
         results = list(ex.map(lambda s: _compile(s, verbose), srcs))
     if verbose:
         for _, log in results:

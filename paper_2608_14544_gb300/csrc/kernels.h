@@ -51,6 +51,18 @@ struct BulkParams {
   float kdt;           // hop_scale * dt
   float p_max;
   uint32_t tmax;       // floor(p_max 2^24)
+  float kappa;         // hop_scale
+  float pad;
+};
+
+// FP32 coefficients of an N_s-state model (N_s <= 8, n_modes <= 32): upper
+// triangles (row-major a <= b) of E and of each K_j.
+struct CoefN {
+  float hk[32];    // dt/2 * k_j
+  float dtm[32];   // dt / M_j
+  float minv[32];  // 1 / M_j
+  float K[32][36];
+  float E[36];
 };
 
 // Kernel launches issued by the library (instrumentation).
@@ -69,6 +81,15 @@ int launch_bulk2(const BulkParams& bp, const Coef2& cf, void* buf, double* part,
                  cudaStream_t st);
 // Kernel-selection description of the bulk kernel chosen for (n, kind).
 const char* bulk2_variant(int n, int kind);
+
+void launch_sampleN(const DevModel* dm, const SampleParams& sp, void* buf, int precision,
+                    cudaStream_t st);
+void launch_stepN_f64(const DevModel* dm, int ns, void* buf, int64_t nt, int n, int64_t step0,
+                      int64_t step, double dt, uint64_t seed, uint64_t traj_off, cudaStream_t st);
+void launch_observeN_f64(int ns, const void* buf, int64_t nt, int n, double* part,
+                         cudaStream_t st);
+int launch_bulkN(int ns, const BulkParams& bp, const CoefN& cf, void* buf, double* part,
+                 int grid_cap, cudaStream_t st);
 
 void launch_fold(const double* part, double* rows_out, double* scratch, int64_t n_tiles,
                  int q2, int n_slots, cudaStream_t st);

@@ -1,0 +1,65 @@
+// kernels_nstate.cu -- dispatch of the N_s-state launchers (N_s = 3..8) to
+// their per-N_s translation units (kernels_nstate_3.cu .. kernels_nstate_8.cu).
+#include "kernels.h"
+
+namespace qcl {
+
+#define QCL_NS_DECL(k)                                                                        \
+  void nstate_sample_##k(const DevModel*, const SampleParams&, void*, int, cudaStream_t);     \
+  void nstate_step64_##k(const DevModel*, void*, int64_t, int, int64_t, int64_t, double,      \
+                         uint64_t, uint64_t, cudaStream_t);                                   \
+  void nstate_observe64_##k(const void*, int64_t, int, double*, cudaStream_t);                \
+  int nstate_bulk_##k(const BulkParams&, const CoefN&, void*, double*, int, cudaStream_t);
+QCL_NS_DECL(3)
+QCL_NS_DECL(4)
+QCL_NS_DECL(5)
+QCL_NS_DECL(6)
+QCL_NS_DECL(7)
+QCL_NS_DECL(8)
+
+#define QCL_NS_SWITCH(ns, F, ...)          \
+  switch (ns) {                            \
+    case 3: F##_3(__VA_ARGS__); break;     \
+    case 4: F##_4(__VA_ARGS__); break;     \
+    case 5: F##_5(__VA_ARGS__); break;     \
+    case 6: F##_6(__VA_ARGS__); break;     \
+    case 7: F##_7(__VA_ARGS__); break;     \
+    case 8: F##_8(__VA_ARGS__); break;     \
+    default: break;                        \
+  }
+
+void launch_sampleN(const DevModel* dm, const SampleParams& sp, void* buf, int precision,
+                    cudaStream_t st) {
+  QCL_NS_SWITCH(sp.ns, nstate_sample, dm, sp, buf, precision, st);
+  launches_add(1);
+}
+
+void launch_stepN_f64(const DevModel* dm, int ns, void* buf, int64_t nt, int n, int64_t step0,
+                      int64_t step, double dt, uint64_t seed, uint64_t traj_off, cudaStream_t st) {
+  QCL_NS_SWITCH(ns, nstate_step64, dm, buf, nt, n, step0, step, dt, seed, traj_off, st);
+  launches_add(1);
+}
+
+void launch_observeN_f64(int ns, const void* buf, int64_t nt, int n, double* part,
+                         cudaStream_t st) {
+  QCL_NS_SWITCH(ns, nstate_observe64, buf, nt, n, part, st);
+  launches_add(1);
+}
+
+int launch_bulkN(int ns, const BulkParams& bp, const CoefN& cf, void* buf, double* part,
+                 int grid_cap, cudaStream_t st) {
+  int g = 0;
+  switch (ns) {
+    case 3: g = nstate_bulk_3(bp, cf, buf, part, grid_cap, st); break;
+    case 4: g = nstate_bulk_4(bp, cf, buf, part, grid_cap, st); break;
+    case 5: g = nstate_bulk_5(bp, cf, buf, part, grid_cap, st); break;
+    case 6: g = nstate_bulk_6(bp, cf, buf, part, grid_cap, st); break;
+    case 7: g = nstate_bulk_7(bp, cf, buf, part, grid_cap, st); break;
+    case 8: g = nstate_bulk_8(bp, cf, buf, part, grid_cap, st); break;
+    default: break;
+  }
+  if (g) launches_add(1);
+  return g;
+}
+
+}  // namespace qcl

@@ -1,0 +1,202 @@
+// nstate.cuh -- adiabatic decomposition and couplings of N_s-state linear
+// vibronic-coupling models (N_s = 3..8) for the FP64 and FP32-bulk kernels.
+//
+// W(R) = E + sum_j R_j K_j is diagonalised by cyclic Jacobi rotations.  Along a
+// trajectory the previous eigenvectors U_ref are the starting basis (the
+// rotated matrix U_ref^T W U_ref is nearly diagonal), the eigenvalues are
+// sorted ascending and each eigenvector's sign is aligned with its reference
+// (parallel transport), which makes the couplings d_ab and the products
+// U_ia U_jb continuous along the path.  Without a reference (initial sample)
+// the largest-magnitude component of each eigenvector is made positive.
+#pragma once
+#include "qcl_common.cuh"
+
+namespace qcl {
+
+template <typename T>
+__device__ __forceinline__ T q_sqrt(T x) {
+  return sqrt(x);
+}
+template <>
+__device__ __forceinline__ float q_sqrt<float>(float x) {
+  return sqrtf(x);
+}
+
+// One Jacobi rotation annihilating A[p][q] of the symmetric matrix A and
+// accumulating it into the columns of V (Golub & Van Loan, symmetric Schur).
+template <typename T, int NS>
+__device__ __forceinline__ void jacobi_rotate(T (&A)[NS][NS], T (&V)[NS][NS], int p, int q) {
+  const T apq = A[p][q];
+  if (apq == T(0)) return;
+  const T tau = (A[q][q] - A[p][p]) / (T(2) * apq);
+  const T t = (tau >= T(0) ? T(1) : T(-1)) / (fabs(tau) + q_sqrt<T>(T(1) + tau * tau));
+  const T c = T(1) / q_sqrt<T>(T(1) + t * t);
+  const T s = t * c;
+#pragma unroll
+  for (int k = 0; k < NS; ++k) {  // A <- A J (columns p, q)
+    const T akp = A[k][p], akq = A[k][q];
+    A[k][p] = c * akp - s * akq;
+    A[k][q] = s * akp + c * akq;
+  }
+#pragma unroll
+  for (int k = 0; k < NS; ++k) {  // A <- J^T A (rows p, q)
+    const T apk = A[p][k], aqk = A[q][k];
+    A[p][k] = c * apk - s * aqk;
+    A[q][k] = s * apk + c * aqk;
+  }
+#pragma unroll
+  for (int k = 0; k < NS; ++k) {  // V <- V J
+    const T vkp = V[k][p], vkq = V[k][q];
+    V[k][p] = c * vkp - s * vkq;
+    V[k][q] = s * vkp + c * vkq;
+  }
+}
+
+template <typename T, int NS>
+__device__ __forceinline__ T offdiag2(const T (&A)[NS][NS]) {
+  T off = T(0);
+#pragma unroll
+  for (int p = 0; p < NS; ++p)
+#pragma unroll
+    for (int q = p + 1; q < NS; ++q) off += A[p][q] * A[p][q];
+  return off;
+}
+
+// Diagonalises A (destroyed) into ascending e and eigenvectors U[i][a]; with
+// `ref` the rotation starts from ref's basis and the signs follow ref.
+// Sweeps: at most max_sweeps, stopping when the off-diagonal mass is below
+// tol2 times the matrix norm (a fixed sweep count when tol2 < 0).
+template <typename T, int NS>
+__device__ __forceinline__ void eigh_ns(const T (&W)[NS][NS], const T (*ref)[NS], T (&e)[NS],
+                                        T (&U)[NS][NS], int max_sweeps, T tol2) {
+  T A[NS][NS], V[NS][NS];
+  if (ref) {
+    // A = ref^T W ref
+    T Wr[NS][NS];
+#pragma unroll
+    for (int i = 0; i < NS; ++i)
+#pragma unroll
+      for (int b = 0; b < NS; ++b) {
+        T acc = T(0);
+#pragma unroll
+        for (int k = 0; k < NS; ++k) acc += W[i][k] * ref[k][b];
+        Wr[i][b] = acc;
+      }
+#pragma unroll
+    for (int a = 0; a < NS; ++a)
+#pragma unroll
+      for (int b = 0; b < NS; ++b) {
+        T acc = T(0);
+#pragma unroll
+        for (int k = 0; k < NS; ++k) acc += ref[k][a] * Wr[k][b];
+        A[a][b] = acc;
+      }
+    // symmetrise the rotated matrix (rounding)
+#pragma unroll
+    for (int a = 0; a < NS; ++a)
+#pragma unroll
+      for (int b = a + 1; b < NS; ++b) {
+        const T m = T(0.5) * (A[a][b] + A[b][a]);
+        A[a][b] = m;
+        A[b][a] = m;
+      }
+  } else {
+#pragma unroll
+    for (int a = 0; a < NS; ++a)
+#pragma unroll
+      for (int b = 0; b < NS; ++b) A[a][b] = W[a][b];
+  }
+#pragma unroll
+  for (int a = 0; a < NS; ++a)
+#pragma unroll
+    for (int b = 0; b < NS; ++b) V[a][b] = (a == b) ? T(1) : T(0);
+  T fro = T(0);
+#pragma unroll
+  for (int a = 0; a < NS; ++a)
+#pragma unroll
+    for (int b = 0; b < NS; ++b) fro += A[a][b] * A[a][b];
+  for (int sweep = 0; sweep < max_sweeps; ++sweep) {
+    if (tol2 >= T(0) && offdiag2<T, NS>(A) <= tol2 * fro) break;
+#pragma unroll
+    for (int p = 0; p < NS; ++p)
+#pragma unroll
+      for (int q = p + 1; q < NS; ++q) jacobi_rotate<T, NS>(A, V, p, q);
+  }
+  // eigenvectors in the original basis
+  if (ref) {
+#pragma unroll
+    for (int i = 0; i < NS; ++i)
+#pragma unroll
+      for (int b = 0; b < NS; ++b) {
+        T acc = T(0);
+#pragma unroll
+        for (int k = 0; k < NS; ++k) acc += ref[i][k] * V[k][b];
+        U[i][b] = acc;
+      }
+  } else {
+#pragma unroll
+    for (int i = 0; i < NS; ++i)
+#pragma unroll
+      for (int b = 0; b < NS; ++b) U[i][b] = V[i][b];
+  }
+#pragma unroll
+  for (int a = 0; a < NS; ++a) e[a] = A[a][a];
+  // ascending order (stable insertion sort; fixed compare pattern)
+#pragma unroll
+  for (int i = 1; i < NS; ++i)
+#pragma unroll
+    for (int j = i; j > 0; --j) {
+      const bool sw = e[j] < e[j - 1];
+      const T t0 = e[j], t1 = e[j - 1];
+      e[j] = sw ? t1 : t0;
+      e[j - 1] = sw ? t0 : t1;
+#pragma unroll
+      for (int k = 0; k < NS; ++k) {
+        const T u0 = U[k][j], u1 = U[k][j - 1];
+        U[k][j] = sw ? u1 : u0;
+        U[k][j - 1] = sw ? u0 : u1;
+      }
+    }
+  // gauge: follow the reference, else largest-magnitude component positive
+#pragma unroll
+  for (int a = 0; a < NS; ++a) {
+    bool flip;
+    if (ref) {
+      T dot = T(0);
+#pragma unroll
+      for (int i = 0; i < NS; ++i) dot += U[i][a] * ref[i][a];
+      flip = dot < T(0);
+    } else {
+      int imax = 0;
+      T vmax = fabs(U[0][a]);
+#pragma unroll
+      for (int i = 1; i < NS; ++i) {
+        const bool g = fabs(U[i][a]) > vmax;
+        vmax = g ? fabs(U[i][a]) : vmax;
+        imax = g ? i : imax;
+      }
+      T v = U[0][a];
+#pragma unroll
+      for (int i = 1; i < NS; ++i) v = (i == imax) ? U[i][a] : v;
+      flip = v < T(0);
+    }
+#pragma unroll
+    for (int i = 0; i < NS; ++i) U[i][a] = flip ? -U[i][a] : U[i][a];
+  }
+}
+
+// u_a^T M u_b for a symmetric M given as a full matrix
+template <typename T, int NS>
+__device__ __forceinline__ T bilinear(const T (&M)[NS][NS], const T (&U)[NS][NS], int a, int b) {
+  T acc = T(0);
+#pragma unroll
+  for (int k = 0; k < NS; ++k) {
+    T row = T(0);
+#pragma unroll
+    for (int l = 0; l < NS; ++l) row += M[k][l] * U[l][b];
+    acc += U[k][a] * row;
+  }
+  return acc;
+}
+
+}  // namespace qcl

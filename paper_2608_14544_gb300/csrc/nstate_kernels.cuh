@@ -1,0 +1,861 @@
+// nstate_kernels.cuh -- models with N_s = 3..8 electronic states: sampling,
+// the FP64 one-launch-per-step path and the FP32-bulk persistent kernel.
+// The per-step algorithm is the two-state one with the closed form replaced by
+// a Jacobi decomposition carried along the trajectory (nstate.cuh):
+// velocity Verlet on the mean force -1/2 (F_a + F_b), trapezoid phase
+// (e_a - e_b)/hbar, and one transition among the 2 (N_s - 1) events of the
+// coupling term of Eq. 1.
+#pragma once
+#include "kernels.h"
+#include "nstate.cuh"
+#include "reduce.cuh"
+
+namespace qcl {
+
+namespace nsd {
+
+constexpr double kDegTolD = 1e-12;
+constexpr float kDegTolF = 1e-6f;
+
+template <typename T>
+struct WN {
+  T* R;
+  T* P;
+  T* m;
+  T* mlo;
+  int32_t* mexp;
+  T* phi;
+  T* philo;
+  uint16_t* ab;
+  T* U;  // [NS*NS][n_traj]
+  T* E;  // [NS][n_traj] eigenvalues (FP32 bulk)
+  EnsHeader* hdr;
+};
+
+template <typename T>
+__device__ __forceinline__ WN<T> viewN(void* buf, int64_t nt, int ns, int n, int prec) {
+  const EnsLayout L = EnsLayout::make(nt, ns, n, prec);
+  char* b = (char*)buf;
+  return {(T*)(b + L.off_R),    (T*)(b + L.off_P),       (T*)(b + L.off_m),
+          (T*)(b + L.off_mlo),  (int32_t*)(b + L.off_mexp), (T*)(b + L.off_phi),
+          (T*)(b + L.off_philo), (uint16_t*)(b + L.off_ab), (T*)(b + L.off_U),
+          (T*)(b + L.off_E),     (EnsHeader*)b};
+}
+
+// column a of U (runtime a) without indexing a register array at run time
+template <typename T, int NS>
+__device__ __forceinline__ void column(const T (&U)[NS][NS], int a, T (&u)[NS]) {
+#pragma unroll
+  for (int i = 0; i < NS; ++i) {
+    T v = U[i][0];
+#pragma unroll
+    for (int c = 1; c < NS; ++c) v = (c == a) ? U[i][c] : v;
+    u[i] = v;
+  }
+}
+
+template <typename T, int NS>
+__device__ __forceinline__ T pick(const T (&e)[NS], int a) {
+  T v = e[0];
+#pragma unroll
+  for (int c = 1; c < NS; ++c) v = (c == a) ? e[c] : v;
+  return v;
+}
+
+// W(R) = E + sum_j R_j K_j from the device model (FP64 path, R in global memory)
+template <int NS>
+__device__ __forceinline__ void elec_g(const DevModel* M, const double* R, int64_t nt, int n,
+                                       double (&W)[NS][NS]) {
+#pragma unroll
+  for (int a = 0; a < NS; ++a)
+#pragma unroll
+    for (int b = 0; b < NS; ++b) W[a][b] = M->E[a * NS + b];
+  for (int j = 0; j < n; ++j) {
+    const double x = R[(int64_t)j * nt];
+    const double* Kj = M->K + (size_t)j * NS * NS;
+#pragma unroll
+    for (int a = 0; a < NS; ++a)
+#pragma unroll
+      for (int b = 0; b < NS; ++b) W[a][b] += x * Kj[a * NS + b];
+  }
+}
+
+// P += dt/2 F_ab, F_j = -k_j R_j - 1/2 (u_a^T K_j u_a + u_b^T K_j u_b)   (FP64 path)
+template <int NS>
+__device__ __forceinline__ void half_kick_g(const DevModel* M, double* R, double* P, int64_t nt,
+                                            int n, const double (&U)[NS][NS], int al, int be,
+                                            double dt) {
+  double ua[NS], ub[NS];
+  column<double, NS>(U, al, ua);
+  column<double, NS>(U, be, ub);
+  double Q[NS][NS];
+#pragma unroll
+  for (int k = 0; k < NS; ++k)
+#pragma unroll
+    for (int l = 0; l < NS; ++l) Q[k][l] = ua[k] * ua[l] + ub[k] * ub[l];
+  for (int j = 0; j < n; ++j) {
+    const double* Kj = M->K + (size_t)j * NS * NS;
+    double g = 0.0;
+#pragma unroll
+    for (int k = 0; k < NS; ++k)
+#pragma unroll
+      for (int l = 0; l < NS; ++l) g += Kj[k * NS + l] * Q[k][l];
+    const int64_t o = (int64_t)j * nt;
+    const double F = -M->k[j] * R[o] - 0.5 * g;
+    P[o] += 0.5 * dt * F;
+  }
+}
+
+// Event amplitudes of the coupling term of Eq. 1 at (R, P) with decomposition
+// (e, U), one slot per candidate in the fixed event order: slots 0..NS-1 move
+// the first index a -> nu with A = -dt (v.d)_{nu a}, slots NS..2NS-1 move the
+// second index b -> nu with A = +dt (v.d)_{b nu}; (v.d)_{mu nu} =
+// u_mu^T G u_nu / (e_nu - e_mu), G = sum_j (P_j/M_j) K_j.  The slots nu = a and
+// nu = b are not events (amplitude 0, never drawn), so walking the slots in
+// order walks the 2 (NS - 1) events in their order.  Returns true if a needed
+// gap was degenerate.
+template <typename T, int NS>
+__device__ __forceinline__ bool event_amplitudes(const T (&G)[NS][NS], const T (&U)[NS][NS],
+                                                 const T (&e)[NS], int al, int be, T dt, T tol,
+                                                 T (&A)[2 * NS], bool (&is_event)[2 * NS]) {
+  T ua[NS], ub[NS], Gua[NS], Gub[NS];
+  column<T, NS>(U, al, ua);
+  column<T, NS>(U, be, ub);
+#pragma unroll
+  for (int k = 0; k < NS; ++k) {
+    T s0 = T(0), s1 = T(0);
+#pragma unroll
+    for (int l = 0; l < NS; ++l) {
+      s0 += G[k][l] * ua[l];
+      s1 += G[k][l] * ub[l];
+    }
+    Gua[k] = s0;
+    Gub[k] = s1;
+  }
+  const T ea = pick<T, NS>(e, al), eb = pick<T, NS>(e, be);
+  bool deg = false;
+#pragma unroll
+  for (int slot = 0; slot < 2; ++slot) {
+#pragma unroll
+    for (int nu = 0; nu < NS; ++nu) {
+      T h = T(0);
+#pragma unroll
+      for (int k = 0; k < NS; ++k) h += U[k][nu] * (slot == 0 ? Gua[k] : Gub[k]);
+      const T gap = (slot == 0) ? (ea - e[nu]) : (e[nu] - eb);
+      const bool ev = (slot == 0) ? (nu != al) : (nu != be);
+      const bool dg = ev && fabs(gap) < tol;
+      deg |= dg;
+      const T vd = (!ev || dg) ? T(0) : h / gap;
+      A[slot * NS + nu] = (slot == 0) ? -dt * vd : dt * vd;
+      is_event[slot * NS + nu] = ev;
+    }
+  }
+  return deg;
+}
+
+}  // namespace nsd
+using namespace nsd;
+
+// ----------------------------------------------------------- FP64 sampling --
+template <int NS>
+__global__ void __launch_bounds__(128) k_sampleN_f64(const DevModel* __restrict__ M,
+                                                     SampleParams sp, void* buf) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t nt = sp.n_traj;
+  const int n = sp.n;
+  WN<double> w = viewN<double>(buf, nt, NS, n, QCL_PREC_FP64);
+  if (i == 0) {
+    w.hdr->magic = kEnsMagic;
+    w.hdr->n_traj = nt;
+    w.hdr->precision = QCL_PREC_FP64;
+    w.hdr->ns = NS;
+    w.hdr->n = n;
+    w.hdr->step = 0;
+    w.hdr->flags = 0;
+    w.hdr->n_degenerate = 0;
+    w.hdr->n_nonfinite = 0;
+  }
+  if (i >= nt) return;
+  const uint64_t traj = sp.traj_offset + (uint64_t)i;
+  for (int j = 0; j < n; ++j) {
+    double R = sp.R0[j], P = sp.P0[j];
+    if (sp.wigner) {
+      const u4 wd = philox_draw(sp.seed, (uint32_t)j, traj, kPurposeInit);
+      const double u0 = ((double)wd.x + 0.5) * 0x1p-32;
+      const double u1 = ((double)wd.y + 0.5) * 0x1p-32;
+      const double rad = sqrt(-2.0 * log(u0));
+      double sn, cs;
+      sincospi(2.0 * u1, &sn, &cs);
+      R += sp.sR[j] * rad * cs;
+      P += sp.sP[j] * rad * sn;
+    }
+    w.R[(int64_t)j * nt + i] = R;
+    w.P[(int64_t)j * nt + i] = P;
+  }
+  double W[NS][NS], e[NS], U[NS][NS];
+  elec_g<NS>(M, w.R + i, nt, n, W);
+  eigh_ns<double, NS>(W, nullptr, e, U, 100, 1e-34);
+  double rho_ad[NS * NS];
+#pragma unroll
+  for (int al = 0; al < NS; ++al)
+#pragma unroll
+    for (int be = 0; be < NS; ++be) {
+      double acc = 0.0;
+#pragma unroll
+      for (int k = 0; k < NS; ++k)
+#pragma unroll
+        for (int l = 0; l < NS; ++l) acc += U[k][al] * sp.rho[k * NS + l] * U[l][be];
+      rho_ad[al * NS + be] = acc;
+    }
+  double tot = 0.0;
+  for (int k = 0; k < NS * NS; ++k) tot += fabs(rho_ad[k]);
+  uint32_t Tk[NS * NS];
+  uint64_t sumT = 0;
+  int last = 0;
+  for (int k = 0; k < NS * NS; ++k) {
+    Tk[k] = (uint32_t)floor(fabs(rho_ad[k]) / tot * kP24);
+    sumT += Tk[k];
+    if (rho_ad[k] != 0.0) last = k;
+  }
+  Tk[last] += (uint32_t)(16777216ull - sumT);
+  const u4 wd = philox_draw(sp.seed, (uint32_t)n, traj, kPurposeInit);
+  const uint32_t y = wd.x >> 8;
+  uint64_t cum = 0;
+  int pickk = last;
+  for (int k = 0; k < NS * NS; ++k) {
+    cum += Tk[k];
+    if ((uint64_t)y < cum) {
+      pickk = k;
+      break;
+    }
+  }
+  w.m[i] = rho_ad[pickk] / ((double)Tk[pickk] / kP24);
+  w.phi[i] = 0.0;
+  w.ab[i] = (uint16_t)((pickk / NS) | ((pickk % NS) << 8));
+#pragma unroll
+  for (int a = 0; a < NS; ++a)
+#pragma unroll
+    for (int b = 0; b < NS; ++b) w.U[(int64_t)(a * NS + b) * nt + i] = U[a][b];
+}
+
+// --------------------------------------------------------------- FP64 step --
+template <int NS>
+__global__ void __launch_bounds__(128) k_stepN_f64(const DevModel* __restrict__ M, void* buf,
+                                                   int64_t nt, int n, int64_t step0, int64_t step,
+                                                   double dt, uint64_t seed, uint64_t traj_off) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  WN<double> w = viewN<double>(buf, nt, NS, n, QCL_PREC_FP64);
+  if (i >= nt) return;
+  if (w.hdr->step != step0) {
+    if (i == 0) atomicOr(&w.hdr->flags, QCL_FLAG_STEP_MISMATCH);
+    return;
+  }
+  const uint16_t ab = w.ab[i];
+  int al = ab & 0xff, be = ab >> 8;
+  double m = w.m[i], phi = w.phi[i];
+  double Uc[NS][NS];
+#pragma unroll
+  for (int a = 0; a < NS; ++a)
+#pragma unroll
+    for (int b = 0; b < NS; ++b) Uc[a][b] = w.U[(int64_t)(a * NS + b) * nt + i];
+  double* R = w.R + i;
+  double* P = w.P + i;
+  double W[NS][NS], e0[NS], U0[NS][NS], e1[NS], U1[NS][NS];
+  // decomposition at R_n, gauge following the carried eigenvectors
+  elec_g<NS>(M, R, nt, n, W);
+  eigh_ns<double, NS>(W, Uc, e0, U0, 50, 1e-34);
+  half_kick_g<NS>(M, R, P, nt, n, U0, al, be, dt);
+  for (int j = 0; j < n; ++j) R[(int64_t)j * nt] += dt * P[(int64_t)j * nt] / M->mass[j];
+  elec_g<NS>(M, R, nt, n, W);
+  eigh_ns<double, NS>(W, U0, e1, U1, 50, 1e-34);
+  half_kick_g<NS>(M, R, P, nt, n, U1, al, be, dt);
+  const double w0 = (pick<double, NS>(e0, al) - pick<double, NS>(e0, be)) / M->hbar;
+  const double w1 = (pick<double, NS>(e1, al) - pick<double, NS>(e1, be)) / M->hbar;
+  phi += 0.5 * dt * (w0 + w1);
+  bool deg = false;
+#pragma unroll
+  for (int a = 0; a + 1 < NS; ++a) deg |= (e0[a + 1] - e0[a] < kDegTolD) || (e1[a + 1] - e1[a] < kDegTolD);
+  // G = sum_j (P_j/M_j) K_j
+  double G[NS][NS];
+#pragma unroll
+  for (int a = 0; a < NS; ++a)
+#pragma unroll
+    for (int b = 0; b < NS; ++b) G[a][b] = 0.0;
+  for (int j = 0; j < n; ++j) {
+    const double v = P[(int64_t)j * nt] / M->mass[j];
+    const double* Kj = M->K + (size_t)j * NS * NS;
+#pragma unroll
+    for (int a = 0; a < NS; ++a)
+#pragma unroll
+      for (int b = 0; b < NS; ++b) G[a][b] += v * Kj[a * NS + b];
+  }
+  constexpr int NC = 2 * NS;
+  double A[NC];
+  bool ev[NC];
+  deg |= event_amplitudes<double, NS>(G, U1, e1, al, be, dt, kDegTolD, A, ev);
+  // thresholds: min(kappa |A|, p_max) quantised to 2^-24, scaled down together in
+  // exact integers when their sum exceeds Tmax = floor(p_max 2^24)
+  uint64_t T[NC], sumT = 0;
+  const uint64_t Tmax = (uint64_t)floor(M->p_max * kP24);
+#pragma unroll
+  for (int k = 0; k < NC; ++k) {
+    const double p = fmin(M->hop_scale * fabs(A[k]), M->p_max);
+    T[k] = ev[k] ? (uint64_t)floor(p * kP24) : 0;
+    sumT += T[k];
+  }
+  if (sumT > Tmax) {
+    const uint64_t s = sumT;
+    sumT = 0;
+#pragma unroll
+    for (int k = 0; k < NC; ++k) {
+      T[k] = T[k] * Tmax / s;
+      sumT += T[k];
+    }
+  }
+  const u4 wd = philox_draw(seed, (uint32_t)(step >> 2), traj_off + (uint64_t)i, kPurposeHop);
+  const uint64_t y = word_of(wd, (int)(step & 3)) >> 8;
+  uint64_t cum = 0;
+  int hit = -1;
+#pragma unroll
+  for (int k = 0; k < NC; ++k) {
+    cum += T[k];
+    if (hit < 0 && y < cum) hit = k;
+  }
+  if (hit < 0) {
+    m = m / (1.0 - (double)sumT / kP24);
+  } else {
+    double Ah = A[0];
+    uint64_t Th = T[0];
+#pragma unroll
+    for (int k = 1; k < NC; ++k) {
+      Ah = (k == hit) ? A[k] : Ah;
+      Th = (k == hit) ? T[k] : Th;
+    }
+    m = m * Ah / ((double)Th / kP24);
+    if (hit < NS) al = hit;
+    else be = hit - NS;
+  }
+  w.m[i] = m;
+  w.phi[i] = phi;
+  w.ab[i] = (uint16_t)(al | (be << 8));
+#pragma unroll
+  for (int a = 0; a < NS; ++a)
+#pragma unroll
+    for (int b = 0; b < NS; ++b) w.U[(int64_t)(a * NS + b) * nt + i] = U1[a][b];
+  if (deg) {
+    atomicAdd(&w.hdr->n_degenerate, 1ull);
+    atomicOr(&w.hdr->flags, QCL_FLAG_DEGENERATE);
+  }
+  if (!isfinite(m) || !isfinite(phi)) {
+    atomicAdd(&w.hdr->n_nonfinite, 1ull);
+    atomicOr(&w.hdr->flags, QCL_FLAG_NONFINITE);
+  }
+}
+
+// --------------------------------------------------------- FP64 observation --
+// Contributions in passes of 32 quantities: pass p holds values 16p..16p+15
+// (lanes 0-15 of the reduce-scatter) and their squares (lanes 16-31).
+template <typename T, int NS>
+__device__ __forceinline__ void contrib_values(const T (&U)[NS][NS], int al, int be, T zr, T zi,
+                                               int p, T (&v)[16]) {
+  T ua[NS], ub[NS];
+  column<T, NS>(U, al, ua);
+  column<T, NS>(U, be, ub);
+  constexpr int NN = NS * NS;
+#pragma unroll
+  for (int t = 0; t < 16; ++t) {
+    const int q = 16 * p + t;  // quantity index in [0, 4 NN)
+    T val = T(0);
+    if (q < 2 * NN) {  // diabatic rho_ij, q = 2 (i NS + j) + c
+      const int ij = q >> 1, ii = ij / NS, jj = ij % NS;
+      const T f = ua[ii] * ub[jj];
+      val = (q & 1) ? zi * f : zr * f;
+    } else if (q < 4 * NN) {  // adiabatic rho_ab at the walker's pair
+      const int ab = (q - 2 * NN) >> 1;
+      const bool hit = ab == al * NS + be;
+      val = hit ? ((q & 1) ? zi : zr) : T(0);
+    }
+    v[t] = val;
+  }
+}
+
+template <int NS>
+__global__ void __launch_bounds__(256) k_observeN_f64(const void* buf, int64_t nt, int n,
+                                                      double* __restrict__ part) {
+  __shared__ double red[8][32];
+  constexpr int NN = NS * NS, NP = (4 * NN + 15) / 16;
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  WN<double> w = viewN<double>((void*)buf, nt, NS, n, QCL_PREC_FP64);
+  double U[NS][NS];
+  double zr = 0.0, zi = 0.0;
+  int al = 0, be = 0;
+  if (i < nt) {
+#pragma unroll
+    for (int a = 0; a < NS; ++a)
+#pragma unroll
+      for (int b = 0; b < NS; ++b) U[a][b] = w.U[(int64_t)(a * NS + b) * nt + i];
+    const uint16_t ab = w.ab[i];
+    al = ab & 0xff;
+    be = ab >> 8;
+    double sn, cs;
+    sincos(w.phi[i], &sn, &cs);
+    zr = w.m[i] * cs;
+    zi = -w.m[i] * sn;
+  } else {
+#pragma unroll
+    for (int a = 0; a < NS; ++a)
+#pragma unroll
+      for (int b = 0; b < NS; ++b) U[a][b] = 0.0;
+  }
+  for (int p = 0; p < NP; ++p) {
+    double v16[16];
+    contrib_values<double, NS>(U, al, be, zr, zi, p, v16);
+    double v[32];
+#pragma unroll
+    for (int t = 0; t < 16; ++t) {
+      v[t] = v16[t];
+      v[16 + t] = v16[t] * v16[t];
+    }
+    const double x = warp_transpose_sum<double>(v);
+    red[threadIdx.x >> 5][threadIdx.x & 31] = x;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+      const int lane = threadIdx.x;
+      const int q = (lane < 16) ? 16 * p + lane : 4 * NN + 16 * p + (lane - 16);
+      if (16 * p + (lane & 15) < 4 * NN)
+        part[(int64_t)blockIdx.x * 8 * NN + q] = tile_tree8(&red[0][0], 32, lane);
+    }
+    __syncthreads();
+  }
+}
+
+// ------------------------------------------------------------ FP32 sampling --
+template <int NS>
+__global__ void __launch_bounds__(128) k_sampleN_f32(const DevModel* __restrict__ M,
+                                                     SampleParams sp, void* buf) {
+  // the FP64 decomposition of the initial sample (once per walker), stored in FP32
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t nt = sp.n_traj;
+  const int n = sp.n;
+  WN<float> w = viewN<float>(buf, nt, NS, n, QCL_PREC_FP32_BULK);
+  if (i == 0) {
+    w.hdr->magic = kEnsMagic;
+    w.hdr->n_traj = nt;
+    w.hdr->precision = QCL_PREC_FP32_BULK;
+    w.hdr->ns = NS;
+    w.hdr->n = n;
+    w.hdr->step = 0;
+    w.hdr->flags = 0;
+    w.hdr->n_degenerate = 0;
+    w.hdr->n_nonfinite = 0;
+  }
+  if (i >= nt) return;
+  const uint64_t traj = sp.traj_offset + (uint64_t)i;
+  double W[NS][NS];
+#pragma unroll
+  for (int a = 0; a < NS; ++a)
+#pragma unroll
+    for (int b = 0; b < NS; ++b) W[a][b] = M->E[a * NS + b];
+  for (int j = 0; j < n; ++j) {
+    float R = (float)sp.R0[j], P = (float)sp.P0[j];
+    if (sp.wigner) {
+      const u4 wd = philox_draw(sp.seed, (uint32_t)j, traj, kPurposeInit);
+      const float u0 = __fmaf_rn(__uint2float_rn(wd.x), 0x1p-32f, 0x1p-33f);
+      const float u1 = __fmaf_rn(__uint2float_rn(wd.y), 0x1p-32f, 0x1p-33f);
+      const float rad = sqrtf(-2.0f * logf(u0));
+      float sn, cs;
+      sincospif(2.0f * u1, &sn, &cs);
+      R = __fmaf_rn((float)sp.sR[j] * rad, cs, R);
+      P = __fmaf_rn((float)sp.sP[j] * rad, sn, P);
+    }
+    w.R[(int64_t)j * nt + i] = R;
+    w.P[(int64_t)j * nt + i] = P;
+    const double* Kj = M->K + (size_t)j * NS * NS;
+#pragma unroll
+    for (int a = 0; a < NS; ++a)
+#pragma unroll
+      for (int b = 0; b < NS; ++b) W[a][b] += (double)R * Kj[a * NS + b];
+  }
+  double e[NS], U[NS][NS];
+  eigh_ns<double, NS>(W, nullptr, e, U, 100, 1e-34);
+  double rho_ad[NS * NS];
+#pragma unroll
+  for (int al = 0; al < NS; ++al)
+#pragma unroll
+    for (int be = 0; be < NS; ++be) {
+      double acc = 0.0;
+#pragma unroll
+      for (int k = 0; k < NS; ++k)
+#pragma unroll
+        for (int l = 0; l < NS; ++l) acc += U[k][al] * sp.rho[k * NS + l] * U[l][be];
+      rho_ad[al * NS + be] = acc;
+    }
+  double tot = 0.0;
+  for (int k = 0; k < NS * NS; ++k) tot += fabs(rho_ad[k]);
+  uint32_t Tk[NS * NS];
+  uint64_t sumT = 0;
+  int last = 0;
+  for (int k = 0; k < NS * NS; ++k) {
+    Tk[k] = (uint32_t)floor(fabs(rho_ad[k]) / tot * kP24);
+    sumT += Tk[k];
+    if (rho_ad[k] != 0.0) last = k;
+  }
+  Tk[last] += (uint32_t)(16777216ull - sumT);
+  const u4 wd = philox_draw(sp.seed, (uint32_t)n, traj, kPurposeInit);
+  const uint32_t y = wd.x >> 8;
+  uint64_t cum = 0;
+  int pickk = last;
+  for (int k = 0; k < NS * NS; ++k) {
+    cum += Tk[k];
+    if ((uint64_t)y < cum) {
+      pickk = k;
+      break;
+    }
+  }
+  w.m[i] = (float)(rho_ad[pickk] / ((double)Tk[pickk] / kP24));
+  w.mlo[i] = 0.0f;
+  w.mexp[i] = 0;
+  w.phi[i] = 0.0f;
+  w.philo[i] = 0.0f;
+  w.ab[i] = (uint16_t)((pickk / NS) | ((pickk % NS) << 8));
+#pragma unroll
+  for (int a = 0; a < NS; ++a)
+#pragma unroll
+    for (int b = 0; b < NS; ++b) w.U[(int64_t)(a * NS + b) * nt + i] = (float)U[a][b];
+#pragma unroll
+  for (int a = 0; a < NS; ++a) w.E[(int64_t)a * nt + i] = (float)e[a];
+}
+
+// ------------------------------------------------------- FP32-bulk kernel --
+__device__ __forceinline__ int fexpN(float x) {
+  return (int)((__float_as_uint(x) >> 23) & 0xffu) - 127;
+}
+__device__ __forceinline__ float pow2iN(int d) {
+  return d < -126 ? 0.0f : __uint_as_float((uint32_t)(127 + d) << 23);
+}
+__device__ __forceinline__ void renormN(f2& m, int& e) {
+  if (m.hi == 0.0f) return;
+  const int k = fexpN(m.hi);
+  const float sc = (k == -127) ? 0x1p+126f : (k >= 127 ? 0x1p-127f : pow2iN(-k));
+  m.hi *= sc;
+  m.lo *= sc;
+  e += (k == -127) ? -126 : k;
+}
+__device__ __forceinline__ double pow2dN(int e) { return __hiloint2double((e + 1023) << 20, 0); }
+
+constexpr float kTwoPi1N = 6.283203125f;
+constexpr float kTwoPi2N = -1.7818063497543335e-05f;
+constexpr float kTwoPi3N = 2.430840251310684e-10f;
+constexpr float kInvTwoPiN = 0.15915494309189535f;
+
+// W's upper triangle index
+template <int NS>
+__host__ __device__ constexpr int tri(int a, int b) {
+  return a <= b ? a * NS - a * (a - 1) / 2 + (b - a) : b * NS - b * (b - 1) / 2 + (a - b);
+}
+
+template <int NS, int NPL>
+__global__ void __launch_bounds__(128, 1)
+    k_bulkN(const BulkParams bp, const CoefN cf, void* buf, double* __restrict__ part) {
+  constexpr int NN = NS * NS, NTRI = NS * (NS + 1) / 2;
+  constexpr int NP = (4 * NN + 15) / 16;  // observation passes of 32 quantities
+  constexpr int TW = 128;                 // walkers per tile (one block)
+  __shared__ double red[2][4][32];
+  __shared__ float obs_rows[TW * 33];
+  WN<float> ws = viewN<float>(buf, bp.n_traj, NS, bp.n, QCL_PREC_FP32_BULK);
+  if (ws.hdr->step != bp.step0) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) atomicOr(&ws.hdr->flags, QCL_FLAG_STEP_MISMATCH);
+    return;
+  }
+  const int64_t nt = bp.n_traj;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  unsigned int n_deg = 0;
+  int rb = 0;
+  for (int64_t tile = blockIdx.x; tile < bp.n_tiles; tile += gridDim.x) {
+    const int64_t i = tile * TW + threadIdx.x;
+    const bool active = i < nt;
+    const int64_t ii = active ? i : 0;
+    float R[NPL], P[NPL];
+#pragma unroll
+    for (int j = 0; j < NPL; ++j) {
+      const bool on = active && j < bp.n;
+      R[j] = on ? ws.R[(int64_t)j * nt + ii] : 0.0f;
+      P[j] = on ? ws.P[(int64_t)j * nt + ii] : 0.0f;
+    }
+    float U[NS][NS], e[NS];
+#pragma unroll
+    for (int a = 0; a < NS; ++a)
+#pragma unroll
+      for (int b = 0; b < NS; ++b) U[a][b] = active ? ws.U[(int64_t)(a * NS + b) * nt + ii] : (a == b ? 1.f : 0.f);
+    f2 m = {active ? ws.m[ii] : 0.0f, active ? ws.mlo[ii] : 0.0f};
+    int mexp = active ? ws.mexp[ii] : 0;
+    f2 ph = {active ? ws.phi[ii] : 0.0f, active ? ws.philo[ii] : 0.0f};
+    const uint32_t ab0 = active ? ws.ab[ii] : 0u;
+    int al = ab0 & 0xff, be = (ab0 >> 8) & 0xff;
+    const uint64_t traj = bp.traj_offset + (uint64_t)ii;
+
+    auto build_w = [&](float (&W)[NS][NS]) {
+      float t[NTRI];
+#pragma unroll
+      for (int k = 0; k < NTRI; ++k) t[k] = cf.E[k];
+#pragma unroll
+      for (int j = 0; j < NPL; ++j)
+#pragma unroll
+        for (int k = 0; k < NTRI; ++k) t[k] = __fmaf_rn(R[j], cf.K[j][k], t[k]);
+#pragma unroll
+      for (int a = 0; a < NS; ++a)
+#pragma unroll
+        for (int b = 0; b < NS; ++b) W[a][b] = t[tri<NS>(a, b)];
+    };
+    // decomposition at R_n as left by the previous step (stored exactly, so a
+    // chunk boundary changes no bit)
+#pragma unroll
+    for (int a = 0; a < NS; ++a) e[a] = active ? ws.E[(int64_t)a * nt + ii] : (float)a;
+    // dt/2 * (1/2)(u_a u_a^T + u_b u_b^T) folded with the off-diagonal factor 2
+    auto kick = [&]() {
+      float ua[NS], ub[NS];
+      column<float, NS>(U, al, ua);
+      column<float, NS>(U, be, ub);
+      float Q[NTRI];
+#pragma unroll
+      for (int a = 0; a < NS; ++a)
+#pragma unroll
+        for (int b = a; b < NS; ++b)
+          Q[tri<NS>(a, b)] = (a == b ? 0.5f : 1.0f) * bp.hdt * (ua[a] * ua[b] + ub[a] * ub[b]);
+#pragma unroll
+      for (int j = 0; j < NPL; ++j) {
+        float g = 0.0f;
+#pragma unroll
+        for (int k = 0; k < NTRI; ++k) g = __fmaf_rn(cf.K[j][k], Q[k], g);
+        P[j] = __fmaf_rn(-cf.hk[j], R[j], P[j]) - g;
+      }
+    };
+    auto observe = [&](int slot) {
+      renormN(m, mexp);
+      const bool live = active && m.hi != 0.0f;
+      int ew = live ? mexp : -(1 << 28);
+#pragma unroll
+      for (int off = 16; off > 0; off >>= 1) ew = max(ew, __shfl_xor_sync(0xffffffffu, ew, off));
+      const float kq = rintf(ph.hi * kInvTwoPiN);
+      ph = df_add(ph, -kq * kTwoPi1N);
+      ph = df_add(ph, -kq * kTwoPi2N);
+      ph = df_add(ph, -kq * kTwoPi3N);
+      float sh, chh;
+      __sincosf(ph.hi, &sh, &chh);
+      const float mm = live ? m.hi * pow2iN(mexp - ew) : 0.0f;
+      const float zr = mm * __fmaf_rn(-ph.lo, sh, chh), zi = -mm * __fmaf_rn(ph.lo, chh, sh);
+      const int ex = (ew < -(1 << 27)) ? 0 : ((lane < 16) ? ew : 2 * ew);
+      float* row = &obs_rows[threadIdx.x * 33];
+#pragma unroll 1
+      for (int p = 0; p < NP; ++p) {
+        float v[16];
+        contrib_values<float, NS>(U, al, be, zr, zi, p, v);
+#pragma unroll
+        for (int t = 0; t < 16; ++t) {
+          row[t] = v[t];
+          row[16 + t] = v[t] * v[t];
+        }
+        __syncwarp();
+        float l1[16];
+        const float* col = &obs_rows[(warp * 32) * 33 + lane];
+#pragma unroll
+        for (int t = 0; t < 16; ++t) l1[t] = col[(2 * t) * 33] + col[(2 * t + 1) * 33];
+#pragma unroll
+        for (int wdt = 8; wdt >= 1; wdt >>= 1)
+#pragma unroll
+          for (int t = 0; t < wdt; ++t) l1[t] = l1[2 * t] + l1[2 * t + 1];
+        __syncwarp();
+        const double xd = (double)l1[0];
+        red[rb][warp][lane] = (ex >= -1022 && ex <= 1023) ? xd * pow2dN(ex) : ldexp(xd, ex);
+        __syncthreads();
+        if (threadIdx.x < 32) {
+          const int q = (lane < 16) ? 16 * p + lane : 4 * NN + 16 * p + (lane - 16);
+          if (16 * p + (lane & 15) < 4 * NN)
+            part[((int64_t)slot * bp.n_tiles + tile) * 8 * NN + q] =
+                (red[rb][0][lane] + red[rb][1][lane]) + (red[rb][2][lane] + red[rb][3][lane]);
+        }
+        rb ^= 1;
+      }
+    };
+
+    int slot = bp.obs_first;
+    if (bp.obs_first) observe(0);
+    int to_out = bp.to_out0;
+    uint32_t blk = bp.blk0;
+    int widx = bp.widx0;
+    u4 wd = philox_draw(bp.seed, blk, traj, kPurposeHop);
+    for (int it = 0; it < bp.len; ++it) {
+      const uint32_t word = (widx & 2) ? ((widx & 1) ? wd.w : wd.z) : ((widx & 1) ? wd.y : wd.x);
+      const float de0 = pick<float, NS>(e, al) - pick<float, NS>(e, be);
+      kick();  // first half kick at R_n
+#pragma unroll
+      for (int j = 0; j < NPL; ++j) R[j] = __fmaf_rn(cf.dtm[j], P[j], R[j]);
+      {
+        float W[NS][NS], Uref[NS][NS];
+#pragma unroll
+        for (int a = 0; a < NS; ++a)
+#pragma unroll
+          for (int b = 0; b < NS; ++b) Uref[a][b] = U[a][b];
+        build_w(W);
+        eigh_ns<float, NS>(W, Uref, e, U, 2, -1.0f);
+      }
+      kick();  // second half kick at R_{n+1}
+      const float de1 = pick<float, NS>(e, al) - pick<float, NS>(e, be);
+      ph = df_add(ph, bp.hdt_hbar * (de0 + de1));
+      // G = sum_j (P_j/M_j) K_j
+      float G[NS][NS];
+      {
+        float t[NTRI];
+#pragma unroll
+        for (int k = 0; k < NTRI; ++k) t[k] = 0.0f;
+#pragma unroll
+        for (int j = 0; j < NPL; ++j) {
+          const float v = P[j] * cf.minv[j];
+#pragma unroll
+          for (int k = 0; k < NTRI; ++k) t[k] = __fmaf_rn(v, cf.K[j][k], t[k]);
+        }
+#pragma unroll
+        for (int a = 0; a < NS; ++a)
+#pragma unroll
+          for (int b = 0; b < NS; ++b) G[a][b] = t[tri<NS>(a, b)];
+      }
+      constexpr int NC = 2 * NS;
+      float A[NC];
+      bool ev[NC];
+      const bool dg = event_amplitudes<float, NS>(G, U, e, al, be, bp.dt, kDegTolF, A, ev);
+      n_deg += (dg && active) ? 1u : 0u;
+      uint32_t T[NC], sumT = 0;
+#pragma unroll
+      for (int k = 0; k < NC; ++k) {
+        T[k] = ev[k] ? min(__float2uint_rz(fminf(bp.kappa * fabsf(A[k]) * kP24f, 33554432.0f)), bp.tmax) : 0u;
+        sumT += T[k];
+      }
+      if (sumT > bp.tmax) {
+        const float sc = (float)bp.tmax / (float)sumT;
+        uint32_t s2 = 0;
+#pragma unroll
+        for (int k = 0; k < NC; ++k) {
+          T[k] = min(__float2uint_rz((float)T[k] * sc), T[k]);
+          s2 += T[k];
+        }
+        sumT = s2;
+      }
+      const uint32_t y = word >> 8;
+      uint32_t cum = 0;
+      int hit = -1;
+#pragma unroll
+      for (int k = 0; k < NC; ++k) {
+        cum += T[k];
+        hit = (hit < 0 && y < cum) ? k : hit;
+      }
+      float Ah = A[0];
+      uint32_t Th = T[0];
+#pragma unroll
+      for (int k = 1; k < NC; ++k) {
+        Ah = (k == hit) ? A[k] : Ah;
+        Th = (k == hit) ? T[k] : Th;
+      }
+      const bool hop = hit >= 0;
+      const float num = hop ? Ah * kP24f : kP24f;
+      const float den = __uint2float_rn(hop ? Th : 16777216u - sumT);
+      const float rd = __frcp_rn(den);
+      const float q0 = num * rd;
+      const float q1 = __fmaf_rn(-q0, den, num) * rd;
+      m = df_mul(m, q0, q1);
+      if (!(fabsf(m.hi) <= 0x1p32f && fabsf(m.hi) >= 0x1p-32f)) renormN(m, mexp);
+      if (hop) {
+        if (hit < NS) al = hit;
+        else be = hit - NS;
+      }
+      if (++widx == 4) {
+        widx = 0;
+        ++blk;
+        if (it + 1 < bp.len) wd = philox_draw(bp.seed, blk, traj, kPurposeHop);
+      }
+      if (--to_out == 0) {
+        observe(slot++);
+        to_out = bp.stride;
+      }
+    }
+    if (active) {
+#pragma unroll
+      for (int j = 0; j < NPL; ++j)
+        if (j < bp.n) {
+          ws.R[(int64_t)j * nt + i] = R[j];
+          ws.P[(int64_t)j * nt + i] = P[j];
+        }
+#pragma unroll
+      for (int a = 0; a < NS; ++a)
+#pragma unroll
+        for (int b = 0; b < NS; ++b) ws.U[(int64_t)(a * NS + b) * nt + i] = U[a][b];
+#pragma unroll
+      for (int a = 0; a < NS; ++a) ws.E[(int64_t)a * nt + i] = e[a];
+      ws.m[i] = m.hi;
+      ws.mlo[i] = m.lo;
+      ws.mexp[i] = mexp;
+      ws.phi[i] = ph.hi;
+      ws.philo[i] = ph.lo;
+      ws.ab[i] = (uint16_t)(al | (be << 8));
+      if (!isfinite(m.hi) || !isfinite(ph.hi)) {
+        atomicAdd(&ws.hdr->n_nonfinite, 1ull);
+        atomicOr(&ws.hdr->flags, QCL_FLAG_NONFINITE);
+      }
+    }
+  }
+  if (n_deg) {
+    atomicAdd(&ws.hdr->n_degenerate, (unsigned long long)n_deg);
+    atomicOr(&ws.hdr->flags, QCL_FLAG_DEGENERATE);
+  }
+}
+
+// ------------------------------------------------------- per-N_s launchers --
+// Instantiated explicitly, one N_s per translation unit (compiled in parallel).
+template <int NS>
+struct NStateOps {
+  static void sample(const DevModel* dm, const SampleParams& sp, void* buf, int precision,
+                     cudaStream_t st) {
+    const int64_t nb = (sp.n_traj + 127) / 128;
+    if (precision == QCL_PREC_FP64)
+      k_sampleN_f64<NS><<<(unsigned)(nb > 0 ? nb : 1), 128, 0, st>>>(dm, sp, buf);
+    else
+      k_sampleN_f32<NS><<<(unsigned)(nb > 0 ? nb : 1), 128, 0, st>>>(dm, sp, buf);
+  }
+  static void step64(const DevModel* dm, void* buf, int64_t nt, int n, int64_t step0,
+                     int64_t step, double dt, uint64_t seed, uint64_t traj_off, cudaStream_t st) {
+    k_stepN_f64<NS><<<(unsigned)((nt + 127) / 128), 128, 0, st>>>(dm, buf, nt, n, step0, step, dt,
+                                                                   seed, traj_off);
+  }
+  static void observe64(const void* buf, int64_t nt, int n, double* part, cudaStream_t st) {
+    k_observeN_f64<NS><<<(unsigned)((nt + 255) / 256), 256, 0, st>>>(buf, nt, n, part);
+  }
+  template <int NPL>
+  static int bulk_npl(const BulkParams& bp, const CoefN& cf, void* buf, double* part,
+                      int grid_cap, cudaStream_t st) {
+    static int per_sm = -1, n_sm = 0;
+    auto fn = k_bulkN<NS, NPL>;
+    if (per_sm < 0) {
+      int dev = 0;
+      cudaGetDevice(&dev);
+      cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
+      if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, 128, 0) != cudaSuccess ||
+          per_sm < 1)
+        per_sm = 1;
+    }
+    int64_t grid = (int64_t)per_sm * n_sm;
+    if (grid_cap > 0 && grid > grid_cap) grid = grid_cap;
+    if (grid > bp.n_tiles) grid = bp.n_tiles;
+    if (grid < 1) grid = 1;
+    fn<<<(unsigned)grid, 128, 0, st>>>(bp, cf, buf, part);
+    return (int)grid;
+  }
+  static int bulk(const BulkParams& bp, const CoefN& cf, void* buf, double* part, int grid_cap,
+                  cudaStream_t st) {
+    // up to 8 modes for any N_s; up to 32 modes for N_s <= 4 (larger N_s x modes
+    // would not fit a walker in registers)
+    if (bp.n <= 8) return bulk_npl<8>(bp, cf, buf, part, grid_cap, st);
+    if (NS <= 4 && bp.n <= 32) return bulk_npl<(NS <= 4 ? 32 : 8)>(bp, cf, buf, part, grid_cap, st);
+    return 0;
+  }
+};
+
+}  // namespace qcl

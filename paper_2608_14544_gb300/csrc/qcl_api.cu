@@ -93,7 +93,8 @@ qcl_status check_ens(const qcl_model* m, const qcl_ensemble_desc* e) {
   if (e->n_traj > (int64_t)1 << 40) return fail(QCL_ERR_INVALID_ARG, "n_traj too large");
   if (e->precision != QCL_PREC_FP64 && e->precision != QCL_PREC_FP32_BULK)
     return fail(QCL_ERR_INVALID_ARG, "unknown precision %d", e->precision);
-  if (m->ns != 2) return fail(QCL_ERR_UNSUPPORTED, "only two-state models are built (n_states = %d)", m->ns);
+  if (m->ns > 2 && e->precision == QCL_PREC_FP32_BULK && m->n > (m->ns <= 4 ? 32 : 8))
+    return fail(QCL_ERR_UNSUPPORTED, "FP32-bulk models with %d states support n_modes <= %d (got %d)", m->ns, m->ns <= 4 ? 32 : 8, m->n);
   return QCL_OK;
 }
 
@@ -155,7 +156,7 @@ qcl_status qcl_kernel_time(int32_t which, double* total_ms, int64_t* launches) {
   return st ? st : ok();
 }
 
-qcl_status qcl_ensemble_layout(const qcl_model* model, const qcl_ensemble_desc* ens, size_t offsets[9]) {
+qcl_status qcl_ensemble_layout(const qcl_model* model, const qcl_ensemble_desc* ens, size_t offsets[11]) {
   if (!offsets) return fail(QCL_ERR_INVALID_ARG, "offsets is NULL");
   qcl_status st = check_ens(model, ens);
   if (st) return st;
@@ -169,6 +170,8 @@ qcl_status qcl_ensemble_layout(const qcl_model* model, const qcl_ensemble_desc* 
   offsets[6] = L.off_ab;
   offsets[7] = L.total;
   offsets[8] = L.off_mexp;
+  offsets[9] = L.off_U;
+  offsets[10] = L.off_E;
   return ok();
 }
 
@@ -276,7 +279,7 @@ qcl_status qcl_obs_bytes(const qcl_model* model, const qcl_ensemble_desc* ens, i
   qcl_status st = check_ens(model, ens);
   if (st) return st;
   if (n_out < 1) return fail(QCL_ERR_INVALID_ARG, "n_out must be >= 1");
-  *bytes = ObsLayout::make(ens->n_traj, model->ns, n_out, tile_walkers(ens->precision, model->n)).total;
+  *bytes = ObsLayout::make(ens->n_traj, model->ns, n_out, tile_walkers(ens->precision, model->n, model->ns)).total;
   return ok();
 }
 
@@ -314,7 +317,9 @@ qcl_status qcl_sample_initial(const qcl_model* model, const qcl_ensemble_desc* e
   }
   for (int k = 0; k < ns * ns; ++k) sp->rho[k] = init->rho_el0[k];
   cudaStream_t s = (cudaStream_t)stream;
-  if (ens->precision == QCL_PREC_FP64)
+  if (ns > 2)
+    launch_sampleN(model->dev, *sp, ens_buf, ens->precision, s);
+  else if (ens->precision == QCL_PREC_FP64)
     launch_sample_f64(model->dev, *sp, ens_buf, s);
   else
     launch_sample_f32(model->dev, *sp, ens_buf, s);
@@ -339,7 +344,7 @@ qcl_status qcl_propagate(const qcl_model* model, const qcl_ensemble_desc* ens, v
   if (k_last >= n_out) return fail(QCL_ERR_INVALID_ARG, "output row %lld beyond n_out = %lld", (long long)k_last, (long long)n_out);
   const EnsLayout EL = EnsLayout::make(ens->n_traj, model->ns, model->n, ens->precision);
   if (ens_bytes < EL.total) return fail(QCL_ERR_OUT_OF_MEMORY, "ens_buf has %zu bytes, needs %zu", ens_bytes, EL.total);
-  const ObsLayout OL = ObsLayout::make(ens->n_traj, model->ns, n_out, tile_walkers(ens->precision, model->n));
+  const ObsLayout OL = ObsLayout::make(ens->n_traj, model->ns, n_out, tile_walkers(ens->precision, model->n, model->ns));
   if (obs_bytes < OL.total) return fail(QCL_ERR_OUT_OF_MEMORY, "obs_buf has %zu bytes, needs %zu", obs_bytes, OL.total);
   cudaStream_t s = (cudaStream_t)stream;
   char* ob = (char*)obs_buf;
@@ -350,17 +355,24 @@ qcl_status qcl_propagate(const qcl_model* model, const qcl_ensemble_desc* ens, v
   const int64_t nt = ens->n_traj;
 
   if (ens->precision == QCL_PREC_FP64) {
-    if (step0 == 0) {
-      launch_observe_f64(model->dev, ens_buf, nt, model->n, part, s);
-      launch_fold(part, rows, fold, OL.n_tiles, q2, 1, s);
-    }
-    for (int64_t t = step0; t < step0 + n_steps; ++t) {
-      TimedLaunch tl(1, s);
-      launch_step_f64(model->dev, ens_buf, nt, model->n, step0, t, dt, ens->seed, ens->traj_id_offset, s);
-      if ((t + 1) % out_stride == 0) {
+    const int ns = model->ns;
+    auto observe = [&](double* row) {
+      if (ns == 2)
         launch_observe_f64(model->dev, ens_buf, nt, model->n, part, s);
-        launch_fold(part, rows + (size_t)((t + 1) / out_stride) * q2, fold, OL.n_tiles, q2, 1, s);
+      else
+        launch_observeN_f64(ns, ens_buf, nt, model->n, part, s);
+      launch_fold(part, row, fold, OL.n_tiles, q2, 1, s);
+    };
+    if (step0 == 0) observe(rows);
+    for (int64_t t = step0; t < step0 + n_steps; ++t) {
+      {
+        TimedLaunch tl(1, s);
+        if (ns == 2)
+          launch_step_f64(model->dev, ens_buf, nt, model->n, step0, t, dt, ens->seed, ens->traj_id_offset, s);
+        else
+          launch_stepN_f64(model->dev, ns, ens_buf, nt, model->n, step0, t, dt, ens->seed, ens->traj_id_offset, s);
       }
+      if ((t + 1) % out_stride == 0) observe(rows + (size_t)((t + 1) / out_stride) * q2);
     }
     st = check_launch("FP64 step");
     if (st) return st;
@@ -394,6 +406,26 @@ qcl_status qcl_propagate(const qcl_model* model, const qcl_ensemble_desc* ens, v
     bp.kdt = (float)(model->hop_scale * dt);
     bp.p_max = (float)model->p_max;
     bp.tmax = (uint32_t)std::floor(model->p_max * kP24);
+    bp.kappa = (float)model->hop_scale;
+    CoefN* cn = nullptr;
+    if (model->ns > 2) {
+      cn = new (std::nothrow) CoefN();
+      if (!cn) {
+        delete cf;
+        return fail(QCL_ERR_OUT_OF_MEMORY, "host allocation failed");
+      }
+      const int ns = model->ns;
+      auto tri = [ns](int a, int b) { return a * ns - a * (a - 1) / 2 + (b - a); };
+      for (int a = 0; a < ns; ++a)
+        for (int b = a; b < ns; ++b) cn->E[tri(a, b)] = (float)model->E[a * ns + b];
+      for (int j = 0; j < model->n; ++j) {
+        cn->hk[j] = (float)(0.5 * dt * h.k[j]);
+        cn->dtm[j] = (float)(dt / h.mass[j]);
+        cn->minv[j] = (float)(1.0 / h.mass[j]);
+        for (int a = 0; a < ns; ++a)
+          for (int b = a; b < ns; ++b) cn->K[j][tri(a, b)] = (float)model->K[(size_t)j * ns * ns + a * ns + b];
+      }
+    }
     // chunks of at most kChunkOut output times
     int64_t cs = step0;
     bool first = (step0 == 0);
@@ -430,10 +462,12 @@ qcl_status qcl_propagate(const qcl_model* model, const qcl_ensemble_desc* ens, v
       int grid = 0;
       {
         TimedLaunch tl(0, s);
-        grid = launch_bulk2(bp, *cf, ens_buf, part, (int)g_opt_grid_cap, s);
+        grid = cn ? launch_bulkN(model->ns, bp, *cn, ens_buf, part, (int)g_opt_grid_cap, s)
+                  : launch_bulk2(bp, *cf, ens_buf, part, (int)g_opt_grid_cap, s);
       }
       if (grid == 0) {
         delete cf;
+        delete cn;
         return fail(QCL_ERR_UNSUPPORTED, "no FP32-bulk kernel for n_modes = %d", model->n);
       }
       if (n_slots > 0) launch_fold(part, rows + (size_t)k_first * q2, fold, OL.n_tiles, q2, n_slots, s);
@@ -441,6 +475,7 @@ qcl_status qcl_propagate(const qcl_model* model, const qcl_ensemble_desc* ens, v
       cs = ce;
     } while (cs < end);
     delete cf;
+    delete cn;
     st = check_launch("FP32-bulk propagate");
     if (st) return st;
   }
@@ -456,7 +491,7 @@ qcl_status qcl_reduce_observables(const qcl_model* model, const qcl_ensemble_des
   if (st) return st;
   if (!obs_buf || !host_out) return fail(QCL_ERR_INVALID_ARG, "obs_buf or host_out is NULL");
   if (n_out < 1 || k0 < 0 || n_rows < 0 || k0 + n_rows > n_out) return fail(QCL_ERR_INVALID_ARG, "rows [%lld, %lld) outside [0, %lld)", (long long)k0, (long long)(k0 + n_rows), (long long)n_out);
-  const ObsLayout OL = ObsLayout::make(ens->n_traj, model->ns, n_out, tile_walkers(ens->precision, model->n));
+  const ObsLayout OL = ObsLayout::make(ens->n_traj, model->ns, n_out, tile_walkers(ens->precision, model->n, model->ns));
   if (obs_bytes < OL.total) return fail(QCL_ERR_OUT_OF_MEMORY, "obs_buf has %zu bytes, needs %zu", obs_bytes, OL.total);
   const int nq = OL.q2 / 2;
   const size_t per = (size_t)(2 * nq + 3);
@@ -479,7 +514,7 @@ qcl_status qcl_read_sums(const qcl_model* model, const qcl_ensemble_desc* ens, c
   if (st) return st;
   if (!obs_buf || !host_out) return fail(QCL_ERR_INVALID_ARG, "obs_buf or host_out is NULL");
   if (n_out < 1 || k0 < 0 || n_rows < 0 || k0 + n_rows > n_out) return fail(QCL_ERR_INVALID_ARG, "rows outside [0, n_out)");
-  const ObsLayout OL = ObsLayout::make(ens->n_traj, model->ns, n_out, tile_walkers(ens->precision, model->n));
+  const ObsLayout OL = ObsLayout::make(ens->n_traj, model->ns, n_out, tile_walkers(ens->precision, model->n, model->ns));
   if (obs_bytes < OL.total) return fail(QCL_ERR_OUT_OF_MEMORY, "obs_buf has %zu bytes, needs %zu", obs_bytes, OL.total);
   if (host_len < (size_t)OL.q2 * n_rows) return fail(QCL_ERR_INVALID_ARG, "host_out too small");
   if (n_rows == 0) return ok();

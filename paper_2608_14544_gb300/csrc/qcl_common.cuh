@@ -132,7 +132,7 @@ __host__ __device__ inline size_t align256(size_t x) { return (x + 255) & ~size_
 
 // SoA ensemble layout.  Every array starts on a 256-byte boundary.
 struct EnsLayout {
-  size_t off_R, off_P, off_m, off_mlo, off_mexp, off_phi, off_philo, off_ab, off_U, total;
+  size_t off_R, off_P, off_m, off_mlo, off_mexp, off_phi, off_philo, off_ab, off_U, off_E, total;
   __host__ __device__ static EnsLayout make(int64_t n_traj, int ns, int n, int precision) {
     EnsLayout L{};
     const size_t nt = (size_t)n_traj;
@@ -156,6 +156,8 @@ struct EnsLayout {
     o = align256(o + 2 * nt);
     L.off_U = o;
     if (ns > 2) o = align256(o + w * nt * (size_t)(ns * ns));
+    L.off_E = o;
+    if (ns > 2) o = align256(o + w * nt * (size_t)ns);
     L.total = o;
     return L;
   }
@@ -172,8 +174,9 @@ constexpr int kFoldBlock = 1024;   // tiles per first-level fold block (power of
 // modes are split over 2 or 4 warps (one thread of each).  A tile (the unit of
 // the fixed reduction tree) is one block of 256 threads: 256 / that walkers.
 __host__ __device__ inline int bulk_lanes(int n) { return n <= 32 ? 1 : (n <= 100 ? 2 : 4); }
-__host__ __device__ inline int tile_walkers(int precision, int n) {
-  return precision == QCL_PREC_FP64 ? kTile : kTile / bulk_lanes(n);
+__host__ __device__ inline int tile_walkers(int precision, int n, int ns = 2) {
+  if (precision == QCL_PREC_FP64) return kTile;
+  return ns > 2 ? 128 : kTile / bulk_lanes(n);
 }
 
 struct ObsLayout {

@@ -147,7 +147,7 @@ def kernel_time(which: int):
 
 
 def ensemble_layout(model, ens) -> list:
-    off = (C.c_size_t * 9)()
+    off = (C.c_size_t * 11)()
     _check(load().qcl_ensemble_layout(model.handle, C.byref(ens), off), "qcl_ensemble_layout")
     return list(off)
 
@@ -320,9 +320,15 @@ class Run:
             return np.frombuffer(raw[o:o + width * count].tobytes(), dtype=dtype).copy()
 
         mexp = np.zeros(nt, dtype=np.int32) if fp64 else arr(off[8], nt, np.int32, 4)
+        ns = self.model.ns
+        extra = {}
+        if ns > 2:
+            extra["U"] = arr(off[9], nt * ns * ns, dt, w).reshape(ns, ns, nt).transpose(2, 0, 1).copy()
+            if not fp64:
+                extra["E"] = arr(off[10], nt * ns, dt, w).reshape(ns, nt).T.copy()
         return {"R": arr(off[0], nt * n, dt, w).reshape(n, nt).T.copy(), "m_exp": mexp,
                 "P": arr(off[1], nt * n, dt, w).reshape(n, nt).T.copy(),
                 "m": arr(off[2], nt, dt, w), "m_lo": arr(off[3], nt, dt, w),
                 "phi": arr(off[4], nt, dt, w), "phi_lo": arr(off[5], nt, dt, w),
                 "alpha": (arr(off[6], nt, np.uint16, 2) & 0xFF).astype(np.int32),
-                "beta": (arr(off[6], nt, np.uint16, 2) >> 8).astype(np.int32)}
+                "beta": (arr(off[6], nt, np.uint16, 2) >> 8).astype(np.int32), **extra}
