@@ -1,0 +1,356 @@
+// bulk2.cuh -- device code of the two-state FP32-bulk walker kernels shared by
+// the single-request persistent kernel (kernels_f32.cu) and the packed
+// multi-request kernel of the server (packed.cu): walker views, compensated
+// weight/phase helpers, the per-step scalar algebra and the tile body.
+#pragma once
+#include "kernels.h"
+#include "reduce.cuh"
+
+namespace qcl {
+
+
+namespace b2 {
+
+// 2 pi = C1 + C2 + C3 with C1, C2 of 14 significant bits (k * C exact for |k| < 2^10)
+constexpr float kTwoPi1 = 6.283203125f;
+constexpr float kTwoPi2 = -1.7818063497543335e-05f;
+constexpr float kTwoPi3 = 2.430840251310684e-10f;
+constexpr float kInvTwoPi = 0.15915494309189535f;
+constexpr float kDegTol32 = 1e-6f;  // |e_b - e_a| below this: coupling set to 0
+
+struct W32 {
+  float* R;
+  float* P;
+  float* mh;
+  float* ml;
+  int32_t* me;
+  float* ph;
+  float* pl;
+  uint16_t* ab;
+  EnsHeader* hdr;
+};
+
+__device__ __forceinline__ W32 view32(void* buf, int64_t nt, int ns, int n) {
+  const EnsLayout L = EnsLayout::make(nt, ns, n, QCL_PREC_FP32_BULK);
+  char* b = (char*)buf;
+  return {(float*)(b + L.off_R),    (float*)(b + L.off_P),     (float*)(b + L.off_m),
+          (float*)(b + L.off_mlo),  (int32_t*)(b + L.off_mexp), (float*)(b + L.off_phi),
+          (float*)(b + L.off_philo), (uint16_t*)(b + L.off_ab),  (EnsHeader*)b};
+}
+
+__device__ __forceinline__ float sgn(int idx) { return idx ? 1.0f : -1.0f; }
+
+// Unbiased exponent of a float (normal numbers), -127 for zero/denormals.
+__device__ __forceinline__ int fexp(float x) {
+  return (int)((__float_as_uint(x) >> 23) & 0xffu) - 127;
+}
+
+// 2^d for -126 <= d <= 127 (0 below)
+__device__ __forceinline__ float pow2i(int d) {
+  return d < -126 ? 0.0f : __uint_as_float((uint32_t)(127 + d) << 23);
+}
+
+// The weight is carried as (hi + lo) * 2^e: move hi's exponent into e so that
+// hi stays in [1, 2) and the FP32 range never limits the weight.
+__device__ __forceinline__ void renorm(f2& m, int& e) {
+  if (m.hi == 0.0f) return;
+  const int k = fexp(m.hi);
+  const float sc = (k == -127) ? 0x1p+126f : (k >= 127 ? 0x1p-127f : pow2i(-k));
+  m.hi *= sc;
+  m.lo *= sc;
+  e += (k == -127) ? -126 : k;
+}
+
+}  // namespace b2
+using namespace b2;
+
+// ------------------------------------------------------- persistent step --
+__device__ __forceinline__ float rcp_approx(float x) {
+  float r;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
+
+// Sum of 32 floats at stride 33 (one column of a warp's rows) by a fixed
+// pairwise tree: ((x0 + x1) + (x2 + x3)) + ...
+__device__ __forceinline__ float column_sum32(const float* col) {
+  float l1[16];
+#pragma unroll
+  for (int t = 0; t < 16; ++t) l1[t] = col[(2 * t) * 33] + col[(2 * t + 1) * 33];
+#pragma unroll
+  for (int w = 8; w >= 1; w >>= 1)
+#pragma unroll
+    for (int t = 0; t < w; ++t) l1[t] = l1[2 * t] + l1[2 * t + 1];
+  return l1[0];
+}
+
+// 2^e as a double, -1022 <= e <= 1023
+__device__ __forceinline__ double pow2d(int e) { return __hiloint2double((e + 1023) << 20, 0); }
+
+// Shared-memory float4 load that the compiler may not hoist out of the step
+// loop (hoisting the per-mode coefficients would hold them all in registers).
+__device__ __forceinline__ float4 lds4(const float4* p) {
+  float4 v;
+  const unsigned a = (unsigned)__cvta_generic_to_shared(p);
+  asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];"
+               : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
+               : "r"(a));
+  return v;
+}
+
+// Scalar state of one walker that every lane holding a part of it keeps
+// identical: weight (compensated pair and exponent), phase (compensated pair),
+// the pair's sigmas, and the closed-form decomposition at the current R.
+struct Scal {
+  f2 m;
+  int mexp;
+  f2 ph;
+  float sa, sb;          // sigma of the index pair: -1 lower, +1 upper adiabatic state
+  float A, B;            // a(R), b(R)
+  float r2, ir, r;       // r^2, 1/r, r
+  float c2, s2;          // cos 2theta, sin 2theta (theta = 0 at r = 0)
+};
+
+__device__ __forceinline__ void closed_form(Scal& z) {
+  z.r2 = __fmaf_rn(z.A, z.A, z.B * z.B);
+  z.ir = rsqrtf(z.r2);
+  z.r = z.r2 * z.ir;
+  z.c2 = z.r2 > 0.0f ? z.A * z.ir : 1.0f;
+  z.s2 = z.r2 > 0.0f ? z.B * z.ir : 0.0f;
+}
+
+// Phase (trapezoid) and transition of one step, given the decomposition at
+// R_{n+1} (in z), r at R_n, and the coupling sums Av = sum a_j P_j/M_j,
+// Bv = sum b_j P_j/M_j at P_{n+1}.
+__device__ __forceinline__ void phase_and_transition(Scal& z, float r_old, float Av, float Bv,
+                                                     uint32_t word, const BulkParams& bp,
+                                                     bool active, unsigned int& n_deg) {
+  // phase: dt/2 (w_ab(R_n) + w_ab(R_{n+1})), hbar w_ab = (sig_a - sig_b) r
+  z.ph = df_add(z.ph, bp.hdt_hbar * (z.sa - z.sb) * (r_old + z.r));
+  // coupling contracted with P/M: g = (a Bv - b Av) / (2 r^2)
+  const bool degen = 2.0f * z.r < kDegTol32;
+  n_deg += (degen && active) ? 1u : 0u;
+  const float g = degen ? 0.0f : (z.A * Bv - z.B * Av) * (0.5f * z.ir * z.ir);
+  // both events have |A_e| = dt |g|: p = min(kappa dt |g|, p_max) quantised to
+  // 24-bit thresholds, scaled down together in integers when 2T > Tmax
+  uint32_t T = min(__float2uint_rz(fminf(bp.kdt * fabsf(g) * kP24f, 33554432.0f)), bp.tmax);
+  if (2u * T > bp.tmax) T = bp.tmax >> 1;
+  const uint32_t y = word >> 8;
+  const bool hop1 = y < T;
+  const bool hop2 = !hop1 && (y < 2u * T);
+  // weight factor: A_e / p_hat on a hop (A_1 = -sig_a dt g, A_2 = -sig_b dt g),
+  // 1 / (1 - sum p_hat) otherwise; num / den as a compensated quotient
+  const float dtg = bp.dt * g * kP24f;
+  const float num = hop1 ? -z.sa * dtg : (hop2 ? -z.sb * dtg : kP24f);
+  const float den = __uint2float_rn((hop1 || hop2) ? T : 16777216u - 2u * T);
+  const float rd = rcp_approx(den);
+  const float q0 = num * rd;
+  const float q1 = __fmaf_rn(-q0, den, num) * rd;
+  z.m = df_mul(z.m, q0, q1);
+  if (!(fabsf(z.m.hi) <= 0x1p32f && fabsf(z.m.hi) >= 0x1p-32f)) renorm(z.m, z.mexp);
+  z.sa = hop1 ? -z.sa : z.sa;
+  z.sb = hop2 ? -z.sb : z.sb;
+}
+
+// The walker's 16 observable contributions (diabatic rho_ij and adiabatic
+// rho_ab, real and imaginary) with weight mantissa `mm`; reduces the phase
+// into [-pi, pi] as a side effect.
+__device__ __forceinline__ void contributions(Scal& z, float mm, float (&v)[16]) {
+  const float kq = rintf(z.ph.hi * kInvTwoPi);
+  z.ph = df_add(z.ph, -kq * kTwoPi1);
+  z.ph = df_add(z.ph, -kq * kTwoPi2);
+  z.ph = df_add(z.ph, -kq * kTwoPi3);
+  float sh, chh;
+  __sincosf(z.ph.hi, &sh, &chh);
+  const float cphi = __fmaf_rn(-z.ph.lo, sh, chh);
+  const float sphi = __fmaf_rn(z.ph.lo, chh, sh);
+  // eigenvector angle theta from (cos 2theta, sin 2theta), half-angle form
+  // without cancellation: the larger of cos/sin is sqrt((1 + |cos2t|)/2)
+  const float t = __fmaf_rn(0.5f, fabsf(z.c2), 0.5f);
+  const float rt = rsqrtf(t);
+  const float big = t * rt, small = 0.5f * fabsf(z.s2) * rt;
+  const bool cpos = z.c2 >= 0.0f;
+  const float c = cpos ? big : small;
+  const float s = copysignf(cpos ? small : big, z.s2);
+  const bool al = z.sa > 0.0f, be = z.sb > 0.0f;
+  const float ua0 = al ? c : -s, ua1 = al ? s : c;  // column alpha of U
+  const float ub0 = be ? c : -s, ub1 = be ? s : c;  // column beta of U
+  const float zr = mm * cphi, zi = -mm * sphi;
+  const float f00 = ua0 * ub0, f01 = ua0 * ub1, f10 = ua1 * ub0, f11 = ua1 * ub1;
+  v[0] = zr * f00;
+  v[1] = zi * f00;
+  v[2] = zr * f01;
+  v[3] = zi * f01;
+  v[4] = zr * f10;
+  v[5] = zi * f10;
+  v[6] = zr * f11;
+  v[7] = zi * f11;
+  const int k = (al ? 2 : 0) + (be ? 1 : 0);
+#pragma unroll
+  for (int kk = 0; kk < 4; ++kk) {
+    v[8 + 2 * kk] = (kk == k) ? zr : 0.0f;
+    v[9 + 2 * kk] = (kk == k) ? zi : 0.0f;
+  }
+}
+
+__device__ __forceinline__ uint32_t pick_word(const u4& wd, int widx) {
+  return (widx & 2) ? ((widx & 1) ? wd.w : wd.z) : ((widx & 1) ? wd.y : wd.x);
+}
+
+template <int NPL>
+struct Walker {
+  float R[NPL], P[NPL];
+};
+
+// P += dt/2 F_ab(R),  F_j = -k_j R_j - s_j - sab (a_j cos2t + b_j sin2t);
+// hu = dt/2 sab cos2t, hv = dt/2 sab sin2t
+template <int NPL, int KIND, typename CF>
+__device__ __forceinline__ void kick(Walker<NPL>& w, const CF& cf, float hu, float hv) {
+#pragma unroll
+  for (int j = 0; j < NPL; ++j) {
+    float p = __fmaf_rn(-cf.hk[j], w.R[j], w.P[j]);
+    if (KIND == 1) p -= cf.hs[j];
+    p = __fmaf_rn(-hu, cf.a[j], p);
+    if (KIND == 1) p = __fmaf_rn(-hv, cf.b[j], p);
+    w.P[j] = p;
+  }
+}
+
+// Per-mode coefficients of a packed request, held in registers.
+template <int NPL>
+struct CoefLocal {
+  float hk[NPL], hs[NPL], dtm[NPL], a[NPL], b[NPL], am[NPL], bm[NPL];
+};
+
+// One 256-walker tile of the one-thread-per-walker kernel: load the tile's
+// walkers, advance them over steps [cs, ce) with their observations, store
+// them.  `cf` holds the per-mode coefficients (kernel parameters, or registers
+// in the packed kernel); all threads of the block call it together.
+template <int NPL, int KIND, typename CF>
+__device__ __forceinline__ void bulk2_tile(const BulkParams& bp, const CF& cf, W32& ws,
+                                           double* __restrict__ part, int64_t tile, int& rb,
+                                           unsigned int& n_deg, double (&red)[2][8][32],
+                                           float* obs_rows) {
+  const int64_t nt = bp.n_traj;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  {
+    const int64_t i = tile * kTile + threadIdx.x;
+    const bool active = i < nt;
+    const int64_t ii = active ? i : 0;
+    Walker<NPL> w;
+#pragma unroll
+    for (int j = 0; j < NPL; ++j) {
+      const bool on = active && j < bp.n;
+      w.R[j] = on ? ws.R[(int64_t)j * nt + ii] : 0.0f;
+      w.P[j] = on ? ws.P[(int64_t)j * nt + ii] : 0.0f;
+    }
+    Scal z;
+    z.m = {active ? ws.mh[ii] : 0.0f, active ? ws.ml[ii] : 0.0f};
+    z.mexp = active ? ws.me[ii] : 0;
+    z.ph = {active ? ws.ph[ii] : 0.0f, active ? ws.pl[ii] : 0.0f};
+    const uint32_t ab = active ? ws.ab[ii] : 0u;
+    z.sa = sgn(ab & 0xff);
+    z.sb = sgn((ab >> 8) & 0xff);
+    const uint64_t traj = bp.traj_offset + (uint64_t)ii;
+    z.A = bp.a0;
+    z.B = bp.b0;
+#pragma unroll
+    for (int j = 0; j < NPL; ++j) {
+      z.A = __fmaf_rn(cf.a[j], w.R[j], z.A);
+      if (KIND == 1) z.B = __fmaf_rn(cf.b[j], w.R[j], z.B);
+    }
+    closed_form(z);
+
+    // observation into slot `slot` of the tile partials: the warp's 32 walkers
+    // share one power of two (FP32 sums of scaled weights, the exponent restored
+    // exactly in FP64); each walker's 16 contributions and their squares go to
+    // its padded row of shared memory and lane q sums column q of its warp's 32
+    // rows by a fixed pairwise tree (conflict-free: row stride 33 words)
+    auto observe = [&](int slot) {
+      renorm(z.m, z.mexp);
+      const bool live = active && z.m.hi != 0.0f;
+      int ew = live ? z.mexp : -(1 << 28);
+#pragma unroll
+      for (int off = 16; off > 0; off >>= 1) ew = max(ew, __shfl_xor_sync(0xffffffffu, ew, off));
+      float v[16];
+      contributions(z, live ? z.m.hi * pow2i(z.mexp - ew) : 0.0f, v);
+      float* row = &obs_rows[threadIdx.x * 33];
+#pragma unroll
+      for (int q = 0; q < 16; ++q) {
+        row[q] = v[q];
+        row[16 + q] = v[q] * v[q];
+      }
+      __syncwarp();
+      const float x = column_sum32(&obs_rows[(warp * 32) * 33 + lane]);
+      __syncwarp();
+      const int ex = (ew < -(1 << 27)) ? 0 : ((lane < 16) ? ew : 2 * ew);
+      const double xd = (double)x;
+      red[rb][warp][lane] = (ex >= -1022 && ex <= 1023) ? xd * pow2d(ex) : ldexp(xd, ex);
+      __syncthreads();
+      if (threadIdx.x < 32)
+        part[((int64_t)slot * bp.n_tiles + tile) * 32 + threadIdx.x] =
+            tile_tree8(&red[rb][0][0], 32, threadIdx.x);
+      rb ^= 1;
+    };
+
+    int slot = bp.obs_first;
+    if (bp.obs_first) observe(0);
+    int to_out = bp.to_out0;
+    uint32_t blk = bp.blk0;
+    int widx = bp.widx0;
+    u4 wd = philox_draw(bp.seed, blk, traj, kPurposeHop);
+    for (int it = 0; it < bp.len; ++it) {
+      const uint32_t word = pick_word(wd, widx);
+      const float hsab = bp.hdt * 0.5f * (z.sa + z.sb);  // dt/2 (sig_a + sig_b)/2
+      kick<NPL, KIND, CF>(w, cf, hsab * z.c2, hsab * z.s2);  // first half kick at R_n
+#pragma unroll
+      for (int j = 0; j < NPL; ++j) w.R[j] = __fmaf_rn(cf.dtm[j], w.P[j], w.R[j]);  // drift
+      const float r_old = z.r;
+      z.A = bp.a0;
+      z.B = bp.b0;
+#pragma unroll
+      for (int j = 0; j < NPL; ++j) {
+        z.A = __fmaf_rn(cf.a[j], w.R[j], z.A);
+        if (KIND == 1) z.B = __fmaf_rn(cf.b[j], w.R[j], z.B);
+      }
+      closed_form(z);
+      kick<NPL, KIND, CF>(w, cf, hsab * z.c2, hsab * z.s2);  // second half kick at R_{n+1}
+      float Av = 0.0f, Bv = 0.0f;
+#pragma unroll
+      for (int j = 0; j < NPL; ++j) {
+        Av = __fmaf_rn(cf.am[j], w.P[j], Av);
+        if (KIND == 1) Bv = __fmaf_rn(cf.bm[j], w.P[j], Bv);
+      }
+      phase_and_transition(z, r_old, Av, Bv, word, bp, active, n_deg);
+      if (++widx == 4) {
+        widx = 0;
+        ++blk;
+        if (it + 1 < bp.len) wd = philox_draw(bp.seed, blk, traj, kPurposeHop);
+      }
+      if (--to_out == 0) {
+        observe(slot++);
+        to_out = bp.stride;
+      }
+    }
+    if (active) {
+#pragma unroll
+      for (int j = 0; j < NPL; ++j)
+        if (j < bp.n) {
+          ws.R[(int64_t)j * nt + i] = w.R[j];
+          ws.P[(int64_t)j * nt + i] = w.P[j];
+        }
+      ws.mh[i] = z.m.hi;
+      ws.ml[i] = z.m.lo;
+      ws.me[i] = z.mexp;
+      ws.ph[i] = z.ph.hi;
+      ws.pl[i] = z.ph.lo;
+      ws.ab[i] = (uint16_t)((z.sa > 0.0f ? 1 : 0) | ((z.sb > 0.0f ? 1 : 0) << 8));
+      if (!isfinite(z.m.hi) || !isfinite(z.ph.hi)) {
+        atomicAdd(&ws.hdr->n_nonfinite, 1ull);
+        atomicOr(&ws.hdr->flags, QCL_FLAG_NONFINITE);
+      }
+    }
+    }
+}
+
+}  // namespace qcl

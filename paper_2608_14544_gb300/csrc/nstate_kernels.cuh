@@ -275,24 +275,51 @@ __global__ void __launch_bounds__(128) k_stepN_f64(const DevModel* __restrict__ 
   bool deg = false;
 #pragma unroll
   for (int a = 0; a + 1 < NS; ++a) deg |= (e0[a + 1] - e0[a] < kDegTolD) || (e1[a + 1] - e1[a] < kDegTolD);
-  // G = sum_j (P_j/M_j) K_j
-  double G[NS][NS];
-#pragma unroll
-  for (int a = 0; a < NS; ++a)
-#pragma unroll
-    for (int b = 0; b < NS; ++b) G[a][b] = 0.0;
-  for (int j = 0; j < n; ++j) {
-    const double v = P[(int64_t)j * nt] / M->mass[j];
-    const double* Kj = M->K + (size_t)j * NS * NS;
-#pragma unroll
-    for (int a = 0; a < NS; ++a)
-#pragma unroll
-      for (int b = 0; b < NS; ++b) G[a][b] += v * Kj[a * NS + b];
-  }
+  // event amplitudes, accumulated mode by mode as sum_j (P_j/M_j) d_j with the
+  // Hellmann-Feynman couplings d_j = (U^T K_j U)_{mu nu} / (e_nu - e_mu)
   constexpr int NC = 2 * NS;
   double A[NC];
   bool ev[NC];
-  deg |= event_amplitudes<double, NS>(G, U1, e1, al, be, dt, kDegTolD, A, ev);
+  {
+    double ua[NS], ub[NS];
+    column<double, NS>(U1, al, ua);
+    column<double, NS>(U1, be, ub);
+    const double ea = pick<double, NS>(e1, al), eb = pick<double, NS>(e1, be);
+    double acc[NC];
+#pragma unroll
+    for (int k = 0; k < NC; ++k) acc[k] = 0.0;
+#pragma unroll
+    for (int nu = 0; nu < NS; ++nu) {
+      ev[nu] = nu != al;
+      ev[NS + nu] = nu != be;
+      deg |= (ev[nu] && fabs(ea - e1[nu]) < kDegTolD) || (ev[NS + nu] && fabs(e1[nu] - eb) < kDegTolD);
+    }
+    for (int j = 0; j < n; ++j) {
+      const double v = P[(int64_t)j * nt] / M->mass[j];
+      const double* Kj = M->K + (size_t)j * NS * NS;
+#pragma unroll
+      for (int nu = 0; nu < NS; ++nu) {
+        double r0 = 0.0, r1 = 0.0;  // (U^T K_j U)_{nu a} and (U^T K_j U)_{b nu}
+#pragma unroll
+        for (int k = 0; k < NS; ++k)
+#pragma unroll
+          for (int l = 0; l < NS; ++l) {
+            r0 += U1[k][nu] * Kj[k * NS + l] * ua[l];
+            r1 += ub[k] * Kj[k * NS + l] * U1[l][nu];
+          }
+        const double g0 = ea - e1[nu], g1 = e1[nu] - eb;
+        const double d0 = (!ev[nu] || fabs(g0) < kDegTolD) ? 0.0 : r0 / g0;
+        const double d1 = (!ev[NS + nu] || fabs(g1) < kDegTolD) ? 0.0 : r1 / g1;
+        acc[nu] += v * d0;
+        acc[NS + nu] += v * d1;
+      }
+    }
+#pragma unroll
+    for (int nu = 0; nu < NS; ++nu) {
+      A[nu] = -dt * acc[nu];
+      A[NS + nu] = dt * acc[NS + nu];
+    }
+  }
   // thresholds: min(kappa |A|, p_max) quantised to 2^-24, scaled down together in
   // exact integers when their sum exceeds Tmax = floor(p_max 2^24)
   uint64_t T[NC], sumT = 0;

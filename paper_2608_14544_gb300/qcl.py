@@ -328,7 +328,9 @@ class Run:
                 extra["E"] = arr(off[10], nt * ns, dt, w).reshape(ns, nt).T.copy()
         return {"R": arr(off[0], nt * n, dt, w).reshape(n, nt).T.copy(), "m_exp": mexp,
                 "P": arr(off[1], nt * n, dt, w).reshape(n, nt).T.copy(),
-                "m": arr(off[2], nt, dt, w), "m_lo": arr(off[3], nt, dt, w),
-                "phi": arr(off[4], nt, dt, w), "phi_lo": arr(off[5], nt, dt, w),
+                "m": arr(off[2], nt, dt, w),
+                "m_lo": np.zeros(nt) if fp64 else arr(off[3], nt, dt, w),
+                "phi": arr(off[4], nt, dt, w),
+                "phi_lo": np.zeros(nt) if fp64 else arr(off[5], nt, dt, w),
                 "alpha": (arr(off[6], nt, np.uint16, 2) & 0xFF).astype(np.int32),
                 "beta": (arr(off[6], nt, np.uint16, 2) >> 8).astype(np.int32), **extra}

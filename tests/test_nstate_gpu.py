@@ -99,7 +99,7 @@ def test_nstate_fp64_per_trajectory_parity(q, case):
         worst["m"] = max(worst.get("m", 0.0), float(err.max()))
         worst["U"] = max(worst.get("U", 0.0), float(np.abs(g["U"][same] - ref.U[same]).max()))
     assert flips <= 1
-    assert max(worst.values()) < 1e-11, worst
+    assert max(worst.values()) < 1e-12, worst
 
 
 @pytest.mark.parametrize("case", [0, 1])
