@@ -83,6 +83,39 @@ def _result_summary(obs, cfg, status):
             "status_flags": status["flags"]}
 
 
+def served_mix_leg(qcl, n_requests: int, traj_hi: float, arena_gb: float, quantum: int):
+    """Poisson-arriving requests (mean gap 5 ms) drawn uniformly from the
+    1-mode, 3-mode, 3-mode vibronic and 100-mode models and a random 4-state
+    model, replayed in real time against the server: per-request latency
+    (finish - submit) percentiles and aggregate trajectory-steps/s."""
+    reqs = wl.served_mix(n_requests=n_requests, traj_range=(1e4, traj_hi))
+    srv = qcl.Server(int(arena_gb * (1 << 30)), max_active=256, quantum_steps=quantum)
+    t0 = time.perf_counter()
+    ids = []
+    for r in reqs:
+        dt_wait = t0 + r["arrival_s"] - time.perf_counter()
+        if dt_wait > 0:
+            time.sleep(dt_wait)
+        ids.append(srv.submit(r))
+    errors = 0
+    for rid in ids:
+        st, _ = srv.wait(rid, 3600.0)
+        errors += st != qcl.REQ_DONE
+    wall = time.perf_counter() - t0
+    st = srv.stats()
+    srv.close()
+    kinds = [0] * 5
+    for r in reqs:
+        kinds[r["kind"]] += 1
+    return {"requests": n_requests, "kinds_sb1_sb3_vib3_sb100_lvc4": kinds,
+            "n_traj_range": [1e4, traj_hi], "steps_range": [500, 4000],
+            "latency_p50_s": st["latency_p50_s"], "latency_p99_s": st["latency_p99_s"],
+            "latency_mean_s": st["latency_mean_s"], "throughput": st["throughput"],
+            "unit": "traj-steps/s", "span_s": st["span_s"], "wall_s": wall,
+            "rounds": st["rounds"], "graph_replays": st["graph_replays"],
+            "errors": int(errors + st["n_error"]), "quantum_steps": quantum}
+
+
 # ------------------------------------------------------------------- clocks --
 class ClockSampler:
     FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
@@ -336,6 +369,11 @@ def run_ours(args):
     st4 = r4.status()
     del r4
 
+    served = None
+    if args.served_requests > 0 and rank == 0:
+        served = served_mix_leg(qcl, args.served_requests, args.served_traj_max,
+                                args.served_arena_gb, args.served_quantum)
+
     if rank != 0:
         if dist:
             dist.destroy_process_group()
@@ -399,6 +437,7 @@ def run_ours(args):
                                         / (k4_ms / 1e3) / 1e12 / peak_tflops) if k4_ms > 0 else None,
                   "kernel": "k_bulk2_split (two warps per 32 walkers)",
                   "status_flags": st4["flags"]},
+        "served_mix": served,
         "clocks": clocks,
         "result": _result_summary(obs, cfg, status),
     }
@@ -415,6 +454,10 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--sb100-walkers", type=int, default=2_000_000)
+    ap.add_argument("--served-requests", type=int, default=256)
+    ap.add_argument("--served-traj-max", type=float, default=1e6)
+    ap.add_argument("--served-arena-gb", type=float, default=48.0)
+    ap.add_argument("--served-quantum", type=int, default=400)
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

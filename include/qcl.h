@@ -245,6 +245,84 @@ qcl_status qcl_propagate_noalloc(const qcl_model* model, const qcl_ensemble_desc
                                  double dt, int32_t out_stride, double* rows, size_t rows_bytes,
                                  int64_t n_out, void* stream);
 
+/* ---------------------------------------------------------------- serving
+ * A request loop for many solves of different models, walker counts and step
+ * counts arriving over time (continuous batching; no counterpart in the paper,
+ * which runs one solve at a time).  The server admits queued requests in
+ * arrival order while the caller's device arena has room for their ensemble
+ * and observation buffers and fewer than max_active are running; it advances
+ * all admitted requests together in rounds of at most quantum_steps steps
+ * (and 16 output times) each, packing two-state requests of up to 8 modes
+ * into shared persistent launches (a CUDA graph replayed every round when
+ * use_graphs is set); requests arriving meanwhile join at the next round.  A
+ * request's results do not depend on what it is batched with.  Requests run
+ * in FP32-bulk precision.  The server owns one CUDA stream and a worker
+ * thread; the caller owns the arena (device memory, 256-byte aligned), which
+ * must stay valid until qcl_server_destroy returns. */
+typedef struct qcl_server qcl_server; /* opaque */
+
+typedef struct {
+  void* arena;            /* device memory the server sub-allocates */
+  size_t arena_bytes;
+  int32_t max_active;     /* requests propagating at the same time (>= 1) */
+  int32_t quantum_steps;  /* steps a request advances per round (>= 1) */
+  int32_t use_graphs;     /* 1: replay the packed launches as a CUDA graph */
+  int32_t max_queue;      /* queued requests beyond which submit returns BUSY (0: no limit) */
+  double round_timeout_s; /* a round not finished after this long fails its requests (0: 600 s) */
+} qcl_server_desc;
+
+typedef struct {
+  const qcl_model_desc* model; /* copied at submit */
+  const qcl_init_desc* init;   /* copied at submit */
+  int64_t n_traj;
+  uint64_t seed;
+  uint64_t traj_id_offset;
+  int64_t n_steps;
+  double dt;
+  int32_t out_stride;
+  int32_t reserved;
+} qcl_request_desc;
+
+#define QCL_REQ_QUEUED 0
+#define QCL_REQ_RUNNING 1
+#define QCL_REQ_DONE 2
+#define QCL_REQ_ERROR 3
+
+typedef struct {
+  int64_t n_submitted, n_done, n_error, n_active, n_queued;
+  int64_t rounds, graph_replays;
+  size_t arena_used;
+  double traj_steps_done;   /* sum over finished requests of n_traj x n_steps */
+  double latency_p50_s;     /* finish - submit, over finished requests */
+  double latency_p99_s;
+  double latency_mean_s;
+  double span_s;            /* first submit to last finish */
+  double throughput;        /* traj_steps_done / span_s */
+} qcl_server_statistics;
+
+qcl_status qcl_server_create(const qcl_server_desc* d, qcl_server** out);
+
+/* Copies the request and queues it; *id identifies it.  QCL_ERR_OUT_OF_MEMORY
+ * if it could never fit the arena, QCL_ERR_BUSY if the queue is full. */
+qcl_status qcl_server_submit(qcl_server* s, const qcl_request_desc* r, int64_t* id);
+
+/* State of a request (QCL_REQ_*) and, once done, its observables: n_rows rows
+ * laid out as qcl_reduce_observables writes them, copied to host_out when it is
+ * not NULL (host_len doubles at least).  A failed request returns
+ * QCL_ERR_NUMERICAL with its message. */
+qcl_status qcl_server_poll(qcl_server* s, int64_t id, int32_t* state, double* host_out,
+                           size_t host_len, int64_t* n_rows);
+
+/* Blocks until the request is done or failed, or timeout_s passes
+ * (QCL_ERR_TIMEOUT). */
+qcl_status qcl_server_wait(qcl_server* s, int64_t id, double timeout_s, int32_t* state);
+
+qcl_status qcl_server_stats(qcl_server* s, qcl_server_statistics* out);
+
+/* Stops the worker after its current round and releases the server's
+ * resources (not the arena).  NULL is accepted. */
+qcl_status qcl_server_destroy(qcl_server* s);
+
 /* ----------------------------------------------------------- instrumentation
  * Process-wide options:
  *   QCL_OPT_GRID_CAP  cap on the persistent grid (0: SMs x resident blocks);

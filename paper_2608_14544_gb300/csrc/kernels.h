@@ -65,6 +65,32 @@ struct CoefN {
   float E[36];
 };
 
+// One request of a packed launch: a two-state model with at most 8 modes
+// advancing over its own steps [cs, ce) (device table entry).
+constexpr int kMaxPacked = 256;
+struct PackedReq {
+  BulkParams bp;
+  void* ens;          // the request's ensemble buffer
+  double* part;       // its per-tile partials
+  int64_t work0;      // first global work item (tile) of this request
+  float hk[8], hs[8], dtm[8], a[8], b[8], am[8], bm[8];
+};
+struct PackedTable {
+  int64_t n_work;     // total tiles of all requests
+  int32_t n_req;
+  int32_t pad;
+  PackedReq req[kMaxPacked];
+};
+// Mode-count buckets of the packed kernel (a request with n modes runs in the
+// smallest bucket >= n); returns the bucket index or -1 if n > 8.
+inline int packed_bucket(int n) {
+  return n <= 1 ? 0 : n <= 2 ? 1 : n <= 3 ? 2 : n <= 4 ? 3 : n <= 6 ? 4 : n <= 8 ? 5 : -1;
+}
+constexpr int kPackedBuckets = 6;
+// Launches the packed kernel of (bucket, kind) over the device table; returns
+// the grid size.
+int launch_packed(int bucket, int kind, const PackedTable* dtab, cudaStream_t st);
+
 // Kernel launches issued by the library (instrumentation).
 void launches_add(int64_t k);
 int64_t launches_read(bool reset);

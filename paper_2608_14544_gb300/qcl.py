@@ -32,7 +32,10 @@ EXPORTS = [
     "qcl_create_model", "qcl_destroy_model", "qcl_ensemble_bytes", "qcl_obs_bytes",
     "qcl_ensemble_layout", "qcl_sample_initial", "qcl_propagate", "qcl_reduce_observables",
     "qcl_read_sums", "qcl_ensemble_status", "qcl_propagate_noalloc",
+    "qcl_server_create", "qcl_server_submit", "qcl_server_poll", "qcl_server_wait",
+    "qcl_server_stats", "qcl_server_destroy",
 ]
+REQ_QUEUED, REQ_RUNNING, REQ_DONE, REQ_ERROR = 0, 1, 2, 3
 
 
 class QclError(RuntimeError):
@@ -55,6 +58,27 @@ class EnsembleDesc(C.Structure):
 class InitDesc(C.Structure):
     _fields_ = [("rho_el0", C.c_void_p), ("R0", C.c_void_p), ("P0", C.c_void_p),
                 ("beta", C.c_double), ("wigner", C.c_int32), ("reserved", C.c_int32)]
+
+
+class ServerDesc(C.Structure):
+    _fields_ = [("arena", C.c_void_p), ("arena_bytes", C.c_size_t), ("max_active", C.c_int32),
+                ("quantum_steps", C.c_int32), ("use_graphs", C.c_int32), ("max_queue", C.c_int32),
+                ("round_timeout_s", C.c_double)]
+
+
+class RequestDesc(C.Structure):
+    _fields_ = [("model", C.c_void_p), ("init", C.c_void_p), ("n_traj", C.c_int64),
+                ("seed", C.c_uint64), ("traj_id_offset", C.c_uint64), ("n_steps", C.c_int64),
+                ("dt", C.c_double), ("out_stride", C.c_int32), ("reserved", C.c_int32)]
+
+
+class ServerStats(C.Structure):
+    _fields_ = [("n_submitted", C.c_int64), ("n_done", C.c_int64), ("n_error", C.c_int64),
+                ("n_active", C.c_int64), ("n_queued", C.c_int64), ("rounds", C.c_int64),
+                ("graph_replays", C.c_int64), ("arena_used", C.c_size_t),
+                ("traj_steps_done", C.c_double), ("latency_p50_s", C.c_double),
+                ("latency_p99_s", C.c_double), ("latency_mean_s", C.c_double),
+                ("span_s", C.c_double), ("throughput", C.c_double)]
 
 
 class EnsStatus(C.Structure):
@@ -92,6 +116,12 @@ def load(path: str = LIB_PATH):
     lib.qcl_ensemble_status.argtypes = [vp, vp, vp, sz, vp, vp]
     lib.qcl_propagate_noalloc.argtypes = [vp, vp, vp, sz, i64, i64, C.c_double, i32, vp, sz, i64,
                                           vp]
+    lib.qcl_server_create.argtypes = [vp, vp]
+    lib.qcl_server_submit.argtypes = [vp, vp, vp]
+    lib.qcl_server_poll.argtypes = [vp, i64, vp, vp, sz, vp]
+    lib.qcl_server_wait.argtypes = [vp, i64, C.c_double, vp]
+    lib.qcl_server_stats.argtypes = [vp, vp]
+    lib.qcl_server_destroy.argtypes = [vp]
     for name in EXPORTS:
         f = getattr(lib, name)
         if name not in ("qcl_last_error", "qcl_version"):
@@ -334,3 +364,81 @@ class Run:
                 "phi_lo": np.zeros(nt) if fp64 else arr(off[5], nt, dt, w),
                 "alpha": (arr(off[6], nt, np.uint16, 2) & 0xFF).astype(np.int32),
                 "beta": (arr(off[6], nt, np.uint16, 2) >> 8).astype(np.int32), **extra}
+
+
+# ------------------------------------------------------------------ serving --
+def _model_desc(m: dict):
+    arrs = [_f64(m["mass"]), _f64(m["omega"]), _f64(m["E"]).reshape(-1), _f64(m["K"]).reshape(-1)]
+    d = ModelDesc(int(m["n_states"]), int(m["n_modes"]), float(m["hbar"]),
+                  *[a.ctypes.data for a in arrs], float(m.get("hop_scale", 1.0)),
+                  float(m.get("p_max", 0.5)))
+    return d, arrs
+
+
+def _init_desc(i: dict):
+    arrs = [_f64(i["rho_el0"]).reshape(-1), _f64(i["R0"]), _f64(i["P0"])]
+    d = InitDesc(*[a.ctypes.data for a in arrs], float(i.get("beta", math.inf)),
+                 int(i.get("wigner", 1)), 0)
+    return d, arrs
+
+
+class Server:
+    """qcl_server_*: continuous-batching request loop over a caller-owned
+    device arena (a torch tensor held by this object)."""
+
+    def __init__(self, arena_bytes: int, max_active: int = 64, quantum_steps: int = 200,
+                 use_graphs: bool = True, max_queue: int = 0, round_timeout_s: float = 0.0,
+                 device="cuda"):
+        self.arena = device_buffer(arena_bytes, device)
+        d = ServerDesc(self.arena.data_ptr(), int(arena_bytes), int(max_active),
+                       int(quantum_steps), 1 if use_graphs else 0, int(max_queue),
+                       float(round_timeout_s))
+        h = C.c_void_p()
+        _check(load().qcl_server_create(C.byref(d), C.byref(h)), "qcl_server_create")
+        self.handle = h
+        self.n_states = {}
+
+    def submit(self, req: dict) -> int:
+        md, keep1 = _model_desc(req["model"])
+        ind, keep2 = _init_desc(req["init"])
+        r = RequestDesc(C.addressof(md), C.addressof(ind), int(req["n_traj"]), int(req["seed"]),
+                        int(req.get("traj_id_offset", 0)), int(req["n_steps"]), float(req["dt"]),
+                        int(req["out_stride"]), 0)
+        rid = C.c_int64()
+        _check(load().qcl_server_submit(self.handle, C.byref(r), C.byref(rid)), "qcl_server_submit")
+        self.n_states[rid.value] = int(req["model"]["n_states"])
+        return rid.value
+
+    def poll(self, rid: int):
+        """(state, observables or None)."""
+        st, n_rows = C.c_int32(), C.c_int64()
+        _check(load().qcl_server_poll(self.handle, rid, C.byref(st), None, 0, C.byref(n_rows)),
+               "qcl_server_poll")
+        if st.value != REQ_DONE:
+            return st.value, None
+        q = 4 * self.n_states[rid] ** 2
+        out = np.zeros((n_rows.value, 2 * q + 3))
+        _check(load().qcl_server_poll(self.handle, rid, C.byref(st), out.ctypes.data, out.size,
+                                      C.byref(n_rows)), "qcl_server_poll")
+        return st.value, out
+
+    def wait(self, rid: int, timeout_s: float = 600.0):
+        st = C.c_int32()
+        _check(load().qcl_server_wait(self.handle, rid, timeout_s, C.byref(st)), "qcl_server_wait")
+        return self.poll(rid)
+
+    def stats(self) -> dict:
+        s = ServerStats()
+        _check(load().qcl_server_stats(self.handle, C.byref(s)), "qcl_server_stats")
+        return {k: getattr(s, k) for k, _ in ServerStats._fields_}
+
+    def close(self):
+        if self.handle:
+            load().qcl_server_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

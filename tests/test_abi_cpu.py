@@ -88,3 +88,17 @@ def test_option_and_null_checks_without_gpu(lib):
     assert lib.qcl_kernel_time(7, None, None) == 1
     b = C.c_size_t()
     assert lib.qcl_ensemble_bytes(None, None, C.byref(b)) == 1
+
+
+def test_server_validation_without_gpu(lib):
+    from paper_2608_14544_gb300 import qcl
+
+    h = C.c_void_p()
+    d = qcl.ServerDesc(None, 1 << 30, 4, 100, 1, 0, 0.0)
+    assert lib.qcl_server_create(C.byref(d), C.byref(h)) == 1 and not h.value
+    d = qcl.ServerDesc(256, 1024, 4, 100, 1, 0, 0.0)
+    assert lib.qcl_server_create(C.byref(d), C.byref(h)) == 3
+    assert lib.qcl_server_create(None, C.byref(h)) == 1
+    assert lib.qcl_server_destroy(None) == 0
+    st = C.c_int32()
+    assert lib.qcl_server_poll(None, 1, C.byref(st), None, 0, None) == 1

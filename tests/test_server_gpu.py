@@ -1,0 +1,115 @@
+"""Serving layer (continuous batching): results the same alone and in a mix,
+agreement with the single-solve entry points, admission by arena memory,
+requests joining while others run, latency statistics."""
+import time
+
+import numpy as np
+import pytest
+
+from paper_2608_14544_gb300 import workloads as wl
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def q():
+    import torch
+
+    from paper_2608_14544_gb300 import build, qcl
+
+    build.build()
+    torch.cuda.set_device(0)
+    return qcl
+
+
+def _req(cfg, n_traj, n_steps, seed, **kw):
+    return dict(model=cfg["model"], init=cfg["init"], n_traj=n_traj, seed=seed,
+                n_steps=n_steps, dt=cfg["dt"], out_stride=cfg["out_stride"], **kw)
+
+
+def _mix():
+    reqs = [
+        _req(wl.config(1), 30_000, 400, 1),
+        _req(wl.config(3), 50_000, 300, 2),
+        _req(wl.config(4), 20_000, 200, 3),
+        _req(wl.lvc4_config(9), 15_000, 300, 4),
+        _req(wl.config(2), 80_000, 500, 5),
+        _req(wl.config(1), 7_001, 250, 6),
+    ]
+    return reqs
+
+
+@pytest.mark.parametrize("graphs", [True, False])
+def test_results_are_the_same_alone_and_in_the_mix(q, graphs):
+    reqs = _mix()
+    alone = []
+    for r in reqs:
+        srv = q.Server(1 << 30, use_graphs=graphs, quantum_steps=120)
+        st, obs = srv.wait(srv.submit(r))
+        assert st == q.REQ_DONE
+        alone.append(obs)
+        srv.close()
+    srv = q.Server(1 << 31, use_graphs=graphs, quantum_steps=120)
+    ids = []
+    for k, r in enumerate(reqs):  # staggered arrivals: later requests join running rounds
+        ids.append(srv.submit(r))
+        time.sleep(0.002 * k)
+    for k, rid in enumerate(ids):
+        st, obs = srv.wait(rid)
+        assert st == q.REQ_DONE
+        assert np.array_equal(obs, alone[k]), k
+    s = srv.stats()
+    assert s["n_done"] == len(reqs) and s["n_error"] == 0
+    assert s["latency_p99_s"] >= s["latency_p50_s"] > 0
+    if graphs:
+        assert s["graph_replays"] == s["rounds"] > 0
+    srv.close()
+
+
+def test_served_matches_single_solve(q):
+    for cfg, n, steps in ((wl.config(2), 60_000, 400), (wl.config(4), 20_000, 200),
+                          (wl.lvc4_config(3), 10_000, 200)):
+        srv = q.Server(1 << 30, quantum_steps=150)
+        st, served = srv.wait(srv.submit(_req(cfg, n, steps, 7)))
+        srv.close()
+        m = q.Model(cfg["model"])
+        run = q.Run(m, n, 7, q.PREC_FP32_BULK, steps // cfg["out_stride"] + 1)
+        run.sample(cfg["init"])
+        run.propagate(steps, cfg["dt"], cfg["out_stride"])
+        single = run.observables()
+        nq = 4 * cfg["model"]["n_states"] ** 2
+        assert np.allclose(served[:, :nq], single[:, :nq], rtol=1e-5,
+                           atol=1e-6 * np.abs(single[:, :nq]).max())
+
+
+def test_admission_waits_for_arena_memory(q):
+    cfg = wl.config(2)
+    r = _req(cfg, 400_000, 600, 3)
+    m = q.Model(cfg["model"])
+    ens = q.ens_desc(r["n_traj"], 3, q.PREC_FP32_BULK)
+    need = q.ensemble_bytes(m, ens) + q.obs_bytes(m, ens, 600 // cfg["out_stride"] + 1)
+    srv = q.Server(int(2.5 * need) + (4 << 20), max_active=16, quantum_steps=100)
+    ids = [srv.submit(dict(r, seed=k)) for k in range(5)]
+    s = srv.stats()
+    assert s["n_active"] <= 2 and s["n_active"] + s["n_queued"] + s["n_done"] == 5
+    for rid in ids:
+        st, _ = srv.wait(rid)
+        assert st == q.REQ_DONE
+    assert srv.stats()["n_done"] == 5 and srv.stats()["arena_used"] == 0
+    with pytest.raises(q.QclError) as e:
+        srv.submit(_req(cfg, 40_000_000, 600, 1))
+    assert e.value.status == 3
+    srv.close()
+
+
+def test_short_request_joins_and_finishes_before_a_long_one(q):
+    srv = q.Server(1 << 31, quantum_steps=100)
+    long_id = srv.submit(_req(wl.config(2), 2_000_000, 2000, 1))
+    time.sleep(0.05)
+    short_id = srv.submit(_req(wl.config(1), 10_000, 100, 2))
+    st, _ = srv.wait(short_id)
+    assert st == q.REQ_DONE
+    assert srv.poll(long_id)[0] == q.REQ_RUNNING
+    st, _ = srv.wait(long_id)
+    assert st == q.REQ_DONE
+    srv.close()
