@@ -245,6 +245,23 @@ qcl_status qcl_propagate_noalloc(const qcl_model* model, const qcl_ensemble_desc
                                  double dt, int32_t out_stride, double* rows, size_t rows_bytes,
                                  int64_t n_out, void* stream);
 
+/* ------------------------------------------------------------------ shards
+ * Walkers are independent and each draws its random numbers from its global id,
+ * so an ensemble can be split into shards of contiguous walkers (one per GPU),
+ * each propagated with traj_id_offset = its first walker.  The output sums of a
+ * shard of 2^k tiles (tiles of qcl_shard_tile_walkers walkers) aligned to a
+ * multiple of 2^k tiles are a subtree of the single-ensemble reduction tree;
+ * combining the shards' sums by the same zero-padded binary tree gives the same
+ * bits as one unsharded run (no counterpart in the paper, which uses one GPU). */
+
+/* Walkers per reduction tile of an FP32-bulk (or FP64) ensemble of this model. */
+qcl_status qcl_shard_tile_walkers(const qcl_model* model, int32_t precision, int64_t* walkers);
+
+/* Host-side combine: out[i] = binary tree over s (zero-padded to a power of
+ * two) of shard_sums[s * n_elems + i], shards in walker order. */
+qcl_status qcl_combine_shards(const double* shard_sums, int32_t n_shards, int64_t n_elems,
+                              double* out);
+
 /* ---------------------------------------------------------------- serving
  * A request loop for many solves of different models, walker counts and step
  * counts arriving over time (continuous batching; no counterpart in the paper,

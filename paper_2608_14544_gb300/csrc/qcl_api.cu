@@ -544,4 +544,25 @@ qcl_status qcl_ensemble_status(const qcl_model* model, const qcl_ensemble_desc* 
   return ok();
 }
 
+qcl_status qcl_shard_tile_walkers(const qcl_model* model, int32_t precision, int64_t* walkers) {
+  if (!model || !walkers) return fail(QCL_ERR_INVALID_ARG, "NULL argument");
+  if (precision != QCL_PREC_FP64 && precision != QCL_PREC_FP32_BULK) return fail(QCL_ERR_INVALID_ARG, "unknown precision");
+  *walkers = tile_walkers(precision, model->n, model->ns);
+  return ok();
+}
+
+qcl_status qcl_combine_shards(const double* shard_sums, int32_t n_shards, int64_t n_elems, double* out) {
+  if (!shard_sums || !out || n_shards < 1 || n_elems < 0) return fail(QCL_ERR_INVALID_ARG, "bad arguments");
+  int32_t p2 = 1;
+  while (p2 < n_shards) p2 <<= 1;
+  std::vector<double> level((size_t)p2);
+  for (int64_t i = 0; i < n_elems; ++i) {
+    for (int32_t s = 0; s < p2; ++s) level[s] = (s < n_shards) ? shard_sums[(size_t)s * n_elems + i] : 0.0;
+    for (int32_t w = p2; w > 1; w >>= 1)
+      for (int32_t s = 0; s < w / 2; ++s) level[s] = level[2 * s] + level[2 * s + 1];
+    out[i] = level[0];
+  }
+  return ok();
+}
+
 }  // extern "C"

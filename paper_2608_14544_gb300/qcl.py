@@ -33,7 +33,7 @@ EXPORTS = [
     "qcl_ensemble_layout", "qcl_sample_initial", "qcl_propagate", "qcl_reduce_observables",
     "qcl_read_sums", "qcl_ensemble_status", "qcl_propagate_noalloc",
     "qcl_server_create", "qcl_server_submit", "qcl_server_poll", "qcl_server_wait",
-    "qcl_server_stats", "qcl_server_destroy",
+    "qcl_server_stats", "qcl_server_destroy", "qcl_shard_tile_walkers", "qcl_combine_shards",
 ]
 REQ_QUEUED, REQ_RUNNING, REQ_DONE, REQ_ERROR = 0, 1, 2, 3
 
@@ -116,6 +116,8 @@ def load(path: str = LIB_PATH):
     lib.qcl_ensemble_status.argtypes = [vp, vp, vp, sz, vp, vp]
     lib.qcl_propagate_noalloc.argtypes = [vp, vp, vp, sz, i64, i64, C.c_double, i32, vp, sz, i64,
                                           vp]
+    lib.qcl_shard_tile_walkers.argtypes = [vp, i32, vp]
+    lib.qcl_combine_shards.argtypes = [vp, i32, i64, vp]
     lib.qcl_server_create.argtypes = [vp, vp]
     lib.qcl_server_submit.argtypes = [vp, vp, vp]
     lib.qcl_server_poll.argtypes = [vp, i64, vp, vp, sz, vp]
@@ -364,6 +366,24 @@ class Run:
                 "phi_lo": np.zeros(nt) if fp64 else arr(off[5], nt, dt, w),
                 "alpha": (arr(off[6], nt, np.uint16, 2) & 0xFF).astype(np.int32),
                 "beta": (arr(off[6], nt, np.uint16, 2) >> 8).astype(np.int32), **extra}
+
+
+# ------------------------------------------------------------------- shards --
+def shard_tile_walkers(model: Model, precision: int) -> int:
+    w = C.c_int64()
+    _check(load().qcl_shard_tile_walkers(model.handle, precision, C.byref(w)),
+           "qcl_shard_tile_walkers")
+    return w.value
+
+
+def combine_shards(shard_sums) -> np.ndarray:
+    """Binary-tree combine of per-shard output sums (first axis = shard, in
+    walker order), the same tree as one unsharded run."""
+    a = np.ascontiguousarray(np.asarray(shard_sums, dtype=np.float64))
+    out = np.zeros(a.shape[1:])
+    _check(load().qcl_combine_shards(a.ctypes.data, a.shape[0], int(out.size), out.ctypes.data),
+           "qcl_combine_shards")
+    return out
 
 
 # ------------------------------------------------------------------ serving --

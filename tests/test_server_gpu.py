@@ -104,8 +104,8 @@ def test_admission_waits_for_arena_memory(q):
 
 def test_short_request_joins_and_finishes_before_a_long_one(q):
     srv = q.Server(1 << 31, quantum_steps=100)
-    long_id = srv.submit(_req(wl.config(2), 2_000_000, 2000, 1))
-    time.sleep(0.05)
+    long_id = srv.submit(_req(wl.config(2), 10_000_000, 4000, 1))
+    time.sleep(0.02)
     short_id = srv.submit(_req(wl.config(1), 10_000, 100, 2))
     st, _ = srv.wait(short_id)
     assert st == q.REQ_DONE
