@@ -11,7 +11,7 @@ import time
 
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("--config", type=int, default=2)
+    ap.add_argument("--config", default="2", help="1-4, or lvc4 (random four-state model)")
     ap.add_argument("--n-traj", type=int, default=None)
     ap.add_argument("--steps", type=int, default=None)
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
@@ -25,7 +25,7 @@ def main():
 
     build.build()
     torch.cuda.set_device(0)
-    cfg = wl.config(args.config)
+    cfg = wl.lvc4_config(1) if args.config == "lvc4" else wl.config(int(args.config))
     n = args.n_traj or cfg["n_traj"]
     steps = args.steps or cfg["n_steps"]
     stride = cfg["out_stride"]
