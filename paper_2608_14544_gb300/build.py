@@ -21,6 +21,11 @@ NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompil
               "--expt-relaxed-constexpr", "-I", os.path.join(ROOT, "include")]
 
 
+# Units compiled without multiply-add contraction: the FP64 many-state kernels
+# whose arithmetic follows the oracle's operation by operation.
+NO_FMA = ("kernels_nstate64_",)
+
+
 def sources():
     return sorted(os.path.join(CSRC, f) for f in os.listdir(CSRC)
                   if f.endswith((".cu", ".cpp")))
@@ -42,6 +47,8 @@ def _nvcc():
 def _compile(src, verbose):
     obj = os.path.join(BUILD, os.path.basename(src) + ".o")
     cmd = [_nvcc(), *ARCH, *NVCC_FLAGS, "-c", src, "-o", obj]
+    if os.path.basename(src).startswith(NO_FMA):
+        cmd.insert(1, "-fmad=false")
     if verbose:
         cmd += ["-Xptxas", "-v"]
     r = subprocess.run(cmd, capture_output=True, text=True)

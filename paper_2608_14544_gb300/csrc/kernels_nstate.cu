@@ -1,11 +1,12 @@
 // kernels_nstate.cu -- dispatch of the N_s-state launchers (N_s = 3..8) to
-// their per-N_s translation units (kernels_nstate_3.cu .. kernels_nstate_8.cu).
+// their per-N_s translation units (kernels_nstate_*.cu, kernels_nstate64_*.cu).
 #include "kernels.h"
 
 namespace qcl {
 
 #define QCL_NS_DECL(k)                                                                        \
-  void nstate_sample_##k(const DevModel*, const SampleParams&, void*, int, cudaStream_t);     \
+  void nstate_sample64_##k(const DevModel*, const SampleParams&, void*, cudaStream_t);        \
+  void nstate_sample32_##k(const DevModel*, const SampleParams&, void*, cudaStream_t);        \
   void nstate_step64_##k(const DevModel*, void*, int64_t, int, int64_t, int64_t, double,      \
                          uint64_t, uint64_t, cudaStream_t);                                   \
   void nstate_observe64_##k(const void*, int64_t, int, double*, cudaStream_t);                \
@@ -30,7 +31,11 @@ QCL_NS_DECL(8)
 
 void launch_sampleN(const DevModel* dm, const SampleParams& sp, void* buf, int precision,
                     cudaStream_t st) {
-  QCL_NS_SWITCH(sp.ns, nstate_sample, dm, sp, buf, precision, st);
+  if (precision == QCL_PREC_FP64) {
+    QCL_NS_SWITCH(sp.ns, nstate_sample64, dm, sp, buf, st);
+  } else {
+    QCL_NS_SWITCH(sp.ns, nstate_sample32, dm, sp, buf, st);
+  }
   launches_add(1);
 }
 

@@ -1,14 +1,10 @@
-// kernels_nstate_3.cu -- the N_s-state kernels instantiated for N_s = 3.
+// kernels_nstate_3.cu -- the FP32-bulk and FP64-observation N_s-state kernels
+// instantiated for N_s = 3.
 #include "nstate_kernels.cuh"
 
 namespace qcl {
-void nstate_sample_3(const DevModel* dm, const SampleParams& sp, void* buf, int precision,
-                     cudaStream_t st) {
-  NStateOps<3>::sample(dm, sp, buf, precision, st);
-}
-void nstate_step64_3(const DevModel* dm, void* buf, int64_t nt, int n, int64_t step0,
-                     int64_t step, double dt, uint64_t seed, uint64_t traj_off, cudaStream_t st) {
-  NStateOps<3>::step64(dm, buf, nt, n, step0, step, dt, seed, traj_off, st);
+void nstate_sample32_3(const DevModel* dm, const SampleParams& sp, void* buf, cudaStream_t st) {
+  NStateOps<3>::sample32(dm, sp, buf, st);
 }
 void nstate_observe64_3(const void* buf, int64_t nt, int n, double* part, cudaStream_t st) {
   NStateOps<3>::observe64(buf, nt, n, part, st);

@@ -62,15 +62,17 @@ __device__ __forceinline__ T offdiag2(const T (&A)[NS][NS]) {
   return off;
 }
 
-// Diagonalises A (destroyed) into ascending e and eigenvectors U[i][a]; with
-// `ref` the rotation starts from ref's basis and the signs follow ref.
-// Sweeps: at most max_sweeps, stopping when the off-diagonal mass is below
-// tol2 times the matrix norm (a fixed sweep count when tol2 < 0).
+// Diagonalises W into ascending e and eigenvectors U[i][a]; with `ref` the
+// signs follow ref, and with `warm` the rotations also start from ref's basis
+// (otherwise from W itself).  Sweeps: at most max_sweeps, stopping when the
+// off-diagonal mass is below tol2 times the matrix norm (a fixed sweep count
+// when tol2 < 0).
 template <typename T, int NS>
 __device__ __forceinline__ void eigh_ns(const T (&W)[NS][NS], const T (*ref)[NS], T (&e)[NS],
-                                        T (&U)[NS][NS], int max_sweeps, T tol2) {
+                                        T (&U)[NS][NS], int max_sweeps, T tol2,
+                                        bool warm = true) {
   T A[NS][NS], V[NS][NS];
-  if (ref) {
+  if (ref && warm) {
     // A = ref^T W ref
     T Wr[NS][NS];
 #pragma unroll
@@ -123,7 +125,7 @@ __device__ __forceinline__ void eigh_ns(const T (&W)[NS][NS], const T (*ref)[NS]
       for (int q = p + 1; q < NS; ++q) jacobi_rotate<T, NS>(A, V, p, q);
   }
   // eigenvectors in the original basis
-  if (ref) {
+  if (ref && warm) {
 #pragma unroll
     for (int i = 0; i < NS; ++i)
 #pragma unroll

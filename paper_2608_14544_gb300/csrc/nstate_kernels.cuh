@@ -80,7 +80,8 @@ __device__ __forceinline__ void elec_g(const DevModel* M, const double* R, int64
   }
 }
 
-// P += dt/2 F_ab, F_j = -k_j R_j - 1/2 (u_a^T K_j u_a + u_b^T K_j u_b)   (FP64 path)
+// P += dt/2 F_ab, F_j = -k_j R_j - 1/2 ((U^T K_j U)_aa + (U^T K_j U)_bb)  (FP64 path;
+// the Hellmann-Feynman elements accumulated in the same order as the oracle)
 template <int NS>
 __device__ __forceinline__ void half_kick_g(const DevModel* M, double* R, double* P, int64_t nt,
                                             int n, const double (&U)[NS][NS], int al, int be,
@@ -88,20 +89,18 @@ __device__ __forceinline__ void half_kick_g(const DevModel* M, double* R, double
   double ua[NS], ub[NS];
   column<double, NS>(U, al, ua);
   column<double, NS>(U, be, ub);
-  double Q[NS][NS];
-#pragma unroll
-  for (int k = 0; k < NS; ++k)
-#pragma unroll
-    for (int l = 0; l < NS; ++l) Q[k][l] = ua[k] * ua[l] + ub[k] * ub[l];
   for (int j = 0; j < n; ++j) {
     const double* Kj = M->K + (size_t)j * NS * NS;
-    double g = 0.0;
+    double ga = 0.0, gb = 0.0;
 #pragma unroll
     for (int k = 0; k < NS; ++k)
 #pragma unroll
-      for (int l = 0; l < NS; ++l) g += Kj[k * NS + l] * Q[k][l];
+      for (int l = 0; l < NS; ++l) {
+        ga += ua[k] * Kj[k * NS + l] * ua[l];
+        gb += ub[k] * Kj[k * NS + l] * ub[l];
+      }
     const int64_t o = (int64_t)j * nt;
-    const double F = -M->k[j] * R[o] - 0.5 * g;
+    const double F = -M->k[j] * R[o] - 0.5 * (ga + gb);
     P[o] += 0.5 * dt * F;
   }
 }
@@ -263,11 +262,11 @@ __global__ void __launch_bounds__(128) k_stepN_f64(const DevModel* __restrict__ 
   double W[NS][NS], e0[NS], U0[NS][NS], e1[NS], U1[NS][NS];
   // decomposition at R_n, gauge following the carried eigenvectors
   elec_g<NS>(M, R, nt, n, W);
-  eigh_ns<double, NS>(W, Uc, e0, U0, 50, 1e-34);
+  eigh_ns<double, NS>(W, Uc, e0, U0, 100, 1e-34, false);
   half_kick_g<NS>(M, R, P, nt, n, U0, al, be, dt);
   for (int j = 0; j < n; ++j) R[(int64_t)j * nt] += dt * P[(int64_t)j * nt] / M->mass[j];
   elec_g<NS>(M, R, nt, n, W);
-  eigh_ns<double, NS>(W, U0, e1, U1, 50, 1e-34);
+  eigh_ns<double, NS>(W, U0, e1, U1, 100, 1e-34, false);
   half_kick_g<NS>(M, R, P, nt, n, U1, al, be, dt);
   const double w0 = (pick<double, NS>(e0, al) - pick<double, NS>(e0, be)) / M->hbar;
   const double w1 = (pick<double, NS>(e1, al) - pick<double, NS>(e1, be)) / M->hbar;
@@ -836,16 +835,18 @@ __global__ void __launch_bounds__(128, 1)
 }
 
 // ------------------------------------------------------- per-N_s launchers --
-// Instantiated explicitly, one N_s per translation unit (compiled in parallel).
+// Instantiated one N_s per translation unit; the FP64 sampling and step
+// kernels in their own units (kernels_nstate64_*.cu, compiled without FMA
+// contraction so that their arithmetic is the oracle's).
 template <int NS>
 struct NStateOps {
-  static void sample(const DevModel* dm, const SampleParams& sp, void* buf, int precision,
-                     cudaStream_t st) {
+  static void sample64(const DevModel* dm, const SampleParams& sp, void* buf, cudaStream_t st) {
     const int64_t nb = (sp.n_traj + 127) / 128;
-    if (precision == QCL_PREC_FP64)
-      k_sampleN_f64<NS><<<(unsigned)(nb > 0 ? nb : 1), 128, 0, st>>>(dm, sp, buf);
-    else
-      k_sampleN_f32<NS><<<(unsigned)(nb > 0 ? nb : 1), 128, 0, st>>>(dm, sp, buf);
+    k_sampleN_f64<NS><<<(unsigned)(nb > 0 ? nb : 1), 128, 0, st>>>(dm, sp, buf);
+  }
+  static void sample32(const DevModel* dm, const SampleParams& sp, void* buf, cudaStream_t st) {
+    const int64_t nb = (sp.n_traj + 127) / 128;
+    k_sampleN_f32<NS><<<(unsigned)(nb > 0 ? nb : 1), 128, 0, st>>>(dm, sp, buf);
   }
   static void step64(const DevModel* dm, void* buf, int64_t nt, int n, int64_t step0,
                      int64_t step, double dt, uint64_t seed, uint64_t traj_off, cudaStream_t st) {

@@ -79,29 +79,16 @@ def test_nstate_fp64_sample_matches_oracle(q, case):
 
 @pytest.mark.parametrize("case", [0, 1])
 def test_nstate_fp64_per_trajectory_parity(q, case):
-    """R, P, phi and U per trajectory to 1e-12.  The weight's hop factors contain
-    d = (U^T K U)_ab / (e_b - e_a): near an avoided crossing the gap amplifies
-    the ~1e-16 difference between two Jacobi eigensolvers' eigenvalues, so the
-    weight is held to 1e-12 except for walkers whose smallest adjacent gap along
-    the segment was small, where the bound scales with 1e-15 / gap."""
+    """R, P, phi, U and the weight per trajectory to 1e-12 over 50-step segments,
+    each restarted from the GPU's own checkpoint; identical decisions."""
     name, model, init, dt = _cases()[case]
     n, seg, steps = 2000, 50, 300
     run = _run(q, model, init, n, q.PREC_FP64, 6, steps // 10 + 1)
     om = oracle.OracleModel(model)
     worst = {}
     flips = 0
-    m_ok = 0
-    m_total = 0
     for s0 in range(0, steps, seg):
         ref = _to_oracle(om, run.state())
-        # smallest adjacent gap per walker along the segment (oracle, step by step)
-        probe = ref.copy()
-        gmin = np.full(n, np.inf)
-        for k in range(seg):
-            oracle.advance(om, probe, 6, 0, s0 + k, 1, dt)
-            for i in range(n):
-                e, _, _ = oracle.adiabatic(om, probe.R[i], probe.U[i])
-                gmin[i] = min(gmin[i], np.diff(e).min())
         oracle.advance(om, ref, 6, 0, s0, seg, dt)
         run.propagate(seg, dt, 10)
         g = run.state()
@@ -112,13 +99,9 @@ def test_nstate_fp64_per_trajectory_parity(q, case):
             worst[key] = max(worst.get(key, 0.0), float(err.max()))
         worst["U"] = max(worst.get("U", 0.0), float(np.abs(g["U"][same] - ref.U[same]).max()))
         merr = np.abs(g["m"][same] - ref.m[same]) / np.abs(ref.m[same])
-        bound = np.maximum(1e-12, 1e-15 / gmin[same])
-        assert np.all(merr <= bound), (merr / bound).max()
-        m_ok += int((merr <= 1e-12).sum())
-        m_total += int(same.sum())
-    assert flips <= 1
+        worst["m"] = max(worst.get("m", 0.0), float(merr.max()))
+    assert flips == 0
     assert max(worst.values()) < 1e-12, worst
-    assert m_ok >= 0.995 * m_total, (m_ok, m_total)
 
 
 @pytest.mark.parametrize("case", [0, 1])
