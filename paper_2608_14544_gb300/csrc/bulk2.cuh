@@ -84,9 +84,6 @@ __device__ __forceinline__ float column_sum32(const float* col) {
   return l1[0];
 }
 
-// 2^e as a double, -1022 <= e <= 1023
-__device__ __forceinline__ double pow2d(int e) { return __hiloint2double((e + 1023) << 20, 0); }
-
 // Shared-memory float4 load that the compiler may not hoist out of the step
 // loop (hoisting the per-mode coefficients would hold them all in registers).
 __device__ __forceinline__ float4 lds4(const float4* p) {
@@ -121,49 +118,68 @@ __device__ __forceinline__ void closed_form(Scal& z) {
 
 // Phase (trapezoid) and transition of one step, given the decomposition at
 // R_{n+1} (in z), r at R_n, and the coupling sums Av = sum a_j P_j/M_j,
-// Bv = sum b_j P_j/M_j at P_{n+1}.
+// Bv = sum b_j P_j/M_j at P_{n+1} (Bv = 0 when only a(R) depends on R).
+// `deg` counts steps whose coupling was set to zero at a degeneracy.  The
+// weight pair is left unnormalised (|lo| may grow past ulp(hi)/2 by a few ulp
+// per step); the step loop renormalises it at every fourth step.
+template <int KIND>
 __device__ __forceinline__ void phase_and_transition(Scal& z, float r_old, float Av, float Bv,
                                                      uint32_t word, const BulkParams& bp,
-                                                     bool active, unsigned int& n_deg) {
+                                                     unsigned int& deg) {
   // phase: dt/2 (w_ab(R_n) + w_ab(R_{n+1})), hbar w_ab = (sig_a - sig_b) r
   z.ph = df_add(z.ph, bp.hdt_hbar * (z.sa - z.sb) * (r_old + z.r));
   // coupling contracted with P/M: g = (a Bv - b Av) / (2 r^2)
   const bool degen = 2.0f * z.r < kDegTol32;
-  n_deg += (degen && active) ? 1u : 0u;
-  const float g = degen ? 0.0f : (z.A * Bv - z.B * Av) * (0.5f * z.ir * z.ir);
+  deg += degen ? 1u : 0u;
+  const float gn = (KIND == 1) ? (z.A * Bv - z.B * Av) : -(z.B * Av);
+  const float g = degen ? 0.0f : gn * (0.5f * z.ir * z.ir);
   // both events have |A_e| = dt |g|: p = min(kappa dt |g|, p_max) quantised to
-  // 24-bit thresholds, scaled down together in integers when 2T > Tmax
-  uint32_t T = min(__float2uint_rz(fminf(bp.kdt * fabsf(g) * kP24f, 33554432.0f)), bp.tmax);
-  if (2u * T > bp.tmax) T = bp.tmax >> 1;
+  // 24-bit thresholds T = floor(p 2^24); when 2T exceeds Tmax = floor(p_max 2^24)
+  // the integer rescale floor(T Tmax / 2T) gives floor(Tmax / 2), so
+  // T = min(floor(kappa dt |g| 2^24), floor(Tmax / 2)) (the conversion saturates)
+  const uint32_t T = min(__float2uint_rz((bp.kdt * kP24f) * fabsf(g)), bp.tmax >> 1);
   const uint32_t y = word >> 8;
   const bool hop1 = y < T;
-  const bool hop2 = !hop1 && (y < 2u * T);
+  const bool hop = y < 2u * T;
+  const bool hop2 = hop && !hop1;
   // weight factor: A_e / p_hat on a hop (A_1 = -sig_a dt g, A_2 = -sig_b dt g),
   // 1 / (1 - sum p_hat) otherwise; num / den as a compensated quotient
-  const float dtg = bp.dt * g * kP24f;
-  const float num = hop1 ? -z.sa * dtg : (hop2 ? -z.sb * dtg : kP24f);
-  const float den = __uint2float_rn((hop1 || hop2) ? T : 16777216u - 2u * T);
+  const float dtg = (bp.dt * kP24f) * g;
+  const float num = hop ? -(hop1 ? z.sa : z.sb) * dtg : kP24f;
+  const float den = __uint2float_rn(hop ? T : 16777216u - 2u * T);
   const float rd = rcp_approx(den);
   const float q0 = num * rd;
   const float q1 = __fmaf_rn(-q0, den, num) * rd;
-  z.m = df_mul(z.m, q0, q1);
+  const float p = z.m.hi * q0;
+  float e = __fmaf_rn(z.m.hi, q0, -p);
+  e = __fmaf_rn(z.m.hi, q1, e);
+  z.m = {p, __fmaf_rn(z.m.lo, q0, e)};
   if (!(fabsf(z.m.hi) <= 0x1p32f && fabsf(z.m.hi) >= 0x1p-32f)) renorm(z.m, z.mexp);
   z.sa = hop1 ? -z.sa : z.sa;
   z.sb = hop2 ? -z.sb : z.sb;
 }
 
+// Keeps the stored phase within about 2^10 rad, where the three-part
+// reduction below is exact; every holder of a walker calls it at the same
+// steps (the observations).
+__device__ __forceinline__ void phase_wrap(Scal& z) {
+  if (fabsf(z.ph.hi) > 1024.0f) {
+    const float kq = rintf(z.ph.hi * kInvTwoPi);
+    z.ph = df_add(z.ph, -kq * kTwoPi1);
+    z.ph = df_add(z.ph, -kq * kTwoPi2);
+    z.ph = df_add(z.ph, -kq * kTwoPi3);
+  }
+}
+
 // The walker's 16 observable contributions (diabatic rho_ij and adiabatic
-// rho_ab, real and imaginary) with weight mantissa `mm`; reduces the phase
-// into [-pi, pi] as a side effect.
-__device__ __forceinline__ void contributions(Scal& z, float mm, float (&v)[16]) {
+// rho_ab, real and imaginary) with weight mantissa `mm`.
+__device__ __forceinline__ void contributions(const Scal& z, float mm, float (&v)[16]) {
+  // phase reduced into [-pi, pi]: ph_hi - k C1 is exact (|k| < 2^10), the
+  // small terms are added once
   const float kq = rintf(z.ph.hi * kInvTwoPi);
-  z.ph = df_add(z.ph, -kq * kTwoPi1);
-  z.ph = df_add(z.ph, -kq * kTwoPi2);
-  z.ph = df_add(z.ph, -kq * kTwoPi3);
-  float sh, chh;
-  __sincosf(z.ph.hi, &sh, &chh);
-  const float cphi = __fmaf_rn(-z.ph.lo, sh, chh);
-  const float sphi = __fmaf_rn(z.ph.lo, chh, sh);
+  const float x = __fmaf_rn(-kq, kTwoPi1, z.ph.hi) + __fmaf_rn(-kq, kTwoPi2, z.ph.lo);
+  float sphi, cphi;
+  __sincosf(x, &sphi, &cphi);
   // eigenvector angle theta from (cos 2theta, sin 2theta), half-angle form
   // without cancellation: the larger of cos/sin is sqrt((1 + |cos2t|)/2)
   const float t = __fmaf_rn(0.5f, fabsf(z.c2), 0.5f);
@@ -191,6 +207,49 @@ __device__ __forceinline__ void contributions(Scal& z, float mm, float (&v)[16])
     v[8 + 2 * kk] = (kk == k) ? zr : 0.0f;
     v[9 + 2 * kk] = (kk == k) ? zi : 0.0f;
   }
+}
+
+// x 2^ex as a double, exactly (built from the bits for normal x and results in
+// the normal double range; zero, subnormal, non-finite or out-of-range values
+// go through ldexp).
+__device__ __forceinline__ double scaled_double(float x, int ex) {
+  const uint32_t u = __float_as_uint(x);
+  const int e8 = (int)((u >> 23) & 0xffu);
+  const int e11 = e8 + (1023 - 127) + ex;
+  if ((u << 1) == 0u) return __hiloint2double((int)(u & 0x80000000u), 0);
+  if (e8 != 0 && e8 != 255 && e11 > 0 && e11 < 2047)
+    return __hiloint2double((int)((u & 0x80000000u) | ((uint32_t)e11 << 20) | ((u & 0x7fffffu) >> 3)),
+                            (int)(u << 29));
+  return ldexp((double)x, ex);
+}
+
+// Observation by one warp of 32 walkers: the warp shares one power of two
+// (FP32 sums of scaled weights, the exponent restored exactly in FP64); each
+// walker's 16 contributions and their squares go to its padded row `row` of
+// shared memory, and lane q sums column q of the warp's 32 rows (from row0) by
+// a fixed pairwise tree (conflict-free: row stride 33 words).  Returns lane q's
+// column sum, scaled.
+__device__ __forceinline__ double observe_warp(Scal& z, bool active, float* obs_rows, int row,
+                                               int row0, int lane) {
+  renorm(z.m, z.mexp);
+  phase_wrap(z);
+  const bool live = active && z.m.hi != 0.0f;
+  int ew = live ? z.mexp : -(1 << 28);
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) ew = max(ew, __shfl_xor_sync(0xffffffffu, ew, off));
+  float v[16];
+  contributions(z, live ? (z.m.hi + z.m.lo) * pow2i(z.mexp - ew) : 0.0f, v);
+  float* r = &obs_rows[row * 33];
+#pragma unroll
+  for (int q = 0; q < 16; ++q) {
+    r[q] = v[q];
+    r[16 + q] = v[q] * v[q];
+  }
+  __syncwarp();
+  const float x = column_sum32(&obs_rows[row0 * 33 + lane]);
+  __syncwarp();
+  const int ex = (ew < -(1 << 27)) ? 0 : ((lane < 16) ? ew : 2 * ew);
+  return scaled_double(x, ex);
 }
 
 __device__ __forceinline__ uint32_t pick_word(const u4& wd, int widx) {
@@ -225,33 +284,62 @@ struct CoefLocal {
 // One 256-walker tile of the one-thread-per-walker kernel: load the tile's
 // walkers, advance them over steps [cs, ce) with their observations, store
 // them.  `cf` holds the per-mode coefficients (kernel parameters, or registers
-// in the packed kernel); all threads of the block call it together.
-template <int NPL, int KIND, typename CF>
+// in the packed kernel); all threads of the block call it together.  BLOCKS
+// selects the unrolled four-step route below (both routes give the same bits;
+// the unrolled one costs registers that many-mode and packed kernels lack).
+template <int NPL, int KIND, typename CF, bool BLOCKS>
 __device__ __forceinline__ void bulk2_tile(const BulkParams& bp, const CF& cf, W32& ws,
                                            double* __restrict__ part, int64_t tile, int& rb,
                                            unsigned int& n_deg, double (&red)[2][8][32],
                                            float* obs_rows) {
   const int64_t nt = bp.n_traj;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  {
-    const int64_t i = tile * kTile + threadIdx.x;
-    const bool active = i < nt;
-    const int64_t ii = active ? i : 0;
-    Walker<NPL> w;
+  const int64_t i = tile * kTile + threadIdx.x;
+  const bool active = i < nt;
+  const int64_t ii = active ? i : 0;
+  Walker<NPL> w;
 #pragma unroll
-    for (int j = 0; j < NPL; ++j) {
-      const bool on = active && j < bp.n;
-      w.R[j] = on ? ws.R[(int64_t)j * nt + ii] : 0.0f;
-      w.P[j] = on ? ws.P[(int64_t)j * nt + ii] : 0.0f;
-    }
-    Scal z;
-    z.m = {active ? ws.mh[ii] : 0.0f, active ? ws.ml[ii] : 0.0f};
-    z.mexp = active ? ws.me[ii] : 0;
-    z.ph = {active ? ws.ph[ii] : 0.0f, active ? ws.pl[ii] : 0.0f};
-    const uint32_t ab = active ? ws.ab[ii] : 0u;
-    z.sa = sgn(ab & 0xff);
-    z.sb = sgn((ab >> 8) & 0xff);
-    const uint64_t traj = bp.traj_offset + (uint64_t)ii;
+  for (int j = 0; j < NPL; ++j) {
+    const bool on = active && j < bp.n;
+    w.R[j] = on ? ws.R[(int64_t)j * nt + ii] : 0.0f;
+    w.P[j] = on ? ws.P[(int64_t)j * nt + ii] : 0.0f;
+  }
+  Scal z;
+  z.m = {active ? ws.mh[ii] : 0.0f, active ? ws.ml[ii] : 0.0f};
+  z.mexp = active ? ws.me[ii] : 0;
+  z.ph = {active ? ws.ph[ii] : 0.0f, active ? ws.pl[ii] : 0.0f};
+  const uint32_t ab = active ? ws.ab[ii] : 0u;
+  z.sa = sgn(ab & 0xff);
+  z.sb = sgn((ab >> 8) & 0xff);
+  const uint64_t traj = bp.traj_offset + (uint64_t)ii;
+  z.A = bp.a0;
+  z.B = bp.b0;
+#pragma unroll
+  for (int j = 0; j < NPL; ++j) {
+    z.A = __fmaf_rn(cf.a[j], w.R[j], z.A);
+    if (KIND == 1) z.B = __fmaf_rn(cf.b[j], w.R[j], z.B);
+  }
+  closed_form(z);
+  unsigned int deg = 0;
+
+  // observation into slot `slot` of the tile partials (8 warps, then the
+  // tile's fixed FP64 tree)
+  auto observe = [&](int slot) {
+    red[rb][warp][lane] = observe_warp(z, active, obs_rows, threadIdx.x, warp * 32, lane);
+    __syncthreads();
+    if (threadIdx.x < 32)
+      part[((int64_t)slot * bp.n_tiles + tile) * 32 + threadIdx.x] =
+          tile_tree8(&red[rb][0][0], 32, threadIdx.x);
+    rb ^= 1;
+  };
+
+  // one velocity-Verlet step with its phase and transition (hop word `word`)
+  auto step = [&](uint32_t word) {
+    const float hsab = bp.hdt * 0.5f * (z.sa + z.sb);  // dt/2 (sig_a + sig_b)/2
+    kick<NPL, KIND, CF>(w, cf, hsab * z.c2, hsab * z.s2);  // first half kick at R_n
+#pragma unroll
+    for (int j = 0; j < NPL; ++j) w.R[j] = __fmaf_rn(cf.dtm[j], w.P[j], w.R[j]);  // drift
+    const float r_old = z.r;
     z.A = bp.a0;
     z.B = bp.b0;
 #pragma unroll
@@ -260,97 +348,74 @@ __device__ __forceinline__ void bulk2_tile(const BulkParams& bp, const CF& cf, W
       if (KIND == 1) z.B = __fmaf_rn(cf.b[j], w.R[j], z.B);
     }
     closed_form(z);
+    kick<NPL, KIND, CF>(w, cf, hsab * z.c2, hsab * z.s2);  // second half kick at R_{n+1}
+    float Av = 0.0f, Bv = 0.0f;
+#pragma unroll
+    for (int j = 0; j < NPL; ++j) {
+      Av = __fmaf_rn(cf.am[j], w.P[j], Av);
+      if (KIND == 1) Bv = __fmaf_rn(cf.bm[j], w.P[j], Bv);
+    }
+    phase_and_transition<KIND>(z, r_old, Av, Bv, word, bp, deg);
+  };
 
-    // observation into slot `slot` of the tile partials: the warp's 32 walkers
-    // share one power of two (FP32 sums of scaled weights, the exponent restored
-    // exactly in FP64); each walker's 16 contributions and their squares go to
-    // its padded row of shared memory and lane q sums column q of its warp's 32
-    // rows by a fixed pairwise tree (conflict-free: row stride 33 words)
-    auto observe = [&](int slot) {
-      renorm(z.m, z.mexp);
-      const bool live = active && z.m.hi != 0.0f;
-      int ew = live ? z.mexp : -(1 << 28);
-#pragma unroll
-      for (int off = 16; off > 0; off >>= 1) ew = max(ew, __shfl_xor_sync(0xffffffffu, ew, off));
-      float v[16];
-      contributions(z, live ? z.m.hi * pow2i(z.mexp - ew) : 0.0f, v);
-      float* row = &obs_rows[threadIdx.x * 33];
-#pragma unroll
-      for (int q = 0; q < 16; ++q) {
-        row[q] = v[q];
-        row[16 + q] = v[q] * v[q];
-      }
-      __syncwarp();
-      const float x = column_sum32(&obs_rows[(warp * 32) * 33 + lane]);
-      __syncwarp();
-      const int ex = (ew < -(1 << 27)) ? 0 : ((lane < 16) ? ew : 2 * ew);
-      const double xd = (double)x;
-      red[rb][warp][lane] = (ex >= -1022 && ex <= 1023) ? xd * pow2d(ex) : ldexp(xd, ex);
-      __syncthreads();
-      if (threadIdx.x < 32)
-        part[((int64_t)slot * bp.n_tiles + tile) * 32 + threadIdx.x] =
-            tile_tree8(&red[rb][0][0], 32, threadIdx.x);
-      rb ^= 1;
-    };
-
-    int slot = bp.obs_first;
-    if (bp.obs_first) observe(0);
-    int to_out = bp.to_out0;
-    uint32_t blk = bp.blk0;
-    int widx = bp.widx0;
-    u4 wd = philox_draw(bp.seed, blk, traj, kPurposeHop);
-    for (int it = 0; it < bp.len; ++it) {
-      const uint32_t word = pick_word(wd, widx);
-      const float hsab = bp.hdt * 0.5f * (z.sa + z.sb);  // dt/2 (sig_a + sig_b)/2
-      kick<NPL, KIND, CF>(w, cf, hsab * z.c2, hsab * z.s2);  // first half kick at R_n
-#pragma unroll
-      for (int j = 0; j < NPL; ++j) w.R[j] = __fmaf_rn(cf.dtm[j], w.P[j], w.R[j]);  // drift
-      const float r_old = z.r;
-      z.A = bp.a0;
-      z.B = bp.b0;
-#pragma unroll
-      for (int j = 0; j < NPL; ++j) {
-        z.A = __fmaf_rn(cf.a[j], w.R[j], z.A);
-        if (KIND == 1) z.B = __fmaf_rn(cf.b[j], w.R[j], z.B);
-      }
-      closed_form(z);
-      kick<NPL, KIND, CF>(w, cf, hsab * z.c2, hsab * z.s2);  // second half kick at R_{n+1}
-      float Av = 0.0f, Bv = 0.0f;
-#pragma unroll
-      for (int j = 0; j < NPL; ++j) {
-        Av = __fmaf_rn(cf.am[j], w.P[j], Av);
-        if (KIND == 1) Bv = __fmaf_rn(cf.bm[j], w.P[j], Bv);
-      }
-      phase_and_transition(z, r_old, Av, Bv, word, bp, active, n_deg);
+  // Steps are grouped by Philox block (four steps share one draw).  A whole
+  // block with no output before its last step runs unrolled with its words in
+  // fixed registers; other steps (a chunk's ragged ends, blocks with an output
+  // inside) run one at a time.  The weight pair is renormalised at the end of
+  // every block, i.e. at the same absolute steps on both routes.
+  int slot = bp.obs_first;
+  if (bp.obs_first) observe(0);
+  int to_out = bp.to_out0;
+  uint32_t blk = bp.blk0;
+  int widx = bp.widx0;
+  u4 wd = philox_draw(bp.seed, blk, traj, kPurposeHop);
+  int it = 0;
+  while (it < bp.len) {
+    if (BLOCKS && widx == 0 && bp.len - it >= 4 && to_out >= 4) {
+      step(wd.x);
+      step(wd.y);
+      step(wd.z);
+      step(wd.w);
+      z.m = fast_two_sum(z.m.hi, z.m.lo);
+      it += 4;
+      to_out -= 4;
+      ++blk;
+      if (it < bp.len) wd = philox_draw(bp.seed, blk, traj, kPurposeHop);
+    } else {
+      step(pick_word(wd, widx));
+      ++it;
+      --to_out;
       if (++widx == 4) {
         widx = 0;
+        z.m = fast_two_sum(z.m.hi, z.m.lo);
         ++blk;
-        if (it + 1 < bp.len) wd = philox_draw(bp.seed, blk, traj, kPurposeHop);
-      }
-      if (--to_out == 0) {
-        observe(slot++);
-        to_out = bp.stride;
+        if (it < bp.len) wd = philox_draw(bp.seed, blk, traj, kPurposeHop);
       }
     }
-    if (active) {
+    if (to_out == 0) {
+      observe(slot++);
+      to_out = bp.stride;
+    }
+  }
+  if (active) {
+    n_deg += deg;
 #pragma unroll
-      for (int j = 0; j < NPL; ++j)
-        if (j < bp.n) {
-          ws.R[(int64_t)j * nt + i] = w.R[j];
-          ws.P[(int64_t)j * nt + i] = w.P[j];
-        }
-      ws.mh[i] = z.m.hi;
-      ws.ml[i] = z.m.lo;
-      ws.me[i] = z.mexp;
-      ws.ph[i] = z.ph.hi;
-      ws.pl[i] = z.ph.lo;
-      ws.ab[i] = (uint16_t)((z.sa > 0.0f ? 1 : 0) | ((z.sb > 0.0f ? 1 : 0) << 8));
-      if (!isfinite(z.m.hi) || !isfinite(z.ph.hi)) {
-        atomicAdd(&ws.hdr->n_nonfinite, 1ull);
-        atomicOr(&ws.hdr->flags, QCL_FLAG_NONFINITE);
+    for (int j = 0; j < NPL; ++j)
+      if (j < bp.n) {
+        ws.R[(int64_t)j * nt + i] = w.R[j];
+        ws.P[(int64_t)j * nt + i] = w.P[j];
       }
+    ws.mh[i] = z.m.hi;
+    ws.ml[i] = z.m.lo;
+    ws.me[i] = z.mexp;
+    ws.ph[i] = z.ph.hi;
+    ws.pl[i] = z.ph.lo;
+    ws.ab[i] = (uint16_t)((z.sa > 0.0f ? 1 : 0) | ((z.sb > 0.0f ? 1 : 0) << 8));
+    if (!isfinite(z.m.hi) || !isfinite(z.ph.hi)) {
+      atomicAdd(&ws.hdr->n_nonfinite, 1ull);
+      atomicOr(&ws.hdr->flags, QCL_FLAG_NONFINITE);
     }
-    }
+  }
 }
 
 }  // namespace qcl

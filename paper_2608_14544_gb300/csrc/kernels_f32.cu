@@ -120,7 +120,7 @@ __global__ void __launch_bounds__(256, 3)
   unsigned int n_deg = 0;
   int rb = 0;
   for (int64_t tile = blockIdx.x; tile < bp.n_tiles; tile += gridDim.x)
-    bulk2_tile<NPL, KIND, Coef2>(bp, cf, ws, part, tile, rb, n_deg, red, obs_rows);
+    bulk2_tile<NPL, KIND, Coef2, (NPL <= 12)>(bp, cf, ws, part, tile, rb, n_deg, red, obs_rows);
   if (n_deg) {
     atomicAdd(&ws.hdr->n_degenerate, (unsigned long long)n_deg);
     atomicOr(&ws.hdr->flags, QCL_FLAG_DEGENERATE);
@@ -175,6 +175,7 @@ __device__ __forceinline__ void split_tiles(const BulkParams& bp, const Coef2& c
     z.sa = sgn(ab & 0xff);
     z.sb = sgn((ab >> 8) & 0xff);
     const uint64_t traj = bp.traj_offset + (uint64_t)ii;
+    unsigned int deg = 0;
 
     // sum over the L roles of per-role partials, in role order
     auto exchange = [&](float (*x)[BW][2], float pa, float pb, float& A, float& B) {
@@ -206,29 +207,11 @@ __device__ __forceinline__ void split_tiles(const BulkParams& bp, const Coef2& c
     closed_form(z);
 
     auto observe = [&](int slot) {
-      renorm(z.m, z.mexp);
       if (ROLE == 0) {
-        const bool live = active && z.m.hi != 0.0f;
-        int ew = live ? z.mexp : -(1 << 28);
-#pragma unroll
-        for (int off = 16; off > 0; off >>= 1) ew = max(ew, __shfl_xor_sync(0xffffffffu, ew, off));
-        float v[16];
-        contributions(z, live ? z.m.hi * pow2i(z.mexp - ew) : 0.0f, v);
-        float* row = &obs_rows[wslot * 33];
-#pragma unroll
-        for (int q = 0; q < 16; ++q) {
-          row[q] = v[q];
-          row[16 + q] = v[q] * v[q];
-        }
-        __syncwarp();
-        const float x = column_sum32(&obs_rows[(grp * 32) * 33 + lane]);
-        __syncwarp();
-        const int ex = (ew < -(1 << 27)) ? 0 : ((lane < 16) ? ew : 2 * ew);
-        const double xd = (double)x;
-        red[rb][grp][lane] = (ex >= -1022 && ex <= 1023) ? xd * pow2d(ex) : ldexp(xd, ex);
-      } else {
-        float v[16];
-        contributions(z, 0.0f, v);  // keeps the phase reduction identical on every role
+        red[rb][grp][lane] = observe_warp(z, active, obs_rows, wslot, grp * 32, lane);
+      } else {  // the same weight and phase bookkeeping on every role
+        renorm(z.m, z.mexp);
+        phase_wrap(z);
       }
       __syncthreads();
       if (threadIdx.x < 32) {
@@ -286,9 +269,10 @@ __device__ __forceinline__ void split_tiles(const BulkParams& bp, const Coef2& c
       }
       float Av, Bv;
       exchange(xv, av, bv, Av, Bv);
-      phase_and_transition(z, r_old, Av, Bv, word, bp, active, n_deg);
-      if (++widx == 4) {
+      phase_and_transition<KIND>(z, r_old, Av, Bv, word, bp, deg);
+      if (++widx == 4) {  // weight pair renormalised at the end of every Philox block
         widx = 0;
+        z.m = fast_two_sum(z.m.hi, z.m.lo);
         ++blk;
         if (it + 1 < bp.len) wd = philox_draw(bp.seed, blk, traj, kPurposeHop);
       }
@@ -298,6 +282,7 @@ __device__ __forceinline__ void split_tiles(const BulkParams& bp, const Coef2& c
       }
     }
     if (active) {
+      n_deg += deg;
 #pragma unroll
       for (int t = 0; t < NPL; ++t)
         if (OFF + t < bp.n) {

@@ -41,7 +41,7 @@ __global__ void __launch_bounds__(256, 3) k_bulk2_packed(const PackedTable* __re
       continue;
     }
     unsigned int n_deg = 0;
-    bulk2_tile<NPL, KIND, CoefLocal<NPL>>(bp, c, ws, R.part, tile, rb, n_deg, red, obs_rows);
+    bulk2_tile<NPL, KIND, CoefLocal<NPL>, false>(bp, c, ws, R.part, tile, rb, n_deg, red, obs_rows);
     if (n_deg) {
       atomicAdd(&ws.hdr->n_degenerate, (unsigned long long)n_deg);
       atomicOr(&ws.hdr->flags, QCL_FLAG_DEGENERATE);
