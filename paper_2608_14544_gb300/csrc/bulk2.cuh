@@ -3,6 +3,8 @@
 // multi-request kernel of the server (packed.cu): walker views, compensated
 // weight/phase helpers, the per-step scalar algebra and the tile body.
 #pragma once
+#include <type_traits>
+
 #include "kernels.h"
 #include "reduce.cuh"
 
@@ -71,12 +73,17 @@ __device__ __forceinline__ float rcp_approx(float x) {
   return r;
 }
 
-// Sum of 32 floats at stride 33 (one column of a warp's rows) by a fixed
+// Row stride (floats) of the observation rows in shared memory: 16-byte rows
+// that a warp writes with 128-bit stores and reads by column, both without
+// bank conflicts (8 threads of a quarter warp start 4 banks apart).
+constexpr int kObsRow = 36;
+
+// Sum of 32 floats at stride kObsRow (one column of a warp's rows) by a fixed
 // pairwise tree: ((x0 + x1) + (x2 + x3)) + ...
 __device__ __forceinline__ float column_sum32(const float* col) {
   float l1[16];
 #pragma unroll
-  for (int t = 0; t < 16; ++t) l1[t] = col[(2 * t) * 33] + col[(2 * t + 1) * 33];
+  for (int t = 0; t < 16; ++t) l1[t] = col[(2 * t) * kObsRow] + col[(2 * t + 1) * kObsRow];
 #pragma unroll
   for (int w = 8; w >= 1; w >>= 1)
 #pragma unroll
@@ -120,14 +127,18 @@ __device__ __forceinline__ void closed_form(Scal& z) {
 // R_{n+1} (in z), r at R_n, and the coupling sums Av = sum a_j P_j/M_j,
 // Bv = sum b_j P_j/M_j at P_{n+1} (Bv = 0 when only a(R) depends on R).
 // `deg` counts steps whose coupling was set to zero at a degeneracy.  The
-// weight pair is left unnormalised (|lo| may grow past ulp(hi)/2 by a few ulp
-// per step); the step loop renormalises it at every fourth step.
+// weight and phase pairs are left unnormalised (|lo| may grow past ulp(hi)/2
+// by about an ulp per step); the step loop renormalises both at every fourth
+// step (block_end).
 template <int KIND>
 __device__ __forceinline__ void phase_and_transition(Scal& z, float r_old, float Av, float Bv,
                                                      uint32_t word, const BulkParams& bp,
                                                      unsigned int& deg) {
-  // phase: dt/2 (w_ab(R_n) + w_ab(R_{n+1})), hbar w_ab = (sig_a - sig_b) r
-  z.ph = df_add(z.ph, bp.hdt_hbar * (z.sa - z.sb) * (r_old + z.r));
+  // phase: dt/2 (w_ab(R_n) + w_ab(R_{n+1})), hbar w_ab = (sig_a - sig_b) r;
+  // the rounding error of each addition is collected in lo (renormalised with
+  // the weight at the end of the Philox block)
+  const f2 ps = two_sum(z.ph.hi, bp.hdt_hbar * (z.sa - z.sb) * (r_old + z.r));
+  z.ph = {ps.hi, z.ph.lo + ps.lo};
   // coupling contracted with P/M: g = (a Bv - b Av) / (2 r^2)
   const bool degen = 2.0f * z.r < kDegTol32;
   deg += degen ? 1u : 0u;
@@ -157,6 +168,13 @@ __device__ __forceinline__ void phase_and_transition(Scal& z, float r_old, float
   if (!(fabsf(z.m.hi) <= 0x1p32f && fabsf(z.m.hi) >= 0x1p-32f)) renorm(z.m, z.mexp);
   z.sa = hop1 ? -z.sa : z.sa;
   z.sb = hop2 ? -z.sb : z.sb;
+}
+
+// Renormalises the weight and phase pairs; called at the end of every Philox
+// block (absolute steps 4k + 3), whatever the chunking.
+__device__ __forceinline__ void block_end(Scal& z) {
+  z.m = fast_two_sum(z.m.hi, z.m.lo);
+  z.ph = two_sum(z.ph.hi, z.ph.lo);
 }
 
 // Keeps the stored phase within about 2^10 rad, where the three-part
@@ -225,28 +243,26 @@ __device__ __forceinline__ double scaled_double(float x, int ex) {
 
 // Observation by one warp of 32 walkers: the warp shares one power of two
 // (FP32 sums of scaled weights, the exponent restored exactly in FP64); each
-// walker's 16 contributions and their squares go to its padded row `row` of
-// shared memory, and lane q sums column q of the warp's 32 rows (from row0) by
-// a fixed pairwise tree (conflict-free: row stride 33 words).  Returns lane q's
-// column sum, scaled.
+// walker's 16 contributions and their squares go to its row `row` of shared
+// memory, and lane q sums column q of the warp's 32 rows (from row0) by a fixed
+// pairwise tree.  Returns lane q's column sum, scaled.
 __device__ __forceinline__ double observe_warp(Scal& z, bool active, float* obs_rows, int row,
                                                int row0, int lane) {
   renorm(z.m, z.mexp);
   phase_wrap(z);
   const bool live = active && z.m.hi != 0.0f;
-  int ew = live ? z.mexp : -(1 << 28);
-#pragma unroll
-  for (int off = 16; off > 0; off >>= 1) ew = max(ew, __shfl_xor_sync(0xffffffffu, ew, off));
+  const int ew = __reduce_max_sync(0xffffffffu, live ? z.mexp : -(1 << 28));
   float v[16];
   contributions(z, live ? (z.m.hi + z.m.lo) * pow2i(z.mexp - ew) : 0.0f, v);
-  float* r = &obs_rows[row * 33];
+  float4* r = reinterpret_cast<float4*>(&obs_rows[row * kObsRow]);
 #pragma unroll
-  for (int q = 0; q < 16; ++q) {
-    r[q] = v[q];
-    r[16 + q] = v[q] * v[q];
+  for (int q = 0; q < 4; ++q) {
+    r[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+    r[4 + q] = make_float4(v[4 * q] * v[4 * q], v[4 * q + 1] * v[4 * q + 1],
+                           v[4 * q + 2] * v[4 * q + 2], v[4 * q + 3] * v[4 * q + 3]);
   }
   __syncwarp();
-  const float x = column_sum32(&obs_rows[row0 * 33 + lane]);
+  const float x = column_sum32(&obs_rows[row0 * kObsRow + lane]);
   __syncwarp();
   const int ex = (ew < -(1 << 27)) ? 0 : ((lane < 16) ? ew : 2 * ew);
   return scaled_double(x, ex);
@@ -255,6 +271,16 @@ __device__ __forceinline__ double observe_warp(Scal& z, bool active, float* obs_
 __device__ __forceinline__ uint32_t pick_word(const u4& wd, int widx) {
   return (widx & 2) ? ((widx & 1) ? wd.w : wd.z) : ((widx & 1) ? wd.y : wd.x);
 }
+
+// The hop stream through the whole Philox function (fewer live registers
+// than PhiloxStream, the same words).
+struct PlainStream {
+  uint64_t seed, traj;
+  __device__ __forceinline__ PlainStream(uint64_t s, uint64_t t, uint32_t) : seed(s), traj(t) {}
+  __device__ __forceinline__ u4 draw(uint32_t n) const {
+    return philox_draw(seed, n, traj, kPurposeHop);
+  }
+};
 
 template <int NPL>
 struct Walker {
@@ -284,10 +310,12 @@ struct CoefLocal {
 // One 256-walker tile of the one-thread-per-walker kernel: load the tile's
 // walkers, advance them over steps [cs, ce) with their observations, store
 // them.  `cf` holds the per-mode coefficients (kernel parameters, or registers
-// in the packed kernel); all threads of the block call it together.  BLOCKS
-// selects the unrolled four-step route below (both routes give the same bits;
-// the unrolled one costs registers that many-mode and packed kernels lack).
-template <int NPL, int KIND, typename CF, bool BLOCKS>
+// in the packed kernel); all threads of the block call it together.  LEAN
+// selects the register-lean form for kernels short of registers (many modes,
+// coefficients in registers): steps one at a time and the whole Philox
+// function per draw, instead of the unrolled four-step blocks below and the
+// precomputed stream.  Both forms give the same bits.
+template <int NPL, int KIND, typename CF, bool LEAN>
 __device__ __forceinline__ void bulk2_tile(const BulkParams& bp, const CF& cf, W32& ws,
                                            double* __restrict__ part, int64_t tile, int& rb,
                                            unsigned int& n_deg, double (&red)[2][8][32],
@@ -361,35 +389,36 @@ __device__ __forceinline__ void bulk2_tile(const BulkParams& bp, const CF& cf, W
   // Steps are grouped by Philox block (four steps share one draw).  A whole
   // block with no output before its last step runs unrolled with its words in
   // fixed registers; other steps (a chunk's ragged ends, blocks with an output
-  // inside) run one at a time.  The weight pair is renormalised at the end of
-  // every block, i.e. at the same absolute steps on both routes.
+  // inside) run one at a time.  The weight and phase pairs are renormalised at
+  // the end of every block, i.e. at the same absolute steps on both routes.
   int slot = bp.obs_first;
   if (bp.obs_first) observe(0);
   int to_out = bp.to_out0;
   uint32_t blk = bp.blk0;
   int widx = bp.widx0;
-  u4 wd = philox_draw(bp.seed, blk, traj, kPurposeHop);
+  const std::conditional_t<LEAN, PlainStream, PhiloxStream> rng(bp.seed, traj, kPurposeHop);
+  u4 wd = rng.draw(blk);
   int it = 0;
   while (it < bp.len) {
-    if (BLOCKS && widx == 0 && bp.len - it >= 4 && to_out >= 4) {
+    if (!LEAN && widx == 0 && bp.len - it >= 4 && to_out >= 4) {
       step(wd.x);
       step(wd.y);
       step(wd.z);
       step(wd.w);
-      z.m = fast_two_sum(z.m.hi, z.m.lo);
+      block_end(z);
       it += 4;
       to_out -= 4;
       ++blk;
-      if (it < bp.len) wd = philox_draw(bp.seed, blk, traj, kPurposeHop);
+      if (it < bp.len) wd = rng.draw(blk);
     } else {
       step(pick_word(wd, widx));
       ++it;
       --to_out;
       if (++widx == 4) {
         widx = 0;
-        z.m = fast_two_sum(z.m.hi, z.m.lo);
+        block_end(z);
         ++blk;
-        if (it < bp.len) wd = philox_draw(bp.seed, blk, traj, kPurposeHop);
+        if (it < bp.len) wd = rng.draw(blk);
       }
     }
     if (to_out == 0) {

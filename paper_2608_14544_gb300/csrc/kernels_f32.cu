@@ -111,7 +111,7 @@ template <int NPL, int KIND>
 __global__ void __launch_bounds__(256, 3)
     k_bulk2(const BulkParams bp, const Coef2 cf, void* buf, double* __restrict__ part) {
   __shared__ double red[2][8][32];      // double-buffered group partials
-  __shared__ float obs_rows[256 * 33];  // per-walker contributions, padded rows
+  __shared__ __align__(16) float obs_rows[256 * kObsRow];  // per-walker contributions
   W32 ws = view32(buf, bp.n_traj, 2, bp.n);
   if (ws.hdr->step != bp.step0) {
     if (blockIdx.x == 0 && threadIdx.x == 0) atomicOr(&ws.hdr->flags, QCL_FLAG_STEP_MISMATCH);
@@ -120,7 +120,7 @@ __global__ void __launch_bounds__(256, 3)
   unsigned int n_deg = 0;
   int rb = 0;
   for (int64_t tile = blockIdx.x; tile < bp.n_tiles; tile += gridDim.x)
-    bulk2_tile<NPL, KIND, Coef2, (NPL <= 12)>(bp, cf, ws, part, tile, rb, n_deg, red, obs_rows);
+    bulk2_tile<NPL, KIND, Coef2, (NPL > 12)>(bp, cf, ws, part, tile, rb, n_deg, red, obs_rows);
   if (n_deg) {
     atomicAdd(&ws.hdr->n_degenerate, (unsigned long long)n_deg);
     atomicOr(&ws.hdr->flags, QCL_FLAG_DEGENERATE);
@@ -230,7 +230,8 @@ __device__ __forceinline__ void split_tiles(const BulkParams& bp, const Coef2& c
     int to_out = bp.to_out0;
     uint32_t blk = bp.blk0;
     int widx = bp.widx0;
-    u4 wd = philox_draw(bp.seed, blk, traj, kPurposeHop);
+    const PhiloxStream rng(bp.seed, traj, kPurposeHop);
+    u4 wd = rng.draw(blk);
     for (int it = 0; it < bp.len; ++it) {
       const uint32_t word = pick_word(wd, widx);
       const float hsab = bp.hdt * 0.5f * (z.sa + z.sb);
@@ -270,11 +271,11 @@ __device__ __forceinline__ void split_tiles(const BulkParams& bp, const Coef2& c
       float Av, Bv;
       exchange(xv, av, bv, Av, Bv);
       phase_and_transition<KIND>(z, r_old, Av, Bv, word, bp, deg);
-      if (++widx == 4) {  // weight pair renormalised at the end of every Philox block
+      if (++widx == 4) {  // pairs renormalised at the end of every Philox block
         widx = 0;
-        z.m = fast_two_sum(z.m.hi, z.m.lo);
+        block_end(z);
         ++blk;
-        if (it + 1 < bp.len) wd = philox_draw(bp.seed, blk, traj, kPurposeHop);
+        if (it + 1 < bp.len) wd = rng.draw(blk);
       }
       if (--to_out == 0) {
         observe(slot++);
@@ -316,7 +317,7 @@ __global__ void __launch_bounds__(256, MINB)
   __shared__ float xa[L][BW][2];
   __shared__ float xv[L][BW][2];
   __shared__ double red[2][8][32];
-  __shared__ float obs_rows[BW * 33];
+  __shared__ __align__(16) float obs_rows[BW * kObsRow];
   W32 ws = view32(buf, bp.n_traj, 2, bp.n);
   if (ws.hdr->step != bp.step0) {
     if (blockIdx.x == 0 && threadIdx.x == 0) atomicOr(&ws.hdr->flags, QCL_FLAG_STEP_MISMATCH);

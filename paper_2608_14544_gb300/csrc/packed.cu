@@ -10,7 +10,7 @@ namespace qcl {
 template <int NPL, int KIND>
 __global__ void __launch_bounds__(256, 3) k_bulk2_packed(const PackedTable* __restrict__ tab) {
   __shared__ double red[2][8][32];
-  __shared__ float obs_rows[256 * 33];
+  __shared__ __align__(16) float obs_rows[256 * kObsRow];
   const int64_t n_work = tab->n_work;
   const int n_req = tab->n_req;
   int rb = 0;
@@ -41,7 +41,7 @@ __global__ void __launch_bounds__(256, 3) k_bulk2_packed(const PackedTable* __re
       continue;
     }
     unsigned int n_deg = 0;
-    bulk2_tile<NPL, KIND, CoefLocal<NPL>, false>(bp, c, ws, R.part, tile, rb, n_deg, red, obs_rows);
+    bulk2_tile<NPL, KIND, CoefLocal<NPL>, true>(bp, c, ws, R.part, tile, rb, n_deg, red, obs_rows);
     if (n_deg) {
       atomicAdd(&ws.hdr->n_degenerate, (unsigned long long)n_deg);
       atomicOr(&ws.hdr->flags, QCL_FLAG_DEGENERATE);

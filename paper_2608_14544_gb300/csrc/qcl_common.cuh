@@ -51,6 +51,64 @@ __device__ __forceinline__ u4 philox_draw(uint64_t seed, uint32_t c0, uint64_t t
                 (uint32_t)(seed >> 32));
 }
 
+__host__ __device__ __forceinline__ uint32_t mulhi32(uint32_t a, uint32_t b) {
+#ifdef __CUDA_ARCH__
+  return __umulhi(a, b);
+#else
+  return (uint32_t)(((uint64_t)a * b) >> 32);
+#endif
+}
+
+// The Philox4x32-10 stream of one walker and purpose: counter (n, traj_lo,
+// traj_hi, purpose) with only the block number n varying between draws.  The
+// terms of the first two rounds that involve the fixed counter words alone are
+// computed once; with n the same on every thread (a block-uniform step), what
+// is left of those two rounds is uniform work and two XORs per walker.
+// draw(n) returns the same words as philox(n, traj_lo, traj_hi, purpose, key).
+struct PhiloxStream {
+  uint32_t e, f, d;  // per-walker words entering round 2 (see draw)
+  uint32_t g;        // purpose ^ k1
+  uint32_t k0, k1;
+
+  __host__ __device__ __forceinline__ PhiloxStream(uint64_t seed, uint64_t traj, uint32_t purpose) {
+    k0 = (uint32_t)seed;
+    k1 = (uint32_t)(seed >> 32);
+    const uint32_t tl = (uint32_t)traj, th = (uint32_t)(traj >> 32);
+    // round 0, the product of the fixed word traj_hi
+    const uint32_t a = mulhi32(0xCD9E8D57u, th) ^ tl ^ k0;  // new word 0
+    const uint32_t b = 0xCD9E8D57u * th;                    // new word 1
+    // round 1, the product of word 0 (fixed)
+    e = b ^ (k0 + 0x9E3779B9u);
+    f = mulhi32(0xD2511F53u, a) ^ (k1 + 0xBB67AE85u);
+    d = 0xD2511F53u * a;
+    g = purpose ^ k1;
+  }
+
+  __host__ __device__ __forceinline__ u4 draw(uint32_t n) const {
+    // round 0: the product of the block number
+    const uint32_t s2 = mulhi32(0xD2511F53u, n) ^ g;
+    const uint32_t s3 = 0xD2511F53u * n;
+    // round 1: the product of word 2
+    uint32_t c0 = mulhi32(0xCD9E8D57u, s2) ^ e;
+    uint32_t c1 = 0xCD9E8D57u * s2;
+    uint32_t c2 = s3 ^ f;
+    uint32_t c3 = d;
+    uint32_t q0 = k0 + 2u * 0x9E3779B9u, q1 = k1 + 2u * 0xBB67AE85u;
+#pragma unroll
+    for (int r = 2; r < 10; ++r) {
+      const uint32_t hi0 = mulhi32(0xD2511F53u, c0), lo0 = 0xD2511F53u * c0;
+      const uint32_t hi1 = mulhi32(0xCD9E8D57u, c2), lo1 = 0xCD9E8D57u * c2;
+      c0 = hi1 ^ c1 ^ q0;
+      c1 = lo1;
+      c2 = hi0 ^ c3 ^ q1;
+      c3 = lo0;
+      q0 += 0x9E3779B9u;
+      q1 += 0xBB67AE85u;
+    }
+    return {c0, c1, c2, c3};
+  }
+};
+
 __device__ __forceinline__ uint32_t word_of(const u4& w, int i) {
   return i == 0 ? w.x : (i == 1 ? w.y : (i == 2 ? w.z : w.w));
 }
