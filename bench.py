@@ -51,14 +51,28 @@ def flops_per_traj_step(model: dict) -> float:
     return per_mode * model["n_modes"] + 20.0
 
 
-def _profiled_traffic(kernel_src: str, summary: str):
-    """DRAM bytes per launch from the committed ncu summary, or None when the
-    kernel source has changed since the counters were taken."""
+def kernel_source_hash(paths) -> str:
+    """sha256 prefix over the kernel's source files (in the given order)."""
     import hashlib
 
+    h = hashlib.sha256()
+    for p in paths:
+        with open(p, "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+BULK2_SOURCES = [os.path.join(ROOT, "paper_2608_14544_gb300", "csrc", f)
+                 for f in ("kernels_f32.cu", "bulk2.cuh", "qcl_common.cuh", "reduce.cuh",
+                           "kernels.h")]
+
+
+def _profiled_traffic(kernel_srcs, summary: str):
+    """DRAM bytes per launch from the committed ncu summary, or None when the
+    kernel's sources have changed since the counters were taken."""
     try:
         txt = open(summary).read()
-        h = hashlib.sha256(open(kernel_src, "rb").read()).hexdigest()[:16]
+        h = kernel_source_hash(kernel_srcs)
     except OSError:
         return None
     vals = dict(ln.split(":", 1) for ln in txt.splitlines()
@@ -409,8 +423,7 @@ def run_ours(args):
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_tflops,
                      "unit": "TFLOP/s", "frac": (achieved / peak_tflops) if achieved else None,
                      "traffic": _profiled_traffic(
-                         os.path.join(ROOT, "paper_2608_14544_gb300", "csrc", "kernels_f32.cu"),
-                         os.path.join(ROOT, "profiles", "k_bulk2_sb3mode.md")),
+                         BULK2_SOURCES, os.path.join(ROOT, "profiles", "k_bulk2_sb3mode.md")),
                      "traffic_unit": "bytes per launch (ncu, small case scaled)",
                      "kernel": "k_bulk2 (persistent FP32-bulk walker kernel)",
                      "flops_per_traj_step": fl,
