@@ -46,8 +46,22 @@ class Model(C.Structure):
     _fields_ = [
         ("n_states", C.c_int32), ("n_modes", C.c_int32), ("hbar", C.c_double),
         ("mass", C.c_void_p), ("omega", C.c_void_p), ("E", C.c_void_p), ("K", C.c_void_p),
-        ("hop_scale", C.c_double), ("p_max", C.c_double),
+        ("hop_scale", C.c_double), ("p_max", C.c_double), ("repr", C.c_int32),
+        ("reserved", C.c_int32),
     ]
+
+
+REPR_ADIABATIC = 0
+REPR_DIABATIC = 1
+
+
+def _repr_code(m: dict) -> int:
+    r = m.get("repr", "adiabatic")
+    if r in ("adiabatic", REPR_ADIABATIC):
+        return REPR_ADIABATIC
+    if r in ("diabatic", REPR_DIABATIC):
+        return REPR_DIABATIC
+    raise ValueError(f"unknown representation {r!r}")
 
 
 class Init(C.Structure):
@@ -71,14 +85,16 @@ def _l():
             lib.orc_mean_force.argtypes = [vp, vp, vp, i32, i32, vp]
             lib.orc_events.argtypes = [vp, vp, vp, vp, i32, i32, d, vp, vp, vp, vp]
             lib.orc_events.restype = i32
+            lib.orc_events_dia.argtypes = [vp, vp, i32, i32, d, vp, vp, vp, vp, vp]
+            lib.orc_events_dia.restype = i32
             lib.orc_step_deterministic.argtypes = [vp, vp, vp, vp, i32, i32, vp, d]
-            lib.orc_sample.argtypes = [vp, vp, u64, u64, i64, vp, vp, vp, vp, vp, vp, vp]
+            lib.orc_sample.argtypes = [vp, vp, u64, u64, i64, vp, vp, vp, vp, vp, vp, vp, vp]
             lib.orc_sample.restype = i32
-            lib.orc_advance.argtypes = [vp, u64, u64, i64, vp, vp, vp, vp, vp, vp, vp, i64, i64,
-                                        d, vp]
+            lib.orc_advance.argtypes = [vp, u64, u64, i64, vp, vp, vp, vp, vp, vp, vp, vp, i64,
+                                        i64, d, vp]
             lib.orc_advance.restype = i32
-            lib.orc_contrib.argtypes = [vp, i64, vp, vp, vp, vp, vp, vp, vp]
-            lib.orc_observe.argtypes = [vp, i64, vp, vp, vp, vp, vp, vp, vp]
+            lib.orc_contrib.argtypes = [vp, i64, vp, vp, vp, vp, vp, vp, vp, vp]
+            lib.orc_observe.argtypes = [vp, i64, vp, vp, vp, vp, vp, vp, vp, vp]
             lib.orc_run.argtypes = [vp, vp, u64, u64, i64, d, i64, i64, vp, vp]
             lib.orc_run.restype = i32
             _lib = lib
@@ -106,8 +122,9 @@ class OracleModel:
         self.K = _f64(m["K"]).reshape(self.n * self.ns * self.ns)
         self.hop_scale = float(m.get("hop_scale", 1.0))
         self.p_max = float(m.get("p_max", 0.5))
+        self.repr = _repr_code(m)
         self.c = Model(self.ns, self.n, self.hbar, _ptr(self.mass), _ptr(self.omega),
-                       _ptr(self.E), _ptr(self.K), self.hop_scale, self.p_max)
+                       _ptr(self.E), _ptr(self.K), self.hop_scale, self.p_max, self.repr, 0)
 
     @property
     def ref(self):
@@ -177,6 +194,19 @@ def events(model: OracleModel, P, e, U, a, b, dt):
     return ta[:ne], tb[:ne], A[:ne], T[:ne]
 
 
+def events_dia(model: OracleModel, R, a, b, dt):
+    """Diabatic events: (target a, target b, real factor c, quarter turns, T)."""
+    ne_max = 2 * model.ns
+    ta = np.zeros(ne_max, dtype=np.int32)
+    tb = np.zeros(ne_max, dtype=np.int32)
+    c = np.zeros(ne_max)
+    dq = np.zeros(ne_max, dtype=np.int32)
+    T = np.zeros(ne_max, dtype=np.uint32)
+    ne = _l().orc_events_dia(model.ref, _ptr(_f64(R)), a, b, dt, _ptr(ta), _ptr(tb), _ptr(c),
+                             _ptr(dq), _ptr(T))
+    return ta[:ne], tb[:ne], c[:ne], dq[:ne], T[:ne]
+
+
 def step_deterministic(model: OracleModel, R, P, phi, a, b, U, dt):
     """Returns new (R, P, phi, U) after the deterministic part of one step."""
     R = _f64(R).copy()
@@ -199,6 +229,7 @@ class State:
         self.alpha = np.zeros(n_traj, dtype=np.int32)
         self.beta = np.zeros(n_traj, dtype=np.int32)
         self.U = np.zeros((n_traj, model.ns, model.ns))
+        self.q = np.zeros(n_traj, dtype=np.int32)  # quarter turns (diabatic representation)
 
     def copy(self):
         s = State.__new__(State)
@@ -208,7 +239,7 @@ class State:
 
     def args(self):
         return (_ptr(self.R), _ptr(self.P), _ptr(self.m), _ptr(self.phi), _ptr(self.alpha),
-                _ptr(self.beta), _ptr(self.U))
+                _ptr(self.beta), _ptr(self.U), _ptr(self.q))
 
 
 def sample(model: OracleModel, init: OracleInit, seed: int, traj_offset: int, n_traj: int):
@@ -230,14 +261,14 @@ def advance(model: OracleModel, st: State, seed: int, traj_offset: int, step0: i
 def contrib(model: OracleModel, st: State):
     q = np.zeros((st.n_traj, 4 * model.ns * model.ns))
     _l().orc_contrib(model.ref, st.n_traj, _ptr(st.R), _ptr(st.m), _ptr(st.phi),
-                     _ptr(st.alpha), _ptr(st.beta), _ptr(st.U), _ptr(q))
+                     _ptr(st.alpha), _ptr(st.beta), _ptr(st.U), _ptr(st.q), _ptr(q))
     return q
 
 
 def observe(model: OracleModel, st: State):
     row = np.zeros(8 * model.ns * model.ns)
     _l().orc_observe(model.ref, st.n_traj, _ptr(st.R), _ptr(st.m), _ptr(st.phi),
-                     _ptr(st.alpha), _ptr(st.beta), _ptr(st.U), _ptr(row))
+                     _ptr(st.alpha), _ptr(st.beta), _ptr(st.U), _ptr(st.q), _ptr(row))
     return row
 
 

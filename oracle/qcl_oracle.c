@@ -280,22 +280,122 @@ static int det_step(const orc_model* md, double* R, double* P, double* phi, int 
   return deg;
 }
 
+/* Diabatic representation: mean force of pair (a, b) from the diagonal of W,
+ * F_j = -k_j R_j - 1/2 (K_j,aa + K_j,bb). */
+static void dia_force(const orc_model* md, const double* R, int a, int b, double* F) {
+  int ns = md->n_states, nn = ns * ns;
+  for (int j = 0; j < md->n_modes; ++j) {
+    double k = md->mass[j] * md->omega[j] * md->omega[j];
+    const double* Kj = md->K + (size_t)j * nn;
+    F[j] = -k * R[j] - 0.5 * (Kj[a * ns + a] + Kj[b * ns + b]);
+  }
+}
+
+/* Diabatic deterministic step: velocity Verlet on the diagonal mean force and
+ * the trapezoid rule for the phase term, hbar w_ab = V_aa(R) - V_bb(R). */
+static void det_step_dia(const orc_model* md, double* R, double* P, double* phi, int a, int b,
+                         double dt) {
+  int n = md->n_modes, ns = md->n_states;
+  double W0[ORC_MAX_NS * ORC_MAX_NS], W1[ORC_MAX_NS * ORC_MAX_NS], F[ORC_MAX_N];
+  elec_matrix(md, R, W0);
+  dia_force(md, R, a, b, F);
+  for (int j = 0; j < n; ++j) P[j] += 0.5 * dt * F[j];
+  for (int j = 0; j < n; ++j) R[j] += dt * P[j] / md->mass[j];
+  elec_matrix(md, R, W1);
+  dia_force(md, R, a, b, F);
+  for (int j = 0; j < n; ++j) P[j] += 0.5 * dt * F[j];
+  double w0 = (W0[a * ns + a] - W0[b * ns + b]) / md->hbar;
+  double w1 = (W1[a * ns + a] - W1[b * ns + b]) / md->hbar;
+  *phi += 0.5 * dt * (w0 + w1);
+}
+
 void orc_step_deterministic(const orc_model* md, double* R, double* P, double* phi, int32_t a,
                             int32_t b, double* U, double dt) {
   int ns = md->n_states;
+  if (md->repr == ORC_REPR_DIABATIC) {
+    det_step_dia(md, R, P, phi, a, b, dt);
+    return;
+  }
   double e1[ORC_MAX_NS], U1[ORC_MAX_NS * ORC_MAX_NS];
   det_step(md, R, P, phi, a, b, U, dt, e1, U1);
   if (ns > 2 && U) memcpy(U, U1, sizeof(double) * (size_t)(ns * ns));
+}
+
+/* Diabatic events (the coupling terms of the diabatic equation above):
+ *   rho_gb receives -(i/hbar) V_ga rho_ab  => walker (a,b) -> (g,b), amplitude
+ *     -i c with c = V_ga dt/hbar (three quarter turns)
+ *   rho_ag receives +(i/hbar) rho_ab V_bg  => walker (a,b) -> (a,g), amplitude
+ *     +i c with c = V_bg dt/hbar (one quarter turn)
+ * with W at the end point R_{n+1}; |A_e| = |c_e|, and the probabilities are
+ * quantised and scaled exactly as in the adiabatic representation. */
+int32_t orc_events_dia(const orc_model* md, const double* R, int32_t a, int32_t b, double dt,
+                       int32_t* ta, int32_t* tb, double* c, int32_t* dq, uint32_t* T) {
+  int ns = md->n_states, ne = 0;
+  double W[ORC_MAX_NS * ORC_MAX_NS];
+  elec_matrix(md, R, W);
+  for (int slot = 0; slot < 2; ++slot) {
+    for (int g = 0; g < ns; ++g) {
+      if (slot == 0 && g == a) continue;
+      if (slot == 1 && g == b) continue;
+      c[ne] = ((slot == 0) ? W[g * ns + a] : W[b * ns + g]) * dt / md->hbar;
+      dq[ne] = (slot == 0) ? 3 : 1;
+      ta[ne] = (slot == 0) ? g : a;
+      tb[ne] = (slot == 0) ? b : g;
+      ++ne;
+    }
+  }
+  uint64_t sumT = 0;
+  const uint64_t Tmax = (uint64_t)floor(md->p_max * P24);
+  for (int k = 0; k < ne; ++k) {
+    double p = md->hop_scale * fabs(c[k]);
+    if (p > md->p_max) p = md->p_max;
+    T[k] = (uint32_t)floor(p * P24);
+    sumT += T[k];
+  }
+  if (sumT > Tmax)
+    for (int k = 0; k < ne; ++k) T[k] = (uint32_t)(((uint64_t)T[k] * Tmax) / sumT);
+  return ne;
 }
 
 /* One full step n -> n+1 of one walker: deterministic part, then one
  * stochastic transition decided by Philox word (n & 3) of block n >> 2.  The
  * walker hops to event e with weight m A_e / p_hat_e, or stays with weight
  * m / (1 - sum p_hat); the momentum is never changed by a hop. */
+static void full_step_dia(const orc_model* md, uint64_t seed, uint64_t traj, double* R,
+                          double* P, double* m, double* phi, int32_t* a, int32_t* b, int32_t* q,
+                          int64_t step, double dt) {
+  det_step_dia(md, R, P, phi, *a, *b, dt);
+  int32_t ta[2 * ORC_MAX_NS], tb[2 * ORC_MAX_NS], dq[2 * ORC_MAX_NS];
+  double c[2 * ORC_MAX_NS];
+  uint32_t T[2 * ORC_MAX_NS];
+  int ne = orc_events_dia(md, R, *a, *b, dt, ta, tb, c, dq, T);
+  uint32_t w[4];
+  draw(seed, (uint32_t)(step >> 2), traj, ORC_PURPOSE_HOP, w);
+  uint32_t y = w[step & 3] >> 8;
+  uint64_t cum = 0, tot = 0;
+  for (int k = 0; k < ne; ++k) tot += T[k];
+  for (int k = 0; k < ne; ++k) {
+    cum += T[k];
+    if ((uint64_t)y < cum) {
+      double phat = (double)T[k] / P24;
+      *m = *m * c[k] / phat;
+      *q = (*q + dq[k]) & 3;
+      *a = ta[k];
+      *b = tb[k];
+      return;
+    }
+  }
+  *m = *m / (1.0 - (double)tot / P24);
+}
+
 static void full_step(const orc_model* md, uint64_t seed, uint64_t traj, double* R, double* P,
-                      double* m, double* phi, int32_t* a, int32_t* b, double* U, int64_t step,
-                      double dt, int64_t* n_deg) {
+                      double* m, double* phi, int32_t* a, int32_t* b, double* U, int32_t* q,
+                      int64_t step, double dt, int64_t* n_deg) {
   int ns = md->n_states;
+  if (md->repr == ORC_REPR_DIABATIC) {
+    full_step_dia(md, seed, traj, R, P, m, phi, a, b, q, step, dt);
+    return;
+  }
   double e1[ORC_MAX_NS], U1[ORC_MAX_NS * ORC_MAX_NS];
   int deg = det_step(md, R, P, phi, *a, *b, U, dt, e1, U1);
   if (ns > 2 && U) memcpy(U, U1, sizeof(double) * (size_t)(ns * ns));
@@ -325,13 +425,16 @@ static void full_step(const orc_model* md, uint64_t seed, uint64_t traj, double*
 
 int32_t orc_advance(const orc_model* md, uint64_t seed, uint64_t traj_offset, int64_t n_traj,
                     double* R, double* P, double* m, double* phi, int32_t* alpha, int32_t* beta,
-                    double* U, int64_t step0, int64_t n_steps, double dt, int64_t* n_deg) {
+                    double* U, int32_t* qturn, int64_t step0, int64_t n_steps, double dt,
+                    int64_t* n_deg) {
   int n = md->n_modes, nn = md->n_states * md->n_states;
+  if (md->repr == ORC_REPR_DIABATIC && !qturn) return -1;
   for (int64_t i = 0; i < n_traj; ++i) {
     double* Ui = (md->n_states > 2) ? U + (size_t)i * nn : 0;
+    int32_t* qi = qturn ? qturn + i : 0;
     for (int64_t s = step0; s < step0 + n_steps; ++s)
       full_step(md, seed, traj_offset + (uint64_t)i, R + (size_t)i * n, P + (size_t)i * n, m + i,
-                phi + i, alpha + i, beta + i, Ui, s, dt, n_deg);
+                phi + i, alpha + i, beta + i, Ui, qi, s, dt, n_deg);
   }
   return 0;
 }
@@ -344,10 +447,12 @@ int32_t orc_advance(const orc_model* md, uint64_t seed, uint64_t traj_offset, in
  * rho_ad = U^T rho_el0 U at the walker's own R; the pair (a,b) is drawn from
  * |rho_ad_ab| / sum |rho_ad| (row-major walk, probabilities quantised to 2^-24,
  * the remainder given to the last nonzero pair) with word 0 of block
- * (c0 = N, purpose INIT), and m0 = rho_ad_ab / p_hat_ab, phi0 = 0. */
+ * (c0 = N, purpose INIT), and m0 = rho_ad_ab / p_hat_ab, phi0 = 0.  In the
+ * diabatic representation the pair is drawn the same way from rho_el0 itself,
+ * and q0 = 0. */
 int32_t orc_sample(const orc_model* md, const orc_init* in, uint64_t seed, uint64_t traj_offset,
                    int64_t n_traj, double* R, double* P, double* m, double* phi, int32_t* alpha,
-                   int32_t* beta, double* U) {
+                   int32_t* beta, double* U, int32_t* qturn) {
   int n = md->n_modes, ns = md->n_states, nn = ns * ns;
   for (int64_t i = 0; i < n_traj; ++i) {
     uint64_t traj = traj_offset + (uint64_t)i;
@@ -376,9 +481,13 @@ int32_t orc_sample(const orc_model* md, const orc_init* in, uint64_t seed, uint6
     for (int al = 0; al < ns; ++al)
       for (int be = 0; be < ns; ++be) {
         double acc = 0.0;
-        for (int k = 0; k < ns; ++k)
-          for (int l = 0; l < ns; ++l)
-            acc += Ua[k * ns + al] * in->rho_el0[k * ns + l] * Ua[l * ns + be];
+        if (md->repr == ORC_REPR_DIABATIC) {
+          acc = in->rho_el0[al * ns + be]; /* pairs of the diabatic basis itself */
+        } else {
+          for (int k = 0; k < ns; ++k)
+            for (int l = 0; l < ns; ++l)
+              acc += Ua[k * ns + al] * in->rho_el0[k * ns + l] * Ua[l * ns + be];
+        }
         rad_[al * ns + be] = acc;
         tot += fabs(acc);
       }
@@ -408,6 +517,7 @@ int32_t orc_sample(const orc_model* md, const orc_init* in, uint64_t seed, uint6
     beta[i] = pick % ns;
     m[i] = rad_[pick] / ((double)T[pick] / P24);
     phi[i] = 0.0;
+    if (qturn) qturn[i] = 0;
     if (ns > 2) memcpy(U + (size_t)i * nn, Ua, sizeof(double) * (size_t)nn);
   }
   return 0;
@@ -421,30 +531,38 @@ int32_t orc_sample(const orc_model* md, const orc_init* in, uint64_t seed, uint6
  * element. */
 void orc_contrib(const orc_model* md, int64_t n_traj, const double* R, const double* m,
                  const double* phi, const int32_t* alpha, const int32_t* beta, const double* U,
-                 double* q) {
+                 const int32_t* qturn, double* q) {
   int ns = md->n_states, nn = ns * ns, n = md->n_modes, nq = 4 * nn;
+  int dia = md->repr == ORC_REPR_DIABATIC;
   for (int64_t i = 0; i < n_traj; ++i) {
     double e[ORC_MAX_NS], Uw[ORC_MAX_NS * ORC_MAX_NS];
     const double* Ui;
-    if (ns > 2) {
+    if (ns > 2 && !dia) {
       Ui = U + (size_t)i * nn;
     } else {
       orc_adiabatic(md, R + (size_t)i * n, 0, e, Uw);
       Ui = Uw;
     }
-    double zr = m[i] * cos(phi[i]);
-    double zi = -m[i] * sin(phi[i]);
+    /* z = m exp(-i phi) i^q */
+    double xr = m[i] * cos(phi[i]);
+    double xi = -m[i] * sin(phi[i]);
+    int qq = qturn ? (qturn[i] & 3) : 0;
+    double zr = (qq == 0) ? xr : (qq == 1) ? -xi : (qq == 2) ? -xr : xi;
+    double zi = (qq == 0) ? xi : (qq == 1) ? xr : (qq == 2) ? -xi : -xr;
     double* qi = q + (size_t)i * nq;
     for (int k = 0; k < nq; ++k) qi[k] = 0.0;
     int a = alpha[i], b = beta[i];
+    /* "own" block: the representation the pair lives in; "other": rotated */
+    int own = dia ? 0 : 2 * nn, other = dia ? 2 * nn : 0;
     for (int ii = 0; ii < ns; ++ii)
       for (int jj = 0; jj < ns; ++jj) {
-        double f = Ui[ii * ns + a] * Ui[jj * ns + b];
-        qi[2 * (ii * ns + jj)] = zr * f;
-        qi[2 * (ii * ns + jj) + 1] = zi * f;
+        /* adiabatic pair: U_ia U_jb; diabatic pair: U_ai U_bj */
+        double f = dia ? Ui[a * ns + ii] * Ui[b * ns + jj] : Ui[ii * ns + a] * Ui[jj * ns + b];
+        qi[other + 2 * (ii * ns + jj)] = zr * f;
+        qi[other + 2 * (ii * ns + jj) + 1] = zi * f;
       }
-    qi[2 * nn + 2 * (a * ns + b)] = zr;
-    qi[2 * nn + 2 * (a * ns + b) + 1] = zi;
+    qi[own + 2 * (a * ns + b)] = zr;
+    qi[own + 2 * (a * ns + b) + 1] = zi;
   }
 }
 
@@ -462,10 +580,10 @@ static double pairwise(const double* x, int64_t stride, int64_t lo, int64_t size
 
 void orc_observe(const orc_model* md, int64_t n_traj, const double* R, const double* m,
                  const double* phi, const int32_t* alpha, const int32_t* beta, const double* U,
-                 double* row) {
+                 const int32_t* qturn, double* row) {
   int nq = 4 * md->n_states * md->n_states;
   double* q = (double*)malloc(sizeof(double) * (size_t)(n_traj > 0 ? n_traj : 1) * nq);
-  orc_contrib(md, n_traj, R, m, phi, alpha, beta, U, q);
+  orc_contrib(md, n_traj, R, m, phi, alpha, beta, U, qturn, q);
   int64_t size = 1;
   while (size < n_traj) size *= 2;
   for (int k = 0; k < nq; ++k) {
@@ -487,15 +605,18 @@ int32_t orc_run(const orc_model* md, const orc_init* in, uint64_t seed, uint64_t
   int32_t* al = (int32_t*)malloc(sizeof(int32_t) * nt);
   int32_t* be = (int32_t*)malloc(sizeof(int32_t) * nt);
   double* U = (double*)malloc(sizeof(double) * nt * nn);
-  int32_t rc = orc_sample(md, in, seed, traj_offset, n_traj, R, P, m, phi, al, be, U);
+  int32_t* qt = (int32_t*)malloc(sizeof(int32_t) * nt);
+  int32_t rc = orc_sample(md, in, seed, traj_offset, n_traj, R, P, m, phi, al, be, U, qt);
   if (rc == 0) {
-    orc_observe(md, n_traj, R, m, phi, al, be, U, rows);
+    orc_observe(md, n_traj, R, m, phi, al, be, U, qt, rows);
     for (int64_t s = 0; s < n_steps; ++s) {
       for (int64_t i = 0; i < n_traj; ++i)
         full_step(md, seed, traj_offset + (uint64_t)i, R + (size_t)i * n, P + (size_t)i * n,
-                  m + i, phi + i, al + i, be + i, (ns > 2) ? U + (size_t)i * nn : 0, s, dt, n_deg);
+                  m + i, phi + i, al + i, be + i, (ns > 2) ? U + (size_t)i * nn : 0, qt + i, s,
+                  dt, n_deg);
       if ((s + 1) % out_stride == 0)
-        orc_observe(md, n_traj, R, m, phi, al, be, U, rows + (size_t)((s + 1) / out_stride) * nrow);
+        orc_observe(md, n_traj, R, m, phi, al, be, U, qt,
+                    rows + (size_t)((s + 1) / out_stride) * nrow);
     }
   }
   free(R);
@@ -505,5 +626,6 @@ int32_t orc_run(const orc_model* md, const orc_init* in, uint64_t seed, uint64_t
   free(al);
   free(be);
   free(U);
+  free(qt);
   return rc;
 }

@@ -33,6 +33,24 @@ extern "C" {
 #define ORC_PURPOSE_INIT 1u
 #define ORC_PURPOSE_HOP 2u
 
+/* Electronic basis of the walkers' index pairs (orc_model.repr).
+ *
+ * ADIABATIC (Eq. 1 as printed): pairs of eigenstates of W(R); phase from
+ * e_a - e_b, mean force from the Hellmann-Feynman diagonal, transitions from
+ * the nonadiabatic coupling d_ab contracted with P/M.
+ *
+ * DIABATIC (the same equation written in the R-independent basis of W, in
+ * which d = 0 and the electronic coupling is the off-diagonal potential):
+ *   d/dt rho_ab = -(i/hbar)(V_aa - V_bb) rho_ab
+ *                 - (i/hbar) sum_{g != a} V_ag rho_gb + (i/hbar) sum_{g != b} rho_ag V_gb
+ *                 - (P/M) d rho_ab/dR - 1/2 (F_a + F_b) d rho_ab/dP,
+ * F_a = -dV_aa/dR (the diagonal diabatic force; off-diagonal force terms are
+ * dropped as in Eq. 1).  The transition amplitudes are imaginary, -i c or +i c
+ * with real c = V dt/hbar, so a walker carries its weight as
+ * m exp(-i phi) i^q with an integer count q (mod 4) of quarter turns. */
+#define ORC_REPR_ADIABATIC 0
+#define ORC_REPR_DIABATIC 1
+
 /* Linear vibronic-coupling model: V(R) = 1/2 sum_j k_j R_j^2 + W(R),
  * W(R) = E + sum_j R_j K_j, with k_j = M_j w_j^2 and E, K_j real symmetric
  * n_states x n_states (row-major).  K is [n_modes][n_states*n_states]. */
@@ -46,6 +64,8 @@ typedef struct {
   const double* K;
   double hop_scale; /* kappa: p_e = min(kappa |A_e|, p_max) */
   double p_max;
+  int32_t repr;     /* ORC_REPR_ADIABATIC (0) or ORC_REPR_DIABATIC (1) */
+  int32_t reserved;
 } orc_model;
 
 /* Initial condition: diabatic electronic density rho_el0 (real symmetric),
@@ -91,34 +111,50 @@ int32_t orc_events(const orc_model* md, const double* P, const double* e, const 
                    int32_t a, int32_t b, double dt, int32_t* tgt_a, int32_t* tgt_b, double* A,
                    uint32_t* T);
 
+/* Diabatic transition events of walker (a, b) at R, in the fixed order (first
+ * index, target ascending), then (second index, target ascending): target pair,
+ * real amplitude factor c_e (V_{g a} dt/hbar, then V_{b g} dt/hbar), quarter
+ * turns dq_e of the amplitude (3 for -i, 1 for +i) and the quantised threshold
+ * T_e.  Returns the event count 2 (NS - 1). */
+int32_t orc_events_dia(const orc_model* md, const double* R, int32_t a, int32_t b, double dt,
+                       int32_t* tgt_a, int32_t* tgt_b, double* c, int32_t* dq, uint32_t* T);
+
 /* Deterministic part of one step (velocity Verlet on the pair's mean force and
- * trapezoid phase); U (NS > 2 only) carries the gauge in and out. */
+ * trapezoid phase); U (NS > 2 only, adiabatic only) carries the gauge in and
+ * out. */
 void orc_step_deterministic(const orc_model* md, double* R, double* P, double* phi, int32_t a,
                             int32_t b, double* U, double dt);
 
-/* Sample n_traj walkers with global ids traj_offset + i. */
+/* Sample n_traj walkers with global ids traj_offset + i.  qturn (may be NULL
+ * in the adiabatic representation) receives the quarter-turn counts. */
 int32_t orc_sample(const orc_model* md, const orc_init* in, uint64_t seed, uint64_t traj_offset,
                    int64_t n_traj, double* R, double* P, double* m, double* phi, int32_t* alpha,
-                   int32_t* beta, double* U);
+                   int32_t* beta, double* U, int32_t* qturn);
 
 /* Advance n_traj walkers from absolute step step0 by n_steps.  n_deg (may be
  * NULL) accumulates the count of degenerate-gap events. */
 int32_t orc_advance(const orc_model* md, uint64_t seed, uint64_t traj_offset, int64_t n_traj,
                     double* R, double* P, double* m, double* phi, int32_t* alpha, int32_t* beta,
-                    double* U, int64_t step0, int64_t n_steps, double dt, int64_t* n_deg);
+                    double* U, int32_t* qturn, int64_t step0, int64_t n_steps, double dt,
+                    int64_t* n_deg);
 
 /* Per-walker observable contributions q[i*4NS^2 + k]:
  *   k = 2(i*NS+j)+c          diabatic rho_ij,  c = 0 real, 1 imaginary
- *   k = 2NS^2 + 2(a*NS+b)+c  adiabatic rho_ab  */
+ *   k = 2NS^2 + 2(a*NS+b)+c  adiabatic rho_ab
+ * With z = m exp(-i phi) i^q: an adiabatic pair (a, b) adds z U_ia U_jb to
+ * rho_ij and z to rho_ab; a diabatic pair (a, b) adds z to rho_ab (diabatic)
+ * and z U_ak U_bl to the adiabatic rho_kl, U the eigenvectors at the walker's R
+ * (closed form for two states, else Jacobi with the largest-magnitude component
+ * of each eigenvector positive). */
 void orc_contrib(const orc_model* md, int64_t n_traj, const double* R, const double* m,
                  const double* phi, const int32_t* alpha, const int32_t* beta, const double* U,
-                 double* q);
+                 const int32_t* qturn, double* q);
 
 /* Sum over walkers (pairwise) of each contribution and of its square:
  * row[k] = sum q_k, row[4NS^2 + k] = sum q_k^2. */
 void orc_observe(const orc_model* md, int64_t n_traj, const double* R, const double* m,
                  const double* phi, const int32_t* alpha, const int32_t* beta, const double* U,
-                 double* row);
+                 const int32_t* qturn, double* row);
 
 /* Whole run: sample, then n_steps steps with an observation row at every
  * absolute step s = k * out_stride (k = 0 .. n_steps / out_stride). */
