@@ -83,7 +83,25 @@ typedef struct {
   const double* K;
   double hop_scale;
   double p_max;
+  int32_t repr;     /* QCL_REPR_ADIABATIC (0, Eq. 1 as printed) or QCL_REPR_DIABATIC */
+  int32_t reserved; /* must be 0 */
 } qcl_model_desc;
+
+/* Electronic basis of the walkers' index pairs.
+ *
+ * QCL_REPR_ADIABATIC: Eq. 1 (Sec. II A) as printed -- pairs of eigenstates of
+ *   W(R), phase from e_a - e_b, mean Hellmann-Feynman force, transitions from
+ *   the nonadiabatic coupling d_ab . P/M.
+ * QCL_REPR_DIABATIC: the same equation in the R-independent basis of W, where
+ *   d = 0 and the coupling is the off-diagonal potential: phase from
+ *   V_aa - V_bb, mean force -1/2 (dV_aa/dR + dV_bb/dR), transitions a -> g with
+ *   amplitude -i V_ga dt/hbar and b -> g with +i V_bg dt/hbar.  The imaginary
+ *   unit is carried as a per-walker count of quarter turns (weight
+ *   m exp(-i phi) i^q).  Two-state models only; the FP32-bulk precision takes
+ *   at most 32 modes.  The observables keep their layout: diabatic rho_ij
+ *   (the walkers' own pairs) and adiabatic rho_ab (rotated at the walker's R). */
+#define QCL_REPR_ADIABATIC 0
+#define QCL_REPR_DIABATIC 1
 
 typedef struct qcl_model qcl_model; /* opaque */
 

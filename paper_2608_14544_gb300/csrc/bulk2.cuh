@@ -108,6 +108,7 @@ __device__ __forceinline__ float4 lds4(const float4* p) {
 struct Scal {
   f2 m;
   int mexp;
+  int q;                 // quarter turns of the weight (diabatic representation)
   f2 ph;
   float sa, sb;          // sigma of the index pair: -1 lower, +1 upper adiabatic state
   float A, B;            // a(R), b(R)
@@ -121,6 +122,21 @@ __device__ __forceinline__ void closed_form(Scal& z) {
   z.r = z.r2 * z.ir;
   z.c2 = z.r2 > 0.0f ? z.A * z.ir : 1.0f;
   z.s2 = z.r2 > 0.0f ? z.B * z.ir : 0.0f;
+}
+
+// m *= num / den (den an integer below 2^25, so exact in FP32) as a
+// compensated quotient: rcp.approx, one exact FMA residual, and the product
+// with the error terms collected in lo.
+__device__ __forceinline__ void weight_factor(Scal& z, float num, uint32_t iden) {
+  const float den = __uint2float_rn(iden);
+  const float rd = rcp_approx(den);
+  const float q0 = num * rd;
+  const float q1 = __fmaf_rn(-q0, den, num) * rd;
+  const float p = z.m.hi * q0;
+  float e = __fmaf_rn(z.m.hi, q0, -p);
+  e = __fmaf_rn(z.m.hi, q1, e);
+  z.m = {p, __fmaf_rn(z.m.lo, q0, e)};
+  if (!(fabsf(z.m.hi) <= 0x1p32f && fabsf(z.m.hi) >= 0x1p-32f)) renorm(z.m, z.mexp);
 }
 
 // Phase (trapezoid) and transition of one step, given the decomposition at
@@ -148,24 +164,36 @@ __device__ __forceinline__ void phase_and_transition(Scal& z, float r_old, float
   // 24-bit thresholds T = floor(p 2^24); when 2T exceeds Tmax = floor(p_max 2^24)
   // the integer rescale floor(T Tmax / 2T) gives floor(Tmax / 2), so
   // T = min(floor(kappa dt |g| 2^24), floor(Tmax / 2)) (the conversion saturates)
-  const uint32_t T = min(__float2uint_rz((bp.kdt * kP24f) * fabsf(g)), bp.tmax >> 1);
+  const uint32_t T = min(__float2uint_rz((bp.kamp * kP24f) * fabsf(g)), bp.tmax >> 1);
   const uint32_t y = word >> 8;
   const bool hop1 = y < T;
   const bool hop = y < 2u * T;
   const bool hop2 = hop && !hop1;
   // weight factor: A_e / p_hat on a hop (A_1 = -sig_a dt g, A_2 = -sig_b dt g),
-  // 1 / (1 - sum p_hat) otherwise; num / den as a compensated quotient
-  const float dtg = (bp.dt * kP24f) * g;
-  const float num = hop ? -(hop1 ? z.sa : z.sb) * dtg : kP24f;
-  const float den = __uint2float_rn(hop ? T : 16777216u - 2u * T);
-  const float rd = rcp_approx(den);
-  const float q0 = num * rd;
-  const float q1 = __fmaf_rn(-q0, den, num) * rd;
-  const float p = z.m.hi * q0;
-  float e = __fmaf_rn(z.m.hi, q0, -p);
-  e = __fmaf_rn(z.m.hi, q1, e);
-  z.m = {p, __fmaf_rn(z.m.lo, q0, e)};
-  if (!(fabsf(z.m.hi) <= 0x1p32f && fabsf(z.m.hi) >= 0x1p-32f)) renorm(z.m, z.mexp);
+  // 1 / (1 - sum p_hat) otherwise
+  const float dtg = (bp.amp * kP24f) * g;
+  weight_factor(z, hop ? -(hop1 ? z.sa : z.sb) * dtg : kP24f, hop ? T : 16777216u - 2u * T);
+  z.sa = hop1 ? -z.sa : z.sa;
+  z.sb = hop2 ? -z.sb : z.sb;
+}
+
+// Diabatic representation: phase with hbar w_ab = V_aa - V_bb = -(sig_a - sig_b)
+// a(R) (sig = -1 for diabatic state 0, whose energy is s + a), a_old = a(R_n),
+// z.A = a(R_{n+1}); the transitions a -> 1-a (amplitude -i c) and b -> 1-b
+// (+i c) with c = V_01 dt / hbar = b(R_{n+1}) dt / hbar = amp * Bc.  Both have
+// |A_e| = |c|, so the thresholds follow the adiabatic rule; a hop adds three or
+// one quarter turns.
+__device__ __forceinline__ void dia_phase_and_transition(Scal& z, float a_old, float Bc,
+                                                         uint32_t word, const BulkParams& bp) {
+  const f2 ps = two_sum(z.ph.hi, bp.hdt_hbar * (z.sb - z.sa) * (a_old + z.A));
+  z.ph = {ps.hi, z.ph.lo + ps.lo};
+  const uint32_t T = min(__float2uint_rz((bp.kamp * kP24f) * fabsf(Bc)), bp.tmax >> 1);
+  const uint32_t y = word >> 8;
+  const bool hop1 = y < T;
+  const bool hop = y < 2u * T;
+  const bool hop2 = hop && !hop1;
+  weight_factor(z, hop ? (bp.amp * kP24f) * Bc : kP24f, hop ? T : 16777216u - 2u * T);
+  z.q = (z.q + (hop1 ? 3 : (hop2 ? 1 : 0))) & 3;
   z.sa = hop1 ? -z.sa : z.sa;
   z.sb = hop2 ? -z.sb : z.sb;
 }
@@ -190,7 +218,11 @@ __device__ __forceinline__ void phase_wrap(Scal& z) {
 }
 
 // The walker's 16 observable contributions (diabatic rho_ij and adiabatic
-// rho_ab, real and imaginary) with weight mantissa `mm`.
+// rho_ab, real and imaginary) with weight mantissa `mm`.  z = mm exp(-i phi)
+// (times i^q for a diabatic walker) goes to the walker's own pair in its own
+// representation and, multiplied by U_{alpha k} U_{beta l}, to every element of
+// the other (U is symmetric: the same products serve both directions).
+template <bool DIA>
 __device__ __forceinline__ void contributions(const Scal& z, float mm, float (&v)[16]) {
   // phase reduced into [-pi, pi]: ph_hi - k C1 is exact (|k| < 2^10), the
   // small terms are added once
@@ -209,21 +241,29 @@ __device__ __forceinline__ void contributions(const Scal& z, float mm, float (&v
   const bool al = z.sa > 0.0f, be = z.sb > 0.0f;
   const float ua0 = al ? c : -s, ua1 = al ? s : c;  // column alpha of U
   const float ub0 = be ? c : -s, ub1 = be ? s : c;  // column beta of U
-  const float zr = mm * cphi, zi = -mm * sphi;
+  float zr = mm * cphi, zi = -mm * sphi;
+  if (DIA) {  // times i^q
+    const float xr = zr, xi = zi;
+    zr = (z.q & 1) ? -xi : xr;
+    zi = (z.q & 1) ? xr : xi;
+    zr = (z.q & 2) ? -zr : zr;
+    zi = (z.q & 2) ? -zi : zi;
+  }
+  constexpr int other = DIA ? 8 : 0, own = DIA ? 0 : 8;
   const float f00 = ua0 * ub0, f01 = ua0 * ub1, f10 = ua1 * ub0, f11 = ua1 * ub1;
-  v[0] = zr * f00;
-  v[1] = zi * f00;
-  v[2] = zr * f01;
-  v[3] = zi * f01;
-  v[4] = zr * f10;
-  v[5] = zi * f10;
-  v[6] = zr * f11;
-  v[7] = zi * f11;
+  v[other + 0] = zr * f00;
+  v[other + 1] = zi * f00;
+  v[other + 2] = zr * f01;
+  v[other + 3] = zi * f01;
+  v[other + 4] = zr * f10;
+  v[other + 5] = zi * f10;
+  v[other + 6] = zr * f11;
+  v[other + 7] = zi * f11;
   const int k = (al ? 2 : 0) + (be ? 1 : 0);
 #pragma unroll
   for (int kk = 0; kk < 4; ++kk) {
-    v[8 + 2 * kk] = (kk == k) ? zr : 0.0f;
-    v[9 + 2 * kk] = (kk == k) ? zi : 0.0f;
+    v[own + 2 * kk] = (kk == k) ? zr : 0.0f;
+    v[own + 1 + 2 * kk] = (kk == k) ? zi : 0.0f;
   }
 }
 
@@ -246,14 +286,16 @@ __device__ __forceinline__ double scaled_double(float x, int ex) {
 // walker's 16 contributions and their squares go to its row `row` of shared
 // memory, and lane q sums column q of the warp's 32 rows (from row0) by a fixed
 // pairwise tree.  Returns lane q's column sum, scaled.
+template <bool DIA>
 __device__ __forceinline__ double observe_warp(Scal& z, bool active, float* obs_rows, int row,
                                                int row0, int lane) {
   renorm(z.m, z.mexp);
   phase_wrap(z);
+  if (DIA) closed_form(z);  // the rotation to the adiabatic basis at the walker's R
   const bool live = active && z.m.hi != 0.0f;
   const int ew = __reduce_max_sync(0xffffffffu, live ? z.mexp : -(1 << 28));
   float v[16];
-  contributions(z, live ? (z.m.hi + z.m.lo) * pow2i(z.mexp - ew) : 0.0f, v);
+  contributions<DIA>(z, live ? (z.m.hi + z.m.lo) * pow2i(z.mexp - ew) : 0.0f, v);
   float4* r = reinterpret_cast<float4*>(&obs_rows[row * kObsRow]);
 #pragma unroll
   for (int q = 0; q < 4; ++q) {
@@ -301,6 +343,18 @@ __device__ __forceinline__ void kick(Walker<NPL>& w, const CF& cf, float hu, flo
   }
 }
 
+// Diabatic kick: P += dt/2 F_ab(R), F_j = -k_j R_j - s_j + sab a_j (the
+// adiabatic kick's force with cos 2theta = -1, sin 2theta = 0), hsab = dt/2 sab.
+template <int NPL, int KIND, typename CF>
+__device__ __forceinline__ void kick_dia(Walker<NPL>& w, const CF& cf, float hsab) {
+#pragma unroll
+  for (int j = 0; j < NPL; ++j) {
+    float p = __fmaf_rn(-cf.hk[j], w.R[j], w.P[j]);
+    if (KIND == 1) p -= cf.hs[j];
+    w.P[j] = __fmaf_rn(hsab, cf.a[j], p);
+  }
+}
+
 // Per-mode coefficients of a packed request, held in registers.
 template <int NPL>
 struct CoefLocal {
@@ -315,7 +369,7 @@ struct CoefLocal {
 // coefficients in registers): steps one at a time and the whole Philox
 // function per draw, instead of the unrolled four-step blocks below and the
 // precomputed stream.  Both forms give the same bits.
-template <int NPL, int KIND, typename CF, bool LEAN>
+template <int NPL, int KIND, typename CF, bool LEAN, bool DIA = false>
 __device__ __forceinline__ void bulk2_tile(const BulkParams& bp, const CF& cf, W32& ws,
                                            double* __restrict__ part, int64_t tile, int& rb,
                                            unsigned int& n_deg, double (&red)[2][8][32],
@@ -336,9 +390,10 @@ __device__ __forceinline__ void bulk2_tile(const BulkParams& bp, const CF& cf, W
   z.m = {active ? ws.mh[ii] : 0.0f, active ? ws.ml[ii] : 0.0f};
   z.mexp = active ? ws.me[ii] : 0;
   z.ph = {active ? ws.ph[ii] : 0.0f, active ? ws.pl[ii] : 0.0f};
-  const uint32_t ab = active ? ws.ab[ii] : 0u;
-  z.sa = sgn(ab & 0xff);
-  z.sb = sgn((ab >> 8) & 0xff);
+  const uint32_t ab = active ? ws.ab[ii] : 0u;  // alpha | q << 4 | beta << 8
+  z.sa = sgn(ab & 0xf);
+  z.sb = sgn((ab >> 8) & 0xf);
+  z.q = DIA ? (int)((ab >> 4) & 3u) : 0;
   const uint64_t traj = bp.traj_offset + (uint64_t)ii;
   z.A = bp.a0;
   z.B = bp.b0;
@@ -353,7 +408,7 @@ __device__ __forceinline__ void bulk2_tile(const BulkParams& bp, const CF& cf, W
   // observation into slot `slot` of the tile partials (8 warps, then the
   // tile's fixed FP64 tree)
   auto observe = [&](int slot) {
-    red[rb][warp][lane] = observe_warp(z, active, obs_rows, threadIdx.x, warp * 32, lane);
+    red[rb][warp][lane] = observe_warp<DIA>(z, active, obs_rows, threadIdx.x, warp * 32, lane);
     __syncthreads();
     if (threadIdx.x < 32)
       part[((int64_t)slot * bp.n_tiles + tile) * 32 + threadIdx.x] =
@@ -364,6 +419,22 @@ __device__ __forceinline__ void bulk2_tile(const BulkParams& bp, const CF& cf, W
   // one velocity-Verlet step with its phase and transition (hop word `word`)
   auto step = [&](uint32_t word) {
     const float hsab = bp.hdt * 0.5f * (z.sa + z.sb);  // dt/2 (sig_a + sig_b)/2
+    if constexpr (DIA) {
+      kick_dia<NPL, KIND, CF>(w, cf, hsab);
+#pragma unroll
+      for (int j = 0; j < NPL; ++j) w.R[j] = __fmaf_rn(cf.dtm[j], w.P[j], w.R[j]);
+      const float a_old = z.A;
+      z.A = bp.a0;
+      if (KIND == 1) z.B = bp.b0;
+#pragma unroll
+      for (int j = 0; j < NPL; ++j) {
+        z.A = __fmaf_rn(cf.a[j], w.R[j], z.A);
+        if (KIND == 1) z.B = __fmaf_rn(cf.b[j], w.R[j], z.B);
+      }
+      kick_dia<NPL, KIND, CF>(w, cf, hsab);
+      dia_phase_and_transition(z, a_old, z.B, word, bp);
+      return;
+    }
     kick<NPL, KIND, CF>(w, cf, hsab * z.c2, hsab * z.s2);  // first half kick at R_n
 #pragma unroll
     for (int j = 0; j < NPL; ++j) w.R[j] = __fmaf_rn(cf.dtm[j], w.P[j], w.R[j]);  // drift
@@ -439,7 +510,7 @@ __device__ __forceinline__ void bulk2_tile(const BulkParams& bp, const CF& cf, W
     ws.me[i] = z.mexp;
     ws.ph[i] = z.ph.hi;
     ws.pl[i] = z.ph.lo;
-    ws.ab[i] = (uint16_t)((z.sa > 0.0f ? 1 : 0) | ((z.sb > 0.0f ? 1 : 0) << 8));
+    ws.ab[i] = (uint16_t)((z.sa > 0.0f ? 1 : 0) | (z.q << 4) | ((z.sb > 0.0f ? 1 : 0) << 8));
     if (!isfinite(z.m.hi) || !isfinite(z.ph.hi)) {
       atomicAdd(&ws.hdr->n_nonfinite, 1ull);
       atomicOr(&ws.hdr->flags, QCL_FLAG_NONFINITE);

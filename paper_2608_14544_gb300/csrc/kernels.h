@@ -3,6 +3,8 @@
 #pragma once
 #include <cuda_runtime.h>
 
+#include <cmath>
+
 #include "qcl_common.cuh"
 
 namespace qcl {
@@ -45,15 +47,36 @@ struct BulkParams {
   int32_t widx0;       // word of step cs in its block (cs & 3)
   int32_t n;           // modes
   int32_t kind;        // 0: a_j only (spin-boson form), 1: general two-state
+  int32_t repr;        // QCL_REPR_ADIABATIC or QCL_REPR_DIABATIC
   float a0, b0;
   float dt, hdt;       // dt, dt/2
   float hdt_hbar;      // dt / (2 hbar)
-  float kdt;           // hop_scale * dt
+  float amp;           // amplitude per unit coupling: |A_e| = amp |g| (adiabatic,
+                       // amp = dt) or amp |V_01| (diabatic, amp = dt / hbar)
+  float kamp;          // hop_scale * amp
   float p_max;
   uint32_t tmax;       // floor(p_max 2^24)
   float kappa;         // hop_scale
-  float pad;
 };
+
+// The model-dependent scalars of a bulk launch for time step dt (every caller
+// fills them here, so the single-request, packed and no-allocation routes see
+// the same values).
+inline void bulk_model_scalars(BulkParams& bp, const DevModel& h, double dt) {
+  bp.kind = h.kind;
+  bp.repr = h.repr;
+  bp.a0 = (float)h.a0;
+  bp.b0 = (float)h.b0;
+  bp.dt = (float)dt;
+  bp.hdt = (float)(0.5 * dt);
+  bp.hdt_hbar = (float)(0.5 * dt / h.hbar);
+  const double amp = (h.repr == QCL_REPR_DIABATIC) ? dt / h.hbar : dt;
+  bp.amp = (float)amp;
+  bp.kamp = (float)(h.hop_scale * amp);
+  bp.p_max = (float)h.p_max;
+  bp.tmax = (uint32_t)std::floor(h.p_max * kP24);
+  bp.kappa = (float)h.hop_scale;
+}
 
 // FP32 coefficients of an N_s-state model (N_s <= 8, n_modes <= 32): upper
 // triangles (row-major a <= b) of E and of each K_j.
@@ -96,7 +119,7 @@ void launches_add(int64_t k);
 int64_t launches_read(bool reset);
 
 void launch_sample_f64(const DevModel* dm, const SampleParams& sp, void* buf, cudaStream_t st);
-void launch_step_f64(const DevModel* dm, void* buf, int64_t nt, int n, int64_t step0,
+void launch_step_f64(const DevModel* dm, int repr, void* buf, int64_t nt, int n, int64_t step0,
                      int64_t step, double dt, uint64_t seed, uint64_t traj_off, cudaStream_t st);
 void launch_observe_f64(const DevModel* dm, const void* buf, int64_t nt, int n, double* part,
                         cudaStream_t st);
@@ -105,6 +128,14 @@ void launch_sample_f32(const DevModel* dm, const SampleParams& sp, void* buf, cu
 // Returns the persistent grid size used (0 on launch failure).
 int launch_bulk2(const BulkParams& bp, const Coef2& cf, void* buf, double* part, int grid_cap,
                  cudaStream_t st);
+// The diabatic-representation bulk kernel (two states, n <= 32 modes).
+int launch_bulk2_dia(const BulkParams& bp, const Coef2& cf, void* buf, double* part, int grid_cap,
+                     cudaStream_t st);
+// Launches a persistent bulk kernel with one wave of resident blocks (capped
+// by grid_cap and the tile count); per_sm / n_sm cache the occupancy query.
+using BulkFn = void (*)(const BulkParams, const Coef2, void*, double*);
+int run_bulk_kernel(BulkFn fn, int& per_sm, int& n_sm, const BulkParams& bp, const Coef2& cf,
+                    void* buf, double* part, int grid_cap, cudaStream_t st);
 // Kernel-selection description of the bulk kernel chosen for (n, kind).
 const char* bulk2_variant(int n, int kind);
 

@@ -64,14 +64,18 @@ __global__ void __launch_bounds__(256) k_sample_f32(const DevModel* __restrict__
     }
   }
   const float U[4] = {-s, c, c, s};
-  double rho_ad[4];
+  double rho_ad[4];  // the density in the walkers' representation
   double tot = 0.0;
   for (int al = 0; al < 2; ++al)
     for (int be = 0; be < 2; ++be) {
       float acc = 0.0f;
-      for (int k = 0; k < 2; ++k)
-        for (int l = 0; l < 2; ++l)
-          acc = __fmaf_rn(U[k * 2 + al] * (float)sp.rho[k * 2 + l], U[l * 2 + be], acc);
+      if (M->repr == QCL_REPR_DIABATIC) {
+        acc = (float)sp.rho[al * 2 + be];
+      } else {
+        for (int k = 0; k < 2; ++k)
+          for (int l = 0; l < 2; ++l)
+            acc = __fmaf_rn(U[k * 2 + al] * (float)sp.rho[k * 2 + l], U[l * 2 + be], acc);
+      }
       rho_ad[al * 2 + be] = acc;
       tot += fabsf(acc);
     }
@@ -172,8 +176,9 @@ __device__ __forceinline__ void split_tiles(const BulkParams& bp, const Coef2& c
     z.mexp = active ? ws.me[ii] : 0;
     z.ph = {active ? ws.ph[ii] : 0.0f, active ? ws.pl[ii] : 0.0f};
     const uint32_t ab = active ? ws.ab[ii] : 0u;
-    z.sa = sgn(ab & 0xff);
-    z.sb = sgn((ab >> 8) & 0xff);
+    z.sa = sgn(ab & 0xf);
+    z.sb = sgn((ab >> 8) & 0xf);
+    z.q = 0;
     const uint64_t traj = bp.traj_offset + (uint64_t)ii;
     unsigned int deg = 0;
 
@@ -208,7 +213,7 @@ __device__ __forceinline__ void split_tiles(const BulkParams& bp, const Coef2& c
 
     auto observe = [&](int slot) {
       if (ROLE == 0) {
-        red[rb][grp][lane] = observe_warp(z, active, obs_rows, wslot, grp * 32, lane);
+        red[rb][grp][lane] = observe_warp<false>(z, active, obs_rows, wslot, grp * 32, lane);
       } else {  // the same weight and phase bookkeeping on every role
         renorm(z.m, z.mexp);
         phase_wrap(z);
@@ -350,11 +355,8 @@ void launch_sample_f32(const DevModel* dm, const SampleParams& sp, void* buf, cu
   launches_add(1);
 }
 
-namespace {
-using BulkFn = void (*)(const BulkParams, const Coef2, void*, double*);
-
-int run_kernel(BulkFn fn, int& per_sm, int& n_sm, const BulkParams& bp, const Coef2& cf, void* buf,
-               double* part, int grid_cap, cudaStream_t st) {
+int run_bulk_kernel(BulkFn fn, int& per_sm, int& n_sm, const BulkParams& bp, const Coef2& cf,
+                    void* buf, double* part, int grid_cap, cudaStream_t st) {
   if (per_sm < 0) {
     int dev = 0;
     cudaGetDevice(&dev);
@@ -370,6 +372,12 @@ int run_kernel(BulkFn fn, int& per_sm, int& n_sm, const BulkParams& bp, const Co
   fn<<<(unsigned)grid, 256, 0, st>>>(bp, cf, buf, part);
   launches_add(1);
   return (int)grid;
+}
+
+namespace {
+int run_kernel(BulkFn fn, int& per_sm, int& n_sm, const BulkParams& bp, const Coef2& cf, void* buf,
+               double* part, int grid_cap, cudaStream_t st) {
+  return run_bulk_kernel(fn, per_sm, n_sm, bp, cf, buf, part, grid_cap, st);
 }
 
 template <int NPL, int KIND>
@@ -413,6 +421,7 @@ int dispatch_n(const BulkParams& bp, const Coef2& cf, void* buf, double* part, i
 
 int launch_bulk2(const BulkParams& bp, const Coef2& cf, void* buf, double* part, int grid_cap,
                  cudaStream_t st) {
+  if (bp.repr == QCL_REPR_DIABATIC) return launch_bulk2_dia(bp, cf, buf, part, grid_cap, st);
   return bp.kind == 0 ? dispatch_n<0>(bp, cf, buf, part, grid_cap, st)
                       : dispatch_n<1>(bp, cf, buf, part, grid_cap, st);
 }

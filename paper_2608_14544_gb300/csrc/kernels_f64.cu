@@ -188,12 +188,16 @@ __global__ void __launch_bounds__(256) k_sample_f64(const DevModel* __restrict__
   double c, s;
   half_angle(d, c, s);
   const double U[4] = {-s, c, c, s};  // U[i*2 + alpha]
-  double rho_ad[4];
+  double rho_ad[4];  // the density in the walkers' representation
   for (int al = 0; al < 2; ++al)
     for (int be = 0; be < 2; ++be) {
       double acc = 0.0;
-      for (int k = 0; k < 2; ++k)
-        for (int l = 0; l < 2; ++l) acc += U[k * 2 + al] * sp.rho[k * 2 + l] * U[l * 2 + be];
+      if (M->repr == QCL_REPR_DIABATIC) {
+        acc = sp.rho[al * 2 + be];
+      } else {
+        for (int k = 0; k < 2; ++k)
+          for (int l = 0; l < 2; ++l) acc += U[k * 2 + al] * sp.rho[k * 2 + l] * U[l * 2 + be];
+      }
       rho_ad[al * 2 + be] = acc;
     }
   const u4 wd = philox_draw(sp.seed, (uint32_t)n, traj, kPurposeInit);
@@ -319,6 +323,112 @@ __global__ void __launch_bounds__(256) k_step_f64(const DevModel* __restrict__ M
   }
 }
 
+// One full step of a diabatic walker: velocity Verlet on the diagonal mean
+// force F_j = -k_j R_j - s_j - 1/2 (d_a + d_b) a_j (d = +1 for state 0, -1 for
+// state 1), trapezoid phase with hbar w_ab = V_aa - V_bb = (d_a - d_b) a(R),
+// and one transition: a -> 1-a with amplitude -i b(R) dt/hbar, b -> 1-b with
+// +i b(R) dt/hbar (R at the end of the step).  The index pair word carries the
+// quarter-turn count in bits 4-5.
+template <int NP>
+__global__ void __launch_bounds__(256) k_step_dia_f64(const DevModel* __restrict__ M, void* buf,
+                                                      int64_t nt, int n, int64_t step0,
+                                                      int64_t step, double dt, uint64_t seed,
+                                                      uint64_t traj_off) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  W64 w = view64(buf, nt, 2, n);
+  if (i >= nt) return;
+  if (w.hdr->step != step0) {
+    if (i == 0) atomicOr(&w.hdr->flags, QCL_FLAG_STEP_MISMATCH);
+    return;
+  }
+  const uint16_t ab = w.ab[i];
+  int al = ab & 0xf, be = (ab >> 8) & 0xf, q = (ab >> 4) & 3;
+  double m = w.m[i], phi = w.phi[i];
+  // the diagonal force is the adiabatic kick's with cos 2theta = -1, sin 2theta = 0
+  Ad2 d0, d1;
+  if constexpr (NP > 0) {
+    double R[NP], P[NP];
+#pragma unroll
+    for (int j = 0; j < NP; ++j)
+      if (j < n) {
+        R[j] = w.R[(int64_t)j * nt + i];
+        P[j] = w.P[(int64_t)j * nt + i];
+      }
+    d0 = decomp<NP>(M, R, n);
+    d0.c2 = -1.0;
+    d0.s2 = 0.0;
+    half_kick<NP>(M, R, P, n, d0, al, be, dt);
+#pragma unroll
+    for (int j = 0; j < NP; ++j)
+      if (j < n) R[j] += dt * P[j] / M->mass[j];
+    d1 = decomp<NP>(M, R, n);
+    d1.c2 = -1.0;
+    d1.s2 = 0.0;
+    half_kick<NP>(M, R, P, n, d1, al, be, dt);
+#pragma unroll
+    for (int j = 0; j < NP; ++j)
+      if (j < n) {
+        w.R[(int64_t)j * nt + i] = R[j];
+        w.P[(int64_t)j * nt + i] = P[j];
+      }
+  } else {
+    double* Rg = w.R + i;
+    double* Pg = w.P + i;
+    d0 = decomp_g(M, Rg, nt, n);
+    const double sab = 0.5 * (sigma(al) + sigma(be));
+    for (int j = 0; j < n; ++j) {
+      const int64_t o = (int64_t)j * nt;
+      const double x = Rg[o];
+      double p = Pg[o];
+      p += 0.5 * dt * (-M->k[j] * x - (M->s[j] + sab * (M->a[j] * -1.0 + M->b[j] * 0.0)));
+      Pg[o] = p;
+      Rg[o] = x + dt * p / M->mass[j];
+    }
+    d1 = decomp_g(M, Rg, nt, n);
+    for (int j = 0; j < n; ++j) {
+      const int64_t o = (int64_t)j * nt;
+      const double x = Rg[o];
+      double p = Pg[o];
+      p += 0.5 * dt * (-M->k[j] * x - (M->s[j] + sab * (M->a[j] * -1.0 + M->b[j] * 0.0)));
+      Pg[o] = p;
+    }
+  }
+  // phase: V_aa - V_bb = (d_a - d_b) a = -(sig_a - sig_b) a
+  const double w0 = -(sigma(al) - sigma(be)) * d0.a / M->hbar;
+  const double w1 = -(sigma(al) - sigma(be)) * d1.a / M->hbar;
+  phi += 0.5 * dt * (w0 + w1);
+  // both events have the real factor c = V_01 dt / hbar = b(R_{n+1}) dt / hbar
+  const double cfac = d1.b * dt / M->hbar;
+  const double p1 = fmin(M->hop_scale * fabs(cfac), M->p_max);
+  uint64_t T1 = (uint64_t)floor(p1 * kP24), T2 = T1;
+  const uint64_t Tmax = (uint64_t)floor(M->p_max * kP24);
+  if (T1 + T2 > Tmax) {
+    const uint64_t sT = T1 + T2;
+    T1 = T1 * Tmax / sT;
+    T2 = T2 * Tmax / sT;
+  }
+  const u4 wd = philox_draw(seed, (uint32_t)(step >> 2), traj_off + (uint64_t)i, kPurposeHop);
+  const uint32_t y = word_of(wd, (int)(step & 3)) >> 8;
+  if ((uint64_t)y < T1) {  // a -> 1 - a, amplitude -i c
+    m = m * cfac / ((double)T1 / kP24);
+    q = (q + 3) & 3;
+    al ^= 1;
+  } else if ((uint64_t)y < T1 + T2) {  // b -> 1 - b, amplitude +i c
+    m = m * cfac / ((double)T2 / kP24);
+    q = (q + 1) & 3;
+    be ^= 1;
+  } else {
+    m = m / (1.0 - (double)(T1 + T2) / kP24);
+  }
+  w.m[i] = m;
+  w.phi[i] = phi;
+  w.ab[i] = (uint16_t)(al | (q << 4) | (be << 8));
+  if (!isfinite(m) || !isfinite(phi)) {
+    atomicAdd(&w.hdr->n_nonfinite, 1ull);
+    atomicOr(&w.hdr->flags, QCL_FLAG_NONFINITE);
+  }
+}
+
 // ------------------------------------------------------------- observation --
 // Walker contributions m exp(-i phi) U_ia U_jb (diabatic) and m exp(-i phi) at
 // (a, b) (adiabatic), and their squares, summed per 256-walker tile.
@@ -337,23 +447,30 @@ __global__ void __launch_bounds__(256) k_observe_f64(const DevModel* __restrict_
     half_angle(d, c, s);
     const double U[4] = {-s, c, c, s};
     const uint16_t ab = w.ab[i];
-    const int al = ab & 0xff, be = ab >> 8;
+    const int al = ab & 0xf, be = (ab >> 8) & 0xf, q = (ab >> 4) & 3;
     double sn, cs;
     sincos(w.phi[i], &sn, &cs);
-    const double zr = w.m[i] * cs, zi = -w.m[i] * sn;
+    // z = m exp(-i phi) i^q
+    const double xr = w.m[i] * cs, xi = -w.m[i] * sn;
+    const double zr = q == 0 ? xr : (q == 1 ? -xi : (q == 2 ? -xr : xi));
+    const double zi = q == 0 ? xi : (q == 1 ? xr : (q == 2 ? -xi : -xr));
+    // the walker's own representation gets z at its pair, the other one the
+    // rotated products (U is symmetric, so U_ia U_jb and U_ai U_bj coincide)
+    const bool dia = M->repr == QCL_REPR_DIABATIC;
+    const int own = dia ? 0 : 8, other = dia ? 8 : 0;
 #pragma unroll
     for (int ii = 0; ii < 2; ++ii)
 #pragma unroll
       for (int jj = 0; jj < 2; ++jj) {
         const double f = U[ii * 2 + al] * U[jj * 2 + be];
-        v[2 * (ii * 2 + jj)] = zr * f;
-        v[2 * (ii * 2 + jj) + 1] = zi * f;
+        v[other + 2 * (ii * 2 + jj)] = zr * f;
+        v[other + 2 * (ii * 2 + jj) + 1] = zi * f;
       }
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
       const bool hit = (k == al * 2 + be);
-      v[8 + 2 * k] = hit ? zr : 0.0;
-      v[8 + 2 * k + 1] = hit ? zi : 0.0;
+      v[own + 2 * k] = hit ? zr : 0.0;
+      v[own + 2 * k + 1] = hit ? zi : 0.0;
     }
 #pragma unroll
     for (int q = 0; q < 16; ++q) v[16 + q] = v[q] * v[q];
@@ -372,9 +489,21 @@ void launch_sample_f64(const DevModel* dm, const SampleParams& sp, void* buf, cu
   launches_add(1);
 }
 
-void launch_step_f64(const DevModel* dm, void* buf, int64_t nt, int n, int64_t step0,
+void launch_step_f64(const DevModel* dm, int repr, void* buf, int64_t nt, int n, int64_t step0,
                      int64_t step, double dt, uint64_t seed, uint64_t traj_off, cudaStream_t st) {
   const unsigned nb = (unsigned)((nt + 255) / 256);
+  if (repr == QCL_REPR_DIABATIC) {
+    if (n <= 1)
+      k_step_dia_f64<1><<<nb, 256, 0, st>>>(dm, buf, nt, n, step0, step, dt, seed, traj_off);
+    else if (n <= 4)
+      k_step_dia_f64<4><<<nb, 256, 0, st>>>(dm, buf, nt, n, step0, step, dt, seed, traj_off);
+    else if (n <= 16)
+      k_step_dia_f64<16><<<nb, 256, 0, st>>>(dm, buf, nt, n, step0, step, dt, seed, traj_off);
+    else
+      k_step_dia_f64<0><<<nb, 256, 0, st>>>(dm, buf, nt, n, step0, step, dt, seed, traj_off);
+    launches_add(1);
+    return;
+  }
   if (n <= 1)
     k_step_f64<1><<<nb, 256, 0, st>>>(dm, buf, nt, n, step0, step, dt, seed, traj_off);
   else if (n <= 4)

@@ -123,15 +123,7 @@ extern "C" qcl_status qcl_propagate_noalloc(const qcl_model* model, const qcl_en
   bp.step0 = step0;
   bp.stride = out_stride;
   bp.n = model->n;
-  bp.kind = h.kind;
-  bp.a0 = (float)h.a0;
-  bp.b0 = (float)h.b0;
-  bp.dt = (float)dt;
-  bp.hdt = (float)(0.5 * dt);
-  bp.hdt_hbar = (float)(0.5 * dt / model->hbar);
-  bp.kdt = (float)(model->hop_scale * dt);
-  bp.p_max = (float)model->p_max;
-  bp.tmax = (uint32_t)std::floor(model->p_max * kP24);
+  bulk_model_scalars(bp, h, dt);
 
   // chunks of at most `slots` output times (the reduction tree does not depend
   // on the chunking, so the rows equal those of qcl_propagate bit for bit)

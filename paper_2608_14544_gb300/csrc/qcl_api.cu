@@ -95,6 +95,8 @@ qcl_status check_ens(const qcl_model* m, const qcl_ensemble_desc* e) {
     return fail(QCL_ERR_INVALID_ARG, "unknown precision %d", e->precision);
   if (m->ns > 2 && e->precision == QCL_PREC_FP32_BULK && m->n > (m->ns <= 4 ? 32 : 8))
     return fail(QCL_ERR_UNSUPPORTED, "FP32-bulk models with %d states support n_modes <= %d (got %d)", m->ns, m->ns <= 4 ? 32 : 8, m->n);
+  if (m->host.repr == QCL_REPR_DIABATIC && e->precision == QCL_PREC_FP32_BULK && m->n > 32)
+    return fail(QCL_ERR_UNSUPPORTED, "diabatic FP32-bulk models support n_modes <= 32 (got %d)", m->n);
   return QCL_OK;
 }
 
@@ -188,6 +190,9 @@ qcl_status qcl_create_model(const qcl_model_desc* d, qcl_model** out) {
   const double pmax = d->p_max == 0.0 ? 0.5 : d->p_max;
   if (!(hop > 0.0) || !std::isfinite(hop)) return fail(QCL_ERR_INVALID_ARG, "hop_scale must be positive");
   if (!(pmax > 0.0 && pmax < 1.0)) return fail(QCL_ERR_INVALID_ARG, "p_max must lie in (0, 1)");
+  if (d->repr != QCL_REPR_ADIABATIC && d->repr != QCL_REPR_DIABATIC) return fail(QCL_ERR_INVALID_ARG, "repr = %d is neither adiabatic (0) nor diabatic (1)", d->repr);
+  if (d->repr == QCL_REPR_DIABATIC && ns != 2) return fail(QCL_ERR_UNSUPPORTED, "the diabatic representation takes two-state models (n_states = %d)", ns);
+  if (d->reserved != 0) return fail(QCL_ERR_INVALID_ARG, "reserved must be 0");
   for (int j = 0; j < n; ++j) {
     if (!(d->mass[j] > 0.0) || !std::isfinite(d->mass[j])) return fail(QCL_ERR_INVALID_ARG, "mass[%d] must be positive", j);
     if (!(d->omega[j] > 0.0) || !std::isfinite(d->omega[j])) return fail(QCL_ERR_INVALID_ARG, "omega[%d] must be positive", j);
@@ -236,6 +241,7 @@ qcl_status qcl_create_model(const qcl_model_desc* d, qcl_model** out) {
   }
   for (size_t k = 0; k < nn; ++k) h.E[k] = d->E[k];
   h.kind = general ? 1 : 0;
+  h.repr = d->repr;
   int dev = 0;
   cudaGetDevice(&dev);
   m->device = dev;
@@ -368,7 +374,7 @@ qcl_status qcl_propagate(const qcl_model* model, const qcl_ensemble_desc* ens, v
       {
         TimedLaunch tl(1, s);
         if (ns == 2)
-          launch_step_f64(model->dev, ens_buf, nt, model->n, step0, t, dt, ens->seed, ens->traj_id_offset, s);
+          launch_step_f64(model->dev, model->host.repr, ens_buf, nt, model->n, step0, t, dt, ens->seed, ens->traj_id_offset, s);
         else
           launch_stepN_f64(model->dev, ns, ens_buf, nt, model->n, step0, t, dt, ens->seed, ens->traj_id_offset, s);
       }
@@ -397,16 +403,7 @@ qcl_status qcl_propagate(const qcl_model* model, const qcl_ensemble_desc* ens, v
     bp.step0 = step0;
     bp.stride = out_stride;
     bp.n = model->n;
-    bp.kind = h.kind;
-    bp.a0 = (float)h.a0;
-    bp.b0 = (float)h.b0;
-    bp.dt = (float)dt;
-    bp.hdt = (float)(0.5 * dt);
-    bp.hdt_hbar = (float)(0.5 * dt / model->hbar);
-    bp.kdt = (float)(model->hop_scale * dt);
-    bp.p_max = (float)model->p_max;
-    bp.tmax = (uint32_t)std::floor(model->p_max * kP24);
-    bp.kappa = (float)model->hop_scale;
+    bulk_model_scalars(bp, h, dt);
     CoefN* cn = nullptr;
     if (model->ns > 2) {
       cn = new (std::nothrow) CoefN();

@@ -161,7 +161,7 @@ __device__ __forceinline__ void df_div(float c, float d, float& q0, float& q1) {
 struct DevModel {
   int32_t ns, n;
   int32_t kind;       // 0: only a_j nonzero (spin-boson form), 1: general two-state
-  int32_t pad;
+  int32_t repr;       // QCL_REPR_ADIABATIC or QCL_REPR_DIABATIC
   double hbar, hop_scale, p_max;
   double a0, b0, s0;
   // per-mode arrays [n]

@@ -105,6 +105,7 @@ struct Request {
   // copies of the caller's descriptors
   int ns = 0, n = 0;
   double hbar = 1, hop = 1, pmax = 0.5;
+  int32_t repr = QCL_REPR_ADIABATIC;
   std::vector<double> mass, omega, E, K, rho, R0, P0;
   double beta = INFINITY;
   int wigner = 1;
@@ -251,16 +252,7 @@ void fill_bulk(const Request& r, const Chunk& c, int64_t n_tiles, BulkParams& bp
   bp.step0 = c.cs;
   bp.stride = r.stride;
   bp.n = r.n;
-  bp.kind = h.kind;
-  bp.a0 = (float)h.a0;
-  bp.b0 = (float)h.b0;
-  bp.dt = (float)r.dt;
-  bp.hdt = (float)(0.5 * r.dt);
-  bp.hdt_hbar = (float)(0.5 * r.dt / r.hbar);
-  bp.kdt = (float)(r.hop * r.dt);
-  bp.p_max = (float)r.pmax;
-  bp.tmax = (uint32_t)std::floor(r.pmax * kP24);
-  bp.kappa = (float)r.hop;
+  bulk_model_scalars(bp, h, r.dt);
   bp.cs = c.cs;
   bp.ce = c.ce;
   bp.k_first = c.k_first;
@@ -395,7 +387,7 @@ void worker_main(qcl_server* s) {
     }
     admit(s, fresh);
     for (auto& r : fresh) {
-      qcl_model_desc md{r->ns, r->n, r->hbar, r->mass.data(), r->omega.data(), r->E.data(), r->K.data(), r->hop, r->pmax};
+      qcl_model_desc md{r->ns, r->n, r->hbar, r->mass.data(), r->omega.data(), r->E.data(), r->K.data(), r->hop, r->pmax, r->repr, 0};
       qcl_status st = qcl_create_model(&md, &r->model);
       if (st == QCL_OK) {
         qcl_init_desc in{r->rho.data(), r->R0.data(), r->P0.data(), r->beta, r->wigner, 0};
@@ -467,6 +459,9 @@ qcl_status qcl_server_submit(qcl_server* s, const qcl_request_desc* r, int64_t* 
     return fail(QCL_ERR_UNSUPPORTED, "model size outside the built range");
   if (m.n_states > 2 && m.n_modes > (m.n_states <= 4 ? 32 : 8))
     return fail(QCL_ERR_UNSUPPORTED, "too many modes for a %d-state FP32-bulk model", m.n_states);
+  if (m.repr != QCL_REPR_ADIABATIC && m.repr != QCL_REPR_DIABATIC) return fail(QCL_ERR_INVALID_ARG, "unknown representation %d", m.repr);
+  if (m.repr == QCL_REPR_DIABATIC && (m.n_states != 2 || m.n_modes > 32))
+    return fail(QCL_ERR_UNSUPPORTED, "the diabatic representation takes two-state FP32-bulk models of at most 32 modes");
   if (!m.mass || !m.omega || !m.E || !m.K || !r->init->rho_el0 || !r->init->R0 || !r->init->P0)
     return fail(QCL_ERR_INVALID_ARG, "a request array is NULL");
   if (r->n_traj < 1 || r->n_steps < 1 || r->out_stride < 1 || !(r->dt > 0.0))
@@ -478,6 +473,7 @@ qcl_status qcl_server_submit(qcl_server* s, const qcl_request_desc* r, int64_t* 
   q->hbar = m.hbar;
   q->hop = m.hop_scale == 0.0 ? 1.0 : m.hop_scale;
   q->pmax = m.p_max == 0.0 ? 0.5 : m.p_max;
+  q->repr = m.repr;
   q->mass.assign(m.mass, m.mass + n);
   q->omega.assign(m.omega, m.omega + n);
   q->E.assign(m.E, m.E + nn);
@@ -494,7 +490,8 @@ qcl_status qcl_server_submit(qcl_server* s, const qcl_request_desc* r, int64_t* 
   q->n_out = r->n_steps / r->out_stride + 1;
   q->ens_bytes = EnsLayout::make(r->n_traj, ns, n, QCL_PREC_FP32_BULK).total;
   q->obs_bytes = ObsLayout::make(r->n_traj, ns, q->n_out, tile_walkers(QCL_PREC_FP32_BULK, n, ns)).total;
-  q->bucket = (ns == 2) ? packed_bucket(n) : -1;
+  // the packed kernel runs adiabatic two-state models; others get their own launches
+  q->bucket = (ns == 2 && m.repr == QCL_REPR_ADIABATIC) ? packed_bucket(n) : -1;
   q->t_submit = now_s();
   std::lock_guard<std::mutex> lk(s->mu);
   if (align256(q->ens_bytes) + align256(q->obs_bytes) > s->alloc.total())

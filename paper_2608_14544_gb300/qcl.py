@@ -47,7 +47,22 @@ class QclError(RuntimeError):
 class ModelDesc(C.Structure):
     _fields_ = [("n_states", C.c_int32), ("n_modes", C.c_int32), ("hbar", C.c_double),
                 ("mass", C.c_void_p), ("omega", C.c_void_p), ("E", C.c_void_p),
-                ("K", C.c_void_p), ("hop_scale", C.c_double), ("p_max", C.c_double)]
+                ("K", C.c_void_p), ("hop_scale", C.c_double), ("p_max", C.c_double),
+                ("repr", C.c_int32), ("reserved", C.c_int32)]
+
+
+REPR_ADIABATIC = 0
+REPR_DIABATIC = 1
+
+
+def repr_code(m: dict) -> int:
+    """QCL_REPR_* of a model dict ("repr": "adiabatic" (default) or "diabatic")."""
+    r = m.get("repr", "adiabatic")
+    if r in ("adiabatic", REPR_ADIABATIC):
+        return REPR_ADIABATIC
+    if r in ("diabatic", REPR_DIABATIC):
+        return REPR_DIABATIC
+    raise ValueError(f"unknown representation {r!r}")
 
 
 class EnsembleDesc(C.Structure):
@@ -193,7 +208,7 @@ class Model:
         self._arrs = [_f64(m["mass"]), _f64(m["omega"]), _f64(m["E"]).reshape(-1),
                       _f64(m["K"]).reshape(-1)]
         d = ModelDesc(self.ns, self.n, float(m["hbar"]), *[a.ctypes.data for a in self._arrs],
-                      float(m.get("hop_scale", 1.0)), float(m.get("p_max", 0.5)))
+                      float(m.get("hop_scale", 1.0)), float(m.get("p_max", 0.5)), repr_code(m), 0)
         h = C.c_void_p()
         _check(load().qcl_create_model(C.byref(d), C.byref(h)), "qcl_create_model")
         self.handle = h
@@ -364,7 +379,10 @@ class Run:
                 "m_lo": np.zeros(nt) if fp64 else arr(off[3], nt, dt, w),
                 "phi": arr(off[4], nt, dt, w),
                 "phi_lo": np.zeros(nt) if fp64 else arr(off[5], nt, dt, w),
-                "alpha": (arr(off[6], nt, np.uint16, 2) & 0xFF).astype(np.int32),
+                # index pair word: alpha | q << 4 | beta << 8 (q: quarter turns of a
+                # diabatic walker's weight, 0 in the adiabatic representation)
+                "alpha": (arr(off[6], nt, np.uint16, 2) & 0xF).astype(np.int32),
+                "q": ((arr(off[6], nt, np.uint16, 2) >> 4) & 0x3).astype(np.int32),
                 "beta": (arr(off[6], nt, np.uint16, 2) >> 8).astype(np.int32), **extra}
 
 
@@ -391,7 +409,7 @@ def _model_desc(m: dict):
     arrs = [_f64(m["mass"]), _f64(m["omega"]), _f64(m["E"]).reshape(-1), _f64(m["K"]).reshape(-1)]
     d = ModelDesc(int(m["n_states"]), int(m["n_modes"]), float(m["hbar"]),
                   *[a.ctypes.data for a in arrs], float(m.get("hop_scale", 1.0)),
-                  float(m.get("p_max", 0.5)))
+                  float(m.get("p_max", 0.5)), repr_code(m), 0)
     return d, arrs
 
 

@@ -53,11 +53,11 @@ def test_library_targets_sm_103a(lib):
 def test_model_validation_without_gpu(lib):
     from paper_2608_14544_gb300 import qcl
 
-    def desc(ns, n, E, K, mass=None, omega=None, hbar=1.0, pmax=0.5):
+    def desc(ns, n, E, K, mass=None, omega=None, hbar=1.0, pmax=0.5, rep=0, reserved=0):
         arrs = [np.ones(n) if mass is None else np.asarray(mass, float),
                 np.ones(n) if omega is None else np.asarray(omega, float),
                 np.ascontiguousarray(E, dtype=float), np.ascontiguousarray(K, dtype=float)]
-        d = qcl.ModelDesc(ns, n, hbar, *[a.ctypes.data for a in arrs], 1.0, pmax)
+        d = qcl.ModelDesc(ns, n, hbar, *[a.ctypes.data for a in arrs], 1.0, pmax, rep, reserved)
         return d, arrs
 
     h = C.c_void_p()
@@ -76,6 +76,15 @@ def test_model_validation_without_gpu(lib):
     assert lib.qcl_create_model(C.byref(d), C.byref(h)) == 2
     assert lib.qcl_create_model(None, C.byref(h)) == 1
     assert lib.qcl_destroy_model(None) == 0
+    # representation: unknown code, diabatic beyond two states, reserved field
+    d, keep = desc(2, 1, E, K, rep=5)
+    assert lib.qcl_create_model(C.byref(d), C.byref(h)) == 1
+    assert b"representation" in lib.qcl_last_error() or b"repr" in lib.qcl_last_error()
+    d, keep = desc(3, 1, np.eye(3), np.zeros((1, 3, 3)), rep=qcl.REPR_DIABATIC)
+    assert lib.qcl_create_model(C.byref(d), C.byref(h)) == 2
+    assert b"diabatic" in lib.qcl_last_error()
+    d, keep = desc(2, 1, E, K, reserved=1)
+    assert lib.qcl_create_model(C.byref(d), C.byref(h)) == 1
 
 
 def test_option_and_null_checks_without_gpu(lib):
