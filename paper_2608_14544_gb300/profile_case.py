@@ -16,6 +16,7 @@ def main():
     ap.add_argument("--steps", type=int, default=None)
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
     ap.add_argument("--repeat", type=int, default=1)
+    ap.add_argument("--repr", default="adiabatic", choices=["adiabatic", "diabatic"])
     args = ap.parse_args()
 
     import torch
@@ -26,6 +27,7 @@ def main():
     build.build()
     torch.cuda.set_device(0)
     cfg = wl.lvc4_config(1) if args.config == "lvc4" else wl.config(int(args.config))
+    cfg["model"]["repr"] = args.repr
     n = args.n_traj or cfg["n_traj"]
     steps = args.steps or cfg["n_steps"]
     stride = cfg["out_stride"]
