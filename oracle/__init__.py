@@ -97,6 +97,13 @@ def _l():
             lib.orc_observe.argtypes = [vp, i64, vp, vp, vp, vp, vp, vp, vp, vp]
             lib.orc_run.argtypes = [vp, vp, u64, u64, i64, d, i64, i64, vp, vp]
             lib.orc_run.restype = i32
+            lib.orc_spawn_sample.argtypes = [vp, vp, u64, u64, i64] + [vp] * 10
+            lib.orc_spawn_sample.restype = i32
+            lib.orc_spawn_advance.argtypes = [vp, u64, i64, vp] + [vp] * 10 + [i64, i64, d]
+            lib.orc_spawn_advance.restype = i32
+            lib.orc_spawn_observe.argtypes = [vp, i64, i64] + [vp] * 9
+            lib.orc_run_spawn.argtypes = [vp, vp, u64, u64, i64, i64, d, i64, i64, vp, vp]
+            lib.orc_run_spawn.restype = i32
             _lib = lib
     return _lib
 
@@ -315,3 +322,70 @@ def finalize(rows: np.ndarray, n_traj: int):
     var = np.maximum(s2 - s * s / n_traj, 0.0) / max(n_traj - 1, 1)
     se = np.sqrt(var / n_traj)
     return mean, se
+
+
+# ------------------------------------------------------------------ spawning --
+class SpawnState(State):
+    """Spawning ensemble: arrays of `capacity` walkers, the first n_live live (in
+    family order), with each walker's random-stream id and family index."""
+
+    def __init__(self, model: OracleModel, n0: int, capacity: int):
+        super().__init__(model, capacity)
+        self.n0 = n0
+        self.capacity = capacity
+        self.n_live = n0
+        self.id = np.zeros(capacity, dtype=np.uint64)
+        self.family = np.zeros(capacity, dtype=np.int64)
+
+    def sargs(self):
+        return self.args() + (_ptr(self.id), _ptr(self.family))
+
+    def live(self):
+        """Dict of the live walkers' arrays."""
+        k = self.n_live
+        return {"R": self.R[:k], "P": self.P[:k], "m": self.m[:k], "phi": self.phi[:k],
+                "alpha": self.alpha[:k], "beta": self.beta[:k], "q": self.q[:k],
+                "id": self.id[:k], "family": self.family[:k]}
+
+
+def spawn_sample(model: OracleModel, init: OracleInit, seed: int, traj_offset: int, n0: int,
+                 capacity: int):
+    st = SpawnState(model, n0, capacity)
+    rc = _l().orc_spawn_sample(model.ref, init.ref, seed, traj_offset, n0, *st.sargs())
+    if rc != 0:
+        raise ValueError("oracle: initial electronic density has no nonzero element")
+    return st
+
+
+def spawn_advance(model: OracleModel, st: SpawnState, seed: int, step0: int, n_steps: int,
+                  dt: float) -> int:
+    """Returns 0, or -2 on capacity overflow."""
+    nl = np.array([st.n_live], dtype=np.int64)
+    rc = _l().orc_spawn_advance(model.ref, seed, st.capacity, _ptr(nl), *st.sargs(), step0,
+                                n_steps, dt)
+    st.n_live = int(nl[0])
+    return rc
+
+
+def spawn_observe(model: OracleModel, st: SpawnState):
+    row = np.zeros(8 * model.ns * model.ns)
+    _l().orc_spawn_observe(model.ref, st.n0, st.n_live, _ptr(st.R), _ptr(st.m), _ptr(st.phi),
+                           _ptr(st.alpha), _ptr(st.beta), _ptr(st.U), _ptr(st.q),
+                           _ptr(st.family), _ptr(row))
+    return row
+
+
+def run_spawn(model: OracleModel, init: OracleInit, seed: int, traj_offset: int, n0: int,
+              capacity: int, dt: float, n_steps: int, out_stride: int):
+    """Whole spawning run: (rows[n_out, 8 NS^2] of family sums and their squares,
+    live walkers at each output).  Raises OverflowError past capacity."""
+    n_out = n_steps // out_stride + 1
+    rows = np.zeros((n_out, 8 * model.ns * model.ns))
+    n_live = np.zeros(n_out, dtype=np.int64)
+    rc = _l().orc_run_spawn(model.ref, init.ref, seed, traj_offset, n0, capacity, dt, n_steps,
+                            out_stride, _ptr(rows), _ptr(n_live))
+    if rc == -2:
+        raise OverflowError("oracle: spawning ensemble exceeded its capacity")
+    if rc != 0:
+        raise ValueError("oracle: initial electronic density has no nonzero element")
+    return rows, n_live

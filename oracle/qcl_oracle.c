@@ -629,3 +629,192 @@ int32_t orc_run(const orc_model* md, const orc_init* in, uint64_t seed, uint64_t
   free(qt);
   return rc;
 }
+
+/* ------------------------------------------------------------- spawning -- */
+static uint64_t child_id(uint64_t seed, int64_t step, uint64_t parent) {
+  uint32_t w[4];
+  draw(seed, (uint32_t)step, parent, ORC_PURPOSE_SPAWN, w);
+  return (((uint64_t)w[1] << 32) | w[0]) | (1ull << 63);
+}
+
+int32_t orc_spawn_sample(const orc_model* md, const orc_init* in, uint64_t seed,
+                         uint64_t traj_offset, int64_t n0, double* R, double* P, double* m,
+                         double* phi, int32_t* alpha, int32_t* beta, double* U, int32_t* qturn,
+                         uint64_t* id, int64_t* family) {
+  int32_t rc = orc_sample(md, in, seed, traj_offset, n0, R, P, m, phi, alpha, beta, U, qturn);
+  for (int64_t i = 0; i < n0; ++i) {
+    id[i] = traj_offset + (uint64_t)i;
+    family[i] = i;
+  }
+  return rc;
+}
+
+/* One walker's step under spawning: the deterministic part, then the same
+ * transition test as full_step.  Returns 1 and fills the child's pair, weight
+ * and quarter turns when the test fires. */
+static int spawn_walker_step(const orc_model* md, uint64_t seed, uint64_t traj, double* R,
+                             double* P, double* m, double* phi, int32_t a, int32_t b, double* U,
+                             int32_t q, int64_t step, double dt, int32_t* ca, int32_t* cb,
+                             double* cm, int32_t* cq) {
+  int ns = md->n_states;
+  int32_t ta[2 * ORC_MAX_NS], tb[2 * ORC_MAX_NS], dq[2 * ORC_MAX_NS];
+  double A[2 * ORC_MAX_NS];
+  uint32_t T[2 * ORC_MAX_NS];
+  int ne;
+  if (md->repr == ORC_REPR_DIABATIC) {
+    det_step_dia(md, R, P, phi, a, b, dt);
+    ne = orc_events_dia(md, R, a, b, dt, ta, tb, A, dq, T);
+  } else {
+    double e1[ORC_MAX_NS], U1[ORC_MAX_NS * ORC_MAX_NS];
+    det_step(md, R, P, phi, a, b, U, dt, e1, U1);
+    if (ns > 2 && U) memcpy(U, U1, sizeof(double) * (size_t)(ns * ns));
+    ne = events_impl(md, P, e1, U1, a, b, dt, ta, tb, A, T, 0);
+    for (int k = 0; k < ne; ++k) dq[k] = 0;
+  }
+  uint32_t w[4];
+  draw(seed, (uint32_t)(step >> 2), traj, ORC_PURPOSE_HOP, w);
+  uint32_t y = w[step & 3] >> 8;
+  uint64_t cum = 0;
+  for (int k = 0; k < ne; ++k) {
+    cum += T[k];
+    if ((uint64_t)y < cum) {
+      *ca = ta[k];
+      *cb = tb[k];
+      *cm = *m * A[k] / ((double)T[k] / P24);
+      *cq = (q + dq[k]) & 3;
+      return 1;
+    }
+  }
+  return 0;
+}
+
+int32_t orc_spawn_advance(const orc_model* md, uint64_t seed, int64_t capacity, int64_t* n_live,
+                          double* R, double* P, double* m, double* phi, int32_t* alpha,
+                          int32_t* beta, double* U, int32_t* qturn, uint64_t* id,
+                          int64_t* family, int64_t step0, int64_t n_steps, double dt) {
+  int n = md->n_modes, ns = md->n_states, nn = ns * ns;
+  for (int64_t s = step0; s < step0 + n_steps; ++s) {
+    int64_t nl = *n_live;
+    /* step every live walker; children go to scratch, in parent order */
+    int32_t* hit = (int32_t*)calloc((size_t)(nl > 0 ? nl : 1), sizeof(int32_t));
+    int32_t* ca = (int32_t*)malloc(sizeof(int32_t) * (size_t)(nl > 0 ? nl : 1));
+    int32_t* cb = (int32_t*)malloc(sizeof(int32_t) * (size_t)(nl > 0 ? nl : 1));
+    int32_t* cq = (int32_t*)malloc(sizeof(int32_t) * (size_t)(nl > 0 ? nl : 1));
+    double* cm = (double*)malloc(sizeof(double) * (size_t)(nl > 0 ? nl : 1));
+    /* keep the pre-step ensemble in case the step overflows */
+    double* keep = (double*)malloc(sizeof(double) * (size_t)(nl > 0 ? nl : 1) * (2 * n + 2 + nn));
+    int64_t n_child = 0;
+    for (int64_t i = 0; i < nl; ++i) {
+      double* k = keep + (size_t)i * (2 * n + 2 + nn);
+      memcpy(k, R + (size_t)i * n, sizeof(double) * n);
+      memcpy(k + n, P + (size_t)i * n, sizeof(double) * n);
+      k[2 * n] = m[i];
+      k[2 * n + 1] = phi[i];
+      memcpy(k + 2 * n + 2, U + (size_t)i * nn, sizeof(double) * nn);
+      hit[i] = spawn_walker_step(md, seed, id[i], R + (size_t)i * n, P + (size_t)i * n, m + i,
+                                 phi + i, alpha[i], beta[i], (ns > 2) ? U + (size_t)i * nn : 0,
+                                 qturn[i], s, dt, ca + i, cb + i, cm + i, cq + i);
+      n_child += hit[i];
+    }
+    if (nl + n_child > capacity) {
+      for (int64_t i = 0; i < nl; ++i) {
+        double* k = keep + (size_t)i * (2 * n + 2 + nn);
+        memcpy(R + (size_t)i * n, k, sizeof(double) * n);
+        memcpy(P + (size_t)i * n, k + n, sizeof(double) * n);
+        m[i] = k[2 * n];
+        phi[i] = k[2 * n + 1];
+        memcpy(U + (size_t)i * nn, k + 2 * n + 2, sizeof(double) * nn);
+      }
+      free(hit); free(ca); free(cb); free(cq); free(cm); free(keep);
+      return -2;
+    }
+    /* insert each child right after its parent: walk from the end so that
+     * every walker moves to its final place before its old slot is reused */
+    int64_t dst = nl + n_child;
+    for (int64_t i = nl - 1; i >= 0; --i) {
+      if (hit[i]) {
+        --dst;
+        memcpy(R + (size_t)dst * n, R + (size_t)i * n, sizeof(double) * n);
+        memcpy(P + (size_t)dst * n, P + (size_t)i * n, sizeof(double) * n);
+        memcpy(U + (size_t)dst * nn, U + (size_t)i * nn, sizeof(double) * nn);
+        m[dst] = cm[i];
+        phi[dst] = phi[i];
+        alpha[dst] = ca[i];
+        beta[dst] = cb[i];
+        qturn[dst] = cq[i];
+        id[dst] = child_id(seed, s, id[i]);
+        family[dst] = family[i];
+      }
+      --dst;
+      if (dst != i) {
+        memcpy(R + (size_t)dst * n, R + (size_t)i * n, sizeof(double) * n);
+        memcpy(P + (size_t)dst * n, P + (size_t)i * n, sizeof(double) * n);
+        memcpy(U + (size_t)dst * nn, U + (size_t)i * nn, sizeof(double) * nn);
+        m[dst] = m[i];
+        phi[dst] = phi[i];
+        alpha[dst] = alpha[i];
+        beta[dst] = beta[i];
+        qturn[dst] = qturn[i];
+        id[dst] = id[i];
+        family[dst] = family[i];
+      }
+    }
+    *n_live = nl + n_child;
+    free(hit); free(ca); free(cb); free(cq); free(cm); free(keep);
+  }
+  return 0;
+}
+
+void orc_spawn_observe(const orc_model* md, int64_t n0, int64_t n_live, const double* R,
+                       const double* m, const double* phi, const int32_t* alpha,
+                       const int32_t* beta, const double* U, const int32_t* qturn,
+                       const int64_t* family, double* row) {
+  int ns = md->n_states, nq = 4 * ns * ns;
+  double* q = (double*)malloc(sizeof(double) * (size_t)(n_live > 0 ? n_live : 1) * nq);
+  double* X = (double*)calloc((size_t)(n0 > 0 ? n0 : 1) * nq, sizeof(double));
+  orc_contrib(md, n_live, R, m, phi, alpha, beta, U, qturn, q);
+  for (int64_t i = 0; i < n_live; ++i) /* in walker order within each family */
+    for (int k = 0; k < nq; ++k) X[(size_t)family[i] * nq + k] += q[(size_t)i * nq + k];
+  int64_t size = 1;
+  while (size < n0) size *= 2;
+  for (int k = 0; k < nq; ++k) {
+    row[k] = (n0 > 0) ? pairwise(X + k, nq, 0, size, n0, 0) : 0.0;
+    row[nq + k] = (n0 > 0) ? pairwise(X + k, nq, 0, size, n0, 1) : 0.0;
+  }
+  free(q);
+  free(X);
+}
+
+int32_t orc_run_spawn(const orc_model* md, const orc_init* in, uint64_t seed, uint64_t traj_offset,
+                      int64_t n0, int64_t capacity, double dt, int64_t n_steps, int64_t out_stride,
+                      double* rows, int64_t* n_live_out) {
+  int n = md->n_modes, ns = md->n_states, nn = ns * ns, nrow = 8 * nn;
+  if (capacity < n0) return -2;
+  size_t c = (size_t)(capacity > 0 ? capacity : 1);
+  double* R = (double*)malloc(sizeof(double) * c * n);
+  double* P = (double*)malloc(sizeof(double) * c * n);
+  double* m = (double*)malloc(sizeof(double) * c);
+  double* phi = (double*)malloc(sizeof(double) * c);
+  int32_t* al = (int32_t*)malloc(sizeof(int32_t) * c);
+  int32_t* be = (int32_t*)malloc(sizeof(int32_t) * c);
+  double* U = (double*)calloc(c * nn, sizeof(double));
+  int32_t* qt = (int32_t*)malloc(sizeof(int32_t) * c);
+  uint64_t* id = (uint64_t*)malloc(sizeof(uint64_t) * c);
+  int64_t* fam = (int64_t*)malloc(sizeof(int64_t) * c);
+  int64_t nl = n0;
+  int32_t rc = orc_spawn_sample(md, in, seed, traj_offset, n0, R, P, m, phi, al, be, U, qt, id, fam);
+  if (rc == 0) {
+    orc_spawn_observe(md, n0, nl, R, m, phi, al, be, U, qt, fam, rows);
+    if (n_live_out) n_live_out[0] = nl;
+    for (int64_t s = 0; s < n_steps && rc == 0; ++s) {
+      rc = orc_spawn_advance(md, seed, capacity, &nl, R, P, m, phi, al, be, U, qt, id, fam, s, 1, dt);
+      if (rc == 0 && (s + 1) % out_stride == 0) {
+        orc_spawn_observe(md, n0, nl, R, m, phi, al, be, U, qt, fam,
+                          rows + (size_t)((s + 1) / out_stride) * nrow);
+        if (n_live_out) n_live_out[(s + 1) / out_stride] = nl;
+      }
+    }
+  }
+  free(R); free(P); free(m); free(phi); free(al); free(be); free(U); free(qt); free(id); free(fam);
+  return rc;
+}

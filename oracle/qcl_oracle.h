@@ -32,6 +32,7 @@ extern "C" {
  * stream definition that the GPU library follows too. */
 #define ORC_PURPOSE_INIT 1u
 #define ORC_PURPOSE_HOP 2u
+#define ORC_PURPOSE_SPAWN 3u
 
 /* Electronic basis of the walkers' index pairs (orc_model.repr).
  *
@@ -161,6 +162,53 @@ void orc_observe(const orc_model* md, int64_t n_traj, const double* R, const dou
 int32_t orc_run(const orc_model* md, const orc_init* in, uint64_t seed, uint64_t traj_offset,
                 int64_t n_traj, double dt, int64_t n_steps, int64_t out_stride, double* rows,
                 int64_t* n_deg);
+
+/* ------------------------------------------------------------- spawning --
+ * Trajectory spawning, the scheme of the CPU code that the paper's GPU version
+ * replaces (Sec. II B): the transition test of a step (the same Philox word and
+ * thresholds as without spawning) does not move the walker; when it fires for
+ * event e the walker spawns a child at e's target pair with weight
+ * m A_e / p_hat_e (diabatic: m c_e / p_hat_e and q + dq_e) and the same (R, P,
+ * phi, U), and the parent keeps its pair and weight -- no 1/(1 - sum p_hat)
+ * factor.  The expectation of parent plus child is (1 + dt L) m, as without
+ * spawning, but no weight grows by the stay factor; the walker count grows
+ * instead.
+ *
+ * Walker order: each child is inserted right after its parent, so the walkers
+ * descending from one initial walker (a family) stay contiguous; family[i] is
+ * that initial walker's index.  A child's random stream is keyed by the id
+ * made of words 0 and 1 of Philox block (c0 = step, parent id, purpose SPAWN)
+ * with bit 63 set (initial walkers: traj_offset + index).  Observables are the
+ * sums over families of the family sums X_k and of X_k^2, so the standard error
+ * counts the n0 independent families, not the correlated walkers. */
+
+/* Initial spawning ensemble of n0 walkers (arrays of capacity >= n0 walkers). */
+int32_t orc_spawn_sample(const orc_model* md, const orc_init* in, uint64_t seed,
+                         uint64_t traj_offset, int64_t n0, double* R, double* P, double* m,
+                         double* phi, int32_t* alpha, int32_t* beta, double* U, int32_t* qturn,
+                         uint64_t* id, int64_t* family);
+
+/* Advances the *n_live walkers by n_steps from absolute step step0.  Returns
+ * 0, or -2 if a step would exceed capacity (the ensemble is left at the end of
+ * the previous step and *n_live unchanged by that step). */
+int32_t orc_spawn_advance(const orc_model* md, uint64_t seed, int64_t capacity, int64_t* n_live,
+                          double* R, double* P, double* m, double* phi, int32_t* alpha,
+                          int32_t* beta, double* U, int32_t* qturn, uint64_t* id,
+                          int64_t* family, int64_t step0, int64_t n_steps, double dt);
+
+/* row[k] = sum over families of X_k, row[4NS^2 + k] = sum of X_k^2 (pairwise
+ * over the n0 families), X_k = the family's sum of the contributions of
+ * orc_contrib. */
+void orc_spawn_observe(const orc_model* md, int64_t n0, int64_t n_live, const double* R,
+                       const double* m, const double* phi, const int32_t* alpha,
+                       const int32_t* beta, const double* U, const int32_t* qturn,
+                       const int64_t* family, double* row);
+
+/* Whole spawning run: rows as orc_run, n_live_out[k] = live walkers at output k.
+ * Returns -2 on capacity overflow. */
+int32_t orc_run_spawn(const orc_model* md, const orc_init* in, uint64_t seed, uint64_t traj_offset,
+                      int64_t n0, int64_t capacity, double dt, int64_t n_steps, int64_t out_stride,
+                      double* rows, int64_t* n_live_out);
 
 #ifdef __cplusplus
 }
