@@ -146,6 +146,7 @@ typedef struct {
 #define QCL_FLAG_NONFINITE 1u
 #define QCL_FLAG_DEGENERATE 2u
 #define QCL_FLAG_STEP_MISMATCH 4u
+#define QCL_FLAG_SPAWN_OVERFLOW 8u
 
 /* Message for the last failing call on this thread ("" if none). */
 const char* qcl_last_error(void);
@@ -279,6 +280,64 @@ qcl_status qcl_shard_tile_walkers(const qcl_model* model, int32_t precision, int
  * two) of shard_sums[s * n_elems + i], shards in walker order. */
 qcl_status qcl_combine_shards(const double* shard_sums, int32_t n_shards, int64_t n_elems,
                               double* out);
+
+/* ---------------------------------------------------------------------------
+ * Trajectory spawning (FP64, two-state models, either representation).
+ *
+ * The scheme of the CPU code that the paper's GPU version replaces (Sec. II B:
+ * there a new trajectory was started each time a transition test fired, so
+ * the walker count was not fixed).  Each step a walker runs the same
+ * deterministic step and
+ * transition test as in qcl_propagate, but a fired test does not move it: it
+ * keeps its pair and weight and spawns a child at the event's target pair
+ * with weight m A_e / p_hat_e (diabatic: with the event's quarter turns) and
+ * the parent's (R, P, phi); no 1/(1 - sum p_hat) factor is applied.  Children
+ * are inserted right after their parents (deterministic count / scan /
+ * scatter), so results are reproducible bit for bit and the walkers descending
+ * from one initial walker (its family) stay contiguous.  A child's random
+ * stream is keyed by words 0-1 of Philox block (c0 = step, parent id, purpose
+ * 3) with bit 63 set.
+ *
+ * ens->n_traj is the number n0 of initial walkers (families); capacity is the
+ * walker slots the buffer holds (n0 <= capacity <= 2^36).  The observation
+ * buffer is sized by qcl_obs_bytes(model, ens, n_out) as for any FP64
+ * ensemble; its rows hold, per output, the sums over families of the family
+ * sums X_k of the walker contributions and of X_k^2, so qcl_reduce_observables
+ * gives means over n0 and standard errors over independent families.  When a
+ * step's children would exceed capacity they are dropped and
+ * QCL_FLAG_SPAWN_OVERFLOW is set in the status: every later result of that
+ * ensemble is invalid.  Buffers are caller-owned and 256-byte aligned.
+ * ------------------------------------------------------------------------ */
+
+/* Bytes of a spawning ensemble buffer (header, two walker sets of capacity
+ * slots, per-parent staging, scan scratch, family starts). */
+qcl_status qcl_spawn_bytes(const qcl_model* model, const qcl_ensemble_desc* ens, int64_t capacity,
+                           size_t* bytes);
+
+/* Byte offsets within the buffer of walker set `set` (0 or 1; the current set
+ * is the ensemble's step & 1): offsets[0..6] = R [n_modes][capacity] (double),
+ * P (same), m (double), phi (double), index pair (uint16: a | q << 4 | b << 8),
+ * random-stream id (uint64), family (uint32); offsets[7] = total bytes. */
+qcl_status qcl_spawn_layout(const qcl_model* model, const qcl_ensemble_desc* ens, int64_t capacity,
+                            int32_t set, size_t offsets[8]);
+
+/* Samples the n0 initial walkers into set 0 (as qcl_sample_initial; ids
+ * traj_id_offset + i, family i). */
+qcl_status qcl_spawn_sample(const qcl_model* model, const qcl_ensemble_desc* ens,
+                            const qcl_init_desc* init, int64_t capacity, void* buf, size_t bytes,
+                            void* stream);
+
+/* Advances the spawning ensemble by n_steps from absolute step step0 (< 2^32
+ * in total), observing at every absolute step that is a multiple of
+ * out_stride (and at step 0 when step0 == 0).  Arguments as qcl_propagate. */
+qcl_status qcl_spawn_propagate(const qcl_model* model, const qcl_ensemble_desc* ens,
+                               int64_t capacity, void* buf, size_t bytes, int64_t step0,
+                               int64_t n_steps, double dt, int32_t out_stride, void* obs_buf,
+                               size_t obs_bytes, int64_t n_out, void* stream);
+
+/* Live walkers of the current set (synchronises the stream). */
+qcl_status qcl_spawn_live(const qcl_model* model, const qcl_ensemble_desc* ens, int64_t capacity,
+                          const void* buf, int64_t* n_live, void* stream);
 
 /* ---------------------------------------------------------------- serving
  * A request loop for many solves of different models, walker counts and step

@@ -114,6 +114,78 @@ constexpr int kPackedBuckets = 6;
 // the grid size.
 int launch_packed(int bucket, int kind, const PackedTable* dtab, cudaStream_t st);
 
+// ------------------------------------------------------------- spawning --
+// Buffer of a spawning ensemble (FP64, two states): the common header (its
+// n_traj = the n0 initial walkers = families) with SpawnHeader after it, then
+// two walker sets of `capacity` slots (the current set alternates with the
+// absolute step: set = step & 1), per-parent staging of the children of a
+// step, per-block spawn counts and offsets, and the family start indices.
+struct SpawnHeader {
+  int64_t capacity;
+  int64_t n0;
+  int64_t n_live[2];  // live walkers of set 0 and set 1
+  int32_t drop;       // set by the scan when a step's children do not fit
+  int32_t pad;
+};
+constexpr size_t kSpawnHeaderOff = 64;  // after EnsHeader, inside the first 256 bytes
+
+struct SpawnLayout {
+  // walker set: R[n][cap], P[n][cap], m, phi, ab, id (uint64), fam (uint32)
+  size_t set_off[2];
+  size_t R, P, m, phi, ab, id, fam, set_bytes;
+  size_t cm, cab, flag, bsum, boff, fstart, total;
+  int64_t n_blocks;  // capacity / 256, rounded up
+  __host__ __device__ static SpawnLayout make(int64_t cap, int n, int64_t n0) {
+    SpawnLayout L{};
+    const size_t c = (size_t)cap;
+    size_t o = 0;
+    L.R = o;
+    o = align256(o + 8 * c * (size_t)n);
+    L.P = o;
+    o = align256(o + 8 * c * (size_t)n);
+    L.m = o;
+    o = align256(o + 8 * c);
+    L.phi = o;
+    o = align256(o + 8 * c);
+    L.ab = o;
+    o = align256(o + 2 * c);
+    L.id = o;
+    o = align256(o + 8 * c);
+    L.fam = o;
+    o = align256(o + 4 * c);
+    L.set_bytes = o;
+    L.set_off[0] = 256;
+    L.set_off[1] = 256 + L.set_bytes;
+    o = 256 + 2 * L.set_bytes;
+    L.cm = o;
+    o = align256(o + 8 * c);
+    L.cab = o;
+    o = align256(o + 2 * c);
+    L.flag = o;
+    o = align256(o + c);
+    L.n_blocks = (cap + 255) / 256;
+    L.bsum = o;
+    o = align256(o + 4 * (size_t)L.n_blocks);
+    L.boff = o;
+    o = align256(o + 8 * (size_t)L.n_blocks);
+    L.fstart = o;
+    o = align256(o + 8 * ((size_t)n0 + 1));
+    L.total = o;
+    return L;
+  }
+};
+
+void launch_spawn_sample(const DevModel* dm, const SampleParams& sp, int64_t capacity, void* buf,
+                         cudaStream_t st);
+// One spawning step (step kernel, scan, scatter) from set step & 1 to the other.
+void launch_spawn_step(const DevModel* dm, int repr, void* buf, int64_t capacity, int n,
+                       int64_t n0, int64_t step0, int64_t step, double dt, uint64_t seed,
+                       cudaStream_t st);
+// Family sums of the current set (set) into per-tile partials (tiles of 256
+// families).
+void launch_spawn_observe(const DevModel* dm, const void* buf, int64_t capacity, int n, int64_t n0,
+                          int set, double* part, cudaStream_t st);
+
 // Kernel launches issued by the library (instrumentation).
 void launches_add(int64_t k);
 int64_t launches_read(bool reset);

@@ -3,6 +3,7 @@
 // sequences of the FP64 comparator and the FP32-bulk persistent path.
 #include <cmath>
 #include <cstdarg>
+#include <cstddef>
 #include <cstdio>
 #include <cstring>
 #include <mutex>
@@ -289,15 +290,14 @@ qcl_status qcl_obs_bytes(const qcl_model* model, const qcl_ensemble_desc* ens, i
   return ok();
 }
 
-qcl_status qcl_sample_initial(const qcl_model* model, const qcl_ensemble_desc* ens, const qcl_init_desc* init,
-                              void* ens_buf, size_t ens_bytes, void* stream) {
-  qcl_status st = check_ens(model, ens);
-  if (st) return st;
+}  // extern "C"
+
+namespace {
+// Validates an initial condition and builds the sampling parameters.
+qcl_status prepare_sample(const qcl_model* model, const qcl_ensemble_desc* ens, const qcl_init_desc* init,
+                          SampleParams** out) {
+  *out = nullptr;
   if (!init || !init->rho_el0 || !init->R0 || !init->P0) return fail(QCL_ERR_INVALID_ARG, "init descriptor or one of its arrays is NULL");
-  if (!ens_buf) return fail(QCL_ERR_INVALID_ARG, "ens_buf is NULL");
-  if (((uintptr_t)ens_buf & 255) != 0) return fail(QCL_ERR_INVALID_ARG, "ens_buf must be 256-byte aligned");
-  const size_t need = EnsLayout::make(ens->n_traj, model->ns, model->n, ens->precision).total;
-  if (ens_bytes < need) return fail(QCL_ERR_OUT_OF_MEMORY, "ens_buf has %zu bytes, needs %zu", ens_bytes, need);
   const int ns = model->ns, n = model->n;
   if (!finite_all(init->rho_el0, (size_t)ns * ns) || !symmetric(init->rho_el0, ns)) return fail(QCL_ERR_INVALID_ARG, "rho_el0 must be finite and symmetric");
   bool nz = false;
@@ -322,6 +322,25 @@ qcl_status qcl_sample_initial(const qcl_model* model, const qcl_ensemble_desc* e
     sp->sP[j] = std::sqrt(0.5 * hb * M * w * cth);
   }
   for (int k = 0; k < ns * ns; ++k) sp->rho[k] = init->rho_el0[k];
+  *out = sp;
+  return QCL_OK;
+}
+}  // namespace
+
+extern "C" {
+
+qcl_status qcl_sample_initial(const qcl_model* model, const qcl_ensemble_desc* ens, const qcl_init_desc* init,
+                              void* ens_buf, size_t ens_bytes, void* stream) {
+  qcl_status st = check_ens(model, ens);
+  if (st) return st;
+  if (!ens_buf) return fail(QCL_ERR_INVALID_ARG, "ens_buf is NULL");
+  if (((uintptr_t)ens_buf & 255) != 0) return fail(QCL_ERR_INVALID_ARG, "ens_buf must be 256-byte aligned");
+  const size_t need = EnsLayout::make(ens->n_traj, model->ns, model->n, ens->precision).total;
+  if (ens_bytes < need) return fail(QCL_ERR_OUT_OF_MEMORY, "ens_buf has %zu bytes, needs %zu", ens_bytes, need);
+  SampleParams* sp = nullptr;
+  st = prepare_sample(model, ens, init, &sp);
+  if (st) return st;
+  const int ns = model->ns;
   cudaStream_t s = (cudaStream_t)stream;
   if (ns > 2)
     launch_sampleN(model->dev, *sp, ens_buf, ens->precision, s);
@@ -538,6 +557,130 @@ qcl_status qcl_ensemble_status(const qcl_model* model, const qcl_ensemble_desc* 
   out->reserved = 0;
   out->n_degenerate = h.n_degenerate;
   out->n_nonfinite = h.n_nonfinite;
+  return ok();
+}
+
+// ------------------------------------------------------------- spawning --
+}  // extern "C"
+
+namespace {
+qcl_status check_spawn(const qcl_model* m, const qcl_ensemble_desc* e, int64_t capacity) {
+  qcl_status st = check_ens(m, e);
+  if (st) return st;
+  if (e->precision != QCL_PREC_FP64) return fail(QCL_ERR_UNSUPPORTED, "spawning ensembles are FP64");
+  if (m->ns != 2) return fail(QCL_ERR_UNSUPPORTED, "spawning takes two-state models (n_states = %d)", m->ns);
+  if (e->n_traj >= ((int64_t)1 << 31)) return fail(QCL_ERR_INVALID_ARG, "n_traj must be below 2^31 for a spawning ensemble");
+  if (capacity < e->n_traj || capacity > ((int64_t)1 << 36))
+    return fail(QCL_ERR_INVALID_ARG, "capacity %lld outside [n_traj, 2^36]", (long long)capacity);
+  return QCL_OK;
+}
+}  // namespace
+
+extern "C" {
+
+qcl_status qcl_spawn_bytes(const qcl_model* model, const qcl_ensemble_desc* ens, int64_t capacity, size_t* bytes) {
+  if (!bytes) return fail(QCL_ERR_INVALID_ARG, "bytes is NULL");
+  qcl_status st = check_spawn(model, ens, capacity);
+  if (st) return st;
+  *bytes = SpawnLayout::make(capacity, model->n, ens->n_traj).total;
+  return ok();
+}
+
+qcl_status qcl_spawn_layout(const qcl_model* model, const qcl_ensemble_desc* ens, int64_t capacity, int32_t set,
+                            size_t offsets[8]) {
+  if (!offsets) return fail(QCL_ERR_INVALID_ARG, "offsets is NULL");
+  qcl_status st = check_spawn(model, ens, capacity);
+  if (st) return st;
+  if (set != 0 && set != 1) return fail(QCL_ERR_INVALID_ARG, "set must be 0 or 1");
+  const SpawnLayout L = SpawnLayout::make(capacity, model->n, ens->n_traj);
+  const size_t b = L.set_off[set];
+  offsets[0] = b + L.R;
+  offsets[1] = b + L.P;
+  offsets[2] = b + L.m;
+  offsets[3] = b + L.phi;
+  offsets[4] = b + L.ab;
+  offsets[5] = b + L.id;
+  offsets[6] = b + L.fam;
+  offsets[7] = L.total;
+  return ok();
+}
+
+qcl_status qcl_spawn_sample(const qcl_model* model, const qcl_ensemble_desc* ens, const qcl_init_desc* init,
+                            int64_t capacity, void* buf, size_t bytes, void* stream) {
+  qcl_status st = check_spawn(model, ens, capacity);
+  if (st) return st;
+  if (!buf) return fail(QCL_ERR_INVALID_ARG, "buf is NULL");
+  if (((uintptr_t)buf & 255) != 0) return fail(QCL_ERR_INVALID_ARG, "buf must be 256-byte aligned");
+  const size_t need = SpawnLayout::make(capacity, model->n, ens->n_traj).total;
+  if (bytes < need) return fail(QCL_ERR_OUT_OF_MEMORY, "buf has %zu bytes, needs %zu", bytes, need);
+  SampleParams* sp = nullptr;
+  st = prepare_sample(model, ens, init, &sp);
+  if (st) return st;
+  launch_spawn_sample(model->dev, *sp, capacity, buf, (cudaStream_t)stream);
+  delete sp;
+  st = check_launch("spawn sample");
+  return st ? st : ok();
+}
+
+qcl_status qcl_spawn_propagate(const qcl_model* model, const qcl_ensemble_desc* ens, int64_t capacity, void* buf,
+                               size_t bytes, int64_t step0, int64_t n_steps, double dt, int32_t out_stride,
+                               void* obs_buf, size_t obs_bytes, int64_t n_out, void* stream) {
+  qcl_status st = check_spawn(model, ens, capacity);
+  if (st) return st;
+  if (!buf || !obs_buf) return fail(QCL_ERR_INVALID_ARG, "buf or obs_buf is NULL");
+  if (((uintptr_t)buf & 255) != 0 || ((uintptr_t)obs_buf & 255) != 0) return fail(QCL_ERR_INVALID_ARG, "buffers must be 256-byte aligned");
+  if (step0 < 0 || n_steps < 0) return fail(QCL_ERR_INVALID_ARG, "step0 and n_steps must be >= 0");
+  if (step0 + n_steps >= ((int64_t)1 << 32)) return fail(QCL_ERR_INVALID_ARG, "absolute step beyond 2^32");
+  if (!(dt > 0.0) || !std::isfinite(dt)) return fail(QCL_ERR_INVALID_ARG, "dt must be positive");
+  if (out_stride < 1) return fail(QCL_ERR_INVALID_ARG, "out_stride must be >= 1");
+  if (n_out < 1) return fail(QCL_ERR_INVALID_ARG, "n_out must be >= 1");
+  const int64_t k_last = (step0 + n_steps) / out_stride;
+  if (k_last >= n_out) return fail(QCL_ERR_INVALID_ARG, "output row %lld beyond n_out = %lld", (long long)k_last, (long long)n_out);
+  const SpawnLayout SL = SpawnLayout::make(capacity, model->n, ens->n_traj);
+  if (bytes < SL.total) return fail(QCL_ERR_OUT_OF_MEMORY, "buf has %zu bytes, needs %zu", bytes, SL.total);
+  const ObsLayout OL = ObsLayout::make(ens->n_traj, model->ns, n_out, tile_walkers(QCL_PREC_FP64, model->n, model->ns));
+  if (obs_bytes < OL.total) return fail(QCL_ERR_OUT_OF_MEMORY, "obs_buf has %zu bytes, needs %zu", obs_bytes, OL.total);
+  cudaStream_t s = (cudaStream_t)stream;
+  char* ob = (char*)obs_buf;
+  double* rows = (double*)(ob + OL.off_rows);
+  double* part = (double*)(ob + OL.off_part);
+  double* fold = (double*)(ob + OL.off_fold);
+  const int q2 = OL.q2;
+  const int64_t n0 = ens->n_traj;
+  auto observe = [&](double* row, int64_t step) {
+    launch_spawn_observe(model->dev, buf, capacity, model->n, n0, (int)(step & 1), part, s);
+    launch_fold(part, row, fold, OL.n_tiles, q2, 1, s);
+  };
+  if (step0 == 0) observe(rows, 0);
+  for (int64_t t = step0; t < step0 + n_steps; ++t) {
+    {
+      TimedLaunch tl(1, s);
+      launch_spawn_step(model->dev, model->host.repr, buf, capacity, model->n, n0, step0, t, dt, ens->seed, s);
+    }
+    if ((t + 1) % out_stride == 0) observe(rows + (size_t)((t + 1) / out_stride) * q2, t + 1);
+  }
+  st = check_launch("spawn step");
+  if (st) return st;
+  launch_header_finish(buf, step0, step0 + n_steps, s);
+  st = check_launch("header");
+  return st ? st : ok();
+}
+
+qcl_status qcl_spawn_live(const qcl_model* model, const qcl_ensemble_desc* ens, int64_t capacity, const void* buf,
+                          int64_t* n_live, void* stream) {
+  qcl_status st = check_spawn(model, ens, capacity);
+  if (st) return st;
+  if (!buf || !n_live) return fail(QCL_ERR_INVALID_ARG, "buf or n_live is NULL");
+  struct {
+    EnsHeader h;
+    SpawnHeader s;
+  } hs;
+  static_assert(offsetof(decltype(hs), s) == kSpawnHeaderOff, "spawn header offset");
+  cudaStream_t s = (cudaStream_t)stream;
+  CUDA_TRY(cudaMemcpyAsync(&hs, buf, sizeof(hs), cudaMemcpyDeviceToHost, s));
+  CUDA_TRY(cudaStreamSynchronize(s));
+  if (hs.h.magic != kEnsMagic) return fail(QCL_ERR_INVALID_ARG, "buf holds no sampled ensemble");
+  *n_live = hs.s.n_live[hs.h.step & 1];
   return ok();
 }
 

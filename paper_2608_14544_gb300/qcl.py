@@ -34,7 +34,10 @@ EXPORTS = [
     "qcl_read_sums", "qcl_ensemble_status", "qcl_propagate_noalloc",
     "qcl_server_create", "qcl_server_submit", "qcl_server_poll", "qcl_server_wait",
     "qcl_server_stats", "qcl_server_destroy", "qcl_shard_tile_walkers", "qcl_combine_shards",
+    "qcl_spawn_bytes", "qcl_spawn_layout", "qcl_spawn_sample", "qcl_spawn_propagate",
+    "qcl_spawn_live",
 ]
+FLAG_SPAWN_OVERFLOW = 8
 REQ_QUEUED, REQ_RUNNING, REQ_DONE, REQ_ERROR = 0, 1, 2, 3
 
 
@@ -139,6 +142,12 @@ def load(path: str = LIB_PATH):
     lib.qcl_server_wait.argtypes = [vp, i64, C.c_double, vp]
     lib.qcl_server_stats.argtypes = [vp, vp]
     lib.qcl_server_destroy.argtypes = [vp]
+    lib.qcl_spawn_bytes.argtypes = [vp, vp, i64, vp]
+    lib.qcl_spawn_layout.argtypes = [vp, vp, i64, i32, vp]
+    lib.qcl_spawn_sample.argtypes = [vp, vp, vp, i64, vp, sz, vp]
+    lib.qcl_spawn_propagate.argtypes = [vp, vp, i64, vp, sz, i64, i64, C.c_double, i32, vp, sz,
+                                        i64, vp]
+    lib.qcl_spawn_live.argtypes = [vp, vp, i64, vp, vp, vp]
     for name in EXPORTS:
         f = getattr(lib, name)
         if name not in ("qcl_last_error", "qcl_version"):
@@ -384,6 +393,79 @@ class Run:
                 "alpha": (arr(off[6], nt, np.uint16, 2) & 0xF).astype(np.int32),
                 "q": ((arr(off[6], nt, np.uint16, 2) >> 4) & 0x3).astype(np.int32),
                 "beta": (arr(off[6], nt, np.uint16, 2) >> 8).astype(np.int32), **extra}
+
+
+# ----------------------------------------------------------------- spawning --
+class SpawnRun:
+    """A trajectory-spawning ensemble (FP64, two states): n0 initial walkers
+    (families) in a buffer of `capacity` walker slots."""
+
+    def __init__(self, model: Model, n0: int, capacity: int, seed: int, n_out: int,
+                 traj_id_offset: int = 0, device="cuda"):
+        self.model = model
+        self.capacity = int(capacity)
+        self.ens = ens_desc(n0, seed, PREC_FP64, traj_id_offset)
+        self.n_out = n_out
+        b = C.c_size_t()
+        _check(load().qcl_spawn_bytes(model.handle, C.byref(self.ens), self.capacity, C.byref(b)),
+               "qcl_spawn_bytes")
+        self.buf = device_buffer(b.value, device)
+        self.obs_buf = device_buffer(obs_bytes(model, self.ens, n_out), device)
+        self.step = 0
+
+    def sample(self, init: dict, stream=None):
+        d, keep = _init_desc(init)
+        _check(load().qcl_spawn_sample(self.model.handle, C.byref(self.ens), C.byref(d),
+                                       self.capacity, _dptr(self.buf), self.buf.numel(),
+                                       _stream_ptr(stream)), "qcl_spawn_sample")
+        self.step = 0
+
+    def propagate(self, n_steps: int, dt: float, out_stride: int, stream=None):
+        _check(load().qcl_spawn_propagate(self.model.handle, C.byref(self.ens), self.capacity,
+                                          _dptr(self.buf), self.buf.numel(), self.step,
+                                          n_steps, dt, out_stride, _dptr(self.obs_buf),
+                                          self.obs_buf.numel(), self.n_out,
+                                          _stream_ptr(stream)), "qcl_spawn_propagate")
+        self.step += n_steps
+
+    def n_live(self, stream=None) -> int:
+        v = C.c_int64()
+        _check(load().qcl_spawn_live(self.model.handle, C.byref(self.ens), self.capacity,
+                                     _dptr(self.buf), C.byref(v), _stream_ptr(stream)),
+               "qcl_spawn_live")
+        return v.value
+
+    def observables(self, stream=None) -> np.ndarray:
+        return reduce_observables(self.model, self.ens, self.obs_buf, self.n_out, stream=stream)
+
+    def sums(self, stream=None) -> np.ndarray:
+        return read_sums(self.model, self.ens, self.obs_buf, self.n_out, stream=stream)
+
+    def status(self, stream=None) -> dict:
+        return ensemble_status(self.model, self.ens, self.buf, stream)
+
+    def state(self) -> dict:
+        """Host copy of the live walkers of the current set, in walker order."""
+        import torch
+
+        torch.cuda.synchronize()
+        nl, n, cap = self.n_live(), self.model.n, self.capacity
+        off = (C.c_size_t * 8)()
+        _check(load().qcl_spawn_layout(self.model.handle, C.byref(self.ens), cap, self.step & 1,
+                                       off), "qcl_spawn_layout")
+        raw = self.buf.cpu().numpy()
+
+        def arr(o, count, dtype, width):
+            return np.frombuffer(raw[o:o + width * count].tobytes(), dtype=dtype).copy()
+
+        R = arr(off[0], n * cap, np.float64, 8).reshape(n, cap)[:, :nl].T.copy()
+        P = arr(off[1], n * cap, np.float64, 8).reshape(n, cap)[:, :nl].T.copy()
+        ab = arr(off[4], nl, np.uint16, 2)
+        return {"R": R, "P": P, "m": arr(off[2], nl, np.float64, 8),
+                "phi": arr(off[3], nl, np.float64, 8),
+                "alpha": (ab & 0xF).astype(np.int32), "q": ((ab >> 4) & 0x3).astype(np.int32),
+                "beta": (ab >> 8).astype(np.int32), "id": arr(off[5], nl, np.uint64, 8),
+                "family": arr(off[6], nl, np.uint32, 4).astype(np.int64)}
 
 
 # ------------------------------------------------------------------- shards --
