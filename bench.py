@@ -97,6 +97,47 @@ def _result_summary(obs, cfg, status):
             "status_flags": status["flags"]}
 
 
+def spawning_leg(qcl, torch, n0: int, steps: int, stride: int):
+    """Trajectory spawning (the CPU code's scheme) against the fixed no-spawn
+    ensemble on the 1-mode spin-boson model: the standard error of the upper
+    adiabatic population at t = steps dt, the walker-steps each scheme spent,
+    and the variance x walker-steps product (lower is better; equal cost
+    compares SE^2 directly).  Both FP64, same seed."""
+    cfg = wl.config(1)
+    dt = cfg["dt"]
+    m = qcl.Model(cfg["model"])
+    cap = 64 * n0
+    sp = qcl.SpawnRun(m, n0, cap, cfg["seed"], steps // stride + 1)
+    sp.sample(cfg["init"])
+    live = [sp.n_live()]
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(steps // stride):
+        sp.propagate(stride, dt, stride)
+        live.append(sp.n_live())
+    torch.cuda.synchronize()
+    t_spawn = time.perf_counter() - t0
+    ws_spawn = float(sum(0.5 * (live[k] + live[k + 1]) * stride for k in range(len(live) - 1)))
+    o_s = sp.observables()
+    flags = sp.status()["flags"]
+    ns = qcl.Run(m, n0, cfg["seed"], qcl.PREC_FP64, steps // stride + 1)
+    ns.sample(cfg["init"])
+    ns.propagate(steps, dt, stride)
+    o_n = ns.observables()
+    ws_ns = float(n0) * steps
+    se_s, se_n = float(o_s[-1, 16 + 14]), float(o_n[-1, 16 + 14])
+    return {"workload": f"1-mode spin-boson (cfg 1 model), {n0} initial walkers, {steps} steps "
+                        f"(t = {steps * dt:g}), FP64",
+            "P_ad_upper": {"spawn": float(o_s[-1, 14]), "no_spawn": float(o_n[-1, 14])},
+            "se_P_ad_upper": {"spawn": se_s, "no_spawn": se_n},
+            "walker_steps": {"spawn": ws_spawn, "no_spawn": ws_ns},
+            "final_walkers": live[-1],
+            "variance_x_walker_steps": {"spawn": se_s ** 2 * ws_spawn,
+                                        "no_spawn": se_n ** 2 * ws_ns},
+            "spawn_walker_steps_per_s": ws_spawn / t_spawn,
+            "status_flags": flags}
+
+
 def served_mix_leg(qcl, n_requests: int, traj_hi: float, arena_gb: float, quantum: int):
     """Poisson-arriving requests (mean gap 5 ms) drawn uniformly from the
     1-mode, 3-mode, 3-mode vibronic and 100-mode models and a random 4-state
@@ -406,6 +447,9 @@ def run_ours(args):
     std = rd.status()
     del rd
 
+    spawning = spawning_leg(qcl, torch, args.spawn_walkers, 400, 20) if args.spawn_walkers > 0 \
+        else None
+
     served = None
     if args.served_requests > 0 and rank == 0:
         served = served_mix_leg(qcl, args.served_requests, args.served_traj_max,
@@ -477,6 +521,7 @@ def run_ours(args):
                                  "representation (propagation only)",
                      "value": rate_dia, "unit": "traj-steps/s", "kernel": "k_bulk2_dia",
                      "status_flags": std["flags"]},
+        "spawning": spawning,
         "served_mix": served,
         "clocks": clocks,
         "result": _result_summary(obs, cfg, status),
@@ -494,6 +539,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--sb100-walkers", type=int, default=2_000_000)
+    ap.add_argument("--spawn-walkers", type=int, default=100_000)
     ap.add_argument("--served-requests", type=int, default=256)
     ap.add_argument("--served-traj-max", type=float, default=1e6)
     ap.add_argument("--served-arena-gb", type=float, default=48.0)
