@@ -40,15 +40,20 @@ def _workload_desc(cfg):
 
 
 def flops_per_traj_step(model: dict) -> float:
-    """Algorithmic FP32 flops of one walker step of a two-state model: per mode
-    two half kicks, a drift and the collective sums (7 FMA for the spin-boson
-    form, 11 FMA + 2 ADD for the general two-state form), plus 20 scalar flops."""
+    """Algorithmic FP32 flops of one walker step of a two-state model, the
+    per-unit figure of the hot-path scope: per mode a drift, the collective
+    coordinate sum, a (merged) kick of two FMA and the coupling sum -- 5 FMA =
+    10 flops for the spin-boson form, about 12 with the second collective of
+    the general two-state form -- plus about 20 scalar FP32 flops and 6 for the
+    compensated phase addition.  The kernel itself issues 7 FMA per mode (two
+    unmerged half kicks, see the kernel notes), so this count is below the
+    flops it executes."""
     K = model["K"]
     s = 0.5 * (K[:, 0, 0] + K[:, 1, 1])
     b = K[:, 0, 1]
     general = bool(np.any(s != 0) or np.any(b != 0))
-    per_mode = 24.0 if general else 14.0
-    return per_mode * model["n_modes"] + 20.0
+    per_mode = 12.0 if general else 10.0
+    return per_mode * model["n_modes"] + 26.0
 
 
 def kernel_source_hash(paths) -> str:
