@@ -116,12 +116,16 @@ struct Scal {
   float c2, s2;          // cos 2theta, sin 2theta (theta = 0 at r = 0)
 };
 
+// cos 2theta = a / r, sin 2theta = b / r.  r^2 is floored at the smallest
+// normal float, so at an exact degeneracy (a = b = 0 in FP32, where the angle
+// is undefined and the coupling is set to zero) both come out 0 -- the mean of
+// the two branches -- instead of a division by zero.
 __device__ __forceinline__ void closed_form(Scal& z) {
   z.r2 = __fmaf_rn(z.A, z.A, z.B * z.B);
-  z.ir = rsqrtf(z.r2);
+  z.ir = rsqrtf(fmaxf(z.r2, 0x1p-126f));
   z.r = z.r2 * z.ir;
-  z.c2 = z.r2 > 0.0f ? z.A * z.ir : 1.0f;
-  z.s2 = z.r2 > 0.0f ? z.B * z.ir : 0.0f;
+  z.c2 = z.A * z.ir;
+  z.s2 = z.B * z.ir;
 }
 
 // m *= num / den (den an integer below 2^25, so exact in FP32) as a
@@ -156,10 +160,12 @@ __device__ __forceinline__ void phase_and_transition(Scal& z, float r_old, float
   const f2 ps = two_sum(z.ph.hi, bp.hdt_hbar * (z.sa - z.sb) * (r_old + z.r));
   z.ph = {ps.hi, z.ph.lo + ps.lo};
   // coupling contracted with P/M: g = (a Bv - b Av) / (2 r^2)
-  const bool degen = 2.0f * z.r < kDegTol32;
+  // (2 r < tol, compared as r^2 < tol^2 / 4)
+  const bool degen = z.r2 < 0.25f * kDegTol32 * kDegTol32;
   deg += degen ? 1u : 0u;
-  const float gn = (KIND == 1) ? (z.A * Bv - z.B * Av) : -(z.B * Av);
-  const float g = degen ? 0.0f : gn * (0.5f * z.ir * z.ir);
+  // the spin-boson form has b = b0: -b/2 is a per-launch constant
+  const float gn = (KIND == 1) ? 0.5f * (z.A * Bv - z.B * Av) : (-0.5f * bp.b0) * Av;
+  const float g = degen ? 0.0f : gn * (z.ir * z.ir);
   // both events have |A_e| = dt |g|: p = min(kappa dt |g|, p_max) quantised to
   // 24-bit thresholds T = floor(p 2^24); when 2T exceeds Tmax = floor(p_max 2^24)
   // the integer rescale floor(T Tmax / 2T) gives floor(Tmax / 2), so
@@ -231,11 +237,13 @@ __device__ __forceinline__ void contributions(const Scal& z, float mm, float (&v
   float sphi, cphi;
   __sincosf(x, &sphi, &cphi);
   // eigenvector angle theta from (cos 2theta, sin 2theta), half-angle form
-  // without cancellation: the larger of cos/sin is sqrt((1 + |cos2t|)/2)
-  const float t = __fmaf_rn(0.5f, fabsf(z.c2), 0.5f);
+  // without cancellation: the larger of cos/sin is sqrt((1 + |cos2t|)/2); at an
+  // exact degeneracy (both 0) theta = 0
+  const float c2 = (z.c2 == 0.0f && z.s2 == 0.0f) ? 1.0f : z.c2;
+  const float t = __fmaf_rn(0.5f, fabsf(c2), 0.5f);
   const float rt = rsqrtf(t);
   const float big = t * rt, small = 0.5f * fabsf(z.s2) * rt;
-  const bool cpos = z.c2 >= 0.0f;
+  const bool cpos = c2 >= 0.0f;
   const float c = cpos ? big : small;
   const float s = copysignf(cpos ? small : big, z.s2);
   const bool al = z.sa > 0.0f, be = z.sb > 0.0f;
