@@ -320,6 +320,9 @@ def run_ours(args):
     n, steps, stride, dt = cfg["n_traj"], cfg["n_steps"], cfg["out_stride"], cfg["dt"]
     n_out = steps // stride + 1
     model = qcl.Model(cfg["model"])
+    # launch shape (walkers per thread, blocks per SM) picked by the library's
+    # autotuner on a probe ensemble -- setup, outside every timed region
+    shape = model.autotune(dt, stride)
     run = qcl.Run(model, n, cfg["seed"], qcl.PREC_FP32_BULK, n_out, traj_id_offset=rank * n)
     stream = torch.cuda.current_stream()
 
@@ -389,6 +392,7 @@ def run_ours(args):
     t0 = time.perf_counter()
     for _ in range(args.steps):
         mm = qcl.Model(m)
+        mm.set_launch_shape(shape["walkers_per_thread"], shape["blocks_per_sm"])
         rr = qcl.Run(mm, n, cfg["seed"], qcl.PREC_FP32_BULK, n_out, traj_id_offset=rank * n)
         rr.sample(cfg["init"])
         rr.propagate(steps, dt, stride)
@@ -409,6 +413,7 @@ def run_ours(args):
     c4 = wl.config(4)
     n4 = args.sb100_walkers
     m4 = qcl.Model(c4["model"])
+    shape4 = m4.autotune(c4["dt"], c4["out_stride"], probe_walkers=1 << 18, n_steps=40)
     r4 = qcl.Run(m4, n4, c4["seed"], qcl.PREC_FP32_BULK, c4["n_steps"] // c4["out_stride"] + 1,
                  traj_id_offset=rank * n4)
     r4.sample(c4["init"])
@@ -437,6 +442,7 @@ def run_ours(args):
     cd = copy.deepcopy(cfg)
     cd["model"]["repr"] = "diabatic"
     md = qcl.Model(cd["model"])
+    md.autotune(dt, stride)
     rd = qcl.Run(md, n, cfg["seed"], qcl.PREC_FP32_BULK, n_out, traj_id_offset=rank * n)
     rd.sample(cd["init"])
     rd.propagate(steps, dt, stride)
@@ -491,7 +497,8 @@ def run_ours(args):
                    "out_stride": stride, "precision": "FP32 bulk, compensated phase/weight, "
                    "FP64 reduction", "l2": "inputs larger than L2 (walker state "
                    f"{qcl.ensemble_bytes(model, run.ens) / 1e6:.0f} MB resident in HBM)",
-                   "parallelism": f"walkers sharded over {world} GPU(s)"},
+                   "parallelism": f"walkers sharded over {world} GPU(s)",
+                   "launch_shape": shape},
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_tflops,
                      "unit": "TFLOP/s", "frac": (achieved / peak_tflops) if achieved else None,
                      "traffic": _profiled_traffic(
@@ -520,7 +527,7 @@ def run_ours(args):
                   / (k4_ms / 1e3) / 1e12 if k4_ms > 0 else None,
                   "frac_of_fp32_peak": (float(n4) * c4["n_steps"] * flops_per_traj_step(c4["model"])
                                         / (k4_ms / 1e3) / 1e12 / peak_tflops) if k4_ms > 0 else None,
-                  "kernel": "k_bulk2_split (two warps per 32 walkers)",
+                  "kernel": "k_bulk2_split (two warps per 32 walkers)", "launch_shape": shape4,
                   "status_flags": st4["flags"]},
         "diabatic": {"workload": "the same 3-mode spin-boson solve in the diabatic "
                                  "representation (propagation only)",

@@ -282,6 +282,48 @@ qcl_status qcl_combine_shards(const double* shard_sums, int32_t n_shards, int64_
                               double* out);
 
 /* ---------------------------------------------------------------------------
+ * Launch shape and autotuning of the FP32-bulk persistent kernels (no
+ * counterpart in the paper).  Two knobs, neither of which changes a bit of any
+ * result (each walker's arithmetic and each 256-walker reduction tile are the
+ * same whatever the shape):
+ *   walkers_per_thread  1 or 2 (0 = default: 2 for two-state models of at most
+ *                       4 modes, else 1).  With 2 a thread advances one walker
+ *                       of each of two consecutive tiles, interleaving their
+ *                       independent dependency chains; two-state models of at
+ *                       most 8 modes, otherwise 1 is used.
+ *   blocks_per_sm       resident blocks per SM of the persistent grid (0 = the
+ *                       kernel's occupancy limit; larger values are clamped).
+ * Threads per block are fixed at 256: the block is the reduction tile, whose
+ * size defines the summation tree of every observable.
+ * ------------------------------------------------------------------------ */
+typedef struct {
+  int32_t walkers_per_thread;
+  int32_t blocks_per_sm;
+  double walker_steps_per_s; /* rate measured by qcl_autotune for this shape (0 if set by hand) */
+} qcl_launch_shape;
+
+/* Sets the shape every later FP32-bulk launch for this model uses.
+ * QCL_ERR_INVALID_ARG for walkers_per_thread outside {0, 1, 2} or negative
+ * blocks_per_sm. */
+qcl_status qcl_set_launch_shape(qcl_model* model, const qcl_launch_shape* shape);
+qcl_status qcl_get_launch_shape(const qcl_model* model, qcl_launch_shape* shape);
+
+/* Scratch bytes qcl_autotune needs for a probe ensemble of probe_walkers
+ * walkers advanced n_steps steps with the given output stride. */
+qcl_status qcl_autotune_bytes(const qcl_model* model, int64_t probe_walkers, int64_t n_steps,
+                              int32_t out_stride, size_t* bytes);
+
+/* Times every candidate shape (walkers per thread 1 and, where available, 2;
+ * blocks per SM from 1 to the occupancy limit) on a probe ensemble sampled in
+ * `scratch` (ground-state Wigner walkers at R = 0 in state 0, FP32 bulk),
+ * each over n_steps steps of dt with outputs every out_stride steps after one
+ * warm-up run, and stores the fastest in the model (as qcl_set_launch_shape);
+ * *best receives it with its measured rate.  Synchronises the stream. */
+qcl_status qcl_autotune(qcl_model* model, int64_t probe_walkers, int64_t n_steps, double dt,
+                        int32_t out_stride, void* scratch, size_t scratch_bytes,
+                        qcl_launch_shape* best, void* stream);
+
+/* ---------------------------------------------------------------------------
  * Trajectory spawning (FP64, two-state models, either representation).
  *
  * The scheme of the CPU code that the paper's GPU version replaces (Sec. II B:

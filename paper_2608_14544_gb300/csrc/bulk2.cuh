@@ -326,6 +326,7 @@ __device__ __forceinline__ uint32_t pick_word(const u4& wd, int widx) {
 // than PhiloxStream, the same words).
 struct PlainStream {
   uint64_t seed, traj;
+  PlainStream() = default;
   __device__ __forceinline__ PlainStream(uint64_t s, uint64_t t, uint32_t) : seed(s), traj(t) {}
   __device__ __forceinline__ u4 draw(uint32_t n) const {
     return philox_draw(seed, n, traj, kPurposeHop);
@@ -369,100 +370,116 @@ struct CoefLocal {
   float hk[NPL], hs[NPL], dtm[NPL], a[NPL], b[NPL], am[NPL], bm[NPL];
 };
 
-// One 256-walker tile of the one-thread-per-walker kernel: load the tile's
+// WPT consecutive 256-walker tiles (tile0, tile0 + 1, ...) of the
+// one-thread-per-walker kernel, thread t owning walker t of each: load the
 // walkers, advance them over steps [cs, ce) with their observations, store
-// them.  `cf` holds the per-mode coefficients (kernel parameters, or registers
-// in the packed kernel); all threads of the block call it together.  LEAN
-// selects the register-lean form for kernels short of registers (many modes,
-// coefficients in registers): steps one at a time and the whole Philox
-// function per draw, instead of the unrolled four-step blocks below and the
-// precomputed stream.  Both forms give the same bits.
-template <int NPL, int KIND, typename CF, bool LEAN, bool DIA = false>
+// them.  The walkers of one thread are independent, so their steps interleave
+// (instruction-level parallelism); each walker's arithmetic and each tile's
+// reduction are exactly those of WPT = 1, so the results do not depend on WPT.
+// `cf` holds the per-mode coefficients (kernel parameters, or registers in the
+// packed kernel); all threads of the block call it together.  LEAN selects the
+// register-lean form for kernels short of registers (many modes, coefficients
+// in registers): steps one at a time and the whole Philox function per draw,
+// instead of the unrolled four-step blocks below and the precomputed stream.
+// Both forms give the same bits.
+template <int NPL, int KIND, typename CF, bool LEAN, bool DIA = false, int WPT = 1>
 __device__ __forceinline__ void bulk2_tile(const BulkParams& bp, const CF& cf, W32& ws,
-                                           double* __restrict__ part, int64_t tile, int& rb,
+                                           double* __restrict__ part, int64_t tile0, int& rb,
                                            unsigned int& n_deg, double (&red)[2][8][32],
                                            float* obs_rows) {
+  using Stream = std::conditional_t<LEAN, PlainStream, PhiloxStream>;
   const int64_t nt = bp.n_traj;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int64_t i = tile * kTile + threadIdx.x;
-  const bool active = i < nt;
-  const int64_t ii = active ? i : 0;
-  Walker<NPL> w;
+  Walker<NPL> w[WPT];
+  Scal z[WPT];
+  bool active[WPT];
+  unsigned int deg[WPT];
 #pragma unroll
-  for (int j = 0; j < NPL; ++j) {
-    const bool on = active && j < bp.n;
-    w.R[j] = on ? ws.R[(int64_t)j * nt + ii] : 0.0f;
-    w.P[j] = on ? ws.P[(int64_t)j * nt + ii] : 0.0f;
-  }
-  Scal z;
-  z.m = {active ? ws.mh[ii] : 0.0f, active ? ws.ml[ii] : 0.0f};
-  z.mexp = active ? ws.me[ii] : 0;
-  z.ph = {active ? ws.ph[ii] : 0.0f, active ? ws.pl[ii] : 0.0f};
-  const uint32_t ab = active ? ws.ab[ii] : 0u;  // alpha | q << 4 | beta << 8
-  z.sa = sgn(ab & 0xf);
-  z.sb = sgn((ab >> 8) & 0xf);
-  z.q = DIA ? (int)((ab >> 4) & 3u) : 0;
-  const uint64_t traj = bp.traj_offset + (uint64_t)ii;
-  z.A = bp.a0;
-  z.B = bp.b0;
+  for (int k = 0; k < WPT; ++k) {
+    const int64_t i = (tile0 + k) * kTile + threadIdx.x;
+    active[k] = i < nt;
+    const int64_t ii = active[k] ? i : 0;
 #pragma unroll
-  for (int j = 0; j < NPL; ++j) {
-    z.A = __fmaf_rn(cf.a[j], w.R[j], z.A);
-    if (KIND == 1) z.B = __fmaf_rn(cf.b[j], w.R[j], z.B);
+    for (int j = 0; j < NPL; ++j) {
+      const bool on = active[k] && j < bp.n;
+      w[k].R[j] = on ? ws.R[(int64_t)j * nt + ii] : 0.0f;
+      w[k].P[j] = on ? ws.P[(int64_t)j * nt + ii] : 0.0f;
+    }
+    z[k].m = {active[k] ? ws.mh[ii] : 0.0f, active[k] ? ws.ml[ii] : 0.0f};
+    z[k].mexp = active[k] ? ws.me[ii] : 0;
+    z[k].ph = {active[k] ? ws.ph[ii] : 0.0f, active[k] ? ws.pl[ii] : 0.0f};
+    const uint32_t ab = active[k] ? ws.ab[ii] : 0u;  // alpha | q << 4 | beta << 8
+    z[k].sa = sgn(ab & 0xf);
+    z[k].sb = sgn((ab >> 8) & 0xf);
+    z[k].q = DIA ? (int)((ab >> 4) & 3u) : 0;
+    z[k].A = bp.a0;
+    z[k].B = bp.b0;
+#pragma unroll
+    for (int j = 0; j < NPL; ++j) {
+      z[k].A = __fmaf_rn(cf.a[j], w[k].R[j], z[k].A);
+      if (KIND == 1) z[k].B = __fmaf_rn(cf.b[j], w[k].R[j], z[k].B);
+    }
+    closed_form(z[k]);
+    deg[k] = 0;
   }
-  closed_form(z);
-  unsigned int deg = 0;
 
-  // observation into slot `slot` of the tile partials (8 warps, then the
-  // tile's fixed FP64 tree)
-  auto observe = [&](int slot) {
-    red[rb][warp][lane] = observe_warp<DIA>(z, active, obs_rows, threadIdx.x, warp * 32, lane);
+  // observation of walker set k into slot `slot` of its tile's partials (8
+  // warps, then the tile's fixed FP64 tree)
+  auto observe = [&](int k, int slot) {
+    red[rb][warp][lane] = observe_warp<DIA>(z[k], active[k], obs_rows, threadIdx.x, warp * 32, lane);
     __syncthreads();
-    if (threadIdx.x < 32)
-      part[((int64_t)slot * bp.n_tiles + tile) * 32 + threadIdx.x] =
+    if (threadIdx.x < 32 && tile0 + k < bp.n_tiles)
+      part[((int64_t)slot * bp.n_tiles + tile0 + k) * 32 + threadIdx.x] =
           tile_tree8(&red[rb][0][0], 32, threadIdx.x);
     rb ^= 1;
   };
-
-  // one velocity-Verlet step with its phase and transition (hop word `word`)
-  auto step = [&](uint32_t word) {
-    const float hsab = bp.hdt * 0.5f * (z.sa + z.sb);  // dt/2 (sig_a + sig_b)/2
-    if constexpr (DIA) {
-      kick_dia<NPL, KIND, CF>(w, cf, hsab);
+  auto observe_all = [&](int slot) {
 #pragma unroll
-      for (int j = 0; j < NPL; ++j) w.R[j] = __fmaf_rn(cf.dtm[j], w.P[j], w.R[j]);
-      const float a_old = z.A;
-      z.A = bp.a0;
-      if (KIND == 1) z.B = bp.b0;
+    for (int k = 0; k < WPT; ++k) observe(k, slot);
+  };
+
+  // one velocity-Verlet step of walker k with its phase and transition (hop
+  // word `word`)
+  auto step = [&](int k, uint32_t word) {
+    Walker<NPL>& wk = w[k];
+    Scal& zk = z[k];
+    const float hsab = bp.hdt * 0.5f * (zk.sa + zk.sb);  // dt/2 (sig_a + sig_b)/2
+    if constexpr (DIA) {
+      kick_dia<NPL, KIND, CF>(wk, cf, hsab);
+#pragma unroll
+      for (int j = 0; j < NPL; ++j) wk.R[j] = __fmaf_rn(cf.dtm[j], wk.P[j], wk.R[j]);
+      const float a_old = zk.A;
+      zk.A = bp.a0;
+      if (KIND == 1) zk.B = bp.b0;
 #pragma unroll
       for (int j = 0; j < NPL; ++j) {
-        z.A = __fmaf_rn(cf.a[j], w.R[j], z.A);
-        if (KIND == 1) z.B = __fmaf_rn(cf.b[j], w.R[j], z.B);
+        zk.A = __fmaf_rn(cf.a[j], wk.R[j], zk.A);
+        if (KIND == 1) zk.B = __fmaf_rn(cf.b[j], wk.R[j], zk.B);
       }
-      kick_dia<NPL, KIND, CF>(w, cf, hsab);
-      dia_phase_and_transition(z, a_old, z.B, word, bp);
+      kick_dia<NPL, KIND, CF>(wk, cf, hsab);
+      dia_phase_and_transition(zk, a_old, zk.B, word, bp);
       return;
     }
-    kick<NPL, KIND, CF>(w, cf, hsab * z.c2, hsab * z.s2);  // first half kick at R_n
+    kick<NPL, KIND, CF>(wk, cf, hsab * zk.c2, hsab * zk.s2);  // first half kick at R_n
 #pragma unroll
-    for (int j = 0; j < NPL; ++j) w.R[j] = __fmaf_rn(cf.dtm[j], w.P[j], w.R[j]);  // drift
-    const float r_old = z.r;
-    z.A = bp.a0;
-    z.B = bp.b0;
+    for (int j = 0; j < NPL; ++j) wk.R[j] = __fmaf_rn(cf.dtm[j], wk.P[j], wk.R[j]);  // drift
+    const float r_old = zk.r;
+    zk.A = bp.a0;
+    zk.B = bp.b0;
 #pragma unroll
     for (int j = 0; j < NPL; ++j) {
-      z.A = __fmaf_rn(cf.a[j], w.R[j], z.A);
-      if (KIND == 1) z.B = __fmaf_rn(cf.b[j], w.R[j], z.B);
+      zk.A = __fmaf_rn(cf.a[j], wk.R[j], zk.A);
+      if (KIND == 1) zk.B = __fmaf_rn(cf.b[j], wk.R[j], zk.B);
     }
-    closed_form(z);
-    kick<NPL, KIND, CF>(w, cf, hsab * z.c2, hsab * z.s2);  // second half kick at R_{n+1}
+    closed_form(zk);
+    kick<NPL, KIND, CF>(wk, cf, hsab * zk.c2, hsab * zk.s2);  // second half kick at R_{n+1}
     float Av = 0.0f, Bv = 0.0f;
 #pragma unroll
     for (int j = 0; j < NPL; ++j) {
-      Av = __fmaf_rn(cf.am[j], w.P[j], Av);
-      if (KIND == 1) Bv = __fmaf_rn(cf.bm[j], w.P[j], Bv);
+      Av = __fmaf_rn(cf.am[j], wk.P[j], Av);
+      if (KIND == 1) Bv = __fmaf_rn(cf.bm[j], wk.P[j], Bv);
     }
-    phase_and_transition<KIND>(z, r_old, Av, Bv, word, bp, deg);
+    phase_and_transition<KIND>(zk, r_old, Av, Bv, word, bp, deg[k]);
   };
 
   // Steps are grouped by Philox block (four steps share one draw).  A whole
@@ -471,55 +488,79 @@ __device__ __forceinline__ void bulk2_tile(const BulkParams& bp, const CF& cf, W
   // inside) run one at a time.  The weight and phase pairs are renormalised at
   // the end of every block, i.e. at the same absolute steps on both routes.
   int slot = bp.obs_first;
-  if (bp.obs_first) observe(0);
+  if (bp.obs_first) observe_all(0);
   int to_out = bp.to_out0;
   uint32_t blk = bp.blk0;
   int widx = bp.widx0;
-  const std::conditional_t<LEAN, PlainStream, PhiloxStream> rng(bp.seed, traj, kPurposeHop);
-  u4 wd = rng.draw(blk);
+  Stream rng[WPT] = {};
+  u4 wd[WPT];
+#pragma unroll
+  for (int k = 0; k < WPT; ++k) {
+    const int64_t ii = active[k] ? (tile0 + k) * kTile + threadIdx.x : 0;
+    rng[k] = Stream(bp.seed, bp.traj_offset + (uint64_t)ii, kPurposeHop);
+    wd[k] = rng[k].draw(blk);
+  }
   int it = 0;
   while (it < bp.len) {
     if (!LEAN && widx == 0 && bp.len - it >= 4 && to_out >= 4) {
-      step(wd.x);
-      step(wd.y);
-      step(wd.z);
-      step(wd.w);
-      block_end(z);
+#pragma unroll
+      for (int k = 0; k < WPT; ++k) step(k, wd[k].x);
+#pragma unroll
+      for (int k = 0; k < WPT; ++k) step(k, wd[k].y);
+#pragma unroll
+      for (int k = 0; k < WPT; ++k) step(k, wd[k].z);
+#pragma unroll
+      for (int k = 0; k < WPT; ++k) {
+        step(k, wd[k].w);
+        block_end(z[k]);
+      }
       it += 4;
       to_out -= 4;
       ++blk;
-      if (it < bp.len) wd = rng.draw(blk);
+      if (it < bp.len) {
+#pragma unroll
+        for (int k = 0; k < WPT; ++k) wd[k] = rng[k].draw(blk);
+      }
     } else {
-      step(pick_word(wd, widx));
+#pragma unroll
+      for (int k = 0; k < WPT; ++k) step(k, pick_word(wd[k], widx));
       ++it;
       --to_out;
       if (++widx == 4) {
         widx = 0;
-        block_end(z);
+#pragma unroll
+        for (int k = 0; k < WPT; ++k) block_end(z[k]);
         ++blk;
-        if (it < bp.len) wd = rng.draw(blk);
+        if (it < bp.len) {
+#pragma unroll
+          for (int k = 0; k < WPT; ++k) wd[k] = rng[k].draw(blk);
+        }
       }
     }
     if (to_out == 0) {
-      observe(slot++);
+      observe_all(slot++);
       to_out = bp.stride;
     }
   }
-  if (active) {
-    n_deg += deg;
+#pragma unroll
+  for (int k = 0; k < WPT; ++k) {
+    if (!active[k]) continue;
+    const int64_t i = (tile0 + k) * kTile + threadIdx.x;
+    const Scal& zk = z[k];
+    n_deg += deg[k];
 #pragma unroll
     for (int j = 0; j < NPL; ++j)
       if (j < bp.n) {
-        ws.R[(int64_t)j * nt + i] = w.R[j];
-        ws.P[(int64_t)j * nt + i] = w.P[j];
+        ws.R[(int64_t)j * nt + i] = w[k].R[j];
+        ws.P[(int64_t)j * nt + i] = w[k].P[j];
       }
-    ws.mh[i] = z.m.hi;
-    ws.ml[i] = z.m.lo;
-    ws.me[i] = z.mexp;
-    ws.ph[i] = z.ph.hi;
-    ws.pl[i] = z.ph.lo;
-    ws.ab[i] = (uint16_t)((z.sa > 0.0f ? 1 : 0) | (z.q << 4) | ((z.sb > 0.0f ? 1 : 0) << 8));
-    if (!isfinite(z.m.hi) || !isfinite(z.ph.hi)) {
+    ws.mh[i] = zk.m.hi;
+    ws.ml[i] = zk.m.lo;
+    ws.me[i] = zk.mexp;
+    ws.ph[i] = zk.ph.hi;
+    ws.pl[i] = zk.ph.lo;
+    ws.ab[i] = (uint16_t)((zk.sa > 0.0f ? 1 : 0) | (zk.q << 4) | ((zk.sb > 0.0f ? 1 : 0) << 8));
+    if (!isfinite(zk.m.hi) || !isfinite(zk.ph.hi)) {
       atomicAdd(&ws.hdr->n_nonfinite, 1ull);
       atomicOr(&ws.hdr->flags, QCL_FLAG_NONFINITE);
     }

@@ -196,18 +196,34 @@ void launch_step_f64(const DevModel* dm, int repr, void* buf, int64_t nt, int n,
 void launch_observe_f64(const DevModel* dm, const void* buf, int64_t nt, int n, double* part,
                         cudaStream_t st);
 
+// Launch shape of a persistent bulk launch; the results do not depend on it.
+struct LaunchShape {
+  int wpt = 0;            // walkers per thread, 1 or 2 (0: the default for the mode count)
+  int blocks_per_sm = 0;  // resident blocks per SM (0: the occupancy maximum)
+  int grid_cap = 0;       // total blocks at most (0: no cap)
+};
+// Walkers per thread a two-state kernel of n modes can take (1 or 2), and the
+// default when none is set.
+inline int max_wpt(int n) { return n <= 8 ? 2 : 1; }
+inline int default_wpt(int n) { return n <= 4 ? 2 : 1; }
+
 void launch_sample_f32(const DevModel* dm, const SampleParams& sp, void* buf, cudaStream_t st);
 // Returns the persistent grid size used (0 on launch failure).
-int launch_bulk2(const BulkParams& bp, const Coef2& cf, void* buf, double* part, int grid_cap,
-                 cudaStream_t st);
+int launch_bulk2(const BulkParams& bp, const Coef2& cf, void* buf, double* part,
+                 const LaunchShape& ls, cudaStream_t st);
 // The diabatic-representation bulk kernel (two states, n <= 32 modes).
-int launch_bulk2_dia(const BulkParams& bp, const Coef2& cf, void* buf, double* part, int grid_cap,
-                     cudaStream_t st);
-// Launches a persistent bulk kernel with one wave of resident blocks (capped
-// by grid_cap and the tile count); per_sm / n_sm cache the occupancy query.
+int launch_bulk2_dia(const BulkParams& bp, const Coef2& cf, void* buf, double* part,
+                     const LaunchShape& ls, cudaStream_t st);
+// Launches a persistent bulk kernel whose blocks take `wpt` tiles at a time:
+// one wave of ls.blocks_per_sm (at most the occupancy limit) blocks per SM,
+// capped by ls.grid_cap and by the tile count; per_sm / n_sm cache the
+// occupancy query.
 using BulkFn = void (*)(const BulkParams, const Coef2, void*, double*);
 int run_bulk_kernel(BulkFn fn, int& per_sm, int& n_sm, const BulkParams& bp, const Coef2& cf,
-                    void* buf, double* part, int grid_cap, cudaStream_t st);
+                    void* buf, double* part, const LaunchShape& ls, int wpt, cudaStream_t st);
+// Occupancy limit (resident blocks per SM) of the two-state bulk kernel that
+// a launch of (n, kind, repr, wpt) would use; 0 if there is none.
+int bulk2_blocks_per_sm(int n, int kind, int repr, int wpt);
 // Kernel-selection description of the bulk kernel chosen for (n, kind).
 const char* bulk2_variant(int n, int kind);
 
@@ -218,7 +234,7 @@ void launch_stepN_f64(const DevModel* dm, int ns, void* buf, int64_t nt, int n, 
 void launch_observeN_f64(int ns, const void* buf, int64_t nt, int n, double* part,
                          cudaStream_t st);
 int launch_bulkN(int ns, const BulkParams& bp, const CoefN& cf, void* buf, double* part,
-                 int grid_cap, cudaStream_t st);
+                 const LaunchShape& ls, cudaStream_t st);
 
 void launch_fold(const double* part, double* rows_out, double* scratch, int64_t n_tiles,
                  int q2, int n_slots, cudaStream_t st);

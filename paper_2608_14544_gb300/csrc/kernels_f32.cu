@@ -111,8 +111,8 @@ __global__ void __launch_bounds__(256) k_sample_f32(const DevModel* __restrict__
 
 // One thread per walker, all modes in registers, coefficients as constant-bank
 // operands.  Tile = the block's 256 walkers.
-template <int NPL, int KIND>
-__global__ void __launch_bounds__(256, 3)
+template <int NPL, int KIND, int WPT = 1>
+__global__ void __launch_bounds__(256, WPT == 1 ? 3 : 2)
     k_bulk2(const BulkParams bp, const Coef2 cf, void* buf, double* __restrict__ part) {
   __shared__ double red[2][8][32];      // double-buffered group partials
   __shared__ __align__(16) float obs_rows[256 * kObsRow];  // per-walker contributions
@@ -123,8 +123,9 @@ __global__ void __launch_bounds__(256, 3)
   }
   unsigned int n_deg = 0;
   int rb = 0;
-  for (int64_t tile = blockIdx.x; tile < bp.n_tiles; tile += gridDim.x)
-    bulk2_tile<NPL, KIND, Coef2, (NPL > 12)>(bp, cf, ws, part, tile, rb, n_deg, red, obs_rows);
+  for (int64_t tile = (int64_t)blockIdx.x * WPT; tile < bp.n_tiles; tile += (int64_t)gridDim.x * WPT)
+    bulk2_tile<NPL, KIND, Coef2, (NPL > 12), false, WPT>(bp, cf, ws, part, tile, rb, n_deg, red,
+                                                        obs_rows);
   if (n_deg) {
     atomicAdd(&ws.hdr->n_degenerate, (unsigned long long)n_deg);
     atomicOr(&ws.hdr->flags, QCL_FLAG_DEGENERATE);
@@ -355,8 +356,8 @@ void launch_sample_f32(const DevModel* dm, const SampleParams& sp, void* buf, cu
   launches_add(1);
 }
 
-int run_bulk_kernel(BulkFn fn, int& per_sm, int& n_sm, const BulkParams& bp, const Coef2& cf,
-                    void* buf, double* part, int grid_cap, cudaStream_t st) {
+namespace {
+void occupancy(BulkFn fn, int& per_sm, int& n_sm) {
   if (per_sm < 0) {
     int dev = 0;
     cudaGetDevice(&dev);
@@ -365,9 +366,17 @@ int run_bulk_kernel(BulkFn fn, int& per_sm, int& n_sm, const BulkParams& bp, con
         per_sm < 1)
       per_sm = 1;
   }
-  int64_t grid = (int64_t)per_sm * n_sm;
-  if (grid_cap > 0 && grid > grid_cap) grid = grid_cap;
-  if (grid > bp.n_tiles) grid = bp.n_tiles;
+}
+}  // namespace
+
+int run_bulk_kernel(BulkFn fn, int& per_sm, int& n_sm, const BulkParams& bp, const Coef2& cf,
+                    void* buf, double* part, const LaunchShape& ls, int wpt, cudaStream_t st) {
+  occupancy(fn, per_sm, n_sm);
+  const int bps = (ls.blocks_per_sm > 0 && ls.blocks_per_sm < per_sm) ? ls.blocks_per_sm : per_sm;
+  int64_t grid = (int64_t)bps * n_sm;
+  if (ls.grid_cap > 0 && grid > ls.grid_cap) grid = ls.grid_cap;
+  const int64_t units = (bp.n_tiles + wpt - 1) / wpt;
+  if (grid > units) grid = units;
   if (grid < 1) grid = 1;
   fn<<<(unsigned)grid, 256, 0, st>>>(bp, cf, buf, part);
   launches_add(1);
@@ -376,28 +385,36 @@ int run_bulk_kernel(BulkFn fn, int& per_sm, int& n_sm, const BulkParams& bp, con
 
 namespace {
 int run_kernel(BulkFn fn, int& per_sm, int& n_sm, const BulkParams& bp, const Coef2& cf, void* buf,
-               double* part, int grid_cap, cudaStream_t st) {
-  return run_bulk_kernel(fn, per_sm, n_sm, bp, cf, buf, part, grid_cap, st);
+               double* part, const LaunchShape& ls, cudaStream_t st) {
+  return run_bulk_kernel(fn, per_sm, n_sm, bp, cf, buf, part, ls, 1, st);
+}
+
+template <int NPL, int KIND, int WPT>
+BulkFn bulk_fn() {
+  if constexpr (WPT == 2 && NPL <= 8) return k_bulk2<NPL, KIND, 2>;
+  else return k_bulk2<NPL, KIND, 1>;
 }
 
 template <int NPL, int KIND>
-int run_bulk(const BulkParams& bp, const Coef2& cf, void* buf, double* part, int grid_cap,
+int run_bulk(const BulkParams& bp, const Coef2& cf, void* buf, double* part, const LaunchShape& ls,
              cudaStream_t st) {
-  static int per_sm = -1, n_sm = 0;
-  return run_kernel(k_bulk2<NPL, KIND>, per_sm, n_sm, bp, cf, buf, part, grid_cap, st);
+  static int per_sm[2] = {-1, -1}, n_sm[2] = {0, 0};
+  const int wpt = (ls.wpt > 0 ? ls.wpt : default_wpt(NPL)) >= 2 && NPL <= 8 ? 2 : 1;
+  if (wpt == 2)
+    return run_bulk_kernel(bulk_fn<NPL, KIND, 2>(), per_sm[1], n_sm[1], bp, cf, buf, part, ls, 2, st);
+  return run_bulk_kernel(bulk_fn<NPL, KIND, 1>(), per_sm[0], n_sm[0], bp, cf, buf, part, ls, 1, st);
 }
 
 template <int NPL, int L, int KIND, int MINB>
-int run_wide(const BulkParams& bp, const Coef2& cf, void* buf, double* part, int grid_cap,
+int run_wide(const BulkParams& bp, const Coef2& cf, void* buf, double* part, const LaunchShape& cap,
              cudaStream_t st) {
   static int per_sm = -1, n_sm = 0;
-  return run_kernel(k_bulk2_split<NPL, L, KIND, MINB>, per_sm, n_sm, bp, cf, buf, part, grid_cap,
-                    st);
+  return run_kernel(k_bulk2_split<NPL, L, KIND, MINB>, per_sm, n_sm, bp, cf, buf, part, cap, st);
 }
 
 template <int KIND>
-int dispatch_n(const BulkParams& bp, const Coef2& cf, void* buf, double* part, int cap,
-               cudaStream_t st) {
+int dispatch_n(const BulkParams& bp, const Coef2& cf, void* buf, double* part,
+               const LaunchShape& cap, cudaStream_t st) {
   const int n = bp.n;
   if (n <= 1) return run_bulk<1, KIND>(bp, cf, buf, part, cap, st);
   if (n <= 2) return run_bulk<2, KIND>(bp, cf, buf, part, cap, st);
@@ -419,11 +436,40 @@ int dispatch_n(const BulkParams& bp, const Coef2& cf, void* buf, double* part, i
 }
 }  // namespace
 
-int launch_bulk2(const BulkParams& bp, const Coef2& cf, void* buf, double* part, int grid_cap,
-                 cudaStream_t st) {
-  if (bp.repr == QCL_REPR_DIABATIC) return launch_bulk2_dia(bp, cf, buf, part, grid_cap, st);
-  return bp.kind == 0 ? dispatch_n<0>(bp, cf, buf, part, grid_cap, st)
-                      : dispatch_n<1>(bp, cf, buf, part, grid_cap, st);
+int launch_bulk2(const BulkParams& bp, const Coef2& cf, void* buf, double* part,
+                 const LaunchShape& ls, cudaStream_t st) {
+  if (bp.repr == QCL_REPR_DIABATIC) return launch_bulk2_dia(bp, cf, buf, part, ls, st);
+  return bp.kind == 0 ? dispatch_n<0>(bp, cf, buf, part, ls, st)
+                      : dispatch_n<1>(bp, cf, buf, part, ls, st);
+}
+
+namespace {
+template <int KIND, int WPT>
+BulkFn adiabatic_fn(int n) {
+  if (n <= 1) return bulk_fn<1, KIND, WPT>();
+  if (n <= 2) return bulk_fn<2, KIND, WPT>();
+  if (n <= 3) return bulk_fn<3, KIND, WPT>();
+  if (n <= 4) return bulk_fn<4, KIND, WPT>();
+  if (n <= 6) return bulk_fn<6, KIND, WPT>();
+  if (n <= 8) return bulk_fn<8, KIND, WPT>();
+  return nullptr;
+}
+}  // namespace
+
+BulkFn bulk2_dia_fn(int n, int kind, int wpt);
+
+int bulk2_blocks_per_sm(int n, int kind, int repr, int wpt) {
+  BulkFn fn = nullptr;
+  if (repr == QCL_REPR_DIABATIC) {
+    fn = bulk2_dia_fn(n, kind, wpt);
+  } else if (n <= 8) {
+    fn = kind == 0 ? (wpt == 2 ? adiabatic_fn<0, 2>(n) : adiabatic_fn<0, 1>(n))
+                   : (wpt == 2 ? adiabatic_fn<1, 2>(n) : adiabatic_fn<1, 1>(n));
+  }
+  if (!fn) return 0;
+  int per_sm = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, 256, 0) != cudaSuccess) return 0;
+  return per_sm;
 }
 
 const char* bulk2_variant(int n, int kind) {

@@ -52,7 +52,17 @@ void launch_observeN_f64(int ns, const void* buf, int64_t nt, int n, double* par
 }
 
 int launch_bulkN(int ns, const BulkParams& bp, const CoefN& cf, void* buf, double* part,
-                 int grid_cap, cudaStream_t st) {
+                 const LaunchShape& ls, cudaStream_t st) {
+  // blocks per SM become a cap on the grid (one walker per thread here)
+  static int n_sm = 0;
+  if (n_sm == 0) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
+  }
+  int grid_cap = ls.grid_cap;
+  if (ls.blocks_per_sm > 0 && (grid_cap == 0 || ls.blocks_per_sm * n_sm < grid_cap))
+    grid_cap = ls.blocks_per_sm * n_sm;
   int g = 0;
   switch (ns) {
     case 3: g = nstate_bulk_3(bp, cf, buf, part, grid_cap, st); break;

@@ -13,6 +13,10 @@ struct qcl_model {
   qcl::DevModel host{};
   qcl::DevModel* dev = nullptr;  // device block: DevModel followed by K
   int device = 0;
+  // launch shape of the FP32-bulk kernels (qcl_set_launch_shape / qcl_autotune;
+  // 0 = default)
+  int shape_wpt = 0, shape_bps = 0;
+  double shape_rate = 0.0;
 };
 
 namespace qcl {

@@ -158,7 +158,10 @@ extern "C" qcl_status qcl_propagate_noalloc(const qcl_model* model, const qcl_en
     bp.to_out0 = (int32_t)(out_stride - (cs % out_stride));
     bp.blk0 = (uint32_t)(cs >> 2);
     bp.widx0 = (int32_t)(cs & 3);
-    if (launch_bulk2(bp, cf, ens_buf, part, 0, s) == 0)
+    LaunchShape ls;
+    ls.wpt = model->shape_wpt;
+    ls.blocks_per_sm = model->shape_bps;
+    if (launch_bulk2(bp, cf, ens_buf, part, ls, s) == 0)
       return fail(QCL_ERR_UNSUPPORTED, "no FP32-bulk kernel for n_modes = %d", model->n);
     if (n_slots > 0) launch_fold(part, rows + (size_t)k_first * q2, fold, n_tiles, q2, n_slots, s);
     first = false;

@@ -478,8 +478,12 @@ qcl_status qcl_propagate(const qcl_model* model, const qcl_ensemble_desc* ens, v
       int grid = 0;
       {
         TimedLaunch tl(0, s);
-        grid = cn ? launch_bulkN(model->ns, bp, *cn, ens_buf, part, (int)g_opt_grid_cap, s)
-                  : launch_bulk2(bp, *cf, ens_buf, part, (int)g_opt_grid_cap, s);
+        LaunchShape ls;
+        ls.wpt = model->shape_wpt;
+        ls.blocks_per_sm = model->shape_bps;
+        ls.grid_cap = (int)g_opt_grid_cap;
+        grid = cn ? launch_bulkN(model->ns, bp, *cn, ens_buf, part, ls, s)
+                  : launch_bulk2(bp, *cf, ens_buf, part, ls, s);
       }
       if (grid == 0) {
         delete cf;
@@ -557,6 +561,126 @@ qcl_status qcl_ensemble_status(const qcl_model* model, const qcl_ensemble_desc* 
   out->reserved = 0;
   out->n_degenerate = h.n_degenerate;
   out->n_nonfinite = h.n_nonfinite;
+  return ok();
+}
+
+// ------------------------------------------------------------ launch shape --
+qcl_status qcl_set_launch_shape(qcl_model* model, const qcl_launch_shape* shape) {
+  if (!model || !shape) return fail(QCL_ERR_INVALID_ARG, "model or shape is NULL");
+  if (shape->walkers_per_thread < 0 || shape->walkers_per_thread > 2)
+    return fail(QCL_ERR_INVALID_ARG, "walkers_per_thread must be 0, 1 or 2");
+  if (shape->blocks_per_sm < 0) return fail(QCL_ERR_INVALID_ARG, "blocks_per_sm must be >= 0");
+  model->shape_wpt = shape->walkers_per_thread;
+  model->shape_bps = shape->blocks_per_sm;
+  model->shape_rate = shape->walker_steps_per_s;
+  return ok();
+}
+
+qcl_status qcl_get_launch_shape(const qcl_model* model, qcl_launch_shape* shape) {
+  if (!model || !shape) return fail(QCL_ERR_INVALID_ARG, "model or shape is NULL");
+  shape->walkers_per_thread = model->shape_wpt;
+  shape->blocks_per_sm = model->shape_bps;
+  shape->walker_steps_per_s = model->shape_rate;
+  return ok();
+}
+
+}  // extern "C"
+
+namespace {
+struct ProbeSizes {
+  qcl_ensemble_desc ens;
+  int64_t n_out;
+  size_t ens_bytes, obs_bytes, total;
+};
+ProbeSizes probe_sizes(const qcl_model* model, int64_t probe_walkers, int64_t n_steps, int32_t out_stride) {
+  ProbeSizes p{};
+  p.ens = qcl_ensemble_desc{probe_walkers, 0x5EEDull, 0, QCL_PREC_FP32_BULK, 0};
+  p.n_out = n_steps / out_stride + 1;
+  p.ens_bytes = align256(EnsLayout::make(probe_walkers, model->ns, model->n, QCL_PREC_FP32_BULK).total);
+  p.obs_bytes = ObsLayout::make(probe_walkers, model->ns, p.n_out,
+                                tile_walkers(QCL_PREC_FP32_BULK, model->n, model->ns)).total;
+  p.total = p.ens_bytes + p.obs_bytes;
+  return p;
+}
+}  // namespace
+
+extern "C" {
+
+qcl_status qcl_autotune_bytes(const qcl_model* model, int64_t probe_walkers, int64_t n_steps, int32_t out_stride,
+                              size_t* bytes) {
+  if (!model || !bytes) return fail(QCL_ERR_INVALID_ARG, "model or bytes is NULL");
+  if (probe_walkers < 1 || n_steps < 1 || out_stride < 1)
+    return fail(QCL_ERR_INVALID_ARG, "probe_walkers, n_steps and out_stride must be >= 1");
+  *bytes = probe_sizes(model, probe_walkers, n_steps, out_stride).total;
+  return ok();
+}
+
+qcl_status qcl_autotune(qcl_model* model, int64_t probe_walkers, int64_t n_steps, double dt, int32_t out_stride,
+                        void* scratch, size_t scratch_bytes, qcl_launch_shape* best, void* stream) {
+  if (!model || !scratch || !best) return fail(QCL_ERR_INVALID_ARG, "model, scratch or best is NULL");
+  if (probe_walkers < 1 || n_steps < 1 || out_stride < 1)
+    return fail(QCL_ERR_INVALID_ARG, "probe_walkers, n_steps and out_stride must be >= 1");
+  if (!(dt > 0.0) || !std::isfinite(dt)) return fail(QCL_ERR_INVALID_ARG, "dt must be positive");
+  const ProbeSizes ps = probe_sizes(model, probe_walkers, n_steps, out_stride);
+  if (scratch_bytes < ps.total) return fail(QCL_ERR_OUT_OF_MEMORY, "scratch has %zu bytes, needs %zu", scratch_bytes, ps.total);
+  qcl_status st = check_ens(model, &ps.ens);
+  if (st) return st;
+  const int ns = model->ns, n = model->n;
+  std::vector<double> rho((size_t)ns * ns, 0.0), zero((size_t)n, 0.0);
+  rho[0] = 1.0;
+  const qcl_init_desc init{rho.data(), zero.data(), zero.data(), INFINITY, 1, 0};
+  // candidates: walkers per thread, then blocks per SM up to the occupancy limit
+  const bool two_state_reg = ns == 2 && (model->host.repr == QCL_REPR_DIABATIC ? n <= 32 : n <= 8);
+  const int wmax = (ns == 2 && n <= 8) ? 2 : 1;
+  const int keep_wpt = model->shape_wpt, keep_bps = model->shape_bps;
+  const double keep_rate = model->shape_rate;
+  cudaStream_t s = (cudaStream_t)stream;
+  char* ens_buf = (char*)scratch;
+  char* obs_buf = ens_buf + ps.ens_bytes;
+  cudaEvent_t e0, e1;
+  CUDA_TRY(cudaEventCreate(&e0));
+  CUDA_TRY(cudaEventCreate(&e1));
+  float best_ms = -1.0f;
+  int best_wpt = 1, best_bps = 0;
+  for (int wpt = 1; wpt <= wmax; ++wpt) {
+    int limit = two_state_reg ? bulk2_blocks_per_sm(n, model->host.kind, model->host.repr, wpt) : 4;
+    if (limit < 1) limit = 1;
+    for (int bps = 1; bps <= limit; ++bps) {
+      model->shape_wpt = wpt;
+      model->shape_bps = bps;
+      float ms = 0.0f;
+      for (int rep = 0; rep < 2 && !st; ++rep) {  // the first run is the warm-up
+        st = qcl_sample_initial(model, &ps.ens, &init, ens_buf, ps.ens_bytes, stream);
+        if (!st) cudaEventRecord(e0, s);
+        if (!st) st = qcl_propagate(model, &ps.ens, ens_buf, ps.ens_bytes, 0, n_steps, dt, out_stride, obs_buf,
+                                    ps.obs_bytes, ps.n_out, stream);
+        if (!st) cudaEventRecord(e1, s);
+        if (!st && cudaEventSynchronize(e1) != cudaSuccess) st = fail(QCL_ERR_CUDA, "autotune: event wait failed");
+        if (!st) cudaEventElapsedTime(&ms, e0, e1);
+      }
+      if (st) break;
+      if (best_ms < 0.0f || ms < best_ms) {
+        best_ms = ms;
+        best_wpt = wpt;
+        best_bps = bps;
+      }
+    }
+    if (st) break;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (st) {
+    model->shape_wpt = keep_wpt;
+    model->shape_bps = keep_bps;
+    model->shape_rate = keep_rate;
+    return st;
+  }
+  model->shape_wpt = best_wpt;
+  model->shape_bps = best_bps;
+  model->shape_rate = best_ms > 0.0f ? (double)probe_walkers * (double)n_steps / (best_ms * 1e-3) : 0.0;
+  best->walkers_per_thread = best_wpt;
+  best->blocks_per_sm = best_bps;
+  best->walker_steps_per_s = model->shape_rate;
   return ok();
 }
 

@@ -70,6 +70,7 @@ struct PhiloxStream {
   uint32_t g;        // purpose ^ k1
   uint32_t k0, k1;
 
+  PhiloxStream() = default;
   __host__ __device__ __forceinline__ PhiloxStream(uint64_t seed, uint64_t traj, uint32_t purpose) {
     k0 = (uint32_t)seed;
     k1 = (uint32_t)(seed >> 32);

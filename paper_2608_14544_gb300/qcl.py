@@ -35,7 +35,8 @@ EXPORTS = [
     "qcl_server_create", "qcl_server_submit", "qcl_server_poll", "qcl_server_wait",
     "qcl_server_stats", "qcl_server_destroy", "qcl_shard_tile_walkers", "qcl_combine_shards",
     "qcl_spawn_bytes", "qcl_spawn_layout", "qcl_spawn_sample", "qcl_spawn_propagate",
-    "qcl_spawn_live",
+    "qcl_spawn_live", "qcl_set_launch_shape", "qcl_get_launch_shape", "qcl_autotune_bytes",
+    "qcl_autotune",
 ]
 FLAG_SPAWN_OVERFLOW = 8
 REQ_QUEUED, REQ_RUNNING, REQ_DONE, REQ_ERROR = 0, 1, 2, 3
@@ -66,6 +67,11 @@ def repr_code(m: dict) -> int:
     if r in ("diabatic", REPR_DIABATIC):
         return REPR_DIABATIC
     raise ValueError(f"unknown representation {r!r}")
+
+
+class LaunchShape(C.Structure):
+    _fields_ = [("walkers_per_thread", C.c_int32), ("blocks_per_sm", C.c_int32),
+                ("walker_steps_per_s", C.c_double)]
 
 
 class EnsembleDesc(C.Structure):
@@ -148,6 +154,10 @@ def load(path: str = LIB_PATH):
     lib.qcl_spawn_propagate.argtypes = [vp, vp, i64, vp, sz, i64, i64, C.c_double, i32, vp, sz,
                                         i64, vp]
     lib.qcl_spawn_live.argtypes = [vp, vp, i64, vp, vp, vp]
+    lib.qcl_set_launch_shape.argtypes = [vp, vp]
+    lib.qcl_get_launch_shape.argtypes = [vp, vp]
+    lib.qcl_autotune_bytes.argtypes = [vp, i64, i64, i32, vp]
+    lib.qcl_autotune.argtypes = [vp, i64, i64, C.c_double, i32, vp, sz, vp, vp]
     for name in EXPORTS:
         f = getattr(lib, name)
         if name not in ("qcl_last_error", "qcl_version"):
@@ -226,6 +236,34 @@ class Model:
         if self.handle:
             load().qcl_destroy_model(self.handle)
             self.handle = None
+
+    def set_launch_shape(self, walkers_per_thread: int = 0, blocks_per_sm: int = 0):
+        """Launch shape of the FP32-bulk kernels (0 = default); results do not
+        depend on it."""
+        sh = LaunchShape(int(walkers_per_thread), int(blocks_per_sm), 0.0)
+        _check(load().qcl_set_launch_shape(self.handle, C.byref(sh)), "qcl_set_launch_shape")
+
+    def launch_shape(self) -> dict:
+        sh = LaunchShape()
+        _check(load().qcl_get_launch_shape(self.handle, C.byref(sh)), "qcl_get_launch_shape")
+        return {"walkers_per_thread": sh.walkers_per_thread, "blocks_per_sm": sh.blocks_per_sm,
+                "walker_steps_per_s": sh.walker_steps_per_s}
+
+    def autotune(self, dt: float, out_stride: int, probe_walkers: int = 1 << 20,
+                 n_steps: int = 160, stream=None) -> dict:
+        """Times the candidate launch shapes on a probe ensemble and keeps the
+        fastest (see qcl_autotune); returns it with its measured rate."""
+        b = C.c_size_t()
+        _check(load().qcl_autotune_bytes(self.handle, probe_walkers, n_steps, out_stride,
+                                         C.byref(b)), "qcl_autotune_bytes")
+        scratch = device_buffer(b.value)
+        sh = LaunchShape()
+        _check(load().qcl_autotune(self.handle, probe_walkers, n_steps, dt, out_stride,
+                                   _dptr(scratch), b.value, C.byref(sh), _stream_ptr(stream)),
+               "qcl_autotune")
+        del scratch
+        return {"walkers_per_thread": sh.walkers_per_thread, "blocks_per_sm": sh.blocks_per_sm,
+                "walker_steps_per_s": sh.walker_steps_per_s}
 
     def __del__(self):
         try:

@@ -111,3 +111,14 @@ def test_server_validation_without_gpu(lib):
     assert lib.qcl_server_destroy(None) == 0
     st = C.c_int32()
     assert lib.qcl_server_poll(None, 1, C.byref(st), None, 0, None) == 1
+
+
+def test_launch_shape_validation_without_gpu(lib):
+    from paper_2608_14544_gb300 import qcl
+
+    sh = qcl.LaunchShape(1, 0, 0.0)
+    assert lib.qcl_set_launch_shape(None, C.byref(sh)) == 1
+    assert lib.qcl_get_launch_shape(None, C.byref(sh)) == 1
+    b = C.c_size_t()
+    assert lib.qcl_autotune_bytes(None, 1024, 10, 10, C.byref(b)) == 1
+    assert lib.qcl_autotune(None, 1024, 10, 0.01, 10, None, 0, C.byref(sh), None) == 1

@@ -1,0 +1,70 @@
+"""Launch shapes of the FP32-bulk kernels (walkers per thread, blocks per SM)
+change no bit of any result, and the autotuner picks one of them."""
+import copy
+
+import numpy as np
+import pytest
+
+from paper_2608_14544_gb300 import workloads as wl
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def q():
+    import torch
+
+    from paper_2608_14544_gb300 import build, qcl
+
+    build.build()
+    torch.cuda.set_device(0)
+    return qcl
+
+
+def _cases():
+    c2 = wl.config(2)
+    c3 = wl.config(3)
+    d2 = copy.deepcopy(c2)
+    d2["model"]["repr"] = "diabatic"
+    c6 = copy.deepcopy(c3)
+    c6["model"] = wl.random_lvc2(6, 3, 0.1)
+    c6["init"] = wl.sb_init(c6["model"], beta=2.0)
+    return [("sb3", c2), ("vib3", c3), ("sb3-diabatic", d2), ("lvc2-6mode", c6),
+            ("lvc4", wl.lvc4_config(2))]
+
+
+@pytest.mark.parametrize("name,cfg", _cases())
+def test_every_launch_shape_gives_the_same_bits(q, name, cfg):
+    n, steps, stride = 70_001, 120, 10
+    outs = []
+    for wpt, bps in ((1, 0), (2, 0), (1, 1), (2, 1), (0, 2), (0, 0)):
+        m = q.Model(cfg["model"])
+        m.set_launch_shape(wpt, bps)
+        run = q.Run(m, n, 6, q.PREC_FP32_BULK, steps // stride + 1)
+        run.sample(cfg["init"])
+        run.propagate(55, cfg["dt"], stride)
+        run.propagate(steps - 55, cfg["dt"], stride)
+        outs.append((run.sums(), run.state()))
+        assert run.status()["flags"] == 0
+    for sums, st in outs[1:]:
+        assert np.array_equal(sums, outs[0][0]), name
+        for k in st:
+            assert np.array_equal(st[k], outs[0][1][k]), (name, k)
+
+
+def test_autotune_picks_a_measured_shape(q):
+    cfg = wl.config(2)
+    m = q.Model(cfg["model"])
+    best = m.autotune(cfg["dt"], cfg["out_stride"], probe_walkers=1 << 19, n_steps=80)
+    assert best["walkers_per_thread"] in (1, 2)
+    assert best["blocks_per_sm"] >= 1
+    assert best["walker_steps_per_s"] > 1e9
+    assert m.launch_shape() == best
+    # the model keeps solving with the tuned shape, same bits as the default
+    res = []
+    for mm in (m, q.Model(cfg["model"])):
+        run = q.Run(mm, 50_000, 1, q.PREC_FP32_BULK, 11)
+        run.sample(cfg["init"])
+        run.propagate(100, cfg["dt"], 10)
+        res.append(run.sums())
+    assert np.array_equal(res[0], res[1])
