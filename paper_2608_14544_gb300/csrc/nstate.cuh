@@ -24,13 +24,17 @@ __device__ __forceinline__ float q_sqrt<float>(float x) {
 
 // One Jacobi rotation annihilating A[p][q] of the symmetric matrix A and
 // accumulating it into the columns of V (Golub & Van Loan, symmetric Schur).
+// A zero A[p][q] gives the identity rotation (c = 1, s = 0 exactly, so every
+// update reproduces its input); it is selected rather than branched to, which
+// keeps the warp's walkers on one path.
 template <typename T, int NS>
 __device__ __forceinline__ void jacobi_rotate(T (&A)[NS][NS], T (&V)[NS][NS], int p, int q) {
   const T apq = A[p][q];
-  if (apq == T(0)) return;
-  const T tau = (A[q][q] - A[p][p]) / (T(2) * apq);
-  const T t = (tau >= T(0) ? T(1) : T(-1)) / (fabs(tau) + q_sqrt<T>(T(1) + tau * tau));
-  const T c = T(1) / q_sqrt<T>(T(1) + t * t);
+  const bool zero = apq == T(0);
+  const T tau = (A[q][q] - A[p][p]) / (T(2) * (zero ? T(1) : apq));
+  const T tr = (tau >= T(0) ? T(1) : T(-1)) / (fabs(tau) + q_sqrt<T>(T(1) + tau * tau));
+  const T t = zero ? T(0) : tr;
+  const T c = zero ? T(1) : T(1) / q_sqrt<T>(T(1) + t * t);
   const T s = t * c;
 #pragma unroll
   for (int k = 0; k < NS; ++k) {  // A <- A J (columns p, q)
@@ -117,6 +121,7 @@ __device__ __forceinline__ void eigh_ns(const T (&W)[NS][NS], const T (*ref)[NS]
   for (int a = 0; a < NS; ++a)
 #pragma unroll
     for (int b = 0; b < NS; ++b) fro += A[a][b] * A[a][b];
+#pragma unroll 1
   for (int sweep = 0; sweep < max_sweeps; ++sweep) {
     if (tol2 >= T(0) && offdiag2<T, NS>(A) <= tol2 * fro) break;
 #pragma unroll

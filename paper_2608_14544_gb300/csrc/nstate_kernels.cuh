@@ -581,7 +581,7 @@ __host__ __device__ constexpr int tri(int a, int b) {
 }
 
 template <int NS, int NPL>
-__global__ void __launch_bounds__(128, 1)
+__global__ void __launch_bounds__(128, NPL <= 8 ? (NS <= 4 ? 4 : (NS == 5 ? 3 : 1)) : 1)
     k_bulkN(const BulkParams bp, const CoefN cf, void* buf, double* __restrict__ part) {
   constexpr int NN = NS * NS, NTRI = NS * (NS + 1) / 2;
   constexpr int NP = (4 * NN + 15) / 16;  // observation passes of 32 quantities
