@@ -192,6 +192,105 @@ __device__ __forceinline__ void eigh_ns(const T (&W)[NS][NS], const T (*ref)[NS]
   }
 }
 
+// Warm-started decomposition for the FP32-bulk kernels: A = ref^T W ref (its
+// upper triangle), two cyclic Jacobi sweeps with the symmetric update
+// (a_pp -= t a_pq, a_qq += t a_pq, a_pq = 0, and the rows r != p, q rotated),
+// then U = ref V, eigenvalues ascending and each eigenvector's sign aligned with
+// its reference column.  The same rotations as eigh_ns in exact arithmetic, with
+// about a third fewer operations per rotation (no update of the elements the
+// rotation annihilates or leaves symmetric).
+template <int NS>
+__device__ __forceinline__ void eigh_warm_sym(const float (&W)[NS][NS], const float (&ref)[NS][NS],
+                                              float (&e)[NS], float (&U)[NS][NS]) {
+  float A[NS][NS], V[NS][NS];
+  {
+    float Wr[NS][NS];
+#pragma unroll
+    for (int i = 0; i < NS; ++i)
+#pragma unroll
+      for (int b = 0; b < NS; ++b) {
+        float acc = 0.0f;
+#pragma unroll
+        for (int k = 0; k < NS; ++k) acc = __fmaf_rn(W[i][k], ref[k][b], acc);
+        Wr[i][b] = acc;
+      }
+#pragma unroll
+    for (int a = 0; a < NS; ++a)
+#pragma unroll
+      for (int b = a; b < NS; ++b) {
+        float acc = 0.0f;
+#pragma unroll
+        for (int k = 0; k < NS; ++k) acc = __fmaf_rn(ref[k][a], Wr[k][b], acc);
+        A[a][b] = acc;  // upper triangle only
+      }
+  }
+#pragma unroll
+  for (int a = 0; a < NS; ++a)
+#pragma unroll
+    for (int b = 0; b < NS; ++b) V[a][b] = (a == b) ? 1.0f : 0.0f;
+  // upper-triangle element (i, j) of A for any order of i, j
+  auto at = [&](int i, int j) -> float& { return i < j ? A[i][j] : A[j][i]; };
+#pragma unroll 1
+  for (int sweep = 0; sweep < 2; ++sweep) {
+#pragma unroll
+    for (int p = 0; p < NS; ++p)
+#pragma unroll
+      for (int q = p + 1; q < NS; ++q) {
+        const float apq = A[p][q];
+        const bool zero = apq == 0.0f;
+        const float tau = (A[q][q] - A[p][p]) / (2.0f * (zero ? 1.0f : apq));
+        const float tr = (tau >= 0.0f ? 1.0f : -1.0f) / (fabsf(tau) + sqrtf(1.0f + tau * tau));
+        const float t = zero ? 0.0f : tr;
+        const float c = zero ? 1.0f : rsqrtf(1.0f + t * t);
+        const float sn = t * c;
+        A[p][p] = __fmaf_rn(-t, apq, A[p][p]);
+        A[q][q] = __fmaf_rn(t, apq, A[q][q]);
+        A[p][q] = 0.0f;
+#pragma unroll
+        for (int r = 0; r < NS; ++r) {
+          if (r == p || r == q) continue;
+          const float arp = at(r, p), arq = at(r, q);
+          at(r, p) = c * arp - sn * arq;
+          at(r, q) = sn * arp + c * arq;
+        }
+#pragma unroll
+        for (int k = 0; k < NS; ++k) {
+          const float vkp = V[k][p], vkq = V[k][q];
+          V[k][p] = c * vkp - sn * vkq;
+          V[k][q] = sn * vkp + c * vkq;
+        }
+      }
+  }
+#pragma unroll
+  for (int a = 0; a < NS; ++a) e[a] = A[a][a];
+  // ascending order of (e, columns of V) by a fixed compare network
+#pragma unroll
+  for (int i = 1; i < NS; ++i)
+#pragma unroll
+    for (int j = i; j > 0; --j) {
+      const bool sw = e[j] < e[j - 1];
+      const float t0 = e[j], t1 = e[j - 1];
+      e[j] = sw ? t1 : t0;
+      e[j - 1] = sw ? t0 : t1;
+#pragma unroll
+      for (int k = 0; k < NS; ++k) {
+        const float u0 = V[k][j], u1 = V[k][j - 1];
+        V[k][j] = sw ? u1 : u0;
+        V[k][j - 1] = sw ? u0 : u1;
+      }
+    }
+  // U = ref V; eigenvector a follows reference column a: <U_a, ref_a> = V[a][a]
+#pragma unroll
+  for (int i = 0; i < NS; ++i)
+#pragma unroll
+    for (int b = 0; b < NS; ++b) {
+      float acc = 0.0f;
+#pragma unroll
+      for (int k = 0; k < NS; ++k) acc = __fmaf_rn(ref[i][k], V[k][b], acc);
+      U[i][b] = V[b][b] < 0.0f ? -acc : acc;
+    }
+}
+
 // u_a^T M u_b for a symmetric M given as a full matrix
 template <typename T, int NS>
 __device__ __forceinline__ T bilinear(const T (&M)[NS][NS], const T (&U)[NS][NS], int a, int b) {

@@ -723,7 +723,7 @@ __global__ void __launch_bounds__(128, NPL <= 8 ? (NS <= 4 ? 4 : (NS == 5 ? 3 : 
 #pragma unroll
           for (int b = 0; b < NS; ++b) Uref[a][b] = U[a][b];
         build_w(W);
-        eigh_ns<float, NS>(W, Uref, e, U, 2, -1.0f);
+        eigh_warm_sym<NS>(W, Uref, e, U);
       }
       kick();  // second half kick at R_{n+1}
       const float de1 = pick<float, NS>(e, al) - pick<float, NS>(e, be);
