@@ -238,10 +238,15 @@ __device__ __forceinline__ void eigh_warm_sym(const float (&W)[NS][NS], const fl
       for (int q = p + 1; q < NS; ++q) {
         const float apq = A[p][q];
         const bool zero = apq == 0.0f;
-        const float tau = (A[q][q] - A[p][p]) / (2.0f * (zero ? 1.0f : apq));
-        const float tr = (tau >= 0.0f ? 1.0f : -1.0f) / (fabsf(tau) + sqrtf(1.0f + tau * tau));
+        // t = sgn(tau) / (|tau| + sqrt(1 + tau^2)) with approximate division and
+        // square root (c and s follow from the same t, so the rotation stays
+        // orthogonal to rounding); |tau| is capped at 1e18, where t < 1e-18
+        const float tau = fminf(fmaxf(__fdividef(A[q][q] - A[p][p], 2.0f * (zero ? 1.0f : apq)),
+                                      -1e18f), 1e18f);
+        const float w2 = __fmaf_rn(tau, tau, 1.0f);
+        const float tr = __fdividef(tau >= 0.0f ? 1.0f : -1.0f, fabsf(tau) + w2 * rsqrtf(w2));
         const float t = zero ? 0.0f : tr;
-        const float c = zero ? 1.0f : rsqrtf(1.0f + t * t);
+        const float c = zero ? 1.0f : rsqrtf(__fmaf_rn(t, t, 1.0f));
         const float sn = t * c;
         A[p][p] = __fmaf_rn(-t, apq, A[p][p]);
         A[q][q] = __fmaf_rn(t, apq, A[q][q]);

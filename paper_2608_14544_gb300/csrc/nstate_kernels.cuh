@@ -113,6 +113,15 @@ __device__ __forceinline__ void half_kick_g(const DevModel* M, double* R, double
 // nu = b are not events (amplitude 0, never drawn), so walking the slots in
 // order walks the 2 (NS - 1) events in their order.  Returns true if a needed
 // gap was degenerate.
+template <typename T>
+__device__ __forceinline__ T quot(T a, T b) {
+  return a / b;
+}
+template <>
+__device__ __forceinline__ float quot<float>(float a, float b) {
+  return __fdividef(a, b);
+}
+
 template <typename T, int NS>
 __device__ __forceinline__ bool event_amplitudes(const T (&G)[NS][NS], const T (&U)[NS][NS],
                                                  const T (&e)[NS], int al, int be, T dt, T tol,
@@ -144,7 +153,9 @@ __device__ __forceinline__ bool event_amplitudes(const T (&G)[NS][NS], const T (
       const bool ev = (slot == 0) ? (nu != al) : (nu != be);
       const bool dg = ev && fabs(gap) < tol;
       deg |= dg;
-      const T vd = (!ev || dg) ? T(0) : h / gap;
+      // FP32: approximate division (the amplitude enters a probability and a
+      // weight factor, both far above its 2-ulp error)
+      const T vd = (!ev || dg) ? T(0) : quot<T>(h, gap);
       A[slot * NS + nu] = (slot == 0) ? -dt * vd : dt * vd;
       is_event[slot * NS + nu] = ev;
     }
