@@ -143,6 +143,35 @@ def spawning_leg(qcl, torch, n0: int, steps: int, stride: int):
             "status_flags": flags}
 
 
+def ntraj_sweep_leg(qcl, torch, counts, steps: int):
+    """Walker-count sweep of the config-2 workload (the paper's statement that
+    the time is linear in the number of walkers): per N the CUDA-event time of
+    sample + propagate of `steps` steps, after one warm-up solve."""
+    cfg = wl.config(2)
+    stride, dt = cfg["out_stride"], cfg["dt"]
+    m = qcl.Model(cfg["model"])
+    m.autotune(dt, stride)
+    out = []
+    for nt in counts:
+        run = qcl.Run(m, int(nt), cfg["seed"], qcl.PREC_FP32_BULK, steps // stride + 1)
+        run.sample(cfg["init"])
+        run.propagate(steps, dt, stride)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record()
+        run.sample(cfg["init"])
+        run.propagate(steps, dt, stride)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        out.append({"n_traj": int(nt), "ms": ms, "walker_steps_per_s": nt * steps / (ms / 1e3),
+                    "ns_per_walker_step": ms * 1e6 / (nt * steps)})
+        del run
+    return {"workload": f"config-2 model, {steps} steps per point, FP32 bulk (sample + propagate)",
+            "points": out}
+
+
 def served_mix_leg(qcl, n_requests: int, traj_hi: float, arena_gb: float, quantum: int):
     """Poisson-arriving requests (mean gap 5 ms) drawn uniformly from the
     1-mode, 3-mode, 3-mode vibronic and 100-mode models and a random 4-state
@@ -460,6 +489,8 @@ def run_ours(args):
 
     spawning = spawning_leg(qcl, torch, args.spawn_walkers, 400, 20) if args.spawn_walkers > 0 \
         else None
+    sweep = ntraj_sweep_leg(qcl, torch, [1e4, 1e5, 1e6, 1e7, 1e8], 400) \
+        if (args.ntraj_sweep and rank == 0) else None
 
     served = None
     if args.served_requests > 0 and rank == 0:
@@ -534,6 +565,7 @@ def run_ours(args):
                      "value": rate_dia, "unit": "traj-steps/s", "kernel": "k_bulk2_dia",
                      "status_flags": std["flags"]},
         "spawning": spawning,
+        "ntraj_sweep": sweep,
         "served_mix": served,
         "clocks": clocks,
         "result": _result_summary(obs, cfg, status),
@@ -552,6 +584,7 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--sb100-walkers", type=int, default=2_000_000)
     ap.add_argument("--spawn-walkers", type=int, default=100_000)
+    ap.add_argument("--ntraj-sweep", type=int, default=1, help="0 skips the walker-count sweep")
     ap.add_argument("--served-requests", type=int, default=256)
     ap.add_argument("--served-traj-max", type=float, default=1e6)
     ap.add_argument("--served-arena-gb", type=float, default=48.0)
