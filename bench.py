@@ -502,6 +502,11 @@ def run_ours(args):
             dist.destroy_process_group()
         return
 
+    # our own FMA microbenchmarks beside the derived peak (FP32 FFMA for the bulk
+    # kernels, FP64 DFMA for the comparator)
+    peak_fp32_meas = qcl.measure_peak(0) / 1e12
+    peak_fp64_meas = qcl.measure_peak(1) / 1e12
+
     # roofline of the dominant kernel (FP32 ALU bound)
     props = torch.cuda.get_device_properties(0)
     n_sm = props.multi_processor_count
@@ -538,6 +543,8 @@ def run_ours(args):
                      "kernel": "k_bulk2 (persistent FP32-bulk walker kernel)",
                      "flops_per_traj_step": fl,
                      "peak_basis": f"{n_sm} SMs x 128 FP32 lanes x 2 flop x {max_mhz:.0f} MHz",
+                     "peak_microbench_tflops": {"fp32_ffma": peak_fp32_meas,
+                                                "fp64_dfma": peak_fp64_meas},
                      "kernel_ms_per_launch": bulk_ms / max(bulk_n, 1),
                      "launches": bulk_n},
         "cpu_baseline": {"value": cpu_rate, "unit": "traj-steps/s", "cores": cpu_threads,
@@ -549,7 +556,9 @@ def run_ours(args):
         "fp64_comparator": {"value": fp64_rate, "unit": "traj-steps/s",
                             "sample": f"{n:.0e} walkers x {fp64_steps - stride} steps, one "
                                       "launch per step", "step_kernel_ms": f64_ms / max(f64_n, 1),
-                            "speedup_of_fp32_bulk": value / world / fp64_rate},
+                            "speedup_of_fp32_bulk": value / world / fp64_rate,
+                            "frac_of_fp64_dfma_peak": fp64_rate * fl / 1e12 / peak_fp64_meas
+                            if peak_fp64_meas > 0 else None},
         "sb100": {"workload": f"100-mode ohmic spin-boson (eps=Delta=1, xi=0.25, wc=5, beta=1), "
                               f"{n4} walkers x {c4['n_steps']} steps, dt={c4['dt']}",
                   "value": rate4, "unit": "traj-steps/s",

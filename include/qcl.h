@@ -281,6 +281,13 @@ qcl_status qcl_shard_tile_walkers(const qcl_model* model, int32_t precision, int
 qcl_status qcl_combine_shards(const double* shard_sums, int32_t n_shards, int64_t n_elems,
                               double* out);
 
+/* Measured multiply-add throughput of the current device (no counterpart in
+ * the paper; the roofline denominators): which = 0 FP32 FFMA, 1 FP64 DFMA.
+ * Runs a fixed microbenchmark (independent FMA chains on every SM, timed with
+ * CUDA events on `stream`, about 10-100 ms) and returns flops per second
+ * (2 per FMA).  Synchronises the stream. */
+qcl_status qcl_measure_peak(int32_t which, double* flops_per_s, void* stream);
+
 /* ---------------------------------------------------------------------------
  * Launch shape and autotuning of the FP32-bulk persistent kernels (no
  * counterpart in the paper).  Two knobs, neither of which changes a bit of any

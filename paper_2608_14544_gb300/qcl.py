@@ -36,7 +36,7 @@ EXPORTS = [
     "qcl_server_stats", "qcl_server_destroy", "qcl_shard_tile_walkers", "qcl_combine_shards",
     "qcl_spawn_bytes", "qcl_spawn_layout", "qcl_spawn_sample", "qcl_spawn_propagate",
     "qcl_spawn_live", "qcl_set_launch_shape", "qcl_get_launch_shape", "qcl_autotune_bytes",
-    "qcl_autotune",
+    "qcl_autotune", "qcl_measure_peak",
 ]
 FLAG_SPAWN_OVERFLOW = 8
 REQ_QUEUED, REQ_RUNNING, REQ_DONE, REQ_ERROR = 0, 1, 2, 3
@@ -158,6 +158,7 @@ def load(path: str = LIB_PATH):
     lib.qcl_get_launch_shape.argtypes = [vp, vp]
     lib.qcl_autotune_bytes.argtypes = [vp, i64, i64, i32, vp]
     lib.qcl_autotune.argtypes = [vp, i64, i64, C.c_double, i32, vp, sz, vp, vp]
+    lib.qcl_measure_peak.argtypes = [i32, vp, vp]
     for name in EXPORTS:
         f = getattr(lib, name)
         if name not in ("qcl_last_error", "qcl_version"):
@@ -431,6 +432,14 @@ class Run:
                 "alpha": (arr(off[6], nt, np.uint16, 2) & 0xF).astype(np.int32),
                 "q": ((arr(off[6], nt, np.uint16, 2) >> 4) & 0x3).astype(np.int32),
                 "beta": (arr(off[6], nt, np.uint16, 2) >> 8).astype(np.int32), **extra}
+
+
+def measure_peak(which: int, stream=None) -> float:
+    """Measured FMA throughput of the device in flops/s: 0 = FP32, 1 = FP64."""
+    v = C.c_double()
+    _check(load().qcl_measure_peak(int(which), C.byref(v), _stream_ptr(stream)),
+           "qcl_measure_peak")
+    return v.value
 
 
 # ----------------------------------------------------------------- spawning --

@@ -122,3 +122,9 @@ def test_launch_shape_validation_without_gpu(lib):
     b = C.c_size_t()
     assert lib.qcl_autotune_bytes(None, 1024, 10, 10, C.byref(b)) == 1
     assert lib.qcl_autotune(None, 1024, 10, 0.01, 10, None, 0, C.byref(sh), None) == 1
+
+
+def test_measure_peak_validation_without_gpu(lib):
+    v = C.c_double()
+    assert lib.qcl_measure_peak(0, None, None) == 1
+    assert lib.qcl_measure_peak(7, C.byref(v), None) == 1

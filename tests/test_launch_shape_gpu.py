@@ -68,3 +68,15 @@ def test_autotune_picks_a_measured_shape(q):
         run.propagate(100, cfg["dt"], 10)
         res.append(run.sums())
     assert np.array_equal(res[0], res[1])
+
+
+def test_fma_microbenchmarks_are_plausible(q):
+    import torch
+
+    props = torch.cuda.get_device_properties(0)
+    fp32 = q.measure_peak(0)
+    fp64 = q.measure_peak(1)
+    # FP32: 128 lanes x 2 flop per SM-cycle at 1-2.1 GHz
+    per_sm_cycle = fp32 / props.multi_processor_count / 2.1e9
+    assert 0.3 * 256 < per_sm_cycle < 1.05 * 256, per_sm_cycle
+    assert 0 < fp64 < fp32
