@@ -72,19 +72,38 @@ BULK2_SOURCES = [os.path.join(ROOT, "paper_2608_14544_gb300", "csrc", f)
                            "kernels.h")]
 
 
-def _profiled_traffic(kernel_srcs, summary: str):
-    """DRAM bytes per launch from the committed ncu summary, or None when the
-    kernel's sources have changed since the counters were taken."""
+def _profiled(kernel_srcs, summary: str, key: str):
+    """A figure from the committed ncu summary (`key: value` line), or None
+    when the kernel's sources have changed since the counters were taken."""
     try:
         txt = open(summary).read()
         h = kernel_source_hash(kernel_srcs)
     except OSError:
         return None
     vals = dict(ln.split(":", 1) for ln in txt.splitlines()
-                if ln.startswith(("traffic_bytes_per_launch:", "traffic_source_sha256_prefix:")))
-    if vals.get("traffic_source_sha256_prefix", "").strip() != h:
+                if ln.startswith((key + ":", "traffic_source_sha256_prefix:")))
+    if vals.get("traffic_source_sha256_prefix", "").strip() != h or key not in vals:
         return None
-    return float(vals["traffic_bytes_per_launch"])
+    return float(vals[key])
+
+
+def _profiled_traffic(kernel_srcs, summary: str):
+    """DRAM bytes per launch from the committed ncu summary (None if stale)."""
+    return _profiled(kernel_srcs, summary, "traffic_bytes_per_launch")
+
+
+def _issue_roofline(walker_steps_per_s: float, n_sm: int, mhz: float):
+    """The kernel is bound by instruction issue: warp instructions per second
+    (ncu's instructions per walker-step x the measured rate / 32) against one
+    issue per cycle on each of the 4 schedulers of every SM."""
+    ipw = _profiled(BULK2_SOURCES, os.path.join(ROOT, "profiles", "k_bulk2_sb3mode.md"),
+                    "instructions_per_walker_step")
+    if ipw is None:
+        return None
+    achieved = walker_steps_per_s * ipw / 32.0
+    peak = n_sm * 4 * mhz * 1e6
+    return {"instructions_per_walker_step": ipw, "achieved_warp_instr_per_s": achieved,
+            "peak_warp_instr_per_s": peak, "frac": achieved / peak}
 
 
 def _result_summary(obs, cfg, status):
@@ -545,6 +564,7 @@ def run_ours(args):
                      "peak_basis": f"{n_sm} SMs x 128 FP32 lanes x 2 flop x {max_mhz:.0f} MHz",
                      "peak_microbench_tflops": {"fp32_ffma": peak_fp32_meas,
                                                 "fp64_dfma": peak_fp64_meas},
+                     "issue_slots": _issue_roofline(value / world, n_sm, max_mhz),
                      "kernel_ms_per_launch": bulk_ms / max(bulk_n, 1),
                      "launches": bulk_n},
         "cpu_baseline": {"value": cpu_rate, "unit": "traj-steps/s", "cores": cpu_threads,
