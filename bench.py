@@ -123,43 +123,64 @@ def _result_summary(obs, cfg, status):
 
 def spawning_leg(qcl, torch, n0: int, steps: int, stride: int):
     """Trajectory spawning (the CPU code's scheme) against the fixed no-spawn
-    ensemble on the 1-mode spin-boson model: the standard error of the upper
-    adiabatic population at t = steps dt, the walker-steps each scheme spent,
-    and the variance x walker-steps product (lower is better; equal cost
-    compares SE^2 directly).  Both FP64, same seed."""
+    ensemble on the 1-mode spin-boson model, in FP64 and in FP32 bulk: the
+    standard error of the upper adiabatic population at t = steps dt, the
+    walker-steps each spent, the GPU time (CUDA events, sample + propagate), and
+    the products variance x walker-steps and variance x seconds (lower is
+    better).  Same seed for all four."""
     cfg = wl.config(1)
     dt = cfg["dt"]
     m = qcl.Model(cfg["model"])
-    cap = 64 * n0
-    sp = qcl.SpawnRun(m, n0, cap, cfg["seed"], steps // stride + 1)
-    sp.sample(cfg["init"])
-    live = [sp.n_live()]
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    for _ in range(steps // stride):
-        sp.propagate(stride, dt, stride)
-        live.append(sp.n_live())
-    torch.cuda.synchronize()
-    t_spawn = time.perf_counter() - t0
-    ws_spawn = float(sum(0.5 * (live[k] + live[k + 1]) * stride for k in range(len(live) - 1)))
-    o_s = sp.observables()
-    flags = sp.status()["flags"]
-    ns = qcl.Run(m, n0, cfg["seed"], qcl.PREC_FP64, steps // stride + 1)
-    ns.sample(cfg["init"])
-    ns.propagate(steps, dt, stride)
-    o_n = ns.observables()
-    ws_ns = float(n0) * steps
-    se_s, se_n = float(o_s[-1, 16 + 14]), float(o_n[-1, 16 + 14])
-    return {"workload": f"1-mode spin-boson (cfg 1 model), {n0} initial walkers, {steps} steps "
-                        f"(t = {steps * dt:g}), FP64",
+    out = {"workload": f"1-mode spin-boson (cfg 1 model), {n0} initial walkers, {steps} steps "
+                       f"(t = {steps * dt:g})"}
+    for name, prec in (("fp64", qcl.PREC_FP64), ("fp32", qcl.PREC_FP32_BULK)):
+        sp = qcl.SpawnRun(m, n0, 64 * n0, cfg["seed"], steps // stride + 1, precision=prec)
+        live = []
+        t_sp = 0.0
+        for rep in range(2):  # the first run warms up
+            sp.sample(cfg["init"])
+            live = [sp.n_live()]
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            ms = 0.0
+            for _ in range(steps // stride):
+                e0.record()
+                sp.propagate(stride, dt, stride)
+                e1.record()
+                torch.cuda.synchronize()
+                ms += e0.elapsed_time(e1)
+                live.append(sp.n_live())
+            t_sp = ms / 1e3
+        ws = float(sum(0.5 * (live[k] + live[k + 1]) * stride for k in range(len(live) - 1)))
+        o_s = sp.observables()
+        flags = sp.status()["flags"]
+        del sp
+        ns = qcl.Run(m, n0, cfg["seed"], prec, steps // stride + 1)
+        ns.sample(cfg["init"])
+        ns.propagate(steps, dt, stride)
+        ns.sample(cfg["init"])
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        ns.propagate(steps, dt, stride)
+        e1.record()
+        torch.cuda.synchronize()
+        t_ns = e0.elapsed_time(e1) / 1e3
+        o_n = ns.observables()
+        del ns
+        ws_ns = float(n0) * steps
+        se_s, se_n = float(o_s[-1, 16 + 14]), float(o_n[-1, 16 + 14])
+        out[name] = {
             "P_ad_upper": {"spawn": float(o_s[-1, 14]), "no_spawn": float(o_n[-1, 14])},
             "se_P_ad_upper": {"spawn": se_s, "no_spawn": se_n},
-            "walker_steps": {"spawn": ws_spawn, "no_spawn": ws_ns},
+            "walker_steps": {"spawn": ws, "no_spawn": ws_ns},
             "final_walkers": live[-1],
-            "variance_x_walker_steps": {"spawn": se_s ** 2 * ws_spawn,
-                                        "no_spawn": se_n ** 2 * ws_ns},
-            "spawn_walker_steps_per_s": ws_spawn / t_spawn,
+            "seconds": {"spawn": t_sp, "no_spawn": t_ns},
+            "walker_steps_per_s": {"spawn": ws / t_sp, "no_spawn": ws_ns / t_ns},
+            "variance_x_walker_steps": {"spawn": se_s ** 2 * ws, "no_spawn": se_n ** 2 * ws_ns},
+            "variance_x_seconds": {"spawn": se_s ** 2 * t_sp, "no_spawn": se_n ** 2 * t_ns},
             "status_flags": flags}
+    return out
 
 
 def ntraj_sweep_leg(qcl, torch, counts, steps: int):

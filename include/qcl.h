@@ -331,7 +331,8 @@ qcl_status qcl_autotune(qcl_model* model, int64_t probe_walkers, int64_t n_steps
                         qcl_launch_shape* best, void* stream);
 
 /* ---------------------------------------------------------------------------
- * Trajectory spawning (FP64, two-state models, either representation).
+ * Trajectory spawning (two-state models, either representation; FP64, or
+ * FP32 bulk with at most 32 modes).
  *
  * The scheme of the CPU code that the paper's GPU version replaces (Sec. II B:
  * there a new trajectory was started each time a transition test fired, so
@@ -347,8 +348,11 @@ qcl_status qcl_autotune(qcl_model* model, int64_t probe_walkers, int64_t n_steps
  * stream is keyed by words 0-1 of Philox block (c0 = step, parent id, purpose
  * 3) with bit 63 set.
  *
- * ens->n_traj is the number n0 of initial walkers (families); capacity is the
- * walker slots the buffer holds (n0 <= capacity <= 2^36).  The observation
+ * ens->n_traj is the number n0 of initial walkers (families) and
+ * ens->precision the arithmetic (QCL_PREC_FP64, or QCL_PREC_FP32_BULK: the
+ * FP32-bulk walker arithmetic -- compensated phase and weight pairs with a
+ * carried exponent -- one step per launch with the state in HBM); capacity is
+ * the walker slots the buffer holds (n0 <= capacity <= 2^36).  The observation
  * buffer is sized by qcl_obs_bytes(model, ens, n_out) as for any FP64
  * ensemble; its rows hold, per output, the sums over families of the family
  * sums X_k of the walker contributions and of X_k^2, so qcl_reduce_observables
@@ -364,11 +368,13 @@ qcl_status qcl_spawn_bytes(const qcl_model* model, const qcl_ensemble_desc* ens,
                            size_t* bytes);
 
 /* Byte offsets within the buffer of walker set `set` (0 or 1; the current set
- * is the ensemble's step & 1): offsets[0..6] = R [n_modes][capacity] (double),
- * P (same), m (double), phi (double), index pair (uint16: a | q << 4 | b << 8),
- * random-stream id (uint64), family (uint32); offsets[7] = total bytes. */
+ * is the ensemble's step & 1): offsets[0..6] = R [n_modes][capacity], P (same),
+ * m, phi (double in FP64, float in FP32), index pair (uint16: a | q << 4 |
+ * b << 8), random-stream id (uint64), family (uint32); offsets[7] = total
+ * bytes; FP32 only (0 in FP64): offsets[8] = m_lo (float), [9] = m_exp
+ * (int32; the weight is (m + m_lo) 2^m_exp), [10] = phi_lo (float). */
 qcl_status qcl_spawn_layout(const qcl_model* model, const qcl_ensemble_desc* ens, int64_t capacity,
-                            int32_t set, size_t offsets[8]);
+                            int32_t set, size_t offsets[11]);
 
 /* Samples the n0 initial walkers into set 0 (as qcl_sample_initial; ids
  * traj_id_offset + i, family i). */

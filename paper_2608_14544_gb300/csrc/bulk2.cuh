@@ -211,6 +211,130 @@ __device__ __forceinline__ void block_end(Scal& z) {
   z.ph = two_sum(z.ph.hi, z.ph.lo);
 }
 
+// FP32 initial sample of one walker with random-stream id `traj` from the same
+// Philox words as the FP64 path: (R, P) at Rg[j * stride], Pg[j * stride], the
+// weight mantissa mh (low part, exponent and phase start at 0) and the index
+// pair word ab.
+__device__ __forceinline__ void sample_walker_f32(const DevModel* __restrict__ M,
+                                                  const SampleParams& sp, uint64_t traj,
+                                                  float* Rg, float* Pg, int64_t stride, float& mh,
+                                                  uint16_t& ab) {
+  const int n = sp.n;
+  float a = (float)M->a0, b = (float)M->b0;
+  for (int j = 0; j < n; ++j) {
+    float R = (float)sp.R0[j], P = (float)sp.P0[j];
+    if (sp.wigner) {
+      const u4 wd = philox_draw(sp.seed, (uint32_t)j, traj, kPurposeInit);
+      const float u0 = __fmaf_rn(__uint2float_rn(wd.x), 0x1p-32f, 0x1p-33f);
+      const float u1 = __fmaf_rn(__uint2float_rn(wd.y), 0x1p-32f, 0x1p-33f);
+      const float rad = sqrtf(-2.0f * logf(u0));
+      float sn, cs;
+      sincospif(2.0f * u1, &sn, &cs);
+      R = __fmaf_rn((float)sp.sR[j] * rad, cs, R);
+      P = __fmaf_rn((float)sp.sP[j] * rad, sn, P);
+    }
+    Rg[(int64_t)j * stride] = R;
+    Pg[(int64_t)j * stride] = P;
+    a = __fmaf_rn((float)M->a[j], R, a);
+    b = __fmaf_rn((float)M->b[j], R, b);
+  }
+  const float r2 = a * a + b * b;
+  float c = 1.0f, s = 0.0f;
+  if (r2 > 0.0f) {
+    const float ir = rsqrtf(r2);
+    const float c2 = a * ir, s2 = b * ir;
+    if (a >= 0.0f) {
+      c = sqrtf(0.5f + 0.5f * c2);
+      s = 0.5f * s2 / c;
+    } else {
+      s = copysignf(sqrtf(0.5f - 0.5f * c2), b);
+      c = 0.5f * s2 / s;
+    }
+  }
+  const float U[4] = {-s, c, c, s};
+  double rho_ad[4];  // the density in the walkers' representation
+  double tot = 0.0;
+  for (int al = 0; al < 2; ++al)
+    for (int be = 0; be < 2; ++be) {
+      float acc = 0.0f;
+      if (M->repr == QCL_REPR_DIABATIC) {
+        acc = (float)sp.rho[al * 2 + be];
+      } else {
+        for (int k = 0; k < 2; ++k)
+          for (int l = 0; l < 2; ++l)
+            acc = __fmaf_rn(U[k * 2 + al] * (float)sp.rho[k * 2 + l], U[l * 2 + be], acc);
+      }
+      rho_ad[al * 2 + be] = acc;
+      tot += fabsf(acc);
+    }
+  // index pair from |rho_ad| with 2^-24 quantised probabilities (remainder to the
+  // last nonzero pair), m0 = rho_ad / p_hat
+  uint32_t Tk[4];
+  uint32_t sumT = 0;
+  int last = 0;
+  for (int k = 0; k < 4; ++k) {
+    Tk[k] = (uint32_t)floorf((float)(fabs(rho_ad[k]) / tot) * kP24f);
+    sumT += Tk[k];
+    if (rho_ad[k] != 0.0) last = k;
+  }
+  Tk[last] += 16777216u - sumT;
+  const u4 wd = philox_draw(sp.seed, (uint32_t)n, traj, kPurposeInit);
+  const uint32_t y = wd.x >> 8;
+  uint32_t cum = 0;
+  int pick = last;
+  for (int k = 0; k < 4; ++k) {
+    cum += Tk[k];
+    if (y < cum) {
+      pick = k;
+      break;
+    }
+  }
+  mh = (float)rho_ad[pick] * (kP24f / (float)Tk[pick]);
+  ab = (uint16_t)((pick >> 1) | ((pick & 1) << 8));
+}
+
+// Transition test of a spawning walker (the scheme that starts a new walker
+// whenever the test fires): the phase as in phase_and_transition (DIA: as in
+// dia_phase_and_transition, w_old = a(R_n), Bv = b(R_{n+1})); when the test
+// fires for event e, `child` becomes a copy of the walker with its weight times
+// A_e / p_hat_e, the flipped index and (DIA) the event's quarter turns, and the
+// walker keeps its pair and weight (no stay factor).  Returns whether it fired.
+template <int KIND, bool DIA>
+__device__ __forceinline__ bool spawn_transition(Scal& z, float w_old, float Av, float Bv,
+                                                 uint32_t word, const BulkParams& bp,
+                                                 unsigned int& deg, Scal& child) {
+  uint32_t T;
+  float fac;  // A_e 2^24 of the first-index event (DIA: both events)
+  if (DIA) {
+    const f2 ps = two_sum(z.ph.hi, bp.hdt_hbar * (z.sb - z.sa) * (w_old + z.A));
+    z.ph = {ps.hi, z.ph.lo + ps.lo};
+    T = min(__float2uint_rz((bp.kamp * kP24f) * fabsf(Bv)), bp.tmax >> 1);
+    fac = (bp.amp * kP24f) * Bv;
+  } else {
+    const f2 ps = two_sum(z.ph.hi, bp.hdt_hbar * (z.sa - z.sb) * (w_old + z.r));
+    z.ph = {ps.hi, z.ph.lo + ps.lo};
+    const bool degen = z.r2 < 0.25f * kDegTol32 * kDegTol32;
+    deg += degen ? 1u : 0u;
+    const float gn = (KIND == 1) ? 0.5f * (z.A * Bv - z.B * Av) : (-0.5f * bp.b0) * Av;
+    const float g = degen ? 0.0f : gn * (z.ir * z.ir);
+    T = min(__float2uint_rz((bp.kamp * kP24f) * fabsf(g)), bp.tmax >> 1);
+    fac = (bp.amp * kP24f) * g;
+  }
+  const uint32_t y = word >> 8;
+  const bool hop1 = y < T;
+  const bool hop = y < 2u * T;
+  if (!hop) return false;
+  child = z;
+  // adiabatic: A_1 = -sig_a dt g, A_2 = -sig_b dt g; diabatic: both c = b dt / hbar
+  const float num = DIA ? fac : -(hop1 ? z.sa : z.sb) * fac;
+  weight_factor(child, num, T);
+  child.m = fast_two_sum(child.m.hi, child.m.lo);
+  if (hop1) child.sa = -child.sa;
+  else child.sb = -child.sb;
+  if (DIA) child.q = (child.q + (hop1 ? 3 : 1)) & 3;
+  return true;
+}
+
 // Keeps the stored phase within about 2^10 rad, where the three-part
 // reduction below is exact; every holder of a walker calls it at the same
 // steps (the observations).

@@ -130,23 +130,34 @@ struct SpawnHeader {
 constexpr size_t kSpawnHeaderOff = 64;  // after EnsHeader, inside the first 256 bytes
 
 struct SpawnLayout {
-  // walker set: R[n][cap], P[n][cap], m, phi, ab, id (uint64), fam (uint32)
+  // walker set: R[n][cap], P[n][cap], m, phi, ab (uint16), id (uint64),
+  // fam (uint32); FP32 sets add m_lo, m_exp (int32) and phi_lo (compensated
+  // pairs with a carried exponent, as in the bulk kernels)
   size_t set_off[2];
-  size_t R, P, m, phi, ab, id, fam, set_bytes;
-  size_t cm, cab, flag, bsum, boff, fstart, total;
+  size_t R, P, m, mlo, mexp, phi, philo, ab, id, fam, set_bytes;
+  // staging of a step's children, per parent: weight (FP32: hi, lo, exp), pair
+  size_t cm, cmlo, cmexp, cab, flag, bsum, boff, fstart, total;
   int64_t n_blocks;  // capacity / 256, rounded up
-  __host__ __device__ static SpawnLayout make(int64_t cap, int n, int64_t n0) {
+  __host__ __device__ static SpawnLayout make(int64_t cap, int n, int64_t n0, int precision) {
     SpawnLayout L{};
     const size_t c = (size_t)cap;
+    const bool f32 = precision == QCL_PREC_FP32_BULK;
+    const size_t w = f32 ? 4 : 8;
     size_t o = 0;
     L.R = o;
-    o = align256(o + 8 * c * (size_t)n);
+    o = align256(o + w * c * (size_t)n);
     L.P = o;
-    o = align256(o + 8 * c * (size_t)n);
+    o = align256(o + w * c * (size_t)n);
     L.m = o;
-    o = align256(o + 8 * c);
+    o = align256(o + w * c);
+    L.mlo = o;
+    if (f32) o = align256(o + 4 * c);
+    L.mexp = o;
+    if (f32) o = align256(o + 4 * c);
     L.phi = o;
-    o = align256(o + 8 * c);
+    o = align256(o + w * c);
+    L.philo = o;
+    if (f32) o = align256(o + 4 * c);
     L.ab = o;
     o = align256(o + 2 * c);
     L.id = o;
@@ -158,7 +169,11 @@ struct SpawnLayout {
     L.set_off[1] = 256 + L.set_bytes;
     o = 256 + 2 * L.set_bytes;
     L.cm = o;
-    o = align256(o + 8 * c);
+    o = align256(o + w * c);
+    L.cmlo = o;
+    if (f32) o = align256(o + 4 * c);
+    L.cmexp = o;
+    if (f32) o = align256(o + 4 * c);
     L.cab = o;
     o = align256(o + 2 * c);
     L.flag = o;
@@ -185,6 +200,22 @@ void launch_spawn_step(const DevModel* dm, int repr, void* buf, int64_t capacity
 // families).
 void launch_spawn_observe(const DevModel* dm, const void* buf, int64_t capacity, int n, int64_t n0,
                           int set, double* part, cudaStream_t st);
+// Grid of the spawning kernels: a few blocks per SM, each walking groups of 256
+// walkers up to the live count (which the host does not know).
+unsigned spawn_grid(int64_t capacity);
+// The block-count scan and the family starts, for either precision's layout.
+void launch_spawn_scan(void* buf, int64_t capacity, int n, int64_t n0, int precision, int64_t step0,
+                       int64_t step, cudaStream_t st);
+void launch_spawn_fstart(const void* buf, int64_t capacity, int n, int64_t n0, int precision, int set,
+                         cudaStream_t st);
+// FP32-bulk spawning (two states, n <= 32 modes): sample, one step (step
+// kernel, scan, scatter), family observation.
+void launch_spawn_sample32(const DevModel* dm, const SampleParams& sp, int64_t capacity, void* buf,
+                           cudaStream_t st);
+int launch_spawn_step32(const BulkParams& bp, const Coef2& cf, void* buf, int64_t capacity,
+                        int64_t n0, int64_t step0, int64_t step, cudaStream_t st);
+void launch_spawn_observe32(const BulkParams& bp, const Coef2& cf, const void* buf, int64_t capacity,
+                            int64_t n0, int set, double* part, cudaStream_t st);
 
 // Kernel launches issued by the library (instrumentation).
 void launches_add(int64_t k);

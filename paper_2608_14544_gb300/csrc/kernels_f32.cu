@@ -31,82 +31,15 @@ __global__ void __launch_bounds__(256) k_sample_f32(const DevModel* __restrict__
     w.hdr->n_nonfinite = 0;
   }
   if (i >= nt) return;
-  const uint64_t traj = sp.traj_offset + (uint64_t)i;
-  float a = (float)M->a0, b = (float)M->b0;
-  for (int j = 0; j < n; ++j) {
-    float R = (float)sp.R0[j], P = (float)sp.P0[j];
-    if (sp.wigner) {
-      const u4 wd = philox_draw(sp.seed, (uint32_t)j, traj, kPurposeInit);
-      const float u0 = __fmaf_rn(__uint2float_rn(wd.x), 0x1p-32f, 0x1p-33f);
-      const float u1 = __fmaf_rn(__uint2float_rn(wd.y), 0x1p-32f, 0x1p-33f);
-      const float rad = sqrtf(-2.0f * logf(u0));
-      float sn, cs;
-      sincospif(2.0f * u1, &sn, &cs);
-      R = __fmaf_rn((float)sp.sR[j] * rad, cs, R);
-      P = __fmaf_rn((float)sp.sP[j] * rad, sn, P);
-    }
-    w.R[(int64_t)j * nt + i] = R;
-    w.P[(int64_t)j * nt + i] = P;
-    a = __fmaf_rn((float)M->a[j], R, a);
-    b = __fmaf_rn((float)M->b[j], R, b);
-  }
-  const float r2 = a * a + b * b;
-  float c = 1.0f, s = 0.0f;
-  if (r2 > 0.0f) {
-    const float ir = rsqrtf(r2);
-    const float c2 = a * ir, s2 = b * ir;
-    if (a >= 0.0f) {
-      c = sqrtf(0.5f + 0.5f * c2);
-      s = 0.5f * s2 / c;
-    } else {
-      s = copysignf(sqrtf(0.5f - 0.5f * c2), b);
-      c = 0.5f * s2 / s;
-    }
-  }
-  const float U[4] = {-s, c, c, s};
-  double rho_ad[4];  // the density in the walkers' representation
-  double tot = 0.0;
-  for (int al = 0; al < 2; ++al)
-    for (int be = 0; be < 2; ++be) {
-      float acc = 0.0f;
-      if (M->repr == QCL_REPR_DIABATIC) {
-        acc = (float)sp.rho[al * 2 + be];
-      } else {
-        for (int k = 0; k < 2; ++k)
-          for (int l = 0; l < 2; ++l)
-            acc = __fmaf_rn(U[k * 2 + al] * (float)sp.rho[k * 2 + l], U[l * 2 + be], acc);
-      }
-      rho_ad[al * 2 + be] = acc;
-      tot += fabsf(acc);
-    }
-  // index pair from |rho_ad| with 2^-24 quantised probabilities (remainder to the
-  // last nonzero pair), m0 = rho_ad / p_hat
-  uint32_t Tk[4];
-  uint32_t sumT = 0;
-  int last = 0;
-  for (int k = 0; k < 4; ++k) {
-    Tk[k] = (uint32_t)floorf((float)(fabs(rho_ad[k]) / tot) * kP24f);
-    sumT += Tk[k];
-    if (rho_ad[k] != 0.0) last = k;
-  }
-  Tk[last] += 16777216u - sumT;
-  const u4 wd = philox_draw(sp.seed, (uint32_t)n, traj, kPurposeInit);
-  const uint32_t y = wd.x >> 8;
-  uint32_t cum = 0;
-  int pick = last;
-  for (int k = 0; k < 4; ++k) {
-    cum += Tk[k];
-    if (y < cum) {
-      pick = k;
-      break;
-    }
-  }
-  w.mh[i] = (float)rho_ad[pick] * (kP24f / (float)Tk[pick]);
+  float mh;
+  uint16_t ab;
+  sample_walker_f32(M, sp, sp.traj_offset + (uint64_t)i, w.R + i, w.P + i, nt, mh, ab);
+  w.mh[i] = mh;
   w.ml[i] = 0.0f;
   w.me[i] = 0;
   w.ph[i] = 0.0f;
   w.pl[i] = 0.0f;
-  w.ab[i] = (uint16_t)((pick >> 1) | ((pick & 1) << 8));
+  w.ab[i] = ab;
 }
 
 // One thread per walker, all modes in registers, coefficients as constant-bank

@@ -293,6 +293,20 @@ qcl_status qcl_obs_bytes(const qcl_model* model, const qcl_ensemble_desc* ens, i
 }  // extern "C"
 
 namespace {
+// FP32 per-mode coefficients of a two-state model for time step dt.
+void fill_coef2(const qcl_model* model, double dt, Coef2* cf) {
+  const DevModel& h = model->host;
+  for (int j = 0; j < model->n; ++j) {
+    cf->hk[j] = (float)(0.5 * dt * h.k[j]);
+    cf->hs[j] = (float)(0.5 * dt * h.s[j]);
+    cf->dtm[j] = (float)(dt / h.mass[j]);
+    cf->a[j] = (float)h.a[j];
+    cf->b[j] = (float)h.b[j];
+    cf->am[j] = (float)(h.a[j] / h.mass[j]);
+    cf->bm[j] = (float)(h.b[j] / h.mass[j]);
+  }
+}
+
 // Validates an initial condition and builds the sampling parameters.
 qcl_status prepare_sample(const qcl_model* model, const qcl_ensemble_desc* ens, const qcl_init_desc* init,
                           SampleParams** out) {
@@ -405,15 +419,7 @@ qcl_status qcl_propagate(const qcl_model* model, const qcl_ensemble_desc* ens, v
     Coef2* cf = new (std::nothrow) Coef2();
     if (!cf) return fail(QCL_ERR_OUT_OF_MEMORY, "host allocation failed");
     const DevModel& h = model->host;
-    for (int j = 0; j < model->n; ++j) {
-      cf->hk[j] = (float)(0.5 * dt * h.k[j]);
-      cf->hs[j] = (float)(0.5 * dt * h.s[j]);
-      cf->dtm[j] = (float)(dt / h.mass[j]);
-      cf->a[j] = (float)h.a[j];
-      cf->b[j] = (float)h.b[j];
-      cf->am[j] = (float)(h.a[j] / h.mass[j]);
-      cf->bm[j] = (float)(h.b[j] / h.mass[j]);
-    }
+    fill_coef2(model, dt, cf);
     BulkParams bp{};
     bp.n_traj = nt;
     bp.n_tiles = OL.n_tiles;
@@ -691,8 +697,9 @@ namespace {
 qcl_status check_spawn(const qcl_model* m, const qcl_ensemble_desc* e, int64_t capacity) {
   qcl_status st = check_ens(m, e);
   if (st) return st;
-  if (e->precision != QCL_PREC_FP64) return fail(QCL_ERR_UNSUPPORTED, "spawning ensembles are FP64");
   if (m->ns != 2) return fail(QCL_ERR_UNSUPPORTED, "spawning takes two-state models (n_states = %d)", m->ns);
+  if (e->precision == QCL_PREC_FP32_BULK && m->n > 32)
+    return fail(QCL_ERR_UNSUPPORTED, "FP32-bulk spawning takes at most 32 modes (got %d)", m->n);
   if (e->n_traj >= ((int64_t)1 << 31)) return fail(QCL_ERR_INVALID_ARG, "n_traj must be below 2^31 for a spawning ensemble");
   if (capacity < e->n_traj || capacity > ((int64_t)1 << 36))
     return fail(QCL_ERR_INVALID_ARG, "capacity %lld outside [n_traj, 2^36]", (long long)capacity);
@@ -706,18 +713,19 @@ qcl_status qcl_spawn_bytes(const qcl_model* model, const qcl_ensemble_desc* ens,
   if (!bytes) return fail(QCL_ERR_INVALID_ARG, "bytes is NULL");
   qcl_status st = check_spawn(model, ens, capacity);
   if (st) return st;
-  *bytes = SpawnLayout::make(capacity, model->n, ens->n_traj).total;
+  *bytes = SpawnLayout::make(capacity, model->n, ens->n_traj, ens->precision).total;
   return ok();
 }
 
 qcl_status qcl_spawn_layout(const qcl_model* model, const qcl_ensemble_desc* ens, int64_t capacity, int32_t set,
-                            size_t offsets[8]) {
+                            size_t offsets[11]) {
   if (!offsets) return fail(QCL_ERR_INVALID_ARG, "offsets is NULL");
   qcl_status st = check_spawn(model, ens, capacity);
   if (st) return st;
   if (set != 0 && set != 1) return fail(QCL_ERR_INVALID_ARG, "set must be 0 or 1");
-  const SpawnLayout L = SpawnLayout::make(capacity, model->n, ens->n_traj);
+  const SpawnLayout L = SpawnLayout::make(capacity, model->n, ens->n_traj, ens->precision);
   const size_t b = L.set_off[set];
+  const bool f32 = ens->precision == QCL_PREC_FP32_BULK;
   offsets[0] = b + L.R;
   offsets[1] = b + L.P;
   offsets[2] = b + L.m;
@@ -726,6 +734,9 @@ qcl_status qcl_spawn_layout(const qcl_model* model, const qcl_ensemble_desc* ens
   offsets[5] = b + L.id;
   offsets[6] = b + L.fam;
   offsets[7] = L.total;
+  offsets[8] = f32 ? b + L.mlo : 0;
+  offsets[9] = f32 ? b + L.mexp : 0;
+  offsets[10] = f32 ? b + L.philo : 0;
   return ok();
 }
 
@@ -735,12 +746,15 @@ qcl_status qcl_spawn_sample(const qcl_model* model, const qcl_ensemble_desc* ens
   if (st) return st;
   if (!buf) return fail(QCL_ERR_INVALID_ARG, "buf is NULL");
   if (((uintptr_t)buf & 255) != 0) return fail(QCL_ERR_INVALID_ARG, "buf must be 256-byte aligned");
-  const size_t need = SpawnLayout::make(capacity, model->n, ens->n_traj).total;
+  const size_t need = SpawnLayout::make(capacity, model->n, ens->n_traj, ens->precision).total;
   if (bytes < need) return fail(QCL_ERR_OUT_OF_MEMORY, "buf has %zu bytes, needs %zu", bytes, need);
   SampleParams* sp = nullptr;
   st = prepare_sample(model, ens, init, &sp);
   if (st) return st;
-  launch_spawn_sample(model->dev, *sp, capacity, buf, (cudaStream_t)stream);
+  if (ens->precision == QCL_PREC_FP32_BULK)
+    launch_spawn_sample32(model->dev, *sp, capacity, buf, (cudaStream_t)stream);
+  else
+    launch_spawn_sample(model->dev, *sp, capacity, buf, (cudaStream_t)stream);
   delete sp;
   st = check_launch("spawn sample");
   return st ? st : ok();
@@ -760,9 +774,10 @@ qcl_status qcl_spawn_propagate(const qcl_model* model, const qcl_ensemble_desc* 
   if (n_out < 1) return fail(QCL_ERR_INVALID_ARG, "n_out must be >= 1");
   const int64_t k_last = (step0 + n_steps) / out_stride;
   if (k_last >= n_out) return fail(QCL_ERR_INVALID_ARG, "output row %lld beyond n_out = %lld", (long long)k_last, (long long)n_out);
-  const SpawnLayout SL = SpawnLayout::make(capacity, model->n, ens->n_traj);
+  const SpawnLayout SL = SpawnLayout::make(capacity, model->n, ens->n_traj, ens->precision);
   if (bytes < SL.total) return fail(QCL_ERR_OUT_OF_MEMORY, "buf has %zu bytes, needs %zu", bytes, SL.total);
-  const ObsLayout OL = ObsLayout::make(ens->n_traj, model->ns, n_out, tile_walkers(QCL_PREC_FP64, model->n, model->ns));
+  // tiles of 256 families in either precision (FP32 spawning takes <= 32 modes)
+  const ObsLayout OL = ObsLayout::make(ens->n_traj, model->ns, n_out, tile_walkers(ens->precision, model->n, model->ns));
   if (obs_bytes < OL.total) return fail(QCL_ERR_OUT_OF_MEMORY, "obs_buf has %zu bytes, needs %zu", obs_bytes, OL.total);
   cudaStream_t s = (cudaStream_t)stream;
   char* ob = (char*)obs_buf;
@@ -771,18 +786,39 @@ qcl_status qcl_spawn_propagate(const qcl_model* model, const qcl_ensemble_desc* 
   double* fold = (double*)(ob + OL.off_fold);
   const int q2 = OL.q2;
   const int64_t n0 = ens->n_traj;
+  const bool f32 = ens->precision == QCL_PREC_FP32_BULK;
+  Coef2* cf = nullptr;
+  BulkParams bp{};
+  if (f32) {
+    cf = new (std::nothrow) Coef2();
+    if (!cf) return fail(QCL_ERR_OUT_OF_MEMORY, "host allocation failed");
+    fill_coef2(model, dt, cf);
+    bp.n_traj = n0;
+    bp.seed = ens->seed;
+    bp.step0 = step0;
+    bp.stride = out_stride;
+    bp.n = model->n;
+    bulk_model_scalars(bp, model->host, dt);
+  }
   auto observe = [&](double* row, int64_t step) {
-    launch_spawn_observe(model->dev, buf, capacity, model->n, n0, (int)(step & 1), part, s);
+    if (f32)
+      launch_spawn_observe32(bp, *cf, buf, capacity, n0, (int)(step & 1), part, s);
+    else
+      launch_spawn_observe(model->dev, buf, capacity, model->n, n0, (int)(step & 1), part, s);
     launch_fold(part, row, fold, OL.n_tiles, q2, 1, s);
   };
   if (step0 == 0) observe(rows, 0);
   for (int64_t t = step0; t < step0 + n_steps; ++t) {
     {
       TimedLaunch tl(1, s);
-      launch_spawn_step(model->dev, model->host.repr, buf, capacity, model->n, n0, step0, t, dt, ens->seed, s);
+      if (f32)
+        launch_spawn_step32(bp, *cf, buf, capacity, n0, step0, t, s);
+      else
+        launch_spawn_step(model->dev, model->host.repr, buf, capacity, model->n, n0, step0, t, dt, ens->seed, s);
     }
     if ((t + 1) % out_stride == 0) observe(rows + (size_t)((t + 1) / out_stride) * q2, t + 1);
   }
+  delete cf;
   st = check_launch("spawn step");
   if (st) return st;
   launch_header_finish(buf, step0, step0 + n_steps, s);

@@ -49,7 +49,7 @@ __global__ void __launch_bounds__(256) k_spawn_sample(const DevModel* __restrict
                                                       SampleParams sp, int64_t cap, void* buf) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const int64_t n0 = sp.n_traj;
-  const SpawnLayout L = SpawnLayout::make(cap, sp.n, n0);
+  const SpawnLayout L = SpawnLayout::make(cap, sp.n, n0, QCL_PREC_FP64);
   EnsHeader* hdr = (EnsHeader*)buf;
   SpawnHeader* sh = spawn_header(buf);
   if (i == 0) {
@@ -86,58 +86,64 @@ template <int NP, bool DIA>
 __global__ void __launch_bounds__(256) k_spawn_step(const DevModel* __restrict__ M, void* buf,
                                                     int64_t cap, int n, int64_t n0, int64_t step0,
                                                     int64_t step, double dt, uint64_t seed) {
-  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  const SpawnLayout L = SpawnLayout::make(cap, n, n0);
+  const SpawnLayout L = SpawnLayout::make(cap, n, n0, QCL_PREC_FP64);
   EnsHeader* hdr = (EnsHeader*)buf;
   const int src = (int)(step & 1);
   const int64_t n_live = spawn_header(buf)->n_live[src];
   const bool ok = hdr->step == step0;
-  if (!ok && i == 0) atomicOr(&hdr->flags, QCL_FLAG_STEP_MISMATCH);
-  int flag = 0;
-  if (ok && i < n_live) {
-    const Set64 w = spawn_set(buf, L, src);
-    const uint16_t ab = w.ab[i];
-    const int al = ab & 0xf, be = (ab >> 8) & 0xf, q = (ab >> 4) & 3;
-    double phi = w.phi[i];
-    const double m = w.m[i];
-    const Step64 o = walker_step_f64<NP, DIA>(M, w.R + i, w.P + i, cap, n, al, be, phi, dt,
-                                              seed, w.id[i], step);
-    w.phi[i] = phi;
-    flag = o.ev > 0;
-    double* cm = (double*)((char*)buf + L.cm);
-    uint16_t* cab = (uint16_t*)((char*)buf + L.cab);
-    uint8_t* fl = (uint8_t*)((char*)buf + L.flag);
-    fl[i] = (uint8_t)flag;
-    if (flag) {
-      const double mc = m * o.num / o.den;
-      cm[i] = mc;
-      cab[i] = (uint16_t)((al ^ (o.ev == 1)) | (((q + o.dq) & 3) << 4) | ((be ^ (o.ev == 2)) << 8));
-      if (!isfinite(mc)) {
+  if (!ok) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) atomicOr(&hdr->flags, QCL_FLAG_STEP_MISMATCH);
+    return;
+  }
+  // a grid of a few blocks per SM walks the live walkers in groups of 256
+  const int64_t nvb = (n_live + 255) / 256;
+  for (int64_t vb = blockIdx.x; vb < nvb; vb += gridDim.x) {
+    const int64_t i = vb * 256 + threadIdx.x;
+    int flag = 0;
+    if (i < n_live) {
+      const Set64 w = spawn_set(buf, L, src);
+      const uint16_t ab = w.ab[i];
+      const int al = ab & 0xf, be = (ab >> 8) & 0xf, q = (ab >> 4) & 3;
+      double phi = w.phi[i];
+      const double m = w.m[i];
+      const Step64 o = walker_step_f64<NP, DIA>(M, w.R + i, w.P + i, cap, n, al, be, phi, dt,
+                                                seed, w.id[i], step);
+      w.phi[i] = phi;
+      flag = o.ev > 0;
+      double* cm = (double*)((char*)buf + L.cm);
+      uint16_t* cab = (uint16_t*)((char*)buf + L.cab);
+      uint8_t* fl = (uint8_t*)((char*)buf + L.flag);
+      fl[i] = (uint8_t)flag;
+      if (flag) {
+        const double mc = m * o.num / o.den;
+        cm[i] = mc;
+        cab[i] = (uint16_t)((al ^ (o.ev == 1)) | (((q + o.dq) & 3) << 4) | ((be ^ (o.ev == 2)) << 8));
+        if (!isfinite(mc)) {
+          atomicAdd(&hdr->n_nonfinite, 1ull);
+          atomicOr(&hdr->flags, QCL_FLAG_NONFINITE);
+        }
+      }
+      if (o.deg) {
+        atomicAdd(&hdr->n_degenerate, 1ull);
+        atomicOr(&hdr->flags, QCL_FLAG_DEGENERATE);
+      }
+      if (!isfinite(phi)) {
         atomicAdd(&hdr->n_nonfinite, 1ull);
         atomicOr(&hdr->flags, QCL_FLAG_NONFINITE);
       }
     }
-    if (o.deg) {
-      atomicAdd(&hdr->n_degenerate, 1ull);
-      atomicOr(&hdr->flags, QCL_FLAG_DEGENERATE);
-    }
-    if (!isfinite(phi)) {
-      atomicAdd(&hdr->n_nonfinite, 1ull);
-      atomicOr(&hdr->flags, QCL_FLAG_NONFINITE);
-    }
+    const int cnt = __syncthreads_count(flag);
+    if (threadIdx.x == 0) ((int32_t*)((char*)buf + L.bsum))[vb] = cnt;
   }
-  const int cnt = __syncthreads_count(flag);
-  if (threadIdx.x == 0 && (int64_t)blockIdx.x < L.n_blocks)
-    ((int32_t*)((char*)buf + L.bsum))[blockIdx.x] = cnt;
 }
 
 // Exclusive scan of the block counts of the live blocks (one block of 1024
 // threads, each over a contiguous run of blocks), the destination set's live
 // count, and the overflow test.
 __global__ void __launch_bounds__(1024) k_spawn_scan(void* buf, int64_t cap, int n, int64_t n0,
-                                                     int64_t step0, int64_t step) {
+                                                     int prec, int64_t step0, int64_t step) {
   __shared__ int64_t wsum[32];
-  const SpawnLayout L = SpawnLayout::make(cap, n, n0);
+  const SpawnLayout L = SpawnLayout::make(cap, n, n0, prec);
   EnsHeader* hdr = (EnsHeader*)buf;
   SpawnHeader* sh = spawn_header(buf);
   if (hdr->step != step0) return;
@@ -192,68 +198,73 @@ __global__ void __launch_bounds__(256) k_spawn_scatter(void* buf, int64_t cap, i
                                                        int64_t step0, int64_t step,
                                                        uint64_t seed) {
   __shared__ int wcnt[8];
-  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  const SpawnLayout L = SpawnLayout::make(cap, n, n0);
+  const SpawnLayout L = SpawnLayout::make(cap, n, n0, QCL_PREC_FP64);
   EnsHeader* hdr = (EnsHeader*)buf;
   SpawnHeader* sh = spawn_header(buf);
   if (hdr->step != step0) return;  // uniform over the grid
   const int src = (int)(step & 1);
   const int64_t n_live = sh->n_live[src];
-  if ((int64_t)blockIdx.x * 256 >= n_live) return;  // whole block past the live walkers
   const bool drop = sh->drop != 0;
   const uint8_t* fl = (const uint8_t*)((char*)buf + L.flag);
-  const bool live = i < n_live;
-  const int flag = (live && !drop) ? fl[i] : 0;
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  const unsigned bal = __ballot_sync(0xffffffffu, flag);
-  if (lane == 0) wcnt[wid] = __popc(bal);
-  __syncthreads();
-  int before = __popc(bal & ((1u << lane) - 1u));
-  for (int k = 0; k < wid; ++k) before += wcnt[k];
-  if (!live) return;
-  const int64_t boff = drop ? 0 : ((const int64_t*)((char*)buf + L.boff))[blockIdx.x];
-  const int64_t pos = i + boff + before;
-  const Set64 s = spawn_set(buf, L, src);
-  const Set64 d = spawn_set(buf, L, src ^ 1);
-  for (int j = 0; j < n; ++j) {
-    const double r = s.R[(int64_t)j * cap + i], p = s.P[(int64_t)j * cap + i];
-    d.R[(int64_t)j * cap + pos] = r;
-    d.P[(int64_t)j * cap + pos] = p;
-    if (flag) {
-      d.R[(int64_t)j * cap + pos + 1] = r;
-      d.P[(int64_t)j * cap + pos + 1] = p;
+  const int64_t nvb = (n_live + 255) / 256;
+  for (int64_t vb = blockIdx.x; vb < nvb; vb += gridDim.x) {
+    const int64_t i = vb * 256 + threadIdx.x;
+    const bool live = i < n_live;
+    const int flag = (live && !drop) ? fl[i] : 0;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const unsigned bal = __ballot_sync(0xffffffffu, flag);
+    if (lane == 0) wcnt[wid] = __popc(bal);
+    __syncthreads();
+    int before = __popc(bal & ((1u << lane) - 1u));
+    for (int k = 0; k < wid; ++k) before += wcnt[k];
+    if (live) {
+      const int64_t boff = drop ? 0 : ((const int64_t*)((char*)buf + L.boff))[vb];
+      const int64_t pos = i + boff + before;
+      const Set64 s = spawn_set(buf, L, src);
+      const Set64 d = spawn_set(buf, L, src ^ 1);
+      for (int j = 0; j < n; ++j) {
+        const double r = s.R[(int64_t)j * cap + i], p = s.P[(int64_t)j * cap + i];
+        d.R[(int64_t)j * cap + pos] = r;
+        d.P[(int64_t)j * cap + pos] = p;
+        if (flag) {
+          d.R[(int64_t)j * cap + pos + 1] = r;
+          d.P[(int64_t)j * cap + pos + 1] = p;
+        }
+      }
+      const double phi = s.phi[i];
+      const uint64_t id = s.id[i];
+      const uint32_t fam = s.fam[i];
+      d.m[pos] = s.m[i];
+      d.phi[pos] = phi;
+      d.ab[pos] = s.ab[i];
+      d.id[pos] = id;
+      d.fam[pos] = fam;
+      if (flag) {
+        d.m[pos + 1] = ((const double*)((char*)buf + L.cm))[i];
+        d.phi[pos + 1] = phi;
+        d.ab[pos + 1] = ((const uint16_t*)((char*)buf + L.cab))[i];
+        d.id[pos + 1] = child_id(seed, step, id);
+        d.fam[pos + 1] = fam;
+      }
     }
-  }
-  const double phi = s.phi[i];
-  const uint64_t id = s.id[i];
-  const uint32_t fam = s.fam[i];
-  d.m[pos] = s.m[i];
-  d.phi[pos] = phi;
-  d.ab[pos] = s.ab[i];
-  d.id[pos] = id;
-  d.fam[pos] = fam;
-  if (flag) {
-    d.m[pos + 1] = ((const double*)((char*)buf + L.cm))[i];
-    d.phi[pos + 1] = phi;
-    d.ab[pos + 1] = ((const uint16_t*)((char*)buf + L.cab))[i];
-    d.id[pos + 1] = child_id(seed, step, id);
-    d.fam[pos + 1] = fam;
+    __syncthreads();  // wcnt is rewritten by the next group
   }
 }
 
 // Family start indices of set `set`: fstart[k] = index of family k's first
 // walker, fstart[n0] = the live count.
 __global__ void __launch_bounds__(256) k_spawn_fstart(const void* buf, int64_t cap, int n,
-                                                      int64_t n0, int set) {
-  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  const SpawnLayout L = SpawnLayout::make(cap, n, n0);
+                                                      int64_t n0, int prec, int set) {
+  const SpawnLayout L = SpawnLayout::make(cap, n, n0, prec);
   const int64_t n_live = spawn_header((void*)buf)->n_live[set];
-  const Set64 s = spawn_set((void*)buf, L, set);
+  const uint32_t* fam = (const uint32_t*)((const char*)buf + L.set_off[set] + L.fam);
   int64_t* fstart = (int64_t*)((char*)buf + L.fstart);
-  if (i >= n_live) return;
-  const uint32_t f = s.fam[i];
-  if (i == 0 || s.fam[i - 1] != f) fstart[f] = i;
-  if (i == n_live - 1) fstart[n0] = n_live;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n_live;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const uint32_t f = fam[i];
+    if (i == 0 || fam[i - 1] != f) fstart[f] = i;
+    if (i == n_live - 1) fstart[n0] = n_live;
+  }
 }
 
 // One thread per family: the family sum X of the walkers' contributions (in
@@ -265,7 +276,7 @@ __global__ void __launch_bounds__(256) k_spawn_observe(const DevModel* __restric
                                                        double* __restrict__ part) {
   __shared__ double red[8][32];
   const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  const SpawnLayout L = SpawnLayout::make(cap, n, n0);
+  const SpawnLayout L = SpawnLayout::make(cap, n, n0, QCL_PREC_FP64);
   const Set64 s = spawn_set((void*)buf, L, set);
   const int64_t* fstart = (const int64_t*)((const char*)buf + L.fstart);
   double v[32];
@@ -291,6 +302,19 @@ __global__ void __launch_bounds__(256) k_spawn_observe(const DevModel* __restric
 
 }  // namespace
 
+unsigned spawn_grid(int64_t capacity) {
+  static int n_sm = 0;
+  if (n_sm == 0) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
+    if (n_sm < 1) n_sm = 1;
+  }
+  const int64_t groups = (capacity + 255) / 256;
+  const int64_t g = (int64_t)8 * n_sm;
+  return (unsigned)(groups < g ? (groups > 0 ? groups : 1) : g);
+}
+
 void launch_spawn_sample(const DevModel* dm, const SampleParams& sp, int64_t capacity, void* buf,
                          cudaStream_t st) {
   const int64_t nb = (sp.n_traj + 255) / 256;
@@ -301,7 +325,7 @@ void launch_spawn_sample(const DevModel* dm, const SampleParams& sp, int64_t cap
 void launch_spawn_step(const DevModel* dm, int repr, void* buf, int64_t capacity, int n,
                        int64_t n0, int64_t step0, int64_t step, double dt, uint64_t seed,
                        cudaStream_t st) {
-  const unsigned nb = (unsigned)((capacity + 255) / 256);
+  const unsigned nb = spawn_grid(capacity);
   const bool dia = repr == QCL_REPR_DIABATIC;
 #define QCL_SPAWN_STEP(NP)                                                                   \
   (dia ? k_spawn_step<NP, true><<<nb, 256, 0, st>>>(dm, buf, capacity, n, n0, step0, step, dt, seed) \
@@ -315,18 +339,29 @@ void launch_spawn_step(const DevModel* dm, int repr, void* buf, int64_t capacity
   else
     QCL_SPAWN_STEP(0);
 #undef QCL_SPAWN_STEP
-  k_spawn_scan<<<1, 1024, 0, st>>>(buf, capacity, n, n0, step0, step);
+  k_spawn_scan<<<1, 1024, 0, st>>>(buf, capacity, n, n0, QCL_PREC_FP64, step0, step);
   k_spawn_scatter<<<nb, 256, 0, st>>>(buf, capacity, n, n0, step0, step, seed);
   launches_add(3);
 }
 
 void launch_spawn_observe(const DevModel* dm, const void* buf, int64_t capacity, int n, int64_t n0,
                           int set, double* part, cudaStream_t st) {
-  const unsigned nw = (unsigned)((capacity + 255) / 256);
   const unsigned nf = (unsigned)((n0 + 255) / 256);
-  k_spawn_fstart<<<nw, 256, 0, st>>>(buf, capacity, n, n0, set);
+  k_spawn_fstart<<<spawn_grid(capacity), 256, 0, st>>>(buf, capacity, n, n0, QCL_PREC_FP64, set);
   k_spawn_observe<<<nf, 256, 0, st>>>(dm, buf, capacity, n, n0, set, part);
   launches_add(2);
+}
+
+void launch_spawn_scan(void* buf, int64_t capacity, int n, int64_t n0, int precision, int64_t step0,
+                       int64_t step, cudaStream_t st) {
+  k_spawn_scan<<<1, 1024, 0, st>>>(buf, capacity, n, n0, precision, step0, step);
+  launches_add(1);
+}
+
+void launch_spawn_fstart(const void* buf, int64_t capacity, int n, int64_t n0, int precision, int set,
+                         cudaStream_t st) {
+  k_spawn_fstart<<<spawn_grid(capacity), 256, 0, st>>>(buf, capacity, n, n0, precision, set);
+  launches_add(1);
 }
 
 }  // namespace qcl

@@ -1,0 +1,391 @@
+// spawn32.cu -- trajectory spawning in FP32 bulk precision (two states, up to
+// 32 modes, either representation).  The same scheme and walker order as the
+// FP64 spawning kernels (spawn.cu): one step per launch, a child inserted right
+// after its parent by the deterministic count / scan / scatter; the walker's
+// arithmetic is that of the FP32-bulk kernels (compensated phase and weight
+// pairs with a carried exponent), with the state read from and written to HBM
+// every step.  Family observation in FP64 from the walkers' FP32 contributions.
+#include "bulk2.cuh"
+#include "reduce.cuh"
+
+namespace qcl {
+
+namespace {
+
+struct Set32 {
+  float* R;
+  float* P;
+  float* mh;
+  float* ml;
+  int32_t* me;
+  float* ph;
+  float* pl;
+  uint16_t* ab;
+  uint64_t* id;
+  uint32_t* fam;
+};
+
+__device__ __forceinline__ Set32 set32(void* buf, const SpawnLayout& L, int set) {
+  char* b = (char*)buf + L.set_off[set];
+  return {(float*)(b + L.R),     (float*)(b + L.P),    (float*)(b + L.m),
+          (float*)(b + L.mlo),   (int32_t*)(b + L.mexp), (float*)(b + L.phi),
+          (float*)(b + L.philo), (uint16_t*)(b + L.ab), (uint64_t*)(b + L.id),
+          (uint32_t*)(b + L.fam)};
+}
+
+__device__ __forceinline__ SpawnHeader* hdr_spawn(void* buf) {
+  return (SpawnHeader*)((char*)buf + kSpawnHeaderOff);
+}
+
+// the child's random-stream id (the definition used by the FP64 kernels)
+__device__ __forceinline__ uint64_t child_id32(uint64_t seed, int64_t step, uint64_t parent) {
+  const u4 w = philox_draw(seed, (uint32_t)step, parent, 3u);
+  return (((uint64_t)w.y << 32) | w.x) | (1ull << 63);
+}
+
+__global__ void __launch_bounds__(256) k_spawn_sample32(const DevModel* __restrict__ M,
+                                                        SampleParams sp, int64_t cap, void* buf) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t n0 = sp.n_traj;
+  const SpawnLayout L = SpawnLayout::make(cap, sp.n, n0, QCL_PREC_FP32_BULK);
+  EnsHeader* hdr = (EnsHeader*)buf;
+  SpawnHeader* sh = hdr_spawn(buf);
+  if (i == 0) {
+    hdr->magic = kEnsMagic;
+    hdr->n_traj = n0;
+    hdr->precision = QCL_PREC_FP32_BULK;
+    hdr->ns = 2;
+    hdr->n = sp.n;
+    hdr->step = 0;
+    hdr->flags = 0;
+    hdr->n_degenerate = 0;
+    hdr->n_nonfinite = 0;
+    sh->capacity = cap;
+    sh->n0 = n0;
+    sh->n_live[0] = n0;
+    sh->n_live[1] = 0;
+    sh->drop = 0;
+  }
+  if (i >= n0) return;
+  const Set32 w = set32(buf, L, 0);
+  const uint64_t traj = sp.traj_offset + (uint64_t)i;
+  float mh;
+  uint16_t ab;
+  sample_walker_f32(M, sp, traj, w.R + i, w.P + i, cap, mh, ab);
+  w.mh[i] = mh;
+  w.ml[i] = 0.0f;
+  w.me[i] = 0;
+  w.ph[i] = 0.0f;
+  w.pl[i] = 0.0f;
+  w.ab[i] = ab;
+  w.id[i] = traj;
+  w.fam[i] = (uint32_t)i;
+}
+
+// One step of every live walker of set `src` (in place); children to the
+// per-parent staging, each block's child count to bsum.
+template <int NPL, int KIND, bool DIA>
+__global__ void __launch_bounds__(256) k_spawn_step32(const BulkParams bp, const Coef2 cf,
+                                                      void* buf, int64_t cap, int64_t n0,
+                                                      int64_t step) {
+  const SpawnLayout L = SpawnLayout::make(cap, bp.n, n0, QCL_PREC_FP32_BULK);
+  EnsHeader* hdr = (EnsHeader*)buf;
+  const int src = (int)(step & 1);
+  const int64_t n_live = hdr_spawn(buf)->n_live[src];
+  const bool ok = hdr->step == bp.step0;
+  if (!ok) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) atomicOr(&hdr->flags, QCL_FLAG_STEP_MISMATCH);
+    return;
+  }
+  // a grid of a few blocks per SM walks the live walkers in groups of 256
+  const int64_t nvb = (n_live + 255) / 256;
+  for (int64_t vb = blockIdx.x; vb < nvb; vb += gridDim.x) {
+    const int64_t i = vb * 256 + threadIdx.x;
+    int flag = 0;
+    if (i < n_live) {
+      const Set32 s = set32(buf, L, src);
+      Walker<NPL> w;
+  #pragma unroll
+      for (int j = 0; j < NPL; ++j) {
+        const bool on = j < bp.n;
+        w.R[j] = on ? s.R[(int64_t)j * cap + i] : 0.0f;
+        w.P[j] = on ? s.P[(int64_t)j * cap + i] : 0.0f;
+      }
+      Scal z;
+      z.m = {s.mh[i], s.ml[i]};
+      z.mexp = s.me[i];
+      z.ph = {s.ph[i], s.pl[i]};
+      const uint32_t ab = s.ab[i];
+      z.sa = sgn(ab & 0xf);
+      z.sb = sgn((ab >> 8) & 0xf);
+      z.q = DIA ? (int)((ab >> 4) & 3u) : 0;
+      z.A = bp.a0;
+      z.B = bp.b0;
+  #pragma unroll
+      for (int j = 0; j < NPL; ++j) {
+        z.A = __fmaf_rn(cf.a[j], w.R[j], z.A);
+        if (KIND == 1) z.B = __fmaf_rn(cf.b[j], w.R[j], z.B);
+      }
+      closed_form(z);
+      const u4 wd = philox_draw(bp.seed, (uint32_t)(step >> 2), s.id[i], kPurposeHop);
+      const uint32_t word = word_of(wd, (int)(step & 3));
+      unsigned int deg = 0;
+      Scal child;
+      bool hop;
+      const float hsab = bp.hdt * 0.5f * (z.sa + z.sb);
+      if (DIA) {
+        kick_dia<NPL, KIND, Coef2>(w, cf, hsab);
+  #pragma unroll
+        for (int j = 0; j < NPL; ++j) w.R[j] = __fmaf_rn(cf.dtm[j], w.P[j], w.R[j]);
+        const float a_old = z.A;
+        z.A = bp.a0;
+        if (KIND == 1) z.B = bp.b0;
+  #pragma unroll
+        for (int j = 0; j < NPL; ++j) {
+          z.A = __fmaf_rn(cf.a[j], w.R[j], z.A);
+          if (KIND == 1) z.B = __fmaf_rn(cf.b[j], w.R[j], z.B);
+        }
+        kick_dia<NPL, KIND, Coef2>(w, cf, hsab);
+        hop = spawn_transition<KIND, true>(z, a_old, 0.0f, z.B, word, bp, deg, child);
+      } else {
+        kick<NPL, KIND, Coef2>(w, cf, hsab * z.c2, hsab * z.s2);
+  #pragma unroll
+        for (int j = 0; j < NPL; ++j) w.R[j] = __fmaf_rn(cf.dtm[j], w.P[j], w.R[j]);
+        const float r_old = z.r;
+        z.A = bp.a0;
+        z.B = bp.b0;
+  #pragma unroll
+        for (int j = 0; j < NPL; ++j) {
+          z.A = __fmaf_rn(cf.a[j], w.R[j], z.A);
+          if (KIND == 1) z.B = __fmaf_rn(cf.b[j], w.R[j], z.B);
+        }
+        closed_form(z);
+        kick<NPL, KIND, Coef2>(w, cf, hsab * z.c2, hsab * z.s2);
+        float Av = 0.0f, Bv = 0.0f;
+  #pragma unroll
+        for (int j = 0; j < NPL; ++j) {
+          Av = __fmaf_rn(cf.am[j], w.P[j], Av);
+          if (KIND == 1) Bv = __fmaf_rn(cf.bm[j], w.P[j], Bv);
+        }
+        hop = spawn_transition<KIND, false>(z, r_old, Av, Bv, word, bp, deg, child);
+      }
+      // the phase pair is renormalised, and wrapped past 2^10 rad, at the end of
+      // every Philox block (absolute steps 4k + 3)
+      if ((step & 3) == 3) {
+        z.ph = two_sum(z.ph.hi, z.ph.lo);
+        phase_wrap(z);
+      }
+  #pragma unroll
+      for (int j = 0; j < NPL; ++j)
+        if (j < bp.n) {
+          s.R[(int64_t)j * cap + i] = w.R[j];
+          s.P[(int64_t)j * cap + i] = w.P[j];
+        }
+      s.ph[i] = z.ph.hi;
+      s.pl[i] = z.ph.lo;
+      flag = hop ? 1 : 0;
+      uint8_t* fl = (uint8_t*)((char*)buf + L.flag);
+      fl[i] = (uint8_t)flag;
+      if (hop) {
+        renorm(child.m, child.mexp);
+        ((float*)((char*)buf + L.cm))[i] = child.m.hi;
+        ((float*)((char*)buf + L.cmlo))[i] = child.m.lo;
+        ((int32_t*)((char*)buf + L.cmexp))[i] = child.mexp;
+        ((uint16_t*)((char*)buf + L.cab))[i] =
+            (uint16_t)((child.sa > 0.0f ? 1 : 0) | (child.q << 4) | ((child.sb > 0.0f ? 1 : 0) << 8));
+        if (!isfinite(child.m.hi)) {
+          atomicAdd(&hdr->n_nonfinite, 1ull);
+          atomicOr(&hdr->flags, QCL_FLAG_NONFINITE);
+        }
+      }
+      if (deg) {
+        atomicAdd(&hdr->n_degenerate, 1ull);
+        atomicOr(&hdr->flags, QCL_FLAG_DEGENERATE);
+      }
+      if (!isfinite(z.ph.hi)) {
+        atomicAdd(&hdr->n_nonfinite, 1ull);
+        atomicOr(&hdr->flags, QCL_FLAG_NONFINITE);
+      }
+    }
+    const int cnt = __syncthreads_count(flag);
+    if (threadIdx.x == 0) ((int32_t*)((char*)buf + L.bsum))[vb] = cnt;
+  }
+}
+
+// Moves every live walker of set src to its place in the other set and writes
+// each child right after its parent.
+__global__ void __launch_bounds__(256) k_spawn_scatter32(void* buf, int64_t cap, int n, int64_t n0,
+                                                         int64_t step0, int64_t step,
+                                                         uint64_t seed) {
+  __shared__ int wcnt[8];
+  const SpawnLayout L = SpawnLayout::make(cap, n, n0, QCL_PREC_FP32_BULK);
+  EnsHeader* hdr = (EnsHeader*)buf;
+  SpawnHeader* sh = hdr_spawn(buf);
+  if (hdr->step != step0) return;  // uniform over the grid
+  const int src = (int)(step & 1);
+  const int64_t n_live = sh->n_live[src];
+  const bool drop = sh->drop != 0;
+  const uint8_t* fl = (const uint8_t*)((char*)buf + L.flag);
+  const int64_t nvb = (n_live + 255) / 256;
+  for (int64_t vb = blockIdx.x; vb < nvb; vb += gridDim.x) {
+    const int64_t i = vb * 256 + threadIdx.x;
+    const bool live = i < n_live;
+    const int flag = (live && !drop) ? fl[i] : 0;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const unsigned bal = __ballot_sync(0xffffffffu, flag);
+    if (lane == 0) wcnt[wid] = __popc(bal);
+    __syncthreads();
+    int before = __popc(bal & ((1u << lane) - 1u));
+    for (int k = 0; k < wid; ++k) before += wcnt[k];
+    if (live) {
+      const int64_t boff = drop ? 0 : ((const int64_t*)((char*)buf + L.boff))[vb];
+      const int64_t pos = i + boff + before;
+      const Set32 s = set32(buf, L, src);
+      const Set32 d = set32(buf, L, src ^ 1);
+      for (int j = 0; j < n; ++j) {
+        const float r = s.R[(int64_t)j * cap + i], p = s.P[(int64_t)j * cap + i];
+        d.R[(int64_t)j * cap + pos] = r;
+        d.P[(int64_t)j * cap + pos] = p;
+        if (flag) {
+          d.R[(int64_t)j * cap + pos + 1] = r;
+          d.P[(int64_t)j * cap + pos + 1] = p;
+        }
+      }
+      const float ph = s.ph[i], pl = s.pl[i];
+      const uint64_t id = s.id[i];
+      const uint32_t fam = s.fam[i];
+      d.mh[pos] = s.mh[i];
+      d.ml[pos] = s.ml[i];
+      d.me[pos] = s.me[i];
+      d.ph[pos] = ph;
+      d.pl[pos] = pl;
+      d.ab[pos] = s.ab[i];
+      d.id[pos] = id;
+      d.fam[pos] = fam;
+      if (flag) {
+        d.mh[pos + 1] = ((const float*)((char*)buf + L.cm))[i];
+        d.ml[pos + 1] = ((const float*)((char*)buf + L.cmlo))[i];
+        d.me[pos + 1] = ((const int32_t*)((char*)buf + L.cmexp))[i];
+        d.ph[pos + 1] = ph;
+        d.pl[pos + 1] = pl;
+        d.ab[pos + 1] = ((const uint16_t*)((char*)buf + L.cab))[i];
+        d.id[pos + 1] = child_id32(seed, step, id);
+        d.fam[pos + 1] = fam;
+      }
+    }
+    __syncthreads();  // wcnt is rewritten by the next group
+  }
+}
+
+// One thread per family: the family sum X (FP64) of its walkers' contributions
+// (each computed in FP32 with unit weight, then scaled by the walker's exact
+// weight (hi + lo) 2^exp), and X^2, reduced over the tile's 256 families by the
+// fixed tree of the observation kernels.
+template <int KIND, bool DIA>
+__global__ void __launch_bounds__(256) k_spawn_observe32(const BulkParams bp, const Coef2 cf,
+                                                         const void* buf, int64_t cap, int64_t n0,
+                                                         int set, double* __restrict__ part) {
+  __shared__ double red[8][32];
+  const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const SpawnLayout L = SpawnLayout::make(cap, bp.n, n0, QCL_PREC_FP32_BULK);
+  const Set32 s = set32((void*)buf, L, set);
+  const int64_t* fstart = (const int64_t*)((const char*)buf + L.fstart);
+  double v[32];
+#pragma unroll
+  for (int q = 0; q < 32; ++q) v[q] = 0.0;
+  if (k < n0) {
+    const int64_t j0 = fstart[k], j1 = fstart[k + 1];
+    for (int64_t j = j0; j < j1; ++j) {
+      Scal z;
+      z.A = bp.a0;
+      z.B = bp.b0;
+      for (int m = 0; m < bp.n; ++m) {
+        const float r = s.R[(int64_t)m * cap + j];
+        z.A = __fmaf_rn(cf.a[m], r, z.A);
+        if (KIND == 1) z.B = __fmaf_rn(cf.b[m], r, z.B);
+      }
+      closed_form(z);
+      const uint32_t ab = s.ab[j];
+      z.sa = sgn(ab & 0xf);
+      z.sb = sgn((ab >> 8) & 0xf);
+      z.q = DIA ? (int)((ab >> 4) & 3u) : 0;
+      z.ph = {s.ph[j], s.pl[j]};
+      float c[16];
+      contributions<DIA>(z, 1.0f, c);
+      // (hi + lo) 2^exp exactly: the power of two from its bits (ldexp outside
+      // the normal range)
+      const int e = s.me[j];
+      const double w2 = (double)s.mh[j] + (double)s.ml[j];
+      const double wgt = (e >= -1022 && e <= 1023) ? w2 * __hiloint2double((e + 1023) << 20, 0)
+                                                  : ldexp(w2, e);
+#pragma unroll
+      for (int q = 0; q < 16; ++q) v[q] = fma((double)c[q], wgt, v[q]);
+    }
+#pragma unroll
+    for (int q = 0; q < 16; ++q) v[16 + q] = v[q] * v[q];
+  }
+  const double x = warp_transpose_sum<double>(v);
+  red[threadIdx.x >> 5][threadIdx.x & 31] = x;
+  __syncthreads();
+  if (threadIdx.x < 32)
+    part[(int64_t)blockIdx.x * 32 + threadIdx.x] = tile_tree8(&red[0][0], 32, threadIdx.x);
+}
+
+template <int NPL, int KIND, bool DIA>
+void run_step32(const BulkParams& bp, const Coef2& cf, void* buf, int64_t cap, int64_t n0,
+                int64_t step, cudaStream_t st) {
+  k_spawn_step32<NPL, KIND, DIA><<<spawn_grid(cap), 256, 0, st>>>(bp, cf, buf, cap, n0, step);
+}
+
+template <int KIND, bool DIA>
+int dispatch_step32(const BulkParams& bp, const Coef2& cf, void* buf, int64_t cap, int64_t n0,
+                    int64_t step, cudaStream_t st) {
+  const int n = bp.n;
+  if (n <= 1) run_step32<1, KIND, DIA>(bp, cf, buf, cap, n0, step, st);
+  else if (n <= 2) run_step32<2, KIND, DIA>(bp, cf, buf, cap, n0, step, st);
+  else if (n <= 4) run_step32<4, KIND, DIA>(bp, cf, buf, cap, n0, step, st);
+  else if (n <= 8) run_step32<8, KIND, DIA>(bp, cf, buf, cap, n0, step, st);
+  else if (n <= 16) run_step32<16, KIND, DIA>(bp, cf, buf, cap, n0, step, st);
+  else if (n <= 32) run_step32<32, KIND, DIA>(bp, cf, buf, cap, n0, step, st);
+  else return 0;
+  return 1;
+}
+
+}  // namespace
+
+void launch_spawn_sample32(const DevModel* dm, const SampleParams& sp, int64_t capacity, void* buf,
+                           cudaStream_t st) {
+  const int64_t nb = (sp.n_traj + 255) / 256;
+  k_spawn_sample32<<<(unsigned)(nb > 0 ? nb : 1), 256, 0, st>>>(dm, sp, capacity, buf);
+  launches_add(1);
+}
+
+int launch_spawn_step32(const BulkParams& bp, const Coef2& cf, void* buf, int64_t capacity,
+                        int64_t n0, int64_t step0, int64_t step, cudaStream_t st) {
+  const bool dia = bp.repr == QCL_REPR_DIABATIC;
+  const int ok = dia ? (bp.kind == 0 ? dispatch_step32<0, true>(bp, cf, buf, capacity, n0, step, st)
+                                     : dispatch_step32<1, true>(bp, cf, buf, capacity, n0, step, st))
+                     : (bp.kind == 0 ? dispatch_step32<0, false>(bp, cf, buf, capacity, n0, step, st)
+                                     : dispatch_step32<1, false>(bp, cf, buf, capacity, n0, step, st));
+  if (!ok) return 0;
+  launch_spawn_scan(buf, capacity, bp.n, n0, QCL_PREC_FP32_BULK, step0, step, st);
+  k_spawn_scatter32<<<spawn_grid(capacity), 256, 0, st>>>(buf, capacity, bp.n, n0, step0, step, bp.seed);
+  launches_add(2);
+  return 1;
+}
+
+void launch_spawn_observe32(const BulkParams& bp, const Coef2& cf, const void* buf, int64_t capacity,
+                            int64_t n0, int set, double* part, cudaStream_t st) {
+  launch_spawn_fstart(buf, capacity, bp.n, n0, QCL_PREC_FP32_BULK, set, st);
+  const unsigned nf = (unsigned)((n0 + 255) / 256);
+  const bool dia = bp.repr == QCL_REPR_DIABATIC;
+  if (dia)
+    (bp.kind == 0 ? k_spawn_observe32<0, true> : k_spawn_observe32<1, true>)
+        <<<nf, 256, 0, st>>>(bp, cf, buf, capacity, n0, set, part);
+  else
+    (bp.kind == 0 ? k_spawn_observe32<0, false> : k_spawn_observe32<1, false>)
+        <<<nf, 256, 0, st>>>(bp, cf, buf, capacity, n0, set, part);
+  launches_add(1);
+}
+
+}  // namespace qcl

@@ -17,6 +17,8 @@ def main():
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
     ap.add_argument("--repeat", type=int, default=1)
     ap.add_argument("--repr", default="adiabatic", choices=["adiabatic", "diabatic"])
+    ap.add_argument("--spawn", type=int, default=0,
+                    help="> 0: a spawning ensemble with this many walker slots per initial walker")
     args = ap.parse_args()
 
     import torch
@@ -33,7 +35,11 @@ def main():
     stride = cfg["out_stride"]
     prec = qcl.PREC_FP32_BULK if args.precision == "fp32" else qcl.PREC_FP64
     model = qcl.Model(cfg["model"])
-    run = qcl.Run(model, n, cfg["seed"], prec, steps // stride + 1)
+    if args.spawn > 0:
+        run = qcl.SpawnRun(model, n, args.spawn * n, cfg["seed"], steps // stride + 1,
+                           precision=prec)
+    else:
+        run = qcl.Run(model, n, cfg["seed"], prec, steps // stride + 1)
     for _ in range(args.repeat):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
@@ -42,8 +48,9 @@ def main():
         obs = run.observables()
         torch.cuda.synchronize()
         el = time.perf_counter() - t0
+        extra = f", {run.n_live()} walkers at the end" if args.spawn > 0 else ""
         print(f"config {args.config} n_traj {n} steps {steps} {args.precision}: {el * 1e3:.2f} ms, "
-              f"{n * steps / el:.3e} traj-steps/s, trace(t_end) {obs[-1, 32]:.4f}")
+              f"{n * steps / el:.3e} traj-steps/s, trace(t_end) {obs[-1, 32]:.4f}{extra}")
     st = run.status()
     assert st["flags"] == 0, st
 

@@ -444,14 +444,16 @@ def measure_peak(which: int, stream=None) -> float:
 
 # ----------------------------------------------------------------- spawning --
 class SpawnRun:
-    """A trajectory-spawning ensemble (FP64, two states): n0 initial walkers
-    (families) in a buffer of `capacity` walker slots."""
+    """A trajectory-spawning ensemble (two states; FP64, or FP32 bulk with at
+    most 32 modes): n0 initial walkers (families) in a buffer of `capacity`
+    walker slots."""
 
     def __init__(self, model: Model, n0: int, capacity: int, seed: int, n_out: int,
-                 traj_id_offset: int = 0, device="cuda"):
+                 traj_id_offset: int = 0, device="cuda", precision: int = None):
         self.model = model
         self.capacity = int(capacity)
-        self.ens = ens_desc(n0, seed, PREC_FP64, traj_id_offset)
+        prec = PREC_FP64 if precision is None else int(precision)
+        self.ens = ens_desc(n0, seed, prec, traj_id_offset)
         self.n_out = n_out
         b = C.c_size_t()
         _check(load().qcl_spawn_bytes(model.handle, C.byref(self.ens), self.capacity, C.byref(b)),
@@ -497,22 +499,28 @@ class SpawnRun:
 
         torch.cuda.synchronize()
         nl, n, cap = self.n_live(), self.model.n, self.capacity
-        off = (C.c_size_t * 8)()
+        off = (C.c_size_t * 11)()
         _check(load().qcl_spawn_layout(self.model.handle, C.byref(self.ens), cap, self.step & 1,
                                        off), "qcl_spawn_layout")
         raw = self.buf.cpu().numpy()
+        fp64 = self.ens.precision == PREC_FP64
+        dt, w = (np.float64, 8) if fp64 else (np.float32, 4)
 
         def arr(o, count, dtype, width):
             return np.frombuffer(raw[o:o + width * count].tobytes(), dtype=dtype).copy()
 
-        R = arr(off[0], n * cap, np.float64, 8).reshape(n, cap)[:, :nl].T.copy()
-        P = arr(off[1], n * cap, np.float64, 8).reshape(n, cap)[:, :nl].T.copy()
+        R = arr(off[0], n * cap, dt, w).reshape(n, cap)[:, :nl].T.copy()
+        P = arr(off[1], n * cap, dt, w).reshape(n, cap)[:, :nl].T.copy()
         ab = arr(off[4], nl, np.uint16, 2)
-        return {"R": R, "P": P, "m": arr(off[2], nl, np.float64, 8),
-                "phi": arr(off[3], nl, np.float64, 8),
-                "alpha": (ab & 0xF).astype(np.int32), "q": ((ab >> 4) & 0x3).astype(np.int32),
-                "beta": (ab >> 8).astype(np.int32), "id": arr(off[5], nl, np.uint64, 8),
-                "family": arr(off[6], nl, np.uint32, 4).astype(np.int64)}
+        out = {"R": R, "P": P, "m": arr(off[2], nl, dt, w), "phi": arr(off[3], nl, dt, w),
+               "alpha": (ab & 0xF).astype(np.int32), "q": ((ab >> 4) & 0x3).astype(np.int32),
+               "beta": (ab >> 8).astype(np.int32), "id": arr(off[5], nl, np.uint64, 8),
+               "family": arr(off[6], nl, np.uint32, 4).astype(np.int64)}
+        if not fp64:
+            out["m_lo"] = arr(off[8], nl, np.float32, 4)
+            out["m_exp"] = arr(off[9], nl, np.int32, 4)
+            out["phi_lo"] = arr(off[10], nl, np.float32, 4)
+        return out
 
 
 # ------------------------------------------------------------------- shards --

@@ -146,3 +146,60 @@ def test_spawn_overflow_sets_flag(q):
     run2.sample(cfg["init"])
     run2.propagate(10, cfg["dt"], 10)
     assert run2.status()["flags"] & q.FLAG_SPAWN_OVERFLOW == 0
+
+
+# ------------------------------------------------------------ FP32 spawning --
+@pytest.mark.parametrize("cfg_id,rep,n0,steps", [(1, "adiabatic", 6000, 300),
+                                                 (2, "adiabatic", 4000, 200),
+                                                 (2, "diabatic", 4000, 200),
+                                                 (3, "adiabatic", 3000, 200)])
+def test_fp32_spawn_observables_match_oracle(q, cfg_id, rep, n0, steps):
+    cfg = _cfg(cfg_id, rep)
+    stride, cap = cfg["out_stride"], 400 * n0
+    m = q.Model(cfg["model"])
+    run = q.SpawnRun(m, n0, cap, 13, steps // stride + 1, precision=q.PREC_FP32_BULK)
+    run.sample(cfg["init"])
+    run.propagate(steps, cfg["dt"], stride)
+    obs = run.observables()
+    assert run.status()["flags"] == 0
+    om = oracle.OracleModel(cfg["model"])
+    ref, n_live = oracle.run_spawn(om, oracle.OracleInit(om, cfg["init"]), 13, 0, n0, cap,
+                                   cfg["dt"], steps, stride)
+    mean, se = oracle.finalize(ref, n0)
+    diff = np.abs(obs[:, :16] - mean)
+    # both estimate the same expectation; their errors are independent only up
+    # to the shared random streams, so the combined SE bounds the difference
+    se2 = np.hypot(se, obs[:, 16:32])
+    assert np.all(diff <= 3 * se2 + 1e-6), (diff / (se2 + 1e-300)).max()
+    # the walker lists agree closely (decisions in FP32 against FP64 differ only
+    # for rare near-threshold words)
+    assert abs(run.n_live() - n_live[-1]) <= max(5, 0.002 * n_live[-1])
+    assert run.n_live() > 1.1 * n0
+
+
+def test_fp32_spawn_chunking_is_bitwise_invisible(q):
+    cfg = _cfg(2, "adiabatic")
+    n0, cap = 3000, 1_500_000
+    outs = []
+    for split in ((200,), (70, 130), (3, 197)):
+        m = q.Model(cfg["model"])
+        run = q.SpawnRun(m, n0, cap, 4, 200 // 10 + 1, precision=q.PREC_FP32_BULK)
+        run.sample(cfg["init"])
+        for k in split:
+            run.propagate(k, cfg["dt"], 10)
+        outs.append((run.sums(), run.state()))
+    for sums, st in outs[1:]:
+        assert np.array_equal(sums, outs[0][0])
+        for key in st:
+            assert np.array_equal(st[key], outs[0][1][key]), key
+
+
+def test_fp32_spawn_overflow_sets_flag(q):
+    cfg = _cfg(1, "adiabatic")
+    n0 = 500
+    m = q.Model(cfg["model"])
+    run = q.SpawnRun(m, n0, n0 + 40, 2, 31, precision=q.PREC_FP32_BULK)
+    run.sample(cfg["init"])
+    run.propagate(300, cfg["dt"], 10)
+    assert run.status()["flags"] & q.FLAG_SPAWN_OVERFLOW
+    assert n0 <= run.n_live() <= n0 + 40
