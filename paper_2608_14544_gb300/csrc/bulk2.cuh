@@ -120,12 +120,15 @@ struct Scal {
 // normal float, so at an exact degeneracy (a = b = 0 in FP32, where the angle
 // is undefined and the coupling is set to zero) both come out 0 -- the mean of
 // the two branches -- instead of a division by zero.
+// S2 = false leaves s2 stale (the spin-boson step needs no sin 2theta; the
+// observation recomputes it).
+template <bool S2 = true>
 __device__ __forceinline__ void closed_form(Scal& z) {
   z.r2 = __fmaf_rn(z.A, z.A, z.B * z.B);
   z.ir = rsqrtf(fmaxf(z.r2, 0x1p-126f));
   z.r = z.r2 * z.ir;
   z.c2 = z.A * z.ir;
-  z.s2 = z.B * z.ir;
+  if (S2) z.s2 = z.B * z.ir;
 }
 
 // m *= num / den (den an integer below 2^25, so exact in FP32) as a
@@ -154,11 +157,10 @@ template <int KIND>
 __device__ __forceinline__ void phase_and_transition(Scal& z, float r_old, float Av, float Bv,
                                                      uint32_t word, const BulkParams& bp,
                                                      unsigned int& deg) {
-  // phase: dt/2 (w_ab(R_n) + w_ab(R_{n+1})), hbar w_ab = (sig_a - sig_b) r;
-  // the rounding error of each addition is collected in lo (renormalised with
-  // the weight at the end of the Philox block)
-  const f2 ps = two_sum(z.ph.hi, bp.hdt_hbar * (z.sa - z.sb) * (r_old + z.r));
-  z.ph = {ps.hi, z.ph.lo + ps.lo};
+  // phase: dt/2 (w_ab(R_n) + w_ab(R_{n+1})), hbar w_ab = (sig_a - sig_b) r, added
+  // to the low word of the pair (at most four increments and their rounding
+  // errors until block_end folds it into hi)
+  z.ph.lo = __fmaf_rn(bp.hdt_hbar * (z.sa - z.sb), r_old + z.r, z.ph.lo);
   // coupling contracted with P/M: g = (a Bv - b Av) / (2 r^2)
   // (2 r < tol, compared as r^2 < tol^2 / 4)
   const bool degen = z.r2 < 0.25f * kDegTol32 * kDegTol32;
@@ -191,8 +193,7 @@ __device__ __forceinline__ void phase_and_transition(Scal& z, float r_old, float
 // one quarter turns.
 __device__ __forceinline__ void dia_phase_and_transition(Scal& z, float a_old, float Bc,
                                                          uint32_t word, const BulkParams& bp) {
-  const f2 ps = two_sum(z.ph.hi, bp.hdt_hbar * (z.sb - z.sa) * (a_old + z.A));
-  z.ph = {ps.hi, z.ph.lo + ps.lo};
+  z.ph.lo = __fmaf_rn(bp.hdt_hbar * (z.sb - z.sa), a_old + z.A, z.ph.lo);
   const uint32_t T = min(__float2uint_rz((bp.kamp * kP24f) * fabsf(Bc)), bp.tmax >> 1);
   const uint32_t y = word >> 8;
   const bool hop1 = y < T;
@@ -306,13 +307,11 @@ __device__ __forceinline__ bool spawn_transition(Scal& z, float w_old, float Av,
   uint32_t T;
   float fac;  // A_e 2^24 of the first-index event (DIA: both events)
   if (DIA) {
-    const f2 ps = two_sum(z.ph.hi, bp.hdt_hbar * (z.sb - z.sa) * (w_old + z.A));
-    z.ph = {ps.hi, z.ph.lo + ps.lo};
+    z.ph.lo = __fmaf_rn(bp.hdt_hbar * (z.sb - z.sa), w_old + z.A, z.ph.lo);
     T = min(__float2uint_rz((bp.kamp * kP24f) * fabsf(Bv)), bp.tmax >> 1);
     fac = (bp.amp * kP24f) * Bv;
   } else {
-    const f2 ps = two_sum(z.ph.hi, bp.hdt_hbar * (z.sa - z.sb) * (w_old + z.r));
-    z.ph = {ps.hi, z.ph.lo + ps.lo};
+    z.ph.lo = __fmaf_rn(bp.hdt_hbar * (z.sa - z.sb), w_old + z.r, z.ph.lo);
     const bool degen = z.r2 < 0.25f * kDegTol32 * kDegTol32;
     deg += degen ? 1u : 0u;
     const float gn = (KIND == 1) ? 0.5f * (z.A * Bv - z.B * Av) : (-0.5f * bp.b0) * Av;
@@ -424,6 +423,7 @@ __device__ __forceinline__ double observe_warp(Scal& z, bool active, float* obs_
   renorm(z.m, z.mexp);
   phase_wrap(z);
   if (DIA) closed_form(z);  // the rotation to the adiabatic basis at the walker's R
+  else z.s2 = z.B * z.ir;   // (the same value closed_form gives)
   const bool live = active && z.m.hi != 0.0f;
   const int ew = __reduce_max_sync(0xffffffffu, live ? z.mexp : -(1 << 28));
   float v[16];
@@ -595,7 +595,7 @@ __device__ __forceinline__ void bulk2_tile(const BulkParams& bp, const CF& cf, W
       zk.A = __fmaf_rn(cf.a[j], wk.R[j], zk.A);
       if (KIND == 1) zk.B = __fmaf_rn(cf.b[j], wk.R[j], zk.B);
     }
-    closed_form(zk);
+    closed_form<KIND == 1>(zk);
     kick<NPL, KIND, CF>(wk, cf, hsab * zk.c2, hsab * zk.s2);  // second half kick at R_{n+1}
     float Av = 0.0f, Bv = 0.0f;
 #pragma unroll

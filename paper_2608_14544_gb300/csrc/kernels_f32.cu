@@ -45,7 +45,7 @@ __global__ void __launch_bounds__(256) k_sample_f32(const DevModel* __restrict__
 // One thread per walker, all modes in registers, coefficients as constant-bank
 // operands.  Tile = the block's 256 walkers.
 template <int NPL, int KIND, int WPT = 1>
-__global__ void __launch_bounds__(256, WPT == 1 ? 3 : 2)
+__global__ void __launch_bounds__(256, (WPT == 1 || NPL <= 4) ? 3 : 2)
     k_bulk2(const BulkParams bp, const Coef2 cf, void* buf, double* __restrict__ part) {
   __shared__ double red[2][8][32];      // double-buffered group partials
   __shared__ __align__(16) float obs_rows[256 * kObsRow];  // per-walker contributions
