@@ -73,23 +73,11 @@ __device__ __forceinline__ float rcp_approx(float x) {
   return r;
 }
 
-// Row stride (floats) of the observation rows in shared memory: 16-byte rows
-// that a warp writes with 128-bit stores and reads by column, both without
-// bank conflicts (8 threads of a quarter warp start 4 banks apart).
+// Row stride (floats) of the observation rows in shared memory: 16-byte
+// aligned rows that a warp writes with 128-bit stores (the 8 threads of a
+// quarter warp start 4 banks apart) and reads with 128-bit loads (a quarter
+// warp reads 32 consecutive floats of one row), both without bank conflicts.
 constexpr int kObsRow = 36;
-
-// Sum of 32 floats at stride kObsRow (one column of a warp's rows) by a fixed
-// pairwise tree: ((x0 + x1) + (x2 + x3)) + ...
-__device__ __forceinline__ float column_sum32(const float* col) {
-  float l1[16];
-#pragma unroll
-  for (int t = 0; t < 16; ++t) l1[t] = col[(2 * t) * kObsRow] + col[(2 * t + 1) * kObsRow];
-#pragma unroll
-  for (int w = 8; w >= 1; w >>= 1)
-#pragma unroll
-    for (int t = 0; t < w; ++t) l1[t] = l1[2 * t] + l1[2 * t + 1];
-  return l1[0];
-}
 
 // Shared-memory float4 load that the compiler may not hoist out of the step
 // loop (hoisting the per-mode coefficients would hold them all in registers).
@@ -346,13 +334,19 @@ __device__ __forceinline__ void phase_wrap(Scal& z) {
   }
 }
 
-// The walker's 16 observable contributions (diabatic rho_ij and adiabatic
-// rho_ab, real and imaginary) with weight mantissa `mm`.  z = mm exp(-i phi)
-// (times i^q for a diabatic walker) goes to the walker's own pair in its own
-// representation and, multiplied by U_{alpha k} U_{beta l}, to every element of
-// the other (U is symmetric: the same products serve both directions).
+// The walker's observable factors: z = mm exp(-i phi) (times i^q for a
+// diabatic walker), which goes to the walker's own pair k = 2 alpha + beta in
+// its own representation, and the products f_kl = U_{alpha k} U_{beta l} that
+// carry it to every element of the other (U is symmetric: the same products
+// serve both directions).
+struct Contrib {
+  float zr, zi;
+  float f00, f01, f10, f11;
+  int k;
+};
+
 template <bool DIA>
-__device__ __forceinline__ void contributions(const Scal& z, float mm, float (&v)[16]) {
+__device__ __forceinline__ Contrib contrib_factors(const Scal& z, float mm) {
   // phase reduced into [-pi, pi]: ph_hi - k C1 is exact (|k| < 2^10), the
   // small terms are added once
   const float kq = rintf(z.ph.hi * kInvTwoPi);
@@ -372,29 +366,42 @@ __device__ __forceinline__ void contributions(const Scal& z, float mm, float (&v
   const bool al = z.sa > 0.0f, be = z.sb > 0.0f;
   const float ua0 = al ? c : -s, ua1 = al ? s : c;  // column alpha of U
   const float ub0 = be ? c : -s, ub1 = be ? s : c;  // column beta of U
-  float zr = mm * cphi, zi = -mm * sphi;
+  Contrib o;
+  o.zr = mm * cphi;
+  o.zi = -mm * sphi;
   if (DIA) {  // times i^q
-    const float xr = zr, xi = zi;
-    zr = (z.q & 1) ? -xi : xr;
-    zi = (z.q & 1) ? xr : xi;
-    zr = (z.q & 2) ? -zr : zr;
-    zi = (z.q & 2) ? -zi : zi;
+    const float xr = o.zr, xi = o.zi;
+    o.zr = (z.q & 1) ? -xi : xr;
+    o.zi = (z.q & 1) ? xr : xi;
+    o.zr = (z.q & 2) ? -o.zr : o.zr;
+    o.zi = (z.q & 2) ? -o.zi : o.zi;
   }
+  o.f00 = ua0 * ub0;
+  o.f01 = ua0 * ub1;
+  o.f10 = ua1 * ub0;
+  o.f11 = ua1 * ub1;
+  o.k = (al ? 2 : 0) + (be ? 1 : 0);
+  return o;
+}
+
+// The walker's 16 observable contributions (diabatic rho_ij and adiabatic
+// rho_ab, real and imaginary) with weight mantissa `mm`.
+template <bool DIA>
+__device__ __forceinline__ void contributions(const Scal& z, float mm, float (&v)[16]) {
+  const Contrib c = contrib_factors<DIA>(z, mm);
   constexpr int other = DIA ? 8 : 0, own = DIA ? 0 : 8;
-  const float f00 = ua0 * ub0, f01 = ua0 * ub1, f10 = ua1 * ub0, f11 = ua1 * ub1;
-  v[other + 0] = zr * f00;
-  v[other + 1] = zi * f00;
-  v[other + 2] = zr * f01;
-  v[other + 3] = zi * f01;
-  v[other + 4] = zr * f10;
-  v[other + 5] = zi * f10;
-  v[other + 6] = zr * f11;
-  v[other + 7] = zi * f11;
-  const int k = (al ? 2 : 0) + (be ? 1 : 0);
+  v[other + 0] = c.zr * c.f00;
+  v[other + 1] = c.zi * c.f00;
+  v[other + 2] = c.zr * c.f01;
+  v[other + 3] = c.zi * c.f01;
+  v[other + 4] = c.zr * c.f10;
+  v[other + 5] = c.zi * c.f10;
+  v[other + 6] = c.zr * c.f11;
+  v[other + 7] = c.zi * c.f11;
 #pragma unroll
   for (int kk = 0; kk < 4; ++kk) {
-    v[own + 2 * kk] = (kk == k) ? zr : 0.0f;
-    v[own + 1 + 2 * kk] = (kk == k) ? zi : 0.0f;
+    v[own + 2 * kk] = (kk == c.k) ? c.zr : 0.0f;
+    v[own + 1 + 2 * kk] = (kk == c.k) ? c.zi : 0.0f;
   }
 }
 
@@ -412,34 +419,65 @@ __device__ __forceinline__ double scaled_double(float x, int ex) {
   return ldexp((double)x, ex);
 }
 
-// Observation by one warp of 32 walkers: the warp shares one power of two
-// (FP32 sums of scaled weights, the exponent restored exactly in FP64); each
-// walker's 16 contributions and their squares go to its row `row` of shared
-// memory, and lane q sums column q of the warp's 32 rows (from row0) by a fixed
-// pairwise tree.  Returns lane q's column sum, scaled.
+__device__ __forceinline__ float4 sq4(float4 a) {
+  return make_float4(a.x * a.x, a.y * a.y, a.z * a.z, a.w * a.w);
+}
+__device__ __forceinline__ float4 add4(float4 a, float4 b) {
+  return make_float4(a.x + b.x, a.y + b.y, a.z + b.z, a.w + b.w);
+}
+
+// Observation by one warp of 32 walkers.  The warp shares one power of two
+// (FP32 sums of scaled weights, the exponent restored exactly in FP64).  Each
+// walker writes its 16 contributions and their squares to its row `row` of
+// shared memory (the four slots of its own representation as zeros, then its
+// own pair's slot).  The warp's 32 rows (from row0) are summed column by
+// column with a fixed pairwise tree ((x0 + x1) + (x2 + x3)) + ...: lane
+// L = 8 g + c reads rows 8g .. 8g+7 of columns 4c .. 4c+3 with 128-bit loads
+// and sums them, and two butterfly exchanges with lanes L ^ 8 and L ^ 16 join
+// the four row groups, leaving lane L with the total of column
+// 4c + 2 (g & 1) + (g >> 1), which it writes, scaled, to red_row[column].
 template <bool DIA>
-__device__ __forceinline__ double observe_warp(Scal& z, bool active, float* obs_rows, int row,
-                                               int row0, int lane) {
+__device__ __forceinline__ void observe_warp(Scal& z, bool active, float* obs_rows, int row,
+                                             int row0, int lane, double* red_row) {
   renorm(z.m, z.mexp);
   phase_wrap(z);
   if (DIA) closed_form(z);  // the rotation to the adiabatic basis at the walker's R
   else z.s2 = z.B * z.ir;   // (the same value closed_form gives)
   const bool live = active && z.m.hi != 0.0f;
   const int ew = __reduce_max_sync(0xffffffffu, live ? z.mexp : -(1 << 28));
-  float v[16];
-  contributions<DIA>(z, live ? (z.m.hi + z.m.lo) * pow2i(z.mexp - ew) : 0.0f, v);
-  float4* r = reinterpret_cast<float4*>(&obs_rows[row * kObsRow]);
+  const Contrib c =
+      contrib_factors<DIA>(z, live ? (z.m.hi + z.m.lo) * pow2i(z.mexp - ew) : 0.0f);
+  constexpr int other = DIA ? 8 : 0, own = DIA ? 0 : 8;
+  float* r = &obs_rows[row * kObsRow];
+  const float4 o0 = make_float4(c.zr * c.f00, c.zi * c.f00, c.zr * c.f01, c.zi * c.f01);
+  const float4 o1 = make_float4(c.zr * c.f10, c.zi * c.f10, c.zr * c.f11, c.zi * c.f11);
+  const float4 zero = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+  *reinterpret_cast<float4*>(r + other) = o0;
+  *reinterpret_cast<float4*>(r + other + 4) = o1;
+  *reinterpret_cast<float4*>(r + 16 + other) = sq4(o0);
+  *reinterpret_cast<float4*>(r + 16 + other + 4) = sq4(o1);
+  *reinterpret_cast<float4*>(r + own) = zero;
+  *reinterpret_cast<float4*>(r + own + 4) = zero;
+  *reinterpret_cast<float4*>(r + 16 + own) = zero;
+  *reinterpret_cast<float4*>(r + 16 + own + 4) = zero;
+  *reinterpret_cast<float2*>(r + own + 2 * c.k) = make_float2(c.zr, c.zi);
+  *reinterpret_cast<float2*>(r + 16 + own + 2 * c.k) = make_float2(c.zr * c.zr, c.zi * c.zi);
+  __syncwarp();
+  const int g = lane >> 3, c4 = lane & 7;
+  const float* base = &obs_rows[(row0 + 8 * g) * kObsRow + 4 * c4];
+  float4 s[8];
 #pragma unroll
-  for (int q = 0; q < 4; ++q) {
-    r[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
-    r[4 + q] = make_float4(v[4 * q] * v[4 * q], v[4 * q + 1] * v[4 * q + 1],
-                           v[4 * q + 2] * v[4 * q + 2], v[4 * q + 3] * v[4 * q + 3]);
-  }
+  for (int i = 0; i < 8; ++i) s[i] = *reinterpret_cast<const float4*>(base + i * kObsRow);
   __syncwarp();
-  const float x = column_sum32(&obs_rows[row0 * kObsRow + lane]);
-  __syncwarp();
-  const int ex = (ew < -(1 << 27)) ? 0 : ((lane < 16) ? ew : 2 * ew);
-  return scaled_double(x, ex);
+  const float4 S = add4(add4(add4(s[0], s[1]), add4(s[2], s[3])),
+                        add4(add4(s[4], s[5]), add4(s[6], s[7])));
+  const bool odd = g & 1, hi = g >> 1;
+  const float t0 = (odd ? S.z : S.x) + __shfl_xor_sync(0xffffffffu, odd ? S.x : S.z, 8);
+  const float t1 = (odd ? S.w : S.y) + __shfl_xor_sync(0xffffffffu, odd ? S.y : S.w, 8);
+  const float x = (hi ? t1 : t0) + __shfl_xor_sync(0xffffffffu, hi ? t0 : t1, 16);
+  const int col = 4 * c4 + 2 * (g & 1) + (g >> 1);
+  const int ex = (ew < -(1 << 27)) ? 0 : ((col < 16) ? ew : 2 * ew);
+  red_row[col] = scaled_double(x, ex);
 }
 
 __device__ __forceinline__ uint32_t pick_word(const u4& wd, int widx) {
@@ -550,7 +588,7 @@ __device__ __forceinline__ void bulk2_tile(const BulkParams& bp, const CF& cf, W
   // observation of walker set k into slot `slot` of its tile's partials (8
   // warps, then the tile's fixed FP64 tree)
   auto observe = [&](int k, int slot) {
-    red[rb][warp][lane] = observe_warp<DIA>(z[k], active[k], obs_rows, threadIdx.x, warp * 32, lane);
+    observe_warp<DIA>(z[k], active[k], obs_rows, threadIdx.x, warp * 32, lane, red[rb][warp]);
     __syncthreads();
     if (threadIdx.x < 32 && tile0 + k < bp.n_tiles)
       part[((int64_t)slot * bp.n_tiles + tile0 + k) * 32 + threadIdx.x] =
