@@ -90,19 +90,125 @@ __device__ __forceinline__ float4 lds4(const float4* p) {
   return v;
 }
 
-// Scalar state of one walker that every lane holding a part of it keeps
-// identical: weight (compensated pair and exponent), phase (compensated pair),
-// the pair's sigmas, and the closed-form decomposition at the current R.
-struct Scal {
-  f2 m;
-  int mexp;
-  int q;                 // quarter turns of the weight (diabatic representation)
-  f2 ph;
-  float sa, sb;          // sigma of the index pair: -1 lower, +1 upper adiabatic state
-  float A, B;            // a(R), b(R)
-  float r2, ir, r;       // r^2, 1/r, r
-  float c2, s2;          // cos 2theta, sin 2theta (theta = 0 at r = 0)
+// ------------------------------------------------ walker lanes (1 or 2) --
+// A thread advances one walker (values of type float) or two (float2: walker
+// l in lane l).  All FP32 arithmetic of a step goes through vfma / vmul / vadd
+// / vsub: for float2 these are the packed FP32x2 instructions (one issue slot
+// for both walkers), and every form rounds each lane exactly as the scalar
+// operation does (IEEE round to nearest, never contracted), so a walker's bits
+// do not depend on the lane count.  Work without a packed form (MUFU,
+// conversions, comparisons, selects, integer work) runs lane by lane.
+template <typename V>
+struct Lanes;
+template <>
+struct Lanes<float> {
+  static constexpr int W = 1;
+  using I = int;
+  using U = uint32_t;
 };
+template <>
+struct Lanes<float2> {
+  static constexpr int W = 2;
+  using I = int2;
+  using U = uint2;
+};
+
+__device__ __forceinline__ float vfma(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+__device__ __forceinline__ float2 vfma(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float vmul(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ float2 vmul(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float vadd(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ float2 vadd(float2 a, float2 b) { return __fadd2_rn(a, b); }
+template <typename V>
+__device__ __forceinline__ V splat(float c);
+template <>
+__device__ __forceinline__ float splat<float>(float c) { return c; }
+template <>
+__device__ __forceinline__ float2 splat<float2>(float c) { return make_float2(c, c); }
+// a - b = fma(b, -1, a) exactly (one rounding, as a subtraction)
+template <typename V>
+__device__ __forceinline__ V vsub(V a, V b) { return vfma(b, splat<V>(-1.0f), a); }
+
+// lane l of a value (l a compile-time constant after unrolling)
+__device__ __forceinline__ float& ln(float& v, int) { return v; }
+__device__ __forceinline__ const float& ln(const float& v, int) { return v; }
+__device__ __forceinline__ float& ln(float2& v, int l) { return l ? v.y : v.x; }
+__device__ __forceinline__ const float& ln(const float2& v, int l) { return l ? v.y : v.x; }
+__device__ __forceinline__ int& ln(int& v, int) { return v; }
+__device__ __forceinline__ const int& ln(const int& v, int) { return v; }
+__device__ __forceinline__ int& ln(int2& v, int l) { return l ? v.y : v.x; }
+__device__ __forceinline__ const int& ln(const int2& v, int l) { return l ? v.y : v.x; }
+__device__ __forceinline__ uint32_t& ln(uint32_t& v, int) { return v; }
+__device__ __forceinline__ const uint32_t& ln(const uint32_t& v, int) { return v; }
+__device__ __forceinline__ uint32_t& ln(uint2& v, int l) { return l ? v.y : v.x; }
+__device__ __forceinline__ const uint32_t& ln(const uint2& v, int l) { return l ? v.y : v.x; }
+
+template <typename V>
+__device__ __forceinline__ PairV<V> two_sum_v(V a, V b) {
+  const V s = vadd(a, b);
+  const V bb = vsub(s, a);
+  return {s, vadd(vsub(a, vsub(s, bb)), vsub(b, bb))};
+}
+template <typename V>
+__device__ __forceinline__ PairV<V> fast_two_sum_v(V a, V b) {  // |a| >= |b|
+  const V s = vadd(a, b);
+  return {s, vsub(b, vsub(s, a))};
+}
+
+// State of one walker (V = float) or two (V = float2) that every holder of a
+// walker keeps identical: weight (compensated pair and exponent), phase
+// (compensated pair), the pair's sigmas, and the closed-form decomposition at
+// the current R.
+template <typename V>
+struct ScalV {
+  PairV<V> m;
+  typename Lanes<V>::I mexp;
+  typename Lanes<V>::I q;  // quarter turns of the weight (diabatic representation)
+  PairV<V> ph;
+  V sa, sb;                // sigma of the index pair: -1 lower, +1 upper adiabatic state
+  V A, B;                  // a(R), b(R)
+  V r2, ir, r;             // r^2, 1/r, r
+  V c2, s2;                // cos 2theta, sin 2theta (theta = 0 at r = 0)
+};
+using Scal = ScalV<float>;
+
+// Walker l of a two-walker state as a one-walker state, and back.
+__device__ __forceinline__ Scal lane_of(const ScalV<float2>& z, int l) {
+  Scal o;
+  o.m = {ln(z.m.hi, l), ln(z.m.lo, l)};
+  o.mexp = ln(z.mexp, l);
+  o.q = ln(z.q, l);
+  o.ph = {ln(z.ph.hi, l), ln(z.ph.lo, l)};
+  o.sa = ln(z.sa, l);
+  o.sb = ln(z.sb, l);
+  o.A = ln(z.A, l);
+  o.B = ln(z.B, l);
+  o.r2 = ln(z.r2, l);
+  o.ir = ln(z.ir, l);
+  o.r = ln(z.r, l);
+  o.c2 = ln(z.c2, l);
+  o.s2 = ln(z.s2, l);
+  return o;
+}
+__device__ __forceinline__ void set_lane(ScalV<float2>& z, int l, const Scal& o) {
+  ln(z.m.hi, l) = o.m.hi;
+  ln(z.m.lo, l) = o.m.lo;
+  ln(z.mexp, l) = o.mexp;
+  ln(z.q, l) = o.q;
+  ln(z.ph.hi, l) = o.ph.hi;
+  ln(z.ph.lo, l) = o.ph.lo;
+  ln(z.sa, l) = o.sa;
+  ln(z.sb, l) = o.sb;
+  ln(z.A, l) = o.A;
+  ln(z.B, l) = o.B;
+  ln(z.r2, l) = o.r2;
+  ln(z.ir, l) = o.ir;
+  ln(z.r, l) = o.r;
+  ln(z.c2, l) = o.c2;
+  ln(z.s2, l) = o.s2;
+}
+__device__ __forceinline__ Scal lane_of(const Scal& z, int) { return z; }
+__device__ __forceinline__ void set_lane(Scal& z, int, const Scal& o) { z = o; }
 
 // cos 2theta = a / r, sin 2theta = b / r.  r^2 is floored at the smallest
 // normal float, so at an exact degeneracy (a = b = 0 in FP32, where the angle
@@ -110,28 +216,46 @@ struct Scal {
 // the two branches -- instead of a division by zero.
 // S2 = false leaves s2 stale (the spin-boson step needs no sin 2theta; the
 // observation recomputes it).
-template <bool S2 = true>
-__device__ __forceinline__ void closed_form(Scal& z) {
-  z.r2 = __fmaf_rn(z.A, z.A, z.B * z.B);
-  z.ir = rsqrtf(fmaxf(z.r2, 0x1p-126f));
-  z.r = z.r2 * z.ir;
-  z.c2 = z.A * z.ir;
-  if (S2) z.s2 = z.B * z.ir;
+template <bool S2 = true, typename V>
+__device__ __forceinline__ void closed_form(ScalV<V>& z) {
+  z.r2 = vfma(z.A, z.A, vmul(z.B, z.B));
+#pragma unroll
+  for (int l = 0; l < Lanes<V>::W; ++l) ln(z.ir, l) = rsqrtf(fmaxf(ln(z.r2, l), 0x1p-126f));
+  z.r = vmul(z.r2, z.ir);
+  z.c2 = vmul(z.A, z.ir);
+  if (S2) z.s2 = vmul(z.B, z.ir);
 }
 
 // m *= num / den (den an integer below 2^25, so exact in FP32) as a
 // compensated quotient: rcp.approx, one exact FMA residual, and the product
 // with the error terms collected in lo.
-__device__ __forceinline__ void weight_factor(Scal& z, float num, uint32_t iden) {
-  const float den = __uint2float_rn(iden);
-  const float rd = rcp_approx(den);
-  const float q0 = num * rd;
-  const float q1 = __fmaf_rn(-q0, den, num) * rd;
-  const float p = z.m.hi * q0;
-  float e = __fmaf_rn(z.m.hi, q0, -p);
-  e = __fmaf_rn(z.m.hi, q1, e);
-  z.m = {p, __fmaf_rn(z.m.lo, q0, e)};
-  if (!(fabsf(z.m.hi) <= 0x1p32f && fabsf(z.m.hi) >= 0x1p-32f)) renorm(z.m, z.mexp);
+template <typename V>
+__device__ __forceinline__ void weight_factor(ScalV<V>& z, V num, const typename Lanes<V>::U& iden) {
+  V den, rd;
+#pragma unroll
+  for (int l = 0; l < Lanes<V>::W; ++l) {
+    ln(den, l) = __uint2float_rn(ln(iden, l));
+    ln(rd, l) = rcp_approx(ln(den, l));
+  }
+  const V q0 = vmul(num, rd);
+  // num - q0 den = fma(q0, -den, num), exactly as fma(-q0, den, num)
+  const V q1 = vmul(vfma(q0, vmul(den, splat<V>(-1.0f)), num), rd);
+  const V p = vmul(z.m.hi, q0);
+  V e = vfma(z.m.hi, q0, vmul(p, splat<V>(-1.0f)));
+  e = vfma(z.m.hi, q1, e);
+  z.m = {p, vfma(z.m.lo, q0, e)};
+#pragma unroll
+  for (int l = 0; l < Lanes<V>::W; ++l) {
+    const float h = ln(z.m.hi, l);
+    if (!(fabsf(h) <= 0x1p32f && fabsf(h) >= 0x1p-32f)) {
+      f2 m = {h, ln(z.m.lo, l)};
+      int ex = ln(z.mexp, l);
+      renorm(m, ex);
+      ln(z.m.hi, l) = m.hi;
+      ln(z.m.lo, l) = m.lo;
+      ln(z.mexp, l) = ex;
+    }
+  }
 }
 
 // Phase (trapezoid) and transition of one step, given the decomposition at
@@ -141,36 +265,60 @@ __device__ __forceinline__ void weight_factor(Scal& z, float num, uint32_t iden)
 // weight and phase pairs are left unnormalised (|lo| may grow past ulp(hi)/2
 // by about an ulp per step); the step loop renormalises both at every fourth
 // step (block_end).
-template <int KIND>
-__device__ __forceinline__ void phase_and_transition(Scal& z, float r_old, float Av, float Bv,
-                                                     uint32_t word, const BulkParams& bp,
-                                                     unsigned int& deg) {
+template <int KIND, typename V>
+__device__ __forceinline__ void phase_and_transition(ScalV<V>& z, V r_old, V Av, V Bv,
+                                                     const typename Lanes<V>::U& word,
+                                                     const BulkParams& bp,
+                                                     typename Lanes<V>::U& deg) {
+  constexpr int W = Lanes<V>::W;
   // phase: dt/2 (w_ab(R_n) + w_ab(R_{n+1})), hbar w_ab = (sig_a - sig_b) r, added
   // to the low word of the pair (at most four increments and their rounding
   // errors until block_end folds it into hi)
-  z.ph.lo = __fmaf_rn(bp.hdt_hbar * (z.sa - z.sb), r_old + z.r, z.ph.lo);
+  z.ph.lo = vfma(vmul(splat<V>(bp.hdt_hbar), vsub(z.sa, z.sb)), vadd(r_old, z.r), z.ph.lo);
   // coupling contracted with P/M: g = (a Bv - b Av) / (2 r^2)
-  // (2 r < tol, compared as r^2 < tol^2 / 4)
-  const bool degen = z.r2 < 0.25f * kDegTol32 * kDegTol32;
-  deg += degen ? 1u : 0u;
-  // the spin-boson form has b = b0: -b/2 is a per-launch constant
-  const float gn = (KIND == 1) ? 0.5f * (z.A * Bv - z.B * Av) : (-0.5f * bp.b0) * Av;
-  const float g = degen ? 0.0f : gn * (z.ir * z.ir);
+  // (2 r < tol, compared as r^2 < tol^2 / 4); the spin-boson form has b = b0,
+  // so -b/2 is a per-launch constant
+  const V gn = (KIND == 1) ? vmul(splat<V>(0.5f), vsub(vmul(z.A, Bv), vmul(z.B, Av)))
+                           : vmul(splat<V>(-0.5f * bp.b0), Av);
+  V g = vmul(gn, vmul(z.ir, z.ir));
   // both events have |A_e| = dt |g|: p = min(kappa dt |g|, p_max) quantised to
   // 24-bit thresholds T = floor(p 2^24); when 2T exceeds Tmax = floor(p_max 2^24)
   // the integer rescale floor(T Tmax / 2T) gives floor(Tmax / 2), so
   // T = min(floor(kappa dt |g| 2^24), floor(Tmax / 2)) (the conversion saturates)
-  const uint32_t T = min(__float2uint_rz((bp.kamp * kP24f) * fabsf(g)), bp.tmax >> 1);
-  const uint32_t y = word >> 8;
-  const bool hop1 = y < T;
-  const bool hop = y < 2u * T;
-  const bool hop2 = hop && !hop1;
+  V t;
+  typename Lanes<V>::U T, iden;
+  bool hop1[W], hop2[W], hop[W];
+#pragma unroll
+  for (int l = 0; l < W; ++l) {
+    const bool degen = ln(z.r2, l) < 0.25f * kDegTol32 * kDegTol32;
+    ln(deg, l) += degen ? 1u : 0u;
+    ln(g, l) = degen ? 0.0f : ln(g, l);
+  }
+  t = vmul(splat<V>(bp.kamp * kP24f), g);
   // weight factor: A_e / p_hat on a hop (A_1 = -sig_a dt g, A_2 = -sig_b dt g),
   // 1 / (1 - sum p_hat) otherwise
-  const float dtg = (bp.amp * kP24f) * g;
-  weight_factor(z, hop ? -(hop1 ? z.sa : z.sb) * dtg : kP24f, hop ? T : 16777216u - 2u * T);
-  z.sa = hop1 ? -z.sa : z.sa;
-  z.sb = hop2 ? -z.sb : z.sb;
+  const V dtgn = vmul(splat<V>(-(bp.amp * kP24f)), g);
+  V sel;
+#pragma unroll
+  for (int l = 0; l < W; ++l) {
+    ln(T, l) = min(__float2uint_rz(fabsf(ln(t, l))), bp.tmax >> 1);
+    const uint32_t y = ln(word, l) >> 8;
+    hop1[l] = y < ln(T, l);
+    hop[l] = y < 2u * ln(T, l);
+    hop2[l] = hop[l] && !hop1[l];
+    ln(sel, l) = hop1[l] ? ln(z.sa, l) : ln(z.sb, l);
+    ln(iden, l) = hop[l] ? ln(T, l) : 16777216u - 2u * ln(T, l);
+  }
+  V num = vmul(sel, dtgn);
+  const V nsa = vmul(z.sa, splat<V>(-1.0f)), nsb = vmul(z.sb, splat<V>(-1.0f));
+#pragma unroll
+  for (int l = 0; l < W; ++l) {
+    ln(num, l) = hop[l] ? ln(num, l) : kP24f;
+    ln(z.sa, l) = hop1[l] ? ln(nsa, l) : ln(z.sa, l);
+    ln(z.sb, l) = hop2[l] ? ln(nsb, l) : ln(z.sb, l);
+  }
+  // (sigmas flipped after the weight factor has taken the pre-hop sigma in sel)
+  weight_factor(z, num, iden);
 }
 
 // Diabatic representation: phase with hbar w_ab = V_aa - V_bb = -(sig_a - sig_b)
@@ -179,25 +327,42 @@ __device__ __forceinline__ void phase_and_transition(Scal& z, float r_old, float
 // (+i c) with c = V_01 dt / hbar = b(R_{n+1}) dt / hbar = amp * Bc.  Both have
 // |A_e| = |c|, so the thresholds follow the adiabatic rule; a hop adds three or
 // one quarter turns.
-__device__ __forceinline__ void dia_phase_and_transition(Scal& z, float a_old, float Bc,
-                                                         uint32_t word, const BulkParams& bp) {
-  z.ph.lo = __fmaf_rn(bp.hdt_hbar * (z.sb - z.sa), a_old + z.A, z.ph.lo);
-  const uint32_t T = min(__float2uint_rz((bp.kamp * kP24f) * fabsf(Bc)), bp.tmax >> 1);
-  const uint32_t y = word >> 8;
-  const bool hop1 = y < T;
-  const bool hop = y < 2u * T;
-  const bool hop2 = hop && !hop1;
-  weight_factor(z, hop ? (bp.amp * kP24f) * Bc : kP24f, hop ? T : 16777216u - 2u * T);
-  z.q = (z.q + (hop1 ? 3 : (hop2 ? 1 : 0))) & 3;
-  z.sa = hop1 ? -z.sa : z.sa;
-  z.sb = hop2 ? -z.sb : z.sb;
+template <typename V>
+__device__ __forceinline__ void dia_phase_and_transition(ScalV<V>& z, V a_old, V Bc,
+                                                         const typename Lanes<V>::U& word,
+                                                         const BulkParams& bp) {
+  constexpr int W = Lanes<V>::W;
+  z.ph.lo = vfma(vmul(splat<V>(bp.hdt_hbar), vsub(z.sb, z.sa)), vadd(a_old, z.A), z.ph.lo);
+  const V t = vmul(splat<V>(bp.kamp * kP24f), Bc);
+  V num = vmul(splat<V>(bp.amp * kP24f), Bc);
+  typename Lanes<V>::U iden;
+  bool hop1[W], hop2[W];
+#pragma unroll
+  for (int l = 0; l < W; ++l) {
+    const uint32_t T = min(__float2uint_rz(fabsf(ln(t, l))), bp.tmax >> 1);
+    const uint32_t y = ln(word, l) >> 8;
+    hop1[l] = y < T;
+    const bool hop = y < 2u * T;
+    hop2[l] = hop && !hop1[l];
+    ln(num, l) = hop ? ln(num, l) : kP24f;
+    ln(iden, l) = hop ? T : 16777216u - 2u * T;
+  }
+  weight_factor(z, num, iden);
+  const V nsa = vmul(z.sa, splat<V>(-1.0f)), nsb = vmul(z.sb, splat<V>(-1.0f));
+#pragma unroll
+  for (int l = 0; l < W; ++l) {
+    ln(z.q, l) = (ln(z.q, l) + (hop1[l] ? 3 : (hop2[l] ? 1 : 0))) & 3;
+    ln(z.sa, l) = hop1[l] ? ln(nsa, l) : ln(z.sa, l);
+    ln(z.sb, l) = hop2[l] ? ln(nsb, l) : ln(z.sb, l);
+  }
 }
 
 // Renormalises the weight and phase pairs; called at the end of every Philox
 // block (absolute steps 4k + 3), whatever the chunking.
-__device__ __forceinline__ void block_end(Scal& z) {
-  z.m = fast_two_sum(z.m.hi, z.m.lo);
-  z.ph = two_sum(z.ph.hi, z.ph.lo);
+template <typename V>
+__device__ __forceinline__ void block_end(ScalV<V>& z) {
+  z.m = fast_two_sum_v(z.m.hi, z.m.lo);
+  z.ph = two_sum_v(z.ph.hi, z.ph.lo);
 }
 
 // FP32 initial sample of one walker with random-stream id `traj` from the same
@@ -495,34 +660,36 @@ struct PlainStream {
   }
 };
 
-template <int NPL>
-struct Walker {
-  float R[NPL], P[NPL];
+template <int NPL, typename V = float>
+struct WalkerV {
+  V R[NPL], P[NPL];
 };
+template <int NPL>
+using Walker = WalkerV<NPL, float>;
 
 // P += dt/2 F_ab(R),  F_j = -k_j R_j - s_j - sab (a_j cos2t + b_j sin2t);
 // hu = dt/2 sab cos2t, hv = dt/2 sab sin2t
-template <int NPL, int KIND, typename CF>
-__device__ __forceinline__ void kick(Walker<NPL>& w, const CF& cf, float hu, float hv) {
+template <int NPL, int KIND, typename CF, typename V>
+__device__ __forceinline__ void kick(WalkerV<NPL, V>& w, const CF& cf, V hu, V hv) {
 #pragma unroll
   for (int j = 0; j < NPL; ++j) {
-    float p = __fmaf_rn(-cf.hk[j], w.R[j], w.P[j]);
-    if (KIND == 1) p -= cf.hs[j];
-    p = __fmaf_rn(-hu, cf.a[j], p);
-    if (KIND == 1) p = __fmaf_rn(-hv, cf.b[j], p);
+    V p = vfma(splat<V>(-cf.hk[j]), w.R[j], w.P[j]);
+    if (KIND == 1) p = vadd(p, splat<V>(-cf.hs[j]));
+    p = vfma(hu, splat<V>(-cf.a[j]), p);
+    if (KIND == 1) p = vfma(hv, splat<V>(-cf.b[j]), p);
     w.P[j] = p;
   }
 }
 
 // Diabatic kick: P += dt/2 F_ab(R), F_j = -k_j R_j - s_j + sab a_j (the
 // adiabatic kick's force with cos 2theta = -1, sin 2theta = 0), hsab = dt/2 sab.
-template <int NPL, int KIND, typename CF>
-__device__ __forceinline__ void kick_dia(Walker<NPL>& w, const CF& cf, float hsab) {
+template <int NPL, int KIND, typename CF, typename V>
+__device__ __forceinline__ void kick_dia(WalkerV<NPL, V>& w, const CF& cf, V hsab) {
 #pragma unroll
   for (int j = 0; j < NPL; ++j) {
-    float p = __fmaf_rn(-cf.hk[j], w.R[j], w.P[j]);
-    if (KIND == 1) p -= cf.hs[j];
-    w.P[j] = __fmaf_rn(hsab, cf.a[j], p);
+    V p = vfma(splat<V>(-cf.hk[j]), w.R[j], w.P[j]);
+    if (KIND == 1) p = vadd(p, splat<V>(-cf.hs[j]));
+    w.P[j] = vfma(hsab, splat<V>(cf.a[j]), p);
   }
 }
 
@@ -532,30 +699,34 @@ struct CoefLocal {
   float hk[NPL], hs[NPL], dtm[NPL], a[NPL], b[NPL], am[NPL], bm[NPL];
 };
 
-// WPT consecutive 256-walker tiles (tile0, tile0 + 1, ...) of the
+// WPT (1 or 2) consecutive 256-walker tiles (tile0, tile0 + 1) of the
 // one-thread-per-walker kernel, thread t owning walker t of each: load the
 // walkers, advance them over steps [cs, ce) with their observations, store
-// them.  The walkers of one thread are independent, so their steps interleave
-// (instruction-level parallelism); each walker's arithmetic and each tile's
-// reduction are exactly those of WPT = 1, so the results do not depend on WPT.
-// `cf` holds the per-mode coefficients (kernel parameters, or registers in the
-// packed kernel); all threads of the block call it together.  LEAN selects the
-// register-lean form for kernels short of registers (many modes, coefficients
-// in registers): steps one at a time and the whole Philox function per draw,
-// instead of the unrolled four-step blocks below and the precomputed stream.
-// Both forms give the same bits.
+// them.  With WPT = 2 the thread's two walkers are the two lanes of float2
+// values and step together through the packed FP32x2 instructions; each
+// walker's arithmetic and each tile's reduction are exactly those of WPT = 1,
+// so the results do not depend on WPT.  `cf` holds the per-mode coefficients
+// (kernel parameters, or registers in the packed kernel); all threads of the
+// block call it together.  LEAN selects the register-lean form for kernels
+// short of registers (many modes, coefficients in registers): steps one at a
+// time and the whole Philox function per draw, instead of the unrolled
+// four-step blocks below and the precomputed stream.  Both forms give the same
+// bits.
 template <int NPL, int KIND, typename CF, bool LEAN, bool DIA = false, int WPT = 1>
 __device__ __forceinline__ void bulk2_tile(const BulkParams& bp, const CF& cf, W32& ws,
                                            double* __restrict__ part, int64_t tile0, int& rb,
                                            unsigned int& n_deg, double (&red)[2][8][32],
                                            float* obs_rows) {
+  static_assert(WPT == 1 || WPT == 2, "one or two walkers per thread");
+  using V = std::conditional_t<WPT == 2, float2, float>;
+  using U = typename Lanes<V>::U;
   using Stream = std::conditional_t<LEAN, PlainStream, PhiloxStream>;
   const int64_t nt = bp.n_traj;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  Walker<NPL> w[WPT];
-  Scal z[WPT];
+  WalkerV<NPL, V> w;
+  ScalV<V> z;
   bool active[WPT];
-  unsigned int deg[WPT];
+  U deg;
 #pragma unroll
   for (int k = 0; k < WPT; ++k) {
     const int64_t i = (tile0 + k) * kTile + threadIdx.x;
@@ -564,31 +735,35 @@ __device__ __forceinline__ void bulk2_tile(const BulkParams& bp, const CF& cf, W
 #pragma unroll
     for (int j = 0; j < NPL; ++j) {
       const bool on = active[k] && j < bp.n;
-      w[k].R[j] = on ? ws.R[(int64_t)j * nt + ii] : 0.0f;
-      w[k].P[j] = on ? ws.P[(int64_t)j * nt + ii] : 0.0f;
+      ln(w.R[j], k) = on ? ws.R[(int64_t)j * nt + ii] : 0.0f;
+      ln(w.P[j], k) = on ? ws.P[(int64_t)j * nt + ii] : 0.0f;
     }
-    z[k].m = {active[k] ? ws.mh[ii] : 0.0f, active[k] ? ws.ml[ii] : 0.0f};
-    z[k].mexp = active[k] ? ws.me[ii] : 0;
-    z[k].ph = {active[k] ? ws.ph[ii] : 0.0f, active[k] ? ws.pl[ii] : 0.0f};
+    ln(z.m.hi, k) = active[k] ? ws.mh[ii] : 0.0f;
+    ln(z.m.lo, k) = active[k] ? ws.ml[ii] : 0.0f;
+    ln(z.mexp, k) = active[k] ? ws.me[ii] : 0;
+    ln(z.ph.hi, k) = active[k] ? ws.ph[ii] : 0.0f;
+    ln(z.ph.lo, k) = active[k] ? ws.pl[ii] : 0.0f;
     const uint32_t ab = active[k] ? ws.ab[ii] : 0u;  // alpha | q << 4 | beta << 8
-    z[k].sa = sgn(ab & 0xf);
-    z[k].sb = sgn((ab >> 8) & 0xf);
-    z[k].q = DIA ? (int)((ab >> 4) & 3u) : 0;
-    z[k].A = bp.a0;
-    z[k].B = bp.b0;
-#pragma unroll
-    for (int j = 0; j < NPL; ++j) {
-      z[k].A = __fmaf_rn(cf.a[j], w[k].R[j], z[k].A);
-      if (KIND == 1) z[k].B = __fmaf_rn(cf.b[j], w[k].R[j], z[k].B);
-    }
-    closed_form(z[k]);
-    deg[k] = 0;
+    ln(z.sa, k) = sgn(ab & 0xf);
+    ln(z.sb, k) = sgn((ab >> 8) & 0xf);
+    ln(z.q, k) = DIA ? (int)((ab >> 4) & 3u) : 0;
+    ln(deg, k) = 0u;
   }
+  z.A = splat<V>(bp.a0);
+  z.B = splat<V>(bp.b0);
+#pragma unroll
+  for (int j = 0; j < NPL; ++j) {
+    z.A = vfma(splat<V>(cf.a[j]), w.R[j], z.A);
+    if (KIND == 1) z.B = vfma(splat<V>(cf.b[j]), w.R[j], z.B);
+  }
+  closed_form(z);
 
-  // observation of walker set k into slot `slot` of its tile's partials (8
-  // warps, then the tile's fixed FP64 tree)
+  // observation of walker k into slot `slot` of its tile's partials (8 warps,
+  // then the tile's fixed FP64 tree)
   auto observe = [&](int k, int slot) {
-    observe_warp<DIA>(z[k], active[k], obs_rows, threadIdx.x, warp * 32, lane, red[rb][warp]);
+    Scal zk = lane_of(z, k);
+    observe_warp<DIA>(zk, active[k], obs_rows, threadIdx.x, warp * 32, lane, red[rb][warp]);
+    set_lane(z, k, zk);
     __syncthreads();
     if (threadIdx.x < 32 && tile0 + k < bp.n_tiles)
       part[((int64_t)slot * bp.n_tiles + tile0 + k) * 32 + threadIdx.x] =
@@ -600,48 +775,46 @@ __device__ __forceinline__ void bulk2_tile(const BulkParams& bp, const CF& cf, W
     for (int k = 0; k < WPT; ++k) observe(k, slot);
   };
 
-  // one velocity-Verlet step of walker k with its phase and transition (hop
-  // word `word`)
-  auto step = [&](int k, uint32_t word) {
-    Walker<NPL>& wk = w[k];
-    Scal& zk = z[k];
-    const float hsab = bp.hdt * 0.5f * (zk.sa + zk.sb);  // dt/2 (sig_a + sig_b)/2
+  // one velocity-Verlet step of the walkers with their phase and transition
+  // (hop words `word`)
+  auto step = [&](const U& word) {
+    const V hsab = vmul(splat<V>(bp.hdt * 0.5f), vadd(z.sa, z.sb));  // dt/2 (sig_a + sig_b)/2
     if constexpr (DIA) {
-      kick_dia<NPL, KIND, CF>(wk, cf, hsab);
+      kick_dia<NPL, KIND, CF>(w, cf, hsab);
 #pragma unroll
-      for (int j = 0; j < NPL; ++j) wk.R[j] = __fmaf_rn(cf.dtm[j], wk.P[j], wk.R[j]);
-      const float a_old = zk.A;
-      zk.A = bp.a0;
-      if (KIND == 1) zk.B = bp.b0;
+      for (int j = 0; j < NPL; ++j) w.R[j] = vfma(splat<V>(cf.dtm[j]), w.P[j], w.R[j]);
+      const V a_old = z.A;
+      z.A = splat<V>(bp.a0);
+      if (KIND == 1) z.B = splat<V>(bp.b0);
 #pragma unroll
       for (int j = 0; j < NPL; ++j) {
-        zk.A = __fmaf_rn(cf.a[j], wk.R[j], zk.A);
-        if (KIND == 1) zk.B = __fmaf_rn(cf.b[j], wk.R[j], zk.B);
+        z.A = vfma(splat<V>(cf.a[j]), w.R[j], z.A);
+        if (KIND == 1) z.B = vfma(splat<V>(cf.b[j]), w.R[j], z.B);
       }
-      kick_dia<NPL, KIND, CF>(wk, cf, hsab);
-      dia_phase_and_transition(zk, a_old, zk.B, word, bp);
+      kick_dia<NPL, KIND, CF>(w, cf, hsab);
+      dia_phase_and_transition(z, a_old, z.B, word, bp);
       return;
     }
-    kick<NPL, KIND, CF>(wk, cf, hsab * zk.c2, hsab * zk.s2);  // first half kick at R_n
+    kick<NPL, KIND, CF>(w, cf, vmul(hsab, z.c2), vmul(hsab, z.s2));  // first half kick at R_n
 #pragma unroll
-    for (int j = 0; j < NPL; ++j) wk.R[j] = __fmaf_rn(cf.dtm[j], wk.P[j], wk.R[j]);  // drift
-    const float r_old = zk.r;
-    zk.A = bp.a0;
-    zk.B = bp.b0;
-#pragma unroll
-    for (int j = 0; j < NPL; ++j) {
-      zk.A = __fmaf_rn(cf.a[j], wk.R[j], zk.A);
-      if (KIND == 1) zk.B = __fmaf_rn(cf.b[j], wk.R[j], zk.B);
-    }
-    closed_form<KIND == 1>(zk);
-    kick<NPL, KIND, CF>(wk, cf, hsab * zk.c2, hsab * zk.s2);  // second half kick at R_{n+1}
-    float Av = 0.0f, Bv = 0.0f;
+    for (int j = 0; j < NPL; ++j) w.R[j] = vfma(splat<V>(cf.dtm[j]), w.P[j], w.R[j]);  // drift
+    const V r_old = z.r;
+    z.A = splat<V>(bp.a0);
+    z.B = splat<V>(bp.b0);
 #pragma unroll
     for (int j = 0; j < NPL; ++j) {
-      Av = __fmaf_rn(cf.am[j], wk.P[j], Av);
-      if (KIND == 1) Bv = __fmaf_rn(cf.bm[j], wk.P[j], Bv);
+      z.A = vfma(splat<V>(cf.a[j]), w.R[j], z.A);
+      if (KIND == 1) z.B = vfma(splat<V>(cf.b[j]), w.R[j], z.B);
     }
-    phase_and_transition<KIND>(zk, r_old, Av, Bv, word, bp, deg[k]);
+    closed_form<KIND == 1>(z);
+    kick<NPL, KIND, CF>(w, cf, vmul(hsab, z.c2), vmul(hsab, z.s2));  // second half kick at R_{n+1}
+    V Av = splat<V>(0.0f), Bv = splat<V>(0.0f);
+#pragma unroll
+    for (int j = 0; j < NPL; ++j) {
+      Av = vfma(splat<V>(cf.am[j]), w.P[j], Av);
+      if (KIND == 1) Bv = vfma(splat<V>(cf.bm[j]), w.P[j], Bv);
+    }
+    phase_and_transition<KIND>(z, r_old, Av, Bv, word, bp, deg);
   };
 
   // Steps are grouped by Philox block (four steps share one draw).  A whole
@@ -662,20 +835,20 @@ __device__ __forceinline__ void bulk2_tile(const BulkParams& bp, const CF& cf, W
     rng[k] = Stream(bp.seed, bp.traj_offset + (uint64_t)ii, kPurposeHop);
     wd[k] = rng[k].draw(blk);
   }
+  auto words = [&](int q) {
+    U u;
+#pragma unroll
+    for (int k = 0; k < WPT; ++k) ln(u, k) = pick_word(wd[k], q);
+    return u;
+  };
   int it = 0;
   while (it < bp.len) {
     if (!LEAN && widx == 0 && bp.len - it >= 4 && to_out >= 4) {
-#pragma unroll
-      for (int k = 0; k < WPT; ++k) step(k, wd[k].x);
-#pragma unroll
-      for (int k = 0; k < WPT; ++k) step(k, wd[k].y);
-#pragma unroll
-      for (int k = 0; k < WPT; ++k) step(k, wd[k].z);
-#pragma unroll
-      for (int k = 0; k < WPT; ++k) {
-        step(k, wd[k].w);
-        block_end(z[k]);
-      }
+      step(words(0));
+      step(words(1));
+      step(words(2));
+      step(words(3));
+      block_end(z);
       it += 4;
       to_out -= 4;
       ++blk;
@@ -684,14 +857,12 @@ __device__ __forceinline__ void bulk2_tile(const BulkParams& bp, const CF& cf, W
         for (int k = 0; k < WPT; ++k) wd[k] = rng[k].draw(blk);
       }
     } else {
-#pragma unroll
-      for (int k = 0; k < WPT; ++k) step(k, pick_word(wd[k], widx));
+      step(words(widx));
       ++it;
       --to_out;
       if (++widx == 4) {
         widx = 0;
-#pragma unroll
-        for (int k = 0; k < WPT; ++k) block_end(z[k]);
+        block_end(z);
         ++blk;
         if (it < bp.len) {
 #pragma unroll
@@ -708,21 +879,22 @@ __device__ __forceinline__ void bulk2_tile(const BulkParams& bp, const CF& cf, W
   for (int k = 0; k < WPT; ++k) {
     if (!active[k]) continue;
     const int64_t i = (tile0 + k) * kTile + threadIdx.x;
-    const Scal& zk = z[k];
-    n_deg += deg[k];
+    n_deg += ln(deg, k);
 #pragma unroll
     for (int j = 0; j < NPL; ++j)
       if (j < bp.n) {
-        ws.R[(int64_t)j * nt + i] = w[k].R[j];
-        ws.P[(int64_t)j * nt + i] = w[k].P[j];
+        ws.R[(int64_t)j * nt + i] = ln(w.R[j], k);
+        ws.P[(int64_t)j * nt + i] = ln(w.P[j], k);
       }
-    ws.mh[i] = zk.m.hi;
-    ws.ml[i] = zk.m.lo;
-    ws.me[i] = zk.mexp;
-    ws.ph[i] = zk.ph.hi;
-    ws.pl[i] = zk.ph.lo;
-    ws.ab[i] = (uint16_t)((zk.sa > 0.0f ? 1 : 0) | (zk.q << 4) | ((zk.sb > 0.0f ? 1 : 0) << 8));
-    if (!isfinite(zk.m.hi) || !isfinite(zk.ph.hi)) {
+    const float mh = ln(z.m.hi, k), ph = ln(z.ph.hi, k);
+    ws.mh[i] = mh;
+    ws.ml[i] = ln(z.m.lo, k);
+    ws.me[i] = ln(z.mexp, k);
+    ws.ph[i] = ph;
+    ws.pl[i] = ln(z.ph.lo, k);
+    ws.ab[i] = (uint16_t)((ln(z.sa, k) > 0.0f ? 1 : 0) | (ln(z.q, k) << 4) |
+                          ((ln(z.sb, k) > 0.0f ? 1 : 0) << 8));
+    if (!isfinite(mh) || !isfinite(ph)) {
       atomicAdd(&ws.hdr->n_nonfinite, 1ull);
       atomicOr(&ws.hdr->flags, QCL_FLAG_NONFINITE);
     }

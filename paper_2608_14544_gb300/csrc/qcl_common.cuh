@@ -115,10 +115,13 @@ __device__ __forceinline__ uint32_t word_of(const u4& w, int i) {
 }
 
 // ------------------------------------------------ compensated FP32 pairs --
-// (hi, lo) with |lo| <= ulp(hi)/2 represents hi + lo to about 2^-46.
-struct f2 {
-  float hi, lo;
+// (hi, lo) with |lo| <= ulp(hi)/2 represents hi + lo to about 2^-46.  V is
+// float, or float2 for the same pair of two walkers held in one register pair.
+template <typename V>
+struct PairV {
+  V hi, lo;
 };
+using f2 = PairV<float>;
 
 __device__ __forceinline__ f2 two_sum(float a, float b) {
   const float s = a + b;
