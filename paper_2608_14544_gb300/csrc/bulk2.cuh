@@ -18,7 +18,6 @@ constexpr float kTwoPi1 = 6.283203125f;
 constexpr float kTwoPi2 = -1.7818063497543335e-05f;
 constexpr float kTwoPi3 = 2.430840251310684e-10f;
 constexpr float kInvTwoPi = 0.15915494309189535f;
-constexpr float kDegTol32 = 1e-6f;  // |e_b - e_a| below this: coupling set to 0
 
 struct W32 {
   float* R;
@@ -226,10 +225,26 @@ __device__ __forceinline__ void closed_form(ScalV<V>& z) {
   if (S2) z.s2 = vmul(z.B, z.ir);
 }
 
+// Lane l's weight: moves hi's exponent into mexp when hi has left
+// [2^-32, 2^32].
+template <typename V>
+__device__ __forceinline__ void weight_range(ScalV<V>& z, int l) {
+  const float h = ln(z.m.hi, l);
+  if (!(fabsf(h) <= 0x1p32f && fabsf(h) >= 0x1p-32f)) {
+    f2 m = {h, ln(z.m.lo, l)};
+    int ex = ln(z.mexp, l);
+    renorm(m, ex);
+    ln(z.m.hi, l) = m.hi;
+    ln(z.m.lo, l) = m.lo;
+    ln(z.mexp, l) = ex;
+  }
+}
+
 // m *= num / den (den an integer below 2^25, so exact in FP32) as a
 // compensated quotient: rcp.approx, one exact FMA residual, and the product
-// with the error terms collected in lo.
-template <typename V>
+// with the error terms collected in lo.  CHECK = false leaves the range check
+// (weight_range) to the caller.
+template <bool CHECK = true, typename V>
 __device__ __forceinline__ void weight_factor(ScalV<V>& z, V num, const typename Lanes<V>::U& iden) {
   V den, rd;
 #pragma unroll
@@ -244,17 +259,9 @@ __device__ __forceinline__ void weight_factor(ScalV<V>& z, V num, const typename
   V e = vfma(z.m.hi, q0, vmul(p, splat<V>(-1.0f)));
   e = vfma(z.m.hi, q1, e);
   z.m = {p, vfma(z.m.lo, q0, e)};
+  if (CHECK) {
 #pragma unroll
-  for (int l = 0; l < Lanes<V>::W; ++l) {
-    const float h = ln(z.m.hi, l);
-    if (!(fabsf(h) <= 0x1p32f && fabsf(h) >= 0x1p-32f)) {
-      f2 m = {h, ln(z.m.lo, l)};
-      int ex = ln(z.mexp, l);
-      renorm(m, ex);
-      ln(z.m.hi, l) = m.hi;
-      ln(z.m.lo, l) = m.lo;
-      ln(z.mexp, l) = ex;
-    }
+    for (int l = 0; l < Lanes<V>::W; ++l) weight_range(z, l);
   }
 }
 
@@ -285,16 +292,17 @@ __device__ __forceinline__ void phase_and_transition(ScalV<V>& z, V r_old, V Av,
   // 24-bit thresholds T = floor(p 2^24); when 2T exceeds Tmax = floor(p_max 2^24)
   // the integer rescale floor(T Tmax / 2T) gives floor(Tmax / 2), so
   // T = min(floor(kappa dt |g| 2^24), floor(Tmax / 2)) (the conversion saturates)
-  V t;
   typename Lanes<V>::U T, iden;
   bool hop1[W], hop2[W], hop[W];
+  if (KIND == 1) {  // (the spin-boson form runs only where r^2 >= b0^2 excludes degeneracy)
 #pragma unroll
-  for (int l = 0; l < W; ++l) {
-    const bool degen = ln(z.r2, l) < 0.25f * kDegTol32 * kDegTol32;
-    ln(deg, l) += degen ? 1u : 0u;
-    ln(g, l) = degen ? 0.0f : ln(g, l);
+    for (int l = 0; l < W; ++l) {
+      const bool degen = ln(z.r2, l) < kDegR2_32;
+      ln(deg, l) += degen ? 1u : 0u;
+      ln(g, l) = degen ? 0.0f : ln(g, l);
+    }
   }
-  t = vmul(splat<V>(bp.kamp * kP24f), g);
+  const V t = vmul(splat<V>(bp.kamp * kP24f), g);
   // weight factor: A_e / p_hat on a hop (A_1 = -sig_a dt g, A_2 = -sig_b dt g),
   // 1 / (1 - sum p_hat) otherwise
   const V dtgn = vmul(splat<V>(-(bp.amp * kP24f)), g);
@@ -317,8 +325,14 @@ __device__ __forceinline__ void phase_and_transition(ScalV<V>& z, V r_old, V Av,
     ln(z.sa, l) = hop1[l] ? ln(nsa, l) : ln(z.sa, l);
     ln(z.sb, l) = hop2[l] ? ln(nsb, l) : ln(z.sb, l);
   }
-  // (sigmas flipped after the weight factor has taken the pre-hop sigma in sel)
-  weight_factor(z, num, iden);
+  // (sigmas flipped after the weight factor has taken the pre-hop sigma in sel).
+  // A stay multiplies the weight by at most 1 / (1 - p_max) per step, so its
+  // range is checked at the end of the Philox block; a hop's factor is checked
+  // at once.
+  weight_factor<false>(z, num, iden);
+#pragma unroll
+  for (int l = 0; l < W; ++l)
+    if (hop[l]) weight_range(z, l);
 }
 
 // Diabatic representation: phase with hbar w_ab = V_aa - V_bb = -(sig_a - sig_b)
@@ -336,18 +350,21 @@ __device__ __forceinline__ void dia_phase_and_transition(ScalV<V>& z, V a_old, V
   const V t = vmul(splat<V>(bp.kamp * kP24f), Bc);
   V num = vmul(splat<V>(bp.amp * kP24f), Bc);
   typename Lanes<V>::U iden;
-  bool hop1[W], hop2[W];
+  bool hop1[W], hop2[W], hop[W];
 #pragma unroll
   for (int l = 0; l < W; ++l) {
     const uint32_t T = min(__float2uint_rz(fabsf(ln(t, l))), bp.tmax >> 1);
     const uint32_t y = ln(word, l) >> 8;
     hop1[l] = y < T;
-    const bool hop = y < 2u * T;
-    hop2[l] = hop && !hop1[l];
-    ln(num, l) = hop ? ln(num, l) : kP24f;
-    ln(iden, l) = hop ? T : 16777216u - 2u * T;
+    hop[l] = y < 2u * T;
+    hop2[l] = hop[l] && !hop1[l];
+    ln(num, l) = hop[l] ? ln(num, l) : kP24f;
+    ln(iden, l) = hop[l] ? T : 16777216u - 2u * T;
   }
-  weight_factor(z, num, iden);
+  weight_factor<false>(z, num, iden);  // (range: as in phase_and_transition)
+#pragma unroll
+  for (int l = 0; l < W; ++l)
+    if (hop[l]) weight_range(z, l);
   const V nsa = vmul(z.sa, splat<V>(-1.0f)), nsb = vmul(z.sb, splat<V>(-1.0f));
 #pragma unroll
   for (int l = 0; l < W; ++l) {
@@ -357,12 +374,15 @@ __device__ __forceinline__ void dia_phase_and_transition(ScalV<V>& z, V a_old, V
   }
 }
 
-// Renormalises the weight and phase pairs; called at the end of every Philox
-// block (absolute steps 4k + 3), whatever the chunking.
+// Renormalises the weight and phase pairs and checks the weight's range;
+// called at the end of every Philox block (absolute steps 4k + 3), whatever
+// the chunking.
 template <typename V>
 __device__ __forceinline__ void block_end(ScalV<V>& z) {
   z.m = fast_two_sum_v(z.m.hi, z.m.lo);
   z.ph = two_sum_v(z.ph.hi, z.ph.lo);
+#pragma unroll
+  for (int l = 0; l < Lanes<V>::W; ++l) weight_range(z, l);
 }
 
 // FP32 initial sample of one walker with random-stream id `traj` from the same
@@ -465,7 +485,7 @@ __device__ __forceinline__ bool spawn_transition(Scal& z, float w_old, float Av,
     fac = (bp.amp * kP24f) * Bv;
   } else {
     z.ph.lo = __fmaf_rn(bp.hdt_hbar * (z.sa - z.sb), w_old + z.r, z.ph.lo);
-    const bool degen = z.r2 < 0.25f * kDegTol32 * kDegTol32;
+    const bool degen = z.r2 < kDegR2_32;
     deg += degen ? 1u : 0u;
     const float gn = (KIND == 1) ? 0.5f * (z.A * Bv - z.B * Av) : (-0.5f * bp.b0) * Av;
     const float g = degen ? 0.0f : gn * (z.ir * z.ir);

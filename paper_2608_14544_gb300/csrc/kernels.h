@@ -62,8 +62,24 @@ struct BulkParams {
 // The model-dependent scalars of a bulk launch for time step dt (every caller
 // fills them here, so the single-request, packed and no-allocation routes see
 // the same values).
+// FP32 degeneracy test of the adiabatic two-state kernels: the coupling is set
+// to zero where r^2 < kDegR2_32 (2r = e_b - e_a below kDegTol32).
+constexpr float kDegTol32 = 1e-6f;
+constexpr float kDegR2_32 = 0.25f * kDegTol32 * kDegTol32;
+
+// Kernel form of a two-state model in the FP32-bulk kernels: 0 (only a(R)
+// depends on R, b = b0) or 1 (general).  In the adiabatic representation the
+// spin-boson form is used only when b0^2 alone keeps r^2 = a^2 + b0^2 at or
+// above the degeneracy threshold, so that its kernels need no degeneracy
+// test; a spin-boson model with |b0| that small runs the general form.
+inline int bulk_kind(const DevModel& h) {
+  if (h.kind != 0 || h.repr == QCL_REPR_DIABATIC) return h.kind;
+  const float b0 = (float)h.b0;
+  return b0 * b0 >= kDegR2_32 ? 0 : 1;
+}
+
 inline void bulk_model_scalars(BulkParams& bp, const DevModel& h, double dt) {
-  bp.kind = h.kind;
+  bp.kind = bulk_kind(h);
   bp.repr = h.repr;
   bp.a0 = (float)h.a0;
   bp.b0 = (float)h.b0;

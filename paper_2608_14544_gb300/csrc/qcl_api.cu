@@ -649,7 +649,7 @@ qcl_status qcl_autotune(qcl_model* model, int64_t probe_walkers, int64_t n_steps
   float best_ms = -1.0f;
   int best_wpt = 1, best_bps = 0;
   for (int wpt = 1; wpt <= wmax; ++wpt) {
-    int limit = two_state_reg ? bulk2_blocks_per_sm(n, model->host.kind, model->host.repr, wpt) : 4;
+    int limit = two_state_reg ? bulk2_blocks_per_sm(n, bulk_kind(model->host), model->host.repr, wpt) : 4;
     if (limit < 1) limit = 1;
     for (int bps = 1; bps <= limit; ++bps) {
       model->shape_wpt = wpt;

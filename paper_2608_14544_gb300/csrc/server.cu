@@ -295,7 +295,7 @@ void run_round(qcl_server* s) {
     const Chunk c = plan(*r, s->d.quantum_steps);
     items.push_back({r, c});
     if (r->bucket < 0) continue;
-    PackedTable* T = htab(s, r->model->host.kind, r->bucket);
+    PackedTable* T = htab(s, bulk_kind(r->model->host), r->bucket);
     if (T->n_req >= kMaxPacked) {  // table full: this request runs its own launch
       r->bucket = -2;
       continue;
