@@ -242,9 +242,10 @@ __device__ __forceinline__ void weight_range(ScalV<V>& z, int l) {
 
 // m *= num / den (den an integer below 2^25, so exact in FP32) as a
 // compensated quotient: rcp.approx, one exact FMA residual, and the product
-// with the error terms collected in lo.  CHECK = false leaves the range check
-// (weight_range) to the caller.
-template <bool CHECK = true, typename V>
+// with the error terms collected in lo, then the range check.  (Checking only
+// after hops and at block ends measured slower: the branch costs more than
+// the two compares it saves.)
+template <typename V>
 __device__ __forceinline__ void weight_factor(ScalV<V>& z, V num, const typename Lanes<V>::U& iden) {
   V den, rd;
 #pragma unroll
@@ -259,10 +260,8 @@ __device__ __forceinline__ void weight_factor(ScalV<V>& z, V num, const typename
   V e = vfma(z.m.hi, q0, vmul(p, splat<V>(-1.0f)));
   e = vfma(z.m.hi, q1, e);
   z.m = {p, vfma(z.m.lo, q0, e)};
-  if (CHECK) {
 #pragma unroll
-    for (int l = 0; l < Lanes<V>::W; ++l) weight_range(z, l);
-  }
+  for (int l = 0; l < Lanes<V>::W; ++l) weight_range(z, l);
 }
 
 // Phase (trapezoid) and transition of one step, given the decomposition at
@@ -325,14 +324,8 @@ __device__ __forceinline__ void phase_and_transition(ScalV<V>& z, V r_old, V Av,
     ln(z.sa, l) = hop1[l] ? ln(nsa, l) : ln(z.sa, l);
     ln(z.sb, l) = hop2[l] ? ln(nsb, l) : ln(z.sb, l);
   }
-  // (sigmas flipped after the weight factor has taken the pre-hop sigma in sel).
-  // A stay multiplies the weight by at most 1 / (1 - p_max) per step, so its
-  // range is checked at the end of the Philox block; a hop's factor is checked
-  // at once.
-  weight_factor<false>(z, num, iden);
-#pragma unroll
-  for (int l = 0; l < W; ++l)
-    if (hop[l]) weight_range(z, l);
+  // (sigmas flipped after the weight factor has taken the pre-hop sigma in sel)
+  weight_factor(z, num, iden);
 }
 
 // Diabatic representation: phase with hbar w_ab = V_aa - V_bb = -(sig_a - sig_b)
@@ -361,10 +354,7 @@ __device__ __forceinline__ void dia_phase_and_transition(ScalV<V>& z, V a_old, V
     ln(num, l) = hop[l] ? ln(num, l) : kP24f;
     ln(iden, l) = hop[l] ? T : 16777216u - 2u * T;
   }
-  weight_factor<false>(z, num, iden);  // (range: as in phase_and_transition)
-#pragma unroll
-  for (int l = 0; l < W; ++l)
-    if (hop[l]) weight_range(z, l);
+  weight_factor(z, num, iden);
   const V nsa = vmul(z.sa, splat<V>(-1.0f)), nsb = vmul(z.sb, splat<V>(-1.0f));
 #pragma unroll
   for (int l = 0; l < W; ++l) {
@@ -374,29 +364,25 @@ __device__ __forceinline__ void dia_phase_and_transition(ScalV<V>& z, V a_old, V
   }
 }
 
-// Renormalises the weight and phase pairs and checks the weight's range;
-// called at the end of every Philox block (absolute steps 4k + 3), whatever
-// the chunking.
+// Renormalises the weight and phase pairs; called at the end of every Philox
+// block (absolute steps 4k + 3), whatever the chunking.
 template <typename V>
 __device__ __forceinline__ void block_end(ScalV<V>& z) {
   z.m = fast_two_sum_v(z.m.hi, z.m.lo);
   z.ph = two_sum_v(z.ph.hi, z.ph.lo);
-#pragma unroll
-  for (int l = 0; l < Lanes<V>::W; ++l) weight_range(z, l);
 }
 
 // FP32 initial sample of one walker with random-stream id `traj` from the same
 // Philox words as the FP64 path: (R, P) at Rg[j * stride], Pg[j * stride], the
 // weight mantissa mh (low part, exponent and phase start at 0) and the index
-// pair word ab.
-__device__ __forceinline__ void sample_walker_f32(const DevModel* __restrict__ M,
-                                                  const SampleParams& sp, uint64_t traj,
-                                                  float* Rg, float* Pg, int64_t stride, float& mh,
+// pair word ab.  All arithmetic in FP32 (inputs converted on the host).
+__device__ __forceinline__ void sample_walker_f32(const Sample32& sp, uint64_t traj, float* Rg,
+                                                  float* Pg, int64_t stride, float& mh,
                                                   uint16_t& ab) {
   const int n = sp.n;
-  float a = (float)M->a0, b = (float)M->b0;
+  float a = sp.a0, b = sp.b0;
   for (int j = 0; j < n; ++j) {
-    float R = (float)sp.R0[j], P = (float)sp.P0[j];
+    float R = sp.R0[j], P = sp.P0[j];
     if (sp.wigner) {
       const u4 wd = philox_draw(sp.seed, (uint32_t)j, traj, kPurposeInit);
       const float u0 = __fmaf_rn(__uint2float_rn(wd.x), 0x1p-32f, 0x1p-33f);
@@ -404,13 +390,13 @@ __device__ __forceinline__ void sample_walker_f32(const DevModel* __restrict__ M
       const float rad = sqrtf(-2.0f * logf(u0));
       float sn, cs;
       sincospif(2.0f * u1, &sn, &cs);
-      R = __fmaf_rn((float)sp.sR[j] * rad, cs, R);
-      P = __fmaf_rn((float)sp.sP[j] * rad, sn, P);
+      R = __fmaf_rn(sp.sR[j] * rad, cs, R);
+      P = __fmaf_rn(sp.sP[j] * rad, sn, P);
     }
     Rg[(int64_t)j * stride] = R;
     Pg[(int64_t)j * stride] = P;
-    a = __fmaf_rn((float)M->a[j], R, a);
-    b = __fmaf_rn((float)M->b[j], R, b);
+    a = __fmaf_rn(sp.a[j], R, a);
+    b = __fmaf_rn(sp.b[j], R, b);
   }
   const float r2 = a * a + b * b;
   float c = 1.0f, s = 0.0f;
@@ -426,32 +412,36 @@ __device__ __forceinline__ void sample_walker_f32(const DevModel* __restrict__ M
     }
   }
   const float U[4] = {-s, c, c, s};
-  double rho_ad[4];  // the density in the walkers' representation
-  double tot = 0.0;
+  float rho_ad[4];  // the density in the walkers' representation
+  float tot = 0.0f;
   for (int al = 0; al < 2; ++al)
     for (int be = 0; be < 2; ++be) {
       float acc = 0.0f;
-      if (M->repr == QCL_REPR_DIABATIC) {
-        acc = (float)sp.rho[al * 2 + be];
+      if (sp.repr == QCL_REPR_DIABATIC) {
+        acc = sp.rho[al * 2 + be];
       } else {
         for (int k = 0; k < 2; ++k)
           for (int l = 0; l < 2; ++l)
-            acc = __fmaf_rn(U[k * 2 + al] * (float)sp.rho[k * 2 + l], U[l * 2 + be], acc);
+            acc = __fmaf_rn(U[k * 2 + al] * sp.rho[k * 2 + l], U[l * 2 + be], acc);
       }
       rho_ad[al * 2 + be] = acc;
       tot += fabsf(acc);
     }
   // index pair from |rho_ad| with 2^-24 quantised probabilities (remainder to the
-  // last nonzero pair), m0 = rho_ad / p_hat
+  // last nonzero pair), m0 = rho_ad / p_hat.  FP32 rounding of the quotients can
+  // make the floors sum past 2^24 by a few units; the excess then comes off the
+  // largest threshold.
   uint32_t Tk[4];
   uint32_t sumT = 0;
-  int last = 0;
+  int last = 0, big = 0;
   for (int k = 0; k < 4; ++k) {
-    Tk[k] = (uint32_t)floorf((float)(fabs(rho_ad[k]) / tot) * kP24f);
+    Tk[k] = (uint32_t)floorf(__fdiv_rn(fabsf(rho_ad[k]), tot) * kP24f);
     sumT += Tk[k];
-    if (rho_ad[k] != 0.0) last = k;
+    if (rho_ad[k] != 0.0f) last = k;
+    if (Tk[k] > Tk[big]) big = k;
   }
-  Tk[last] += 16777216u - sumT;
+  if (sumT <= 16777216u) Tk[last] += 16777216u - sumT;
+  else Tk[big] -= sumT - 16777216u;
   const u4 wd = philox_draw(sp.seed, (uint32_t)n, traj, kPurposeInit);
   const uint32_t y = wd.x >> 8;
   uint32_t cum = 0;
@@ -463,7 +453,7 @@ __device__ __forceinline__ void sample_walker_f32(const DevModel* __restrict__ M
       break;
     }
   }
-  mh = (float)rho_ad[pick] * (kP24f / (float)Tk[pick]);
+  mh = rho_ad[pick] * (kP24f / (float)Tk[pick]);
   ab = (uint16_t)((pick >> 1) | ((pick & 1) << 8));
 }
 

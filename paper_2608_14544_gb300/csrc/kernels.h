@@ -20,6 +20,40 @@ struct SampleParams {
   double rho[kMaxNS * kMaxNS];
 };
 
+// The two-state FP32 sampler's inputs, converted to FP32 once on the host
+// (make_sample32), so that the sampler does no FP64 arithmetic.
+struct Sample32 {
+  int64_t n_traj;
+  uint64_t traj_offset;
+  uint64_t seed;
+  int32_t n, wigner, repr, pad;
+  float a0, b0;
+  float rho[4];
+  float R0[kMaxN], P0[kMaxN], sR[kMaxN], sP[kMaxN], a[kMaxN], b[kMaxN];
+};
+
+inline void make_sample32(const DevModel& h, const SampleParams& sp, Sample32& s) {
+  s.n_traj = sp.n_traj;
+  s.traj_offset = sp.traj_offset;
+  s.seed = sp.seed;
+  s.n = sp.n;
+  s.wigner = sp.wigner;
+  s.repr = h.repr;
+  s.pad = 0;
+  s.a0 = (float)h.a0;
+  s.b0 = (float)h.b0;
+  for (int k = 0; k < 4; ++k) s.rho[k] = (float)sp.rho[k];
+  for (int j = 0; j < kMaxN; ++j) {
+    const bool on = j < sp.n;
+    s.R0[j] = on ? (float)sp.R0[j] : 0.0f;
+    s.P0[j] = on ? (float)sp.P0[j] : 0.0f;
+    s.sR[j] = on ? (float)sp.sR[j] : 0.0f;
+    s.sP[j] = on ? (float)sp.sP[j] : 0.0f;
+    s.a[j] = on ? (float)h.a[j] : 0.0f;
+    s.b[j] = on ? (float)h.b[j] : 0.0f;
+  }
+}
+
 // FP32 per-mode coefficients of a two-state model for one time step dt.
 struct Coef2 {
   float hk[kMaxN];   // dt/2 * k_j
@@ -226,7 +260,7 @@ void launch_spawn_fstart(const void* buf, int64_t capacity, int n, int64_t n0, i
                          cudaStream_t st);
 // FP32-bulk spawning (two states, n <= 32 modes): sample, one step (step
 // kernel, scan, scatter), family observation.
-void launch_spawn_sample32(const DevModel* dm, const SampleParams& sp, int64_t capacity, void* buf,
+void launch_spawn_sample32(const DevModel& host, const SampleParams& sp, int64_t capacity, void* buf,
                            cudaStream_t st);
 int launch_spawn_step32(const BulkParams& bp, const Coef2& cf, void* buf, int64_t capacity,
                         int64_t n0, int64_t step0, int64_t step, cudaStream_t st);
@@ -254,7 +288,7 @@ struct LaunchShape {
 inline int max_wpt(int n) { return n <= 8 ? 2 : 1; }
 inline int default_wpt(int n) { return n <= 4 ? 2 : 1; }
 
-void launch_sample_f32(const DevModel* dm, const SampleParams& sp, void* buf, cudaStream_t st);
+void launch_sample_f32(const DevModel& host, const SampleParams& sp, void* buf, cudaStream_t st);
 // Returns the persistent grid size used (0 on launch failure).
 int launch_bulk2(const BulkParams& bp, const Coef2& cf, void* buf, double* part,
                  const LaunchShape& ls, cudaStream_t st);

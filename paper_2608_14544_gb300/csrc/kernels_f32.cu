@@ -13,8 +13,7 @@ namespace qcl {
 
 // ---------------------------------------------------------------- sampling --
 // FP32 initial sample from the same Philox words as the FP64 path.
-__global__ void __launch_bounds__(256) k_sample_f32(const DevModel* __restrict__ M,
-                                                    SampleParams sp, void* buf) {
+__global__ void __launch_bounds__(256) k_sample_f32(const Sample32 sp, void* buf) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const int64_t nt = sp.n_traj;
   const int n = sp.n;
@@ -33,7 +32,7 @@ __global__ void __launch_bounds__(256) k_sample_f32(const DevModel* __restrict__
   if (i >= nt) return;
   float mh;
   uint16_t ab;
-  sample_walker_f32(M, sp, sp.traj_offset + (uint64_t)i, w.R + i, w.P + i, nt, mh, ab);
+  sample_walker_f32(sp, sp.traj_offset + (uint64_t)i, w.R + i, w.P + i, nt, mh, ab);
   w.mh[i] = mh;
   w.ml[i] = 0.0f;
   w.me[i] = 0;
@@ -283,9 +282,11 @@ int64_t launches_read(bool reset) {
   return reset ? g_launches.exchange(0) : g_launches.load();
 }
 
-void launch_sample_f32(const DevModel* dm, const SampleParams& sp, void* buf, cudaStream_t st) {
+void launch_sample_f32(const DevModel& host, const SampleParams& sp, void* buf, cudaStream_t st) {
   const int64_t nb = (sp.n_traj + 255) / 256;
-  k_sample_f32<<<(unsigned)(nb > 0 ? nb : 1), 256, 0, st>>>(dm, sp, buf);
+  Sample32 s32;
+  make_sample32(host, sp, s32);
+  k_sample_f32<<<(unsigned)(nb > 0 ? nb : 1), 256, 0, st>>>(s32, buf);
   launches_add(1);
 }
 

@@ -361,7 +361,7 @@ qcl_status qcl_sample_initial(const qcl_model* model, const qcl_ensemble_desc* e
   else if (ens->precision == QCL_PREC_FP64)
     launch_sample_f64(model->dev, *sp, ens_buf, s);
   else
-    launch_sample_f32(model->dev, *sp, ens_buf, s);
+    launch_sample_f32(model->host, *sp, ens_buf, s);
   delete sp;
   st = check_launch("sample");
   return st ? st : ok();
@@ -752,7 +752,7 @@ qcl_status qcl_spawn_sample(const qcl_model* model, const qcl_ensemble_desc* ens
   st = prepare_sample(model, ens, init, &sp);
   if (st) return st;
   if (ens->precision == QCL_PREC_FP32_BULK)
-    launch_spawn_sample32(model->dev, *sp, capacity, buf, (cudaStream_t)stream);
+    launch_spawn_sample32(model->host, *sp, capacity, buf, (cudaStream_t)stream);
   else
     launch_spawn_sample(model->dev, *sp, capacity, buf, (cudaStream_t)stream);
   delete sp;

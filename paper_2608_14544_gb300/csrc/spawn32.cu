@@ -43,8 +43,7 @@ __device__ __forceinline__ uint64_t child_id32(uint64_t seed, int64_t step, uint
   return (((uint64_t)w.y << 32) | w.x) | (1ull << 63);
 }
 
-__global__ void __launch_bounds__(256) k_spawn_sample32(const DevModel* __restrict__ M,
-                                                        SampleParams sp, int64_t cap, void* buf) {
+__global__ void __launch_bounds__(256) k_spawn_sample32(const Sample32 sp, int64_t cap, void* buf) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const int64_t n0 = sp.n_traj;
   const SpawnLayout L = SpawnLayout::make(cap, sp.n, n0, QCL_PREC_FP32_BULK);
@@ -71,7 +70,7 @@ __global__ void __launch_bounds__(256) k_spawn_sample32(const DevModel* __restri
   const uint64_t traj = sp.traj_offset + (uint64_t)i;
   float mh;
   uint16_t ab;
-  sample_walker_f32(M, sp, traj, w.R + i, w.P + i, cap, mh, ab);
+  sample_walker_f32(sp, traj, w.R + i, w.P + i, cap, mh, ab);
   w.mh[i] = mh;
   w.ml[i] = 0.0f;
   w.me[i] = 0;
@@ -353,10 +352,12 @@ int dispatch_step32(const BulkParams& bp, const Coef2& cf, void* buf, int64_t ca
 
 }  // namespace
 
-void launch_spawn_sample32(const DevModel* dm, const SampleParams& sp, int64_t capacity, void* buf,
+void launch_spawn_sample32(const DevModel& host, const SampleParams& sp, int64_t capacity, void* buf,
                            cudaStream_t st) {
   const int64_t nb = (sp.n_traj + 255) / 256;
-  k_spawn_sample32<<<(unsigned)(nb > 0 ? nb : 1), 256, 0, st>>>(dm, sp, capacity, buf);
+  Sample32 s32;
+  make_sample32(host, sp, s32);
+  k_spawn_sample32<<<(unsigned)(nb > 0 ? nb : 1), 256, 0, st>>>(s32, capacity, buf);
   launches_add(1);
 }
 
