@@ -295,9 +295,11 @@ qcl_status qcl_measure_peak(int32_t which, double* flops_per_s, void* stream);
  * same whatever the shape):
  *   walkers_per_thread  1 or 2 (0 = default: 2 for two-state models of at most
  *                       4 modes, else 1).  With 2 a thread advances one walker
- *                       of each of two consecutive tiles, interleaving their
- *                       independent dependency chains; two-state models of at
- *                       most 8 modes, otherwise 1 is used.
+ *                       of each of two consecutive tiles as the two lanes of
+ *                       packed FP32x2 instructions; two-state models of at
+ *                       most 8 modes, otherwise 1 is used.  A launch whose
+ *                       tiles do not outnumber the resident block slots also
+ *                       runs 1, so that every slot gets a tile.
  *   blocks_per_sm       resident blocks per SM of the persistent grid (0 = the
  *                       kernel's occupancy limit; larger values are clamped).
  * Threads per block are fixed at 256: the block is the reduction tile, whose

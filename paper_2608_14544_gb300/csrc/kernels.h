@@ -300,6 +300,11 @@ int launch_bulk2_dia(const BulkParams& bp, const Coef2& cf, void* buf, double* p
 // capped by ls.grid_cap and by the tile count; per_sm / n_sm cache the
 // occupancy query.
 using BulkFn = void (*)(const BulkParams, const Coef2, void*, double*);
+// Walkers per thread actually launched when two are asked for: 2 only if the
+// tiles outnumber the resident block slots of the two-walker kernel fn2 (at
+// ls.blocks_per_sm and ls.grid_cap); a smaller ensemble runs one walker per
+// thread so that every slot gets a tile.  Results do not depend on it.
+int bulk_wpt(BulkFn fn2, int& per_sm, int& n_sm, int64_t n_tiles, const LaunchShape& ls);
 int run_bulk_kernel(BulkFn fn, int& per_sm, int& n_sm, const BulkParams& bp, const Coef2& cf,
                     void* buf, double* part, const LaunchShape& ls, int wpt, cudaStream_t st);
 // Occupancy limit (resident blocks per SM) of the two-state bulk kernel that

@@ -34,7 +34,8 @@ template <int NPL, int KIND>
 int run_dia(const BulkParams& bp, const Coef2& cf, void* buf, double* part, const LaunchShape& ls,
             cudaStream_t st) {
   static int per_sm[2] = {-1, -1}, n_sm[2] = {0, 0};
-  const int wpt = (ls.wpt > 0 ? ls.wpt : default_wpt(NPL)) >= 2 && NPL <= 8 ? 2 : 1;
+  int wpt = (ls.wpt > 0 ? ls.wpt : default_wpt(NPL)) >= 2 && NPL <= 8 ? 2 : 1;
+  if (wpt == 2) wpt = bulk_wpt(dia_fn<NPL, KIND, 2>(), per_sm[1], n_sm[1], bp.n_tiles, ls);
   if (wpt == 2)
     return run_bulk_kernel(dia_fn<NPL, KIND, 2>(), per_sm[1], n_sm[1], bp, cf, buf, part, ls, 2, st);
   return run_bulk_kernel(dia_fn<NPL, KIND, 1>(), per_sm[0], n_sm[0], bp, cf, buf, part, ls, 1, st);

@@ -303,6 +303,14 @@ void occupancy(BulkFn fn, int& per_sm, int& n_sm) {
 }
 }  // namespace
 
+int bulk_wpt(BulkFn fn2, int& per_sm, int& n_sm, int64_t n_tiles, const LaunchShape& ls) {
+  occupancy(fn2, per_sm, n_sm);
+  const int bps = (ls.blocks_per_sm > 0 && ls.blocks_per_sm < per_sm) ? ls.blocks_per_sm : per_sm;
+  int64_t slots = (int64_t)bps * n_sm;
+  if (ls.grid_cap > 0 && slots > ls.grid_cap) slots = ls.grid_cap;
+  return n_tiles > slots ? 2 : 1;
+}
+
 int run_bulk_kernel(BulkFn fn, int& per_sm, int& n_sm, const BulkParams& bp, const Coef2& cf,
                     void* buf, double* part, const LaunchShape& ls, int wpt, cudaStream_t st) {
   occupancy(fn, per_sm, n_sm);
@@ -333,7 +341,8 @@ template <int NPL, int KIND>
 int run_bulk(const BulkParams& bp, const Coef2& cf, void* buf, double* part, const LaunchShape& ls,
              cudaStream_t st) {
   static int per_sm[2] = {-1, -1}, n_sm[2] = {0, 0};
-  const int wpt = (ls.wpt > 0 ? ls.wpt : default_wpt(NPL)) >= 2 && NPL <= 8 ? 2 : 1;
+  int wpt = (ls.wpt > 0 ? ls.wpt : default_wpt(NPL)) >= 2 && NPL <= 8 ? 2 : 1;
+  if (wpt == 2) wpt = bulk_wpt(bulk_fn<NPL, KIND, 2>(), per_sm[1], n_sm[1], bp.n_tiles, ls);
   if (wpt == 2)
     return run_bulk_kernel(bulk_fn<NPL, KIND, 2>(), per_sm[1], n_sm[1], bp, cf, buf, part, ls, 2, st);
   return run_bulk_kernel(bulk_fn<NPL, KIND, 1>(), per_sm[0], n_sm[0], bp, cf, buf, part, ls, 1, st);

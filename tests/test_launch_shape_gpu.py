@@ -35,7 +35,9 @@ def _cases():
 
 @pytest.mark.parametrize("name,cfg", _cases())
 def test_every_launch_shape_gives_the_same_bits(q, name, cfg):
-    n, steps, stride = 70_001, 120, 10
+    # 586 tiles: more than the resident block slots at every shape, so that
+    # walkers-per-thread 2 is launched as asked (smaller ensembles run 1)
+    n, steps, stride = 150_001, 120, 10
     outs = []
     for wpt, bps in ((1, 0), (2, 0), (1, 1), (2, 1), (0, 2), (0, 0)):
         m = q.Model(cfg["model"])
