@@ -54,6 +54,21 @@ inline void make_sample32(const DevModel& h, const SampleParams& sp, Sample32& s
   }
 }
 
+// The N_s-state FP32 sampler's inputs, converted to FP32 once on the host:
+// E (N_s x N_s), K_j (N_s x N_s each, j < n; n N_s^2 <= kSampleNK, which the
+// FP32-bulk mode limits guarantee) and the initial density.
+constexpr int kSampleNK = 512;
+struct SampleN32 {
+  int64_t n_traj;
+  uint64_t traj_offset;
+  uint64_t seed;
+  int32_t n, ns, wigner, pad;
+  float R0[kMaxN], P0[kMaxN], sR[kMaxN], sP[kMaxN];
+  float E[kMaxNS * kMaxNS];
+  float rho[kMaxNS * kMaxNS];
+  float K[kSampleNK];
+};
+
 // FP32 per-mode coefficients of a two-state model for one time step dt.
 struct Coef2 {
   float hk[kMaxN];   // dt/2 * k_j
@@ -313,8 +328,9 @@ int bulk2_blocks_per_sm(int n, int kind, int repr, int wpt);
 // Kernel-selection description of the bulk kernel chosen for (n, kind).
 const char* bulk2_variant(int n, int kind);
 
-void launch_sampleN(const DevModel* dm, const SampleParams& sp, void* buf, int precision,
-                    cudaStream_t st);
+// N_s-state initial sample: FP64 (dm, sp) or FP32 bulk (s32).
+void launch_sampleN(const DevModel* dm, const SampleParams& sp, const SampleN32* s32, void* buf,
+                    int precision, cudaStream_t st);
 void launch_stepN_f64(const DevModel* dm, int ns, void* buf, int64_t nt, int n, int64_t step0,
                       int64_t step, double dt, uint64_t seed, uint64_t traj_off, cudaStream_t st);
 void launch_observeN_f64(int ns, const void* buf, int64_t nt, int n, double* part,

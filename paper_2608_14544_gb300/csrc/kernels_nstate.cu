@@ -6,7 +6,7 @@ namespace qcl {
 
 #define QCL_NS_DECL(k)                                                                        \
   void nstate_sample64_##k(const DevModel*, const SampleParams&, void*, cudaStream_t);        \
-  void nstate_sample32_##k(const DevModel*, const SampleParams&, void*, cudaStream_t);        \
+  void nstate_sample32_##k(const SampleN32&, void*, cudaStream_t);                           \
   void nstate_step64_##k(const DevModel*, void*, int64_t, int, int64_t, int64_t, double,      \
                          uint64_t, uint64_t, cudaStream_t);                                   \
   void nstate_observe64_##k(const void*, int64_t, int, double*, cudaStream_t);                \
@@ -29,12 +29,12 @@ QCL_NS_DECL(8)
     default: break;                        \
   }
 
-void launch_sampleN(const DevModel* dm, const SampleParams& sp, void* buf, int precision,
-                    cudaStream_t st) {
+void launch_sampleN(const DevModel* dm, const SampleParams& sp, const SampleN32* s32, void* buf,
+                    int precision, cudaStream_t st) {
   if (precision == QCL_PREC_FP64) {
     QCL_NS_SWITCH(sp.ns, nstate_sample64, dm, sp, buf, st);
   } else {
-    QCL_NS_SWITCH(sp.ns, nstate_sample32, dm, sp, buf, st);
+    QCL_NS_SWITCH(sp.ns, nstate_sample32, *s32, buf, st);
   }
   launches_add(1);
 }

@@ -3,8 +3,8 @@
 #include "nstate_kernels.cuh"
 
 namespace qcl {
-void nstate_sample32_5(const DevModel* dm, const SampleParams& sp, void* buf, cudaStream_t st) {
-  NStateOps<5>::sample32(dm, sp, buf, st);
+void nstate_sample32_5(const SampleN32& sp, void* buf, cudaStream_t st) {
+  NStateOps<5>::sample32(sp, buf, st);
 }
 void nstate_observe64_5(const void* buf, int64_t nt, int n, double* part, cudaStream_t st) {
   NStateOps<5>::observe64(buf, nt, n, part, st);

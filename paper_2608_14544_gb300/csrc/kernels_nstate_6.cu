@@ -3,8 +3,8 @@
 #include "nstate_kernels.cuh"
 
 namespace qcl {
-void nstate_sample32_6(const DevModel* dm, const SampleParams& sp, void* buf, cudaStream_t st) {
-  NStateOps<6>::sample32(dm, sp, buf, st);
+void nstate_sample32_6(const SampleN32& sp, void* buf, cudaStream_t st) {
+  NStateOps<6>::sample32(sp, buf, st);
 }
 void nstate_observe64_6(const void* buf, int64_t nt, int n, double* part, cudaStream_t st) {
   NStateOps<6>::observe64(buf, nt, n, part, st);

@@ -468,9 +468,11 @@ __global__ void __launch_bounds__(256) k_observeN_f64(const void* buf, int64_t n
 
 // ------------------------------------------------------------ FP32 sampling --
 template <int NS>
-__global__ void __launch_bounds__(128) k_sampleN_f32(const DevModel* __restrict__ M,
-                                                     SampleParams sp, void* buf) {
-  // the FP64 decomposition of the initial sample (once per walker), stored in FP32
+__global__ void __launch_bounds__(128) k_sampleN_f32(const SampleN32 sp, void* buf) {
+  // the initial sample and its decomposition in FP32 (inputs converted on the
+  // host): Jacobi to FP32 convergence, eigenvalues ascending, each
+  // eigenvector's largest-magnitude component positive (the FP64 sampler's
+  // conventions)
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const int64_t nt = sp.n_traj;
   const int n = sp.n;
@@ -488,13 +490,13 @@ __global__ void __launch_bounds__(128) k_sampleN_f32(const DevModel* __restrict_
   }
   if (i >= nt) return;
   const uint64_t traj = sp.traj_offset + (uint64_t)i;
-  double W[NS][NS];
+  float W[NS][NS];
 #pragma unroll
   for (int a = 0; a < NS; ++a)
 #pragma unroll
-    for (int b = 0; b < NS; ++b) W[a][b] = M->E[a * NS + b];
+    for (int b = 0; b < NS; ++b) W[a][b] = sp.E[a * NS + b];
   for (int j = 0; j < n; ++j) {
-    float R = (float)sp.R0[j], P = (float)sp.P0[j];
+    float R = sp.R0[j], P = sp.P0[j];
     if (sp.wigner) {
       const u4 wd = philox_draw(sp.seed, (uint32_t)j, traj, kPurposeInit);
       const float u0 = __fmaf_rn(__uint2float_rn(wd.x), 0x1p-32f, 0x1p-33f);
@@ -502,54 +504,58 @@ __global__ void __launch_bounds__(128) k_sampleN_f32(const DevModel* __restrict_
       const float rad = sqrtf(-2.0f * logf(u0));
       float sn, cs;
       sincospif(2.0f * u1, &sn, &cs);
-      R = __fmaf_rn((float)sp.sR[j] * rad, cs, R);
-      P = __fmaf_rn((float)sp.sP[j] * rad, sn, P);
+      R = __fmaf_rn(sp.sR[j] * rad, cs, R);
+      P = __fmaf_rn(sp.sP[j] * rad, sn, P);
     }
     w.R[(int64_t)j * nt + i] = R;
     w.P[(int64_t)j * nt + i] = P;
-    const double* Kj = M->K + (size_t)j * NS * NS;
+    const float* Kj = sp.K + j * NS * NS;
 #pragma unroll
     for (int a = 0; a < NS; ++a)
 #pragma unroll
-      for (int b = 0; b < NS; ++b) W[a][b] += (double)R * Kj[a * NS + b];
+      for (int b = 0; b < NS; ++b) W[a][b] = __fmaf_rn(R, Kj[a * NS + b], W[a][b]);
   }
-  double e[NS], U[NS][NS];
-  eigh_ns<double, NS>(W, nullptr, e, U, 100, 1e-34);
-  double rho_ad[NS * NS];
+  float e[NS], U[NS][NS];
+  eigh_ns<float, NS>(W, nullptr, e, U, 12, 1e-13f);
+  float rho_ad[NS * NS];
+  float tot = 0.0f;
 #pragma unroll
   for (int al = 0; al < NS; ++al)
 #pragma unroll
     for (int be = 0; be < NS; ++be) {
-      double acc = 0.0;
+      float acc = 0.0f;
 #pragma unroll
       for (int k = 0; k < NS; ++k)
 #pragma unroll
-        for (int l = 0; l < NS; ++l) acc += U[k][al] * sp.rho[k * NS + l] * U[l][be];
+        for (int l = 0; l < NS; ++l) acc = __fmaf_rn(U[k][al] * sp.rho[k * NS + l], U[l][be], acc);
       rho_ad[al * NS + be] = acc;
+      tot += fabsf(acc);
     }
-  double tot = 0.0;
-  for (int k = 0; k < NS * NS; ++k) tot += fabs(rho_ad[k]);
+  // thresholds as in the two-state FP32 sampler: remainder to the last nonzero
+  // pair, an excess from FP32 rounding off the largest threshold
   uint32_t Tk[NS * NS];
-  uint64_t sumT = 0;
-  int last = 0;
+  uint32_t sumT = 0;
+  int last = 0, big = 0;
   for (int k = 0; k < NS * NS; ++k) {
-    Tk[k] = (uint32_t)floor(fabs(rho_ad[k]) / tot * kP24);
+    Tk[k] = (uint32_t)floorf(__fdiv_rn(fabsf(rho_ad[k]), tot) * kP24f);
     sumT += Tk[k];
-    if (rho_ad[k] != 0.0) last = k;
+    if (rho_ad[k] != 0.0f) last = k;
+    if (Tk[k] > Tk[big]) big = k;
   }
-  Tk[last] += (uint32_t)(16777216ull - sumT);
+  if (sumT <= 16777216u) Tk[last] += 16777216u - sumT;
+  else Tk[big] -= sumT - 16777216u;
   const u4 wd = philox_draw(sp.seed, (uint32_t)n, traj, kPurposeInit);
   const uint32_t y = wd.x >> 8;
-  uint64_t cum = 0;
+  uint32_t cum = 0;
   int pickk = last;
   for (int k = 0; k < NS * NS; ++k) {
     cum += Tk[k];
-    if ((uint64_t)y < cum) {
+    if (y < cum) {
       pickk = k;
       break;
     }
   }
-  w.m[i] = (float)(rho_ad[pickk] / ((double)Tk[pickk] / kP24));
+  w.m[i] = rho_ad[pickk] * (kP24f / (float)Tk[pickk]);
   w.mlo[i] = 0.0f;
   w.mexp[i] = 0;
   w.phi[i] = 0.0f;
@@ -558,9 +564,9 @@ __global__ void __launch_bounds__(128) k_sampleN_f32(const DevModel* __restrict_
 #pragma unroll
   for (int a = 0; a < NS; ++a)
 #pragma unroll
-    for (int b = 0; b < NS; ++b) w.U[(int64_t)(a * NS + b) * nt + i] = (float)U[a][b];
+    for (int b = 0; b < NS; ++b) w.U[(int64_t)(a * NS + b) * nt + i] = U[a][b];
 #pragma unroll
-  for (int a = 0; a < NS; ++a) w.E[(int64_t)a * nt + i] = (float)e[a];
+  for (int a = 0; a < NS; ++a) w.E[(int64_t)a * nt + i] = e[a];
 }
 
 // ------------------------------------------------------- FP32-bulk kernel --
@@ -855,9 +861,9 @@ struct NStateOps {
     const int64_t nb = (sp.n_traj + 127) / 128;
     k_sampleN_f64<NS><<<(unsigned)(nb > 0 ? nb : 1), 128, 0, st>>>(dm, sp, buf);
   }
-  static void sample32(const DevModel* dm, const SampleParams& sp, void* buf, cudaStream_t st) {
+  static void sample32(const SampleN32& sp, void* buf, cudaStream_t st) {
     const int64_t nb = (sp.n_traj + 127) / 128;
-    k_sampleN_f32<NS><<<(unsigned)(nb > 0 ? nb : 1), 128, 0, st>>>(dm, sp, buf);
+    k_sampleN_f32<NS><<<(unsigned)(nb > 0 ? nb : 1), 128, 0, st>>>(sp, buf);
   }
   static void step64(const DevModel* dm, void* buf, int64_t nt, int n, int64_t step0,
                      int64_t step, double dt, uint64_t seed, uint64_t traj_off, cudaStream_t st) {
@@ -890,7 +896,12 @@ struct NStateOps {
   static int bulk(const BulkParams& bp, const CoefN& cf, void* buf, double* part, int grid_cap,
                   cudaStream_t st) {
     // up to 8 modes for any N_s; up to 32 modes for N_s <= 4 (larger N_s x modes
-    // would not fit a walker in registers)
+    // would not fit a walker in registers).  For N_s <= 5 models of at most 4 or
+    // 6 modes get their own instantiations, which skip the padding modes'
+    // arithmetic (the results are the same: padding modes have zero
+    // coefficients and stay at zero)
+    if (NS <= 5 && bp.n <= 4) return bulk_npl<4>(bp, cf, buf, part, grid_cap, st);
+    if (NS <= 5 && bp.n <= 6) return bulk_npl<6>(bp, cf, buf, part, grid_cap, st);
     if (bp.n <= 8) return bulk_npl<8>(bp, cf, buf, part, grid_cap, st);
     if (NS <= 4 && bp.n <= 32) return bulk_npl<(NS <= 4 ? 32 : 8)>(bp, cf, buf, part, grid_cap, st);
     return 0;

@@ -307,6 +307,32 @@ void fill_coef2(const qcl_model* model, double dt, Coef2* cf) {
   }
 }
 
+// FP32 copies of an N_s-state model's E, K and the sampling inputs (the FP32-bulk
+// mode limits keep n N_s^2 within kSampleNK).
+void make_sampleN32(const qcl_model* model, const SampleParams& sp, SampleN32& s) {
+  const int ns = model->ns, n = model->n;
+  s.n_traj = sp.n_traj;
+  s.traj_offset = sp.traj_offset;
+  s.seed = sp.seed;
+  s.n = n;
+  s.ns = ns;
+  s.wigner = sp.wigner;
+  s.pad = 0;
+  for (int j = 0; j < kMaxN; ++j) {
+    const bool on = j < n;
+    s.R0[j] = on ? (float)sp.R0[j] : 0.0f;
+    s.P0[j] = on ? (float)sp.P0[j] : 0.0f;
+    s.sR[j] = on ? (float)sp.sR[j] : 0.0f;
+    s.sP[j] = on ? (float)sp.sP[j] : 0.0f;
+  }
+  for (int k = 0; k < kMaxNS * kMaxNS; ++k) {
+    s.E[k] = k < ns * ns ? (float)model->E[k] : 0.0f;
+    s.rho[k] = k < ns * ns ? (float)sp.rho[k] : 0.0f;
+  }
+  const size_t nk = (size_t)n * ns * ns;
+  for (size_t k = 0; k < (size_t)kSampleNK; ++k) s.K[k] = k < nk ? (float)model->K[k] : 0.0f;
+}
+
 // Validates an initial condition and builds the sampling parameters.
 qcl_status prepare_sample(const qcl_model* model, const qcl_ensemble_desc* ens, const qcl_init_desc* init,
                           SampleParams** out) {
@@ -356,8 +382,23 @@ qcl_status qcl_sample_initial(const qcl_model* model, const qcl_ensemble_desc* e
   if (st) return st;
   const int ns = model->ns;
   cudaStream_t s = (cudaStream_t)stream;
-  if (ns > 2)
-    launch_sampleN(model->dev, *sp, ens_buf, ens->precision, s);
+  if (ns > 2) {
+    SampleN32* s32 = nullptr;
+    if (ens->precision == QCL_PREC_FP32_BULK) {
+      if ((size_t)model->n * ns * ns > (size_t)kSampleNK) {
+        delete sp;
+        return fail(QCL_ERR_UNSUPPORTED, "FP32-bulk sampling takes n_modes * n_states^2 <= %d", kSampleNK);
+      }
+      s32 = new (std::nothrow) SampleN32();
+      if (!s32) {
+        delete sp;
+        return fail(QCL_ERR_OUT_OF_MEMORY, "host allocation failed");
+      }
+      make_sampleN32(model, *sp, *s32);
+    }
+    launch_sampleN(model->dev, *sp, s32, ens_buf, ens->precision, s);
+    delete s32;
+  }
   else if (ens->precision == QCL_PREC_FP64)
     launch_sample_f64(model->dev, *sp, ens_buf, s);
   else
