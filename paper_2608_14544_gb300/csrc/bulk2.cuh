@@ -725,7 +725,7 @@ struct CoefLocal {
 template <int NPL, int KIND, typename CF, bool LEAN, bool DIA = false, int WPT = 1>
 __device__ __forceinline__ void bulk2_tile(const BulkParams& bp, const CF& cf, W32& ws,
                                            double* __restrict__ part, int64_t tile0, int& rb,
-                                           unsigned int& n_deg, double (&red)[2][8][32],
+                                           unsigned int& n_deg, double (*red)[8][32],
                                            float* obs_rows) {
   static_assert(WPT == 1 || WPT == 2, "one or two walkers per thread");
   using V = std::conditional_t<WPT == 2, float2, float>;
@@ -768,21 +768,24 @@ __device__ __forceinline__ void bulk2_tile(const BulkParams& bp, const CF& cf, W
   }
   closed_form(z);
 
-  // observation of walker k into slot `slot` of its tile's partials (8 warps,
-  // then the tile's fixed FP64 tree)
-  auto observe = [&](int k, int slot) {
-    Scal zk = lane_of(z, k);
-    observe_warp<DIA>(zk, active[k], obs_rows, threadIdx.x, warp * 32, lane, red[rb][warp]);
-    set_lane(z, k, zk);
-    __syncthreads();
-    if (threadIdx.x < 32 && tile0 + k < bp.n_tiles)
-      part[((int64_t)slot * bp.n_tiles + tile0 + k) * 32 + threadIdx.x] =
-          tile_tree8(&red[rb][0][0], 32, threadIdx.x);
-    rb ^= 1;
-  };
+  // observation into slot `slot` of the tiles' partials: each warp's column
+  // sums of walker k go to red[WPT rb + k], then (one barrier for all k) warp k
+  // folds tile k's 8 warp rows by the fixed FP64 tree.  red holds 2 WPT
+  // buffers: consecutive observations alternate between two sets, so a set is
+  // rewritten only after the barrier that follows the warps' reads of it.
   auto observe_all = [&](int slot) {
 #pragma unroll
-    for (int k = 0; k < WPT; ++k) observe(k, slot);
+    for (int k = 0; k < WPT; ++k) {
+      Scal zk = lane_of(z, k);
+      observe_warp<DIA>(zk, active[k], obs_rows, threadIdx.x, warp * 32, lane,
+                        red[WPT * rb + k][warp]);
+      set_lane(z, k, zk);
+    }
+    __syncthreads();
+    if (warp < WPT && tile0 + warp < bp.n_tiles)
+      part[((int64_t)slot * bp.n_tiles + tile0 + warp) * 32 + lane] =
+          tile_tree8(&red[WPT * rb + warp][0][0], 32, lane);
+    rb ^= 1;
   };
 
   // one velocity-Verlet step of the walkers with their phase and transition

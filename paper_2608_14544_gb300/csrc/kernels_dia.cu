@@ -9,7 +9,7 @@ namespace qcl {
 template <int NPL, int KIND, int WPT>
 __global__ void __launch_bounds__(256, (WPT == 1 || NPL <= 4) ? 3 : 2)
     k_bulk2_dia(const BulkParams bp, const Coef2 cf, void* buf, double* __restrict__ part) {
-  __shared__ double red[2][8][32];
+  __shared__ double red[2 * WPT][8][32];
   __shared__ __align__(16) float obs_rows[256 * kObsRow];
   W32 ws = view32(buf, bp.n_traj, 2, bp.n);
   if (ws.hdr->step != bp.step0) {

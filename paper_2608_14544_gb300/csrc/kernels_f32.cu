@@ -46,7 +46,7 @@ __global__ void __launch_bounds__(256) k_sample_f32(const Sample32 sp, void* buf
 template <int NPL, int KIND, int WPT = 1>
 __global__ void __launch_bounds__(256, (WPT == 1 || NPL <= 4) ? 3 : 2)
     k_bulk2(const BulkParams bp, const Coef2 cf, void* buf, double* __restrict__ part) {
-  __shared__ double red[2][8][32];      // double-buffered group partials
+  __shared__ double red[2 * WPT][8][32];  // per-warp partials, two sets of WPT
   __shared__ __align__(16) float obs_rows[256 * kObsRow];  // per-walker contributions
   W32 ws = view32(buf, bp.n_traj, 2, bp.n);
   if (ws.hdr->step != bp.step0) {
