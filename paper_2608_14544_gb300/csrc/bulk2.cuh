@@ -611,7 +611,9 @@ __device__ __forceinline__ float4 add4(float4 a, float4 b) {
 // and sums them, and two butterfly exchanges with lanes L ^ 8 and L ^ 16 join
 // the four row groups, leaving lane L with the total of column
 // 4c + 2 (g & 1) + (g >> 1), which it writes, scaled, to red_row[column].
-template <bool DIA>
+// WIDE = false sums the same tree with lane q reading column q by 32-bit loads
+// (for kernels short of registers).
+template <bool DIA, bool WIDE = true>
 __device__ __forceinline__ void observe_warp(Scal& z, bool active, float* obs_rows, int row,
                                              int row0, int lane, double* red_row) {
   renorm(z.m, z.mexp);
@@ -638,19 +640,35 @@ __device__ __forceinline__ void observe_warp(Scal& z, bool active, float* obs_ro
   *reinterpret_cast<float2*>(r + own + 2 * c.k) = make_float2(c.zr, c.zi);
   *reinterpret_cast<float2*>(r + 16 + own + 2 * c.k) = make_float2(c.zr * c.zr, c.zi * c.zi);
   __syncwarp();
-  const int g = lane >> 3, c4 = lane & 7;
-  const float* base = &obs_rows[(row0 + 8 * g) * kObsRow + 4 * c4];
-  float4 s[8];
+  float x;
+  int col;
+  if (WIDE) {
+    const int g = lane >> 3, c4 = lane & 7;
+    const float* base = &obs_rows[(row0 + 8 * g) * kObsRow + 4 * c4];
+    float4 s[8];
 #pragma unroll
-  for (int i = 0; i < 8; ++i) s[i] = *reinterpret_cast<const float4*>(base + i * kObsRow);
-  __syncwarp();
-  const float4 S = add4(add4(add4(s[0], s[1]), add4(s[2], s[3])),
-                        add4(add4(s[4], s[5]), add4(s[6], s[7])));
-  const bool odd = g & 1, hi = g >> 1;
-  const float t0 = (odd ? S.z : S.x) + __shfl_xor_sync(0xffffffffu, odd ? S.x : S.z, 8);
-  const float t1 = (odd ? S.w : S.y) + __shfl_xor_sync(0xffffffffu, odd ? S.y : S.w, 8);
-  const float x = (hi ? t1 : t0) + __shfl_xor_sync(0xffffffffu, hi ? t0 : t1, 16);
-  const int col = 4 * c4 + 2 * (g & 1) + (g >> 1);
+    for (int i = 0; i < 8; ++i) s[i] = *reinterpret_cast<const float4*>(base + i * kObsRow);
+    __syncwarp();
+    const float4 S = add4(add4(add4(s[0], s[1]), add4(s[2], s[3])),
+                          add4(add4(s[4], s[5]), add4(s[6], s[7])));
+    const bool odd = g & 1, hi = g >> 1;
+    const float t0 = (odd ? S.z : S.x) + __shfl_xor_sync(0xffffffffu, odd ? S.x : S.z, 8);
+    const float t1 = (odd ? S.w : S.y) + __shfl_xor_sync(0xffffffffu, odd ? S.y : S.w, 8);
+    x = (hi ? t1 : t0) + __shfl_xor_sync(0xffffffffu, hi ? t0 : t1, 16);
+    col = 4 * c4 + 2 * (g & 1) + (g >> 1);
+  } else {  // the same tree, one column per lane with 32-bit loads (fewer live registers)
+    const float* cl = &obs_rows[row0 * kObsRow + lane];
+    float l1[16];
+#pragma unroll
+    for (int t = 0; t < 16; ++t) l1[t] = cl[(2 * t) * kObsRow] + cl[(2 * t + 1) * kObsRow];
+#pragma unroll
+    for (int w = 8; w >= 1; w >>= 1)
+#pragma unroll
+      for (int t = 0; t < w; ++t) l1[t] = l1[2 * t] + l1[2 * t + 1];
+    __syncwarp();
+    x = l1[0];
+    col = lane;
+  }
   const int ex = (ew < -(1 << 27)) ? 0 : ((col < 16) ? ew : 2 * ew);
   red_row[col] = scaled_double(x, ex);
 }

@@ -146,7 +146,7 @@ __device__ __forceinline__ void split_tiles(const BulkParams& bp, const Coef2& c
 
     auto observe = [&](int slot) {
       if (ROLE == 0) {
-        observe_warp<false>(z, active, obs_rows, wslot, grp * 32, lane, red[rb][grp]);
+        observe_warp<false, false>(z, active, obs_rows, wslot, grp * 32, lane, red[rb][grp]);
       } else {  // the same weight and phase bookkeeping on every role
         renorm(z.m, z.mexp);
         phase_wrap(z);
@@ -193,7 +193,7 @@ __device__ __forceinline__ void split_tiles(const BulkParams& bp, const Coef2& c
         z.A = bp.a0 + A;
         z.B = bp.b0 + B;
       }
-      closed_form(z);
+      closed_form<KIND == 1>(z);
       const float hu2 = hsab * z.c2, hv2 = hsab * z.s2;
       float av = 0.0f, bv = 0.0f;
 #pragma unroll
