@@ -268,22 +268,30 @@ __device__ __forceinline__ void eigh_warm_sym(const float (&W)[NS][NS], const fl
   }
 #pragma unroll
   for (int a = 0; a < NS; ++a) e[a] = A[a][a];
-  // ascending order of (e, columns of V) by a fixed compare network
+  // ascending order of (e, columns of V) by a fixed compare network.  The warm
+  // start keeps the reference's ascending order except where eigenvalues pass
+  // each other, and on sorted input the network swaps nothing, so it runs only
+  // when some walker of the warp is out of order (the same result either way).
+  bool unsorted = false;
 #pragma unroll
-  for (int i = 1; i < NS; ++i)
+  for (int j = 1; j < NS; ++j) unsorted |= e[j] < e[j - 1];
+  if (__any_sync(0xffffffffu, unsorted)) {
 #pragma unroll
-    for (int j = i; j > 0; --j) {
-      const bool sw = e[j] < e[j - 1];
-      const float t0 = e[j], t1 = e[j - 1];
-      e[j] = sw ? t1 : t0;
-      e[j - 1] = sw ? t0 : t1;
+    for (int i = 1; i < NS; ++i)
 #pragma unroll
-      for (int k = 0; k < NS; ++k) {
-        const float u0 = V[k][j], u1 = V[k][j - 1];
-        V[k][j] = sw ? u1 : u0;
-        V[k][j - 1] = sw ? u0 : u1;
+      for (int j = i; j > 0; --j) {
+        const bool sw = e[j] < e[j - 1];
+        const float t0 = e[j], t1 = e[j - 1];
+        e[j] = sw ? t1 : t0;
+        e[j - 1] = sw ? t0 : t1;
+#pragma unroll
+        for (int k = 0; k < NS; ++k) {
+          const float u0 = V[k][j], u1 = V[k][j - 1];
+          V[k][j] = sw ? u1 : u0;
+          V[k][j - 1] = sw ? u0 : u1;
+        }
       }
-    }
+  }
   // U = ref V; eigenvector a follows reference column a: <U_a, ref_a> = V[a][a]
 #pragma unroll
   for (int i = 0; i < NS; ++i)

@@ -122,13 +122,14 @@ __device__ __forceinline__ float quot<float>(float a, float b) {
   return __fdividef(a, b);
 }
 
+// (with columns al, be of U already extracted into ua, ub)
 template <typename T, int NS>
-__device__ __forceinline__ bool event_amplitudes(const T (&G)[NS][NS], const T (&U)[NS][NS],
-                                                 const T (&e)[NS], int al, int be, T dt, T tol,
-                                                 T (&A)[2 * NS], bool (&is_event)[2 * NS]) {
-  T ua[NS], ub[NS], Gua[NS], Gub[NS];
-  column<T, NS>(U, al, ua);
-  column<T, NS>(U, be, ub);
+__device__ __forceinline__ bool event_amplitudes_cols(const T (&G)[NS][NS], const T (&U)[NS][NS],
+                                                      const T (&ua)[NS], const T (&ub)[NS],
+                                                      const T (&e)[NS], int al, int be, T dt,
+                                                      T tol, T (&A)[2 * NS],
+                                                      bool (&is_event)[2 * NS]) {
+  T Gua[NS], Gub[NS];
 #pragma unroll
   for (int k = 0; k < NS; ++k) {
     T s0 = T(0), s1 = T(0);
@@ -161,6 +162,16 @@ __device__ __forceinline__ bool event_amplitudes(const T (&G)[NS][NS], const T (
     }
   }
   return deg;
+}
+
+template <typename T, int NS>
+__device__ __forceinline__ bool event_amplitudes(const T (&G)[NS][NS], const T (&U)[NS][NS],
+                                                 const T (&e)[NS], int al, int be, T dt, T tol,
+                                                 T (&A)[2 * NS], bool (&is_event)[2 * NS]) {
+  T ua[NS], ub[NS];
+  column<T, NS>(U, al, ua);
+  column<T, NS>(U, be, ub);
+  return event_amplitudes_cols<T, NS>(G, U, ua, ub, e, al, be, dt, tol, A, is_event);
 }
 
 }  // namespace nsd
@@ -655,10 +666,8 @@ __global__ void __launch_bounds__(128, NPL <= 8 ? (NS <= 4 ? 4 : (NS == 5 ? 3 : 
 #pragma unroll
     for (int a = 0; a < NS; ++a) e[a] = active ? ws.E[(int64_t)a * nt + ii] : (float)a;
     // dt/2 * (1/2)(u_a u_a^T + u_b u_b^T) folded with the off-diagonal factor 2
-    auto kick = [&]() {
-      float ua[NS], ub[NS];
-      column<float, NS>(U, al, ua);
-      column<float, NS>(U, be, ub);
+    // (ua, ub: columns al, be of U)
+    auto kick = [&](const float (&ua)[NS], const float (&ub)[NS]) {
       float Q[NTRI];
 #pragma unroll
       for (int a = 0; a < NS; ++a)
@@ -730,7 +739,10 @@ __global__ void __launch_bounds__(128, NPL <= 8 ? (NS <= 4 ? 4 : (NS == 5 ? 3 : 
     for (int it = 0; it < bp.len; ++it) {
       const uint32_t word = (widx & 2) ? ((widx & 1) ? wd.w : wd.z) : ((widx & 1) ? wd.y : wd.x);
       const float de0 = pick<float, NS>(e, al) - pick<float, NS>(e, be);
-      kick();  // first half kick at R_n
+      float ua[NS], ub[NS];
+      column<float, NS>(U, al, ua);
+      column<float, NS>(U, be, ub);
+      kick(ua, ub);  // first half kick at R_n
 #pragma unroll
       for (int j = 0; j < NPL; ++j) R[j] = __fmaf_rn(cf.dtm[j], P[j], R[j]);
       {
@@ -742,7 +754,9 @@ __global__ void __launch_bounds__(128, NPL <= 8 ? (NS <= 4 ? 4 : (NS == 5 ? 3 : 
         build_w(W);
         eigh_warm_sym<NS>(W, Uref, e, U);
       }
-      kick();  // second half kick at R_{n+1}
+      column<float, NS>(U, al, ua);  // (the new decomposition's columns, used twice)
+      column<float, NS>(U, be, ub);
+      kick(ua, ub);  // second half kick at R_{n+1}
       const float de1 = pick<float, NS>(e, al) - pick<float, NS>(e, be);
       ph = df_add(ph, bp.hdt_hbar * (de0 + de1));
       // G = sum_j (P_j/M_j) K_j
@@ -765,7 +779,7 @@ __global__ void __launch_bounds__(128, NPL <= 8 ? (NS <= 4 ? 4 : (NS == 5 ? 3 : 
       constexpr int NC = 2 * NS;
       float A[NC];
       bool ev[NC];
-      const bool dg = event_amplitudes<float, NS>(G, U, e, al, be, bp.dt, kDegTolF, A, ev);
+      const bool dg = event_amplitudes_cols<float, NS>(G, U, ua, ub, e, al, be, bp.dt, kDegTolF, A, ev);
       n_deg += (dg && active) ? 1u : 0u;
       uint32_t T[NC], sumT = 0;
 #pragma unroll
@@ -900,8 +914,10 @@ struct NStateOps {
     // 6 modes get their own instantiations, which skip the padding modes'
     // arithmetic (the results are the same: padding modes have zero
     // coefficients and stay at zero)
-    if (NS <= 5 && bp.n <= 4) return bulk_npl<4>(bp, cf, buf, part, grid_cap, st);
-    if (NS <= 5 && bp.n <= 6) return bulk_npl<6>(bp, cf, buf, part, grid_cap, st);
+    if constexpr (NS <= 5) {
+      if (bp.n <= 4) return bulk_npl<4>(bp, cf, buf, part, grid_cap, st);
+      if (bp.n <= 6) return bulk_npl<6>(bp, cf, buf, part, grid_cap, st);
+    }
     if (bp.n <= 8) return bulk_npl<8>(bp, cf, buf, part, grid_cap, st);
     if (NS <= 4 && bp.n <= 32) return bulk_npl<(NS <= 4 ? 32 : 8)>(bp, cf, buf, part, grid_cap, st);
     return 0;
