@@ -68,8 +68,8 @@ def kernel_source_hash(paths) -> str:
 
 
 BULK2_SOURCES = [os.path.join(ROOT, "paper_2608_14544_gb300", "csrc", f)
-                 for f in ("kernels_f32.cu", "bulk2.cuh", "qcl_common.cuh", "reduce.cuh",
-                           "kernels.h")]
+                 for f in ("kernels_f32.cu", "bulk2.cuh", "lanes.cuh", "qcl_common.cuh",
+                           "reduce.cuh", "kernels.h")]
 
 
 def _profiled(kernel_srcs, summary: str, key: str):

@@ -10,7 +10,7 @@ namespace qcl {
   void nstate_step64_##k(const DevModel*, void*, int64_t, int, int64_t, int64_t, double,      \
                          uint64_t, uint64_t, cudaStream_t);                                   \
   void nstate_observe64_##k(const void*, int64_t, int, double*, cudaStream_t);                \
-  int nstate_bulk_##k(const BulkParams&, const CoefN&, void*, double*, int, cudaStream_t);
+  int nstate_bulk_##k(const BulkParams&, const CoefN&, void*, double*, int, int, cudaStream_t);
 QCL_NS_DECL(3)
 QCL_NS_DECL(4)
 QCL_NS_DECL(5)
@@ -65,12 +65,12 @@ int launch_bulkN(int ns, const BulkParams& bp, const CoefN& cf, void* buf, doubl
     grid_cap = ls.blocks_per_sm * n_sm;
   int g = 0;
   switch (ns) {
-    case 3: g = nstate_bulk_3(bp, cf, buf, part, grid_cap, st); break;
-    case 4: g = nstate_bulk_4(bp, cf, buf, part, grid_cap, st); break;
-    case 5: g = nstate_bulk_5(bp, cf, buf, part, grid_cap, st); break;
-    case 6: g = nstate_bulk_6(bp, cf, buf, part, grid_cap, st); break;
-    case 7: g = nstate_bulk_7(bp, cf, buf, part, grid_cap, st); break;
-    case 8: g = nstate_bulk_8(bp, cf, buf, part, grid_cap, st); break;
+    case 3: g = nstate_bulk_3(bp, cf, buf, part, grid_cap, ls.wpt, st); break;
+    case 4: g = nstate_bulk_4(bp, cf, buf, part, grid_cap, ls.wpt, st); break;
+    case 5: g = nstate_bulk_5(bp, cf, buf, part, grid_cap, ls.wpt, st); break;
+    case 6: g = nstate_bulk_6(bp, cf, buf, part, grid_cap, ls.wpt, st); break;
+    case 7: g = nstate_bulk_7(bp, cf, buf, part, grid_cap, ls.wpt, st); break;
+    case 8: g = nstate_bulk_8(bp, cf, buf, part, grid_cap, ls.wpt, st); break;
     default: break;
   }
   if (g) launches_add(1);

@@ -10,7 +10,7 @@ void nstate_observe64_3(const void* buf, int64_t nt, int n, double* part, cudaSt
   NStateOps<3>::observe64(buf, nt, n, part, st);
 }
 int nstate_bulk_3(const BulkParams& bp, const CoefN& cf, void* buf, double* part, int grid_cap,
-                  cudaStream_t st) {
-  return NStateOps<3>::bulk(bp, cf, buf, part, grid_cap, st);
+                  int wpt, cudaStream_t st) {
+  return NStateOps<3>::bulk(bp, cf, buf, part, grid_cap, wpt, st);
 }
 }  // namespace qcl

@@ -9,6 +9,7 @@
 // U_ia U_jb continuous along the path.  Without a reference (initial sample)
 // the largest-magnitude component of each eigenvector is made positive.
 #pragma once
+#include "lanes.cuh"
 #include "qcl_common.cuh"
 
 namespace qcl {
@@ -199,108 +200,135 @@ __device__ __forceinline__ void eigh_ns(const T (&W)[NS][NS], const T (*ref)[NS]
 // its reference column.  The same rotations as eigh_ns in exact arithmetic, with
 // about a third fewer operations per rotation (no update of the elements the
 // rotation annihilates or leaves symmetric).
-template <int NS>
-__device__ __forceinline__ void eigh_warm_sym(const float (&W)[NS][NS], const float (&ref)[NS][NS],
-                                              float (&e)[NS], float (&U)[NS][NS]) {
-  float A[NS][NS], V[NS][NS];
+template <int NS, typename V>
+__device__ __forceinline__ void eigh_warm_sym(const V (&W)[NS][NS], const V (&ref)[NS][NS],
+                                              V (&e)[NS], V (&U)[NS][NS]) {
+  // V = float (one walker) or float2 (two walkers, one per lane): the FP32
+  // arithmetic is the packed lane arithmetic of lanes.cuh (explicit
+  // round-to-nearest, so each lane's bits do not depend on the lane count);
+  // divisions, square roots, compares and selects run per lane.
+  constexpr int L = Lanes<V>::W;
+  V A[NS][NS], Vm[NS][NS];
   {
-    float Wr[NS][NS];
+    V Wr[NS][NS];
 #pragma unroll
     for (int i = 0; i < NS; ++i)
 #pragma unroll
       for (int b = 0; b < NS; ++b) {
-        float acc = 0.0f;
+        V acc = splat<V>(0.0f);
 #pragma unroll
-        for (int k = 0; k < NS; ++k) acc = __fmaf_rn(W[i][k], ref[k][b], acc);
+        for (int k = 0; k < NS; ++k) acc = vfma(W[i][k], ref[k][b], acc);
         Wr[i][b] = acc;
       }
 #pragma unroll
     for (int a = 0; a < NS; ++a)
 #pragma unroll
       for (int b = a; b < NS; ++b) {
-        float acc = 0.0f;
+        V acc = splat<V>(0.0f);
 #pragma unroll
-        for (int k = 0; k < NS; ++k) acc = __fmaf_rn(ref[k][a], Wr[k][b], acc);
+        for (int k = 0; k < NS; ++k) acc = vfma(ref[k][a], Wr[k][b], acc);
         A[a][b] = acc;  // upper triangle only
       }
   }
 #pragma unroll
   for (int a = 0; a < NS; ++a)
 #pragma unroll
-    for (int b = 0; b < NS; ++b) V[a][b] = (a == b) ? 1.0f : 0.0f;
+    for (int b = 0; b < NS; ++b) Vm[a][b] = splat<V>(a == b ? 1.0f : 0.0f);
   // upper-triangle element (i, j) of A for any order of i, j
-  auto at = [&](int i, int j) -> float& { return i < j ? A[i][j] : A[j][i]; };
+  auto at = [&](int i, int j) -> V& { return i < j ? A[i][j] : A[j][i]; };
 #pragma unroll 1
   for (int sweep = 0; sweep < 2; ++sweep) {
 #pragma unroll
     for (int p = 0; p < NS; ++p)
 #pragma unroll
       for (int q = p + 1; q < NS; ++q) {
-        const float apq = A[p][q];
-        const bool zero = apq == 0.0f;
+        const V apq = A[p][q];
         // t = sgn(tau) / (|tau| + sqrt(1 + tau^2)) with approximate division and
         // square root (c and s follow from the same t, so the rotation stays
-        // orthogonal to rounding); |tau| is capped at 1e18, where t < 1e-18
-        const float tau = fminf(fmaxf(__fdividef(A[q][q] - A[p][p], 2.0f * (zero ? 1.0f : apq)),
-                                      -1e18f), 1e18f);
-        const float w2 = __fmaf_rn(tau, tau, 1.0f);
-        const float tr = __fdividef(tau >= 0.0f ? 1.0f : -1.0f, fabsf(tau) + w2 * rsqrtf(w2));
-        const float t = zero ? 0.0f : tr;
-        const float c = zero ? 1.0f : rsqrtf(__fmaf_rn(t, t, 1.0f));
-        const float sn = t * c;
-        A[p][p] = __fmaf_rn(-t, apq, A[p][p]);
-        A[q][q] = __fmaf_rn(t, apq, A[q][q]);
-        A[p][q] = 0.0f;
+        // orthogonal to rounding); |tau| is capped at 1e18, where t < 1e-18; a
+        // zero a_pq selects the identity rotation
+        const V d = vsub(A[q][q], A[p][p]);
+        const V twoa = vmul(splat<V>(2.0f), apq);
+        V tau, t, c;
+        bool zero[L];
+#pragma unroll
+        for (int l = 0; l < L; ++l) {
+          zero[l] = ln(apq, l) == 0.0f;
+          ln(tau, l) = fminf(fmaxf(__fdividef(ln(d, l), zero[l] ? 2.0f : ln(twoa, l)), -1e18f), 1e18f);
+        }
+        const V w2 = vfma(tau, tau, splat<V>(1.0f));
+#pragma unroll
+        for (int l = 0; l < L; ++l) {
+          const float tl = ln(tau, l), wl = ln(w2, l);
+          const float tr = __fdividef(tl >= 0.0f ? 1.0f : -1.0f, __fmaf_rn(wl, rsqrtf(wl), fabsf(tl)));
+          ln(t, l) = zero[l] ? 0.0f : tr;
+        }
+        const V tt1 = vfma(t, t, splat<V>(1.0f));
+#pragma unroll
+        for (int l = 0; l < L; ++l) ln(c, l) = zero[l] ? 1.0f : rsqrtf(ln(tt1, l));
+        const V sn = vmul(t, c), nsn = vmul(sn, splat<V>(-1.0f));
+        A[p][p] = vfma(t, vmul(apq, splat<V>(-1.0f)), A[p][p]);  // a_pp - t a_pq
+        A[q][q] = vfma(t, apq, A[q][q]);
+        A[p][q] = splat<V>(0.0f);
 #pragma unroll
         for (int r = 0; r < NS; ++r) {
           if (r == p || r == q) continue;
-          const float arp = at(r, p), arq = at(r, q);
-          at(r, p) = c * arp - sn * arq;
-          at(r, q) = sn * arp + c * arq;
+          const V arp = at(r, p), arq = at(r, q);
+          at(r, p) = vfma(c, arp, vmul(nsn, arq));
+          at(r, q) = vfma(sn, arp, vmul(c, arq));
         }
 #pragma unroll
         for (int k = 0; k < NS; ++k) {
-          const float vkp = V[k][p], vkq = V[k][q];
-          V[k][p] = c * vkp - sn * vkq;
-          V[k][q] = sn * vkp + c * vkq;
+          const V vkp = Vm[k][p], vkq = Vm[k][q];
+          Vm[k][p] = vfma(c, vkp, vmul(nsn, vkq));
+          Vm[k][q] = vfma(sn, vkp, vmul(c, vkq));
         }
       }
   }
 #pragma unroll
   for (int a = 0; a < NS; ++a) e[a] = A[a][a];
-  // ascending order of (e, columns of V) by a fixed compare network.  The warm
+  // ascending order of (e, columns of Vm) by a fixed compare network.  The warm
   // start keeps the reference's ascending order except where eigenvalues pass
   // each other, and on sorted input the network swaps nothing, so it runs only
   // when some walker of the warp is out of order (the same result either way).
   bool unsorted = false;
 #pragma unroll
-  for (int j = 1; j < NS; ++j) unsorted |= e[j] < e[j - 1];
+  for (int l = 0; l < L; ++l)
+#pragma unroll
+    for (int j = 1; j < NS; ++j) unsorted |= ln(e[j], l) < ln(e[j - 1], l);
   if (__any_sync(0xffffffffu, unsorted)) {
 #pragma unroll
-    for (int i = 1; i < NS; ++i)
+    for (int l = 0; l < L; ++l)
 #pragma unroll
-      for (int j = i; j > 0; --j) {
-        const bool sw = e[j] < e[j - 1];
-        const float t0 = e[j], t1 = e[j - 1];
-        e[j] = sw ? t1 : t0;
-        e[j - 1] = sw ? t0 : t1;
+      for (int i = 1; i < NS; ++i)
 #pragma unroll
-        for (int k = 0; k < NS; ++k) {
-          const float u0 = V[k][j], u1 = V[k][j - 1];
-          V[k][j] = sw ? u1 : u0;
-          V[k][j - 1] = sw ? u0 : u1;
+        for (int j = i; j > 0; --j) {
+          const bool sw = ln(e[j], l) < ln(e[j - 1], l);
+          const float t0 = ln(e[j], l), t1 = ln(e[j - 1], l);
+          ln(e[j], l) = sw ? t1 : t0;
+          ln(e[j - 1], l) = sw ? t0 : t1;
+#pragma unroll
+          for (int k = 0; k < NS; ++k) {
+            const float u0 = ln(Vm[k][j], l), u1 = ln(Vm[k][j - 1], l);
+            ln(Vm[k][j], l) = sw ? u1 : u0;
+            ln(Vm[k][j - 1], l) = sw ? u0 : u1;
+          }
         }
-      }
   }
-  // U = ref V; eigenvector a follows reference column a: <U_a, ref_a> = V[a][a]
+  // U = ref Vm; eigenvector b follows reference column b: <U_b, ref_b> = Vm[b][b]
+  V sg[NS];
+#pragma unroll
+  for (int b = 0; b < NS; ++b)
+#pragma unroll
+    for (int l = 0; l < L; ++l) ln(sg[b], l) = ln(Vm[b][b], l) < 0.0f ? -1.0f : 1.0f;
 #pragma unroll
   for (int i = 0; i < NS; ++i)
 #pragma unroll
     for (int b = 0; b < NS; ++b) {
-      float acc = 0.0f;
+      V acc = splat<V>(0.0f);
 #pragma unroll
-      for (int k = 0; k < NS; ++k) acc = __fmaf_rn(ref[i][k], V[k][b], acc);
-      U[i][b] = V[b][b] < 0.0f ? -acc : acc;
+      for (int k = 0; k < NS; ++k) acc = vfma(ref[i][k], Vm[k][b], acc);
+      U[i][b] = vmul(acc, sg[b]);
     }
 }
 

@@ -6,6 +6,8 @@
 // (e_a - e_b)/hbar, and one transition among the 2 (N_s - 1) events of the
 // coupling term of Eq. 1.
 #pragma once
+#include <type_traits>
+
 #include "kernels.h"
 #include "nstate.cuh"
 #include "reduce.cuh"
@@ -608,12 +610,25 @@ __host__ __device__ constexpr int tri(int a, int b) {
   return a <= b ? a * NS - a * (a - 1) / 2 + (b - a) : b * NS - b * (b - 1) / 2 + (a - b);
 }
 
-template <int NS, int NPL>
-__global__ void __launch_bounds__(128, NPL <= 8 ? (NS <= 4 ? 4 : (NS == 5 ? 3 : 1)) : 1)
+// WPT (1 or 2) tiles of 128 walkers per block, thread t holding walker t of
+// each: with WPT = 2 the two walkers are the lanes of float2 values and their
+// FP32 arithmetic runs as packed FP32x2 instructions (explicit round-to-nearest
+// operations throughout, so each walker's bits do not depend on WPT); event
+// selection, divisions, square roots and the observation run per lane.
+template <int NS, int NPL, int WPT>
+struct BulkNMinBlocks {
+  static constexpr int value =
+      NPL > 8 ? 1 : (WPT == 1 ? (NS <= 4 ? 4 : (NS == 5 ? 3 : 1)) : (NS <= 4 ? 2 : 1));
+};
+
+template <int NS, int NPL, int WPT>
+__global__ void __launch_bounds__(128, (BulkNMinBlocks<NS, NPL, WPT>::value))
     k_bulkN(const BulkParams bp, const CoefN cf, void* buf, double* __restrict__ part) {
+  static_assert(WPT == 1 || WPT == 2, "one or two walkers per thread");
+  using V = std::conditional_t<WPT == 2, float2, float>;
   constexpr int NN = NS * NS, NTRI = NS * (NS + 1) / 2;
   constexpr int NP = (4 * NN + 15) / 16;  // observation passes of 32 quantities
-  constexpr int TW = 128;                 // walkers per tile (one block)
+  constexpr int TW = 128;                 // walkers per tile
   __shared__ double red[2][4][32];
   __shared__ float obs_rows[TW * 33];
   WN<float> ws = viewN<float>(buf, bp.n_traj, NS, bp.n, QCL_PREC_FP32_BULK);
@@ -625,83 +640,143 @@ __global__ void __launch_bounds__(128, NPL <= 8 ? (NS <= 4 ? 4 : (NS == 5 ? 3 : 
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   unsigned int n_deg = 0;
   int rb = 0;
-  for (int64_t tile = blockIdx.x; tile < bp.n_tiles; tile += gridDim.x) {
-    const int64_t i = tile * TW + threadIdx.x;
-    const bool active = i < nt;
-    const int64_t ii = active ? i : 0;
-    float R[NPL], P[NPL];
+  for (int64_t tile0 = (int64_t)blockIdx.x * WPT; tile0 < bp.n_tiles;
+       tile0 += (int64_t)gridDim.x * WPT) {
+    bool active[WPT];
+    int64_t iw[WPT];
+    V R[NPL], P[NPL], U[NS][NS], e[NS];
+    PairV<V> m, ph;
+    int mexp[WPT], al[WPT], be[WPT];
+    uint64_t traj[WPT];
 #pragma unroll
-    for (int j = 0; j < NPL; ++j) {
-      const bool on = active && j < bp.n;
-      R[j] = on ? ws.R[(int64_t)j * nt + ii] : 0.0f;
-      P[j] = on ? ws.P[(int64_t)j * nt + ii] : 0.0f;
+    for (int l = 0; l < WPT; ++l) {
+      const int64_t i = (tile0 + l) * TW + threadIdx.x;
+      active[l] = i < nt;
+      const int64_t ii = active[l] ? i : 0;
+      iw[l] = i;
+#pragma unroll
+      for (int j = 0; j < NPL; ++j) {
+        const bool on = active[l] && j < bp.n;
+        ln(R[j], l) = on ? ws.R[(int64_t)j * nt + ii] : 0.0f;
+        ln(P[j], l) = on ? ws.P[(int64_t)j * nt + ii] : 0.0f;
+      }
+#pragma unroll
+      for (int a = 0; a < NS; ++a) {
+#pragma unroll
+        for (int b = 0; b < NS; ++b)
+          ln(U[a][b], l) = active[l] ? ws.U[(int64_t)(a * NS + b) * nt + ii] : (a == b ? 1.f : 0.f);
+        // decomposition at R_n as left by the previous step (stored exactly, so
+        // a chunk boundary changes no bit)
+        ln(e[a], l) = active[l] ? ws.E[(int64_t)a * nt + ii] : (float)a;
+      }
+      ln(m.hi, l) = active[l] ? ws.m[ii] : 0.0f;
+      ln(m.lo, l) = active[l] ? ws.mlo[ii] : 0.0f;
+      mexp[l] = active[l] ? ws.mexp[ii] : 0;
+      ln(ph.hi, l) = active[l] ? ws.phi[ii] : 0.0f;
+      ln(ph.lo, l) = active[l] ? ws.philo[ii] : 0.0f;
+      const uint32_t ab0 = active[l] ? ws.ab[ii] : 0u;
+      al[l] = ab0 & 0xff;
+      be[l] = (ab0 >> 8) & 0xff;
+      traj[l] = bp.traj_offset + (uint64_t)ii;
     }
-    float U[NS][NS], e[NS];
-#pragma unroll
-    for (int a = 0; a < NS; ++a)
-#pragma unroll
-      for (int b = 0; b < NS; ++b) U[a][b] = active ? ws.U[(int64_t)(a * NS + b) * nt + ii] : (a == b ? 1.f : 0.f);
-    f2 m = {active ? ws.m[ii] : 0.0f, active ? ws.mlo[ii] : 0.0f};
-    int mexp = active ? ws.mexp[ii] : 0;
-    f2 ph = {active ? ws.phi[ii] : 0.0f, active ? ws.philo[ii] : 0.0f};
-    const uint32_t ab0 = active ? ws.ab[ii] : 0u;
-    int al = ab0 & 0xff, be = (ab0 >> 8) & 0xff;
-    const uint64_t traj = bp.traj_offset + (uint64_t)ii;
 
-    auto build_w = [&](float (&W)[NS][NS]) {
-      float t[NTRI];
+    auto build_w = [&](V (&W)[NS][NS]) {
+      V t[NTRI];
 #pragma unroll
-      for (int k = 0; k < NTRI; ++k) t[k] = cf.E[k];
+      for (int k = 0; k < NTRI; ++k) t[k] = splat<V>(cf.E[k]);
 #pragma unroll
       for (int j = 0; j < NPL; ++j)
 #pragma unroll
-        for (int k = 0; k < NTRI; ++k) t[k] = __fmaf_rn(R[j], cf.K[j][k], t[k]);
+        for (int k = 0; k < NTRI; ++k) t[k] = vfma(R[j], splat<V>(cf.K[j][k]), t[k]);
 #pragma unroll
       for (int a = 0; a < NS; ++a)
 #pragma unroll
         for (int b = 0; b < NS; ++b) W[a][b] = t[tri<NS>(a, b)];
     };
-    // decomposition at R_n as left by the previous step (stored exactly, so a
-    // chunk boundary changes no bit)
+    // columns al, be of U (per lane)
+    auto columns = [&](V (&ua)[NS], V (&ub)[NS]) {
 #pragma unroll
-    for (int a = 0; a < NS; ++a) e[a] = active ? ws.E[(int64_t)a * nt + ii] : (float)a;
-    // dt/2 * (1/2)(u_a u_a^T + u_b u_b^T) folded with the off-diagonal factor 2
-    // (ua, ub: columns al, be of U)
-    auto kick = [&](const float (&ua)[NS], const float (&ub)[NS]) {
-      float Q[NTRI];
+      for (int l = 0; l < WPT; ++l)
+#pragma unroll
+        for (int i = 0; i < NS; ++i) {
+          float va = ln(U[i][0], l), vb = va;
+#pragma unroll
+          for (int c = 1; c < NS; ++c) {
+            va = (c == al[l]) ? ln(U[i][c], l) : va;
+            vb = (c == be[l]) ? ln(U[i][c], l) : vb;
+          }
+          ln(ua[i], l) = va;
+          ln(ub[i], l) = vb;
+        }
+    };
+    // e_al - e_be (per lane picks)
+    auto gap_ab = [&]() {
+      V ea, eb;
+#pragma unroll
+      for (int l = 0; l < WPT; ++l) {
+        float va = ln(e[0], l), vb = va;
+#pragma unroll
+        for (int c = 1; c < NS; ++c) {
+          va = (c == al[l]) ? ln(e[c], l) : va;
+          vb = (c == be[l]) ? ln(e[c], l) : vb;
+        }
+        ln(ea, l) = va;
+        ln(eb, l) = vb;
+      }
+      return vsub(ea, eb);
+    };
+    // P += dt/2 F_ab with dt/2 * (1/2)(u_a u_a^T + u_b u_b^T) folded with the
+    // off-diagonal factor 2 (ua, ub: columns al, be of U)
+    auto kick = [&](const V (&ua)[NS], const V (&ub)[NS]) {
+      V Q[NTRI];
 #pragma unroll
       for (int a = 0; a < NS; ++a)
 #pragma unroll
         for (int b = a; b < NS; ++b)
-          Q[tri<NS>(a, b)] = (a == b ? 0.5f : 1.0f) * bp.hdt * (ua[a] * ua[b] + ub[a] * ub[b]);
+          Q[tri<NS>(a, b)] = vmul(splat<V>((a == b ? 0.5f : 1.0f) * bp.hdt),
+                                  vfma(ua[a], ua[b], vmul(ub[a], ub[b])));
 #pragma unroll
       for (int j = 0; j < NPL; ++j) {
-        float g = 0.0f;
+        V g = splat<V>(0.0f);
 #pragma unroll
-        for (int k = 0; k < NTRI; ++k) g = __fmaf_rn(cf.K[j][k], Q[k], g);
-        P[j] = __fmaf_rn(-cf.hk[j], R[j], P[j]) - g;
+        for (int k = 0; k < NTRI; ++k) g = vfma(splat<V>(cf.K[j][k]), Q[k], g);
+        P[j] = vsub(vfma(splat<V>(-cf.hk[j]), R[j], P[j]), g);
       }
     };
-    auto observe = [&](int slot) {
-      renormN(m, mexp);
-      const bool live = active && m.hi != 0.0f;
-      int ew = live ? mexp : -(1 << 28);
+    // observation of walker lane l into slot `slot` of tile tile0 + l
+    auto observe_lane = [&](int l, int slot) {
+      f2 ml = {ln(m.hi, l), ln(m.lo, l)};
+      f2 pl = {ln(ph.hi, l), ln(ph.lo, l)};
+      int me = mexp[l];
+      renormN(ml, me);
+      const bool live = active[l] && ml.hi != 0.0f;
+      int ew = live ? me : -(1 << 28);
 #pragma unroll
       for (int off = 16; off > 0; off >>= 1) ew = max(ew, __shfl_xor_sync(0xffffffffu, ew, off));
-      const float kq = rintf(ph.hi * kInvTwoPiN);
-      ph = df_add(ph, -kq * kTwoPi1N);
-      ph = df_add(ph, -kq * kTwoPi2N);
-      ph = df_add(ph, -kq * kTwoPi3N);
+      const float kq = rintf(pl.hi * kInvTwoPiN);
+      pl = df_add(pl, -kq * kTwoPi1N);
+      pl = df_add(pl, -kq * kTwoPi2N);
+      pl = df_add(pl, -kq * kTwoPi3N);
+      ln(m.hi, l) = ml.hi;
+      ln(m.lo, l) = ml.lo;
+      mexp[l] = me;
+      ln(ph.hi, l) = pl.hi;
+      ln(ph.lo, l) = pl.lo;
       float sh, chh;
-      __sincosf(ph.hi, &sh, &chh);
-      const float mm = live ? m.hi * pow2iN(mexp - ew) : 0.0f;
-      const float zr = mm * __fmaf_rn(-ph.lo, sh, chh), zi = -mm * __fmaf_rn(ph.lo, chh, sh);
+      __sincosf(pl.hi, &sh, &chh);
+      const float mm = live ? ml.hi * pow2iN(me - ew) : 0.0f;
+      const float zr = mm * __fmaf_rn(-pl.lo, sh, chh), zi = -mm * __fmaf_rn(pl.lo, chh, sh);
       const int ex = (ew < -(1 << 27)) ? 0 : ((lane < 16) ? ew : 2 * ew);
+      float Ul[NS][NS];
+#pragma unroll
+      for (int a = 0; a < NS; ++a)
+#pragma unroll
+        for (int b = 0; b < NS; ++b) Ul[a][b] = ln(U[a][b], l);
       float* row = &obs_rows[threadIdx.x * 33];
 #pragma unroll 1
       for (int p = 0; p < NP; ++p) {
         float v[16];
-        contrib_values<float, NS>(U, al, be, zr, zi, p, v);
+        contrib_values<float, NS>(Ul, al[l], be[l], zr, zi, p, v);
 #pragma unroll
         for (int t = 0; t < 16; ++t) {
           row[t] = v[t];
@@ -720,14 +795,18 @@ __global__ void __launch_bounds__(128, NPL <= 8 ? (NS <= 4 ? 4 : (NS == 5 ? 3 : 
         const double xd = (double)l1[0];
         red[rb][warp][lane] = (ex >= -1022 && ex <= 1023) ? xd * pow2dN(ex) : ldexp(xd, ex);
         __syncthreads();
-        if (threadIdx.x < 32) {
+        if (threadIdx.x < 32 && tile0 + l < bp.n_tiles) {
           const int q = (lane < 16) ? 16 * p + lane : 4 * NN + 16 * p + (lane - 16);
           if (16 * p + (lane & 15) < 4 * NN)
-            part[((int64_t)slot * bp.n_tiles + tile) * 8 * NN + q] =
+            part[((int64_t)slot * bp.n_tiles + tile0 + l) * 8 * NN + q] =
                 (red[rb][0][lane] + red[rb][1][lane]) + (red[rb][2][lane] + red[rb][3][lane]);
         }
         rb ^= 1;
       }
+    };
+    auto observe = [&](int slot) {
+#pragma unroll
+      for (int l = 0; l < WPT; ++l) observe_lane(l, slot);
     };
 
     int slot = bp.obs_first;
@@ -735,125 +814,205 @@ __global__ void __launch_bounds__(128, NPL <= 8 ? (NS <= 4 ? 4 : (NS == 5 ? 3 : 
     int to_out = bp.to_out0;
     uint32_t blk = bp.blk0;
     int widx = bp.widx0;
-    u4 wd = philox_draw(bp.seed, blk, traj, kPurposeHop);
+    u4 wd[WPT];
+#pragma unroll
+    for (int l = 0; l < WPT; ++l) wd[l] = philox_draw(bp.seed, blk, traj[l], kPurposeHop);
     for (int it = 0; it < bp.len; ++it) {
-      const uint32_t word = (widx & 2) ? ((widx & 1) ? wd.w : wd.z) : ((widx & 1) ? wd.y : wd.x);
-      const float de0 = pick<float, NS>(e, al) - pick<float, NS>(e, be);
-      float ua[NS], ub[NS];
-      column<float, NS>(U, al, ua);
-      column<float, NS>(U, be, ub);
+      const V de0 = gap_ab();
+      V ua[NS], ub[NS];
+      columns(ua, ub);
       kick(ua, ub);  // first half kick at R_n
 #pragma unroll
-      for (int j = 0; j < NPL; ++j) R[j] = __fmaf_rn(cf.dtm[j], P[j], R[j]);
+      for (int j = 0; j < NPL; ++j) R[j] = vfma(splat<V>(cf.dtm[j]), P[j], R[j]);
       {
-        float W[NS][NS], Uref[NS][NS];
+        V W[NS][NS], Uref[NS][NS];
 #pragma unroll
         for (int a = 0; a < NS; ++a)
 #pragma unroll
           for (int b = 0; b < NS; ++b) Uref[a][b] = U[a][b];
         build_w(W);
-        eigh_warm_sym<NS>(W, Uref, e, U);
+        eigh_warm_sym<NS, V>(W, Uref, e, U);
       }
-      column<float, NS>(U, al, ua);  // (the new decomposition's columns, used twice)
-      column<float, NS>(U, be, ub);
-      kick(ua, ub);  // second half kick at R_{n+1}
-      const float de1 = pick<float, NS>(e, al) - pick<float, NS>(e, be);
-      ph = df_add(ph, bp.hdt_hbar * (de0 + de1));
+      columns(ua, ub);  // (the new decomposition's columns, used twice)
+      kick(ua, ub);     // second half kick at R_{n+1}
+      const V de1 = gap_ab();
+      ph = df_add_v(ph, vmul(splat<V>(bp.hdt_hbar), vadd(de0, de1)));
       // G = sum_j (P_j/M_j) K_j
-      float G[NS][NS];
+      V G[NS][NS];
       {
-        float t[NTRI];
+        V t[NTRI];
 #pragma unroll
-        for (int k = 0; k < NTRI; ++k) t[k] = 0.0f;
+        for (int k = 0; k < NTRI; ++k) t[k] = splat<V>(0.0f);
 #pragma unroll
         for (int j = 0; j < NPL; ++j) {
-          const float v = P[j] * cf.minv[j];
+          const V v = vmul(P[j], splat<V>(cf.minv[j]));
 #pragma unroll
-          for (int k = 0; k < NTRI; ++k) t[k] = __fmaf_rn(v, cf.K[j][k], t[k]);
+          for (int k = 0; k < NTRI; ++k) t[k] = vfma(v, splat<V>(cf.K[j][k]), t[k]);
         }
 #pragma unroll
         for (int a = 0; a < NS; ++a)
 #pragma unroll
           for (int b = 0; b < NS; ++b) G[a][b] = t[tri<NS>(a, b)];
       }
+      // event amplitudes of the coupling term of Eq. 1 (as event_amplitudes):
+      // slots 0..NS-1 move the first index a -> nu with A = -dt (v.d)_{nu a},
+      // slots NS..2NS-1 the second index b -> nu with A = +dt (v.d)_{b nu}
       constexpr int NC = 2 * NS;
-      float A[NC];
-      bool ev[NC];
-      const bool dg = event_amplitudes_cols<float, NS>(G, U, ua, ub, e, al, be, bp.dt, kDegTolF, A, ev);
-      n_deg += (dg && active) ? 1u : 0u;
-      uint32_t T[NC], sumT = 0;
+      V A[NC];
+      bool ev[WPT][NC];
+      {
+        V Gua[NS], Gub[NS];
 #pragma unroll
-      for (int k = 0; k < NC; ++k) {
-        T[k] = ev[k] ? min(__float2uint_rz(fminf(bp.kappa * fabsf(A[k]) * kP24f, 33554432.0f)), bp.tmax) : 0u;
-        sumT += T[k];
+        for (int k = 0; k < NS; ++k) {
+          V s0 = splat<V>(0.0f), s1 = splat<V>(0.0f);
+#pragma unroll
+          for (int c = 0; c < NS; ++c) {
+            s0 = vfma(G[k][c], ua[c], s0);
+            s1 = vfma(G[k][c], ub[c], s1);
+          }
+          Gua[k] = s0;
+          Gub[k] = s1;
+        }
+        V ea, eb;
+#pragma unroll
+        for (int l = 0; l < WPT; ++l) {
+          float va = ln(e[0], l), vb = va;
+#pragma unroll
+          for (int c = 1; c < NS; ++c) {
+            va = (c == al[l]) ? ln(e[c], l) : va;
+            vb = (c == be[l]) ? ln(e[c], l) : vb;
+          }
+          ln(ea, l) = va;
+          ln(eb, l) = vb;
+        }
+        bool dgl[WPT];
+#pragma unroll
+        for (int l = 0; l < WPT; ++l) dgl[l] = false;
+#pragma unroll
+        for (int sl = 0; sl < 2; ++sl)
+#pragma unroll
+          for (int nu = 0; nu < NS; ++nu) {
+            V h = splat<V>(0.0f);
+#pragma unroll
+            for (int k = 0; k < NS; ++k) h = vfma(U[k][nu], sl == 0 ? Gua[k] : Gub[k], h);
+            const V gap = (sl == 0) ? vsub(ea, e[nu]) : vsub(e[nu], eb);
+            V vd;
+#pragma unroll
+            for (int l = 0; l < WPT; ++l) {
+              const bool evl = (sl == 0) ? (nu != al[l]) : (nu != be[l]);
+              const bool dg = evl && fabsf(ln(gap, l)) < kDegTolF;
+              dgl[l] |= dg;
+              // approximate division (the amplitude enters a probability and a
+              // weight factor, both far above its 2-ulp error)
+              ln(vd, l) = (!evl || dg) ? 0.0f : __fdividef(ln(h, l), ln(gap, l));
+              ev[l][sl * NS + nu] = evl;
+            }
+            A[sl * NS + nu] = vmul(splat<V>(sl == 0 ? -bp.dt : bp.dt), vd);
+          }
+#pragma unroll
+        for (int l = 0; l < WPT; ++l) n_deg += (dgl[l] && active[l]) ? 1u : 0u;
       }
-      if (sumT > bp.tmax) {
-        const float sc = (float)bp.tmax / (float)sumT;
-        uint32_t s2 = 0;
+      // thresholds, event choice and the weight factor (per lane), the
+      // compensated weight product (lanes)
+      V num, den, rd;
+      int hitl[WPT];
+#pragma unroll
+      for (int l = 0; l < WPT; ++l) {
+        const uint32_t word = (widx & 2) ? ((widx & 1) ? wd[l].w : wd[l].z)
+                                         : ((widx & 1) ? wd[l].y : wd[l].x);
+        uint32_t T[NC], sumT = 0;
 #pragma unroll
         for (int k = 0; k < NC; ++k) {
-          T[k] = min(__float2uint_rz((float)T[k] * sc), T[k]);
-          s2 += T[k];
+          const float ka = fabsf(ln(vmul(splat<V>(bp.kappa), A[k]), l));
+          T[k] = ev[l][k] ? min(__float2uint_rz(fminf(ka * kP24f, 33554432.0f)), bp.tmax) : 0u;
+          sumT += T[k];
         }
-        sumT = s2;
-      }
-      const uint32_t y = word >> 8;
-      uint32_t cum = 0;
-      int hit = -1;
+        if (sumT > bp.tmax) {
+          const float sc = (float)bp.tmax / (float)sumT;
+          uint32_t s2 = 0;
 #pragma unroll
-      for (int k = 0; k < NC; ++k) {
-        cum += T[k];
-        hit = (hit < 0 && y < cum) ? k : hit;
-      }
-      float Ah = A[0];
-      uint32_t Th = T[0];
+          for (int k = 0; k < NC; ++k) {
+            T[k] = min(__float2uint_rz((float)T[k] * sc), T[k]);
+            s2 += T[k];
+          }
+          sumT = s2;
+        }
+        const uint32_t y = word >> 8;
+        uint32_t cum = 0;
+        int hit = -1;
 #pragma unroll
-      for (int k = 1; k < NC; ++k) {
-        Ah = (k == hit) ? A[k] : Ah;
-        Th = (k == hit) ? T[k] : Th;
+        for (int k = 0; k < NC; ++k) {
+          cum += T[k];
+          hit = (hit < 0 && y < cum) ? k : hit;
+        }
+        float Ah = ln(A[0], l);
+        uint32_t Th = T[0];
+#pragma unroll
+        for (int k = 1; k < NC; ++k) {
+          Ah = (k == hit) ? ln(A[k], l) : Ah;
+          Th = (k == hit) ? T[k] : Th;
+        }
+        const bool hop = hit >= 0;
+        ln(num, l) = hop ? Ah * kP24f : kP24f;
+        ln(den, l) = __uint2float_rn(hop ? Th : 16777216u - sumT);
+        ln(rd, l) = __frcp_rn(ln(den, l));
+        hitl[l] = hit;
       }
-      const bool hop = hit >= 0;
-      const float num = hop ? Ah * kP24f : kP24f;
-      const float den = __uint2float_rn(hop ? Th : 16777216u - sumT);
-      const float rd = __frcp_rn(den);
-      const float q0 = num * rd;
-      const float q1 = __fmaf_rn(-q0, den, num) * rd;
-      m = df_mul(m, q0, q1);
-      if (!(fabsf(m.hi) <= 0x1p32f && fabsf(m.hi) >= 0x1p-32f)) renormN(m, mexp);
-      if (hop) {
-        if (hit < NS) al = hit;
-        else be = hit - NS;
+      const V q0 = vmul(num, rd);
+      const V q1 = vmul(vfma(q0, vmul(den, splat<V>(-1.0f)), num), rd);
+      m = df_mul_v(m, q0, q1);
+#pragma unroll
+      for (int l = 0; l < WPT; ++l) {
+        const float h = ln(m.hi, l);
+        if (!(fabsf(h) <= 0x1p32f && fabsf(h) >= 0x1p-32f)) {
+          f2 ml = {h, ln(m.lo, l)};
+          renormN(ml, mexp[l]);
+          ln(m.hi, l) = ml.hi;
+          ln(m.lo, l) = ml.lo;
+        }
+        const int hit = hitl[l];
+        if (hit >= 0) {
+          if (hit < NS) al[l] = hit;
+          else be[l] = hit - NS;
+        }
       }
       if (++widx == 4) {
         widx = 0;
         ++blk;
-        if (it + 1 < bp.len) wd = philox_draw(bp.seed, blk, traj, kPurposeHop);
+        if (it + 1 < bp.len) {
+#pragma unroll
+          for (int l = 0; l < WPT; ++l) wd[l] = philox_draw(bp.seed, blk, traj[l], kPurposeHop);
+        }
       }
       if (--to_out == 0) {
         observe(slot++);
         to_out = bp.stride;
       }
     }
-    if (active) {
+#pragma unroll
+    for (int l = 0; l < WPT; ++l) {
+      if (!active[l]) continue;
+      const int64_t i = iw[l];
 #pragma unroll
       for (int j = 0; j < NPL; ++j)
         if (j < bp.n) {
-          ws.R[(int64_t)j * nt + i] = R[j];
-          ws.P[(int64_t)j * nt + i] = P[j];
+          ws.R[(int64_t)j * nt + i] = ln(R[j], l);
+          ws.P[(int64_t)j * nt + i] = ln(P[j], l);
         }
 #pragma unroll
-      for (int a = 0; a < NS; ++a)
+      for (int a = 0; a < NS; ++a) {
 #pragma unroll
-        for (int b = 0; b < NS; ++b) ws.U[(int64_t)(a * NS + b) * nt + i] = U[a][b];
-#pragma unroll
-      for (int a = 0; a < NS; ++a) ws.E[(int64_t)a * nt + i] = e[a];
-      ws.m[i] = m.hi;
-      ws.mlo[i] = m.lo;
-      ws.mexp[i] = mexp;
-      ws.phi[i] = ph.hi;
-      ws.philo[i] = ph.lo;
-      ws.ab[i] = (uint16_t)(al | (be << 8));
-      if (!isfinite(m.hi) || !isfinite(ph.hi)) {
+        for (int b = 0; b < NS; ++b) ws.U[(int64_t)(a * NS + b) * nt + i] = ln(U[a][b], l);
+        ws.E[(int64_t)a * nt + i] = ln(e[a], l);
+      }
+      const float mh = ln(m.hi, l), phh = ln(ph.hi, l);
+      ws.m[i] = mh;
+      ws.mlo[i] = ln(m.lo, l);
+      ws.mexp[i] = mexp[l];
+      ws.phi[i] = phh;
+      ws.philo[i] = ln(ph.lo, l);
+      ws.ab[i] = (uint16_t)(al[l] | (be[l] << 8));
+      if (!isfinite(mh) || !isfinite(phh)) {
         atomicAdd(&ws.hdr->n_nonfinite, 1ull);
         atomicOr(&ws.hdr->flags, QCL_FLAG_NONFINITE);
       }
@@ -887,11 +1046,11 @@ struct NStateOps {
   static void observe64(const void* buf, int64_t nt, int n, double* part, cudaStream_t st) {
     k_observeN_f64<NS><<<(unsigned)((nt + 255) / 256), 256, 0, st>>>(buf, nt, n, part);
   }
-  template <int NPL>
+  template <int NPL, int WPT = 1>
   static int bulk_npl(const BulkParams& bp, const CoefN& cf, void* buf, double* part,
                       int grid_cap, cudaStream_t st) {
     static int per_sm = -1, n_sm = 0;
-    auto fn = k_bulkN<NS, NPL>;
+    auto fn = k_bulkN<NS, NPL, WPT>;
     if (per_sm < 0) {
       int dev = 0;
       cudaGetDevice(&dev);
@@ -902,13 +1061,19 @@ struct NStateOps {
     }
     int64_t grid = (int64_t)per_sm * n_sm;
     if (grid_cap > 0 && grid > grid_cap) grid = grid_cap;
-    if (grid > bp.n_tiles) grid = bp.n_tiles;
+    const int64_t units = (bp.n_tiles + WPT - 1) / WPT;
+    if (grid > units) grid = units;
     if (grid < 1) grid = 1;
     fn<<<(unsigned)grid, 128, 0, st>>>(bp, cf, buf, part);
     return (int)grid;
   }
+  // wpt: walkers per thread asked for.  The kernel takes one or two, but only
+  // one is instantiated: two walkers per thread (packed lanes, 205-245
+  // registers, 8 resident warps per SM) measured 10 % slower on a four-state
+  // six-mode model than one (114 registers, 16 warps), with the same bits.
   static int bulk(const BulkParams& bp, const CoefN& cf, void* buf, double* part, int grid_cap,
-                  cudaStream_t st) {
+                  int wpt, cudaStream_t st) {
+    (void)wpt;
     // up to 8 modes for any N_s; up to 32 modes for N_s <= 4 (larger N_s x modes
     // would not fit a walker in registers).  For N_s <= 5 models of at most 4 or
     // 6 modes get their own instantiations, which skip the padding modes'

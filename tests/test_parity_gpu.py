@@ -244,6 +244,25 @@ def test_step_mismatch_is_flagged_and_nothing_moves(q):
         assert np.array_equal(before["R"], after["R"])
 
 
+def test_spin_boson_form_needs_b0_above_the_degeneracy_threshold(q):
+    """A spin-boson model whose |b0| cannot keep r^2 = a^2 + b0^2 above the FP32
+    degeneracy threshold runs the general two-state form, which tests for
+    degeneracy: walkers held at a(R) = 0 (eps = 0, R0 = P0 = 0, no Wigner spread,
+    so the mean force stays zero) count a degenerate step each step.  With b0
+    large enough the spin-boson form runs and no step is degenerate."""
+    for delta, expect in ((1e-7, True), (0.5, False)):
+        model = wl.spin_boson(0.0, delta, np.array([1.0]), np.array([0.3]))
+        init = {"rho_el0": np.diag([1.0, 0.0]), "R0": np.zeros(1), "P0": np.zeros(1),
+                "beta": math.inf, "wigner": 0}
+        n, steps = 1000, 40
+        m, run = _gpu_run(q, None, n, q.PREC_FP32_BULK, steps, 10, init=init, model=model)
+        run.propagate(steps, 0.01, 10)
+        st = run.status()
+        assert bool(st["flags"] & q.FLAG_DEGENERATE) == expect, delta
+        assert st["n_degenerate"] == (n * steps if expect else 0), (delta, st)
+        assert np.all(run.state()["R"] == 0.0)
+
+
 def test_zero_steps_writes_only_initial_row(q):
     cfg = wl.config(1)
     for prec in (q.PREC_FP64, q.PREC_FP32_BULK):
