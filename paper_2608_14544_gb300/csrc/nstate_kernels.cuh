@@ -702,8 +702,9 @@ __global__ void __launch_bounds__(128, (BulkNMinBlocks<NS, NPL, WPT>::value))
           float va = ln(U[i][0], l), vb = va;
 #pragma unroll
           for (int c = 1; c < NS; ++c) {
-            va = (c == al[l]) ? ln(U[i][c], l) : va;
-            vb = (c == be[l]) ? ln(U[i][c], l) : vb;
+            const float uc = ln(U[i][c], l);  // (a value, not a reference, in the selects)
+            va = (c == al[l]) ? uc : va;
+            vb = (c == be[l]) ? uc : vb;
           }
           ln(ua[i], l) = va;
           ln(ub[i], l) = vb;
@@ -717,8 +718,9 @@ __global__ void __launch_bounds__(128, (BulkNMinBlocks<NS, NPL, WPT>::value))
         float va = ln(e[0], l), vb = va;
 #pragma unroll
         for (int c = 1; c < NS; ++c) {
-          va = (c == al[l]) ? ln(e[c], l) : va;
-          vb = (c == be[l]) ? ln(e[c], l) : vb;
+          const float ec = ln(e[c], l);
+          va = (c == al[l]) ? ec : va;
+          vb = (c == be[l]) ? ec : vb;
         }
         ln(ea, l) = va;
         ln(eb, l) = vb;
@@ -773,7 +775,10 @@ __global__ void __launch_bounds__(128, (BulkNMinBlocks<NS, NPL, WPT>::value))
 #pragma unroll
         for (int b = 0; b < NS; ++b) Ul[a][b] = ln(U[a][b], l);
       float* row = &obs_rows[threadIdx.x * 33];
-#pragma unroll 1
+      // passes unrolled for N_s <= 4 (their quantity indices are then
+      // compile-time: no local-memory arrays), rolled for larger N_s
+      constexpr int kPassUnroll = NP <= 4 ? NP : 1;
+#pragma unroll kPassUnroll
       for (int p = 0; p < NP; ++p) {
         float v[16];
         contrib_values<float, NS>(Ul, al[l], be[l], zr, zi, p, v);
@@ -879,8 +884,9 @@ __global__ void __launch_bounds__(128, (BulkNMinBlocks<NS, NPL, WPT>::value))
           float va = ln(e[0], l), vb = va;
 #pragma unroll
           for (int c = 1; c < NS; ++c) {
-            va = (c == al[l]) ? ln(e[c], l) : va;
-            vb = (c == be[l]) ? ln(e[c], l) : vb;
+            const float ec = ln(e[c], l);
+            va = (c == al[l]) ? ec : va;
+            vb = (c == be[l]) ? ec : vb;
           }
           ln(ea, l) = va;
           ln(eb, l) = vb;
@@ -949,7 +955,8 @@ __global__ void __launch_bounds__(128, (BulkNMinBlocks<NS, NPL, WPT>::value))
         uint32_t Th = T[0];
 #pragma unroll
         for (int k = 1; k < NC; ++k) {
-          Ah = (k == hit) ? ln(A[k], l) : Ah;
+          const float Ak = ln(A[k], l);
+          Ah = (k == hit) ? Ak : Ah;
           Th = (k == hit) ? T[k] : Th;
         }
         const bool hop = hit >= 0;
