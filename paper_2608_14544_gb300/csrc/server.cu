@@ -9,7 +9,8 @@
 // persistent launch that reads a device table of (request, tile) work items;
 // that part of a round is a fixed-shape CUDA graph [table uploads, packed
 // kernels] captured once and replayed every round.  Other requests (many modes,
-// more states) get their own persistent launches in the same round.  Requests
+// more states) get their own persistent launches in the same round, spread
+// over eight side streams so that small launches run side by side.  Requests
 // that arrive meanwhile are admitted at the next round boundary.  A request's
 // arithmetic depends only on its own descriptors, so its results are the same
 // bits alone and in any mix.
@@ -132,6 +133,12 @@ struct qcl_server {
   Arena alloc;
   cudaStream_t stream = nullptr;
   cudaEvent_t done_ev = nullptr;
+  // requests with their own launches run on side streams, so that the small
+  // ones' launches overlap; each round joins them back into `stream`
+  static constexpr int kSide = 8;
+  cudaStream_t side[kSide] = {};
+  cudaEvent_t side_ev[kSide] = {};
+  cudaEvent_t start_ev = nullptr;
   PackedTable* host_tab = nullptr;  // pinned, [2 kinds][buckets]
   PackedTable* dev_tab = nullptr;   // in the arena
   cudaGraphExec_t graph = nullptr;
@@ -263,6 +270,24 @@ void fill_bulk(const Request& r, const Chunk& c, int64_t n_tiles, BulkParams& bp
   bp.widx0 = (int32_t)(c.cs & 3);
 }
 
+// Destroys the server's streams and events (after synchronising the side streams).
+void release_streams(qcl_server* s) {
+  for (int j = 0; j < qcl_server::kSide; ++j) {
+    if (s->side[j]) {
+      cudaStreamSynchronize(s->side[j]);
+      cudaStreamDestroy(s->side[j]);
+    }
+    if (s->side_ev[j]) cudaEventDestroy(s->side_ev[j]);
+    s->side[j] = nullptr;
+    s->side_ev[j] = nullptr;
+  }
+  if (s->start_ev) cudaEventDestroy(s->start_ev);
+  if (s->done_ev) cudaEventDestroy(s->done_ev);
+  if (s->stream) cudaStreamDestroy(s->stream);
+  s->start_ev = s->done_ev = nullptr;
+  s->stream = nullptr;
+}
+
 bool wait_stream(qcl_server* s, double timeout_s) {
   cudaEventRecord(s->done_ev, s->stream);
   const double t0 = now_s();
@@ -320,6 +345,9 @@ void run_round(qcl_server* s) {
     T->n_work += n_tiles;
     ++T->n_req;
   }
+  // the side streams start after everything enqueued on `stream` so far
+  // (admission sampling, the previous round)
+  cudaEventRecord(s->start_ev, s->stream);
   // packed part: one fixed-shape graph (or the same launches directly)
   if (s->graph) {
     cudaGraphLaunch(s->graph, s->stream);
@@ -327,6 +355,8 @@ void run_round(qcl_server* s) {
   } else {
     enqueue_packed(s);
   }
+  bool side_used[qcl_server::kSide] = {};
+  int n_own = 0;
   for (auto& it : items) {
     Request& r = *it.r;
     char* ens_buf = s->arena + r.ens_off;
@@ -339,14 +369,24 @@ void run_round(qcl_server* s) {
       launch_header_finish(ens_buf, it.c.cs, it.c.ce, s->stream);
     } else {
       if (r.bucket == -2) r.bucket = -1;
+      const int j = n_own++ % qcl_server::kSide;
+      if (!side_used[j]) {
+        cudaStreamWaitEvent(s->side[j], s->start_ev, 0);
+        side_used[j] = true;
+      }
       const qcl_status st = qcl_propagate(r.model, &r.ens, ens_buf, r.ens_bytes, it.c.cs, it.c.ce - it.c.cs, r.dt,
-                                          r.stride, obs_buf, r.obs_bytes, r.n_out, s->stream);
+                                          r.stride, obs_buf, r.obs_bytes, r.n_out, s->side[j]);
       if (st != QCL_OK) {
         finish(s, it.r, RQ_ERROR, qcl_last_error());
         it.r = nullptr;
       }
     }
   }
+  for (int j = 0; j < qcl_server::kSide; ++j)
+    if (side_used[j]) {
+      cudaEventRecord(s->side_ev[j], s->side[j]);
+      cudaStreamWaitEvent(s->stream, s->side_ev[j], 0);
+    }
   if (!wait_stream(s, s->d.round_timeout_s > 0 ? s->d.round_timeout_s : 600.0)) {
     const cudaError_t e = cudaGetLastError();
     for (auto& it : items)
@@ -418,10 +458,14 @@ qcl_status qcl_server_create(const qcl_server_desc* d, qcl_server** out) {
   s->alloc.init(table_bytes(), d->arena_bytes - table_bytes());
   cudaError_t e = cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking);
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s->done_ev, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s->start_ev, cudaEventDisableTiming);
+  for (int j = 0; j < qcl_server::kSide && e == cudaSuccess; ++j) {
+    e = cudaStreamCreateWithFlags(&s->side[j], cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s->side_ev[j], cudaEventDisableTiming);
+  }
   if (e == cudaSuccess) e = cudaHostAlloc((void**)&s->host_tab, sizeof(PackedTable) * kTables, cudaHostAllocDefault);
   if (e != cudaSuccess) {
-    if (s->stream) cudaStreamDestroy(s->stream);
-    if (s->done_ev) cudaEventDestroy(s->done_ev);
+    release_streams(s.get());
     return fail(QCL_ERR_CUDA, "server set-up failed: %s", cudaGetErrorString(e));
   }
   memset(s->host_tab, 0, sizeof(PackedTable) * kTables);
@@ -441,8 +485,7 @@ qcl_status qcl_server_create(const qcl_server_desc* d, qcl_server** out) {
   }
   if (e != cudaSuccess) {
     cudaFreeHost(s->host_tab);
-    cudaStreamDestroy(s->stream);
-    cudaEventDestroy(s->done_ev);
+    release_streams(s.get());
     return fail(QCL_ERR_CUDA, "server set-up failed: %s", cudaGetErrorString(e));
   }
   qcl_server* raw = s.release();
@@ -583,8 +626,7 @@ qcl_status qcl_server_destroy(qcl_server* s) {
     if (r->model) qcl_destroy_model(r->model);
   if (s->graph) cudaGraphExecDestroy(s->graph);
   cudaFreeHost(s->host_tab);
-  cudaEventDestroy(s->done_ev);
-  cudaStreamDestroy(s->stream);
+  release_streams(s);
   delete s;
   return qcl::set_error(QCL_OK, "");
 }
