@@ -79,17 +79,6 @@ __device__ __forceinline__ float rcp_approx(float x) {
 // warp reads 32 consecutive floats of one row), both without bank conflicts.
 constexpr int kObsRow = 36;
 
-// Shared-memory float4 load that the compiler may not hoist out of the step
-// loop (hoisting the per-mode coefficients would hold them all in registers).
-__device__ __forceinline__ float4 lds4(const float4* p) {
-  float4 v;
-  const unsigned a = (unsigned)__cvta_generic_to_shared(p);
-  asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];"
-               : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
-               : "r"(a));
-  return v;
-}
-
 // State of one walker (V = float) or two (V = float2) that every holder of a
 // walker keeps identical: weight (compensated pair and exponent), phase
 // (compensated pair), the pair's sigmas, and the closed-form decomposition at

@@ -332,18 +332,4 @@ __device__ __forceinline__ void eigh_warm_sym(const V (&W)[NS][NS], const V (&re
     }
 }
 
-// u_a^T M u_b for a symmetric M given as a full matrix
-template <typename T, int NS>
-__device__ __forceinline__ T bilinear(const T (&M)[NS][NS], const T (&U)[NS][NS], int a, int b) {
-  T acc = T(0);
-#pragma unroll
-  for (int k = 0; k < NS; ++k) {
-    T row = T(0);
-#pragma unroll
-    for (int l = 0; l < NS; ++l) row += M[k][l] * U[l][b];
-    acc += U[k][a] * row;
-  }
-  return acc;
-}
-
 }  // namespace qcl
