@@ -403,12 +403,13 @@ qcl_status qcl_spawn_live(const qcl_model* model, const qcl_ensemble_desc* ens, 
  * arrival order while the caller's device arena has room for their ensemble
  * and observation buffers and fewer than max_active are running; it advances
  * all admitted requests together in rounds of at most quantum_steps steps
- * (and 16 output times) each, packing two-state requests of up to 8 modes
+ * (and 32 output times) each, packing two-state requests of up to 8 modes
  * into shared persistent launches (a CUDA graph replayed every round when
  * use_graphs is set); requests arriving meanwhile join at the next round.  A
  * request's results do not depend on what it is batched with.  Requests run
- * in FP32-bulk precision.  The server owns one CUDA stream and a worker
- * thread; the caller owns the arena (device memory, 256-byte aligned), which
+ * in FP32-bulk precision.  The server owns one CUDA stream (plus eight side
+ * streams on which requests with launches of their own run side by side) and
+ * a worker thread; the caller owns the arena (device memory, 256-byte aligned), which
  * must stay valid until qcl_server_destroy returns. */
 typedef struct qcl_server qcl_server; /* opaque */
 

@@ -228,7 +228,7 @@ struct EnsLayout {
 // Observation buffer: [rows n_out][2Q] FP64 sums, then per-tile partials
 // [chunk][n_tiles][2Q] FP64, then finalised rows [n_out][2Q+3], then fold
 // scratch for block partials.
-constexpr int kChunkOut = 16;      // output times per persistent launch
+constexpr int kChunkOut = 32;      // output times per persistent launch
 constexpr int kFoldBlock = 1024;   // tiles per first-level fold block (power of two)
 
 // Threads per walker of the FP32-bulk kernel for a model of n modes: up to 32

@@ -4,7 +4,7 @@
 // latency percentiles beside throughput.
 //
 // Rounds (continuous batching): every active request advances by one chunk of
-// at most `quantum_steps` steps and 16 output times.  Two-state requests with
+// at most `quantum_steps` steps and 32 output times.  Two-state requests with
 // at most 8 modes are packed, per (mode bucket, model kind), into one
 // persistent launch that reads a device table of (request, tile) work items;
 // that part of a round is a fixed-shape CUDA graph [table uploads, packed
@@ -218,7 +218,7 @@ void finish(qcl_server* s, const std::shared_ptr<Request>& r, int state, const s
   s->cv.notify_all();
 }
 
-// Chunk of request r for this round: steps [cs, ce) with at most 16 output
+// Chunk of request r for this round: steps [cs, ce) with at most 32 output
 // times and at most quantum steps.
 struct Chunk {
   int64_t cs, ce, k_first;
