@@ -541,7 +541,8 @@ __device__ __forceinline__ float4 add4(float4 a, float4 b) {
 template <bool DIA, bool WIDE = true>
 __device__ __forceinline__ void observe_warp(Scal& z, bool active, float* obs_rows, int row,
                                              int row0, int lane, double* red_row) {
-  renorm(z.m, z.mexp);
+  // (no renormalisation of the weight here: the step keeps its mantissa within
+  // [2^-32, 2^32], so scaled contributions and squares stay far inside FP32)
   phase_wrap(z);
   if (DIA) closed_form(z);  // the rotation to the adiabatic basis at the walker's R
   else z.s2 = z.B * z.ir;   // (the same value closed_form gives)

@@ -147,8 +147,7 @@ __device__ __forceinline__ void split_tiles(const BulkParams& bp, const Coef2& c
     auto observe = [&](int slot) {
       if (ROLE == 0) {
         observe_warp<false, false>(z, active, obs_rows, wslot, grp * 32, lane, red[rb][grp]);
-      } else {  // the same weight and phase bookkeeping on every role
-        renorm(z.m, z.mexp);
+      } else {  // the same phase bookkeeping on every role
         phase_wrap(z);
       }
       __syncthreads();
