@@ -276,25 +276,41 @@ __global__ void __launch_bounds__(256) k_spawn_scatter32(void* buf, int64_t cap,
   }
 }
 
-// One thread per family: the family sum X (FP64) of its walkers' contributions
-// (each computed in FP32 with unit weight, then scaled by the walker's exact
-// weight (hi + lo) 2^exp), and X^2, reduced over the tile's 256 families by the
-// fixed tree of the observation kernels.
+// Family observation: for each family the sum X of its walkers' contributions
+// and X^2.  A warp takes 32 families, one at a time: lane l takes the family's
+// walkers l, l + 32, ... (coalesced loads; no lane idles on a small family while
+// another walks a large one).  The family shares one power of two (its largest
+// weight exponent), so each walker's contribution is an FP32 value, summed as a
+// compensated FP32 pair per lane and then over the lanes by a reduce-scatter of
+// pairs, which leaves lanes 2q and 2q + 1 with quantity q; X is rebuilt in FP64
+// from the pair and the exponent exactly, and the even lane accumulates X, the
+// odd lane X^2, over the warp's families in order.  (Accumulating every walker
+// in FP64 kept the FP64 pipe 84 % busy: FP64 is slow on this part.)  The tile's
+// 8 warps are then folded by the fixed tree of the observation kernels.
 template <int KIND, bool DIA>
 __global__ void __launch_bounds__(256) k_spawn_observe32(const BulkParams bp, const Coef2 cf,
                                                          const void* buf, int64_t cap, int64_t n0,
                                                          int set, double* __restrict__ part) {
   __shared__ double red[8][32];
-  const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const SpawnLayout L = SpawnLayout::make(cap, bp.n, n0, QCL_PREC_FP32_BULK);
   const Set32 s = set32((void*)buf, L, set);
   const int64_t* fstart = (const int64_t*)((const char*)buf + L.fstart);
-  double v[32];
-#pragma unroll
-  for (int q = 0; q < 32; ++q) v[q] = 0.0;
-  if (k < n0) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  double T = 0.0;
+  const int64_t f0 = (int64_t)blockIdx.x * 256 + warp * 32;
+#pragma unroll 1
+  for (int f = 0; f < 32; ++f) {
+    const int64_t k = f0 + f;
+    if (k >= n0) break;  // (warp-uniform)
     const int64_t j0 = fstart[k], j1 = fstart[k + 1];
-    for (int64_t j = j0; j < j1; ++j) {
+    int em = -(1 << 28);
+    for (int64_t j = j0 + lane; j < j1; j += 32)
+      if (s.mh[j] != 0.0f) em = max(em, s.me[j]);
+    em = __reduce_max_sync(0xffffffffu, em);
+    f2 acc[16];
+#pragma unroll
+    for (int q = 0; q < 16; ++q) acc[q] = {0.0f, 0.0f};
+    for (int64_t j = j0 + lane; j < j1; j += 32) {
       Scal z;
       z.A = bp.a0;
       z.B = bp.b0;
@@ -309,22 +325,40 @@ __global__ void __launch_bounds__(256) k_spawn_observe32(const BulkParams bp, co
       z.sb = sgn((ab >> 8) & 0xf);
       z.q = DIA ? (int)((ab >> 4) & 3u) : 0;
       z.ph = {s.ph[j], s.pl[j]};
+      const float mh = s.mh[j];
+      const float mm = mh == 0.0f ? 0.0f : (mh + s.ml[j]) * pow2i(s.me[j] - em);
       float c[16];
-      contributions<DIA>(z, 1.0f, c);
-      // (hi + lo) 2^exp exactly: the power of two from its bits (ldexp outside
-      // the normal range)
-      const int e = s.me[j];
-      const double w2 = (double)s.mh[j] + (double)s.ml[j];
-      const double wgt = (e >= -1022 && e <= 1023) ? w2 * __hiloint2double((e + 1023) << 20, 0)
-                                                  : ldexp(w2, e);
+      contributions<DIA>(z, mm, c);
 #pragma unroll
-      for (int q = 0; q < 16; ++q) v[q] = fma((double)c[q], wgt, v[q]);
+      for (int q = 0; q < 16; ++q) {
+        const f2 t = two_sum(acc[q].hi, c[q]);
+        acc[q] = {t.hi, acc[q].lo + t.lo};
+      }
     }
+    // reduce-scatter of the pairs: at the step with offset `off`, the lane with
+    // that bit set keeps the upper half of its values
 #pragma unroll
-    for (int q = 0; q < 16; ++q) v[16 + q] = v[q] * v[q];
+    for (int lev = 0; lev < 4; ++lev) {
+      const int half = 8 >> lev, off = 16 >> lev;
+      const bool upper = (lane & off) != 0;
+#pragma unroll
+      for (int i2 = 0; i2 < half; ++i2) {
+        const f2 snd = upper ? acc[i2] : acc[half + i2];
+        const f2 kp = upper ? acc[half + i2] : acc[i2];
+        const float rh = __shfl_xor_sync(0xffffffffu, snd.hi, off);
+        const float rl = __shfl_xor_sync(0xffffffffu, snd.lo, off);
+        const f2 t = two_sum(kp.hi, rh);
+        acc[i2] = {t.hi, t.lo + (kp.lo + rl)};
+      }
+    }
+    const float rh = __shfl_xor_sync(0xffffffffu, acc[0].hi, 1);
+    const float rl = __shfl_xor_sync(0xffffffffu, acc[0].lo, 1);
+    const f2 t = two_sum(acc[0].hi, rh);
+    const int ex = (em < -(1 << 27)) ? 0 : em;
+    const double X = scaled_double(t.hi, ex) + scaled_double(t.lo + (acc[0].lo + rl), ex);
+    T = (lane & 1) ? fma(X, X, T) : T + X;
   }
-  const double x = warp_transpose_sum<double>(v);
-  red[threadIdx.x >> 5][threadIdx.x & 31] = x;
+  red[warp][(lane & 1) ? 16 + (lane >> 1) : (lane >> 1)] = T;
   __syncthreads();
   if (threadIdx.x < 32)
     part[(int64_t)blockIdx.x * 32 + threadIdx.x] = tile_tree8(&red[0][0], 32, threadIdx.x);
