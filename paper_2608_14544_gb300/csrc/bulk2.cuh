@@ -519,6 +519,14 @@ __device__ __forceinline__ double scaled_double(float x, int ex) {
   return ldexp((double)x, ex);
 }
 
+// The same value on the FP64 pipe (a conversion and one multiply), which the
+// two-state bulk kernels leave idle: their observations take it, sparing the
+// issue slots of the bit construction above.
+__device__ __forceinline__ double scaled_double_fp64(float x, int ex) {
+  return (ex >= -1022 && ex <= 1023) ? (double)x * __hiloint2double((ex + 1023) << 20, 0)
+                                     : ldexp((double)x, ex);
+}
+
 __device__ __forceinline__ float4 sq4(float4 a) {
   return make_float4(a.x * a.x, a.y * a.y, a.z * a.z, a.w * a.w);
 }
@@ -596,7 +604,7 @@ __device__ __forceinline__ void observe_warp(Scal& z, bool active, float* obs_ro
     col = lane;
   }
   const int ex = (ew < -(1 << 27)) ? 0 : ((col < 16) ? ew : 2 * ew);
-  red_row[col] = scaled_double(x, ex);
+  red_row[col] = scaled_double_fp64(x, ex);
 }
 
 __device__ __forceinline__ uint32_t pick_word(const u4& wd, int widx) {
