@@ -207,6 +207,15 @@ qcl_status qcl_reduce_observables(const qcl_model* model, const qcl_ensemble_des
                                   int64_t k0, int64_t n_rows, double* host_out, size_t host_len,
                                   void* stream);
 
+/* The same rows as qcl_reduce_observables, written to device memory dev_out
+ * (dev_len doubles, at least n_rows * (2Q + 3)) by a kernel enqueued on
+ * `stream`, without synchronising or copying to the host: for pipelines that
+ * keep results on the device or read them later. */
+qcl_status qcl_finalize_observables(const qcl_model* model, const qcl_ensemble_desc* ens,
+                                    const void* obs_buf, size_t obs_bytes, int64_t n_out,
+                                    int64_t k0, int64_t n_rows, double* dev_out, size_t dev_len,
+                                    void* stream);
+
 /* Copies the raw FP64 sum rows [k0, k0 + n_rows) (2Q doubles each: sums, then
  * sums of squares) to host memory (synchronises `stream`); used to combine
  * shards. */

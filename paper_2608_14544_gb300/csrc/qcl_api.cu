@@ -575,6 +575,25 @@ qcl_status qcl_reduce_observables(const qcl_model* model, const qcl_ensemble_des
   return ok();
 }
 
+qcl_status qcl_finalize_observables(const qcl_model* model, const qcl_ensemble_desc* ens, const void* obs_buf,
+                                    size_t obs_bytes, int64_t n_out, int64_t k0, int64_t n_rows, double* dev_out,
+                                    size_t dev_len, void* stream) {
+  qcl_status st = check_ens(model, ens);
+  if (st) return st;
+  if (!obs_buf || !dev_out) return fail(QCL_ERR_INVALID_ARG, "obs_buf or dev_out is NULL");
+  if (n_out < 1 || k0 < 0 || n_rows < 0 || k0 + n_rows > n_out) return fail(QCL_ERR_INVALID_ARG, "rows [%lld, %lld) outside [0, %lld)", (long long)k0, (long long)(k0 + n_rows), (long long)n_out);
+  const ObsLayout OL = ObsLayout::make(ens->n_traj, model->ns, n_out, tile_walkers(ens->precision, model->n, model->ns));
+  if (obs_bytes < OL.total) return fail(QCL_ERR_OUT_OF_MEMORY, "obs_buf has %zu bytes, needs %zu", obs_bytes, OL.total);
+  const int nq = OL.q2 / 2;
+  const size_t per = (size_t)(2 * nq + 3);
+  if (dev_len < per * (size_t)n_rows) return fail(QCL_ERR_INVALID_ARG, "dev_out holds %zu doubles, needs %zu", dev_len, per * (size_t)n_rows);
+  if (n_rows == 0) return ok();
+  launch_finalize((const double*)((const char*)obs_buf + OL.off_rows), dev_out, nq, k0, n_rows, ens->n_traj,
+                  model->ns, (cudaStream_t)stream);
+  st = check_launch("finalize");
+  return st ? st : ok();
+}
+
 qcl_status qcl_read_sums(const qcl_model* model, const qcl_ensemble_desc* ens, const void* obs_buf, size_t obs_bytes,
                          int64_t n_out, int64_t k0, int64_t n_rows, double* host_out, size_t host_len, void* stream) {
   qcl_status st = check_ens(model, ens);

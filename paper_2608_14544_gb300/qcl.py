@@ -31,6 +31,7 @@ EXPORTS = [
     "qcl_last_error", "qcl_version", "qcl_set_option", "qcl_launch_count", "qcl_kernel_time",
     "qcl_create_model", "qcl_destroy_model", "qcl_ensemble_bytes", "qcl_obs_bytes",
     "qcl_ensemble_layout", "qcl_sample_initial", "qcl_propagate", "qcl_reduce_observables",
+    "qcl_finalize_observables",
     "qcl_read_sums", "qcl_ensemble_status", "qcl_propagate_noalloc",
     "qcl_server_create", "qcl_server_submit", "qcl_server_poll", "qcl_server_wait",
     "qcl_server_stats", "qcl_server_destroy", "qcl_shard_tile_walkers", "qcl_combine_shards",
@@ -136,6 +137,7 @@ def load(path: str = LIB_PATH):
     lib.qcl_sample_initial.argtypes = [vp, vp, vp, vp, sz, vp]
     lib.qcl_propagate.argtypes = [vp, vp, vp, sz, i64, i64, C.c_double, i32, vp, sz, i64, vp]
     lib.qcl_reduce_observables.argtypes = [vp, vp, vp, sz, i64, i64, i64, vp, sz, vp]
+    lib.qcl_finalize_observables.argtypes = [vp, vp, vp, sz, i64, i64, i64, vp, sz, vp]
     lib.qcl_read_sums.argtypes = [vp, vp, vp, sz, i64, i64, i64, vp, sz, vp]
     lib.qcl_ensemble_status.argtypes = [vp, vp, vp, sz, vp, vp]
     lib.qcl_propagate_noalloc.argtypes = [vp, vp, vp, sz, i64, i64, C.c_double, i32, vp, sz, i64,
@@ -339,6 +341,18 @@ def reduce_observables(model: Model, ens: EnsembleDesc, obs_buf, n_out: int, k0:
     return out
 
 
+def finalize_observables(model: Model, ens: EnsembleDesc, obs_buf, n_out: int, dev_out,
+                         k0: int = 0, n_rows: int | None = None, stream=None):
+    """Means and standard errors into the device tensor dev_out (float64,
+    [n_rows, 2Q + 3]), enqueued on `stream` without synchronising."""
+    n_rows = n_out - k0 if n_rows is None else n_rows
+    _check(load().qcl_finalize_observables(model.handle, C.byref(ens), _dptr(obs_buf),
+                                           obs_buf.numel() * obs_buf.element_size(), n_out, k0,
+                                           n_rows, _dptr(dev_out), dev_out.numel(),
+                                           _stream_ptr(stream)), "qcl_finalize_observables")
+    return dev_out
+
+
 def read_sums(model: Model, ens: EnsembleDesc, obs_buf, n_out: int, k0: int = 0,
               n_rows: int | None = None, stream=None) -> np.ndarray:
     n_rows = n_out - k0 if n_rows is None else n_rows
@@ -392,6 +406,11 @@ class Run:
 
     def observables(self, stream=None) -> np.ndarray:
         return reduce_observables(self.model, self.ens, self.obs_buf, self.n_out, stream=stream)
+
+    def observables_device(self, dev_out, stream=None):
+        """observables() into a device float64 tensor, without a host copy."""
+        return finalize_observables(self.model, self.ens, self.obs_buf, self.n_out, dev_out,
+                                    stream=stream)
 
     def sums(self, stream=None) -> np.ndarray:
         return read_sums(self.model, self.ens, self.obs_buf, self.n_out, stream=stream)

@@ -97,6 +97,10 @@ def test_option_and_null_checks_without_gpu(lib):
     assert lib.qcl_kernel_time(7, None, None) == 1
     b = C.c_size_t()
     assert lib.qcl_ensemble_bytes(None, None, C.byref(b)) == 1
+    # a NULL model is rejected before any device work
+    assert lib.qcl_finalize_observables(None, None, None, C.c_size_t(0), C.c_int64(1),
+                                        C.c_int64(0), C.c_int64(1), None, C.c_size_t(0),
+                                        None) == 1
 
 
 def test_server_validation_without_gpu(lib):

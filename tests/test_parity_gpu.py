@@ -263,6 +263,22 @@ def test_spin_boson_form_needs_b0_above_the_degeneracy_threshold(q):
         assert np.all(run.state()["R"] == 0.0)
 
 
+def test_device_finalisation_matches_host_reduction(q):
+    """qcl_finalize_observables writes the same rows as qcl_reduce_observables,
+    on the device and without synchronising."""
+    import torch
+
+    cfg = wl.config(1)
+    for prec in (q.PREC_FP64, q.PREC_FP32_BULK):
+        m, run = _gpu_run(q, cfg, 3000, prec, 100, 10)
+        run.propagate(100, cfg["dt"], 10)
+        host = run.observables()
+        dev = torch.full(host.shape, float("nan"), dtype=torch.float64, device="cuda")
+        run.observables_device(dev)
+        torch.cuda.synchronize()
+        assert np.array_equal(dev.cpu().numpy(), host)
+
+
 def test_zero_steps_writes_only_initial_row(q):
     cfg = wl.config(1)
     for prec in (q.PREC_FP64, q.PREC_FP32_BULK):
