@@ -614,7 +614,8 @@ def run_ours(args):
                   / (k4_ms / 1e3) / 1e12 if k4_ms > 0 else None,
                   "frac_of_fp32_peak": (float(n4) * c4["n_steps"] * flops_per_traj_step(c4["model"])
                                         / (k4_ms / 1e3) / 1e12 / peak_tflops) if k4_ms > 0 else None,
-                  "kernel": "k_bulk2_split (two warps per 32 walkers)", "launch_shape": shape4,
+                  "kernel": "k_bulk2_split2 (four warps per 32 walker slots, two walkers per "
+                            "thread)", "launch_shape": shape4,
                   "status_flags": st4["flags"]},
         "diabatic": {"workload": "the same 3-mode spin-boson solve in the diabatic "
                                  "representation (propagation only)",

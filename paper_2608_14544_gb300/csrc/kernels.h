@@ -106,6 +106,9 @@ struct BulkParams {
   float p_max;
   uint32_t tmax;       // floor(p_max 2^24)
   float kappa;         // hop_scale
+  // sum_j a_j a_j / M_j, sum_j a_j b_j / M_j, sum_j b_j b_j / M_j over the
+  // FP32 coefficients (the split kernel's one-exchange coupling sums)
+  float caa, cab, cbb;
 };
 
 // The model-dependent scalars of a bulk launch for time step dt (every caller
@@ -141,6 +144,17 @@ inline void bulk_model_scalars(BulkParams& bp, const DevModel& h, double dt) {
   bp.p_max = (float)h.p_max;
   bp.tmax = (uint32_t)std::floor(h.p_max * kP24);
   bp.kappa = (float)h.hop_scale;
+  double caa = 0.0, cab = 0.0, cbb = 0.0;
+  for (int j = 0; j < h.n; ++j) {
+    const double a = (float)h.a[j], b = (float)h.b[j];
+    const double am = (float)(h.a[j] / h.mass[j]), bm = (float)(h.b[j] / h.mass[j]);
+    caa += am * a;
+    cab += am * b;
+    cbb += bm * b;
+  }
+  bp.caa = (float)caa;
+  bp.cab = (float)cab;
+  bp.cbb = (float)cbb;
 }
 
 // FP32 coefficients of an N_s-state model (N_s <= 8, n_modes <= 32): upper
@@ -300,13 +314,18 @@ struct LaunchShape {
 };
 // Walkers per thread a two-state kernel of n modes can take (1 or 2), and the
 // default when none is set.
-inline int max_wpt(int n) { return n <= 8 ? 2 : 1; }
-inline int default_wpt(int n) { return n <= 4 ? 2 : 1; }
+// (n = 65..100 modes: the split kernel with two walkers per thread.)
+inline int max_wpt(int n) { return (n <= 8 || (n > 64 && n <= 100)) ? 2 : 1; }
+inline int default_wpt(int n) { return (n <= 4 || (n > 64 && n <= 100)) ? 2 : 1; }
 
 void launch_sample_f32(const DevModel& host, const SampleParams& sp, void* buf, cudaStream_t st);
 // Returns the persistent grid size used (0 on launch failure).
 int launch_bulk2(const BulkParams& bp, const Coef2& cf, void* buf, double* part,
                  const LaunchShape& ls, cudaStream_t st);
+// The two-walkers-per-thread split kernel (two states, 65..100 modes, a
+// walker's modes over four warps).
+int launch_bulk2_split2(const BulkParams& bp, const Coef2& cf, void* buf, double* part,
+                        const LaunchShape& ls, cudaStream_t st);
 // The diabatic-representation bulk kernel (two states, n <= 32 modes).
 int launch_bulk2_dia(const BulkParams& bp, const Coef2& cf, void* buf, double* part,
                      const LaunchShape& ls, cudaStream_t st);
@@ -315,6 +334,8 @@ int launch_bulk2_dia(const BulkParams& bp, const Coef2& cf, void* buf, double* p
 // capped by ls.grid_cap and by the tile count; per_sm / n_sm cache the
 // occupancy query.
 using BulkFn = void (*)(const BulkParams, const Coef2, void*, double*);
+// The split kernel's instantiation for a model kind and walkers per thread.
+BulkFn bulk2_split2_fn(int kind, int wpt);
 // Walkers per thread actually launched when two are asked for: 2 only if the
 // tiles outnumber the resident block slots of the two-walker kernel fn2 (at
 // ls.blocks_per_sm and ls.grid_cap); a smaller ensemble runs one walker per

@@ -371,7 +371,7 @@ int dispatch_n(const BulkParams& bp, const Coef2& cf, void* buf, double* part,
   // warps per walker must agree with bulk_lanes(n)
   constexpr int MB = KIND == 0 ? 2 : 1;
   if (n <= 64) return run_wide<32, 2, KIND, MB>(bp, cf, buf, part, cap, st);
-  if (n <= 100) return run_wide<50, 2, KIND, 1>(bp, cf, buf, part, cap, st);
+  if (n <= 100) return launch_bulk2_split2(bp, cf, buf, part, cap, st);
   if (n <= 128) return run_wide<32, 4, KIND, MB>(bp, cf, buf, part, cap, st);
   if (n <= 256) return run_wide<64, 4, KIND, 1>(bp, cf, buf, part, cap, st);
   return 0;
@@ -404,6 +404,8 @@ int bulk2_blocks_per_sm(int n, int kind, int repr, int wpt) {
   BulkFn fn = nullptr;
   if (repr == QCL_REPR_DIABATIC) {
     fn = bulk2_dia_fn(n, kind, wpt);
+  } else if (n > 64 && n <= 100) {
+    fn = bulk2_split2_fn(kind, wpt);
   } else if (n <= 8) {
     fn = kind == 0 ? (wpt == 2 ? adiabatic_fn<0, 2>(n) : adiabatic_fn<0, 1>(n))
                    : (wpt == 2 ? adiabatic_fn<1, 2>(n) : adiabatic_fn<1, 1>(n));
@@ -419,7 +421,9 @@ const char* bulk2_variant(int n, int kind) {
   switch (bulk_lanes(n)) {
     case 1: return "k_bulk2: one thread per walker, all modes in registers";
     case 2: return "k_bulk2_split: two warps per 32 walkers";
-    default: return "k_bulk2_split: four warps per 32 walkers";
+    default:
+      return n <= 100 ? "k_bulk2_split2: four warps per 32 walker slots, two walkers per thread"
+                      : "k_bulk2_split: four warps per 32 walkers";
   }
 }
 

@@ -235,7 +235,7 @@ constexpr int kFoldBlock = 1024;   // tiles per first-level fold block (power of
 // modes a thread holds a whole walker in registers; beyond that the walker's
 // modes are split over 2 or 4 warps (one thread of each).  A tile (the unit of
 // the fixed reduction tree) is one block of 256 threads: 256 / that walkers.
-__host__ __device__ inline int bulk_lanes(int n) { return n <= 32 ? 1 : (n <= 100 ? 2 : 4); }
+__host__ __device__ inline int bulk_lanes(int n) { return n <= 32 ? 1 : (n <= 64 ? 2 : 4); }
 __host__ __device__ inline int tile_walkers(int precision, int n, int ns = 2) {
   if (precision == QCL_PREC_FP64) return kTile;
   return ns > 2 ? 128 : kTile / bulk_lanes(n);

@@ -29,8 +29,12 @@ def _cases():
     c6 = copy.deepcopy(c3)
     c6["model"] = wl.random_lvc2(6, 3, 0.1)
     c6["init"] = wl.sb_init(c6["model"], beta=2.0)
+    c4 = wl.config(4)
+    c80 = copy.deepcopy(c3)
+    c80["model"] = wl.random_lvc2(80, 5, 0.1)
+    c80["init"] = wl.sb_init(c80["model"], beta=2.0)
     return [("sb3", c2), ("vib3", c3), ("sb3-diabatic", d2), ("lvc2-6mode", c6),
-            ("lvc4", wl.lvc4_config(2))]
+            ("lvc4", wl.lvc4_config(2)), ("sb100-split", c4), ("lvc2-80mode-split", c80)]
 
 
 @pytest.mark.parametrize("name,cfg", _cases())
