@@ -488,7 +488,11 @@ def run_ours(args):
     c4 = wl.config(4)
     n4 = args.sb100_walkers
     m4 = qcl.Model(c4["model"])
-    shape4 = m4.autotune(c4["dt"], c4["out_stride"], probe_walkers=1 << 18, n_steps=40)
+    # (probe: 2^20 walkers over one full persistent launch of 32 outputs; a
+    # short probe of 40 steps favoured one walker per thread, which is slower
+    # at 2e6 walkers x 4000 steps)
+    shape4 = m4.autotune(c4["dt"], c4["out_stride"], probe_walkers=1 << 20,
+                         n_steps=32 * c4["out_stride"])
     r4 = qcl.Run(m4, n4, c4["seed"], qcl.PREC_FP32_BULK, c4["n_steps"] // c4["out_stride"] + 1,
                  traj_id_offset=rank * n4)
     r4.sample(c4["init"])

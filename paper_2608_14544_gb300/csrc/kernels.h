@@ -322,10 +322,10 @@ void launch_sample_f32(const DevModel& host, const SampleParams& sp, void* buf, 
 // Returns the persistent grid size used (0 on launch failure).
 int launch_bulk2(const BulkParams& bp, const Coef2& cf, void* buf, double* part,
                  const LaunchShape& ls, cudaStream_t st);
-// The two-walkers-per-thread split kernel (two states, 65..100 modes, a
-// walker's modes over four warps).
-int launch_bulk2_split2(const BulkParams& bp, const Coef2& cf, void* buf, double* part,
-                        const LaunchShape& ls, cudaStream_t st);
+// The split kernels (two states, 33..256 modes, a walker's modes over 2 or 4
+// warps; two walkers per thread for 65..100 modes).
+int launch_bulk2_split(const BulkParams& bp, const Coef2& cf, void* buf, double* part,
+                       const LaunchShape& ls, cudaStream_t st);
 // The diabatic-representation bulk kernel (two states, n <= 32 modes).
 int launch_bulk2_dia(const BulkParams& bp, const Coef2& cf, void* buf, double* part,
                      const LaunchShape& ls, cudaStream_t st);
@@ -334,8 +334,8 @@ int launch_bulk2_dia(const BulkParams& bp, const Coef2& cf, void* buf, double* p
 // capped by ls.grid_cap and by the tile count; per_sm / n_sm cache the
 // occupancy query.
 using BulkFn = void (*)(const BulkParams, const Coef2, void*, double*);
-// The split kernel's instantiation for a model kind and walkers per thread.
-BulkFn bulk2_split2_fn(int kind, int wpt);
+// The split kernel a launch of (n modes, kind, walkers per thread) uses.
+BulkFn bulk2_split_fn(int n, int kind, int wpt);
 // Walkers per thread actually launched when two are asked for: 2 only if the
 // tiles outnumber the resident block slots of the two-walker kernel fn2 (at
 // ls.blocks_per_sm and ls.grid_cap); a smaller ensemble runs one walker per

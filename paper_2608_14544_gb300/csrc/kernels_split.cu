@@ -1,12 +1,16 @@
-// kernels_split.cu -- many-mode two-state models (65..100 modes) on the FP32
-// bulk path with two walkers per thread.  A walker's modes are split over four
-// warps (warp role r holds modes r NPL .. r NPL + NPL - 1 of the same 32 walker
-// slots), and each thread carries the walker in that slot of two consecutive
-// 64-walker tiles as the two lanes of packed FP32x2 values: every mode FMA of a
-// step (half kicks, drift, collective sums) is one FFMA2 for both walkers, with
-// the model coefficients as broadcast constant-bank operands.  With one walker
-// per thread (small ensembles) the same code runs on scalar lanes and gives the
-// same bits.
+// kernels_split.cu -- many-mode two-state models (33..256 modes) on the FP32
+// bulk path.  A walker's modes are split over L warps (warp role r holds modes
+// r NPL .. r NPL + NPL - 1 of the same 32 walker slots); a tile is 256 / L
+// walkers.  Coefficient indices are warp-uniform: compile-time constant-bank
+// operands with one copy of the unrolled code per role, or, where those copies
+// would not fit the instruction cache, one copy for all roles reading the
+// role's coefficients from shared memory (split_shared below).  For 65..100 modes (four roles of 25
+// modes) each thread carries the walker in its slot of two consecutive tiles as
+// the two lanes of packed FP32x2 values: every mode FMA of a step (half kicks,
+// drift, collective sums) is one FFMA2 for both walkers, with the model
+// coefficients as broadcast constant-bank operands.  With one walker per
+// thread (small ensembles, or more modes per warp) the same code runs on
+// scalar lanes and gives the same bits.
 //
 // One exchange per step.  The coupling sums need the momentum after the second
 // half kick, P'' = q - hu2 a - hv2 b with q = P' - (dt/2)(k R' + s) and
@@ -41,16 +45,70 @@ struct XBuf {
   XVec<V, NV> x[L][BW];
 };
 
-template <int NPL, int L, int KIND, int ROLE, int WPT>
+// Warp-to-role mapping.  false: role = warp / G, so a walker group's L role
+// warps sit on two of the four schedulers; true: role = warp % L, one role per
+// scheduler (each scheduler then fetches one role's unrolled code).  Measured
+// at 40-200 modes, both forms: the first is as fast or faster everywhere but
+// on the 200-mode spin-boson model (7 %).
+template <int NPL, int L, int KIND, int WPT>
+constexpr bool split_rps() {
+  return false;
+}
+
+// Where the coefficients come from.  false: constant-bank operands at
+// compile-time offsets, one copy of the unrolled code per role; true: one
+// copy of the code for all roles (the role is a runtime value), the role's
+// coefficients loaded from shared memory (two broadcast loads per mode and
+// kick).  The unrolled code of all roles has to fit the SM's instruction
+// cache: four roles of the general form, or of 64 modes, do not (measured,
+// 1e6 walkers: 100-mode general model 8.9e9 -> 1.35e10 walker-steps/s with one
+// copy, 128 modes 3.3e9 -> 9.4e9, 200 modes 1.2e9 -> 5.5e9, 200-mode
+// spin-boson 2.6e9 -> 7.5e9), while the spin-boson form of at most 32 modes
+// per warp, and the general form on two roles, run faster with constant
+// operands (100-mode spin-boson 2.83e10 against 2.06e10).
+template <int NPL, int L, int KIND, int WPT>
+constexpr bool split_shared() {
+  return (KIND == 1 && L == 4) || NPL >= 64;
+}
+
+// One mode's coefficients: c0 = (dt/2 k, dt/M, a/M, b/M), c1 = (a, b, dt/2 s, 0).
+struct ModeCoef {
+  float hk, dtm, am, bm, a, b, hs;
+};
+
+template <int NPL, int L, int KIND, int ROLE, int WPT, bool SH>
 __device__ __forceinline__ void split_tiles_v(const BulkParams& bp, const Coef2& cf, W32& ws,
                                               double* __restrict__ part, void* xbuf,
                                               double (*red)[8][32], float* obs_rows,
-                                              unsigned int& n_deg) {
+                                              unsigned int& n_deg, const float4* scoef,
+                                              int role_rt) {
   using V = std::conditional_t<WPT == 2, float2, float>;
   using U = typename Lanes<V>::U;
   constexpr int BW = 256 / L;  // walkers per tile
   constexpr int G = BW / 32;   // groups (of 32 walkers) per tile
-  constexpr int OFF = ROLE * NPL;
+  const int role = SH ? role_rt : ROLE;
+  const int OFF = role * NPL;
+  // mode t's coefficients (all of them, or only a and b for the second kick)
+  auto coef = [&](int t) {
+    ModeCoef c;
+    if constexpr (SH) {
+      const float4 c0 = scoef[2 * (OFF + t)], c1 = scoef[2 * (OFF + t) + 1];
+      c = {c0.x, c0.y, c0.z, c0.w, c1.x, c1.y, c1.z};
+    } else {
+      c = {cf.hk[ROLE * NPL + t], cf.dtm[ROLE * NPL + t], cf.am[ROLE * NPL + t],
+           cf.bm[ROLE * NPL + t], cf.a[ROLE * NPL + t],  cf.b[ROLE * NPL + t],
+           cf.hs[ROLE * NPL + t]};
+    }
+    return c;
+  };
+  auto coef_ab = [&](int t) {
+    if constexpr (SH) {
+      const float2 ab = *reinterpret_cast<const float2*>(&scoef[2 * (OFF + t) + 1]);
+      return ab;
+    } else {
+      return make_float2(cf.a[ROLE * NPL + t], cf.b[ROLE * NPL + t]);
+    }
+  };
   constexpr int NV = KIND == 1 ? 4 : 2;
   using X = XBuf<V, L, BW, NV>;
   using XV = XVec<V, NV>;
@@ -60,7 +118,7 @@ __device__ __forceinline__ void split_tiles_v(const BulkParams& bp, const Coef2&
   X* const x = reinterpret_cast<X*>(xbuf);
   const int64_t nt = bp.n_traj;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int grp = warp % G;           // this warp's walker group in the tile
+  const int grp = split_rps<NPL, L, KIND, WPT>() ? warp / L : warp % G;  // walker group in the tile
   const int wslot = grp * 32 + lane;  // walker slot within the tile
   const int bar_id = 1 + grp;         // named barrier of the group's L warps
   int rb = 0;
@@ -100,7 +158,7 @@ __device__ __forceinline__ void split_tiles_v(const BulkParams& bp, const Coef2&
 
     // sums over the L roles of per-role partials, in role order
     auto exchange = [&](X& xb, XV& v) {
-      xb.x[ROLE][wslot] = v;
+      xb.x[role][wslot] = v;
       group_sync(bar_id, 32 * L);
       v = xb.x[0][wslot];
 #pragma unroll
@@ -117,8 +175,9 @@ __device__ __forceinline__ void split_tiles_v(const BulkParams& bp, const Coef2&
       for (int c = 0; c < NV; ++c) v.v[c] = splat<V>(0.0f);
 #pragma unroll
       for (int t = 0; t < NPL; ++t) {
-        v.v[0] = vfma(splat<V>(cf.a[OFF + t]), w.R[t], v.v[0]);
-        if (KIND == 1) v.v[2] = vfma(splat<V>(cf.b[OFF + t]), w.R[t], v.v[2]);
+        const float2 ab = coef_ab(t);
+        v.v[0] = vfma(splat<V>(ab.x), w.R[t], v.v[0]);
+        if (KIND == 1) v.v[2] = vfma(splat<V>(ab.y), w.R[t], v.v[2]);
       }
       exchange(x[0], v);
       z.A = vadd(splat<V>(bp.a0), v.v[0]);
@@ -128,7 +187,7 @@ __device__ __forceinline__ void split_tiles_v(const BulkParams& bp, const Coef2&
 
     // observation by the role-0 warps, lane by lane, then the tiles' trees
     auto observe = [&](int slot) {
-      if (ROLE == 0) {
+      if (role == 0) {
 #pragma unroll
         for (int k = 0; k < WPT; ++k) {
           Scal zk = lane_of(z, k);
@@ -170,19 +229,20 @@ __device__ __forceinline__ void split_tiles_v(const BulkParams& bp, const Coef2&
       for (int t = 0; t < NPL; ++t) {
         // first half kick at R_n, drift, then the R_{n+1} terms of the second
         // half kick (q); its coupling terms wait for the exchange
-        V p = vfma(splat<V>(-cf.hk[OFF + t]), w.R[t], w.P[t]);
-        if (KIND == 1) p = vadd(p, splat<V>(-cf.hs[OFF + t]));
-        p = vfma(hu, splat<V>(-cf.a[OFF + t]), p);
-        if (KIND == 1) p = vfma(hv, splat<V>(-cf.b[OFF + t]), p);
-        const V r = vfma(splat<V>(cf.dtm[OFF + t]), p, w.R[t]);
+        const ModeCoef c = coef(t);
+        V p = vfma(splat<V>(-c.hk), w.R[t], w.P[t]);
+        if (KIND == 1) p = vadd(p, splat<V>(-c.hs));
+        p = vfma(hu, splat<V>(-c.a), p);
+        if (KIND == 1) p = vfma(hv, splat<V>(-c.b), p);
+        const V r = vfma(splat<V>(c.dtm), p, w.R[t]);
         w.R[t] = r;
-        v.v[0] = vfma(splat<V>(cf.a[OFF + t]), r, v.v[0]);
-        if (KIND == 1) v.v[2] = vfma(splat<V>(cf.b[OFF + t]), r, v.v[2]);
-        V qm = vfma(splat<V>(-cf.hk[OFF + t]), r, p);
-        if (KIND == 1) qm = vadd(qm, splat<V>(-cf.hs[OFF + t]));
+        v.v[0] = vfma(splat<V>(c.a), r, v.v[0]);
+        if (KIND == 1) v.v[2] = vfma(splat<V>(c.b), r, v.v[2]);
+        V qm = vfma(splat<V>(-c.hk), r, p);
+        if (KIND == 1) qm = vadd(qm, splat<V>(-c.hs));
         w.P[t] = qm;
-        v.v[1] = vfma(splat<V>(cf.am[OFF + t]), qm, v.v[1]);
-        if (KIND == 1) v.v[3] = vfma(splat<V>(cf.bm[OFF + t]), qm, v.v[3]);
+        v.v[1] = vfma(splat<V>(c.am), qm, v.v[1]);
+        if (KIND == 1) v.v[3] = vfma(splat<V>(c.bm), qm, v.v[3]);
       }
       const V r_old = z.r;
       exchange(x[1 + xsel], v);
@@ -193,8 +253,9 @@ __device__ __forceinline__ void split_tiles_v(const BulkParams& bp, const Coef2&
       const V hu2 = vmul(hsab, z.c2), hv2 = vmul(hsab, z.s2);
 #pragma unroll
       for (int t = 0; t < NPL; ++t) {  // coupling terms of the second half kick at R_{n+1}
-        V p = vfma(hu2, splat<V>(-cf.a[OFF + t]), w.P[t]);
-        if (KIND == 1) p = vfma(hv2, splat<V>(-cf.b[OFF + t]), p);
+        const float2 ab = coef_ab(t);
+        V p = vfma(hu2, splat<V>(-ab.x), w.P[t]);
+        if (KIND == 1) p = vfma(hv2, splat<V>(-ab.y), p);
         w.P[t] = p;
       }
       // coupling sums at P_{n+1}: the q sums less the kick's coupling terms
@@ -230,7 +291,7 @@ __device__ __forceinline__ void split_tiles_v(const BulkParams& bp, const Coef2&
           ws.R[(int64_t)(OFF + t) * nt + i] = ln(w.R[t], k);
           ws.P[(int64_t)(OFF + t) * nt + i] = ln(w.P[t], k);
         }
-      if (ROLE == 0) {
+      if (role == 0) {
         const float mh = ln(z.m.hi, k), ph = ln(z.ph.hi, k);
         ws.mh[i] = mh;
         ws.ml[i] = ln(z.m.lo, k);
@@ -249,9 +310,10 @@ __device__ __forceinline__ void split_tiles_v(const BulkParams& bp, const Coef2&
 
 }  // namespace
 
-template <int NPL, int L, int KIND, int WPT>
-__global__ void __launch_bounds__(256, 1)
+template <int NPL, int L, int KIND, int WPT, int MINB>
+__global__ void __launch_bounds__(256, MINB)
     k_bulk2_split2(const BulkParams bp, const Coef2 cf, void* buf, double* __restrict__ part) {
+  static_assert(L == 2 || L == 4, "two or four roles");
   using V = std::conditional_t<WPT == 2, float2, float>;
   constexpr int BW = 256 / L;
   // exchange buffers: the sums at tile start and two alternating for the steps
@@ -263,20 +325,34 @@ __global__ void __launch_bounds__(256, 1)
     if (blockIdx.x == 0 && threadIdx.x == 0) atomicOr(&ws.hdr->flags, QCL_FLAG_STEP_MISMATCH);
     return;
   }
-  static_assert(L == 4, "four roles");
   unsigned int n_deg = 0;
   // role = warp / G.  (Measured: role = warp % L, which puts one role's warps
   // on each scheduler, is 6 % slower with two walkers per thread -- longer
   // barrier waits -- though 11 % faster with one.)
-  const int role = (threadIdx.x >> 5) / (BW / 32);
-  if (role == 0)
-    split_tiles_v<NPL, L, KIND, 0, WPT>(bp, cf, ws, part, xbuf, red, obs_rows, n_deg);
-  else if (role == 1)
-    split_tiles_v<NPL, L, KIND, 1, WPT>(bp, cf, ws, part, xbuf, red, obs_rows, n_deg);
-  else if (role == 2)
-    split_tiles_v<NPL, L, KIND, 2, WPT>(bp, cf, ws, part, xbuf, red, obs_rows, n_deg);
-  else
-    split_tiles_v<NPL, L, KIND, 3, WPT>(bp, cf, ws, part, xbuf, red, obs_rows, n_deg);
+  const int role = split_rps<NPL, L, KIND, WPT>() ? (threadIdx.x >> 5) % L : (threadIdx.x >> 5) / (BW / 32);
+  if constexpr (split_shared<NPL, L, KIND, WPT>()) {
+    __shared__ float4 scoef[2 * L * NPL];
+    for (int i = threadIdx.x; i < L * NPL; i += blockDim.x) {
+      scoef[2 * i] = make_float4(cf.hk[i], cf.dtm[i], cf.am[i], cf.bm[i]);
+      scoef[2 * i + 1] = make_float4(cf.a[i], cf.b[i], cf.hs[i], 0.0f);
+    }
+    __syncthreads();
+    split_tiles_v<NPL, L, KIND, 0, WPT, true>(bp, cf, ws, part, xbuf, red, obs_rows, n_deg, scoef,
+                                              role);
+  } else {
+    if (role == 0)
+      split_tiles_v<NPL, L, KIND, 0, WPT, false>(bp, cf, ws, part, xbuf, red, obs_rows, n_deg,
+                                                 nullptr, 0);
+    else if (role == 1)
+      split_tiles_v<NPL, L, KIND, 1, WPT, false>(bp, cf, ws, part, xbuf, red, obs_rows, n_deg,
+                                                 nullptr, 1);
+    else if (role == 2)
+      split_tiles_v<NPL, L, KIND, 2 % L, WPT, false>(bp, cf, ws, part, xbuf, red, obs_rows, n_deg,
+                                                     nullptr, 2);
+    else
+      split_tiles_v<NPL, L, KIND, 3 % L, WPT, false>(bp, cf, ws, part, xbuf, red, obs_rows, n_deg,
+                                                     nullptr, 3);
+  }
   if (n_deg && role == 0) {  // every role counted the same walkers
     atomicAdd(&ws.hdr->n_degenerate, (unsigned long long)n_deg);
     atomicOr(&ws.hdr->flags, QCL_FLAG_DEGENERATE);
@@ -284,31 +360,65 @@ __global__ void __launch_bounds__(256, 1)
 }
 
 namespace {
-template <int KIND>
-int run_split2(const BulkParams& bp, const Coef2& cf, void* buf, double* part,
-               const LaunchShape& ls, cudaStream_t st) {
-  constexpr int NPL = 25, L = 4;
+// Resident blocks per SM the launch bounds ask for: two for the spin-boson
+// form with at most 32 modes per warp and one walker per thread (the state fits
+// 128 registers), else one.
+template <int NPL, int KIND, int WPT>
+constexpr int split_minb() {
+  return (KIND == 0 && NPL <= 32 && WPT == 1) ? 2 : 1;
+}
+
+template <int NPL, int L, int KIND, int WPT>
+BulkFn split_fn() {
+  return k_bulk2_split2<NPL, L, KIND, WPT, split_minb<NPL, KIND, WPT>()>;
+}
+
+// Two walkers per thread where a warp holds at most 25 modes (twice its modes'
+// R and P must fit the registers); otherwise one.
+template <int NPL, int L, int KIND>
+int run_split(const BulkParams& bp, const Coef2& cf, void* buf, double* part,
+              const LaunchShape& ls, cudaStream_t st) {
   static int per_sm[2] = {-1, -1}, n_sm[2] = {0, 0};
-  int wpt = (ls.wpt > 0 ? ls.wpt : default_wpt(65)) >= 2 ? 2 : 1;
-  if (wpt == 2) wpt = bulk_wpt(k_bulk2_split2<NPL, L, KIND, 2>, per_sm[1], n_sm[1], bp.n_tiles, ls);
-  if (wpt == 2)
-    return run_bulk_kernel(k_bulk2_split2<NPL, L, KIND, 2>, per_sm[1], n_sm[1], bp, cf, buf, part,
-                           ls, 2, st);
-  return run_bulk_kernel(k_bulk2_split2<NPL, L, KIND, 1>, per_sm[0], n_sm[0], bp, cf, buf, part,
-                         ls, 1, st);
+  if constexpr (NPL <= 25) {
+    int wpt = (ls.wpt > 0 ? ls.wpt : 2) >= 2 ? 2 : 1;
+    if (wpt == 2) wpt = bulk_wpt(split_fn<NPL, L, KIND, 2>(), per_sm[1], n_sm[1], bp.n_tiles, ls);
+    if (wpt == 2)
+      return run_bulk_kernel(split_fn<NPL, L, KIND, 2>(), per_sm[1], n_sm[1], bp, cf, buf, part,
+                             ls, 2, st);
+  }
+  return run_bulk_kernel(split_fn<NPL, L, KIND, 1>(), per_sm[0], n_sm[0], bp, cf, buf, part, ls,
+                         1, st);
+}
+
+// warps per walker must agree with bulk_lanes(n)
+template <int KIND>
+int dispatch_split(const BulkParams& bp, const Coef2& cf, void* buf, double* part,
+                   const LaunchShape& ls, cudaStream_t st) {
+  const int n = bp.n;
+  if (n <= 64) return run_split<32, 2, KIND>(bp, cf, buf, part, ls, st);
+  if (n <= 100) return run_split<25, 4, KIND>(bp, cf, buf, part, ls, st);
+  if (n <= 128) return run_split<32, 4, KIND>(bp, cf, buf, part, ls, st);
+  if (n <= 256) return run_split<64, 4, KIND>(bp, cf, buf, part, ls, st);
+  return 0;
 }
 }  // namespace
 
-int launch_bulk2_split2(const BulkParams& bp, const Coef2& cf, void* buf, double* part,
-                        const LaunchShape& ls, cudaStream_t st) {
-  return bp.kind == 0 ? run_split2<0>(bp, cf, buf, part, ls, st)
-                      : run_split2<1>(bp, cf, buf, part, ls, st);
+int launch_bulk2_split(const BulkParams& bp, const Coef2& cf, void* buf, double* part,
+                       const LaunchShape& ls, cudaStream_t st) {
+  return bp.kind == 0 ? dispatch_split<0>(bp, cf, buf, part, ls, st)
+                      : dispatch_split<1>(bp, cf, buf, part, ls, st);
 }
 
-BulkFn bulk2_split2_fn(int kind, int wpt) {
-  constexpr int NPL = 25, L = 4;
-  if (kind == 0) return wpt == 2 ? k_bulk2_split2<NPL, L, 0, 2> : k_bulk2_split2<NPL, L, 0, 1>;
-  return wpt == 2 ? k_bulk2_split2<NPL, L, 1, 2> : k_bulk2_split2<NPL, L, 1, 1>;
+BulkFn bulk2_split_fn(int n, int kind, int wpt) {
+  const bool two = wpt == 2 && n > 64 && n <= 100;
+  if (n <= 64) return kind == 0 ? split_fn<32, 2, 0, 1>() : split_fn<32, 2, 1, 1>();
+  if (n <= 100) {
+    if (kind == 0) return two ? split_fn<25, 4, 0, 2>() : split_fn<25, 4, 0, 1>();
+    return two ? split_fn<25, 4, 1, 2>() : split_fn<25, 4, 1, 1>();
+  }
+  if (n <= 128) return kind == 0 ? split_fn<32, 4, 0, 1>() : split_fn<32, 4, 1, 1>();
+  if (n <= 256) return kind == 0 ? split_fn<64, 4, 0, 1>() : split_fn<64, 4, 1, 1>();
+  return nullptr;
 }
 
 }  // namespace qcl
