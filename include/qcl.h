@@ -184,10 +184,12 @@ qcl_status qcl_sample_initial(const qcl_model* model, const qcl_ensemble_desc* e
  * step0 < s <= step0 + n_steps (and at s = 0 when step0 == 0) it writes output
  * row k = s / out_stride (k < n_out) of obs_buf: the FP64 sums over walkers of
  * every observable contribution and of its square, added in a fixed tree
- * (32-walker groups, 256-walker tiles, tiles in index order), so that results
- * do not depend on the launch shape and two calls give the same bits as one.
- * FP64 ensembles launch one kernel per step; FP32-bulk ensembles run a
- * persistent kernel over 256-walker tiles with state held in registers. */
+ * (32-walker groups, tiles of qcl_shard_tile_walkers walkers, tiles in index
+ * order), so that results do not depend on the launch shape and two calls give
+ * the same bits as one.  FP64 ensembles launch one kernel per step; FP32-bulk
+ * ensembles run a persistent kernel over the tiles with state held in
+ * registers (models of 33..256 modes split each walker's modes over 2 or 4
+ * warps, so their tiles hold 128 or 64 walkers). */
 qcl_status qcl_propagate(const qcl_model* model, const qcl_ensemble_desc* ens, void* ens_buf,
                          size_t ens_bytes, int64_t step0, int64_t n_steps, double dt,
                          int32_t out_stride, void* obs_buf, size_t obs_bytes, int64_t n_out,
@@ -313,8 +315,9 @@ qcl_status qcl_measure_peak(int32_t which, double* flops_per_s, void* stream);
  *                       runs 1, so that every slot gets a tile.
  *   blocks_per_sm       resident blocks per SM of the persistent grid (0 = the
  *                       kernel's occupancy limit; larger values are clamped).
- * Threads per block are fixed at 256: the block is the reduction tile, whose
- * size defines the summation tree of every observable.
+ * Threads per block are fixed at 256: a block's threads hold one reduction
+ * tile (or two, with two walkers per thread), whose size defines the
+ * summation tree of every observable.
  * ------------------------------------------------------------------------ */
 typedef struct {
   int32_t walkers_per_thread;
