@@ -47,8 +47,12 @@ def _compare(a, b, n_rows_needed=4):
     assert diff[resolved].max() < 1e-3
 
 
+# (33, 65, 101 and 129 modes: the first model of each split-kernel range --
+# two roles; four roles of 25 with two walkers per thread; four of 32; four of
+# 64 with shared-memory coefficients)
 @pytest.mark.parametrize("n_modes,kind", [(100, "sb"), (40, "lvc"), (100, "lvc"), (120, "lvc"),
-                                          (200, "sb")])
+                                          (200, "sb"), (33, "sb"), (65, "lvc"), (101, "sb"),
+                                          (129, "lvc")])
 def test_manymode_fp32_matches_fp64(q, n_modes, kind):
     if kind == "sb":
         w, c = wl.ohmic_modes(n_modes, 0.25, 5.0)
