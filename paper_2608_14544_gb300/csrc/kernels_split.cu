@@ -4,23 +4,23 @@
 // walkers.  Coefficient indices are warp-uniform: compile-time constant-bank
 // operands with one copy of the unrolled code per role, or, where those copies
 // would not fit the instruction cache, one copy for all roles reading the
-// role's coefficients from shared memory (split_shared below).  For 65..100 modes (four roles of 25
-// modes) each thread carries the walker in its slot of two consecutive tiles as
-// the two lanes of packed FP32x2 values: every mode FMA of a step (half kicks,
-// drift, collective sums) is one FFMA2 for both walkers, with the model
-// coefficients as broadcast constant-bank operands.  With one walker per
-// thread (small ensembles, or more modes per warp) the same code runs on
+// role's coefficients from shared memory (split_shared below).  For 65..100
+// modes (four roles of 25 modes) each thread carries the walker in its slot of
+// two consecutive tiles as the two lanes of packed FP32x2 values: every mode
+// FMA of a step (half kicks, drift, collective sums) is one FFMA2 for both
+// walkers, with the model coefficients as broadcast operands.  With one walker
+// per thread (small ensembles, or more modes per warp) the same code runs on
 // scalar lanes and gives the same bits.
 //
 // One exchange per step.  The coupling sums need the momentum after the second
 // half kick, P'' = q - hu2 a - hv2 b with q = P' - (dt/2)(k R' + s) and
 // hu2, hv2 known only once a(R'), b(R') are summed over all modes.  So each
 // role sums a_j R'_j, b_j R'_j and the coupling sums over q,
-// sum_j (a_j / M_j) q_j, sum_j (b_j / M_j) q_j, in its mode loop; the four
-// partials of the four roles are exchanged together through shared memory under
-// one named barrier of the group's warps and added in role order (every role
-// then holds the same bits of the scalar state), and the second half kick's
-// terms enter the coupling sums through the model constants
+// sum_j (a_j / M_j) q_j, sum_j (b_j / M_j) q_j, in its mode loop; the L roles'
+// partials are exchanged together through shared memory under one named
+// barrier of the group's warps and added in role order (every role then holds
+// the same bits of the scalar state), and the second half kick's terms enter
+// the coupling sums through the model constants
 // sum_j a_j a_j / M_j, sum_j a_j b_j / M_j, sum_j b_j b_j / M_j:
 //   Av = Xa - hu2 caa - hv2 cab,  Bv = Xb - hu2 cab - hv2 cbb.
 // The momenta themselves are updated exactly as in the two-exchange form.
