@@ -326,10 +326,9 @@ __global__ void __launch_bounds__(256, MINB)
     return;
   }
   unsigned int n_deg = 0;
-  // role = warp / G.  (Measured: role = warp % L, which puts one role's warps
-  // on each scheduler, is 6 % slower with two walkers per thread -- longer
-  // barrier waits -- though 11 % faster with one.)
-  const int role = split_rps<NPL, L, KIND, WPT>() ? (threadIdx.x >> 5) % L : (threadIdx.x >> 5) / (BW / 32);
+  // (the warp-to-role mapping: split_rps above)
+  const int warp = threadIdx.x >> 5;
+  const int role = split_rps<NPL, L, KIND, WPT>() ? warp % L : warp / (BW / 32);
   if constexpr (split_shared<NPL, L, KIND, WPT>()) {
     __shared__ float4 scoef[2 * L * NPL];
     for (int i = threadIdx.x; i < L * NPL; i += blockDim.x) {
