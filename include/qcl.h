@@ -196,7 +196,11 @@ qcl_status qcl_propagate(const qcl_model* model, const qcl_ensemble_desc* ens, v
                          void* stream);
 
 /* Ensemble averages (divide by n_traj) of the output rows [k0, k0 + n_rows),
- * computed on the device and copied to host_out (synchronises `stream`).
+ * computed on the device and copied to host_out (synchronises `stream`): the
+ * diabatic and adiabatic density matrices whose averages the paper reduces
+ * (Sec. II B) and plots (P_ad, Sec. III).  QCL_ERR_INVALID_ARG for a NULL
+ * pointer or rows outside [0, n_out); QCL_ERR_OUT_OF_MEMORY when obs_bytes or
+ * host_len is below what the layout needs.
  * Per row, with NS = n_states and Q = 4 NS^2 quantities:
  *   [0, Q)      means: q = 2(i NS + j) + c, diabatic rho_ij (c = 0 real, 1 imag);
  *               q = 2 NS^2 + 2(a NS + b) + c, adiabatic rho_ab
@@ -210,9 +214,11 @@ qcl_status qcl_reduce_observables(const qcl_model* model, const qcl_ensemble_des
                                   void* stream);
 
 /* The same rows as qcl_reduce_observables, written to device memory dev_out
- * (dev_len doubles, at least n_rows * (2Q + 3)) by a kernel enqueued on
- * `stream`, without synchronising or copying to the host: for pipelines that
- * keep results on the device or read them later. */
+ * (dev_len doubles, at least n_rows * (2Q + 3); caller-owned) by a kernel
+ * enqueued on `stream`, without synchronising or copying to the host: for
+ * pipelines that keep results on the device or read them later.  The same
+ * argument checks and error codes as qcl_reduce_observables (dev_len in place
+ * of host_len). */
 qcl_status qcl_finalize_observables(const qcl_model* model, const qcl_ensemble_desc* ens,
                                     const void* obs_buf, size_t obs_bytes, int64_t n_out,
                                     int64_t k0, int64_t n_rows, double* dev_out, size_t dev_len,
