@@ -199,8 +199,9 @@ qcl_status qcl_propagate(const qcl_model* model, const qcl_ensemble_desc* ens, v
  * computed on the device and copied to host_out (synchronises `stream`): the
  * diabatic and adiabatic density matrices whose averages the paper reduces
  * (Sec. II B) and plots (P_ad, Sec. III).  QCL_ERR_INVALID_ARG for a NULL
- * pointer or rows outside [0, n_out); QCL_ERR_OUT_OF_MEMORY when obs_bytes or
- * host_len is below what the layout needs.
+ * pointer, an invalid ensemble descriptor, rows outside [0, n_out) or host_len
+ * below n_rows (2Q + 3); QCL_ERR_OUT_OF_MEMORY when obs_bytes is below
+ * qcl_obs_bytes for this ensemble and n_out.
  * Per row, with NS = n_states and Q = 4 NS^2 quantities:
  *   [0, Q)      means: q = 2(i NS + j) + c, diabatic rho_ij (c = 0 real, 1 imag);
  *               q = 2 NS^2 + 2(a NS + b) + c, adiabatic rho_ab
