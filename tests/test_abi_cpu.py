@@ -132,3 +132,31 @@ def test_measure_peak_validation_without_gpu(lib):
     v = C.c_double()
     assert lib.qcl_measure_peak(0, None, None) == 1
     assert lib.qcl_measure_peak(7, C.byref(v), None) == 1
+
+
+def test_product_path_fails_loudly_without_the_cuda_library_or_device():
+    # no CPU fallback: a missing library is an ImportError, and without a GPU
+    # the first call that needs device memory raises with the CUDA message
+    import subprocess
+    import sys
+
+    code = (
+        "from paper_2608_14544_gb300 import qcl, workloads as wl\n"
+        "try:\n"
+        "    qcl.load('/nonexistent/libqcl.so')\n"
+        "    print('LOADED')\n"
+        "except ImportError as e:\n"
+        "    print('IMPORT-ERROR', 'no CPU fallback' in str(e))\n"
+        "import torch\n"
+        "if not torch.cuda.is_available():\n"
+        "    try:\n"
+        "        qcl.Model(wl.config(2)['model'])\n"
+        "        print('MODEL')\n"
+        "    except qcl.QclError as e:\n"
+        "        print('QCL-ERROR', 'CUDA' in str(e))\n")
+    out = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True,
+                         timeout=300, cwd=os.path.dirname(os.path.dirname(__file__)))
+    assert out.returncode == 0, out.stderr[-2000:]
+    assert "IMPORT-ERROR True" in out.stdout
+    assert "LOADED" not in out.stdout and "MODEL" not in out.stdout.split()
+    assert "QCL-ERROR False" not in out.stdout
