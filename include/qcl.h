@@ -243,6 +243,22 @@ qcl_status qcl_read_sums(const qcl_model* model, const qcl_ensemble_desc* ens,
 qcl_status qcl_ensemble_layout(const qcl_model* model, const qcl_ensemble_desc* ens,
                                size_t offsets[11]);
 
+/* Checkpoint restore (no counterpart in the paper): makes ens_buf an
+ * ensemble at absolute step `step` from walker arrays the caller has written
+ * into it at the offsets of qcl_ensemble_layout -- the arrays of a saved
+ * ensemble of the same model, walker count and precision, or another
+ * precision's state converted by the caller (FP32 bulk: R, P rounded to FP32,
+ * weight as (hi + lo) 2^e, phase as hi + lo).  Writes the header (identity and
+ * step; status flags and counters cleared) by a kernel enqueued on `stream`;
+ * the walker arrays are not read or changed.  The next qcl_propagate passes
+ * step0 = step and continues each walker's random stream at that step, so a
+ * restored ensemble advances exactly as the saved one would have.
+ * QCL_ERR_INVALID_ARG for a NULL or unaligned buffer, an invalid descriptor or
+ * step < 0; QCL_ERR_OUT_OF_MEMORY when ens_bytes is below
+ * qcl_ensemble_bytes. */
+qcl_status qcl_ensemble_restore(const qcl_model* model, const qcl_ensemble_desc* ens,
+                                void* ens_buf, size_t ens_bytes, int64_t step, void* stream);
+
 /* Reads the ensemble header's status words (synchronises `stream`). */
 qcl_status qcl_ensemble_status(const qcl_model* model, const qcl_ensemble_desc* ens,
                                const void* ens_buf, size_t ens_bytes, qcl_ens_status* out,
@@ -264,18 +280,25 @@ qcl_status qcl_ensemble_status(const qcl_model* model, const qcl_ensemble_desc* 
  *  - The call allocates nothing (no cudaMalloc, no cudaFree, no host heap).
  *  - The first call on each device looks up the array's device address with
  *    that device current (cudaGetSymbolAddress); make that first call before
- *    any stream capture on the device.
+ *    any stream capture on the device.  The address is kept for the device's
+ *    primary context (the one the CUDA runtime uses): calls under another
+ *    context, or after cudaDeviceReset, are not supported.
  *  - All calls share the one array and it keeps the last call's contents; no
  *    part of it needs to start at zero (every value a call reads, the same
  *    call wrote first).  Calls that overlap on the GPU (other streams or other
  *    host threads) race on the array: serialise them.
- *  - One output time of a two-state model needs ceil(n_traj / 256) x 256
- *    bytes of the array; a walker count that does not fit even one output
- *    time (about 33 million walkers) is rejected with QCL_ERR_UNSUPPORTED and
- *    a message giving the limit.  Larger counts fit more output times per
- *    launch.
- *  - Only FP32-bulk ensembles of two-state models are accepted
- *    (QCL_ERR_UNSUPPORTED otherwise); other errors as for qcl_propagate. */
+ *  - One output time needs ceil(n_traj / tile) x 256 bytes of the array, with
+ *    tile = qcl_shard_tile_walkers (256 walkers for models of at most 32
+ *    modes, 128 for 33-64 modes, 64 for 65-256 modes); a walker count that
+ *    does not fit even one output time -- about 33 million walkers up to 32
+ *    modes, 16.7 million for 33-64 modes, 8.3 million beyond -- is rejected
+ *    with QCL_ERR_UNSUPPORTED and a message giving the limit.  Smaller counts
+ *    fit more output times per launch (at most 32).
+ *  - The argument checks and their error codes are those of qcl_propagate
+ *    (in the same order); after them, ensembles that are not FP32 bulk, models
+ *    of more than two states and walker counts beyond the array are rejected
+ *    with QCL_ERR_UNSUPPORTED.  The QCL_OPT_GRID_CAP option and the model's
+ *    launch shape apply as for qcl_propagate. */
 #define QCL_NOALLOC_SCRATCH_BYTES ((size_t)32 << 20)
 qcl_status qcl_propagate_noalloc(const qcl_model* model, const qcl_ensemble_desc* ens,
                                  void* ens_buf, size_t ens_bytes, int64_t step0, int64_t n_steps,
@@ -424,9 +447,12 @@ qcl_status qcl_spawn_live(const qcl_model* model, const qcl_ensemble_desc* ens, 
  * arrival order while the caller's device arena has room for their ensemble
  * and observation buffers and fewer than max_active are running; it advances
  * all admitted requests together in rounds of at most quantum_steps steps
- * (and 32 output times) each, packing two-state requests of up to 8 modes
- * into shared persistent launches (a CUDA graph replayed every round when
- * use_graphs is set); requests arriving meanwhile join at the next round.  A
+ * (and 32 output times) each, packing adiabatic two-state requests of up to 8
+ * modes into shared persistent launches (a CUDA graph replayed every round
+ * when use_graphs is set) unless their walkers fill the GPU by themselves
+ * (at least 6 x SMs tiles of 256 walkers), which, like the other requests,
+ * get persistent launches of their own; requests arriving meanwhile join at
+ * the next round.  A
  * request's results do not depend on what it is batched with.  Requests run
  * in FP32-bulk precision.  The server owns one CUDA stream (plus eight side
  * streams on which requests with launches of their own run side by side) and
@@ -471,6 +497,11 @@ typedef struct {
   double latency_mean_s;
   double span_s;            /* first submit to last finish */
   double throughput;        /* traj_steps_done / span_s */
+  double device_busy_s;     /* device time of the busy periods: CUDA events on the
+                               server's stream from the work of the first admission
+                               after an idle spell (sampling included) to the end of
+                               the work that retires the last active request */
+  double device_throughput; /* traj_steps_done / device_busy_s */
 } qcl_server_statistics;
 
 qcl_status qcl_server_create(const qcl_server_desc* d, qcl_server** out);

@@ -364,5 +364,7 @@ void launch_fold(const double* part, double* rows_out, double* scratch, int64_t 
 void launch_finalize(const double* rows, double* fin, int nq, int64_t k0, int64_t nrows,
                      int64_t n_traj, int ns, cudaStream_t st);
 void launch_header_finish(void* buf, int64_t step0, int64_t step1, cudaStream_t st);
+// Writes a whole ensemble header (checkpoint restore).
+void launch_header_set(void* buf, const EnsHeader& v, cudaStream_t st);
 
 }  // namespace qcl

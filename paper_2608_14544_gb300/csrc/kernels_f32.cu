@@ -215,4 +215,11 @@ void launch_header_finish(void* buf, int64_t step0, int64_t step1, cudaStream_t 
   launches_add(1);
 }
 
+__global__ void k_header_set(EnsHeader* h, const EnsHeader v) { *h = v; }
+
+void launch_header_set(void* buf, const EnsHeader& v, cudaStream_t st) {
+  k_header_set<<<1, 1, 0, st>>>((EnsHeader*)buf, v);
+  launches_add(1);
+}
+
 }  // namespace qcl

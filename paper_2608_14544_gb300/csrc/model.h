@@ -22,4 +22,8 @@ struct qcl_model {
 namespace qcl {
 // Records `msg` as the calling thread's last error and returns `st`.
 qcl_status set_error(qcl_status st, const char* msg);
+// The ensemble-descriptor checks every entry point makes (message recorded).
+qcl_status check_ensemble(const qcl_model* m, const qcl_ensemble_desc* e);
+// The process-wide QCL_OPT_GRID_CAP value.
+int64_t option_grid_cap();
 }  // namespace qcl

@@ -37,7 +37,10 @@ qcl_status fail(qcl_status st, const char* fmt, ...) {
 }
 
 // The array's name is only a host-side stand-in; its device address is looked
-// up once per device (with that device current) and cached.
+// up once per device (with that device current) and cached.  The cache
+// belongs to the device's primary context: after cudaDeviceReset, or under a
+// context the caller created with the driver API, the module is loaded anew
+// and the cached address would be stale (both are documented preconditions).
 qcl_status scratch_address(double** out) {
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
@@ -63,26 +66,10 @@ extern "C" qcl_status qcl_propagate_noalloc(const qcl_model* model, const qcl_en
                                             double* rows, size_t rows_bytes, int64_t n_out,
                                             void* stream) {
   using namespace qcl;
-  if (!model || !ens) return fail(QCL_ERR_INVALID_ARG, "model or ensemble descriptor is NULL");
-  if (ens->precision != QCL_PREC_FP32_BULK)
-    return fail(QCL_ERR_UNSUPPORTED, "qcl_propagate_noalloc runs FP32-bulk ensembles only");
-  if (model->ns != 2)
-    return fail(QCL_ERR_UNSUPPORTED, "qcl_propagate_noalloc supports two-state models");
-  if (ens->n_traj < 1) return fail(QCL_ERR_INVALID_ARG, "n_traj must be >= 1");
-  // static-scratch capacity: per output time n_tiles x q2 partials plus fold scratch
-  const int q2 = 8 * model->ns * model->ns;
-  const int tile = tile_walkers(ens->precision, model->n);
-  const int64_t n_tiles = (ens->n_traj + tile - 1) / tile;
-  const int64_t nb1 = (n_tiles + kFoldBlock - 1) / kFoldBlock;
-  const int64_t per_slot = n_tiles * q2 + (nb1 + (nb1 + kFoldBlock - 1) / kFoldBlock + 1) * q2;
-  int64_t slots = (int64_t)kScratchDoubles / per_slot;
-  if (slots < 1)
-    return fail(QCL_ERR_UNSUPPORTED,
-                "n_traj = %lld needs %lld bytes of scratch per output time; the static scratch holds "
-                "%zu bytes (at most about %lld walkers)",
-                (long long)ens->n_traj, (long long)(per_slot * 8), kScratchBytes,
-                (long long)((int64_t)kScratchDoubles / (q2 + 1) * tile * 99 / 100));
-  if (slots > kChunkOut) slots = kChunkOut;
+  // the checks of qcl_propagate first, in its order, so that the same bad
+  // input gets the same code from both calls
+  qcl_status st = check_ensemble(model, ens);
+  if (st) return st;
   if (!ens_buf || !rows) return fail(QCL_ERR_INVALID_ARG, "ens_buf or rows is NULL");
   if (((uintptr_t)ens_buf & 255) != 0 || ((uintptr_t)rows & 7) != 0)
     return fail(QCL_ERR_INVALID_ARG, "ens_buf must be 256-byte aligned and rows 8-byte aligned");
@@ -91,13 +78,33 @@ extern "C" qcl_status qcl_propagate_noalloc(const qcl_model* model, const qcl_en
   if (!(dt > 0.0) || !std::isfinite(dt)) return fail(QCL_ERR_INVALID_ARG, "dt must be positive");
   if (out_stride < 1 || n_out < 1) return fail(QCL_ERR_INVALID_ARG, "out_stride and n_out must be >= 1");
   if ((step0 + n_steps) / out_stride >= n_out) return fail(QCL_ERR_INVALID_ARG, "last output row beyond n_out");
+  const int q2 = 8 * model->ns * model->ns;
   const EnsLayout EL = EnsLayout::make(ens->n_traj, model->ns, model->n, ens->precision);
   if (ens_bytes < EL.total) return fail(QCL_ERR_OUT_OF_MEMORY, "ens_buf has %zu bytes, needs %zu", ens_bytes, EL.total);
   if (rows_bytes < sizeof(double) * (size_t)n_out * q2)
     return fail(QCL_ERR_OUT_OF_MEMORY, "rows has %zu bytes, needs %zu", rows_bytes, sizeof(double) * (size_t)n_out * q2);
+  // what only this call rejects: other precisions, more states, and walker
+  // counts whose scratch does not fit the static array
+  if (ens->precision != QCL_PREC_FP32_BULK)
+    return fail(QCL_ERR_UNSUPPORTED, "qcl_propagate_noalloc runs FP32-bulk ensembles only");
+  if (model->ns != 2)
+    return fail(QCL_ERR_UNSUPPORTED, "qcl_propagate_noalloc supports two-state models");
+  // static-scratch capacity: per output time n_tiles x q2 partials plus fold scratch
+  const int tile = tile_walkers(ens->precision, model->n);
+  const int64_t n_tiles = (ens->n_traj + tile - 1) / tile;
+  const int64_t nb1 = (n_tiles + kFoldBlock - 1) / kFoldBlock;
+  const int64_t per_slot = n_tiles * q2 + (nb1 + (nb1 + kFoldBlock - 1) / kFoldBlock + 1) * q2;
+  int64_t slots = (int64_t)kScratchDoubles / per_slot;
+  if (slots < 1)
+    return fail(QCL_ERR_UNSUPPORTED,
+                "n_traj = %lld needs %lld bytes of scratch per output time; the static scratch holds "
+                "%zu bytes (at most about %lld walkers for this model's %d-walker tiles)",
+                (long long)ens->n_traj, (long long)(per_slot * 8), kScratchBytes,
+                (long long)((int64_t)kScratchDoubles / (q2 + 1) * tile * 99 / 100), tile);
+  if (slots > kChunkOut) slots = kChunkOut;
 
   double* scratch = nullptr;
-  qcl_status st = scratch_address(&scratch);
+  st = scratch_address(&scratch);
   if (st) return st;
   double* part = scratch;
   double* fold = scratch + (size_t)slots * n_tiles * q2;
@@ -161,6 +168,7 @@ extern "C" qcl_status qcl_propagate_noalloc(const qcl_model* model, const qcl_en
     LaunchShape ls;
     ls.wpt = model->shape_wpt;
     ls.blocks_per_sm = model->shape_bps;
+    ls.grid_cap = (int)option_grid_cap();
     if (launch_bulk2(bp, cf, ens_buf, part, ls, s) == 0)
       return fail(QCL_ERR_UNSUPPORTED, "no FP32-bulk kernel for n_modes = %d", model->n);
     if (n_slots > 0) launch_fold(part, rows + (size_t)k_first * q2, fold, n_tiles, q2, n_slots, s);

@@ -108,6 +108,8 @@ qcl_status set_error(qcl_status st, const char* msg) {
   g_err = msg ? msg : "";
   return st;
 }
+qcl_status check_ensemble(const qcl_model* m, const qcl_ensemble_desc* e) { return check_ens(m, e); }
+int64_t option_grid_cap() { return g_opt_grid_cap; }
 }  // namespace qcl
 
 extern "C" {
@@ -175,6 +177,27 @@ qcl_status qcl_ensemble_layout(const qcl_model* model, const qcl_ensemble_desc* 
   offsets[8] = L.off_mexp;
   offsets[9] = L.off_U;
   offsets[10] = L.off_E;
+  return ok();
+}
+
+qcl_status qcl_ensemble_restore(const qcl_model* model, const qcl_ensemble_desc* ens, void* ens_buf,
+                                size_t ens_bytes, int64_t step, void* stream) {
+  qcl_status st = check_ens(model, ens);
+  if (st) return st;
+  if (!ens_buf) return fail(QCL_ERR_INVALID_ARG, "ens_buf is NULL");
+  if (((uintptr_t)ens_buf & 255) != 0) return fail(QCL_ERR_INVALID_ARG, "ens_buf must be 256-byte aligned");
+  if (step < 0) return fail(QCL_ERR_INVALID_ARG, "step must be >= 0 (got %lld)", (long long)step);
+  const EnsLayout L = EnsLayout::make(ens->n_traj, model->ns, model->n, ens->precision);
+  if (ens_bytes < L.total) return fail(QCL_ERR_OUT_OF_MEMORY, "ens_buf holds %zu bytes, needs %zu", ens_bytes, L.total);
+  EnsHeader h{};
+  h.magic = kEnsMagic;
+  h.n_traj = ens->n_traj;
+  h.precision = ens->precision;
+  h.ns = model->ns;
+  h.n = model->n;
+  h.step = step;
+  launch_header_set(ens_buf, h, (cudaStream_t)stream);
+  CUDA_TRY(cudaGetLastError());
   return ok();
 }
 

@@ -4,8 +4,9 @@
 // latency percentiles beside throughput.
 //
 // Rounds (continuous batching): every active request advances by one chunk of
-// at most `quantum_steps` steps and 32 output times.  Two-state requests with
-// at most 8 modes are packed, per (mode bucket, model kind), into one
+// at most `quantum_steps` steps and 32 output times.  Adiabatic two-state
+// requests with at most 8 modes and too few walkers to fill the GPU alone are
+// packed, per (mode bucket, model kind), into one
 // persistent launch that reads a device table of (request, tile) work items;
 // that part of a round is a fixed-shape CUDA graph [table uploads, packed
 // kernels] captured once and replayed every round.  Other requests (many modes,
@@ -139,6 +140,12 @@ struct qcl_server {
   cudaStream_t side[kSide] = {};
   cudaEvent_t side_ev[kSide] = {};
   cudaEvent_t start_ev = nullptr;
+  // device-time span of each busy period (first admission's work to the last
+  // retirement's work, CUDA events on `stream`)
+  cudaEvent_t busy_ev = nullptr, idle_ev = nullptr;
+  bool busy = false;
+  double device_busy_s = 0.0;
+  int n_sm = 1;
   PackedTable* host_tab = nullptr;  // pinned, [2 kinds][buckets]
   PackedTable* dev_tab = nullptr;   // in the arena
   cudaGraphExec_t graph = nullptr;
@@ -283,8 +290,10 @@ void release_streams(qcl_server* s) {
   }
   if (s->start_ev) cudaEventDestroy(s->start_ev);
   if (s->done_ev) cudaEventDestroy(s->done_ev);
+  if (s->busy_ev) cudaEventDestroy(s->busy_ev);
+  if (s->idle_ev) cudaEventDestroy(s->idle_ev);
   if (s->stream) cudaStreamDestroy(s->stream);
-  s->start_ev = s->done_ev = nullptr;
+  s->start_ev = s->done_ev = s->busy_ev = s->idle_ev = nullptr;
   s->stream = nullptr;
 }
 
@@ -298,6 +307,19 @@ bool wait_stream(qcl_server* s, double timeout_s) {
     if (now_s() - t0 > timeout_s) return false;
     std::this_thread::sleep_for(std::chrono::microseconds(50));
   }
+}
+
+// Ends a busy period: records an event after the work enqueued so far and adds
+// the device time since the period's first event to the statistics.
+void end_busy(qcl_server* s) {
+  if (!s->busy) return;
+  float ms = 0.0f;
+  if (cudaEventRecord(s->idle_ev, s->stream) == cudaSuccess && cudaEventSynchronize(s->idle_ev) == cudaSuccess &&
+      cudaEventElapsedTime(&ms, s->busy_ev, s->idle_ev) == cudaSuccess) {
+    std::lock_guard<std::mutex> lk(s->mu);
+    s->device_busy_s += 1e-3 * ms;
+  }
+  s->busy = false;
 }
 
 void run_round(qcl_server* s) {
@@ -348,11 +370,15 @@ void run_round(qcl_server* s) {
   // the side streams start after everything enqueued on `stream` so far
   // (admission sampling, the previous round)
   cudaEventRecord(s->start_ev, s->stream);
-  // packed part: one fixed-shape graph (or the same launches directly)
-  if (s->graph) {
+  // packed part: one fixed-shape graph (or the same launches directly), in
+  // rounds that have packed requests
+  bool any_packed = false;
+  for (int t = 0; t < kTables; ++t) any_packed = any_packed || s->host_tab[t].n_req > 0;
+  if (any_packed && s->graph) {
     cudaGraphLaunch(s->graph, s->stream);
+    launches_add(kTables);
     ++s->graph_replays;
-  } else {
+  } else if (any_packed) {
     enqueue_packed(s);
   }
   bool side_used[qcl_server::kSide] = {};
@@ -394,6 +420,12 @@ void run_round(qcl_server* s) {
     return;
   }
   ++s->rounds;
+  struct Retire {
+    std::shared_ptr<Request> r;
+    int state;
+    std::string err;
+  };
+  std::vector<Retire> retire;
   for (auto& it : items) {
     if (!it.r) continue;
     Request& r = *it.r;
@@ -407,13 +439,22 @@ void run_round(qcl_server* s) {
                                              r.result.data(), r.result.size(), s->stream);
       if (st == QCL_OK) st = qcl_ensemble_status(r.model, &r.ens, s->arena + r.ens_off, r.ens_bytes, &es, s->stream);
       if (st != QCL_OK)
-        finish(s, it.r, RQ_ERROR, qcl_last_error());
+        retire.push_back({it.r, RQ_ERROR, qcl_last_error()});
       else if (es.flags & (QCL_FLAG_NONFINITE | QCL_FLAG_STEP_MISMATCH))
-        finish(s, it.r, RQ_ERROR, "non-finite value or step mismatch in the ensemble");
+        retire.push_back({it.r, RQ_ERROR, "non-finite value or step mismatch in the ensemble"});
       else
-        finish(s, it.r, RQ_DONE, "");
+        retire.push_back({it.r, RQ_DONE, ""});
     }
   }
+  // when every active request retires, the busy period ends here, before the
+  // waiters are told (so statistics read after a wait include it)
+  size_t n_active;
+  {
+    std::lock_guard<std::mutex> lk(s->mu);
+    n_active = s->active.size();
+  }
+  if (!retire.empty() && retire.size() == n_active) end_busy(s);
+  for (auto& x : retire) finish(s, x.r, x.state, x.err);
 }
 
 void worker_main(qcl_server* s) {
@@ -426,6 +467,10 @@ void worker_main(qcl_server* s) {
       if (s->stop) break;
     }
     admit(s, fresh);
+    if (!fresh.empty() && !s->busy) {  // an idle device starts a busy period
+      cudaEventRecord(s->busy_ev, s->stream);
+      s->busy = true;
+    }
     for (auto& r : fresh) {
       qcl_model_desc md{r->ns, r->n, r->hbar, r->mass.data(), r->omega.data(), r->E.data(), r->K.data(), r->hop, r->pmax, r->repr, 0};
       qcl_status st = qcl_create_model(&md, &r->model);
@@ -436,6 +481,12 @@ void worker_main(qcl_server* s) {
       if (st != QCL_OK) finish(s, r, RQ_ERROR, qcl_last_error());
     }
     run_round(s);
+    bool idle;
+    {
+      std::lock_guard<std::mutex> lk(s->mu);
+      idle = s->active.empty();
+    }
+    if (idle) end_busy(s);  // (requests that failed outside a round's retirement)
   }
 }
 
@@ -459,6 +510,9 @@ qcl_status qcl_server_create(const qcl_server_desc* d, qcl_server** out) {
   cudaError_t e = cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking);
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s->done_ev, cudaEventDisableTiming);
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s->start_ev, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaEventCreate(&s->busy_ev);
+  if (e == cudaSuccess) e = cudaEventCreate(&s->idle_ev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&s->n_sm, cudaDevAttrMultiProcessorCount, s->device);
   for (int j = 0; j < qcl_server::kSide && e == cudaSuccess; ++j) {
     e = cudaStreamCreateWithFlags(&s->side[j], cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s->side_ev[j], cudaEventDisableTiming);
@@ -533,8 +587,13 @@ qcl_status qcl_server_submit(qcl_server* s, const qcl_request_desc* r, int64_t* 
   q->n_out = r->n_steps / r->out_stride + 1;
   q->ens_bytes = EnsLayout::make(r->n_traj, ns, n, QCL_PREC_FP32_BULK).total;
   q->obs_bytes = ObsLayout::make(r->n_traj, ns, q->n_out, tile_walkers(QCL_PREC_FP32_BULK, n, ns)).total;
-  // the packed kernel runs adiabatic two-state models; others get their own launches
+  // the packed kernel runs adiabatic two-state models; others get their own
+  // launches, and so do requests whose tiles fill two waves of the persistent
+  // grid by themselves (three resident blocks per SM): packing gains them
+  // nothing, and their own launch runs the single-solve kernel with two walkers
+  // per thread.  Both routes give the same bits.
   q->bucket = (ns == 2 && m.repr == QCL_REPR_ADIABATIC) ? packed_bucket(n) : -1;
+  if (q->bucket >= 0 && (r->n_traj + kTile - 1) / kTile >= 6 * (int64_t)s->n_sm) q->bucket = -1;
   q->t_submit = now_s();
   std::lock_guard<std::mutex> lk(s->mu);
   if (align256(q->ens_bytes) + align256(q->obs_bytes) > s->alloc.total())
@@ -609,6 +668,8 @@ qcl_status qcl_server_stats(qcl_server* s, qcl_server_statistics* out) {
   st.latency_mean_s = l.empty() ? 0.0 : sum / l.size();
   st.span_s = (s->first_submit >= 0 && s->last_done >= 0) ? s->last_done - s->first_submit : 0.0;
   st.throughput = st.span_s > 0 ? s->traj_steps / st.span_s : 0.0;
+  st.device_busy_s = s->device_busy_s;
+  st.device_throughput = s->device_busy_s > 0 ? s->traj_steps / s->device_busy_s : 0.0;
   *out = st;
   return qcl::set_error(QCL_OK, "");
 }

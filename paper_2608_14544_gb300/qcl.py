@@ -32,7 +32,7 @@ EXPORTS = [
     "qcl_create_model", "qcl_destroy_model", "qcl_ensemble_bytes", "qcl_obs_bytes",
     "qcl_ensemble_layout", "qcl_sample_initial", "qcl_propagate", "qcl_reduce_observables",
     "qcl_finalize_observables",
-    "qcl_read_sums", "qcl_ensemble_status", "qcl_propagate_noalloc",
+    "qcl_read_sums", "qcl_ensemble_status", "qcl_ensemble_restore", "qcl_propagate_noalloc",
     "qcl_server_create", "qcl_server_submit", "qcl_server_poll", "qcl_server_wait",
     "qcl_server_stats", "qcl_server_destroy", "qcl_shard_tile_walkers", "qcl_combine_shards",
     "qcl_spawn_bytes", "qcl_spawn_layout", "qcl_spawn_sample", "qcl_spawn_propagate",
@@ -103,7 +103,8 @@ class ServerStats(C.Structure):
                 ("graph_replays", C.c_int64), ("arena_used", C.c_size_t),
                 ("traj_steps_done", C.c_double), ("latency_p50_s", C.c_double),
                 ("latency_p99_s", C.c_double), ("latency_mean_s", C.c_double),
-                ("span_s", C.c_double), ("throughput", C.c_double)]
+                ("span_s", C.c_double), ("throughput", C.c_double),
+                ("device_busy_s", C.c_double), ("device_throughput", C.c_double)]
 
 
 class EnsStatus(C.Structure):
@@ -140,6 +141,7 @@ def load(path: str = LIB_PATH):
     lib.qcl_finalize_observables.argtypes = [vp, vp, vp, sz, i64, i64, i64, vp, sz, vp]
     lib.qcl_read_sums.argtypes = [vp, vp, vp, sz, i64, i64, i64, vp, sz, vp]
     lib.qcl_ensemble_status.argtypes = [vp, vp, vp, sz, vp, vp]
+    lib.qcl_ensemble_restore.argtypes = [vp, vp, vp, sz, i64, vp]
     lib.qcl_propagate_noalloc.argtypes = [vp, vp, vp, sz, i64, i64, C.c_double, i32, vp, sz, i64,
                                           vp]
     lib.qcl_shard_tile_walkers.argtypes = [vp, i32, vp]
@@ -372,6 +374,14 @@ def ensemble_status(model: Model, ens: EnsembleDesc, ens_buf, stream=None) -> di
             "n_nonfinite": s.n_nonfinite}
 
 
+def ensemble_restore(model: Model, ens: EnsembleDesc, ens_buf, step: int, stream=None):
+    """qcl_ensemble_restore: the header of an ensemble at absolute step `step`
+    whose walker arrays the caller has written."""
+    _check(load().qcl_ensemble_restore(model.handle, C.byref(ens), _dptr(ens_buf),
+                                       ens_buf.numel() * ens_buf.element_size(), int(step),
+                                       _stream_ptr(stream)), "qcl_ensemble_restore")
+
+
 # ------------------------------------------------------------- conveniences --
 def device_buffer(nbytes: int, device="cuda"):
     """Caller-owned device memory from torch (256-byte aligned)."""
@@ -417,6 +427,43 @@ class Run:
 
     def status(self, stream=None) -> dict:
         return ensemble_status(self.model, self.ens, self.ens_buf, stream)
+
+    def load_state(self, st: dict, step: int, stream=None):
+        """Checkpoint restore: writes walker arrays already in this ensemble's
+        precision and layout -- the dict state() returns: R, P [n_traj, n];
+        m, m_lo, m_exp, phi, phi_lo, alpha, q, beta [n_traj]; U [n_traj, NS, NS]
+        and E [n_traj, NS] for models of more than two states -- into the
+        buffer, then qcl_ensemble_restore sets its step."""
+        import torch
+
+        nt, n, ns = self.ens.n_traj, self.model.n, self.model.ns
+        off = ensemble_layout(self.model, self.ens)
+        fp64 = self.ens.precision == PREC_FP64
+        ft = np.float64 if fp64 else np.float32
+        host = np.zeros(self.ens_buf.numel(), dtype=np.uint8)
+
+        def put(o, a, dtype):
+            b = np.ascontiguousarray(np.asarray(a, dtype=dtype)).view(np.uint8).reshape(-1)
+            host[o:o + b.size] = b
+
+        put(off[0], np.asarray(st["R"]).reshape(nt, n).T, ft)
+        put(off[1], np.asarray(st["P"]).reshape(nt, n).T, ft)
+        put(off[2], st["m"], ft)
+        put(off[4], st["phi"], ft)
+        if not fp64:
+            put(off[3], st["m_lo"], ft)
+            put(off[5], st["phi_lo"], ft)
+            put(off[8], st["m_exp"], np.int32)
+        ab = (np.asarray(st["alpha"]) | (np.asarray(st.get("q", 0)) << 4)
+              | (np.asarray(st["beta"]) << 8))
+        put(off[6], ab, np.uint16)
+        if ns > 2:
+            put(off[9], np.asarray(st["U"]).reshape(nt, ns * ns).T, ft)
+            if not fp64:
+                put(off[10], np.asarray(st["E"]).reshape(nt, ns).T, ft)
+        self.ens_buf.copy_(torch.from_numpy(host).to(self.ens_buf.device))
+        ensemble_restore(self.model, self.ens, self.ens_buf, step, stream)
+        self.step = int(step)
 
     def state(self):
         """Host copy of the SoA walker state (for checkpoints and parity tests)."""

@@ -117,22 +117,6 @@ def test_fp64_dia_observables_match_oracle(q):
     assert err.max() < 1e-10, err.max()
 
 
-@pytest.mark.parametrize("cfg_id,n,steps", [(1, 8000, 600), (2, 6000, 400), (3, 4000, 400)])
-def test_fp32_dia_observables_match_oracle(q, cfg_id, n, steps):
-    cfg = _dia(wl.config(cfg_id))
-    stride = cfg["out_stride"]
-    m, run = _run(q, cfg, n, q.PREC_FP32_BULK, steps, stride, seed=11)
-    run.propagate(steps, cfg["dt"], stride)
-    obs = run.observables()
-    om = oracle.OracleModel(cfg["model"])
-    ref, _ = oracle.run(om, oracle.OracleInit(om, cfg["init"]), 11, 0, n, cfg["dt"], steps, stride)
-    mean, se = oracle.finalize(ref, n)
-    diff = np.abs(obs[:, :16] - mean)
-    assert np.all(diff <= 3 * se + 1e-9), (diff / (se + 1e-300)).max()
-    assert diff.max() <= 1e-3 * max(1.0, np.abs(mean).max()) + 3 * se.max()
-    assert run.status()["flags"] == 0
-
-
 def test_fp32_dia_pure_dephasing_at_eps0(q):
     """Delta = 0, eps = 0: the diabatic levels cross at every bath fluctuation;
     the coherence is the Gaussian characteristic function of the phase."""

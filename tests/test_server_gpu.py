@@ -61,25 +61,77 @@ def test_results_are_the_same_alone_and_in_the_mix(q, graphs):
     s = srv.stats()
     assert s["n_done"] == len(reqs) and s["n_error"] == 0
     assert s["latency_p99_s"] >= s["latency_p50_s"] > 0
-    if graphs:
-        assert s["graph_replays"] == s["rounds"] > 0
+    if graphs:  # replayed in every round that had packed requests
+        assert 0 < s["graph_replays"] <= s["rounds"]
+    assert s["device_busy_s"] > 0 and s["device_throughput"] > 0
     srv.close()
 
 
-def test_served_matches_single_solve(q):
-    for cfg, n, steps in ((wl.config(2), 60_000, 400), (wl.config(4), 20_000, 200),
-                          (wl.lvc4_config(3), 10_000, 200)):
+def _dia(cfg):
+    cfg["model"]["repr"] = "diabatic"
+    return cfg
+
+
+def _kinds():
+    """One request of each model kind the server takes (packed two-state
+    launches, many-mode and N-state launches of their own, both
+    representations)."""
+    return [("sb1", wl.config(1), 1000), ("sb3", wl.config(2), 600),
+            ("vib3", wl.config(3), 800), ("sb100", wl.config(4), 400),
+            ("lvc4", wl.lvc4_config(3), 400), ("sb3-diabatic", _dia(wl.config(2)), 600)]
+
+
+def test_served_matches_single_solve_bitwise(q):
+    """A served request runs the same walker arithmetic and the same reduction
+    tree as the single-solve entry points (only the chunking into rounds
+    differs, which changes no bit), so the results are identical."""
+    for name, cfg, steps in _kinds():
+        n = 20_000 if name == "sb100" else 60_000
         srv = q.Server(1 << 30, quantum_steps=150)
         st, served = srv.wait(srv.submit(_req(cfg, n, steps, 7)))
         srv.close()
+        assert st == q.REQ_DONE, name
         m = q.Model(cfg["model"])
         run = q.Run(m, n, 7, q.PREC_FP32_BULK, steps // cfg["out_stride"] + 1)
         run.sample(cfg["init"])
         run.propagate(steps, cfg["dt"], cfg["out_stride"])
         single = run.observables()
+        assert np.array_equal(served, single), name
+
+
+def test_served_requests_match_oracle(q):
+    """Each kind of request, sent through qcl_server_submit, against the oracle
+    run on the same walkers (same seed and ids): within 3 standard errors at
+    every output and 1e-3 absolute where the estimator resolves (SE < 1e-2)."""
+    import os
+
+    import oracle
+
+    oracle.build()
+    threads = max(1, min(16, os.cpu_count() or 1))
+    srv = q.Server(1 << 31, quantum_steps=200)
+    n = 1 << 14
+    # output strides fine enough that the resolved window (SE < 1e-2 at this
+    # walker count) holds several outputs for every model
+    strides = {"vib3": 4, "sb100": 4}
+    subs = []
+    for k, (name, cfg, steps) in enumerate(_kinds()):
+        cfg["out_stride"] = strides.get(name, cfg["out_stride"])
+        subs.append((name, cfg, steps, 100 + k, srv.submit(_req(cfg, n, steps, 100 + k))))
+    for name, cfg, steps, seed, rid in subs:
+        st, served = srv.wait(rid)
+        assert st == q.REQ_DONE, name
+        om = oracle.OracleModel(cfg["model"])
+        rows = oracle.run_threaded(om, oracle.OracleInit(om, cfg["init"]), seed, n, cfg["dt"],
+                                   steps, cfg["out_stride"], threads)
+        mean, se = oracle.finalize(rows, n)
         nq = 4 * cfg["model"]["n_states"] ** 2
-        assert np.allclose(served[:, :nq], single[:, :nq], rtol=1e-5,
-                           atol=1e-6 * np.abs(single[:, :nq]).max())
+        diff = np.abs(served[:, :nq] - mean)
+        res = se < 1e-2
+        assert res.any(axis=1).sum() >= 5, name
+        assert diff[res].max() < 1e-3, (name, diff[res].max())
+        assert np.all(diff[res] <= 3 * se[res] + 1e-7), (name, (diff / (se + 1e-300))[res].max())
+    srv.close()
 
 
 def test_admission_waits_for_arena_memory(q):

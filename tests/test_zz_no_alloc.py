@@ -52,35 +52,55 @@ def _noalloc_rows(q, cfg, n, seed, splits, stride):
     torch.cuda.synchronize()
     st = q.ensemble_status(m, ens, ens_buf)
     assert st["step"] == step and st["flags"] == 0, st
-    return rows.cpu().numpy()
+    view = q.Run.__new__(q.Run)  # the state reader of a Run over this buffer
+    view.model, view.ens, view.ens_buf = m, ens, ens_buf
+    return rows.cpu().numpy(), view.state()
 
 
 def test_noalloc_rows_match_propagate_on_two_calls(q):
-    # two calls in a row: a large ensemble (several launches per call, since
-    # fewer output times fit the static scratch) and then a small ragged one,
-    # so the second call runs over the first one's leftovers
-    for cfg_id, n, splits, seed in ((2, 4_000_000, (130, 270), 5), (3, 3001, (200,), 9)):
+    """The same bits as qcl_propagate, rows and walker states, on two calls in
+    a row per case.  The cases cover: several launches per call (fewer output
+    times fit the static scratch than the call spans), a small ragged ensemble
+    that runs over the previous case's leftovers, a many-mode model (its
+    walkers' modes split over four warps, 64-walker tiles) with so many walkers
+    that only one output time fits per launch (the output at t = 0 then gets a
+    launch of its own), and the same kernel with a handful of walkers."""
+    cases = ((2, 4_000_000, (130, 270), 5), (3, 3001, (200,), 9),
+             (4, 6_000_000, (40, 60), 2), (4, 2001, (37, 23), 4))
+    for cfg_id, n, splits, seed in cases:
         cfg = wl.config(cfg_id)
         stride = cfg["out_stride"]
-        ref, _ = _reference_rows(q, cfg, n, seed, splits, stride)
-        got = _noalloc_rows(q, cfg, n, seed, splits, stride)
-        assert np.all(np.isfinite(got))
-        scale = np.sqrt(n * np.abs(ref[:, 16:])) + 1e-300
-        assert np.all(np.abs(got[:, :16] - ref[:, :16]) <= 1e-12 * scale)
-        assert np.allclose(got[:, 16:], ref[:, 16:], rtol=1e-12, atol=0)
+        ref, ref_state = _reference_rows(q, cfg, n, seed, splits, stride)
+        got, got_state = _noalloc_rows(q, cfg, n, seed, splits, stride)
+        assert np.all(np.isfinite(got)), cfg_id
+        assert np.array_equal(got, ref), (cfg_id, n)
+        for k in ref_state:
+            assert np.array_equal(got_state[k], ref_state[k]), (cfg_id, n, k)
 
 
 def test_noalloc_rejects_walker_counts_beyond_the_static_scratch(q):
+    """Past the static array's capacity (about 33 million walkers of a
+    3-mode model) the call fails with QCL_ERR_UNSUPPORTED and says so, after
+    the argument checks it shares with qcl_propagate; an FP64 ensemble is
+    rejected the same way."""
+    import torch
+
     cfg = wl.config(2)
     m = q.Model(cfg["model"])
-    ens = q.ens_desc(200_000_000, 0, q.PREC_FP32_BULK)
-    import ctypes as C
-
-    st = q.load().qcl_propagate_noalloc(m.handle, C.byref(ens), None, 0, 0, 10, 0.01, 10, None,
-                                        0, 2, None)
-    assert st == 2  # QCL_ERR_UNSUPPORTED
-    assert "static scratch" in q.last_error()
+    n_out = 2
+    rows = torch.zeros((n_out, 8 * m.ns * m.ns), dtype=torch.float64, device="cuda")
+    ens = q.ens_desc(40_000_000, 0, q.PREC_FP32_BULK)
+    buf = q.device_buffer(q.ensemble_bytes(m, ens))
+    with pytest.raises(q.QclError) as e:
+        q.propagate_noalloc(m, ens, buf, 0, 10, cfg["dt"], 10, rows, n_out)
+    assert e.value.status == 2 and "static scratch" in q.last_error()
+    # an argument error is reported first, with qcl_propagate's code
+    with pytest.raises(q.QclError) as e:
+        q.propagate_noalloc(m, ens, buf, 0, 10, -1.0, 10, rows, n_out)
+    assert e.value.status == 1
+    del buf
     fp64 = q.ens_desc(1000, 0, q.PREC_FP64)
-    st = q.load().qcl_propagate_noalloc(m.handle, C.byref(fp64), None, 0, 0, 10, 0.01, 10, None,
-                                        0, 2, None)
-    assert st == 2
+    buf64 = q.device_buffer(q.ensemble_bytes(m, fp64))
+    with pytest.raises(q.QclError) as e:
+        q.propagate_noalloc(m, fp64, buf64, 0, 10, cfg["dt"], 10, rows, n_out)
+    assert e.value.status == 2 and "FP32-bulk" in q.last_error()
