@@ -318,9 +318,30 @@ qcl_status qcl_propagate_noalloc(const qcl_model* model, const qcl_ensemble_desc
 qcl_status qcl_shard_tile_walkers(const qcl_model* model, int32_t precision, int64_t* walkers);
 
 /* Host-side combine: out[i] = binary tree over s (zero-padded to a power of
- * two) of shard_sums[s * n_elems + i], shards in walker order. */
+ * two) of shard_sums[s * n_elems + i], shards in walker order.  Applied to
+ * the chunk sums of all shards (qcl_read_chunk_sums, chunks in walker order)
+ * it gives the unsharded rows bit for bit. */
 qcl_status qcl_combine_shards(const double* shard_sums, int32_t n_shards, int64_t n_elems,
                               double* out);
+
+/* Balanced shards.  Walkers per chunk: 1024 reduction tiles (the first level
+ * of the tile fold, an aligned subtree of the reduction tree).  A shard that
+ * starts at a multiple of this count (its traj_id_offset) and ends there or at
+ * the ensemble's end computes its chunks' sums exactly as the unsharded run
+ * does, so ranks can take contiguous runs of floor(C / world) or
+ * ceil(C / world) of the C chunks, within one chunk of each other. */
+qcl_status qcl_shard_chunk_walkers(const qcl_model* model, int32_t precision, int64_t* walkers);
+
+/* The per-chunk FP64 sums of output rows [k0, k0 + n_rows) of an ensemble
+ * propagated by qcl_propagate: host_out[(k - k0) C q2 + c q2 + i] for chunk c
+ * (of *n_chunks = C, in walker order) and entry i of the row's 2Q sums (sums,
+ * then sums of squares; q2 = 8 NS^2).  With one chunk these are the rows
+ * themselves.  host_out = NULL only sets *n_chunks.  Synchronises `stream`.
+ * Not kept by qcl_propagate_noalloc or for spawning ensembles. */
+qcl_status qcl_read_chunk_sums(const qcl_model* model, const qcl_ensemble_desc* ens,
+                               const void* obs_buf, size_t obs_bytes, int64_t n_out, int64_t k0,
+                               int64_t n_rows, double* host_out, size_t host_len,
+                               int64_t* n_chunks, void* stream);
 
 /* Measured multiply-add throughput of the current device (no counterpart in
  * the paper; the roofline denominators): which = 0 FP32 FFMA, 1 FP64 DFMA.

@@ -359,8 +359,11 @@ void launch_observeN_f64(int ns, const void* buf, int64_t nt, int n, double* par
 int launch_bulkN(int ns, const BulkParams& bp, const CoefN& cf, void* buf, double* part,
                  const LaunchShape& ls, cudaStream_t st);
 
+// Folds n_slots output times of per-tile partials into rows; with chunk_out
+// (rows of [n_slots][ceil(n_tiles / 1024)][q2]) the first level's 1024-tile
+// block sums are kept there when there is more than one block.
 void launch_fold(const double* part, double* rows_out, double* scratch, int64_t n_tiles,
-                 int q2, int n_slots, cudaStream_t st);
+                 int q2, int n_slots, cudaStream_t st, double* chunk_out = nullptr);
 void launch_finalize(const double* rows, double* fin, int nq, int64_t k0, int64_t nrows,
                      int64_t n_traj, int ns, cudaStream_t st);
 void launch_header_finish(void* buf, int64_t step0, int64_t step1, cudaStream_t st);

@@ -456,17 +456,21 @@ qcl_status qcl_propagate(const qcl_model* model, const qcl_ensemble_desc* ens, v
   double* fold = (double*)(ob + OL.off_fold);
   const int q2 = OL.q2;
   const int64_t nt = ens->n_traj;
+  // per-chunk sums of output row k (only kept when there is more than one chunk)
+  auto chunk_row = [&](int64_t k) -> double* {
+    return OL.n_fold_blocks > 1 ? (double*)(ob + OL.off_chunk) + (size_t)k * OL.n_fold_blocks * q2 : nullptr;
+  };
 
   if (ens->precision == QCL_PREC_FP64) {
     const int ns = model->ns;
-    auto observe = [&](double* row) {
+    auto observe = [&](int64_t k) {
       if (ns == 2)
         launch_observe_f64(model->dev, ens_buf, nt, model->n, part, s);
       else
         launch_observeN_f64(ns, ens_buf, nt, model->n, part, s);
-      launch_fold(part, row, fold, OL.n_tiles, q2, 1, s);
+      launch_fold(part, rows + (size_t)k * q2, fold, OL.n_tiles, q2, 1, s, chunk_row(k));
     };
-    if (step0 == 0) observe(rows);
+    if (step0 == 0) observe(0);
     for (int64_t t = step0; t < step0 + n_steps; ++t) {
       {
         TimedLaunch tl(1, s);
@@ -475,7 +479,7 @@ qcl_status qcl_propagate(const qcl_model* model, const qcl_ensemble_desc* ens, v
         else
           launch_stepN_f64(model->dev, ns, ens_buf, nt, model->n, step0, t, dt, ens->seed, ens->traj_id_offset, s);
       }
-      if ((t + 1) % out_stride == 0) observe(rows + (size_t)((t + 1) / out_stride) * q2);
+      if ((t + 1) % out_stride == 0) observe((t + 1) / out_stride);
     }
     st = check_launch("FP64 step");
     if (st) return st;
@@ -560,7 +564,8 @@ qcl_status qcl_propagate(const qcl_model* model, const qcl_ensemble_desc* ens, v
         delete cn;
         return fail(QCL_ERR_UNSUPPORTED, "no FP32-bulk kernel for n_modes = %d", model->n);
       }
-      if (n_slots > 0) launch_fold(part, rows + (size_t)k_first * q2, fold, OL.n_tiles, q2, n_slots, s);
+      if (n_slots > 0)
+        launch_fold(part, rows + (size_t)k_first * q2, fold, OL.n_tiles, q2, n_slots, s, chunk_row(k_first));
       first = false;
       cs = ce;
     } while (cs < end);
@@ -615,6 +620,29 @@ qcl_status qcl_finalize_observables(const qcl_model* model, const qcl_ensemble_d
                   model->ns, (cudaStream_t)stream);
   st = check_launch("finalize");
   return st ? st : ok();
+}
+
+qcl_status qcl_read_chunk_sums(const qcl_model* model, const qcl_ensemble_desc* ens, const void* obs_buf,
+                               size_t obs_bytes, int64_t n_out, int64_t k0, int64_t n_rows, double* host_out,
+                               size_t host_len, int64_t* n_chunks, void* stream) {
+  qcl_status st = check_ens(model, ens);
+  if (st) return st;
+  if (!obs_buf || !n_chunks) return fail(QCL_ERR_INVALID_ARG, "obs_buf or n_chunks is NULL");
+  if (n_out < 1 || k0 < 0 || n_rows < 0 || k0 + n_rows > n_out) return fail(QCL_ERR_INVALID_ARG, "rows outside [0, n_out)");
+  const ObsLayout OL = ObsLayout::make(ens->n_traj, model->ns, n_out, tile_walkers(ens->precision, model->n, model->ns));
+  if (obs_bytes < OL.total) return fail(QCL_ERR_OUT_OF_MEMORY, "obs_buf has %zu bytes, needs %zu", obs_bytes, OL.total);
+  *n_chunks = OL.n_fold_blocks;
+  if (!host_out) return ok();  // size query
+  const size_t per_row = (size_t)OL.n_fold_blocks * OL.q2;
+  if (host_len < per_row * n_rows) return fail(QCL_ERR_INVALID_ARG, "host_out holds %zu doubles, needs %zu", host_len, per_row * n_rows);
+  if (n_rows == 0) return ok();
+  cudaStream_t s = (cudaStream_t)stream;
+  // one chunk: its sums are the rows themselves
+  const size_t off = OL.n_fold_blocks > 1 ? OL.off_chunk : OL.off_rows;
+  const double* src = (const double*)((const char*)obs_buf + off) + (size_t)k0 * per_row;
+  CUDA_TRY(cudaMemcpyAsync(host_out, src, sizeof(double) * per_row * n_rows, cudaMemcpyDeviceToHost, s));
+  CUDA_TRY(cudaStreamSynchronize(s));
+  return ok();
 }
 
 qcl_status qcl_read_sums(const qcl_model* model, const qcl_ensemble_desc* ens, const void* obs_buf, size_t obs_bytes,
@@ -932,6 +960,13 @@ qcl_status qcl_shard_tile_walkers(const qcl_model* model, int32_t precision, int
   if (!model || !walkers) return fail(QCL_ERR_INVALID_ARG, "NULL argument");
   if (precision != QCL_PREC_FP64 && precision != QCL_PREC_FP32_BULK) return fail(QCL_ERR_INVALID_ARG, "unknown precision");
   *walkers = tile_walkers(precision, model->n, model->ns);
+  return ok();
+}
+
+qcl_status qcl_shard_chunk_walkers(const qcl_model* model, int32_t precision, int64_t* walkers) {
+  if (!model || !walkers) return fail(QCL_ERR_INVALID_ARG, "NULL argument");
+  if (precision != QCL_PREC_FP64 && precision != QCL_PREC_FP32_BULK) return fail(QCL_ERR_INVALID_ARG, "unknown precision");
+  *walkers = (int64_t)kFoldBlock * tile_walkers(precision, model->n, model->ns);
   return ok();
 }
 

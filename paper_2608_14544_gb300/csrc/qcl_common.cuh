@@ -241,8 +241,11 @@ __host__ __device__ inline int tile_walkers(int precision, int n, int ns = 2) {
   return ns > 2 ? 128 : kTile / bulk_lanes(n);
 }
 
+// The per-chunk sums (chunks of kFoldBlock tiles, the first level of the tile
+// fold: aligned subtrees of the reduction tree) are kept for every output row
+// when there is more than one chunk, for combining shards.
 struct ObsLayout {
-  size_t off_rows, off_part, off_fin, off_fold, total;
+  size_t off_rows, off_part, off_fin, off_fold, off_chunk, total;
   int64_t n_tiles, n_fold_blocks;
   int q2;
   __host__ __device__ static ObsLayout make(int64_t n_traj, int ns, int64_t n_out,
@@ -261,6 +264,8 @@ struct ObsLayout {
     L.off_fold = o;
     const int64_t fold_rows = L.n_fold_blocks + (L.n_fold_blocks + kFoldBlock - 1) / kFoldBlock + 1;
     o = align256(o + sizeof(double) * (size_t)kChunkOut * (size_t)fold_rows * L.q2);
+    L.off_chunk = o;
+    if (L.n_fold_blocks > 1) o = align256(o + sizeof(double) * (size_t)n_out * (size_t)L.n_fold_blocks * L.q2);
     L.total = o;
     return L;
   }

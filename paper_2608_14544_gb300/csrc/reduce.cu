@@ -61,16 +61,19 @@ __global__ void k_finalize(const double* __restrict__ rows, double* __restrict__
 
 // ------------------------------------------------------------ fold/finalize --
 void launch_fold(const double* part, double* rows_out, double* scratch, int64_t n_tiles, int q2,
-                 int n_slots, cudaStream_t st) {
-  // level 1: tiles -> 1024-tile blocks; repeat until one value per row
+                 int n_slots, cudaStream_t st, double* chunk_out) {
+  // level 1: tiles -> 1024-tile blocks (kept in chunk_out when it is given and
+  // there is more than one block); repeat until one value per row
   const double* in = part;
   int64_t n = n_tiles;
   int64_t in_stride = n_tiles * q2;
   double* bufs[2] = {scratch, scratch + (size_t)n_slots * ((n_tiles + 1023) / 1024) * q2};
   int which = 0;
+  bool first = true;
   while (true) {
     const int64_t nb = (n + 1023) / 1024;
-    double* out = (nb == 1) ? rows_out : bufs[which];
+    double* out = (nb == 1) ? rows_out : ((first && chunk_out) ? chunk_out : bufs[which]);
+    first = false;
     const int64_t out_stride = (nb == 1) ? q2 : nb * q2;
     dim3 grid((unsigned)nb, (unsigned)q2, (unsigned)n_slots);
     k_fold_level<<<grid, 32, 0, st>>>(in, out, n, q2, in_stride, out_stride);

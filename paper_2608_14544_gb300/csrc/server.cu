@@ -391,7 +391,10 @@ void run_round(qcl_server* s) {
       const ObsLayout OL = ObsLayout::make(r.ens.n_traj, 2, r.n_out);
       if (it.c.n_slots > 0)
         launch_fold((double*)(obs_buf + OL.off_part), (double*)(obs_buf + OL.off_rows) + (size_t)it.c.k_first * OL.q2,
-                    (double*)(obs_buf + OL.off_fold), OL.n_tiles, OL.q2, it.c.n_slots, s->stream);
+                    (double*)(obs_buf + OL.off_fold), OL.n_tiles, OL.q2, it.c.n_slots, s->stream,
+                    OL.n_fold_blocks > 1
+                        ? (double*)(obs_buf + OL.off_chunk) + (size_t)it.c.k_first * OL.n_fold_blocks * OL.q2
+                        : nullptr);
       launch_header_finish(ens_buf, it.c.cs, it.c.ce, s->stream);
     } else {
       if (r.bucket == -2) r.bucket = -1;

@@ -36,7 +36,7 @@ EXPORTS = [
     "qcl_server_create", "qcl_server_submit", "qcl_server_poll", "qcl_server_wait",
     "qcl_server_stats", "qcl_server_destroy", "qcl_shard_tile_walkers", "qcl_combine_shards",
     "qcl_spawn_bytes", "qcl_spawn_layout", "qcl_spawn_sample", "qcl_spawn_propagate",
-    "qcl_spawn_live", "qcl_set_launch_shape", "qcl_get_launch_shape", "qcl_autotune_bytes",
+    "qcl_spawn_live", "qcl_shard_chunk_walkers", "qcl_read_chunk_sums", "qcl_set_launch_shape", "qcl_get_launch_shape", "qcl_autotune_bytes",
     "qcl_autotune", "qcl_measure_peak",
 ]
 FLAG_SPAWN_OVERFLOW = 8
@@ -146,6 +146,8 @@ def load(path: str = LIB_PATH):
                                           vp]
     lib.qcl_shard_tile_walkers.argtypes = [vp, i32, vp]
     lib.qcl_combine_shards.argtypes = [vp, i32, i64, vp]
+    lib.qcl_shard_chunk_walkers.argtypes = [vp, i32, vp]
+    lib.qcl_read_chunk_sums.argtypes = [vp, vp, vp, sz, i64, i64, i64, vp, sz, vp, vp]
     lib.qcl_server_create.argtypes = [vp, vp]
     lib.qcl_server_submit.argtypes = [vp, vp, vp]
     lib.qcl_server_poll.argtypes = [vp, i64, vp, vp, sz, vp]
@@ -425,6 +427,9 @@ class Run:
     def sums(self, stream=None) -> np.ndarray:
         return read_sums(self.model, self.ens, self.obs_buf, self.n_out, stream=stream)
 
+    def chunk_sums(self, stream=None) -> np.ndarray:
+        return read_chunk_sums(self.model, self.ens, self.obs_buf, self.n_out, stream=stream)
+
     def status(self, stream=None) -> dict:
         return ensemble_status(self.model, self.ens, self.ens_buf, stream)
 
@@ -595,6 +600,29 @@ def shard_tile_walkers(model: Model, precision: int) -> int:
     _check(load().qcl_shard_tile_walkers(model.handle, precision, C.byref(w)),
            "qcl_shard_tile_walkers")
     return w.value
+
+
+def shard_chunk_walkers(model: Model, precision: int) -> int:
+    w = C.c_int64()
+    _check(load().qcl_shard_chunk_walkers(model.handle, precision, C.byref(w)),
+           "qcl_shard_chunk_walkers")
+    return w.value
+
+
+def read_chunk_sums(model: Model, ens: EnsembleDesc, obs_buf, n_out: int, k0: int = 0,
+                    n_rows: int | None = None, stream=None) -> np.ndarray:
+    """Per-chunk sums of output rows [k0, k0 + n_rows): [n_rows, chunks, 8 NS^2]."""
+    n_rows = n_out - k0 if n_rows is None else n_rows
+    nb = obs_buf.numel() * obs_buf.element_size()
+    nc = C.c_int64()
+    _check(load().qcl_read_chunk_sums(model.handle, C.byref(ens), _dptr(obs_buf), nb, n_out, k0,
+                                      n_rows, None, 0, C.byref(nc), _stream_ptr(stream)),
+           "qcl_read_chunk_sums")
+    out = np.zeros((n_rows, nc.value, 8 * model.ns * model.ns))
+    _check(load().qcl_read_chunk_sums(model.handle, C.byref(ens), _dptr(obs_buf), nb, n_out, k0,
+                                      n_rows, out.ctypes.data, out.size, C.byref(nc),
+                                      _stream_ptr(stream)), "qcl_read_chunk_sums")
+    return out
 
 
 def combine_shards(shard_sums) -> np.ndarray:

@@ -22,6 +22,8 @@ def test_flops_per_walker_step_follow_the_per_mode_count():
     assert bench.flops_per_traj_step(wl.config(4)["model"]) == 10 * 100 + 26
     assert bench.flops_per_traj_step(wl.config(3)["model"]) == 12 * 3 + 26
     assert bench.flops_per_traj_step(wl.random_lvc2(5, seed=1)) == 12 * 5 + 26
+    # more than two states: the scope's four-state figure
+    assert bench.flops_per_traj_step(wl.random_lvc4(3)) == bench.FLOPS_NSTATE
 
 
 def test_profiled_figures_are_dropped_when_the_sources_change(tmp_path):
@@ -79,3 +81,5 @@ def test_reference_arm_prints_one_json_line():
     assert d["cpu_baseline"]["value"] == d["value"]
     assert d["e2e"] == {"value": d["value"], "unit": "traj-steps/s", "h2d_bytes_per_step": 0,
                         "d2h_bytes_per_step": 0}
+    # the same metric and configuration as the GPU arm's line
+    assert d["config"] == bench.bench_config(wl.config(bench.WORKLOAD), 1)

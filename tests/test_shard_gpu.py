@@ -1,5 +1,7 @@
-"""Shards run one after another on one GPU (each with its own traj_id_offset)
-and combined on the host give the same bits as the unsharded ensemble."""
+"""Balanced shards run one after another on one GPU (each with its own
+traj_id_offset, starting on a 1024-tile chunk boundary): their chunk sums,
+folded on the host in walker order, give the same bits as the unsharded
+ensemble, for world sizes 2, 3 and 4."""
 import numpy as np
 import pytest
 
@@ -20,24 +22,34 @@ def q():
     return qcl
 
 
-@pytest.mark.parametrize("cfg_id,prec", [(2, 1), (1, 0), (4, 1)])
-def test_sharded_sums_equal_unsharded(q, cfg_id, prec):
+@pytest.mark.parametrize("cfg_id,prec", [(2, 1), (1, 0), (4, 1), (3, 1)])
+def test_sharded_chunk_sums_equal_unsharded(q, cfg_id, prec):
     cfg = wl.config(cfg_id)
-    n_traj, steps, stride = 256 * 37 + 5, 200, cfg["out_stride"]
+    steps, stride = 200, cfg["out_stride"]
     n_out = steps // stride + 1
     m = q.Model(cfg["model"])
+    chunk = q.shard_chunk_walkers(m, prec)
+    assert chunk == 1024 * q.shard_tile_walkers(m, prec)
+    n_traj = 3 * chunk + 12_345  # four chunks, the last one ragged
 
-    def sums(first, count):
-        run = q.Run(m, count, 3, prec, n_out, traj_id_offset=first)
-        run.sample(cfg["init"])
-        run.propagate(steps, cfg["dt"], stride)
-        return run.sums()
+    def run(first, count):
+        r = q.Run(m, count, 3, prec, n_out, traj_id_offset=first)
+        r.sample(cfg["init"])
+        r.propagate(steps, cfg["dt"], stride)
+        return r
 
-    single = sums(0, n_traj)
-    tile = q.shard_tile_walkers(m, prec)
-    for world in (2, 4):
+    whole = run(0, n_traj)
+    single = whole.sums()
+    cs = whole.chunk_sums()
+    assert cs.shape == (n_out, 4, single.shape[1])
+    assert np.array_equal(shard.combine_chunks(cs), single)
+    del whole
+    for world in (2, 3, 4):
         parts = []
         for r in range(world):
-            first, count = shard.shard_range(n_traj, world, r, tile)
-            parts.append(sums(first, count) if count > 0 else np.zeros_like(single))
-        assert np.array_equal(q.combine_shards(np.stack(parts)), single)
+            first, count = shard.shard_range(n_traj, world, r, chunk)
+            if count:
+                parts.append(run(first, count).chunk_sums())
+        joined = np.concatenate(parts, axis=1)
+        assert joined.shape[1] == 4
+        assert np.array_equal(shard.combine_chunks(joined), single), world
