@@ -195,8 +195,9 @@ __device__ __forceinline__ void weight_factor(ScalV<V>& z, V num, const typename
 // `deg` counts steps whose coupling was set to zero at a degeneracy.  The
 // weight and phase pairs are left unnormalised (|lo| may grow past ulp(hi)/2
 // by about an ulp per step); the step loop renormalises both at every fourth
-// step (block_end).
-template <int KIND, typename V>
+// step (block_end).  WEIGHT = false skips the phase and the weight (for holders
+// of a walker that need only its index pair: the split kernels' other roles).
+template <int KIND, bool WEIGHT = true, typename V>
 __device__ __forceinline__ void phase_and_transition(ScalV<V>& z, V r_old, V Av, V Bv,
                                                      const typename Lanes<V>::U& word,
                                                      const BulkParams& bp,
@@ -205,7 +206,8 @@ __device__ __forceinline__ void phase_and_transition(ScalV<V>& z, V r_old, V Av,
   // phase: dt/2 (w_ab(R_n) + w_ab(R_{n+1})), hbar w_ab = (sig_a - sig_b) r, added
   // to the low word of the pair (at most four increments and their rounding
   // errors until block_end folds it into hi)
-  z.ph.lo = vfma(vmul(splat<V>(bp.hdt_hbar), vsub(z.sa, z.sb)), vadd(r_old, z.r), z.ph.lo);
+  if (WEIGHT)
+    z.ph.lo = vfma(vmul(splat<V>(bp.hdt_hbar), vsub(z.sa, z.sb)), vadd(r_old, z.r), z.ph.lo);
   // coupling contracted with P/M: g = (a Bv - b Av) / (2 r^2)
   // (2 r < tol, compared as r^2 < tol^2 / 4); the spin-boson form has b = b0,
   // so -b/2 is a per-launch constant
@@ -250,7 +252,7 @@ __device__ __forceinline__ void phase_and_transition(ScalV<V>& z, V r_old, V Av,
     ln(z.sb, l) = hop2[l] ? ln(nsb, l) : ln(z.sb, l);
   }
   // (sigmas flipped after the weight factor has taken the pre-hop sigma in sel)
-  weight_factor(z, num, iden);
+  if (WEIGHT) weight_factor(z, num, iden);
 }
 
 // Diabatic representation: phase with hbar w_ab = V_aa - V_bb = -(sig_a - sig_b)

@@ -265,10 +265,13 @@ __device__ __forceinline__ void split_tiles_v(const BulkParams& bp, const Coef2&
         Bv = vfma(hu2, splat<V>(-bp.cab), v.v[3]);
         Bv = vfma(hv2, splat<V>(-bp.cbb), Bv);
       }
-      phase_and_transition<KIND>(z, r_old, Av, Bv, word, bp, deg);
+      // only role 0 keeps the weight and phase (it observes and stores them);
+      // the other roles need the index pair alone
+      if (role == 0) phase_and_transition<KIND, true>(z, r_old, Av, Bv, word, bp, deg);
+      else phase_and_transition<KIND, false>(z, r_old, Av, Bv, word, bp, deg);
       if (++widx == 4) {  // pairs renormalised at the end of every Philox block
         widx = 0;
-        block_end(z);
+        if (role == 0) block_end(z);
         ++blk;
         if (it + 1 < bp.len) {
 #pragma unroll

@@ -193,22 +193,92 @@ __device__ __forceinline__ void eigh_ns(const T (&W)[NS][NS], const T (*ref)[NS]
   }
 }
 
-// Warm-started decomposition for the FP32-bulk kernels: A = ref^T W ref (its
-// upper triangle), two cyclic Jacobi sweeps with the symmetric update
-// (a_pp -= t a_pq, a_qq += t a_pq, a_pq = 0, and the rows r != p, q rotated),
-// then U = ref V, eigenvalues ascending and each eigenvector's sign aligned with
-// its reference column.  The same rotations as eigh_ns in exact arithmetic, with
-// about a third fewer operations per rotation (no update of the elements the
-// rotation annihilates or leaves symmetric).
+// Warm-started decomposition for the FP32-bulk kernels.  A = ref^T W ref (its
+// upper triangle) is nearly diagonal: the previous step's eigenvectors ref
+// almost diagonalise W(R_{n+1}).  Two cyclic Jacobi sweeps annihilate the
+// off-diagonal elements with the symmetric update (a_pp -= t a_pq,
+// a_qq += t a_pq, a_pq = 0, rows r != p, q rotated), and each rotation is
+// applied to the columns of U, which starts as ref, so U = ref J_1 J_2 ...
+// directly.  Sweep 1 computes t = 2 a_pq / (d + sgn(d) sqrt(d^2 + 4 a_pq^2)),
+// d = a_qq - a_pp, c = 1 / sqrt(1 + t^2), s = t c.  After it the angles are
+// small: where every walker of the warp has |a_pq| <= 2^-12 |d| for every
+// pair, sweep 2 takes the small-angle form t = a_pq / d, c = 1, s = t, which
+// equals the full rotation in FP32 (t^2 / 2 <= 2^-25 rounds c to 1, and t
+// differs from a_pq / d by a relative t^2); otherwise (a walker near a
+// crossing) sweep 2 is a full sweep too.  Then the eigenvalues are sorted
+// ascending and each column of U is aligned in sign with its reference column
+// (parallel transport).
+template <int NS, bool SMALL, typename V>
+__device__ __forceinline__ void jacobi_sweep_warm(V (&A)[NS][NS], V (&U)[NS][NS]) {
+  constexpr bool small = SMALL;
+  constexpr int L = Lanes<V>::W;
+  auto at = [&](int i, int j) -> V& { return i < j ? A[i][j] : A[j][i]; };
+#pragma unroll
+  for (int p = 0; p < NS; ++p)
+#pragma unroll
+    for (int q = p + 1; q < NS; ++q) {
+      const V apq = A[p][q];
+      const V d = vsub(A[q][q], A[p][p]);
+      V t, c, sn;
+      if (small) {
+#pragma unroll
+        for (int l = 0; l < L; ++l)  // (a zero a_pq gives t = 0, also where d = 0)
+          ln(t, l) = ln(apq, l) == 0.0f ? 0.0f : __fdividef(ln(apq, l), ln(d, l));
+        sn = t;
+      } else {
+        const V twoa = vmul(splat<V>(2.0f), apq);
+        const V r2 = vfma(d, d, vmul(twoa, twoa));
+#pragma unroll
+        for (int l = 0; l < L; ++l) {
+          // d + sgn(d) sqrt(d^2 + 4 a_pq^2) is never 0 unless a_pq = 0 (then t = 0)
+          const float rl = ln(r2, l);
+          const float den = ln(d, l) + copysignf(rl * rsqrtf(rl), ln(d, l));
+          ln(t, l) = ln(apq, l) == 0.0f ? 0.0f : __fdividef(ln(twoa, l), den);
+        }
+        const V tt1 = vfma(t, t, splat<V>(1.0f));
+#pragma unroll
+        for (int l = 0; l < L; ++l) ln(c, l) = rsqrtf(ln(tt1, l));
+        sn = vmul(t, c);
+      }
+      const V nsn = vmul(sn, splat<V>(-1.0f));
+      A[p][p] = vfma(t, vmul(apq, splat<V>(-1.0f)), A[p][p]);  // a_pp - t a_pq
+      A[q][q] = vfma(t, apq, A[q][q]);
+      A[p][q] = splat<V>(0.0f);
+#pragma unroll
+      for (int r = 0; r < NS; ++r) {
+        if (r == p || r == q) continue;
+        const V arp = at(r, p), arq = at(r, q);
+        if (small) {
+          at(r, p) = vfma(nsn, arq, arp);
+          at(r, q) = vfma(sn, arp, arq);
+        } else {
+          at(r, p) = vfma(c, arp, vmul(nsn, arq));
+          at(r, q) = vfma(sn, arp, vmul(c, arq));
+        }
+      }
+#pragma unroll
+      for (int k = 0; k < NS; ++k) {
+        const V ukp = U[k][p], ukq = U[k][q];
+        if (small) {
+          U[k][p] = vfma(nsn, ukq, ukp);
+          U[k][q] = vfma(sn, ukp, ukq);
+        } else {
+          U[k][p] = vfma(c, ukp, vmul(nsn, ukq));
+          U[k][q] = vfma(sn, ukp, vmul(c, ukq));
+        }
+      }
+    }
+}
+
 template <int NS, typename V>
-__device__ __forceinline__ void eigh_warm_sym(const V (&W)[NS][NS], const V (&ref)[NS][NS],
-                                              V (&e)[NS], V (&U)[NS][NS]) {
+__device__ __forceinline__ void eigh_warm_fast(const V (&W)[NS][NS], const V (&ref)[NS][NS],
+                                               V (&e)[NS], V (&U)[NS][NS]) {
   // V = float (one walker) or float2 (two walkers, one per lane): the FP32
   // arithmetic is the packed lane arithmetic of lanes.cuh (explicit
   // round-to-nearest, so each lane's bits do not depend on the lane count);
   // divisions, square roots, compares and selects run per lane.
   constexpr int L = Lanes<V>::W;
-  V A[NS][NS], Vm[NS][NS];
+  V A[NS][NS];
   {
     V Wr[NS][NS];
 #pragma unroll
@@ -233,61 +303,30 @@ __device__ __forceinline__ void eigh_warm_sym(const V (&W)[NS][NS], const V (&re
 #pragma unroll
   for (int a = 0; a < NS; ++a)
 #pragma unroll
-    for (int b = 0; b < NS; ++b) Vm[a][b] = splat<V>(a == b ? 1.0f : 0.0f);
-  // upper-triangle element (i, j) of A for any order of i, j
-  auto at = [&](int i, int j) -> V& { return i < j ? A[i][j] : A[j][i]; };
+    for (int b = 0; b < NS; ++b) U[a][b] = ref[a][b];
+  // full sweeps (one copy of the code): the first always, the second where
+  // some walker of the warp still has a large angle; else the small-angle sweep
 #pragma unroll 1
   for (int sweep = 0; sweep < 2; ++sweep) {
+    if (sweep == 1) {
+      bool large = false;
 #pragma unroll
-    for (int p = 0; p < NS; ++p)
+      for (int l = 0; l < L; ++l)
 #pragma unroll
-      for (int q = p + 1; q < NS; ++q) {
-        const V apq = A[p][q];
-        // t = sgn(tau) / (|tau| + sqrt(1 + tau^2)) with approximate division and
-        // square root (c and s follow from the same t, so the rotation stays
-        // orthogonal to rounding); |tau| is capped at 1e18, where t < 1e-18; a
-        // zero a_pq selects the identity rotation
-        const V d = vsub(A[q][q], A[p][p]);
-        const V twoa = vmul(splat<V>(2.0f), apq);
-        V tau, t, c;
-        bool zero[L];
+        for (int p = 0; p < NS; ++p)
 #pragma unroll
-        for (int l = 0; l < L; ++l) {
-          zero[l] = ln(apq, l) == 0.0f;
-          ln(tau, l) = fminf(fmaxf(__fdividef(ln(d, l), zero[l] ? 2.0f : ln(twoa, l)), -1e18f), 1e18f);
-        }
-        const V w2 = vfma(tau, tau, splat<V>(1.0f));
-#pragma unroll
-        for (int l = 0; l < L; ++l) {
-          const float tl = ln(tau, l), wl = ln(w2, l);
-          const float tr = __fdividef(tl >= 0.0f ? 1.0f : -1.0f, __fmaf_rn(wl, rsqrtf(wl), fabsf(tl)));
-          ln(t, l) = zero[l] ? 0.0f : tr;
-        }
-        const V tt1 = vfma(t, t, splat<V>(1.0f));
-#pragma unroll
-        for (int l = 0; l < L; ++l) ln(c, l) = zero[l] ? 1.0f : rsqrtf(ln(tt1, l));
-        const V sn = vmul(t, c), nsn = vmul(sn, splat<V>(-1.0f));
-        A[p][p] = vfma(t, vmul(apq, splat<V>(-1.0f)), A[p][p]);  // a_pp - t a_pq
-        A[q][q] = vfma(t, apq, A[q][q]);
-        A[p][q] = splat<V>(0.0f);
-#pragma unroll
-        for (int r = 0; r < NS; ++r) {
-          if (r == p || r == q) continue;
-          const V arp = at(r, p), arq = at(r, q);
-          at(r, p) = vfma(c, arp, vmul(nsn, arq));
-          at(r, q) = vfma(sn, arp, vmul(c, arq));
-        }
-#pragma unroll
-        for (int k = 0; k < NS; ++k) {
-          const V vkp = Vm[k][p], vkq = Vm[k][q];
-          Vm[k][p] = vfma(c, vkp, vmul(nsn, vkq));
-          Vm[k][q] = vfma(sn, vkp, vmul(c, vkq));
-        }
+          for (int q = p + 1; q < NS; ++q)
+            large |= !(fabsf(ln(A[p][q], l)) * 4096.0f <= fabsf(ln(A[q][q], l) - ln(A[p][p], l)));
+      if (!__any_sync(0xffffffffu, large)) {
+        jacobi_sweep_warm<NS, true, V>(A, U);
+        break;
       }
+    }
+    jacobi_sweep_warm<NS, false, V>(A, U);
   }
 #pragma unroll
   for (int a = 0; a < NS; ++a) e[a] = A[a][a];
-  // ascending order of (e, columns of Vm) by a fixed compare network.  The warm
+  // ascending order of (e, columns of U) by a fixed compare network.  The warm
   // start keeps the reference's ascending order except where eigenvalues pass
   // each other, and on sorted input the network swaps nothing, so it runs only
   // when some walker of the warp is out of order (the same result either way).
@@ -309,27 +348,24 @@ __device__ __forceinline__ void eigh_warm_sym(const V (&W)[NS][NS], const V (&re
           ln(e[j - 1], l) = sw ? t0 : t1;
 #pragma unroll
           for (int k = 0; k < NS; ++k) {
-            const float u0 = ln(Vm[k][j], l), u1 = ln(Vm[k][j - 1], l);
-            ln(Vm[k][j], l) = sw ? u1 : u0;
-            ln(Vm[k][j - 1], l) = sw ? u0 : u1;
+            const float u0 = ln(U[k][j], l), u1 = ln(U[k][j - 1], l);
+            ln(U[k][j], l) = sw ? u1 : u0;
+            ln(U[k][j - 1], l) = sw ? u0 : u1;
           }
         }
   }
-  // U = ref Vm; eigenvector b follows reference column b: <U_b, ref_b> = Vm[b][b]
-  V sg[NS];
+  // eigenvector b follows reference column b
 #pragma unroll
-  for (int b = 0; b < NS; ++b)
+  for (int b = 0; b < NS; ++b) {
+    V dot = splat<V>(0.0f);
 #pragma unroll
-    for (int l = 0; l < L; ++l) ln(sg[b], l) = ln(Vm[b][b], l) < 0.0f ? -1.0f : 1.0f;
+    for (int i = 0; i < NS; ++i) dot = vfma(U[i][b], ref[i][b], dot);
+    V sg;
 #pragma unroll
-  for (int i = 0; i < NS; ++i)
+    for (int l = 0; l < L; ++l) ln(sg, l) = ln(dot, l) < 0.0f ? -1.0f : 1.0f;
 #pragma unroll
-    for (int b = 0; b < NS; ++b) {
-      V acc = splat<V>(0.0f);
-#pragma unroll
-      for (int k = 0; k < NS; ++k) acc = vfma(ref[i][k], Vm[k][b], acc);
-      U[i][b] = vmul(acc, sg[b]);
-    }
+    for (int i = 0; i < NS; ++i) U[i][b] = vmul(U[i][b], sg);
+  }
 }
 
 }  // namespace qcl

@@ -836,7 +836,7 @@ __global__ void __launch_bounds__(128, (BulkNMinBlocks<NS, NPL, WPT>::value))
 #pragma unroll
           for (int b = 0; b < NS; ++b) Uref[a][b] = U[a][b];
         build_w(W);
-        eigh_warm_sym<NS, V>(W, Uref, e, U);
+        eigh_warm_fast<NS, V>(W, Uref, e, U);
       }
       columns(ua, ub);  // (the new decomposition's columns, used twice)
       kick(ua, ub);     // second half kick at R_{n+1}
