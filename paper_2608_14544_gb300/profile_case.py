@@ -1,7 +1,10 @@
-"""One solve of a workload through the C ABI, for profilers (ncu): sample,
-propagate, reduce.  Prints the wall time; use bench.py for measurements.
+"""The profiling entry point: one solve of a workload through the C ABI
+(sample, propagate, reduce), or through the request server with --served, for
+ncu; the commands in profiles/ run it.  Prints the wall time; bench.py makes
+the measurements.
 
   python -m paper_2608_14544_gb300.profile_case --config 2 --n-traj 1048576 --steps 160
+  python -m paper_2608_14544_gb300.profile_case --config 2 --served --repeat 2
 """
 from __future__ import annotations
 
@@ -19,6 +22,8 @@ def main():
     ap.add_argument("--repr", default="adiabatic", choices=["adiabatic", "diabatic"])
     ap.add_argument("--spawn", type=int, default=0,
                     help="> 0: a spawning ensemble with this many walker slots per initial walker")
+    ap.add_argument("--served", action="store_true",
+                    help="submit the solve to the request server (qcl_server_submit / wait)")
     args = ap.parse_args()
 
     import torch
@@ -34,6 +39,19 @@ def main():
     steps = args.steps or cfg["n_steps"]
     stride = cfg["out_stride"]
     prec = qcl.PREC_FP32_BULK if args.precision == "fp32" else qcl.PREC_FP64
+    if args.served:
+        srv = qcl.Server(16 << 30, quantum_steps=steps)
+        req = dict(model=cfg["model"], init=cfg["init"], n_traj=n, seed=cfg["seed"],
+                   n_steps=steps, dt=cfg["dt"], out_stride=stride)
+        for _ in range(args.repeat):
+            t0 = time.perf_counter()
+            st, obs = srv.wait(srv.submit(req))
+            el = time.perf_counter() - t0
+            assert st == qcl.REQ_DONE
+            print(f"config {args.config} n_traj {n} steps {steps} served: {el * 1e3:.2f} ms, "
+                  f"{n * steps / el:.3e} traj-steps/s, trace(t_end) {obs[-1, 32]:.4f}")
+        srv.close()
+        return
     model = qcl.Model(cfg["model"])
     if args.spawn > 0:
         run = qcl.SpawnRun(model, n, args.spawn * n, cfg["seed"], steps // stride + 1,
