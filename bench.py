@@ -281,14 +281,17 @@ def ntraj_sweep_leg(qcl, torch, counts, steps: int):
 
 
 
-def served_mix_leg(qcl, reqs, arena_gb: float, quantum: int, paced: bool, peak_tflops: float):
+def served_mix_leg(qcl, reqs, arena_gb: float, quantum: int, paced: bool, peak_tflops: float,
+                   round_flops: float = 0.0):
     """Requests replayed against the server, either at their Poisson arrival
-    times (paced) or all at once (saturating): per-request latency (finish -
-    submit) percentiles, aggregate trajectory-steps/s over the host span and
-    over the device's busy time, and the algorithmic FP32 flops of all
-    requests against the FP32 peak (the fraction of the roofline the mix
-    reaches)."""
-    srv = qcl.Server(int(arena_gb * (1 << 30)), max_active=256, quantum_steps=quantum)
+    times (paced) or all at once (saturating), with every request advancing a
+    quantum per round (round_flops = 0) or the shortest remaining work first
+    under a round budget: per-request latency (finish - submit) percentiles,
+    aggregate trajectory-steps/s over the host span and over the device's busy
+    time, and the algorithmic FP32 flops of all requests against the FP32 peak
+    (the fraction of the roofline the mix reaches)."""
+    srv = qcl.Server(int(arena_gb * (1 << 30)), max_active=256, quantum_steps=quantum,
+                     round_flops=round_flops)
     t0 = time.perf_counter()
     ids = []
     for r in reqs:
@@ -312,6 +315,8 @@ def served_mix_leg(qcl, reqs, arena_gb: float, quantum: int, paced: bool, peak_t
     dev = st["device_busy_s"]
     achieved = flops / dev / 1e12 if dev > 0 else None
     return {"requests": len(reqs), "arrivals": "Poisson, mean gap 5 ms" if paced else "all at t = 0",
+            "scheduling": (f"shortest remaining work first, {round_flops:.0e} flops per round"
+                           if round_flops > 0 else "every active request a quantum per round"),
             "kinds_sb1_sb3_vib3_sb100_lvc4": kinds,
             "n_traj_range": [min(r["n_traj"] for r in reqs), max(r["n_traj"] for r in reqs)],
             "traj_steps": sum(float(r["n_traj"]) * r["n_steps"] for r in reqs),
@@ -643,8 +648,12 @@ def run_ours(args):
         legs["served_mix"] = {
             "paced": served_mix_leg(qcl, reqs, args.served_arena_gb, args.served_quantum, True,
                                     peak_tflops),
-            "saturating": served_mix_leg(qcl, reqs, args.served_arena_gb, args.served_quantum,
-                                         False, peak_tflops)}
+            "paced_shortest_first": served_mix_leg(qcl, reqs, args.served_arena_gb,
+                                                   args.served_quantum, True, peak_tflops,
+                                                   args.served_round_flops),
+            "saturating_shortest_first": served_mix_leg(qcl, reqs, args.served_arena_gb,
+                                                        args.served_quantum, False, peak_tflops,
+                                                        args.served_round_flops)}
 
     if rank != 0:
         if dist:
@@ -723,6 +732,8 @@ def main():
     ap.add_argument("--served-traj-max", type=float, default=1e7)
     ap.add_argument("--served-arena-gb", type=float, default=128.0)
     ap.add_argument("--served-quantum", type=int, default=400)
+    ap.add_argument("--served-round-flops", type=float, default=2e12,
+                    help="round work budget of the shortest-first served-mix legs")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

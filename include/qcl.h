@@ -489,6 +489,14 @@ typedef struct {
   int32_t use_graphs;     /* 1: replay the packed launches as a CUDA graph */
   int32_t max_queue;      /* queued requests beyond which submit returns BUSY (0: no limit) */
   double round_timeout_s; /* a round not finished after this long fails its requests (0: 600 s) */
+  double round_flops;     /* work budget per round in algorithmic flops (walkers x steps x
+                             flops per walker-step: 10 per mode + 26 for two-state models, 12
+                             per mode + 26 in their general form, 25 N_s^2 with more states).
+                             0: every active request advances quantum_steps each round.  > 0:
+                             requests advance in ascending order of remaining work (shortest
+                             first; one skipped 16 rounds in a row goes first) until the budget
+                             is spent, the last one by part of its quantum (at least one step),
+                             the others wait for a later round.  Results do not depend on it. */
 } qcl_server_desc;
 
 typedef struct {

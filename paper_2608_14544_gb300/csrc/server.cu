@@ -120,6 +120,8 @@ struct Request {
   size_t ens_off = 0, ens_bytes = 0, obs_off = 0, obs_bytes = 0;
   int64_t n_out = 0, step = 0;
   bool observed0 = false;
+  int skipped = 0;  // consecutive rounds without a step (round work budget)
+  int64_t round_quantum = 0;  // steps this round may take
   int bucket = -1;  // packed bucket, -1 = own launches
   double t_submit = 0, t_admit = 0, t_done = 0;
   std::vector<double> result;
@@ -233,6 +235,17 @@ struct Chunk {
   bool first;
 };
 
+// Algorithmic flops of one walker step of a request's model (its relative
+// cost): two-state models 10 per mode (12 in the general form) plus 26 scalar,
+// more states 25 N_s^2 (400 at four states).
+double step_flops(const Request& r) {
+  if (r.ns > 2) return 25.0 * r.ns * r.ns;
+  return (r.model && r.model->host.kind != 0 ? 12.0 : 10.0) * r.n + 26.0;
+}
+
+// Rounds skipped after which a request advances first, whatever its size.
+constexpr int kMaxSkipped = 16;
+
 Chunk plan(const Request& r, int64_t quantum) {
   Chunk c{};
   c.cs = r.step;
@@ -338,8 +351,40 @@ void run_round(qcl_server* s) {
     Chunk c;
   };
   std::vector<Item> items;
+  // With a round work budget, requests advance in ascending order of remaining
+  // work (those skipped kMaxSkipped rounds in a row first) until the budget is
+  // spent: a full quantum each, a partial one (at least one step) for the
+  // request that reaches the budget; the others wait for a later round.
+  if (s->d.round_flops > 0.0) {
+    std::vector<std::pair<double, std::shared_ptr<Request>>> order;
+    for (auto& r : act) {
+      const double rem = (double)r->ens.n_traj * (double)(r->n_steps - r->step) * step_flops(*r);
+      order.push_back({r->skipped >= kMaxSkipped ? -1.0 : rem, r});
+    }
+    std::stable_sort(order.begin(), order.end(),
+                     [](const auto& x, const auto& y) { return x.first < y.first; });
+    double left = s->d.round_flops;
+    act.clear();
+    std::vector<int64_t> steps;
+    for (auto& o : order) {
+      Request& r = *o.second;
+      if (left <= 0.0) {
+        ++r.skipped;
+        continue;
+      }
+      const double per_step = (double)r.ens.n_traj * step_flops(r);
+      const int64_t k = std::min<int64_t>(s->d.quantum_steps, std::max<int64_t>(1, (int64_t)(left / per_step)));
+      left -= (double)k * per_step;
+      r.skipped = 0;
+      act.push_back(o.second);
+      steps.push_back(k);
+    }
+    for (size_t i = 0; i < act.size(); ++i) act[i]->round_quantum = steps[i];
+  } else {
+    for (auto& r : act) r->round_quantum = s->d.quantum_steps;
+  }
   for (auto& r : act) {
-    const Chunk c = plan(*r, s->d.quantum_steps);
+    const Chunk c = plan(*r, r->round_quantum);
     items.push_back({r, c});
     if (r->bucket < 0) continue;
     PackedTable* T = htab(s, bulk_kind(r->model->host), r->bucket);
@@ -504,6 +549,7 @@ qcl_status qcl_server_create(const qcl_server_desc* d, qcl_server** out) {
   if (!d->arena || ((uintptr_t)d->arena & 255) != 0) return fail(QCL_ERR_INVALID_ARG, "arena must be a 256-byte aligned device pointer");
   if (d->arena_bytes < table_bytes() + (1 << 20)) return fail(QCL_ERR_OUT_OF_MEMORY, "arena smaller than %zu bytes", table_bytes() + (1 << 20));
   if (d->max_active < 1 || d->quantum_steps < 1) return fail(QCL_ERR_INVALID_ARG, "max_active and quantum_steps must be >= 1");
+  if (!(d->round_flops >= 0.0) || !std::isfinite(d->round_flops)) return fail(QCL_ERR_INVALID_ARG, "round_flops must be finite and >= 0");
   auto s = std::make_unique<qcl_server>();
   s->d = *d;
   cudaGetDevice(&s->device);

@@ -88,7 +88,7 @@ class InitDesc(C.Structure):
 class ServerDesc(C.Structure):
     _fields_ = [("arena", C.c_void_p), ("arena_bytes", C.c_size_t), ("max_active", C.c_int32),
                 ("quantum_steps", C.c_int32), ("use_graphs", C.c_int32), ("max_queue", C.c_int32),
-                ("round_timeout_s", C.c_double)]
+                ("round_timeout_s", C.c_double), ("round_flops", C.c_double)]
 
 
 class RequestDesc(C.Structure):
@@ -657,11 +657,11 @@ class Server:
 
     def __init__(self, arena_bytes: int, max_active: int = 64, quantum_steps: int = 200,
                  use_graphs: bool = True, max_queue: int = 0, round_timeout_s: float = 0.0,
-                 device="cuda"):
+                 round_flops: float = 0.0, device="cuda"):
         self.arena = device_buffer(arena_bytes, device)
         d = ServerDesc(self.arena.data_ptr(), int(arena_bytes), int(max_active),
                        int(quantum_steps), 1 if use_graphs else 0, int(max_queue),
-                       float(round_timeout_s))
+                       float(round_timeout_s), float(round_flops))
         h = C.c_void_p()
         _check(load().qcl_server_create(C.byref(d), C.byref(h)), "qcl_server_create")
         self.handle = h

@@ -111,6 +111,11 @@ def test_server_validation_without_gpu(lib):
     assert lib.qcl_server_create(C.byref(d), C.byref(h)) == 1 and not h.value
     d = qcl.ServerDesc(256, 1024, 4, 100, 1, 0, 0.0)
     assert lib.qcl_server_create(C.byref(d), C.byref(h)) == 3
+    # a negative or non-finite round work budget is rejected before any CUDA call
+    for bad in (-1.0, float("nan"), float("inf")):
+        d = qcl.ServerDesc(256, 1 << 30, 4, 100, 1, 0, 0.0, bad)
+        assert lib.qcl_server_create(C.byref(d), C.byref(h)) == 1 and not h.value
+        assert "round_flops" in qcl.last_error()
     assert lib.qcl_server_create(None, C.byref(h)) == 1
     assert lib.qcl_server_destroy(None) == 0
     st = C.c_int32()

@@ -134,6 +134,34 @@ def test_served_requests_match_oracle(q):
     srv.close()
 
 
+def test_round_budget_serves_short_requests_first_with_the_same_bits(q):
+    """With a round work budget the server advances the requests with the least
+    remaining work first: short requests submitted beside a long one finish
+    well before they would when every request advances a quantum per round,
+    and every result is the same bits either way."""
+    big = _req(wl.lvc4_config(5), 2_000_000, 2000, 1)
+    small = [_req(wl.config(1), 20_000, 1000, 10 + k) for k in range(4)]
+    res, lat = {}, {}
+    for budget in (0.0, 2e10):
+        srv = q.Server(8 << 30, quantum_steps=200, round_flops=budget)
+        t0 = time.perf_counter()
+        ids = [srv.submit(big)] + [srv.submit(r) for r in small]
+        out = []
+        for rid in ids[1:]:
+            st, obs = srv.wait(rid)
+            assert st == q.REQ_DONE
+            out.append(obs)
+        lat[budget] = time.perf_counter() - t0
+        st, obs = srv.wait(ids[0])
+        assert st == q.REQ_DONE
+        res[budget] = [obs] + out
+        assert srv.stats()["n_error"] == 0
+        srv.close()
+    for a, b in zip(res[0.0], res[2e10]):
+        assert np.array_equal(a, b)
+    assert lat[2e10] < 0.5 * lat[0.0], lat
+
+
 def test_admission_waits_for_arena_memory(q):
     cfg = wl.config(2)
     r = _req(cfg, 400_000, 600, 3)
