@@ -366,6 +366,8 @@ qcl_status qcl_measure_peak(int32_t which, double* flops_per_s, void* stream);
  *                       runs 1, so that every slot gets a tile.
  *   blocks_per_sm       resident blocks per SM of the persistent grid (0 = the
  *                       kernel's occupancy limit; larger values are clamped).
+ *   outputs_per_launch  output times per persistent launch, 1..32 (0 = 32): a
+ *                       propagate call is cut into launches at output steps.
  * Threads per block are fixed at 256: a block's threads hold one reduction
  * tile (or two, with two walkers per thread), whose size defines the
  * summation tree of every observable.
@@ -374,11 +376,13 @@ typedef struct {
   int32_t walkers_per_thread;
   int32_t blocks_per_sm;
   double walker_steps_per_s; /* rate measured by qcl_autotune for this shape (0 if set by hand) */
+  int32_t outputs_per_launch;
+  int32_t reserved;          /* must be 0 */
 } qcl_launch_shape;
 
 /* Sets the shape every later FP32-bulk launch for this model uses.
- * QCL_ERR_INVALID_ARG for walkers_per_thread outside {0, 1, 2} or negative
- * blocks_per_sm. */
+ * QCL_ERR_INVALID_ARG for walkers_per_thread outside {0, 1, 2}, negative
+ * blocks_per_sm or outputs_per_launch outside [0, 32]. */
 qcl_status qcl_set_launch_shape(qcl_model* model, const qcl_launch_shape* shape);
 qcl_status qcl_get_launch_shape(const qcl_model* model, qcl_launch_shape* shape);
 
@@ -391,8 +395,11 @@ qcl_status qcl_autotune_bytes(const qcl_model* model, int64_t probe_walkers, int
  * blocks per SM from 1 to the occupancy limit) on a probe ensemble sampled in
  * `scratch` (ground-state Wigner walkers at R = 0 in state 0, FP32 bulk),
  * each over n_steps steps of dt with outputs every out_stride steps after one
- * warm-up run, and stores the fastest in the model (as qcl_set_launch_shape);
- * *best receives it with its measured rate.  Synchronises the stream. */
+ * warm-up run; then, with the fastest of those, 8, 16 and 32 output times per
+ * launch over max(n_steps, 64 out_stride) steps.  Stores the fastest shape in
+ * the model (as qcl_set_launch_shape); *best receives it with its measured
+ * rate.  qcl_autotune_bytes sizes the scratch for the longer probe.
+ * Synchronises the stream. */
 qcl_status qcl_autotune(qcl_model* model, int64_t probe_walkers, int64_t n_steps, double dt,
                         int32_t out_stride, void* scratch, size_t scratch_bytes,
                         qcl_launch_shape* best, void* stream);

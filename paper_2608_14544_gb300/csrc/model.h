@@ -16,6 +16,7 @@ struct qcl_model {
   // launch shape of the FP32-bulk kernels (qcl_set_launch_shape / qcl_autotune;
   // 0 = default)
   int shape_wpt = 0, shape_bps = 0;
+  int shape_outs = 0;  // output times per persistent launch (0 = kChunkOut)
   double shape_rate = 0.0;
 };
 

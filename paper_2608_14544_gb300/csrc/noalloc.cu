@@ -101,7 +101,8 @@ extern "C" qcl_status qcl_propagate_noalloc(const qcl_model* model, const qcl_en
                 "%zu bytes (at most about %lld walkers for this model's %d-walker tiles)",
                 (long long)ens->n_traj, (long long)(per_slot * 8), kScratchBytes,
                 (long long)((int64_t)kScratchDoubles / (q2 + 1) * tile * 99 / 100), tile);
-  if (slots > kChunkOut) slots = kChunkOut;
+  const int outs = model->shape_outs > 0 ? model->shape_outs : kChunkOut;
+  if (slots > outs) slots = outs;
 
   double* scratch = nullptr;
   st = scratch_address(&scratch);

@@ -516,7 +516,8 @@ qcl_status qcl_propagate(const qcl_model* model, const qcl_ensemble_desc* ens, v
           for (int b = a; b < ns; ++b) cn->K[j][tri(a, b)] = (float)model->K[(size_t)j * ns * ns + a * ns + b];
       }
     }
-    // chunks of at most kChunkOut output times
+    // chunks of at most outs (the launch shape's outputs per launch) output times
+    const int outs = model->shape_outs > 0 ? model->shape_outs : kChunkOut;
     int64_t cs = step0;
     bool first = (step0 == 0);
     const int64_t end = step0 + n_steps;
@@ -524,9 +525,9 @@ qcl_status qcl_propagate(const qcl_model* model, const qcl_ensemble_desc* ens, v
       int64_t k_first = first ? 0 : cs / out_stride + 1;
       int n_slots = first ? 1 : 0;
       int64_t ce = cs;
-      // extend to the (kChunkOut - n_slots)-th output step after cs, or to end
+      // extend to the (outs - n_slots)-th output step after cs, or to end
       const int64_t next_out = (cs / out_stride + 1) * out_stride;
-      const int64_t room = kChunkOut - n_slots;
+      const int64_t room = outs - n_slots;
       int64_t last_out = next_out + (room - 1) * out_stride;
       if (last_out <= end) {
         ce = last_out;
@@ -687,8 +688,11 @@ qcl_status qcl_set_launch_shape(qcl_model* model, const qcl_launch_shape* shape)
   if (shape->walkers_per_thread < 0 || shape->walkers_per_thread > 2)
     return fail(QCL_ERR_INVALID_ARG, "walkers_per_thread must be 0, 1 or 2");
   if (shape->blocks_per_sm < 0) return fail(QCL_ERR_INVALID_ARG, "blocks_per_sm must be >= 0");
+  if (shape->outputs_per_launch < 0 || shape->outputs_per_launch > kChunkOut)
+    return fail(QCL_ERR_INVALID_ARG, "outputs_per_launch must be in [0, %d]", kChunkOut);
   model->shape_wpt = shape->walkers_per_thread;
   model->shape_bps = shape->blocks_per_sm;
+  model->shape_outs = shape->outputs_per_launch;
   model->shape_rate = shape->walker_steps_per_s;
   return ok();
 }
@@ -698,6 +702,8 @@ qcl_status qcl_get_launch_shape(const qcl_model* model, qcl_launch_shape* shape)
   shape->walkers_per_thread = model->shape_wpt;
   shape->blocks_per_sm = model->shape_bps;
   shape->walker_steps_per_s = model->shape_rate;
+  shape->outputs_per_launch = model->shape_outs;
+  shape->reserved = 0;
   return ok();
 }
 
@@ -709,10 +715,16 @@ struct ProbeSizes {
   int64_t n_out;
   size_t ens_bytes, obs_bytes, total;
 };
+// Steps of the outputs-per-launch probe: enough output times for two launches
+// of the largest candidate.
+int64_t outs_probe_steps(int64_t n_steps, int32_t out_stride) {
+  return std::max<int64_t>(n_steps, 2 * (int64_t)kChunkOut * out_stride);
+}
+
 ProbeSizes probe_sizes(const qcl_model* model, int64_t probe_walkers, int64_t n_steps, int32_t out_stride) {
   ProbeSizes p{};
   p.ens = qcl_ensemble_desc{probe_walkers, 0x5EEDull, 0, QCL_PREC_FP32_BULK, 0};
-  p.n_out = n_steps / out_stride + 1;
+  p.n_out = outs_probe_steps(n_steps, out_stride) / out_stride + 1;
   p.ens_bytes = align256(EnsLayout::make(probe_walkers, model->ns, model->n, QCL_PREC_FP32_BULK).total);
   p.obs_bytes = ObsLayout::make(probe_walkers, model->ns, p.n_out,
                                 tile_walkers(QCL_PREC_FP32_BULK, model->n, model->ns)).total;
@@ -750,7 +762,7 @@ qcl_status qcl_autotune(qcl_model* model, int64_t probe_walkers, int64_t n_steps
   const bool dia = model->host.repr == QCL_REPR_DIABATIC;
   const bool two_state_reg = ns == 2 && (dia ? n <= 32 : (n <= 8 || (n > 32 && n <= 256)));
   const int wmax = (ns == 2 && (dia ? n <= 8 : max_wpt(n) == 2)) ? 2 : 1;
-  const int keep_wpt = model->shape_wpt, keep_bps = model->shape_bps;
+  const int keep_wpt = model->shape_wpt, keep_bps = model->shape_bps, keep_outs = model->shape_outs;
   const double keep_rate = model->shape_rate;
   cudaStream_t s = (cudaStream_t)stream;
   char* ens_buf = (char*)scratch;
@@ -759,7 +771,22 @@ qcl_status qcl_autotune(qcl_model* model, int64_t probe_walkers, int64_t n_steps
   CUDA_TRY(cudaEventCreate(&e0));
   CUDA_TRY(cudaEventCreate(&e1));
   float best_ms = -1.0f;
-  int best_wpt = 1, best_bps = 0;
+  int best_wpt = 1, best_bps = 0, best_outs = 0;
+  // one warm-up run and one timed run of the probe with the model's current shape
+  auto time_probe = [&](int64_t steps, float* ms) -> qcl_status {
+    qcl_status r = QCL_OK;
+    for (int rep = 0; rep < 2 && !r; ++rep) {
+      r = qcl_sample_initial(model, &ps.ens, &init, ens_buf, ps.ens_bytes, stream);
+      if (!r) cudaEventRecord(e0, s);
+      if (!r) r = qcl_propagate(model, &ps.ens, ens_buf, ps.ens_bytes, 0, steps, dt, out_stride, obs_buf,
+                                ps.obs_bytes, ps.n_out, stream);
+      if (!r) cudaEventRecord(e1, s);
+      if (!r && cudaEventSynchronize(e1) != cudaSuccess) r = fail(QCL_ERR_CUDA, "autotune: event wait failed");
+      if (!r) cudaEventElapsedTime(ms, e0, e1);
+    }
+    return r;
+  };
+  model->shape_outs = 0;
   for (int wpt = 1; wpt <= wmax; ++wpt) {
     int limit = two_state_reg ? bulk2_blocks_per_sm(n, bulk_kind(model->host), model->host.repr, wpt) : 4;
     if (limit < 1) limit = 1;
@@ -767,15 +794,7 @@ qcl_status qcl_autotune(qcl_model* model, int64_t probe_walkers, int64_t n_steps
       model->shape_wpt = wpt;
       model->shape_bps = bps;
       float ms = 0.0f;
-      for (int rep = 0; rep < 2 && !st; ++rep) {  // the first run is the warm-up
-        st = qcl_sample_initial(model, &ps.ens, &init, ens_buf, ps.ens_bytes, stream);
-        if (!st) cudaEventRecord(e0, s);
-        if (!st) st = qcl_propagate(model, &ps.ens, ens_buf, ps.ens_bytes, 0, n_steps, dt, out_stride, obs_buf,
-                                    ps.obs_bytes, ps.n_out, stream);
-        if (!st) cudaEventRecord(e1, s);
-        if (!st && cudaEventSynchronize(e1) != cudaSuccess) st = fail(QCL_ERR_CUDA, "autotune: event wait failed");
-        if (!st) cudaEventElapsedTime(&ms, e0, e1);
-      }
+      st = time_probe(n_steps, &ms);
       if (st) break;
       if (best_ms < 0.0f || ms < best_ms) {
         best_ms = ms;
@@ -785,19 +804,38 @@ qcl_status qcl_autotune(qcl_model* model, int64_t probe_walkers, int64_t n_steps
     }
     if (st) break;
   }
+  // output times per launch, with the fastest walkers per thread and blocks per SM
+  const int64_t steps2 = outs_probe_steps(n_steps, out_stride);
+  float best2 = -1.0f;
+  for (int outs : {8, 16, 32}) {
+    if (st) break;
+    model->shape_wpt = best_wpt;
+    model->shape_bps = best_bps;
+    model->shape_outs = outs;
+    float ms = 0.0f;
+    st = time_probe(steps2, &ms);
+    if (!st && (best2 < 0.0f || ms < best2)) {
+      best2 = ms;
+      best_outs = outs;
+    }
+  }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   if (st) {
     model->shape_wpt = keep_wpt;
     model->shape_bps = keep_bps;
+    model->shape_outs = keep_outs;
     model->shape_rate = keep_rate;
     return st;
   }
   model->shape_wpt = best_wpt;
   model->shape_bps = best_bps;
-  model->shape_rate = best_ms > 0.0f ? (double)probe_walkers * (double)n_steps / (best_ms * 1e-3) : 0.0;
+  model->shape_outs = best_outs;
+  model->shape_rate = best2 > 0.0f ? (double)probe_walkers * (double)steps2 / (best2 * 1e-3) : 0.0;
   best->walkers_per_thread = best_wpt;
   best->blocks_per_sm = best_bps;
+  best->outputs_per_launch = best_outs;
+  best->reserved = 0;
   best->walker_steps_per_s = model->shape_rate;
   return ok();
 }

@@ -72,7 +72,8 @@ def repr_code(m: dict) -> int:
 
 class LaunchShape(C.Structure):
     _fields_ = [("walkers_per_thread", C.c_int32), ("blocks_per_sm", C.c_int32),
-                ("walker_steps_per_s", C.c_double)]
+                ("walker_steps_per_s", C.c_double), ("outputs_per_launch", C.c_int32),
+                ("reserved", C.c_int32)]
 
 
 class EnsembleDesc(C.Structure):
@@ -244,17 +245,24 @@ class Model:
             load().qcl_destroy_model(self.handle)
             self.handle = None
 
-    def set_launch_shape(self, walkers_per_thread: int = 0, blocks_per_sm: int = 0):
+    def set_launch_shape(self, walkers_per_thread: int = 0, blocks_per_sm: int = 0,
+                         outputs_per_launch: int = 0):
         """Launch shape of the FP32-bulk kernels (0 = default); results do not
         depend on it."""
-        sh = LaunchShape(int(walkers_per_thread), int(blocks_per_sm), 0.0)
+        sh = LaunchShape(int(walkers_per_thread), int(blocks_per_sm), 0.0,
+                         int(outputs_per_launch), 0)
         _check(load().qcl_set_launch_shape(self.handle, C.byref(sh)), "qcl_set_launch_shape")
+
+    @staticmethod
+    def _shape_dict(sh) -> dict:
+        return {"walkers_per_thread": sh.walkers_per_thread, "blocks_per_sm": sh.blocks_per_sm,
+                "outputs_per_launch": sh.outputs_per_launch,
+                "walker_steps_per_s": sh.walker_steps_per_s}
 
     def launch_shape(self) -> dict:
         sh = LaunchShape()
         _check(load().qcl_get_launch_shape(self.handle, C.byref(sh)), "qcl_get_launch_shape")
-        return {"walkers_per_thread": sh.walkers_per_thread, "blocks_per_sm": sh.blocks_per_sm,
-                "walker_steps_per_s": sh.walker_steps_per_s}
+        return self._shape_dict(sh)
 
     def autotune(self, dt: float, out_stride: int, probe_walkers: int = 1 << 20,
                  n_steps: int = 160, stream=None) -> dict:
@@ -269,8 +277,7 @@ class Model:
                                    _dptr(scratch), b.value, C.byref(sh), _stream_ptr(stream)),
                "qcl_autotune")
         del scratch
-        return {"walkers_per_thread": sh.walkers_per_thread, "blocks_per_sm": sh.blocks_per_sm,
-                "walker_steps_per_s": sh.walker_steps_per_s}
+        return self._shape_dict(sh)
 
     def __del__(self):
         try:

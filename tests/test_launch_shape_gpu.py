@@ -1,5 +1,6 @@
-"""Launch shapes of the FP32-bulk kernels (walkers per thread, blocks per SM)
-change no bit of any result, and the autotuner picks one of them."""
+"""Launch shapes of the FP32-bulk kernels (walkers per thread, blocks per SM,
+output times per launch) change no bit of any result, and the autotuner picks
+one of them."""
 import copy
 
 import numpy as np
@@ -43,9 +44,9 @@ def test_every_launch_shape_gives_the_same_bits(q, name, cfg):
     # walkers-per-thread 2 is launched as asked (smaller ensembles run 1)
     n, steps, stride = 150_001, 120, 10
     outs = []
-    for wpt, bps in ((1, 0), (2, 0), (1, 1), (2, 1), (0, 2), (0, 0)):
+    for wpt, bps, opl in ((1, 0, 0), (2, 0, 0), (1, 1, 8), (2, 1, 16), (0, 2, 1), (0, 0, 3)):
         m = q.Model(cfg["model"])
-        m.set_launch_shape(wpt, bps)
+        m.set_launch_shape(wpt, bps, opl)
         run = q.Run(m, n, 6, q.PREC_FP32_BULK, steps // stride + 1)
         run.sample(cfg["init"])
         run.propagate(55, cfg["dt"], stride)
@@ -64,6 +65,7 @@ def test_autotune_picks_a_measured_shape(q):
     best = m.autotune(cfg["dt"], cfg["out_stride"], probe_walkers=1 << 19, n_steps=80)
     assert best["walkers_per_thread"] in (1, 2)
     assert best["blocks_per_sm"] >= 1
+    assert best["outputs_per_launch"] in (8, 16, 32)
     assert best["walker_steps_per_s"] > 1e9
     assert m.launch_shape() == best
     # the model keeps solving with the tuned shape, same bits as the default
@@ -74,6 +76,14 @@ def test_autotune_picks_a_measured_shape(q):
         run.propagate(100, cfg["dt"], 10)
         res.append(run.sums())
     assert np.array_equal(res[0], res[1])
+
+
+def test_launch_shape_range_is_checked(q):
+    m = q.Model(wl.config(1)["model"])
+    for bad in ((3, 0, 0), (0, -1, 0), (0, 0, 33), (0, 0, -1)):
+        with pytest.raises(q.QclError) as e:
+            m.set_launch_shape(*bad)
+        assert e.value.status == 1
 
 
 def test_fma_microbenchmarks_are_plausible(q):
