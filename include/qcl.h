@@ -69,10 +69,13 @@ typedef int32_t qcl_status;
  * II C are instances): V(R) = 1/2 sum_j M_j w_j^2 R_j^2 + W(R),
  * W(R) = E + sum_j R_j K_j; E and each K_j are real symmetric
  * n_states x n_states, row-major; K is [n_modes][n_states * n_states].  All
- * arrays are host memory, copied by qcl_create_model.  hop_scale (kappa, > 0)
- * and p_max (in (0, 1)) shape the transition probabilities
- * p_e = min(kappa |A_e|, p_max), scaled down together when their sum exceeds
- * p_max; 0 selects the defaults 1 and 0.5. */
+ * arrays are host memory, copied by qcl_create_model.  hop_scale (kappa, in
+ * [2^-16, 2^16]) and p_max (in (0, 1 - 2^-16]) shape the transition
+ * probabilities p_e = min(kappa |A_e|, p_max), scaled down together when their
+ * sum exceeds p_max; 0 selects the defaults 1 and 0.5.  (The bounds keep a
+ * step's weight factor -- 1/(1 - sum p), or |A_e|/p_e after a transition --
+ * within [2^-16, 2^17] except where |A_e| itself is large; values outside them
+ * are rejected with QCL_ERR_INVALID_ARG.) */
 typedef struct {
   int32_t n_states;
   int32_t n_modes;

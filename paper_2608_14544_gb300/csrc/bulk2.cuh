@@ -167,10 +167,17 @@ __device__ __forceinline__ void weight_range(ScalV<V>& z, int l) {
 
 // m *= num / den (den an integer below 2^25, so exact in FP32) as a
 // compensated quotient: rcp.approx, one exact FMA residual, and the product
-// with the error terms collected in lo, then the range check.  (Checking only
-// after hops and at block ends measured slower: the branch costs more than
-// the two compares it saves.)
-template <typename V>
+// with the error terms collected in lo, then (CHECK) the range check.  The
+// persistent two-state kernels pass CHECK = false and check the range where the
+// pairs are renormalised (block_end, every fourth absolute step) and before
+// each observation.  Model creation bounds the parameter-fixed factors to
+// [2^-16, 2^17] (stay 1/(1 - sum p), uncapped hop in [1/kappa, 2/kappa)), so
+// four of them take a mantissa in [2^-32, 2^32] to [2^-96, 2^100]: hi and lo
+// stay normal FP32 numbers and moving the exponent later is exact, so the
+// values and observables are those of a per-step check.  Only capped hops,
+// |A_e| / p_e ~ 2 |A_e| / p_max, grow with the data; four of them beyond 2^23
+// overflow hi, which the store flags as non-finite.
+template <bool CHECK = true, typename V>
 __device__ __forceinline__ void weight_factor(ScalV<V>& z, V num, const typename Lanes<V>::U& iden) {
   V den, rd;
 #pragma unroll
@@ -185,8 +192,10 @@ __device__ __forceinline__ void weight_factor(ScalV<V>& z, V num, const typename
   V e = vfma(z.m.hi, q0, vmul(p, splat<V>(-1.0f)));
   e = vfma(z.m.hi, q1, e);
   z.m = {p, vfma(z.m.lo, q0, e)};
+  if (CHECK) {
 #pragma unroll
-  for (int l = 0; l < Lanes<V>::W; ++l) weight_range(z, l);
+    for (int l = 0; l < Lanes<V>::W; ++l) weight_range(z, l);
+  }
 }
 
 // Phase (trapezoid) and transition of one step, given the decomposition at
@@ -197,7 +206,7 @@ __device__ __forceinline__ void weight_factor(ScalV<V>& z, V num, const typename
 // by about an ulp per step); the step loop renormalises both at every fourth
 // step (block_end).  WEIGHT = false skips the phase and the weight (for holders
 // of a walker that need only its index pair: the split kernels' other roles).
-template <int KIND, bool WEIGHT = true, typename V>
+template <int KIND, bool WEIGHT = true, bool CHECK = true, bool LANE_PHASE = false, typename V>
 __device__ __forceinline__ void phase_and_transition(ScalV<V>& z, V r_old, V Av, V Bv,
                                                      const typename Lanes<V>::U& word,
                                                      const BulkParams& bp,
@@ -206,8 +215,19 @@ __device__ __forceinline__ void phase_and_transition(ScalV<V>& z, V r_old, V Av,
   // phase: dt/2 (w_ab(R_n) + w_ab(R_{n+1})), hbar w_ab = (sig_a - sig_b) r, added
   // to the low word of the pair (at most four increments and their rounding
   // errors until block_end folds it into hi)
-  if (WEIGHT)
+  // LANE_PHASE: per lane with the scalar round-to-nearest operations.  Measured
+  // on GB300: in the branch-free step (CHECK = false) the packed form of this one
+  // update gave results one ulp apart between one and two walkers per thread,
+  // while the per-lane form keeps both bit for bit (and equal to the packed form
+  // in the step with the range check).
+  if (WEIGHT && LANE_PHASE) {
+#pragma unroll
+    for (int l = 0; l < W; ++l)
+      ln(z.ph.lo, l) = __fmaf_rn(__fmul_rn(bp.hdt_hbar, __fsub_rn(ln(z.sa, l), ln(z.sb, l))),
+                                 __fadd_rn(ln(r_old, l), ln(z.r, l)), ln(z.ph.lo, l));
+  } else if (WEIGHT) {
     z.ph.lo = vfma(vmul(splat<V>(bp.hdt_hbar), vsub(z.sa, z.sb)), vadd(r_old, z.r), z.ph.lo);
+  }
   // coupling contracted with P/M: g = (a Bv - b Av) / (2 r^2)
   // (2 r < tol, compared as r^2 < tol^2 / 4); the spin-boson form has b = b0,
   // so -b/2 is a per-launch constant
@@ -252,7 +272,7 @@ __device__ __forceinline__ void phase_and_transition(ScalV<V>& z, V r_old, V Av,
     ln(z.sb, l) = hop2[l] ? ln(nsb, l) : ln(z.sb, l);
   }
   // (sigmas flipped after the weight factor has taken the pre-hop sigma in sel)
-  if (WEIGHT) weight_factor(z, num, iden);
+  if (WEIGHT) weight_factor<CHECK>(z, num, iden);
 }
 
 // Diabatic representation: phase with hbar w_ab = V_aa - V_bb = -(sig_a - sig_b)
@@ -261,12 +281,15 @@ __device__ __forceinline__ void phase_and_transition(ScalV<V>& z, V r_old, V Av,
 // (+i c) with c = V_01 dt / hbar = b(R_{n+1}) dt / hbar = amp * Bc.  Both have
 // |A_e| = |c|, so the thresholds follow the adiabatic rule; a hop adds three or
 // one quarter turns.
-template <typename V>
+template <bool CHECK = true, typename V>
 __device__ __forceinline__ void dia_phase_and_transition(ScalV<V>& z, V a_old, V Bc,
                                                          const typename Lanes<V>::U& word,
                                                          const BulkParams& bp) {
   constexpr int W = Lanes<V>::W;
-  z.ph.lo = vfma(vmul(splat<V>(bp.hdt_hbar), vsub(z.sb, z.sa)), vadd(a_old, z.A), z.ph.lo);
+#pragma unroll
+  for (int l = 0; l < W; ++l)  // (per lane, as in phase_and_transition)
+    ln(z.ph.lo, l) = __fmaf_rn(__fmul_rn(bp.hdt_hbar, __fsub_rn(ln(z.sb, l), ln(z.sa, l))),
+                               __fadd_rn(ln(a_old, l), ln(z.A, l)), ln(z.ph.lo, l));
   const V t = vmul(splat<V>(bp.kamp * kP24f), Bc);
   V num = vmul(splat<V>(bp.amp * kP24f), Bc);
   typename Lanes<V>::U iden;
@@ -281,7 +304,7 @@ __device__ __forceinline__ void dia_phase_and_transition(ScalV<V>& z, V a_old, V
     ln(num, l) = hop[l] ? ln(num, l) : kP24f;
     ln(iden, l) = hop[l] ? T : 16777216u - 2u * T;
   }
-  weight_factor(z, num, iden);
+  weight_factor<CHECK>(z, num, iden);
   const V nsa = vmul(z.sa, splat<V>(-1.0f)), nsb = vmul(z.sb, splat<V>(-1.0f));
 #pragma unroll
   for (int l = 0; l < W; ++l) {
@@ -291,12 +314,18 @@ __device__ __forceinline__ void dia_phase_and_transition(ScalV<V>& z, V a_old, V
   }
 }
 
-// Renormalises the weight and phase pairs; called at the end of every Philox
-// block (absolute steps 4k + 3), whatever the chunking.
-template <typename V>
+// Renormalises the weight and phase pairs and (CHECK) checks the weight's
+// range; called at the end of every Philox block (absolute steps 4k + 3),
+// whatever the chunking.  Kernels whose steps check the range themselves pass
+// CHECK = false.
+template <bool CHECK = true, typename V>
 __device__ __forceinline__ void block_end(ScalV<V>& z) {
   z.m = fast_two_sum_v(z.m.hi, z.m.lo);
   z.ph = two_sum_v(z.ph.hi, z.ph.lo);
+  if (CHECK) {
+#pragma unroll
+    for (int l = 0; l < Lanes<V>::W; ++l) weight_range(z, l);
+  }
 }
 
 // FP32 initial sample of one walker with random-stream id `traj` from the same
@@ -729,6 +758,8 @@ __device__ __forceinline__ void bulk2_tile(const BulkParams& bp, const CF& cf, W
   // rewritten only after the barrier that follows the warps' reads of it.
   auto observe_all = [&](int slot) {
 #pragma unroll
+    for (int k = 0; k < WPT; ++k) weight_range(z, k);
+#pragma unroll
     for (int k = 0; k < WPT; ++k) {
       Scal zk = lane_of(z, k);
       observe_warp<DIA>(zk, active[k], obs_rows, threadIdx.x, warp * 32, lane,
@@ -759,7 +790,7 @@ __device__ __forceinline__ void bulk2_tile(const BulkParams& bp, const CF& cf, W
         if (KIND == 1) z.B = vfma(splat<V>(cf.b[j]), w.R[j], z.B);
       }
       kick_dia<NPL, KIND, CF>(w, cf, hsab);
-      dia_phase_and_transition(z, a_old, z.B, word, bp);
+      dia_phase_and_transition<false>(z, a_old, z.B, word, bp);
       return;
     }
     kick<NPL, KIND, CF>(w, cf, vmul(hsab, z.c2), vmul(hsab, z.s2));  // first half kick at R_n
@@ -781,7 +812,7 @@ __device__ __forceinline__ void bulk2_tile(const BulkParams& bp, const CF& cf, W
       Av = vfma(splat<V>(cf.am[j]), w.P[j], Av);
       if (KIND == 1) Bv = vfma(splat<V>(cf.bm[j]), w.P[j], Bv);
     }
-    phase_and_transition<KIND>(z, r_old, Av, Bv, word, bp, deg);
+    phase_and_transition<KIND, true, false, true>(z, r_old, Av, Bv, word, bp, deg);
   };
 
   // Steps are grouped by Philox block (four steps share one draw).  A whole

@@ -267,11 +267,13 @@ __device__ __forceinline__ void split_tiles_v(const BulkParams& bp, const Coef2&
       }
       // only role 0 keeps the weight and phase (it observes and stores them);
       // the other roles need the index pair alone
+      // (the split kernel keeps the per-step range check and the packed phase
+      // update: measured faster here than the branch-free form)
       if (role == 0) phase_and_transition<KIND, true>(z, r_old, Av, Bv, word, bp, deg);
       else phase_and_transition<KIND, false>(z, r_old, Av, Bv, word, bp, deg);
       if (++widx == 4) {  // pairs renormalised at the end of every Philox block
         widx = 0;
-        if (role == 0) block_end(z);
+        if (role == 0) block_end<false>(z);
         ++blk;
         if (it + 1 < bp.len) {
 #pragma unroll

@@ -212,8 +212,11 @@ qcl_status qcl_create_model(const qcl_model_desc* d, qcl_model** out) {
   if (!(d->hbar > 0.0) || !std::isfinite(d->hbar)) return fail(QCL_ERR_INVALID_ARG, "hbar must be positive");
   const double hop = d->hop_scale == 0.0 ? 1.0 : d->hop_scale;
   const double pmax = d->p_max == 0.0 ? 0.5 : d->p_max;
-  if (!(hop > 0.0) || !std::isfinite(hop)) return fail(QCL_ERR_INVALID_ARG, "hop_scale must be positive");
-  if (!(pmax > 0.0 && pmax < 1.0)) return fail(QCL_ERR_INVALID_ARG, "p_max must lie in (0, 1)");
+  // (bounds that keep one step's weight factor within [2^-16, 2^17] wherever
+  // it follows from the model: the FP32-bulk steps check the weight's range
+  // only every fourth step)
+  if (!(hop >= 0x1p-16 && hop <= 0x1p16)) return fail(QCL_ERR_INVALID_ARG, "hop_scale = %g outside [2^-16, 2^16]", hop);
+  if (!(pmax > 0.0 && pmax <= 1.0 - 0x1p-16)) return fail(QCL_ERR_INVALID_ARG, "p_max = %g outside (0, 1 - 2^-16]", pmax);
   if (d->repr != QCL_REPR_ADIABATIC && d->repr != QCL_REPR_DIABATIC) return fail(QCL_ERR_INVALID_ARG, "repr = %d is neither adiabatic (0) nor diabatic (1)", d->repr);
   if (d->repr == QCL_REPR_DIABATIC && ns != 2) return fail(QCL_ERR_UNSUPPORTED, "the diabatic representation takes two-state models (n_states = %d)", ns);
   if (d->reserved != 0) return fail(QCL_ERR_INVALID_ARG, "reserved must be 0");

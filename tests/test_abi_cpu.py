@@ -53,11 +53,11 @@ def test_library_targets_sm_103a(lib):
 def test_model_validation_without_gpu(lib):
     from paper_2608_14544_gb300 import qcl
 
-    def desc(ns, n, E, K, mass=None, omega=None, hbar=1.0, pmax=0.5, rep=0, reserved=0):
+    def desc(ns, n, E, K, mass=None, omega=None, hbar=1.0, pmax=0.5, rep=0, reserved=0, hop=1.0):
         arrs = [np.ones(n) if mass is None else np.asarray(mass, float),
                 np.ones(n) if omega is None else np.asarray(omega, float),
                 np.ascontiguousarray(E, dtype=float), np.ascontiguousarray(K, dtype=float)]
-        d = qcl.ModelDesc(ns, n, hbar, *[a.ctypes.data for a in arrs], 1.0, pmax, rep, reserved)
+        d = qcl.ModelDesc(ns, n, hbar, *[a.ctypes.data for a in arrs], hop, pmax, rep, reserved)
         return d, arrs
 
     h = C.c_void_p()
@@ -72,6 +72,13 @@ def test_model_validation_without_gpu(lib):
     assert lib.qcl_create_model(C.byref(d), C.byref(h)) == 1
     d, keep = desc(2, 1, E, K, pmax=1.5)
     assert lib.qcl_create_model(C.byref(d), C.byref(h)) == 1
+    # transition-probability shape: a step's weight factor stays within
+    # [2^-16, 2^17] where the model fixes it (stay 1/(1 - p), hop 1/kappa .. 2/kappa)
+    for hop, pmax in ((2.0 ** -17, 0.5), (2.0 ** 17, 0.5), (-1.0, 0.5), (float("nan"), 0.5),
+                      (1.0, 1.0 - 2.0 ** -17), (1.0, 1.0), (1.0, -0.1)):
+        d, keep = desc(2, 1, E, K, pmax=pmax, hop=hop)
+        assert lib.qcl_create_model(C.byref(d), C.byref(h)) == 1 and not h.value, (hop, pmax)
+        assert b"hop_scale" in lib.qcl_last_error() or b"p_max" in lib.qcl_last_error()
     d, keep = desc(9, 1, np.eye(9), np.zeros((1, 9, 9)))
     assert lib.qcl_create_model(C.byref(d), C.byref(h)) == 2
     assert lib.qcl_create_model(None, C.byref(h)) == 1
