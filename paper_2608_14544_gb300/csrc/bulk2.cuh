@@ -635,7 +635,7 @@ __device__ __forceinline__ void observe_warp(Scal& z, bool active, float* obs_ro
     col = lane;
   }
   const int ex = (ew < -(1 << 27)) ? 0 : ((col < 16) ? ew : 2 * ew);
-  red_row[col] = scaled_double_fp64(x, ex);
+  red_row[col] = scaled_double(x, ex);
 }
 
 __device__ __forceinline__ uint32_t pick_word(const u4& wd, int widx) {

@@ -710,9 +710,8 @@ __global__ void __launch_bounds__(128, (BulkNMinBlocks<NS, NPL, WPT>::value))
           ln(ub[i], l) = vb;
         }
     };
-    // e_al - e_be (per lane picks)
-    auto gap_ab = [&]() {
-      V ea, eb;
+    // e_al, e_be (per lane picks) and their difference
+    auto gap_ab = [&](V& ea, V& eb) {
 #pragma unroll
       for (int l = 0; l < WPT; ++l) {
         float va = ln(e[0], l), vb = va;
@@ -727,9 +726,10 @@ __global__ void __launch_bounds__(128, (BulkNMinBlocks<NS, NPL, WPT>::value))
       }
       return vsub(ea, eb);
     };
-    // P += dt/2 F_ab with dt/2 * (1/2)(u_a u_a^T + u_b u_b^T) folded with the
-    // off-diagonal factor 2 (ua, ub: columns al, be of U)
-    auto kick = [&](const V (&ua)[NS], const V (&ub)[NS]) {
+    // the coupling part of dt/2 F_ab: g_j = sum_k K_jk Q_k with
+    // Q = dt/2 * (1/2)(u_a u_a^T + u_b u_b^T) folded with the off-diagonal
+    // factor 2 (ua, ub: columns al, be of U)
+    auto force = [&](const V (&ua)[NS], const V (&ub)[NS], V (&g)[NPL]) {
       V Q[NTRI];
 #pragma unroll
       for (int a = 0; a < NS; ++a)
@@ -739,11 +739,16 @@ __global__ void __launch_bounds__(128, (BulkNMinBlocks<NS, NPL, WPT>::value))
                                   vfma(ua[a], ua[b], vmul(ub[a], ub[b])));
 #pragma unroll
       for (int j = 0; j < NPL; ++j) {
-        V g = splat<V>(0.0f);
+        V gj = splat<V>(0.0f);
 #pragma unroll
-        for (int k = 0; k < NTRI; ++k) g = vfma(splat<V>(cf.K[j][k]), Q[k], g);
-        P[j] = vsub(vfma(splat<V>(-cf.hk[j]), R[j], P[j]), g);
+        for (int k = 0; k < NTRI; ++k) gj = vfma(splat<V>(cf.K[j][k]), Q[k], gj);
+        g[j] = gj;
       }
+    };
+    // P += dt/2 F_ab(R) = P - dt/2 k R - g
+    auto kick = [&](const V (&g)[NPL]) {
+#pragma unroll
+      for (int j = 0; j < NPL; ++j) P[j] = vsub(vfma(splat<V>(-cf.hk[j]), R[j], P[j]), g[j]);
     };
     // observation of walker lane l into slot `slot` of tile tile0 + l
     auto observe_lane = [&](int l, int slot) {
@@ -822,11 +827,20 @@ __global__ void __launch_bounds__(128, (BulkNMinBlocks<NS, NPL, WPT>::value))
     u4 wd[WPT];
 #pragma unroll
     for (int l = 0; l < WPT; ++l) wd[l] = philox_draw(bp.seed, blk, traj[l], kPurposeHop);
+    // Carried from one step to the next while no walker of the thread hops:
+    // the pair's columns ua, ub and energies ea, eb at R_{n+1}, their gap and the
+    // force term g, which the next step's first half kick (the same R, U and
+    // pair) would compute again bit for bit.  A hop, and the first step of a
+    // launch, compute them afresh.
+    V ua[NS], ub[NS], gk[NPL], ea, eb, de0;
+    bool cached = false;
     for (int it = 0; it < bp.len; ++it) {
-      const V de0 = gap_ab();
-      V ua[NS], ub[NS];
-      columns(ua, ub);
-      kick(ua, ub);  // first half kick at R_n
+      if (!cached) {
+        de0 = gap_ab(ea, eb);
+        columns(ua, ub);
+        force(ua, ub, gk);
+      }
+      kick(gk);  // first half kick at R_n
 #pragma unroll
       for (int j = 0; j < NPL; ++j) R[j] = vfma(splat<V>(cf.dtm[j]), P[j], R[j]);
       {
@@ -838,10 +852,12 @@ __global__ void __launch_bounds__(128, (BulkNMinBlocks<NS, NPL, WPT>::value))
         build_w(W);
         eigh_warm_fast<NS, V>(W, Uref, e, U);
       }
-      columns(ua, ub);  // (the new decomposition's columns, used twice)
-      kick(ua, ub);     // second half kick at R_{n+1}
-      const V de1 = gap_ab();
+      columns(ua, ub);  // (the new decomposition's columns)
+      force(ua, ub, gk);
+      kick(gk);  // second half kick at R_{n+1}
+      const V de1 = gap_ab(ea, eb);
       ph = df_add_v(ph, vmul(splat<V>(bp.hdt_hbar), vadd(de0, de1)));
+      de0 = de1;
       // G = sum_j (P_j/M_j) K_j
       V G[NS][NS];
       {
@@ -877,19 +893,6 @@ __global__ void __launch_bounds__(128, (BulkNMinBlocks<NS, NPL, WPT>::value))
           }
           Gua[k] = s0;
           Gub[k] = s1;
-        }
-        V ea, eb;
-#pragma unroll
-        for (int l = 0; l < WPT; ++l) {
-          float va = ln(e[0], l), vb = va;
-#pragma unroll
-          for (int c = 1; c < NS; ++c) {
-            const float ec = ln(e[c], l);
-            va = (c == al[l]) ? ec : va;
-            vb = (c == be[l]) ? ec : vb;
-          }
-          ln(ea, l) = va;
-          ln(eb, l) = vb;
         }
         bool dgl[WPT];
 #pragma unroll
@@ -983,6 +986,9 @@ __global__ void __launch_bounds__(128, (BulkNMinBlocks<NS, NPL, WPT>::value))
           else be[l] = hit - NS;
         }
       }
+      cached = true;
+#pragma unroll
+      for (int l = 0; l < WPT; ++l) cached = cached && hitl[l] < 0;
       if (++widx == 4) {
         widx = 0;
         ++blk;

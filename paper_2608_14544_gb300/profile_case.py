@@ -20,6 +20,8 @@ def main():
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
     ap.add_argument("--repeat", type=int, default=1)
     ap.add_argument("--repr", default="adiabatic", choices=["adiabatic", "diabatic"])
+    ap.add_argument("--stride", type=int, default=None,
+                    help="steps between output times (default: the workload's)")
     ap.add_argument("--spawn", type=int, default=0,
                     help="> 0: a spawning ensemble with this many walker slots per initial walker")
     ap.add_argument("--served", action="store_true",
@@ -37,7 +39,7 @@ def main():
     cfg["model"]["repr"] = args.repr
     n = args.n_traj or cfg["n_traj"]
     steps = args.steps or cfg["n_steps"]
-    stride = cfg["out_stride"]
+    stride = args.stride or cfg["out_stride"]
     prec = qcl.PREC_FP32_BULK if args.precision == "fp32" else qcl.PREC_FP64
     if args.served:
         srv = qcl.Server(16 << 30, quantum_steps=steps)
