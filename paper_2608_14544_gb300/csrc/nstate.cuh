@@ -208,8 +208,9 @@ __device__ __forceinline__ void eigh_ns(const T (&W)[NS][NS], const T (*ref)[NS]
 // crossing) sweep 2 is a full sweep too.  Then the eigenvalues are sorted
 // ascending and each column of U is aligned in sign with its reference column
 // (parallel transport).
+// (tm: the largest |t| of the sweep's rotations so far, per lane)
 template <int NS, bool SMALL, typename V>
-__device__ __forceinline__ void jacobi_sweep_warm(V (&A)[NS][NS], V (&U)[NS][NS]) {
+__device__ __forceinline__ void jacobi_sweep_warm(V (&A)[NS][NS], V (&U)[NS][NS], V& tm) {
   constexpr bool small = SMALL;
   constexpr int L = Lanes<V>::W;
   auto at = [&](int i, int j) -> V& { return i < j ? A[i][j] : A[j][i]; };
@@ -222,8 +223,10 @@ __device__ __forceinline__ void jacobi_sweep_warm(V (&A)[NS][NS], V (&U)[NS][NS]
       V t, c, sn;
       if (small) {
 #pragma unroll
-        for (int l = 0; l < L; ++l)  // (a zero a_pq gives t = 0, also where d = 0)
-          ln(t, l) = ln(apq, l) == 0.0f ? 0.0f : __fdividef(ln(apq, l), ln(d, l));
+        for (int l = 0; l < L; ++l) {  // (a zero a_pq gives t = 0, also where d = 0)
+          const float q = __fdividef(ln(apq, l), ln(d, l));
+          ln(t, l) = ln(apq, l) == 0.0f ? 0.0f : q;
+        }
         sn = t;
       } else {
         const V twoa = vmul(splat<V>(2.0f), apq);
@@ -233,13 +236,16 @@ __device__ __forceinline__ void jacobi_sweep_warm(V (&A)[NS][NS], V (&U)[NS][NS]
           // d + sgn(d) sqrt(d^2 + 4 a_pq^2) is never 0 unless a_pq = 0 (then t = 0)
           const float rl = ln(r2, l);
           const float den = ln(d, l) + copysignf(rl * rsqrtf(rl), ln(d, l));
-          ln(t, l) = ln(apq, l) == 0.0f ? 0.0f : __fdividef(ln(twoa, l), den);
+          const float q = __fdividef(ln(twoa, l), den);
+          ln(t, l) = ln(apq, l) == 0.0f ? 0.0f : q;
         }
         const V tt1 = vfma(t, t, splat<V>(1.0f));
 #pragma unroll
         for (int l = 0; l < L; ++l) ln(c, l) = rsqrtf(ln(tt1, l));
         sn = vmul(t, c);
       }
+#pragma unroll
+      for (int l = 0; l < L; ++l) ln(tm, l) = fmaxf(ln(tm, l), fabsf(ln(t, l)));
       const V nsn = vmul(sn, splat<V>(-1.0f));
       A[p][p] = vfma(t, vmul(apq, splat<V>(-1.0f)), A[p][p]);  // a_pp - t a_pq
       A[q][q] = vfma(t, apq, A[q][q]);
@@ -306,6 +312,7 @@ __device__ __forceinline__ void eigh_warm_fast(const V (&W)[NS][NS], const V (&r
     for (int b = 0; b < NS; ++b) U[a][b] = ref[a][b];
   // full sweeps (one copy of the code): the first always, the second where
   // some walker of the warp still has a large angle; else the small-angle sweep
+  V tm = splat<V>(0.0f);
 #pragma unroll 1
   for (int sweep = 0; sweep < 2; ++sweep) {
     if (sweep == 1) {
@@ -318,11 +325,11 @@ __device__ __forceinline__ void eigh_warm_fast(const V (&W)[NS][NS], const V (&r
           for (int q = p + 1; q < NS; ++q)
             large |= !(fabsf(ln(A[p][q], l)) * 4096.0f <= fabsf(ln(A[q][q], l) - ln(A[p][p], l)));
       if (!__any_sync(0xffffffffu, large)) {
-        jacobi_sweep_warm<NS, true, V>(A, U);
+        jacobi_sweep_warm<NS, true, V>(A, U, tm);
         break;
       }
     }
-    jacobi_sweep_warm<NS, false, V>(A, U);
+    jacobi_sweep_warm<NS, false, V>(A, U, tm);
   }
 #pragma unroll
   for (int a = 0; a < NS; ++a) e[a] = A[a][a];
@@ -335,7 +342,8 @@ __device__ __forceinline__ void eigh_warm_fast(const V (&W)[NS][NS], const V (&r
   for (int l = 0; l < L; ++l)
 #pragma unroll
     for (int j = 1; j < NS; ++j) unsorted |= ln(e[j], l) < ln(e[j - 1], l);
-  if (__any_sync(0xffffffffu, unsorted)) {
+  const bool swapped = __any_sync(0xffffffffu, unsorted);
+  if (swapped) {
 #pragma unroll
     for (int l = 0; l < L; ++l)
 #pragma unroll
@@ -354,7 +362,16 @@ __device__ __forceinline__ void eigh_warm_fast(const V (&W)[NS][NS], const V (&r
           }
         }
   }
-  // eigenvector b follows reference column b
+  // eigenvector b follows reference column b.  Without a swap in the sort,
+  // column b is reference column b turned by the rotations (p, q) with b in
+  // {p, q}: at most 2 (N_s - 1) of them, each by |theta| = atan |t|.  While every
+  // |t| <= 1/4 that is at most 6 atan(1/4) = 1.47 < pi/2 for N_s <= 4, so the
+  // dot product is positive and the signs below would all be +1: the warp skips
+  // them.
+  bool far = swapped || NS > 4;
+#pragma unroll
+  for (int l = 0; l < L; ++l) far |= ln(tm, l) > 0.25f;
+  if (!__any_sync(0xffffffffu, far)) return;
 #pragma unroll
   for (int b = 0; b < NS; ++b) {
     V dot = splat<V>(0.0f);

@@ -879,8 +879,7 @@ __global__ void __launch_bounds__(128, (BulkNMinBlocks<NS, NPL, WPT>::value))
       // slots 0..NS-1 move the first index a -> nu with A = -dt (v.d)_{nu a},
       // slots NS..2NS-1 the second index b -> nu with A = +dt (v.d)_{b nu}
       constexpr int NC = 2 * NS;
-      V A[NC];
-      bool ev[WPT][NC];
+      V A[NC];  // (0 for the two slots that would leave the pair unchanged)
       {
         V Gua[NS], Gub[NS];
 #pragma unroll
@@ -912,9 +911,10 @@ __global__ void __launch_bounds__(128, (BulkNMinBlocks<NS, NPL, WPT>::value))
               const bool dg = evl && fabsf(ln(gap, l)) < kDegTolF;
               dgl[l] |= dg;
               // approximate division (the amplitude enters a probability and a
-              // weight factor, both far above its 2-ulp error)
-              ln(vd, l) = (!evl || dg) ? 0.0f : __fdividef(ln(h, l), ln(gap, l));
-              ev[l][sl * NS + nu] = evl;
+              // weight factor, both far above its 2-ulp error), taken on every
+              // slot and discarded by the select (no branch around it)
+              const float qd = __fdividef(ln(h, l), ln(gap, l));
+              ln(vd, l) = (!evl || dg) ? 0.0f : qd;
             }
             A[sl * NS + nu] = vmul(splat<V>(sl == 0 ? -bp.dt : bp.dt), vd);
           }
@@ -929,11 +929,14 @@ __global__ void __launch_bounds__(128, (BulkNMinBlocks<NS, NPL, WPT>::value))
       for (int l = 0; l < WPT; ++l) {
         const uint32_t word = (widx & 2) ? ((widx & 1) ? wd[l].w : wd[l].z)
                                          : ((widx & 1) ? wd[l].y : wd[l].x);
+        // T = min(floor(kappa |A| 2^24), Tmax), the clamp taken in FP32 (Tmax < 2^24
+        // is exact there); the excluded slots have A = 0, so T = 0
+        const float tmaxf = (float)bp.tmax;
         uint32_t T[NC], sumT = 0;
 #pragma unroll
         for (int k = 0; k < NC; ++k) {
           const float ka = fabsf(ln(vmul(splat<V>(bp.kappa), A[k]), l));
-          T[k] = ev[l][k] ? min(__float2uint_rz(fminf(ka * kP24f, 33554432.0f)), bp.tmax) : 0u;
+          T[k] = __float2uint_rz(fminf(ka * kP24f, tmaxf));
           sumT += T[k];
         }
         if (sumT > bp.tmax) {
@@ -946,14 +949,17 @@ __global__ void __launch_bounds__(128, (BulkNMinBlocks<NS, NPL, WPT>::value))
           }
           sumT = s2;
         }
+        // the event whose interval [cum_{k-1}, cum_k) holds y: the number of
+        // cumulative thresholds at or below y (NC: none, no transition)
         const uint32_t y = word >> 8;
         uint32_t cum = 0;
-        int hit = -1;
+        int cnt = 0;
 #pragma unroll
         for (int k = 0; k < NC; ++k) {
           cum += T[k];
-          hit = (hit < 0 && y < cum) ? k : hit;
+          cnt += (y >= cum) ? 1 : 0;
         }
+        const int hit = cnt < NC ? cnt : -1;
         float Ah = ln(A[0], l);
         uint32_t Th = T[0];
 #pragma unroll
