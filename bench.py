@@ -667,6 +667,7 @@ def run_ours(args):
     clocks = clk.summary()
     cpu_threads = os.cpu_count() or 1
     cpu_rate, cpu_n, cpu_s = cpu_oracle_rate(cfg, args.cpu_seconds, cpu_threads)
+    cpu1_rate, cpu1_n, cpu1_s = cpu_oracle_rate(cfg, args.cpu_seconds / 3, 1)
     lat = np.array(solve_s)
     out = {
         "metric": METRIC, "value": value, "unit": "traj-steps/s", "n_gpus": world,
@@ -688,7 +689,10 @@ def run_ours(args):
         "cpu_baseline": {"value": cpu_rate, "unit": "traj-steps/s", "cores": cpu_threads,
                          "kind": "oracle",
                          "sample": f"{cpu_n} walkers x {steps} steps of the same workload "
-                                   f"({cpu_s:.1f} s)"},
+                                   f"({cpu_s:.1f} s)",
+                         "single_thread": {"value": cpu1_rate, "cores": 1,
+                                           "sample": f"{cpu1_n} walkers x {steps} steps "
+                                                     f"({cpu1_s:.1f} s)"}},
         "e2e": e2e,
         "gpu_launches": launches,
         "served": {"path": "qcl_server_submit / qcl_server_wait, one 1e7-walker request per step",

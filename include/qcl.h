@@ -355,18 +355,18 @@ qcl_status qcl_measure_peak(int32_t which, double* flops_per_s, void* stream);
 
 /* ---------------------------------------------------------------------------
  * Launch shape and autotuning of the FP32-bulk persistent kernels (no
- * counterpart in the paper).  Two knobs, neither of which changes a bit of any
+ * counterpart in the paper).  Three knobs, none of which changes a bit of any
  * result (each walker's arithmetic and each reduction tile are the same
  * whatever the shape):
  *   walkers_per_thread  1 or 2 (0 = default: 2 for two-state models of at most
  *                       4 modes or of 65..100 modes, else 1).  With 2 a thread
  *                       advances one walker of each of two consecutive tiles
- *                       as the two lanes of packed FP32x2 instructions;
- *                       two-state models of at most 8 modes or of 65..100
- *                       modes (a walker's modes over four warps), otherwise 1
- *                       is used.  A launch whose
- *                       tiles do not outnumber the resident block slots also
- *                       runs 1, so that every slot gets a tile.
+ *                       as the two lanes of packed FP32x2 instructions; 2 is
+ *                       available for two-state models of at most 8 modes or
+ *                       of 65..100 modes (a walker's modes over four warps),
+ *                       otherwise 1 is used.  A launch whose tiles do not
+ *                       outnumber the resident block slots also runs 1, so
+ *                       that every slot gets a tile.
  *   blocks_per_sm       resident blocks per SM of the persistent grid (0 = the
  *                       kernel's occupancy limit; larger values are clamped).
  *   outputs_per_launch  output times per persistent launch, 1..32 (0 = 32): a
