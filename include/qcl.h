@@ -478,7 +478,8 @@ qcl_status qcl_spawn_live(const qcl_model* model, const qcl_ensemble_desc* ens, 
  * arrival order while the caller's device arena has room for their ensemble
  * and observation buffers and fewer than max_active are running; it advances
  * all admitted requests together in rounds of at most quantum_steps steps
- * (and 32 output times) each, packing adiabatic two-state requests of up to 8
+ * each (a packed request also at most 32 output times), packing adiabatic
+ * two-state requests of up to 8
  * modes into shared persistent launches (a CUDA graph replayed every round
  * when use_graphs is set) unless their walkers fill the GPU by themselves
  * (at least 6 x SMs tiles of 256 walkers), which, like the other requests,

@@ -3,8 +3,10 @@
 // resident, advances all admitted requests together in rounds, and reports
 // latency percentiles beside throughput.
 //
-// Rounds (continuous batching): every active request advances by one chunk of
-// at most `quantum_steps` steps and 32 output times.  Adiabatic two-state
+// Rounds (continuous batching): every active request advances by at most
+// `quantum_steps` steps (a packed request also by at most 32 output times, one
+// packed launch; the others' steps may span several persistent launches of
+// their own, with no host turnaround between them).  Adiabatic two-state
 // requests with at most 8 modes and too few walkers to fill the GPU alone are
 // packed, per (mode bucket, model kind), into one
 // persistent launch that reads a device table of (request, tile) work items;
@@ -227,8 +229,8 @@ void finish(qcl_server* s, const std::shared_ptr<Request>& r, int state, const s
   s->cv.notify_all();
 }
 
-// Chunk of request r for this round: steps [cs, ce) with at most 32 output
-// times and at most quantum steps.
+// Chunk of request r for this round: steps [cs, ce), at most quantum steps
+// and, for a packed request (one launch per round), at most 32 output times.
 struct Chunk {
   int64_t cs, ce, k_first;
   int n_slots;
@@ -246,7 +248,7 @@ double step_flops(const Request& r) {
 // Rounds skipped after which a request advances first, whatever its size.
 constexpr int kMaxSkipped = 16;
 
-Chunk plan(const Request& r, int64_t quantum) {
+Chunk plan(const Request& r, int64_t quantum, bool packed) {
   Chunk c{};
   c.cs = r.step;
   c.first = !r.observed0;
@@ -256,7 +258,7 @@ Chunk plan(const Request& r, int64_t quantum) {
   const int64_t next_out = (c.cs / stride + 1) * stride;
   const int64_t room = kChunkOut - n_slots;
   int64_t ce;
-  if (next_out + (room - 1) * stride <= end) {
+  if (packed && next_out + (room - 1) * stride <= end) {
     ce = next_out + (room - 1) * stride;
     n_slots += (int)room;
   } else {
@@ -384,7 +386,7 @@ void run_round(qcl_server* s) {
     for (auto& r : act) r->round_quantum = s->d.quantum_steps;
   }
   for (auto& r : act) {
-    const Chunk c = plan(*r, r->round_quantum);
+    const Chunk c = plan(*r, r->round_quantum, r->bucket >= 0);
     items.push_back({r, c});
     if (r->bucket < 0) continue;
     PackedTable* T = htab(s, bulk_kind(r->model->host), r->bucket);
