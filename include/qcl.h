@@ -100,9 +100,12 @@ typedef struct {
  *   V_aa - V_bb, mean force -1/2 (dV_aa/dR + dV_bb/dR), transitions a -> g with
  *   amplitude -i V_ga dt/hbar and b -> g with +i V_bg dt/hbar.  The imaginary
  *   unit is carried as a per-walker count of quarter turns (weight
- *   m exp(-i phi) i^q).  Two-state models only; the FP32-bulk precision takes
- *   at most 32 modes.  The observables keep their layout: diabatic rho_ij
- *   (the walkers' own pairs) and adiabatic rho_ab (rotated at the walker's R). */
+ *   m exp(-i phi) i^q).  Any N_s; the FP32-bulk precision takes the modes of
+ *   the adiabatic representation (at most 32 for N_s <= 4, else 8).
+ *   Trajectory spawning takes two-state models.  The observables keep their
+ *   layout: diabatic rho_ij (the walkers' own pairs) and adiabatic rho_ab
+ *   (rotated at the walker's R by its eigenvectors, each with its
+ *   largest-magnitude component positive). */
 #define QCL_REPR_ADIABATIC 0
 #define QCL_REPR_DIABATIC 1
 

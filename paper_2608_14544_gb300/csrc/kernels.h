@@ -62,7 +62,7 @@ struct SampleN32 {
   int64_t n_traj;
   uint64_t traj_offset;
   uint64_t seed;
-  int32_t n, ns, wigner, pad;
+  int32_t n, ns, wigner, repr;
   float R0[kMaxN], P0[kMaxN], sR[kMaxN], sP[kMaxN];
   float E[kMaxNS * kMaxNS];
   float rho[kMaxNS * kMaxNS];
@@ -352,10 +352,11 @@ const char* bulk2_variant(int n, int kind);
 // N_s-state initial sample: FP64 (dm, sp) or FP32 bulk (s32).
 void launch_sampleN(const DevModel* dm, const SampleParams& sp, const SampleN32* s32, void* buf,
                     int precision, cudaStream_t st);
-void launch_stepN_f64(const DevModel* dm, int ns, void* buf, int64_t nt, int n, int64_t step0,
-                      int64_t step, double dt, uint64_t seed, uint64_t traj_off, cudaStream_t st);
-void launch_observeN_f64(int ns, const void* buf, int64_t nt, int n, double* part,
-                         cudaStream_t st);
+void launch_stepN_f64(const DevModel* dm, int repr, int ns, void* buf, int64_t nt, int n,
+                      int64_t step0, int64_t step, double dt, uint64_t seed, uint64_t traj_off,
+                      cudaStream_t st);
+void launch_observeN_f64(const DevModel* dm, int ns, const void* buf, int64_t nt, int n,
+                         double* part, cudaStream_t st);
 int launch_bulkN(int ns, const BulkParams& bp, const CoefN& cf, void* buf, double* part,
                  const LaunchShape& ls, cudaStream_t st);
 

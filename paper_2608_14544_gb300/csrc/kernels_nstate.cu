@@ -7,9 +7,9 @@ namespace qcl {
 #define QCL_NS_DECL(k)                                                                        \
   void nstate_sample64_##k(const DevModel*, const SampleParams&, void*, cudaStream_t);        \
   void nstate_sample32_##k(const SampleN32&, void*, cudaStream_t);                           \
-  void nstate_step64_##k(const DevModel*, void*, int64_t, int, int64_t, int64_t, double,      \
+  void nstate_step64_##k(const DevModel*, int, void*, int64_t, int, int64_t, int64_t, double, \
                          uint64_t, uint64_t, cudaStream_t);                                   \
-  void nstate_observe64_##k(const void*, int64_t, int, double*, cudaStream_t);                \
+  void nstate_observe64_##k(const DevModel*, const void*, int64_t, int, double*, cudaStream_t); \
   int nstate_bulk_##k(const BulkParams&, const CoefN&, void*, double*, int, int, cudaStream_t);
 QCL_NS_DECL(3)
 QCL_NS_DECL(4)
@@ -39,15 +39,16 @@ void launch_sampleN(const DevModel* dm, const SampleParams& sp, const SampleN32*
   launches_add(1);
 }
 
-void launch_stepN_f64(const DevModel* dm, int ns, void* buf, int64_t nt, int n, int64_t step0,
-                      int64_t step, double dt, uint64_t seed, uint64_t traj_off, cudaStream_t st) {
-  QCL_NS_SWITCH(ns, nstate_step64, dm, buf, nt, n, step0, step, dt, seed, traj_off, st);
+void launch_stepN_f64(const DevModel* dm, int repr, int ns, void* buf, int64_t nt, int n,
+                      int64_t step0, int64_t step, double dt, uint64_t seed, uint64_t traj_off,
+                      cudaStream_t st) {
+  QCL_NS_SWITCH(ns, nstate_step64, dm, repr, buf, nt, n, step0, step, dt, seed, traj_off, st);
   launches_add(1);
 }
 
-void launch_observeN_f64(int ns, const void* buf, int64_t nt, int n, double* part,
-                         cudaStream_t st) {
-  QCL_NS_SWITCH(ns, nstate_observe64, buf, nt, n, part, st);
+void launch_observeN_f64(const DevModel* dm, int ns, const void* buf, int64_t nt, int n,
+                         double* part, cudaStream_t st) {
+  QCL_NS_SWITCH(ns, nstate_observe64, dm, buf, nt, n, part, st);
   launches_add(1);
 }
 

@@ -6,8 +6,8 @@ namespace qcl {
 void nstate_sample64_8(const DevModel* dm, const SampleParams& sp, void* buf, cudaStream_t st) {
   NStateOps<8>::sample64(dm, sp, buf, st);
 }
-void nstate_step64_8(const DevModel* dm, void* buf, int64_t nt, int n, int64_t step0,
+void nstate_step64_8(const DevModel* dm, int repr, void* buf, int64_t nt, int n, int64_t step0,
                      int64_t step, double dt, uint64_t seed, uint64_t traj_off, cudaStream_t st) {
-  NStateOps<8>::step64(dm, buf, nt, n, step0, step, dt, seed, traj_off, st);
+  NStateOps<8>::step64(dm, repr, buf, nt, n, step0, step, dt, seed, traj_off, st);
 }
 }  // namespace qcl

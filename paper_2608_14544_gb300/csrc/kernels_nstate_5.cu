@@ -6,8 +6,9 @@ namespace qcl {
 void nstate_sample32_5(const SampleN32& sp, void* buf, cudaStream_t st) {
   NStateOps<5>::sample32(sp, buf, st);
 }
-void nstate_observe64_5(const void* buf, int64_t nt, int n, double* part, cudaStream_t st) {
-  NStateOps<5>::observe64(buf, nt, n, part, st);
+void nstate_observe64_5(const DevModel* dm, const void* buf, int64_t nt, int n, double* part,
+                         cudaStream_t st) {
+  NStateOps<5>::observe64(dm, buf, nt, n, part, st);
 }
 int nstate_bulk_5(const BulkParams& bp, const CoefN& cf, void* buf, double* part, int grid_cap,
                   int wpt, cudaStream_t st) {

@@ -218,6 +218,9 @@ __global__ void __launch_bounds__(128) k_sampleN_f64(const DevModel* __restrict_
   double W[NS][NS], e[NS], U[NS][NS];
   elec_g<NS>(M, w.R + i, nt, n, W);
   eigh_ns<double, NS>(W, nullptr, e, U, 100, 1e-34);
+  // the pair's density: U^T rho U in the adiabatic basis, rho itself in the
+  // diabatic one
+  const bool dia = M->repr == QCL_REPR_DIABATIC;
   double rho_ad[NS * NS];
 #pragma unroll
   for (int al = 0; al < NS; ++al)
@@ -228,7 +231,7 @@ __global__ void __launch_bounds__(128) k_sampleN_f64(const DevModel* __restrict_
       for (int k = 0; k < NS; ++k)
 #pragma unroll
         for (int l = 0; l < NS; ++l) acc += U[k][al] * sp.rho[k * NS + l] * U[l][be];
-      rho_ad[al * NS + be] = acc;
+      rho_ad[al * NS + be] = dia ? sp.rho[al * NS + be] : acc;
     }
   double tot = 0.0;
   for (int k = 0; k < NS * NS; ++k) tot += fabs(rho_ad[k]);
@@ -402,6 +405,138 @@ __global__ void __launch_bounds__(128) k_stepN_f64(const DevModel* __restrict__ 
   }
 }
 
+// --------------------------------------------------------- FP64 diabatic step --
+// The diabatic representation (pairs of the R-independent basis of W, weights
+// carried with a quarter-turn count q in bits 4-5 of the pair word): velocity
+// Verlet on the diagonal mean force F_j = -k_j R_j - 1/2 (K_j,aa + K_j,bb), the
+// trapezoid phase with hbar w_ab = W_aa - W_bb, and one transition among the
+// coupling term's 2 (N_s - 1) events at R_{n+1}: the first index a -> g with
+// amplitude -i c, c = W_ga dt / hbar (three quarter turns), or the second
+// b -> g with +i c, c = W_bg dt / hbar (one quarter turn); probabilities
+// min(kappa |c|, p_max) quantised and scaled as in the adiabatic step.
+template <int NS>
+__device__ __forceinline__ void dia_kick_g(const DevModel* M, double* R, double* P, int64_t nt,
+                                           int n, int al, int be, double dt) {
+  for (int j = 0; j < n; ++j) {
+    const double* Kj = M->K + (size_t)j * NS * NS;
+    double kaa = Kj[0], kbb = Kj[0];
+#pragma unroll
+    for (int c = 1; c < NS; ++c) {
+      kaa = (c == al) ? Kj[c * NS + c] : kaa;
+      kbb = (c == be) ? Kj[c * NS + c] : kbb;
+    }
+    const int64_t o = (int64_t)j * nt;
+    const double F = -M->k[j] * R[o] - 0.5 * (kaa + kbb);
+    P[o] += 0.5 * dt * F;
+  }
+}
+
+template <int NS>
+__device__ __forceinline__ double diag_pick(const double (&W)[NS][NS], int a) {
+  double v = W[0][0];
+#pragma unroll
+  for (int c = 1; c < NS; ++c) v = (c == a) ? W[c][c] : v;
+  return v;
+}
+
+template <int NS>
+__global__ void __launch_bounds__(128) k_stepN_dia_f64(const DevModel* __restrict__ M, void* buf,
+                                                       int64_t nt, int n, int64_t step0,
+                                                       int64_t step, double dt, uint64_t seed,
+                                                       uint64_t traj_off) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  WN<double> w = viewN<double>(buf, nt, NS, n, QCL_PREC_FP64);
+  if (i >= nt) return;
+  if (w.hdr->step != step0) {
+    if (i == 0) atomicOr(&w.hdr->flags, QCL_FLAG_STEP_MISMATCH);
+    return;
+  }
+  const uint16_t ab = w.ab[i];
+  int al = ab & 0xf, be = (ab >> 8) & 0xf, q = (ab >> 4) & 3;
+  double m = w.m[i], phi = w.phi[i];
+  double* R = w.R + i;
+  double* P = w.P + i;
+  double W0[NS][NS], W1[NS][NS];
+  elec_g<NS>(M, R, nt, n, W0);
+  dia_kick_g<NS>(M, R, P, nt, n, al, be, dt);
+  for (int j = 0; j < n; ++j) R[(int64_t)j * nt] += dt * P[(int64_t)j * nt] / M->mass[j];
+  elec_g<NS>(M, R, nt, n, W1);
+  dia_kick_g<NS>(M, R, P, nt, n, al, be, dt);
+  const double w0 = (diag_pick<NS>(W0, al) - diag_pick<NS>(W0, be)) / M->hbar;
+  const double w1 = (diag_pick<NS>(W1, al) - diag_pick<NS>(W1, be)) / M->hbar;
+  phi += 0.5 * dt * (w0 + w1);
+  // slots 0..NS-1: a -> g with c = W_ga dt / hbar; slots NS..2NS-1: b -> g with
+  // c = W_bg dt / hbar; the slots g = a and g = b are not events (T = 0)
+  constexpr int NC = 2 * NS;
+  double c[NC];
+  bool ev[NC];
+#pragma unroll
+  for (int g = 0; g < NS; ++g) {
+    double wga = W1[g][0], wbg = W1[0][g];
+#pragma unroll
+    for (int h = 1; h < NS; ++h) {
+      wga = (h == al) ? W1[g][h] : wga;
+      wbg = (h == be) ? W1[h][g] : wbg;
+    }
+    c[g] = wga * dt / M->hbar;
+    c[NS + g] = wbg * dt / M->hbar;
+    ev[g] = g != al;
+    ev[NS + g] = g != be;
+  }
+  uint64_t T[NC], sumT = 0;
+  const uint64_t Tmax = (uint64_t)floor(M->p_max * kP24);
+#pragma unroll
+  for (int k = 0; k < NC; ++k) {
+    const double p = fmin(M->hop_scale * fabs(c[k]), M->p_max);
+    T[k] = ev[k] ? (uint64_t)floor(p * kP24) : 0;
+    sumT += T[k];
+  }
+  if (sumT > Tmax) {
+    const uint64_t s = sumT;
+    sumT = 0;
+#pragma unroll
+    for (int k = 0; k < NC; ++k) {
+      T[k] = T[k] * Tmax / s;
+      sumT += T[k];
+    }
+  }
+  const u4 wd = philox_draw(seed, (uint32_t)(step >> 2), traj_off + (uint64_t)i, kPurposeHop);
+  const uint64_t y = word_of(wd, (int)(step & 3)) >> 8;
+  uint64_t cum = 0;
+  int hit = -1;
+#pragma unroll
+  for (int k = 0; k < NC; ++k) {
+    cum += T[k];
+    if (hit < 0 && y < cum) hit = k;
+  }
+  if (hit < 0) {
+    m = m / (1.0 - (double)sumT / kP24);
+  } else {
+    double ch = c[0];
+    uint64_t Th = T[0];
+#pragma unroll
+    for (int k = 1; k < NC; ++k) {
+      ch = (k == hit) ? c[k] : ch;
+      Th = (k == hit) ? T[k] : Th;
+    }
+    m = m * ch / ((double)Th / kP24);
+    if (hit < NS) {
+      al = hit;
+      q = (q + 3) & 3;
+    } else {
+      be = hit - NS;
+      q = (q + 1) & 3;
+    }
+  }
+  w.m[i] = m;
+  w.phi[i] = phi;
+  w.ab[i] = (uint16_t)(al | (q << 4) | (be << 8));
+  if (!isfinite(m) || !isfinite(phi)) {
+    atomicAdd(&w.hdr->n_nonfinite, 1ull);
+    atomicOr(&w.hdr->flags, QCL_FLAG_NONFINITE);
+  }
+}
+
 // --------------------------------------------------------- FP64 observation --
 // Contributions in passes of 32 quantities: pass p holds values 16p..16p+15
 // (lanes 0-15 of the reduce-scatter) and their squares (lanes 16-31).
@@ -429,28 +564,73 @@ __device__ __forceinline__ void contrib_values(const T (&U)[NS][NS], int al, int
   }
 }
 
+// A diabatic walker's contributions: z at its own pair in the diabatic block,
+// z U_ai U_bj (rows a, b of the eigenvectors at its R) in the adiabatic one.
+template <typename T, int NS>
+__device__ __forceinline__ void contrib_values_dia(const T (&U)[NS][NS], int al, int be, T zr,
+                                                   T zi, int p, T (&v)[16]) {
+  T ra[NS], rb[NS];
+#pragma unroll
+  for (int k = 0; k < NS; ++k) {
+    T x = U[0][k], y = U[0][k];
+#pragma unroll
+    for (int c = 1; c < NS; ++c) {
+      x = (c == al) ? U[c][k] : x;
+      y = (c == be) ? U[c][k] : y;
+    }
+    ra[k] = x;
+    rb[k] = y;
+  }
+  constexpr int NN = NS * NS;
+#pragma unroll
+  for (int t = 0; t < 16; ++t) {
+    const int q = 16 * p + t;
+    T val = T(0);
+    if (q < 2 * NN) {  // diabatic rho_ij at the walker's pair
+      const int ij = q >> 1;
+      const bool hit = ij == al * NS + be;
+      val = hit ? ((q & 1) ? zi : zr) : T(0);
+    } else if (q < 4 * NN) {  // adiabatic rho_kl, q = 2 NN + 2 (k NS + l) + c
+      const int kl = (q - 2 * NN) >> 1, kk = kl / NS, ll = kl % NS;
+      const T f = ra[kk] * rb[ll];
+      val = (q & 1) ? zi * f : zr * f;
+    }
+    v[t] = val;
+  }
+}
+
 template <int NS>
-__global__ void __launch_bounds__(256) k_observeN_f64(const void* buf, int64_t nt, int n,
+__global__ void __launch_bounds__(256) k_observeN_f64(const DevModel* __restrict__ M,
+                                                      const void* buf, int64_t nt, int n,
                                                       double* __restrict__ part) {
   __shared__ double red[8][32];
   constexpr int NN = NS * NS, NP = (4 * NN + 15) / 16;
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   WN<double> w = viewN<double>((void*)buf, nt, NS, n, QCL_PREC_FP64);
+  const bool dia = M->repr == QCL_REPR_DIABATIC;
   double U[NS][NS];
   double zr = 0.0, zi = 0.0;
   int al = 0, be = 0;
   if (i < nt) {
+    if (dia) {  // the eigenvectors at the walker's R, decomposed afresh
+      double W[NS][NS], e[NS];
+      elec_g<NS>(M, w.R + i, nt, n, W);
+      eigh_ns<double, NS>(W, nullptr, e, U, 100, 1e-34);
+    } else {
 #pragma unroll
-    for (int a = 0; a < NS; ++a)
+      for (int a = 0; a < NS; ++a)
 #pragma unroll
-      for (int b = 0; b < NS; ++b) U[a][b] = w.U[(int64_t)(a * NS + b) * nt + i];
+        for (int b = 0; b < NS; ++b) U[a][b] = w.U[(int64_t)(a * NS + b) * nt + i];
+    }
     const uint16_t ab = w.ab[i];
-    al = ab & 0xff;
-    be = ab >> 8;
+    al = ab & 0xf;
+    be = (ab >> 8) & 0xf;
+    const int qt = (ab >> 4) & 3;  // quarter turns (diabatic walkers): z = m exp(-i phi) i^q
     double sn, cs;
     sincos(w.phi[i], &sn, &cs);
-    zr = w.m[i] * cs;
-    zi = -w.m[i] * sn;
+    const double xr = w.m[i] * cs, xi = -w.m[i] * sn;
+    zr = qt == 0 ? xr : (qt == 1 ? -xi : (qt == 2 ? -xr : xi));
+    zi = qt == 0 ? xi : (qt == 1 ? xr : (qt == 2 ? -xi : -xr));
   } else {
 #pragma unroll
     for (int a = 0; a < NS; ++a)
@@ -459,7 +639,8 @@ __global__ void __launch_bounds__(256) k_observeN_f64(const void* buf, int64_t n
   }
   for (int p = 0; p < NP; ++p) {
     double v16[16];
-    contrib_values<double, NS>(U, al, be, zr, zi, p, v16);
+    if (dia) contrib_values_dia<double, NS>(U, al, be, zr, zi, p, v16);
+    else contrib_values<double, NS>(U, al, be, zr, zi, p, v16);
     double v[32];
 #pragma unroll
     for (int t = 0; t < 16; ++t) {
@@ -530,6 +711,9 @@ __global__ void __launch_bounds__(128) k_sampleN_f32(const SampleN32 sp, void* b
   }
   float e[NS], U[NS][NS];
   eigh_ns<float, NS>(W, nullptr, e, U, 12, 1e-13f);
+  // the pair's density: U^T rho U in the adiabatic basis, rho itself in the
+  // diabatic one
+  const bool dia = sp.repr == QCL_REPR_DIABATIC;
   float rho_ad[NS * NS];
   float tot = 0.0f;
 #pragma unroll
@@ -541,6 +725,7 @@ __global__ void __launch_bounds__(128) k_sampleN_f32(const SampleN32 sp, void* b
       for (int k = 0; k < NS; ++k)
 #pragma unroll
         for (int l = 0; l < NS; ++l) acc = __fmaf_rn(U[k][al] * sp.rho[k * NS + l], U[l][be], acc);
+      acc = dia ? sp.rho[al * NS + be] : acc;
       rho_ad[al * NS + be] = acc;
       tot += fabsf(acc);
     }
@@ -1043,6 +1228,270 @@ __global__ void __launch_bounds__(128, (BulkNMinBlocks<NS, NPL, WPT>::value))
   }
 }
 
+// ----------------------------------------- FP32-bulk kernel, diabatic pairs --
+// The diabatic representation of N_s-state models on the FP32-bulk path: one
+// walker per thread, 128-walker tiles, persistent over tiles.  No
+// decomposition is carried or needed for the step: the mean force is the
+// diagonal one (its coupling part (dt/2) 1/2 (K_j,aa + K_j,bb) is a constant of
+// the pair, taken again after a hop), the phase comes from W's diagonal and
+// the events from its columns a and b at R_{n+1} (the FP64 step's order of
+// events, quarter turns and 24-bit thresholds).  The observation diagonalises
+// W(R) afresh at output times (Jacobi, the sampler's conventions) for the
+// adiabatic block.
+template <int NS, int NPL>
+__global__ void __launch_bounds__(128, (NPL > 8 || NS > 5) ? 2 : 4)
+    k_bulkN_dia(const BulkParams bp, const CoefN cf, void* buf, double* __restrict__ part) {
+  constexpr int NN = NS * NS, NTRI = NS * (NS + 1) / 2;
+  constexpr int NP = (4 * NN + 15) / 16;
+  constexpr int TW = 128;
+  constexpr int NC = 2 * NS;
+  __shared__ double red[2][4][32];
+  __shared__ float obs_rows[TW * 33];
+  WN<float> ws = viewN<float>(buf, bp.n_traj, NS, bp.n, QCL_PREC_FP32_BULK);
+  if (ws.hdr->step != bp.step0) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) atomicOr(&ws.hdr->flags, QCL_FLAG_STEP_MISMATCH);
+    return;
+  }
+  const int64_t nt = bp.n_traj;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  int rb = 0;
+  for (int64_t tile0 = blockIdx.x; tile0 < bp.n_tiles; tile0 += gridDim.x) {
+    const int64_t i = tile0 * TW + threadIdx.x;
+    const bool active = i < nt;
+    const int64_t ii = active ? i : 0;
+    float R[NPL], P[NPL];
+#pragma unroll
+    for (int j = 0; j < NPL; ++j) {
+      const bool on = active && j < bp.n;
+      R[j] = on ? ws.R[(int64_t)j * nt + ii] : 0.0f;
+      P[j] = on ? ws.P[(int64_t)j * nt + ii] : 0.0f;
+    }
+    f2 m = {active ? ws.m[ii] : 0.0f, active ? ws.mlo[ii] : 0.0f};
+    int mexp = active ? ws.mexp[ii] : 0;
+    f2 ph = {active ? ws.phi[ii] : 0.0f, active ? ws.philo[ii] : 0.0f};
+    const uint32_t ab0 = active ? ws.ab[ii] : 0u;
+    int al = ab0 & 0xf, be = (ab0 >> 8) & 0xf, q = (ab0 >> 4) & 3;
+    const uint64_t traj = bp.traj_offset + (uint64_t)ii;
+
+    // W(R) (upper triangle) at the walker's R
+    auto build_w = [&](float (&t)[NTRI]) {
+#pragma unroll
+      for (int k = 0; k < NTRI; ++k) t[k] = cf.E[k];
+#pragma unroll
+      for (int j = 0; j < NPL; ++j)
+#pragma unroll
+        for (int k = 0; k < NTRI; ++k) t[k] = __fmaf_rn(R[j], cf.K[j][k], t[k]);
+    };
+    // W_aa - W_bb
+    auto diag_gap = [&](const float (&t)[NTRI]) {
+      float va = t[tri<NS>(0, 0)], vb = va;
+#pragma unroll
+      for (int c = 1; c < NS; ++c) {
+        const float d = t[tri<NS>(c, c)];
+        va = (c == al) ? d : va;
+        vb = (c == be) ? d : vb;
+      }
+      return __fsub_rn(va, vb);
+    };
+    // the pair's force constants: hkd_j = dt/2 * 1/2 (K_j,aa + K_j,bb)
+    float hkd[NPL];
+    auto pair_force = [&]() {
+#pragma unroll
+      for (int j = 0; j < NPL; ++j) {
+        float ka = cf.K[j][tri<NS>(0, 0)], kb = ka;
+#pragma unroll
+        for (int c = 1; c < NS; ++c) {
+          const float d = cf.K[j][tri<NS>(c, c)];
+          ka = (c == al) ? d : ka;
+          kb = (c == be) ? d : kb;
+        }
+        hkd[j] = __fmul_rn(0.5f * bp.hdt, __fadd_rn(ka, kb));
+      }
+    };
+    auto kick = [&]() {
+#pragma unroll
+      for (int j = 0; j < NPL; ++j)
+        P[j] = __fsub_rn(__fmaf_rn(-cf.hk[j], R[j], P[j]), hkd[j]);
+    };
+    float t[NTRI];
+    build_w(t);
+    pair_force();
+    float w0 = diag_gap(t);  // hbar w_ab at R_n (times 1/hbar in hdt_hbar)
+
+    // observation of the walker into slot `slot` (W(R) in t)
+    auto observe = [&](int slot) {
+      renormN(m, mexp);
+      const bool live = active && m.hi != 0.0f;
+      int ew = live ? mexp : -(1 << 28);
+#pragma unroll
+      for (int off = 16; off > 0; off >>= 1) ew = max(ew, __shfl_xor_sync(0xffffffffu, ew, off));
+      const float kq = rintf(ph.hi * kInvTwoPiN);
+      ph = df_add(ph, -kq * kTwoPi1N);
+      ph = df_add(ph, -kq * kTwoPi2N);
+      ph = df_add(ph, -kq * kTwoPi3N);
+      float sh, chh;
+      __sincosf(ph.hi, &sh, &chh);
+      const float mm = live ? m.hi * pow2iN(mexp - ew) : 0.0f;
+      const float xr = mm * __fmaf_rn(-ph.lo, sh, chh), xi = -mm * __fmaf_rn(ph.lo, chh, sh);
+      const float zr = q == 0 ? xr : (q == 1 ? -xi : (q == 2 ? -xr : xi));
+      const float zi = q == 0 ? xi : (q == 1 ? xr : (q == 2 ? -xi : -xr));
+      const int ex = (ew < -(1 << 27)) ? 0 : ((lane < 16) ? ew : 2 * ew);
+      float W[NS][NS], e[NS], U[NS][NS];
+#pragma unroll
+      for (int a = 0; a < NS; ++a)
+#pragma unroll
+        for (int b = 0; b < NS; ++b) W[a][b] = t[tri<NS>(a, b)];
+      eigh_ns<float, NS>(W, nullptr, e, U, 12, 1e-13f);
+      float* row = &obs_rows[threadIdx.x * 33];
+      constexpr int kPassUnroll = NP <= 4 ? NP : 1;
+#pragma unroll kPassUnroll
+      for (int p = 0; p < NP; ++p) {
+        float v[16];
+        contrib_values_dia<float, NS>(U, al, be, zr, zi, p, v);
+#pragma unroll
+        for (int k = 0; k < 16; ++k) {
+          row[k] = v[k];
+          row[16 + k] = v[k] * v[k];
+        }
+        __syncwarp();
+        float l1[16];
+        const float* col = &obs_rows[(warp * 32) * 33 + lane];
+#pragma unroll
+        for (int k = 0; k < 16; ++k) l1[k] = col[(2 * k) * 33] + col[(2 * k + 1) * 33];
+#pragma unroll
+        for (int wdt = 8; wdt >= 1; wdt >>= 1)
+#pragma unroll
+          for (int k = 0; k < wdt; ++k) l1[k] = l1[2 * k] + l1[2 * k + 1];
+        __syncwarp();
+        const double xd = (double)l1[0];
+        red[rb][warp][lane] = (ex >= -1022 && ex <= 1023) ? xd * pow2dN(ex) : ldexp(xd, ex);
+        __syncthreads();
+        if (threadIdx.x < 32) {
+          const int qq = (lane < 16) ? 16 * p + lane : 4 * NN + 16 * p + (lane - 16);
+          if (16 * p + (lane & 15) < 4 * NN)
+            part[((int64_t)slot * bp.n_tiles + tile0) * 8 * NN + qq] =
+                (red[rb][0][lane] + red[rb][1][lane]) + (red[rb][2][lane] + red[rb][3][lane]);
+        }
+        rb ^= 1;
+      }
+    };
+
+    int slot = bp.obs_first;
+    if (bp.obs_first) observe(0);
+    int to_out = bp.to_out0;
+    uint32_t blk = bp.blk0;
+    int widx = bp.widx0;
+    u4 wd = philox_draw(bp.seed, blk, traj, kPurposeHop);
+    const float tmaxf = (float)bp.tmax;
+    for (int it = 0; it < bp.len; ++it) {
+      kick();  // first half kick at R_n
+#pragma unroll
+      for (int j = 0; j < NPL; ++j) R[j] = __fmaf_rn(cf.dtm[j], P[j], R[j]);
+      build_w(t);
+      kick();  // second half kick at R_{n+1} (the diagonal force's coupling part is a constant)
+      const float w1 = diag_gap(t);
+      ph = df_add(ph, __fmul_rn(bp.hdt_hbar, __fadd_rn(w0, w1)));
+      // events at R_{n+1}: slots 0..NS-1 a -> g with c = W_ga dt / hbar (three
+      // quarter turns), slots NS..2NS-1 b -> g with c = W_bg dt / hbar (one);
+      // the slots g = a and g = b are not events (c = 0)
+      float c[NC];
+#pragma unroll
+      for (int g = 0; g < NS; ++g) {
+        float wga = t[tri<NS>(g, 0)], wbg = wga;
+#pragma unroll
+        for (int h = 1; h < NS; ++h) {
+          const float x = t[tri<NS>(g, h)];
+          wga = (h == al) ? x : wga;
+          wbg = (h == be) ? x : wbg;
+        }
+        c[g] = (g == al) ? 0.0f : __fmul_rn(bp.amp, wga);
+        c[NS + g] = (g == be) ? 0.0f : __fmul_rn(bp.amp, wbg);
+      }
+      const uint32_t word = (widx & 2) ? ((widx & 1) ? wd.w : wd.z) : ((widx & 1) ? wd.y : wd.x);
+      uint32_t T[NC], sumT = 0;
+#pragma unroll
+      for (int k = 0; k < NC; ++k) {
+        const float ka = fabsf(__fmul_rn(bp.kappa, c[k]));
+        T[k] = __float2uint_rz(fminf(ka * kP24f, tmaxf));
+        sumT += T[k];
+      }
+      if (sumT > bp.tmax) {
+        const float sc = (float)bp.tmax / (float)sumT;
+        uint32_t s2 = 0;
+#pragma unroll
+        for (int k = 0; k < NC; ++k) {
+          T[k] = min(__float2uint_rz((float)T[k] * sc), T[k]);
+          s2 += T[k];
+        }
+        sumT = s2;
+      }
+      const uint32_t y = word >> 8;
+      uint32_t cum = 0;
+      int cnt = 0;
+#pragma unroll
+      for (int k = 0; k < NC; ++k) {
+        cum += T[k];
+        cnt += (y >= cum) ? 1 : 0;
+      }
+      const int hit = cnt < NC ? cnt : -1;
+      float ch = c[0];
+      uint32_t Th = T[0];
+#pragma unroll
+      for (int k = 1; k < NC; ++k) {
+        ch = (k == hit) ? c[k] : ch;
+        Th = (k == hit) ? T[k] : Th;
+      }
+      const bool hop = hit >= 0;
+      const float num = hop ? ch * kP24f : kP24f;
+      const float den = __uint2float_rn(hop ? Th : 16777216u - sumT);
+      const float rd = __frcp_rn(den);
+      const float q0 = __fmul_rn(num, rd);
+      const float q1 = __fmul_rn(__fmaf_rn(-q0, den, num), rd);
+      m = df_mul(m, q0, q1);
+      if (!(fabsf(m.hi) <= 0x1p32f && fabsf(m.hi) >= 0x1p-32f)) renormN(m, mexp);
+      w0 = w1;
+      if (hop) {
+        if (hit < NS) {
+          al = hit;
+          q = (q + 3) & 3;
+        } else {
+          be = hit - NS;
+          q = (q + 1) & 3;
+        }
+        pair_force();
+        w0 = diag_gap(t);  // the new pair's gap at R_{n+1}
+      }
+      if (++widx == 4) {
+        widx = 0;
+        ++blk;
+        if (it + 1 < bp.len) wd = philox_draw(bp.seed, blk, traj, kPurposeHop);
+      }
+      if (--to_out == 0) {
+        observe(slot++);
+        to_out = bp.stride;
+      }
+    }
+    if (active) {
+#pragma unroll
+      for (int j = 0; j < NPL; ++j)
+        if (j < bp.n) {
+          ws.R[(int64_t)j * nt + i] = R[j];
+          ws.P[(int64_t)j * nt + i] = P[j];
+        }
+      ws.m[i] = m.hi;
+      ws.mlo[i] = m.lo;
+      ws.mexp[i] = mexp;
+      ws.phi[i] = ph.hi;
+      ws.philo[i] = ph.lo;
+      ws.ab[i] = (uint16_t)(al | (q << 4) | (be << 8));
+      if (!isfinite(m.hi) || !isfinite(ph.hi)) {
+        atomicAdd(&ws.hdr->n_nonfinite, 1ull);
+        atomicOr(&ws.hdr->flags, QCL_FLAG_NONFINITE);
+      }
+    }
+  }
+}
+
 // ------------------------------------------------------- per-N_s launchers --
 // Instantiated one N_s per translation unit; the FP64 sampling and step
 // kernels in their own units (kernels_nstate64_*.cu, compiled without FMA
@@ -1057,19 +1506,35 @@ struct NStateOps {
     const int64_t nb = (sp.n_traj + 127) / 128;
     k_sampleN_f32<NS><<<(unsigned)(nb > 0 ? nb : 1), 128, 0, st>>>(sp, buf);
   }
-  static void step64(const DevModel* dm, void* buf, int64_t nt, int n, int64_t step0,
+  static void step64(const DevModel* dm, int repr, void* buf, int64_t nt, int n, int64_t step0,
                      int64_t step, double dt, uint64_t seed, uint64_t traj_off, cudaStream_t st) {
-    k_stepN_f64<NS><<<(unsigned)((nt + 127) / 128), 128, 0, st>>>(dm, buf, nt, n, step0, step, dt,
-                                                                   seed, traj_off);
+    const unsigned nb = (unsigned)((nt + 127) / 128);
+    if (repr == QCL_REPR_DIABATIC)
+      k_stepN_dia_f64<NS><<<nb, 128, 0, st>>>(dm, buf, nt, n, step0, step, dt, seed, traj_off);
+    else
+      k_stepN_f64<NS><<<nb, 128, 0, st>>>(dm, buf, nt, n, step0, step, dt, seed, traj_off);
   }
-  static void observe64(const void* buf, int64_t nt, int n, double* part, cudaStream_t st) {
-    k_observeN_f64<NS><<<(unsigned)((nt + 255) / 256), 256, 0, st>>>(buf, nt, n, part);
+  static void observe64(const DevModel* dm, const void* buf, int64_t nt, int n, double* part,
+                        cudaStream_t st) {
+    k_observeN_f64<NS><<<(unsigned)((nt + 255) / 256), 256, 0, st>>>(dm, buf, nt, n, part);
   }
   template <int NPL, int WPT = 1>
   static int bulk_npl(const BulkParams& bp, const CoefN& cf, void* buf, double* part,
                       int grid_cap, cudaStream_t st) {
-    static int per_sm = -1, n_sm = 0;
-    auto fn = k_bulkN<NS, NPL, WPT>;
+    // (occupancy cached per kernel: [0] adiabatic, [1] diabatic)
+    static int per_sm[2] = {-1, -1}, n_sm[2] = {0, 0};
+    if (bp.repr == QCL_REPR_DIABATIC)
+      return launch_persistent(k_bulkN_dia<NS, NPL>, per_sm[1], n_sm[1], bp, cf, buf, part,
+                               grid_cap, 1, st);
+    return launch_persistent(k_bulkN<NS, NPL, WPT>, per_sm[0], n_sm[0], bp, cf, buf, part,
+                             grid_cap, WPT, st);
+  }
+  // one persistent grid: the occupancy limit of resident blocks on every SM
+  // (capped), at most one block per WPT tiles
+  template <typename Fn>
+  static int launch_persistent(Fn fn, int& per_sm, int& n_sm, const BulkParams& bp,
+                               const CoefN& cf, void* buf, double* part, int grid_cap, int WPT,
+                               cudaStream_t st) {
     if (per_sm < 0) {
       int dev = 0;
       cudaGetDevice(&dev);

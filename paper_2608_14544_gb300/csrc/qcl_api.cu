@@ -218,7 +218,6 @@ qcl_status qcl_create_model(const qcl_model_desc* d, qcl_model** out) {
   if (!(hop >= 0x1p-16 && hop <= 0x1p16)) return fail(QCL_ERR_INVALID_ARG, "hop_scale = %g outside [2^-16, 2^16]", hop);
   if (!(pmax > 0.0 && pmax <= 1.0 - 0x1p-16)) return fail(QCL_ERR_INVALID_ARG, "p_max = %g outside (0, 1 - 2^-16]", pmax);
   if (d->repr != QCL_REPR_ADIABATIC && d->repr != QCL_REPR_DIABATIC) return fail(QCL_ERR_INVALID_ARG, "repr = %d is neither adiabatic (0) nor diabatic (1)", d->repr);
-  if (d->repr == QCL_REPR_DIABATIC && ns != 2) return fail(QCL_ERR_UNSUPPORTED, "the diabatic representation takes two-state models (n_states = %d)", ns);
   if (d->reserved != 0) return fail(QCL_ERR_INVALID_ARG, "reserved must be 0");
   for (int j = 0; j < n; ++j) {
     if (!(d->mass[j] > 0.0) || !std::isfinite(d->mass[j])) return fail(QCL_ERR_INVALID_ARG, "mass[%d] must be positive", j);
@@ -343,7 +342,7 @@ void make_sampleN32(const qcl_model* model, const SampleParams& sp, SampleN32& s
   s.n = n;
   s.ns = ns;
   s.wigner = sp.wigner;
-  s.pad = 0;
+  s.repr = model->host.repr;
   for (int j = 0; j < kMaxN; ++j) {
     const bool on = j < n;
     s.R0[j] = on ? (float)sp.R0[j] : 0.0f;
@@ -470,7 +469,7 @@ qcl_status qcl_propagate(const qcl_model* model, const qcl_ensemble_desc* ens, v
       if (ns == 2)
         launch_observe_f64(model->dev, ens_buf, nt, model->n, part, s);
       else
-        launch_observeN_f64(ns, ens_buf, nt, model->n, part, s);
+        launch_observeN_f64(model->dev, ns, ens_buf, nt, model->n, part, s);
       launch_fold(part, rows + (size_t)k * q2, fold, OL.n_tiles, q2, 1, s, chunk_row(k));
     };
     if (step0 == 0) observe(0);
@@ -480,7 +479,7 @@ qcl_status qcl_propagate(const qcl_model* model, const qcl_ensemble_desc* ens, v
         if (ns == 2)
           launch_step_f64(model->dev, model->host.repr, ens_buf, nt, model->n, step0, t, dt, ens->seed, ens->traj_id_offset, s);
         else
-          launch_stepN_f64(model->dev, ns, ens_buf, nt, model->n, step0, t, dt, ens->seed, ens->traj_id_offset, s);
+          launch_stepN_f64(model->dev, model->host.repr, ns, ens_buf, nt, model->n, step0, t, dt, ens->seed, ens->traj_id_offset, s);
       }
       if ((t + 1) % out_stride == 0) observe((t + 1) / out_stride);
     }

@@ -608,7 +608,7 @@ qcl_status qcl_server_submit(qcl_server* s, const qcl_request_desc* r, int64_t* 
   if (m.n_states > 2 && m.n_modes > (m.n_states <= 4 ? 32 : 8))
     return fail(QCL_ERR_UNSUPPORTED, "too many modes for a %d-state FP32-bulk model", m.n_states);
   if (m.repr != QCL_REPR_ADIABATIC && m.repr != QCL_REPR_DIABATIC) return fail(QCL_ERR_INVALID_ARG, "unknown representation %d", m.repr);
-  if (m.repr == QCL_REPR_DIABATIC && (m.n_states != 2 || m.n_modes > 32))
+  if (m.repr == QCL_REPR_DIABATIC && m.n_states == 2 && m.n_modes > 32)
     return fail(QCL_ERR_UNSUPPORTED, "the diabatic representation takes two-state FP32-bulk models of at most 32 modes");
   if (!m.mass || !m.omega || !m.E || !m.K || !r->init->rho_el0 || !r->init->R0 || !r->init->P0)
     return fail(QCL_ERR_INVALID_ARG, "a request array is NULL");

@@ -243,3 +243,29 @@ def test_diabatic_walkers_match_branch_enumeration():
     # transitions fired: the populations moved and imaginary parts appeared
     assert abs(exact[k, 0] - exact[0, 0]) > 1e-3
     assert np.abs(exact[k, 1::2]).max() > 1e-3
+
+
+def test_diabatic_three_state_walkers_match_branch_enumeration():
+    """The same enumeration for three states with nuclear coupling in every
+    K_j: four events per step (two per index) besides the stay, each with its
+    own quarter turns, and the adiabatic block rotated by the eigenvectors at
+    each branch's R."""
+    E = np.diag([0.0, 0.3, 0.7]) + 0.1 * (np.ones((3, 3)) - np.eye(3))
+    K = np.zeros((2, 3, 3))
+    K[0] = np.array([[0.4, 0.2, 0.0], [0.2, -0.3, 0.15], [0.0, 0.15, 0.1]])
+    K[1] = np.array([[-0.2, 0.05, 0.25], [0.05, 0.3, -0.1], [0.25, -0.1, 0.0]])
+    model = wl._model(E, K, np.ones(2), np.array([1.0, 1.3]), name="lvc3-dia-pin")
+    model["repr"] = "diabatic"
+    om = O.OracleModel(model)
+    R0, P0 = np.array([0.3, -0.5]), np.array([1.2, 0.8])
+    rho = np.array([[0.6, 0.2, 0.0], [0.2, 0.3, 0.1], [0.0, 0.1, 0.1]])
+    init = {"rho_el0": rho, "R0": R0, "P0": P0, "beta": math.inf, "wigner": 0}
+    dt, k, n = 0.1, 4, 400_000
+    exact = _enumerate_dia(om, model, R0, P0, rho, dt, k)
+    rows, _ = O.run(om, O.OracleInit(om, init), 23, 0, n, dt, k, 1)
+    mean, se = O.finalize(rows, n)
+    z = np.abs(mean - exact) / np.maximum(se, 1e-15)
+    assert np.all((z < 4.5) | (np.abs(mean - exact) < 1e-12)), z.max()
+    # transitions fired into every state and the coherences turned complex
+    assert abs(exact[k, 2 * (2 * 3 + 2)] - exact[0, 2 * (2 * 3 + 2)]) > 1e-3
+    assert np.abs(exact[k, 1:18:2]).max() > 1e-3
