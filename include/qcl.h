@@ -411,8 +411,8 @@ qcl_status qcl_autotune(qcl_model* model, int64_t probe_walkers, int64_t n_steps
                         qcl_launch_shape* best, void* stream);
 
 /* ---------------------------------------------------------------------------
- * Trajectory spawning (two-state models, either representation; FP64, or
- * FP32 bulk with at most 32 modes).
+ * Trajectory spawning (either representation; FP64 for any N_s, or FP32 bulk
+ * for two-state models of at most 32 modes).
  *
  * The scheme of the CPU code that the paper's GPU version replaces (Sec. II B:
  * there a new trajectory was started each time a transition test fired, so
@@ -452,9 +452,11 @@ qcl_status qcl_spawn_bytes(const qcl_model* model, const qcl_ensemble_desc* ens,
  * m, phi (double in FP64, float in FP32), index pair (uint16: a | q << 4 |
  * b << 8), random-stream id (uint64), family (uint32); offsets[7] = total
  * bytes; FP32 only (0 in FP64): offsets[8] = m_lo (float), [9] = m_exp
- * (int32; the weight is (m + m_lo) 2^m_exp), [10] = phi_lo (float). */
+ * (int32; the weight is (m + m_lo) 2^m_exp), [10] = phi_lo (float); N_s > 2
+ * only (else 0): offsets[11] = the carried eigenvectors U [N_s * N_s][capacity]
+ * (double; element (i, a) at row i * N_s + a). */
 qcl_status qcl_spawn_layout(const qcl_model* model, const qcl_ensemble_desc* ens, int64_t capacity,
-                            int32_t set, size_t offsets[11]);
+                            int32_t set, size_t offsets[12]);
 
 /* Samples the n0 initial walkers into set 0 (as qcl_sample_initial; ids
  * traj_id_offset + i, family i). */

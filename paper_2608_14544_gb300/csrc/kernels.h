@@ -211,13 +211,15 @@ constexpr size_t kSpawnHeaderOff = 64;  // after EnsHeader, inside the first 256
 struct SpawnLayout {
   // walker set: R[n][cap], P[n][cap], m, phi, ab (uint16), id (uint64),
   // fam (uint32); FP32 sets add m_lo, m_exp (int32) and phi_lo (compensated
-  // pairs with a carried exponent, as in the bulk kernels)
+  // pairs with a carried exponent, as in the bulk kernels); sets of N_s > 2
+  // states (FP64) add the carried eigenvectors U[ns * ns][cap]
   size_t set_off[2];
-  size_t R, P, m, mlo, mexp, phi, philo, ab, id, fam, set_bytes;
+  size_t R, P, m, mlo, mexp, phi, philo, ab, id, fam, U, set_bytes;
   // staging of a step's children, per parent: weight (FP32: hi, lo, exp), pair
   size_t cm, cmlo, cmexp, cab, flag, bsum, boff, fstart, total;
   int64_t n_blocks;  // capacity / 256, rounded up
-  __host__ __device__ static SpawnLayout make(int64_t cap, int n, int64_t n0, int precision) {
+  __host__ __device__ static SpawnLayout make(int64_t cap, int n, int64_t n0, int precision,
+                                              int ns = 2) {
     SpawnLayout L{};
     const size_t c = (size_t)cap;
     const bool f32 = precision == QCL_PREC_FP32_BULK;
@@ -243,6 +245,8 @@ struct SpawnLayout {
     o = align256(o + 8 * c);
     L.fam = o;
     o = align256(o + 4 * c);
+    L.U = o;
+    if (ns > 2) o = align256(o + w * c * (size_t)(ns * ns));
     L.set_bytes = o;
     L.set_off[0] = 256;
     L.set_off[1] = 256 + L.set_bytes;
@@ -283,10 +287,18 @@ void launch_spawn_observe(const DevModel* dm, const void* buf, int64_t capacity,
 // walkers up to the live count (which the host does not know).
 unsigned spawn_grid(int64_t capacity);
 // The block-count scan and the family starts, for either precision's layout.
-void launch_spawn_scan(void* buf, int64_t capacity, int n, int64_t n0, int precision, int64_t step0,
+void launch_spawn_scan(void* buf, int64_t capacity, int n, int64_t n0, int precision, int ns, int64_t step0,
                        int64_t step, cudaStream_t st);
-void launch_spawn_fstart(const void* buf, int64_t capacity, int n, int64_t n0, int precision, int set,
+void launch_spawn_fstart(const void* buf, int64_t capacity, int n, int64_t n0, int precision, int ns, int set,
                          cudaStream_t st);
+// FP64 spawning for N_s = 3..8 states (either representation): sample, one
+// step (step kernel, scan, scatter), observation (family starts, family sums).
+void launch_spawnN_sample(const DevModel* dm, int ns, const SampleParams& sp, int64_t capacity,
+                          void* buf, cudaStream_t st);
+void launch_spawnN_step(const DevModel* dm, int ns, void* buf, int64_t capacity, int n, int64_t n0,
+                        int64_t step0, int64_t step, double dt, uint64_t seed, cudaStream_t st);
+void launch_spawnN_observe(const DevModel* dm, int ns, const void* buf, int64_t capacity, int n,
+                           int64_t n0, int set, double* part, cudaStream_t st);
 // FP32-bulk spawning (two states, n <= 32 modes): sample, one step (step
 // kernel, scan, scatter), family observation.
 void launch_spawn_sample32(const DevModel& host, const SampleParams& sp, int64_t capacity, void* buf,

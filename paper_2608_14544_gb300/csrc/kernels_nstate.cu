@@ -10,7 +10,13 @@ namespace qcl {
   void nstate_step64_##k(const DevModel*, int, void*, int64_t, int, int64_t, int64_t, double, \
                          uint64_t, uint64_t, cudaStream_t);                                   \
   void nstate_observe64_##k(const DevModel*, const void*, int64_t, int, double*, cudaStream_t); \
-  int nstate_bulk_##k(const BulkParams&, const CoefN&, void*, double*, int, int, cudaStream_t);
+  int nstate_bulk_##k(const BulkParams&, const CoefN&, void*, double*, int, int, cudaStream_t); \
+  void nstate_spawn_sample64_##k(const DevModel*, const SampleParams&, int64_t, void*,        \
+                                 cudaStream_t);                                               \
+  void nstate_spawn_step64_##k(const DevModel*, void*, int64_t, int, int64_t, int64_t, int64_t, \
+                               double, uint64_t, cudaStream_t);                               \
+  void nstate_spawn_observe64_##k(const DevModel*, const void*, int64_t, int, int64_t, int,   \
+                                  double*, cudaStream_t);
 QCL_NS_DECL(3)
 QCL_NS_DECL(4)
 QCL_NS_DECL(5)
@@ -50,6 +56,21 @@ void launch_observeN_f64(const DevModel* dm, int ns, const void* buf, int64_t nt
                          double* part, cudaStream_t st) {
   QCL_NS_SWITCH(ns, nstate_observe64, dm, buf, nt, n, part, st);
   launches_add(1);
+}
+
+void launch_spawnN_sample(const DevModel* dm, int ns, const SampleParams& sp, int64_t capacity,
+                          void* buf, cudaStream_t st) {
+  QCL_NS_SWITCH(ns, nstate_spawn_sample64, dm, sp, capacity, buf, st);
+}
+
+void launch_spawnN_step(const DevModel* dm, int ns, void* buf, int64_t capacity, int n, int64_t n0,
+                        int64_t step0, int64_t step, double dt, uint64_t seed, cudaStream_t st) {
+  QCL_NS_SWITCH(ns, nstate_spawn_step64, dm, buf, capacity, n, n0, step0, step, dt, seed, st);
+}
+
+void launch_spawnN_observe(const DevModel* dm, int ns, const void* buf, int64_t capacity, int n,
+                           int64_t n0, int set, double* part, cudaStream_t st) {
+  QCL_NS_SWITCH(ns, nstate_spawn_observe64, dm, buf, capacity, n, n0, set, part, st);
 }
 
 int launch_bulkN(int ns, const BulkParams& bp, const CoefN& cf, void* buf, double* part,

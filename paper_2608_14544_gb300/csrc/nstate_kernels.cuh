@@ -180,26 +180,17 @@ __device__ __forceinline__ bool event_amplitudes(const T (&G)[NS][NS], const T (
 using namespace nsd;
 
 // ----------------------------------------------------------- FP64 sampling --
+// One initial walker (FP64): Wigner (R, P) at Rg[j * stride], Pg[j * stride],
+// the decomposition U at R_0, and the pair drawn from |rho| (U^T rho_el0 U in
+// the adiabatic basis, rho_el0 itself in the diabatic one) with m_0 = rho /
+// p_hat.
 template <int NS>
-__global__ void __launch_bounds__(128) k_sampleN_f64(const DevModel* __restrict__ M,
-                                                     SampleParams sp, void* buf) {
-  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  const int64_t nt = sp.n_traj;
+__device__ __forceinline__ void sample_walkerN_f64(const DevModel* __restrict__ M,
+                                                   const SampleParams& sp, uint64_t traj,
+                                                   double* Rg, double* Pg, int64_t stride,
+                                                   double& m0, uint16_t& ab,
+                                                   double (&U)[NS][NS]) {
   const int n = sp.n;
-  WN<double> w = viewN<double>(buf, nt, NS, n, QCL_PREC_FP64);
-  if (i == 0) {
-    w.hdr->magic = kEnsMagic;
-    w.hdr->n_traj = nt;
-    w.hdr->precision = QCL_PREC_FP64;
-    w.hdr->ns = NS;
-    w.hdr->n = n;
-    w.hdr->step = 0;
-    w.hdr->flags = 0;
-    w.hdr->n_degenerate = 0;
-    w.hdr->n_nonfinite = 0;
-  }
-  if (i >= nt) return;
-  const uint64_t traj = sp.traj_offset + (uint64_t)i;
   for (int j = 0; j < n; ++j) {
     double R = sp.R0[j], P = sp.P0[j];
     if (sp.wigner) {
@@ -212,11 +203,11 @@ __global__ void __launch_bounds__(128) k_sampleN_f64(const DevModel* __restrict_
       R += sp.sR[j] * rad * cs;
       P += sp.sP[j] * rad * sn;
     }
-    w.R[(int64_t)j * nt + i] = R;
-    w.P[(int64_t)j * nt + i] = P;
+    Rg[(int64_t)j * stride] = R;
+    Pg[(int64_t)j * stride] = P;
   }
-  double W[NS][NS], e[NS], U[NS][NS];
-  elec_g<NS>(M, w.R + i, nt, n, W);
+  double W[NS][NS], e[NS];
+  elec_g<NS>(M, Rg, stride, n, W);
   eigh_ns<double, NS>(W, nullptr, e, U, 100, 1e-34);
   // the pair's density: U^T rho U in the adiabatic basis, rho itself in the
   // diabatic one
@@ -255,9 +246,36 @@ __global__ void __launch_bounds__(128) k_sampleN_f64(const DevModel* __restrict_
       break;
     }
   }
-  w.m[i] = rho_ad[pickk] / ((double)Tk[pickk] / kP24);
+  m0 = rho_ad[pickk] / ((double)Tk[pickk] / kP24);
+  ab = (uint16_t)((pickk / NS) | ((pickk % NS) << 8));
+}
+
+template <int NS>
+__global__ void __launch_bounds__(128) k_sampleN_f64(const DevModel* __restrict__ M,
+                                                     SampleParams sp, void* buf) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t nt = sp.n_traj;
+  const int n = sp.n;
+  WN<double> w = viewN<double>(buf, nt, NS, n, QCL_PREC_FP64);
+  if (i == 0) {
+    w.hdr->magic = kEnsMagic;
+    w.hdr->n_traj = nt;
+    w.hdr->precision = QCL_PREC_FP64;
+    w.hdr->ns = NS;
+    w.hdr->n = n;
+    w.hdr->step = 0;
+    w.hdr->flags = 0;
+    w.hdr->n_degenerate = 0;
+    w.hdr->n_nonfinite = 0;
+  }
+  if (i >= nt) return;
+  double U[NS][NS];
+  double m0;
+  uint16_t ab;
+  sample_walkerN_f64<NS>(M, sp, sp.traj_offset + (uint64_t)i, w.R + i, w.P + i, nt, m0, ab, U);
+  w.m[i] = m0;
   w.phi[i] = 0.0;
-  w.ab[i] = (uint16_t)((pickk / NS) | ((pickk % NS) << 8));
+  w.ab[i] = ab;
 #pragma unroll
   for (int a = 0; a < NS; ++a)
 #pragma unroll
@@ -265,28 +283,54 @@ __global__ void __launch_bounds__(128) k_sampleN_f64(const DevModel* __restrict_
 }
 
 // --------------------------------------------------------------- FP64 step --
-template <int NS>
-__global__ void __launch_bounds__(128) k_stepN_f64(const DevModel* __restrict__ M, void* buf,
-                                                   int64_t nt, int n, int64_t step0, int64_t step,
-                                                   double dt, uint64_t seed, uint64_t traj_off) {
-  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  WN<double> w = viewN<double>(buf, nt, NS, n, QCL_PREC_FP64);
-  if (i >= nt) return;
-  if (w.hdr->step != step0) {
-    if (i == 0) atomicOr(&w.hdr->flags, QCL_FLAG_STEP_MISMATCH);
-    return;
+// Outcome of one walker's FP64 N_s-state step (either representation): the
+// event slot drawn (-1: none), its amplitude and threshold, the sum of all
+// thresholds (for the stay factor) and whether a gap was degenerate.  The
+// caller applies it: a moving walker takes the hop or the stay factor, a
+// spawning walker stages a child and keeps its own pair and weight.
+struct StepN {
+  int hit;
+  double A;
+  uint64_t T, sumT;
+  bool deg;
+};
+
+// The draw of `step` for the walker with random stream `traj` among the
+// slots' thresholds, in slot order.
+template <int NC>
+__device__ __forceinline__ StepN draw_event(const double (&A)[NC], const uint64_t (&T)[NC],
+                                            uint64_t sumT, bool deg, uint64_t seed, uint64_t traj,
+                                            int64_t step) {
+  const u4 wd = philox_draw(seed, (uint32_t)(step >> 2), traj, kPurposeHop);
+  const uint64_t y = word_of(wd, (int)(step & 3)) >> 8;
+  uint64_t cum = 0;
+  int hit = -1;
+#pragma unroll
+  for (int k = 0; k < NC; ++k) {
+    cum += T[k];
+    if (hit < 0 && y < cum) hit = k;
   }
-  const uint16_t ab = w.ab[i];
-  int al = ab & 0xff, be = ab >> 8;
-  double m = w.m[i], phi = w.phi[i];
-  double Uc[NS][NS];
+  double Ah = A[0];
+  uint64_t Th = T[0];
 #pragma unroll
-  for (int a = 0; a < NS; ++a)
-#pragma unroll
-    for (int b = 0; b < NS; ++b) Uc[a][b] = w.U[(int64_t)(a * NS + b) * nt + i];
-  double* R = w.R + i;
-  double* P = w.P + i;
-  double W[NS][NS], e0[NS], U0[NS][NS], e1[NS], U1[NS][NS];
+  for (int k = 1; k < NC; ++k) {
+    Ah = (k == hit) ? A[k] : Ah;
+    Th = (k == hit) ? T[k] : Th;
+  }
+  return {hit, Ah, Th, sumT, deg};
+}
+
+// Adiabatic pairs: velocity Verlet on the pair's mean force with the
+// decompositions at R_n and R_{n+1} (gauge following the carried eigenvectors
+// Uc; U1 receives those at R_{n+1}), the trapezoid phase, the 2 N_s event
+// slots' amplitudes and thresholds, and the draw.  R and P at R[j * nt].
+template <int NS>
+__device__ __forceinline__ StepN walker_stepN_f64(const DevModel* __restrict__ M, double* R,
+                                                  double* P, int64_t nt, int n, int al, int be,
+                                                  double& phi, const double (&Uc)[NS][NS],
+                                                  double (&U1)[NS][NS], double dt, uint64_t seed,
+                                                  uint64_t traj, int64_t step) {
+  double W[NS][NS], e0[NS], U0[NS][NS], e1[NS];
   // decomposition at R_n, gauge following the carried eigenvectors
   elec_g<NS>(M, R, nt, n, W);
   eigh_ns<double, NS>(W, Uc, e0, U0, 100, 1e-34, false);
@@ -365,28 +409,36 @@ __global__ void __launch_bounds__(128) k_stepN_f64(const DevModel* __restrict__ 
       sumT += T[k];
     }
   }
-  const u4 wd = philox_draw(seed, (uint32_t)(step >> 2), traj_off + (uint64_t)i, kPurposeHop);
-  const uint64_t y = word_of(wd, (int)(step & 3)) >> 8;
-  uint64_t cum = 0;
-  int hit = -1;
-#pragma unroll
-  for (int k = 0; k < NC; ++k) {
-    cum += T[k];
-    if (hit < 0 && y < cum) hit = k;
+  return draw_event<NC>(A, T, sumT, deg, seed, traj, step);
+}
+
+template <int NS>
+__global__ void __launch_bounds__(128) k_stepN_f64(const DevModel* __restrict__ M, void* buf,
+                                                   int64_t nt, int n, int64_t step0, int64_t step,
+                                                   double dt, uint64_t seed, uint64_t traj_off) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  WN<double> w = viewN<double>(buf, nt, NS, n, QCL_PREC_FP64);
+  if (i >= nt) return;
+  if (w.hdr->step != step0) {
+    if (i == 0) atomicOr(&w.hdr->flags, QCL_FLAG_STEP_MISMATCH);
+    return;
   }
-  if (hit < 0) {
-    m = m / (1.0 - (double)sumT / kP24);
-  } else {
-    double Ah = A[0];
-    uint64_t Th = T[0];
+  const uint16_t ab = w.ab[i];
+  int al = ab & 0xf, be = (ab >> 8) & 0xf;
+  double m = w.m[i], phi = w.phi[i];
+  double Uc[NS][NS], U1[NS][NS];
 #pragma unroll
-    for (int k = 1; k < NC; ++k) {
-      Ah = (k == hit) ? A[k] : Ah;
-      Th = (k == hit) ? T[k] : Th;
-    }
-    m = m * Ah / ((double)Th / kP24);
-    if (hit < NS) al = hit;
-    else be = hit - NS;
+  for (int a = 0; a < NS; ++a)
+#pragma unroll
+    for (int b = 0; b < NS; ++b) Uc[a][b] = w.U[(int64_t)(a * NS + b) * nt + i];
+  const StepN o = walker_stepN_f64<NS>(M, w.R + i, w.P + i, nt, n, al, be, phi, Uc, U1, dt, seed,
+                                       traj_off + (uint64_t)i, step);
+  if (o.hit < 0) {
+    m = m / (1.0 - (double)o.sumT / kP24);
+  } else {
+    m = m * o.A / ((double)o.T / kP24);
+    if (o.hit < NS) al = o.hit;
+    else be = o.hit - NS;
   }
   w.m[i] = m;
   w.phi[i] = phi;
@@ -395,7 +447,7 @@ __global__ void __launch_bounds__(128) k_stepN_f64(const DevModel* __restrict__ 
   for (int a = 0; a < NS; ++a)
 #pragma unroll
     for (int b = 0; b < NS; ++b) w.U[(int64_t)(a * NS + b) * nt + i] = U1[a][b];
-  if (deg) {
+  if (o.deg) {
     atomicAdd(&w.hdr->n_degenerate, 1ull);
     atomicOr(&w.hdr->flags, QCL_FLAG_DEGENERATE);
   }
@@ -439,23 +491,13 @@ __device__ __forceinline__ double diag_pick(const double (&W)[NS][NS], int a) {
   return v;
 }
 
+// Diabatic pairs: the deterministic part and the draw (A = c, the real factor
+// of the event's amplitude; slot < NS takes three quarter turns, the others one).
 template <int NS>
-__global__ void __launch_bounds__(128) k_stepN_dia_f64(const DevModel* __restrict__ M, void* buf,
-                                                       int64_t nt, int n, int64_t step0,
-                                                       int64_t step, double dt, uint64_t seed,
-                                                       uint64_t traj_off) {
-  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  WN<double> w = viewN<double>(buf, nt, NS, n, QCL_PREC_FP64);
-  if (i >= nt) return;
-  if (w.hdr->step != step0) {
-    if (i == 0) atomicOr(&w.hdr->flags, QCL_FLAG_STEP_MISMATCH);
-    return;
-  }
-  const uint16_t ab = w.ab[i];
-  int al = ab & 0xf, be = (ab >> 8) & 0xf, q = (ab >> 4) & 3;
-  double m = w.m[i], phi = w.phi[i];
-  double* R = w.R + i;
-  double* P = w.P + i;
+__device__ __forceinline__ StepN walker_stepN_dia_f64(const DevModel* __restrict__ M, double* R,
+                                                      double* P, int64_t nt, int n, int al, int be,
+                                                      double& phi, double dt, uint64_t seed,
+                                                      uint64_t traj, int64_t step) {
   double W0[NS][NS], W1[NS][NS];
   elec_g<NS>(M, R, nt, n, W0);
   dia_kick_g<NS>(M, R, P, nt, n, al, be, dt);
@@ -500,31 +542,35 @@ __global__ void __launch_bounds__(128) k_stepN_dia_f64(const DevModel* __restric
       sumT += T[k];
     }
   }
-  const u4 wd = philox_draw(seed, (uint32_t)(step >> 2), traj_off + (uint64_t)i, kPurposeHop);
-  const uint64_t y = word_of(wd, (int)(step & 3)) >> 8;
-  uint64_t cum = 0;
-  int hit = -1;
-#pragma unroll
-  for (int k = 0; k < NC; ++k) {
-    cum += T[k];
-    if (hit < 0 && y < cum) hit = k;
+  return draw_event<NC>(c, T, sumT, false, seed, traj, step);
+}
+
+template <int NS>
+__global__ void __launch_bounds__(128) k_stepN_dia_f64(const DevModel* __restrict__ M, void* buf,
+                                                       int64_t nt, int n, int64_t step0,
+                                                       int64_t step, double dt, uint64_t seed,
+                                                       uint64_t traj_off) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  WN<double> w = viewN<double>(buf, nt, NS, n, QCL_PREC_FP64);
+  if (i >= nt) return;
+  if (w.hdr->step != step0) {
+    if (i == 0) atomicOr(&w.hdr->flags, QCL_FLAG_STEP_MISMATCH);
+    return;
   }
-  if (hit < 0) {
-    m = m / (1.0 - (double)sumT / kP24);
+  const uint16_t ab = w.ab[i];
+  int al = ab & 0xf, be = (ab >> 8) & 0xf, q = (ab >> 4) & 3;
+  double m = w.m[i], phi = w.phi[i];
+  const StepN o = walker_stepN_dia_f64<NS>(M, w.R + i, w.P + i, nt, n, al, be, phi, dt, seed,
+                                           traj_off + (uint64_t)i, step);
+  if (o.hit < 0) {
+    m = m / (1.0 - (double)o.sumT / kP24);
   } else {
-    double ch = c[0];
-    uint64_t Th = T[0];
-#pragma unroll
-    for (int k = 1; k < NC; ++k) {
-      ch = (k == hit) ? c[k] : ch;
-      Th = (k == hit) ? T[k] : Th;
-    }
-    m = m * ch / ((double)Th / kP24);
-    if (hit < NS) {
-      al = hit;
+    m = m * o.A / ((double)o.T / kP24);
+    if (o.hit < NS) {
+      al = o.hit;
       q = (q + 3) & 3;
     } else {
-      be = hit - NS;
+      be = o.hit - NS;
       q = (q + 1) & 3;
     }
   }
@@ -655,6 +701,291 @@ __global__ void __launch_bounds__(256) k_observeN_f64(const DevModel* __restrict
       const int q = (lane < 16) ? 16 * p + lane : 4 * NN + 16 * p + (lane - 16);
       if (16 * p + (lane & 15) < 4 * NN)
         part[(int64_t)blockIdx.x * 8 * NN + q] = tile_tree8(&red[0][0], 32, lane);
+    }
+    __syncthreads();
+  }
+}
+
+// ------------------------------------------------------ FP64 spawning, N_s --
+// Trajectory spawning for N_s-state models (FP64, either representation): the
+// two-state scheme with the N_s-state step.  Every step a walker whose
+// transition test fires keeps its pair, eigenvectors and weight and spawns a
+// child at the event's target pair with weight m A_e / p_hat_e (the diabatic
+// one with the event's quarter turns); children follow their parents by the
+// same count / scan / scatter, so the walker order is reproducible bit for
+// bit and each family stays contiguous.
+struct SetN {
+  double* R;
+  double* P;
+  double* m;
+  double* phi;
+  uint16_t* ab;
+  uint64_t* id;
+  uint32_t* fam;
+  double* U;  // [NS * NS][cap]
+};
+
+__device__ __forceinline__ SetN spawn_setN(void* buf, const SpawnLayout& L, int set) {
+  char* b = (char*)buf + L.set_off[set];
+  return {(double*)(b + L.R),   (double*)(b + L.P),    (double*)(b + L.m),
+          (double*)(b + L.phi), (uint16_t*)(b + L.ab), (uint64_t*)(b + L.id),
+          (uint32_t*)(b + L.fam), (double*)(b + L.U)};
+}
+
+// Random-stream id of the child spawned at `step` by the walker `parent`
+// (the two-state spawning's: words 0 and 1 of Philox block (step, parent,
+// purpose 3), bit 63 set).
+__device__ __forceinline__ uint64_t spawn_child_id(uint64_t seed, int64_t step, uint64_t parent) {
+  const u4 w = philox_draw(seed, (uint32_t)step, parent, 3u);
+  return (((uint64_t)w.y << 32) | w.x) | (1ull << 63);
+}
+
+template <int NS>
+__global__ void __launch_bounds__(128) k_spawnN_sample(const DevModel* __restrict__ M,
+                                                       SampleParams sp, int64_t cap, void* buf) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t n0 = sp.n_traj;
+  const SpawnLayout L = SpawnLayout::make(cap, sp.n, n0, QCL_PREC_FP64, NS);
+  EnsHeader* hdr = (EnsHeader*)buf;
+  SpawnHeader* sh = (SpawnHeader*)((char*)buf + kSpawnHeaderOff);
+  if (i == 0) {
+    hdr->magic = kEnsMagic;
+    hdr->n_traj = n0;
+    hdr->precision = QCL_PREC_FP64;
+    hdr->ns = NS;
+    hdr->n = sp.n;
+    hdr->step = 0;
+    hdr->flags = 0;
+    hdr->n_degenerate = 0;
+    hdr->n_nonfinite = 0;
+    sh->capacity = cap;
+    sh->n0 = n0;
+    sh->n_live[0] = n0;
+    sh->n_live[1] = 0;
+    sh->drop = 0;
+  }
+  if (i >= n0) return;
+  const SetN w = spawn_setN(buf, L, 0);
+  const uint64_t traj = sp.traj_offset + (uint64_t)i;
+  double U[NS][NS];
+  double m0;
+  uint16_t ab;
+  sample_walkerN_f64<NS>(M, sp, traj, w.R + i, w.P + i, cap, m0, ab, U);
+  w.m[i] = m0;
+  w.phi[i] = 0.0;
+  w.ab[i] = ab;
+  w.id[i] = traj;
+  w.fam[i] = (uint32_t)i;
+#pragma unroll
+  for (int a = 0; a < NS; ++a)
+#pragma unroll
+    for (int b = 0; b < NS; ++b) w.U[(int64_t)(a * NS + b) * cap + i] = U[a][b];
+}
+
+// Step of every live walker of set `src` in place; the children's weights and
+// pair words go to the per-parent staging arrays, each group's child count to
+// bsum (groups of 256 walkers, as the scan expects).
+template <int NS>
+__global__ void __launch_bounds__(256) k_spawnN_step(const DevModel* __restrict__ M, void* buf,
+                                                     int64_t cap, int n, int64_t n0, int64_t step0,
+                                                     int64_t step, double dt, uint64_t seed) {
+  const SpawnLayout L = SpawnLayout::make(cap, n, n0, QCL_PREC_FP64, NS);
+  EnsHeader* hdr = (EnsHeader*)buf;
+  const int src = (int)(step & 1);
+  const int64_t n_live = ((SpawnHeader*)((char*)buf + kSpawnHeaderOff))->n_live[src];
+  if (hdr->step != step0) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) atomicOr(&hdr->flags, QCL_FLAG_STEP_MISMATCH);
+    return;
+  }
+  const bool dia = M->repr == QCL_REPR_DIABATIC;
+  const int64_t nvb = (n_live + 255) / 256;
+  for (int64_t vb = blockIdx.x; vb < nvb; vb += gridDim.x) {
+    const int64_t i = vb * 256 + threadIdx.x;
+    int flag = 0;
+    if (i < n_live) {
+      const SetN w = spawn_setN(buf, L, src);
+      const uint16_t ab = w.ab[i];
+      const int al = ab & 0xf, be = (ab >> 8) & 0xf, q = (ab >> 4) & 3;
+      double phi = w.phi[i];
+      const double m = w.m[i];
+      StepN o;
+      if (dia) {
+        o = walker_stepN_dia_f64<NS>(M, w.R + i, w.P + i, cap, n, al, be, phi, dt, seed, w.id[i],
+                                     step);
+      } else {
+        double Uc[NS][NS], U1[NS][NS];
+#pragma unroll
+        for (int a = 0; a < NS; ++a)
+#pragma unroll
+          for (int b = 0; b < NS; ++b) Uc[a][b] = w.U[(int64_t)(a * NS + b) * cap + i];
+        o = walker_stepN_f64<NS>(M, w.R + i, w.P + i, cap, n, al, be, phi, Uc, U1, dt, seed,
+                                 w.id[i], step);
+#pragma unroll
+        for (int a = 0; a < NS; ++a)
+#pragma unroll
+          for (int b = 0; b < NS; ++b) w.U[(int64_t)(a * NS + b) * cap + i] = U1[a][b];
+      }
+      w.phi[i] = phi;
+      flag = o.hit >= 0;
+      uint8_t* fl = (uint8_t*)((char*)buf + L.flag);
+      fl[i] = (uint8_t)flag;
+      if (flag) {
+        const double mc = m * o.A / ((double)o.T / kP24);
+        const bool first = o.hit < NS;
+        const int ca = first ? o.hit : al, cb = first ? be : o.hit - NS;
+        const int cq = dia ? ((q + (first ? 3 : 1)) & 3) : q;
+        ((double*)((char*)buf + L.cm))[i] = mc;
+        ((uint16_t*)((char*)buf + L.cab))[i] = (uint16_t)(ca | (cq << 4) | (cb << 8));
+        if (!isfinite(mc)) {
+          atomicAdd(&hdr->n_nonfinite, 1ull);
+          atomicOr(&hdr->flags, QCL_FLAG_NONFINITE);
+        }
+      }
+      if (o.deg) {
+        atomicAdd(&hdr->n_degenerate, 1ull);
+        atomicOr(&hdr->flags, QCL_FLAG_DEGENERATE);
+      }
+      if (!isfinite(phi)) {
+        atomicAdd(&hdr->n_nonfinite, 1ull);
+        atomicOr(&hdr->flags, QCL_FLAG_NONFINITE);
+      }
+    }
+    const int cnt = __syncthreads_count(flag);
+    if (threadIdx.x == 0) ((int32_t*)((char*)buf + L.bsum))[vb] = cnt;
+  }
+}
+
+// Moves every live walker of set src (eigenvectors too) to its place in the
+// other set, after the children of the walkers before it, and writes each
+// child right after its parent.
+template <int NS>
+__global__ void __launch_bounds__(256) k_spawnN_scatter(void* buf, int64_t cap, int n, int64_t n0,
+                                                        int64_t step0, int64_t step,
+                                                        uint64_t seed) {
+  __shared__ int wcnt[8];
+  const SpawnLayout L = SpawnLayout::make(cap, n, n0, QCL_PREC_FP64, NS);
+  EnsHeader* hdr = (EnsHeader*)buf;
+  SpawnHeader* sh = (SpawnHeader*)((char*)buf + kSpawnHeaderOff);
+  if (hdr->step != step0) return;  // uniform over the grid
+  const int src = (int)(step & 1);
+  const int64_t n_live = sh->n_live[src];
+  const bool drop = sh->drop != 0;
+  const uint8_t* fl = (const uint8_t*)((char*)buf + L.flag);
+  const int64_t nvb = (n_live + 255) / 256;
+  for (int64_t vb = blockIdx.x; vb < nvb; vb += gridDim.x) {
+    const int64_t i = vb * 256 + threadIdx.x;
+    const bool live = i < n_live;
+    const int flag = (live && !drop) ? fl[i] : 0;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const unsigned bal = __ballot_sync(0xffffffffu, flag);
+    if (lane == 0) wcnt[wid] = __popc(bal);
+    __syncthreads();
+    int before = __popc(bal & ((1u << lane) - 1u));
+    for (int k = 0; k < wid; ++k) before += wcnt[k];
+    if (live) {
+      const int64_t boff = drop ? 0 : ((const int64_t*)((char*)buf + L.boff))[vb];
+      const int64_t pos = i + boff + before;
+      const SetN s = spawn_setN(buf, L, src);
+      const SetN d = spawn_setN(buf, L, src ^ 1);
+      for (int j = 0; j < n; ++j) {
+        const double r = s.R[(int64_t)j * cap + i], p = s.P[(int64_t)j * cap + i];
+        d.R[(int64_t)j * cap + pos] = r;
+        d.P[(int64_t)j * cap + pos] = p;
+        if (flag) {
+          d.R[(int64_t)j * cap + pos + 1] = r;
+          d.P[(int64_t)j * cap + pos + 1] = p;
+        }
+      }
+#pragma unroll
+      for (int k = 0; k < NS * NS; ++k) {
+        const double u = s.U[(int64_t)k * cap + i];
+        d.U[(int64_t)k * cap + pos] = u;
+        if (flag) d.U[(int64_t)k * cap + pos + 1] = u;
+      }
+      const double phi = s.phi[i];
+      const uint64_t id = s.id[i];
+      const uint32_t fam = s.fam[i];
+      d.m[pos] = s.m[i];
+      d.phi[pos] = phi;
+      d.ab[pos] = s.ab[i];
+      d.id[pos] = id;
+      d.fam[pos] = fam;
+      if (flag) {
+        d.m[pos + 1] = ((const double*)((char*)buf + L.cm))[i];
+        d.phi[pos + 1] = phi;
+        d.ab[pos + 1] = ((const uint16_t*)((char*)buf + L.cab))[i];
+        d.id[pos + 1] = spawn_child_id(seed, step, id);
+        d.fam[pos + 1] = fam;
+      }
+    }
+    __syncthreads();  // wcnt is rewritten by the next group
+  }
+}
+
+// One thread per family: the family sum X of its walkers' 4 N_s^2
+// contributions (in walker order), then X and X^2 reduced over the tile's 256
+// families by the fixed tree of the observation kernel, in passes of 16.
+template <int NS>
+__global__ void __launch_bounds__(256) k_spawnN_observe(const DevModel* __restrict__ M,
+                                                        const void* buf, int64_t cap, int n,
+                                                        int64_t n0, int set,
+                                                        double* __restrict__ part) {
+  __shared__ double red[8][32];
+  constexpr int NN = NS * NS, NQ = 4 * NN, NP = (NQ + 15) / 16;
+  const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const SpawnLayout L = SpawnLayout::make(cap, n, n0, QCL_PREC_FP64, NS);
+  const SetN s = spawn_setN((void*)buf, L, set);
+  const int64_t* fstart = (const int64_t*)((const char*)buf + L.fstart);
+  const bool dia = M->repr == QCL_REPR_DIABATIC;
+  double X[NQ];
+  for (int t = 0; t < NQ; ++t) X[t] = 0.0;
+  if (k < n0) {
+    const int64_t j0 = fstart[k], j1 = fstart[k + 1];
+    for (int64_t j = j0; j < j1; ++j) {
+      double U[NS][NS];
+      if (dia) {
+        double W[NS][NS], e[NS];
+        elec_g<NS>(M, s.R + j, cap, n, W);
+        eigh_ns<double, NS>(W, nullptr, e, U, 100, 1e-34);
+      } else {
+#pragma unroll
+        for (int a = 0; a < NS; ++a)
+#pragma unroll
+          for (int b = 0; b < NS; ++b) U[a][b] = s.U[(int64_t)(a * NS + b) * cap + j];
+      }
+      const uint16_t ab = s.ab[j];
+      const int al = ab & 0xf, be = (ab >> 8) & 0xf, qt = (ab >> 4) & 3;
+      double sn, cs;
+      sincos(s.phi[j], &sn, &cs);
+      const double xr = s.m[j] * cs, xi = -s.m[j] * sn;
+      const double zr = qt == 0 ? xr : (qt == 1 ? -xi : (qt == 2 ? -xr : xi));
+      const double zi = qt == 0 ? xi : (qt == 1 ? xr : (qt == 2 ? -xi : -xr));
+      for (int p = 0; p < NP; ++p) {
+        double v16[16];
+        if (dia) contrib_values_dia<double, NS>(U, al, be, zr, zi, p, v16);
+        else contrib_values<double, NS>(U, al, be, zr, zi, p, v16);
+#pragma unroll
+        for (int t = 0; t < 16; ++t)
+          if (16 * p + t < NQ) X[16 * p + t] += v16[t];
+      }
+    }
+  }
+  for (int p = 0; p < NP; ++p) {
+    double v[32];
+#pragma unroll
+    for (int t = 0; t < 16; ++t) {
+      const double x = (16 * p + t < NQ) ? X[16 * p + t] : 0.0;
+      v[t] = x;
+      v[16 + t] = x * x;
+    }
+    const double x = warp_transpose_sum<double>(v);
+    red[threadIdx.x >> 5][threadIdx.x & 31] = x;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+      const int lane = threadIdx.x;
+      const int qq = (lane < 16) ? 16 * p + lane : NQ + 16 * p + (lane - 16);
+      if (16 * p + (lane & 15) < NQ)
+        part[(int64_t)blockIdx.x * 8 * NN + qq] = tile_tree8(&red[0][0], 32, lane);
     }
     __syncthreads();
   }
@@ -1517,6 +1848,29 @@ struct NStateOps {
   static void observe64(const DevModel* dm, const void* buf, int64_t nt, int n, double* part,
                         cudaStream_t st) {
     k_observeN_f64<NS><<<(unsigned)((nt + 255) / 256), 256, 0, st>>>(dm, buf, nt, n, part);
+  }
+  static void spawn_sample64(const DevModel* dm, const SampleParams& sp, int64_t cap, void* buf,
+                             cudaStream_t st) {
+    const int64_t nb = (sp.n_traj + 127) / 128;
+    k_spawnN_sample<NS><<<(unsigned)(nb > 0 ? nb : 1), 128, 0, st>>>(dm, sp, cap, buf);
+    launches_add(1);
+  }
+  // one spawning step: step kernel, scan, scatter (set step & 1 -> the other)
+  static void spawn_step64(const DevModel* dm, void* buf, int64_t cap, int n, int64_t n0,
+                           int64_t step0, int64_t step, double dt, uint64_t seed,
+                           cudaStream_t st) {
+    const unsigned nb = spawn_grid(cap);
+    k_spawnN_step<NS><<<nb, 256, 0, st>>>(dm, buf, cap, n, n0, step0, step, dt, seed);
+    launch_spawn_scan(buf, cap, n, n0, QCL_PREC_FP64, NS, step0, step, st);
+    k_spawnN_scatter<NS><<<nb, 256, 0, st>>>(buf, cap, n, n0, step0, step, seed);
+    launches_add(2);
+  }
+  static void spawn_observe64(const DevModel* dm, const void* buf, int64_t cap, int n,
+                              int64_t n0, int set, double* part, cudaStream_t st) {
+    launch_spawn_fstart(buf, cap, n, n0, QCL_PREC_FP64, NS, set, st);
+    k_spawnN_observe<NS><<<(unsigned)((n0 + 255) / 256), 256, 0, st>>>(dm, buf, cap, n, n0, set,
+                                                                       part);
+    launches_add(1);
   }
   template <int NPL, int WPT = 1>
   static int bulk_npl(const BulkParams& bp, const CoefN& cf, void* buf, double* part,

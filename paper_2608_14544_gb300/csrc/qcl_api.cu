@@ -849,7 +849,8 @@ namespace {
 qcl_status check_spawn(const qcl_model* m, const qcl_ensemble_desc* e, int64_t capacity) {
   qcl_status st = check_ens(m, e);
   if (st) return st;
-  if (m->ns != 2) return fail(QCL_ERR_UNSUPPORTED, "spawning takes two-state models (n_states = %d)", m->ns);
+  if (m->ns != 2 && e->precision == QCL_PREC_FP32_BULK)
+    return fail(QCL_ERR_UNSUPPORTED, "FP32-bulk spawning takes two-state models (n_states = %d)", m->ns);
   if (e->precision == QCL_PREC_FP32_BULK && m->n > 32)
     return fail(QCL_ERR_UNSUPPORTED, "FP32-bulk spawning takes at most 32 modes (got %d)", m->n);
   if (e->n_traj >= ((int64_t)1 << 31)) return fail(QCL_ERR_INVALID_ARG, "n_traj must be below 2^31 for a spawning ensemble");
@@ -865,17 +866,17 @@ qcl_status qcl_spawn_bytes(const qcl_model* model, const qcl_ensemble_desc* ens,
   if (!bytes) return fail(QCL_ERR_INVALID_ARG, "bytes is NULL");
   qcl_status st = check_spawn(model, ens, capacity);
   if (st) return st;
-  *bytes = SpawnLayout::make(capacity, model->n, ens->n_traj, ens->precision).total;
+  *bytes = SpawnLayout::make(capacity, model->n, ens->n_traj, ens->precision, model->ns).total;
   return ok();
 }
 
 qcl_status qcl_spawn_layout(const qcl_model* model, const qcl_ensemble_desc* ens, int64_t capacity, int32_t set,
-                            size_t offsets[11]) {
+                            size_t offsets[12]) {
   if (!offsets) return fail(QCL_ERR_INVALID_ARG, "offsets is NULL");
   qcl_status st = check_spawn(model, ens, capacity);
   if (st) return st;
   if (set != 0 && set != 1) return fail(QCL_ERR_INVALID_ARG, "set must be 0 or 1");
-  const SpawnLayout L = SpawnLayout::make(capacity, model->n, ens->n_traj, ens->precision);
+  const SpawnLayout L = SpawnLayout::make(capacity, model->n, ens->n_traj, ens->precision, model->ns);
   const size_t b = L.set_off[set];
   const bool f32 = ens->precision == QCL_PREC_FP32_BULK;
   offsets[0] = b + L.R;
@@ -889,6 +890,7 @@ qcl_status qcl_spawn_layout(const qcl_model* model, const qcl_ensemble_desc* ens
   offsets[8] = f32 ? b + L.mlo : 0;
   offsets[9] = f32 ? b + L.mexp : 0;
   offsets[10] = f32 ? b + L.philo : 0;
+  offsets[11] = model->ns > 2 ? b + L.U : 0;
   return ok();
 }
 
@@ -898,12 +900,14 @@ qcl_status qcl_spawn_sample(const qcl_model* model, const qcl_ensemble_desc* ens
   if (st) return st;
   if (!buf) return fail(QCL_ERR_INVALID_ARG, "buf is NULL");
   if (((uintptr_t)buf & 255) != 0) return fail(QCL_ERR_INVALID_ARG, "buf must be 256-byte aligned");
-  const size_t need = SpawnLayout::make(capacity, model->n, ens->n_traj, ens->precision).total;
+  const size_t need = SpawnLayout::make(capacity, model->n, ens->n_traj, ens->precision, model->ns).total;
   if (bytes < need) return fail(QCL_ERR_OUT_OF_MEMORY, "buf has %zu bytes, needs %zu", bytes, need);
   SampleParams* sp = nullptr;
   st = prepare_sample(model, ens, init, &sp);
   if (st) return st;
-  if (ens->precision == QCL_PREC_FP32_BULK)
+  if (model->ns > 2)
+    launch_spawnN_sample(model->dev, model->ns, *sp, capacity, buf, (cudaStream_t)stream);
+  else if (ens->precision == QCL_PREC_FP32_BULK)
     launch_spawn_sample32(model->host, *sp, capacity, buf, (cudaStream_t)stream);
   else
     launch_spawn_sample(model->dev, *sp, capacity, buf, (cudaStream_t)stream);
@@ -926,7 +930,7 @@ qcl_status qcl_spawn_propagate(const qcl_model* model, const qcl_ensemble_desc* 
   if (n_out < 1) return fail(QCL_ERR_INVALID_ARG, "n_out must be >= 1");
   const int64_t k_last = (step0 + n_steps) / out_stride;
   if (k_last >= n_out) return fail(QCL_ERR_INVALID_ARG, "output row %lld beyond n_out = %lld", (long long)k_last, (long long)n_out);
-  const SpawnLayout SL = SpawnLayout::make(capacity, model->n, ens->n_traj, ens->precision);
+  const SpawnLayout SL = SpawnLayout::make(capacity, model->n, ens->n_traj, ens->precision, model->ns);
   if (bytes < SL.total) return fail(QCL_ERR_OUT_OF_MEMORY, "buf has %zu bytes, needs %zu", bytes, SL.total);
   // tiles of 256 families in either precision (FP32 spawning takes <= 32 modes)
   const ObsLayout OL = ObsLayout::make(ens->n_traj, model->ns, n_out, tile_walkers(ens->precision, model->n, model->ns));
@@ -955,6 +959,8 @@ qcl_status qcl_spawn_propagate(const qcl_model* model, const qcl_ensemble_desc* 
   auto observe = [&](double* row, int64_t step) {
     if (f32)
       launch_spawn_observe32(bp, *cf, buf, capacity, n0, (int)(step & 1), part, s);
+    else if (model->ns > 2)
+      launch_spawnN_observe(model->dev, model->ns, buf, capacity, model->n, n0, (int)(step & 1), part, s);
     else
       launch_spawn_observe(model->dev, buf, capacity, model->n, n0, (int)(step & 1), part, s);
     launch_fold(part, row, fold, OL.n_tiles, q2, 1, s);
@@ -965,6 +971,8 @@ qcl_status qcl_spawn_propagate(const qcl_model* model, const qcl_ensemble_desc* 
       TimedLaunch tl(1, s);
       if (f32)
         launch_spawn_step32(bp, *cf, buf, capacity, n0, step0, t, s);
+      else if (model->ns > 2)
+        launch_spawnN_step(model->dev, model->ns, buf, capacity, model->n, n0, step0, t, dt, ens->seed, s);
       else
         launch_spawn_step(model->dev, model->host.repr, buf, capacity, model->n, n0, step0, t, dt, ens->seed, s);
     }

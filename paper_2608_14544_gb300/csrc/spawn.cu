@@ -141,9 +141,10 @@ __global__ void __launch_bounds__(256) k_spawn_step(const DevModel* __restrict__
 // threads, each over a contiguous run of blocks), the destination set's live
 // count, and the overflow test.
 __global__ void __launch_bounds__(1024) k_spawn_scan(void* buf, int64_t cap, int n, int64_t n0,
-                                                     int prec, int64_t step0, int64_t step) {
+                                                     int prec, int ns, int64_t step0,
+                                                     int64_t step) {
   __shared__ int64_t wsum[32];
-  const SpawnLayout L = SpawnLayout::make(cap, n, n0, prec);
+  const SpawnLayout L = SpawnLayout::make(cap, n, n0, prec, ns);
   EnsHeader* hdr = (EnsHeader*)buf;
   SpawnHeader* sh = spawn_header(buf);
   if (hdr->step != step0) return;
@@ -254,8 +255,8 @@ __global__ void __launch_bounds__(256) k_spawn_scatter(void* buf, int64_t cap, i
 // Family start indices of set `set`: fstart[k] = index of family k's first
 // walker, fstart[n0] = the live count.
 __global__ void __launch_bounds__(256) k_spawn_fstart(const void* buf, int64_t cap, int n,
-                                                      int64_t n0, int prec, int set) {
-  const SpawnLayout L = SpawnLayout::make(cap, n, n0, prec);
+                                                      int64_t n0, int prec, int ns, int set) {
+  const SpawnLayout L = SpawnLayout::make(cap, n, n0, prec, ns);
   const int64_t n_live = spawn_header((void*)buf)->n_live[set];
   const uint32_t* fam = (const uint32_t*)((const char*)buf + L.set_off[set] + L.fam);
   int64_t* fstart = (int64_t*)((char*)buf + L.fstart);
@@ -339,7 +340,7 @@ void launch_spawn_step(const DevModel* dm, int repr, void* buf, int64_t capacity
   else
     QCL_SPAWN_STEP(0);
 #undef QCL_SPAWN_STEP
-  k_spawn_scan<<<1, 1024, 0, st>>>(buf, capacity, n, n0, QCL_PREC_FP64, step0, step);
+  k_spawn_scan<<<1, 1024, 0, st>>>(buf, capacity, n, n0, QCL_PREC_FP64, 2, step0, step);
   k_spawn_scatter<<<nb, 256, 0, st>>>(buf, capacity, n, n0, step0, step, seed);
   launches_add(3);
 }
@@ -347,20 +348,20 @@ void launch_spawn_step(const DevModel* dm, int repr, void* buf, int64_t capacity
 void launch_spawn_observe(const DevModel* dm, const void* buf, int64_t capacity, int n, int64_t n0,
                           int set, double* part, cudaStream_t st) {
   const unsigned nf = (unsigned)((n0 + 255) / 256);
-  k_spawn_fstart<<<spawn_grid(capacity), 256, 0, st>>>(buf, capacity, n, n0, QCL_PREC_FP64, set);
+  k_spawn_fstart<<<spawn_grid(capacity), 256, 0, st>>>(buf, capacity, n, n0, QCL_PREC_FP64, 2, set);
   k_spawn_observe<<<nf, 256, 0, st>>>(dm, buf, capacity, n, n0, set, part);
   launches_add(2);
 }
 
-void launch_spawn_scan(void* buf, int64_t capacity, int n, int64_t n0, int precision, int64_t step0,
-                       int64_t step, cudaStream_t st) {
-  k_spawn_scan<<<1, 1024, 0, st>>>(buf, capacity, n, n0, precision, step0, step);
+void launch_spawn_scan(void* buf, int64_t capacity, int n, int64_t n0, int precision, int ns,
+                       int64_t step0, int64_t step, cudaStream_t st) {
+  k_spawn_scan<<<1, 1024, 0, st>>>(buf, capacity, n, n0, precision, ns, step0, step);
   launches_add(1);
 }
 
-void launch_spawn_fstart(const void* buf, int64_t capacity, int n, int64_t n0, int precision, int set,
-                         cudaStream_t st) {
-  k_spawn_fstart<<<spawn_grid(capacity), 256, 0, st>>>(buf, capacity, n, n0, precision, set);
+void launch_spawn_fstart(const void* buf, int64_t capacity, int n, int64_t n0, int precision, int ns,
+                         int set, cudaStream_t st) {
+  k_spawn_fstart<<<spawn_grid(capacity), 256, 0, st>>>(buf, capacity, n, n0, precision, ns, set);
   launches_add(1);
 }
 

@@ -403,7 +403,7 @@ int launch_spawn_step32(const BulkParams& bp, const Coef2& cf, void* buf, int64_
                      : (bp.kind == 0 ? dispatch_step32<0, false>(bp, cf, buf, capacity, n0, step, st)
                                      : dispatch_step32<1, false>(bp, cf, buf, capacity, n0, step, st));
   if (!ok) return 0;
-  launch_spawn_scan(buf, capacity, bp.n, n0, QCL_PREC_FP32_BULK, step0, step, st);
+  launch_spawn_scan(buf, capacity, bp.n, n0, QCL_PREC_FP32_BULK, 2, step0, step, st);
   k_spawn_scatter32<<<spawn_grid(capacity), 256, 0, st>>>(buf, capacity, bp.n, n0, step0, step, bp.seed);
   launches_add(2);
   return 1;
@@ -411,7 +411,7 @@ int launch_spawn_step32(const BulkParams& bp, const Coef2& cf, void* buf, int64_
 
 void launch_spawn_observe32(const BulkParams& bp, const Coef2& cf, const void* buf, int64_t capacity,
                             int64_t n0, int set, double* part, cudaStream_t st) {
-  launch_spawn_fstart(buf, capacity, bp.n, n0, QCL_PREC_FP32_BULK, set, st);
+  launch_spawn_fstart(buf, capacity, bp.n, n0, QCL_PREC_FP32_BULK, 2, set, st);
   const unsigned nf = (unsigned)((n0 + 255) / 256);
   const bool dia = bp.repr == QCL_REPR_DIABATIC;
   if (dia)

@@ -577,7 +577,7 @@ class SpawnRun:
 
         torch.cuda.synchronize()
         nl, n, cap = self.n_live(), self.model.n, self.capacity
-        off = (C.c_size_t * 11)()
+        off = (C.c_size_t * 12)()
         _check(load().qcl_spawn_layout(self.model.handle, C.byref(self.ens), cap, self.step & 1,
                                        off), "qcl_spawn_layout")
         raw = self.buf.cpu().numpy()
@@ -598,6 +598,10 @@ class SpawnRun:
             out["m_lo"] = arr(off[8], nl, np.float32, 4)
             out["m_exp"] = arr(off[9], nl, np.int32, 4)
             out["phi_lo"] = arr(off[10], nl, np.float32, 4)
+        ns = self.model.ns
+        if ns > 2:
+            out["U"] = arr(off[11], ns * ns * cap, dt, w).reshape(ns, ns, cap)[:, :, :nl]
+            out["U"] = out["U"].transpose(2, 0, 1).copy()
         return out
 
 
