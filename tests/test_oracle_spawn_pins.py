@@ -142,3 +142,26 @@ def test_observation_sums_families_before_squaring():
     assert np.allclose(row[nq:], (X ** 2).sum(axis=0), rtol=1e-12, atol=1e-12)
     # the grouping matters: per-walker squares differ from family squares
     assert not np.allclose(row[nq:], (qw ** 2).sum(axis=0), rtol=1e-3)
+
+
+def test_three_state_diabatic_spawn_ensemble_matches_branch_enumeration():
+    """Spawning for three states (four events per step besides the stay, each
+    child with its event's quarter turns): the family-summed mean against the
+    exact enumeration of every branch."""
+    E = np.diag([0.0, 0.3, 0.7]) + 0.1 * (np.ones((3, 3)) - np.eye(3))
+    K = np.zeros((2, 3, 3))
+    K[0] = np.array([[0.4, 0.2, 0.0], [0.2, -0.3, 0.15], [0.0, 0.15, 0.1]])
+    K[1] = np.array([[-0.2, 0.05, 0.25], [0.05, 0.3, -0.1], [0.25, -0.1, 0.0]])
+    model = wl._model(E, K, np.ones(2), np.array([1.0, 1.3]), name="lvc3-spawn-pin")
+    model["repr"] = "diabatic"
+    om = O.OracleModel(model)
+    R0, P0 = np.array([0.3, -0.5]), np.array([1.2, 0.8])
+    rho = np.array([[0.6, 0.2, 0.0], [0.2, 0.3, 0.1], [0.0, 0.1, 0.1]])
+    dt, k, n0 = 0.1, 4, 200_000
+    exact = _enumerate_dia(om, model, R0, P0, rho, dt, k)
+    rows, n_live = O.run_spawn(om, O.OracleInit(om, _point_init(R0, P0, rho)), 31, 0, n0,
+                               8 * n0, dt, k, 1)
+    mean, se = O.finalize(rows, n0)
+    z = np.abs(mean - exact) / np.maximum(se, 1e-15)
+    assert np.all((z < 4.5) | (np.abs(mean - exact) < 1e-12)), z.max()
+    assert n_live[-1] > n0 * 1.05
