@@ -133,13 +133,16 @@ def _result_summary(obs, cfg, status_flags):
     grow like exp(2 int |P d/M| dt), so the standard error grows with time; the
     horizon is the last output time at which SE(P_ad) < 0.01."""
     t = np.arange(obs.shape[0]) * cfg["out_stride"] * cfg["dt"]
-    p_ad, se_p = obs[:, 14], obs[:, 16 + 14]
+    ns = int(cfg["model"]["n_states"])
+    nq, top = 4 * ns * ns, ns - 1
+    ip = 2 * ns * ns + 2 * (top * ns + top)  # the top adiabatic population
+    p_ad, se_p = obs[:, ip], obs[:, nq + ip]
     ok = np.where(se_p < 0.01)[0]
     k = int(ok[-1]) if len(ok) else 0
     return {"horizon_t_se_below_0.01": float(t[k]), "P_ad_upper_at_horizon": float(p_ad[k]),
             "se_at_horizon": float(se_p[k]),
-            "rho11_minus_rho22_at_horizon": float(obs[k, 0] - obs[k, 6]),
-            "trace_at_horizon": float(obs[k, 32]), "se_P_ad_t_end": float(se_p[-1]),
+            "rho11_minus_rho22_at_horizon": float(obs[k, 0] - obs[k, 2 * (ns + 1)]),
+            "trace_at_horizon": float(obs[k, 2 * nq]), "se_P_ad_t_end": float(se_p[-1]),
             "status_flags": status_flags}
 
 
@@ -331,11 +334,13 @@ def served_mix_leg(qcl, reqs, arena_gb: float, quantum: int, paced: bool, peak_t
             "errors": int(errors + st["n_error"]), "quantum_steps": quantum}
 
 
-def config_leg(qcl, torch, cfg, n_traj: int, stream, peak_tflops: float, probe_steps=None):
+def config_leg(qcl, torch, cfg, n_traj: int, stream, peak_tflops: float, probe_steps=None,
+               counted: bool = True):
     """One full-size solve of a configuration through the single-solve entry
     points (sample + propagate + device reduction), after a short warm-up run
     of the same kernels: walker-steps/s, and the dominant kernel's algorithmic
-    FP32 flops against the FP32 peak."""
+    FP32 flops against the FP32 peak (counted = False: no per-unit flop figure
+    applies, the rate alone)."""
     stride, dt, steps = cfg["out_stride"], cfg["dt"], cfg["n_steps"]
     m = qcl.Model(cfg["model"])
     shape = m.autotune(dt, stride, probe_walkers=1 << 20,
@@ -358,8 +363,8 @@ def config_leg(qcl, torch, cfg, n_traj: int, stream, peak_tflops: float, probe_s
     ms = _event_ms(torch, solve, stream)
     qcl.set_option(qcl.OPT_TIMING, 0)
     k_ms, k_n = qcl.kernel_time(qcl.KERNEL_BULK)
-    fl = flops_per_traj_step(cfg["model"])
-    ach = float(n_traj) * steps * fl / (k_ms / 1e3) / 1e12 if k_ms > 0 else None
+    fl = flops_per_traj_step(cfg["model"]) if counted else None
+    ach = float(n_traj) * steps * fl / (k_ms / 1e3) / 1e12 if (k_ms > 0 and fl) else None
     flags = run.status()["flags"]
     obs = dev.cpu().numpy()
     del run
@@ -634,6 +639,17 @@ def run_ours(args):
     cd["model"]["repr"] = "diabatic"
     legs["diabatic"] = dict(config_leg(qcl, torch, cd, n, stream, peak_tflops),
                             workload="the benchmark solve in the diabatic representation")
+    if args.nstate_walkers > 0:
+        c4 = wl.lvc4_config(1)
+        legs["lvc4"] = dict(config_leg(qcl, torch, c4, args.nstate_walkers, stream, peak_tflops),
+                            workload="random four-state six-mode LVC model (the served mix's "
+                                     "four-state kind), 1000 steps, outputs every 10")
+        c4d = copy.deepcopy(c4)
+        c4d["model"]["repr"] = "diabatic"
+        legs["lvc4_diabatic"] = dict(
+            config_leg(qcl, torch, c4d, args.nstate_walkers, stream, peak_tflops, counted=False),
+            workload="the same model in the diabatic representation (no decomposition in the "
+                     "step; no per-unit flop figure in the scope)")
     if args.spawn_walkers > 0:
         legs["spawning"] = spawning_leg(qcl, torch, wl.config(1), args.spawn_walkers, 400, 20)
         # (horizon, initial spawning walkers, slots per initial walker): the
@@ -736,6 +752,8 @@ def main():
     ap.add_argument("--served-traj-max", type=float, default=1e7)
     ap.add_argument("--served-arena-gb", type=float, default=128.0)
     ap.add_argument("--served-quantum", type=int, default=400)
+    ap.add_argument("--nstate-walkers", type=int, default=4_000_000,
+                    help="walkers of the four-state legs (0: skip)")
     ap.add_argument("--served-round-flops", type=float, default=2e12,
                     help="round work budget of the shortest-first served-mix legs")
     args = ap.parse_args()
