@@ -102,10 +102,10 @@ typedef struct {
  *   unit is carried as a per-walker count of quarter turns (weight
  *   m exp(-i phi) i^q).  Any N_s; the FP32-bulk precision takes the modes of
  *   the adiabatic representation (at most 32 for N_s <= 4, else 8).
- *   Trajectory spawning takes two-state models.  The observables keep their
- *   layout: diabatic rho_ij (the walkers' own pairs) and adiabatic rho_ab
- *   (rotated at the walker's R by its eigenvectors, each with its
- *   largest-magnitude component positive). */
+ *   Trajectory spawning takes any N_s in FP64, two states in FP32 bulk.  The
+ *   observables keep their layout: diabatic rho_ij (the walkers' own pairs)
+ *   and adiabatic rho_ab (rotated at the walker's R by its eigenvectors, each
+ *   with its largest-magnitude component positive). */
 #define QCL_REPR_ADIABATIC 0
 #define QCL_REPR_DIABATIC 1
 

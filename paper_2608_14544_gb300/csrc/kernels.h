@@ -194,7 +194,7 @@ constexpr int kPackedBuckets = 6;
 int launch_packed(int bucket, int kind, const PackedTable* dtab, cudaStream_t st);
 
 // ------------------------------------------------------------- spawning --
-// Buffer of a spawning ensemble (FP64, two states): the common header (its
+// Buffer of a spawning ensemble (any precision and N_s): the common header (its
 // n_traj = the n0 initial walkers = families) with SpawnHeader after it, then
 // two walker sets of `capacity` slots (the current set alternates with the
 // absolute step: set = step & 1), per-parent staging of the children of a
