@@ -212,9 +212,10 @@ struct SpawnLayout {
   // walker set: R[n][cap], P[n][cap], m, phi, ab (uint16), id (uint64),
   // fam (uint32); FP32 sets add m_lo, m_exp (int32) and phi_lo (compensated
   // pairs with a carried exponent, as in the bulk kernels); sets of N_s > 2
-  // states (FP64) add the carried eigenvectors U[ns * ns][cap]
+  // states add the carried eigenvectors U[ns * ns][cap] and, in FP32, the
+  // eigenvalues E[ns][cap] (the warm start of the next decomposition)
   size_t set_off[2];
-  size_t R, P, m, mlo, mexp, phi, philo, ab, id, fam, U, set_bytes;
+  size_t R, P, m, mlo, mexp, phi, philo, ab, id, fam, U, E, set_bytes;
   // staging of a step's children, per parent: weight (FP32: hi, lo, exp), pair
   size_t cm, cmlo, cmexp, cab, flag, bsum, boff, fstart, total;
   int64_t n_blocks;  // capacity / 256, rounded up
@@ -247,6 +248,8 @@ struct SpawnLayout {
     o = align256(o + 4 * c);
     L.U = o;
     if (ns > 2) o = align256(o + w * c * (size_t)(ns * ns));
+    L.E = o;
+    if (ns > 2 && f32) o = align256(o + 4 * c * (size_t)ns);
     L.set_bytes = o;
     L.set_off[0] = 256;
     L.set_off[1] = 256 + L.set_bytes;
@@ -299,6 +302,16 @@ void launch_spawnN_step(const DevModel* dm, int ns, void* buf, int64_t capacity,
                         int64_t step0, int64_t step, double dt, uint64_t seed, cudaStream_t st);
 void launch_spawnN_observe(const DevModel* dm, int ns, const void* buf, int64_t capacity, int n,
                            int64_t n0, int set, double* part, cudaStream_t st);
+// FP32-bulk spawning for N_s = 3..8 states (either representation, n <= 8
+// modes): sample, one step (0 if no kernel for n), observation.
+void launch_spawnN_sample32(int ns, const SampleN32& sp, int64_t capacity, void* buf,
+                            cudaStream_t st);
+int launch_spawnN_step32(int ns, const BulkParams& bp, const CoefN& cf, void* buf,
+                         int64_t capacity, int64_t n0, int64_t step0, int64_t step,
+                         cudaStream_t st);
+void launch_spawnN_observe32(int ns, const BulkParams& bp, const CoefN& cf, const void* buf,
+                             int64_t capacity, int64_t n0, int set, double* part,
+                             cudaStream_t st);
 // FP32-bulk spawning (two states, n <= 32 modes): sample, one step (step
 // kernel, scan, scatter), family observation.
 void launch_spawn_sample32(const DevModel& host, const SampleParams& sp, int64_t capacity, void* buf,

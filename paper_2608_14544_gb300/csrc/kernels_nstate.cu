@@ -16,7 +16,12 @@ namespace qcl {
   void nstate_spawn_step64_##k(const DevModel*, void*, int64_t, int, int64_t, int64_t, int64_t, \
                                double, uint64_t, cudaStream_t);                               \
   void nstate_spawn_observe64_##k(const DevModel*, const void*, int64_t, int, int64_t, int,   \
-                                  double*, cudaStream_t);
+                                  double*, cudaStream_t);                                     \
+  void nstate_spawn_sample32_##k(const SampleN32&, int64_t, void*, cudaStream_t);            \
+  int nstate_spawn_step32_##k(const BulkParams&, const CoefN&, void*, int64_t, int64_t,       \
+                              int64_t, int64_t, cudaStream_t);                                \
+  void nstate_spawn_observe32_##k(const BulkParams&, const CoefN&, const void*, int64_t,      \
+                                  int64_t, int, double*, cudaStream_t);
 QCL_NS_DECL(3)
 QCL_NS_DECL(4)
 QCL_NS_DECL(5)
@@ -71,6 +76,31 @@ void launch_spawnN_step(const DevModel* dm, int ns, void* buf, int64_t capacity,
 void launch_spawnN_observe(const DevModel* dm, int ns, const void* buf, int64_t capacity, int n,
                            int64_t n0, int set, double* part, cudaStream_t st) {
   QCL_NS_SWITCH(ns, nstate_spawn_observe64, dm, buf, capacity, n, n0, set, part, st);
+}
+
+void launch_spawnN_sample32(int ns, const SampleN32& sp, int64_t capacity, void* buf,
+                            cudaStream_t st) {
+  QCL_NS_SWITCH(ns, nstate_spawn_sample32, sp, capacity, buf, st);
+}
+
+int launch_spawnN_step32(int ns, const BulkParams& bp, const CoefN& cf, void* buf,
+                         int64_t capacity, int64_t n0, int64_t step0, int64_t step,
+                         cudaStream_t st) {
+  switch (ns) {
+    case 3: return nstate_spawn_step32_3(bp, cf, buf, capacity, n0, step0, step, st);
+    case 4: return nstate_spawn_step32_4(bp, cf, buf, capacity, n0, step0, step, st);
+    case 5: return nstate_spawn_step32_5(bp, cf, buf, capacity, n0, step0, step, st);
+    case 6: return nstate_spawn_step32_6(bp, cf, buf, capacity, n0, step0, step, st);
+    case 7: return nstate_spawn_step32_7(bp, cf, buf, capacity, n0, step0, step, st);
+    case 8: return nstate_spawn_step32_8(bp, cf, buf, capacity, n0, step0, step, st);
+    default: return 0;
+  }
+}
+
+void launch_spawnN_observe32(int ns, const BulkParams& bp, const CoefN& cf, const void* buf,
+                             int64_t capacity, int64_t n0, int set, double* part,
+                             cudaStream_t st) {
+  QCL_NS_SWITCH(ns, nstate_spawn_observe32, bp, cf, buf, capacity, n0, set, part, st);
 }
 
 int launch_bulkN(int ns, const BulkParams& bp, const CoefN& cf, void* buf, double* part,

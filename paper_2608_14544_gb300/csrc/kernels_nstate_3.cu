@@ -14,4 +14,15 @@ int nstate_bulk_3(const BulkParams& bp, const CoefN& cf, void* buf, double* part
                   int wpt, cudaStream_t st) {
   return NStateOps<3>::bulk(bp, cf, buf, part, grid_cap, wpt, st);
 }
+void nstate_spawn_sample32_3(const SampleN32& sp, int64_t cap, void* buf, cudaStream_t st) {
+  NStateOps<3>::spawn_sample32(sp, cap, buf, st);
+}
+int nstate_spawn_step32_3(const BulkParams& bp, const CoefN& cf, void* buf, int64_t cap,
+                          int64_t n0, int64_t step0, int64_t step, cudaStream_t st) {
+  return NStateOps<3>::spawn_step32(bp, cf, buf, cap, n0, step0, step, st);
+}
+void nstate_spawn_observe32_3(const BulkParams& bp, const CoefN& cf, const void* buf, int64_t cap,
+                              int64_t n0, int set, double* part, cudaStream_t st) {
+  NStateOps<3>::spawn_observe32(bp, cf, buf, cap, n0, set, part, st);
+}
 }  // namespace qcl

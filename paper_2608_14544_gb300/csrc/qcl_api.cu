@@ -334,6 +334,23 @@ void fill_coef2(const qcl_model* model, double dt, Coef2* cf) {
 
 // FP32 copies of an N_s-state model's E, K and the sampling inputs (the FP32-bulk
 // mode limits keep n N_s^2 within kSampleNK).
+// FP32 per-mode coefficients of an N_s-state model for one time step dt
+// (upper triangles of E and of each K_j).
+void fill_coefN(const qcl_model* model, double dt, CoefN& cn) {
+  const DevModel& h = model->host;
+  const int ns = model->ns;
+  auto tri = [ns](int a, int b) { return a * ns - a * (a - 1) / 2 + (b - a); };
+  for (int a = 0; a < ns; ++a)
+    for (int b = a; b < ns; ++b) cn.E[tri(a, b)] = (float)model->E[a * ns + b];
+  for (int j = 0; j < model->n; ++j) {
+    cn.hk[j] = (float)(0.5 * dt * h.k[j]);
+    cn.dtm[j] = (float)(dt / h.mass[j]);
+    cn.minv[j] = (float)(1.0 / h.mass[j]);
+    for (int a = 0; a < ns; ++a)
+      for (int b = a; b < ns; ++b) cn.K[j][tri(a, b)] = (float)model->K[(size_t)j * ns * ns + a * ns + b];
+  }
+}
+
 void make_sampleN32(const qcl_model* model, const SampleParams& sp, SampleN32& s) {
   const int ns = model->ns, n = model->n;
   s.n_traj = sp.n_traj;
@@ -506,17 +523,7 @@ qcl_status qcl_propagate(const qcl_model* model, const qcl_ensemble_desc* ens, v
         delete cf;
         return fail(QCL_ERR_OUT_OF_MEMORY, "host allocation failed");
       }
-      const int ns = model->ns;
-      auto tri = [ns](int a, int b) { return a * ns - a * (a - 1) / 2 + (b - a); };
-      for (int a = 0; a < ns; ++a)
-        for (int b = a; b < ns; ++b) cn->E[tri(a, b)] = (float)model->E[a * ns + b];
-      for (int j = 0; j < model->n; ++j) {
-        cn->hk[j] = (float)(0.5 * dt * h.k[j]);
-        cn->dtm[j] = (float)(dt / h.mass[j]);
-        cn->minv[j] = (float)(1.0 / h.mass[j]);
-        for (int a = 0; a < ns; ++a)
-          for (int b = a; b < ns; ++b) cn->K[j][tri(a, b)] = (float)model->K[(size_t)j * ns * ns + a * ns + b];
-      }
+      fill_coefN(model, dt, *cn);
     }
     // chunks of at most outs (the launch shape's outputs per launch) output times
     const int outs = model->shape_outs > 0 ? model->shape_outs : kChunkOut;
@@ -849,8 +856,8 @@ namespace {
 qcl_status check_spawn(const qcl_model* m, const qcl_ensemble_desc* e, int64_t capacity) {
   qcl_status st = check_ens(m, e);
   if (st) return st;
-  if (m->ns != 2 && e->precision == QCL_PREC_FP32_BULK)
-    return fail(QCL_ERR_UNSUPPORTED, "FP32-bulk spawning takes two-state models (n_states = %d)", m->ns);
+  if (m->ns != 2 && e->precision == QCL_PREC_FP32_BULK && m->n > 8)
+    return fail(QCL_ERR_UNSUPPORTED, "FP32-bulk spawning of %d-state models takes at most 8 modes (got %d)", m->ns, m->n);
   if (e->precision == QCL_PREC_FP32_BULK && m->n > 32)
     return fail(QCL_ERR_UNSUPPORTED, "FP32-bulk spawning takes at most 32 modes (got %d)", m->n);
   if (e->n_traj >= ((int64_t)1 << 31)) return fail(QCL_ERR_INVALID_ARG, "n_traj must be below 2^31 for a spawning ensemble");
@@ -905,7 +912,16 @@ qcl_status qcl_spawn_sample(const qcl_model* model, const qcl_ensemble_desc* ens
   SampleParams* sp = nullptr;
   st = prepare_sample(model, ens, init, &sp);
   if (st) return st;
-  if (model->ns > 2)
+  if (model->ns > 2 && ens->precision == QCL_PREC_FP32_BULK) {
+    SampleN32* s32 = new (std::nothrow) SampleN32();
+    if (!s32) {
+      delete sp;
+      return fail(QCL_ERR_OUT_OF_MEMORY, "host allocation failed");
+    }
+    make_sampleN32(model, *sp, *s32);
+    launch_spawnN_sample32(model->ns, *s32, capacity, buf, (cudaStream_t)stream);
+    delete s32;
+  } else if (model->ns > 2)
     launch_spawnN_sample(model->dev, model->ns, *sp, capacity, buf, (cudaStream_t)stream);
   else if (ens->precision == QCL_PREC_FP32_BULK)
     launch_spawn_sample32(model->host, *sp, capacity, buf, (cudaStream_t)stream);
@@ -932,7 +948,8 @@ qcl_status qcl_spawn_propagate(const qcl_model* model, const qcl_ensemble_desc* 
   if (k_last >= n_out) return fail(QCL_ERR_INVALID_ARG, "output row %lld beyond n_out = %lld", (long long)k_last, (long long)n_out);
   const SpawnLayout SL = SpawnLayout::make(capacity, model->n, ens->n_traj, ens->precision, model->ns);
   if (bytes < SL.total) return fail(QCL_ERR_OUT_OF_MEMORY, "buf has %zu bytes, needs %zu", bytes, SL.total);
-  // tiles of 256 families in either precision (FP32 spawning takes <= 32 modes)
+  // tiles of families as the ensemble's own tiles: 256 (two states, <= 32 modes in
+  // FP32), 128 for FP32 N_s-state models
   const ObsLayout OL = ObsLayout::make(ens->n_traj, model->ns, n_out, tile_walkers(ens->precision, model->n, model->ns));
   if (obs_bytes < OL.total) return fail(QCL_ERR_OUT_OF_MEMORY, "obs_buf has %zu bytes, needs %zu", obs_bytes, OL.total);
   cudaStream_t s = (cudaStream_t)stream;
@@ -943,12 +960,20 @@ qcl_status qcl_spawn_propagate(const qcl_model* model, const qcl_ensemble_desc* 
   const int q2 = OL.q2;
   const int64_t n0 = ens->n_traj;
   const bool f32 = ens->precision == QCL_PREC_FP32_BULK;
+  const bool f32n = f32 && model->ns > 2;
   Coef2* cf = nullptr;
+  CoefN* cn = nullptr;
   BulkParams bp{};
   if (f32) {
     cf = new (std::nothrow) Coef2();
-    if (!cf) return fail(QCL_ERR_OUT_OF_MEMORY, "host allocation failed");
+    if (f32n) cn = new (std::nothrow) CoefN();
+    if (!cf || (f32n && !cn)) {
+      delete cf;
+      delete cn;
+      return fail(QCL_ERR_OUT_OF_MEMORY, "host allocation failed");
+    }
     fill_coef2(model, dt, cf);
+    if (f32n) fill_coefN(model, dt, *cn);
     bp.n_traj = n0;
     bp.seed = ens->seed;
     bp.step0 = step0;
@@ -957,7 +982,9 @@ qcl_status qcl_spawn_propagate(const qcl_model* model, const qcl_ensemble_desc* 
     bulk_model_scalars(bp, model->host, dt);
   }
   auto observe = [&](double* row, int64_t step) {
-    if (f32)
+    if (f32n)
+      launch_spawnN_observe32(model->ns, bp, *cn, buf, capacity, n0, (int)(step & 1), part, s);
+    else if (f32)
       launch_spawn_observe32(bp, *cf, buf, capacity, n0, (int)(step & 1), part, s);
     else if (model->ns > 2)
       launch_spawnN_observe(model->dev, model->ns, buf, capacity, model->n, n0, (int)(step & 1), part, s);
@@ -969,7 +996,9 @@ qcl_status qcl_spawn_propagate(const qcl_model* model, const qcl_ensemble_desc* 
   for (int64_t t = step0; t < step0 + n_steps; ++t) {
     {
       TimedLaunch tl(1, s);
-      if (f32)
+      if (f32n)
+        launch_spawnN_step32(model->ns, bp, *cn, buf, capacity, n0, step0, t, s);
+      else if (f32)
         launch_spawn_step32(bp, *cf, buf, capacity, n0, step0, t, s);
       else if (model->ns > 2)
         launch_spawnN_step(model->dev, model->ns, buf, capacity, model->n, n0, step0, t, dt, ens->seed, s);
@@ -979,6 +1008,7 @@ qcl_status qcl_spawn_propagate(const qcl_model* model, const qcl_ensemble_desc* 
     if ((t + 1) % out_stride == 0) observe(rows + (size_t)((t + 1) / out_stride) * q2, t + 1);
   }
   delete cf;
+  delete cn;
   st = check_launch("spawn step");
   if (st) return st;
   launch_header_finish(buf, step0, step0 + n_steps, s);

@@ -148,8 +148,63 @@ def test_spawn_nstate_overflow_sets_flag(q):
     assert run2.status()["flags"] & q.FLAG_SPAWN_OVERFLOW == 0
 
 
-def test_fp32_spawn_rejects_more_than_two_states(q):
-    model, init, dt = _case("adiabatic")
+@pytest.mark.parametrize("rep", ["adiabatic", "diabatic"])
+def test_fp32_spawn_nstate_observables_match_oracle(q, rep):
+    """FP32 bulk spawning (one step per launch, the FP32 N_s-state walker
+    arithmetic) against the oracle's FP64 spawning on the same walkers: the
+    family means within the combined standard error, and walker lists of
+    nearly the same length (FP32 decides differently only on rare
+    near-threshold words)."""
+    model, init, dt = _case(rep)
+    n0, steps, stride = 3000, 120, 10
+    cap = 60 * n0
     m = q.Model(model)
-    with pytest.raises(q.QclError, match="two-state"):
-        q.SpawnRun(m, 100, 1000, 1, 2, precision=q.PREC_FP32_BULK)
+    run = q.SpawnRun(m, n0, cap, 13, steps // stride + 1, precision=q.PREC_FP32_BULK)
+    run.sample(init)
+    run.propagate(steps, dt, stride)
+    obs = run.observables()
+    assert run.status()["flags"] & (q.FLAG_NONFINITE | q.FLAG_SPAWN_OVERFLOW) == 0
+    om = oracle.OracleModel(model)
+    ref, n_live = oracle.run_spawn(om, oracle.OracleInit(om, init), 13, 0, n0, cap, dt, steps,
+                                   stride)
+    mean, se = oracle.finalize(ref, n0)
+    nq = 4 * model["n_states"] ** 2
+    diff = np.abs(obs[:, :nq] - mean)
+    se2 = np.hypot(se, obs[:, nq:2 * nq])
+    assert np.all(diff <= 3 * se2 + 1e-6), (diff / (se2 + 1e-300)).max()
+    assert abs(run.n_live() - n_live[-1]) <= max(10, 0.01 * n_live[-1]), (run.n_live(), n_live[-1])
+    assert run.n_live() > 1.2 * n0
+    st = run.state()
+    assert np.array_equal(np.unique(st["family"]), np.arange(n0))
+
+
+def test_fp32_spawn_nstate_chunking_is_bitwise_invisible(q):
+    model, init, dt = _case("adiabatic")
+    n0, cap = 2000, 100_000
+    outs = []
+    for split in ((100,), (30, 70), (3, 97)):
+        m = q.Model(model)
+        run = q.SpawnRun(m, n0, cap, 4, 100 // 10 + 1, precision=q.PREC_FP32_BULK)
+        run.sample(init)
+        for k in split:
+            run.propagate(k, dt, 10)
+        outs.append((run.sums(), run.state()))
+    for sums, st in outs[1:]:
+        assert np.array_equal(sums, outs[0][0])
+        for key in st:
+            assert np.array_equal(st[key], outs[0][1][key]), key
+
+
+def test_fp32_spawn_nstate_overflow_and_mode_limit(q):
+    model, init, dt = _case("diabatic")
+    n0 = 300
+    m = q.Model(model)
+    run = q.SpawnRun(m, n0, n0 + 30, 2, 21, precision=q.PREC_FP32_BULK)
+    run.sample(init)
+    run.propagate(200, dt, 10)
+    assert run.status()["flags"] & q.FLAG_SPAWN_OVERFLOW
+    assert n0 <= run.n_live() <= n0 + 30
+    # more than 8 modes: FP64 only
+    big = wl._model(model["E"], np.zeros((10, 3, 3)), np.ones(10), np.ones(10), name="lvc3-10")
+    with pytest.raises(q.QclError, match="at most 8 modes"):
+        q.SpawnRun(q.Model(big), 100, 1000, 1, 2, precision=q.PREC_FP32_BULK)
