@@ -102,7 +102,8 @@ typedef struct {
  *   unit is carried as a per-walker count of quarter turns (weight
  *   m exp(-i phi) i^q).  Any N_s; the FP32-bulk precision takes the modes of
  *   the adiabatic representation (at most 32 for N_s <= 4, else 8).
- *   Trajectory spawning takes any N_s in FP64, two states in FP32 bulk.  The
+ *   Trajectory spawning takes any N_s (FP32 bulk: up to 8 modes beyond two
+ *   states).  The
  *   observables keep their layout: diabatic rho_ij (the walkers' own pairs)
  *   and adiabatic rho_ab (rotated at the walker's R by its eigenvectors, each
  *   with its largest-magnitude component positive). */
@@ -412,7 +413,7 @@ qcl_status qcl_autotune(qcl_model* model, int64_t probe_walkers, int64_t n_steps
 
 /* ---------------------------------------------------------------------------
  * Trajectory spawning (either representation; FP64 for any N_s, or FP32 bulk
- * for two-state models of at most 32 modes).
+ * for two-state models of at most 32 modes and N_s-state models of at most 8).
  *
  * The scheme of the CPU code that the paper's GPU version replaces (Sec. II B:
  * there a new trajectory was started each time a transition test fired, so

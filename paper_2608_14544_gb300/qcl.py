@@ -523,8 +523,8 @@ def measure_peak(which: int, stream=None) -> float:
 # ----------------------------------------------------------------- spawning --
 class SpawnRun:
     """A trajectory-spawning ensemble (FP64 for any number of states, or FP32
-    bulk for two states with at most 32 modes): n0 initial walkers (families)
-    in a buffer of `capacity` walker slots."""
+    bulk for two states with at most 32 modes and more states with at most 8):
+    n0 initial walkers (families) in a buffer of `capacity` walker slots."""
 
     def __init__(self, model: Model, n0: int, capacity: int, seed: int, n_out: int,
                  traj_id_offset: int = 0, device="cuda", precision: int = None):
