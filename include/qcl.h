@@ -103,10 +103,9 @@ typedef struct {
  *   m exp(-i phi) i^q).  Any N_s; the FP32-bulk precision takes the modes of
  *   the adiabatic representation (at most 32 for N_s <= 4, else 8).
  *   Trajectory spawning takes any N_s (FP32 bulk: up to 8 modes beyond two
- *   states).  The
- *   observables keep their layout: diabatic rho_ij (the walkers' own pairs)
- *   and adiabatic rho_ab (rotated at the walker's R by its eigenvectors, each
- *   with its largest-magnitude component positive). */
+ *   states).  The observables keep their layout: diabatic rho_ij (the
+ *   walkers' own pairs) and adiabatic rho_ab (rotated at the walker's R by its
+ *   eigenvectors, each with its largest-magnitude component positive). */
 #define QCL_REPR_ADIABATIC 0
 #define QCL_REPR_DIABATIC 1
 
