@@ -5,32 +5,49 @@
 
 namespace qcl {
 
-// One level of the tile fold: in[row][n][nq] -> out[row][ceil(n/1024)][nq].
-// Grid (ceil(n/1024), nq, rows), 32 threads: lane l reduces 32 consecutive
-// entries by a binary tree, then the warp combines lanes by a butterfly.
-__global__ void k_fold_level(const double* __restrict__ in, double* __restrict__ out, int64_t n,
-                             int nq, int64_t in_row_stride, int64_t out_row_stride) {
+// One level of the tile fold: in[row][n][nq] -> out[row][ceil(n/1024)][nq],
+// each output the perfect binary tree over its 1024 inputs in natural order
+// (zero past n).  Grid (ceil(n/1024), ceil(nq/32), rows), 256 threads: lane c
+// of warp w takes column q0 + c and the tiles [128 w, 128 w + 128) of the
+// block, as four 32-leaf trees in registers (a warp's load is 32 consecutive
+// columns of one tile row, 256 contiguous bytes); the eight warp results are
+// paired in shared memory.  The tree is the same for every launch shape.
+__global__ void __launch_bounds__(256) k_fold_level(const double* __restrict__ in,
+                                                    double* __restrict__ out, int64_t n, int nq,
+                                                    int64_t in_row_stride,
+                                                    int64_t out_row_stride) {
+  __shared__ double c8[8][32];
   const int64_t blk = blockIdx.x;
-  const int q = blockIdx.y;
+  const int q = blockIdx.y * 32 + (threadIdx.x & 31);
+  const int w = threadIdx.x >> 5;
   const int row = blockIdx.z;
-  const int lane = threadIdx.x;
-  const double* src = in + (int64_t)row * in_row_stride;
-  double v[32];
-  const int64_t base = blk * 1024 + (int64_t)lane * 32;
+  const bool col = q < nq;
+  const double* src = in + (int64_t)row * in_row_stride + (col ? q : 0);
+  double g[4];
 #pragma unroll
-  for (int i = 0; i < 32; ++i) {
-    const int64_t t = base + i;
-    v[i] = (t < n) ? src[t * nq + q] : 0.0;
+  for (int k = 0; k < 4; ++k) {
+    const int64_t base = blk * 1024 + (int64_t)(w * 4 + k) * 32;
+    double v[32];
+#pragma unroll
+    for (int i = 0; i < 32; ++i) {
+      const int64_t t = base + i;
+      v[i] = (col && t < n) ? src[t * nq] : 0.0;
+    }
+#pragma unroll
+    for (int s = 1; s < 32; s *= 2) {
+#pragma unroll
+      for (int i = 0; i < 32; i += 2 * s) v[i] += v[i + s];
+    }
+    g[k] = v[0];
   }
-#pragma unroll
-  for (int s = 1; s < 32; s *= 2) {
-#pragma unroll
-    for (int i = 0; i < 32; i += 2 * s) v[i] += v[i + s];
+  c8[w][threadIdx.x & 31] = (g[0] + g[1]) + (g[2] + g[3]);
+  __syncthreads();
+  if (w == 0 && col) {
+    const int c = threadIdx.x;
+    const double x = ((c8[0][c] + c8[1][c]) + (c8[2][c] + c8[3][c])) +
+                     ((c8[4][c] + c8[5][c]) + (c8[6][c] + c8[7][c]));
+    out[(int64_t)row * out_row_stride + blk * nq + q] = x;
   }
-  double x = v[0];
-#pragma unroll
-  for (int off = 1; off < 32; off *= 2) x += __shfl_xor_sync(0xffffffffu, x, off);
-  if (lane == 0) out[(int64_t)row * out_row_stride + blk * nq + q] = x;
 }
 
 // Means and standard errors of rows [k0, k0 + nrows) of sums (divide by N).
@@ -75,8 +92,8 @@ void launch_fold(const double* part, double* rows_out, double* scratch, int64_t 
     double* out = (nb == 1) ? rows_out : ((first && chunk_out) ? chunk_out : bufs[which]);
     first = false;
     const int64_t out_stride = (nb == 1) ? q2 : nb * q2;
-    dim3 grid((unsigned)nb, (unsigned)q2, (unsigned)n_slots);
-    k_fold_level<<<grid, 32, 0, st>>>(in, out, n, q2, in_stride, out_stride);
+    dim3 grid((unsigned)nb, (unsigned)((q2 + 31) / 32), (unsigned)n_slots);
+    k_fold_level<<<grid, 256, 0, st>>>(in, out, n, q2, in_stride, out_stride);
     launches_add(1);
     if (nb == 1) break;
     in = out;
