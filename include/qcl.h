@@ -100,10 +100,9 @@ typedef struct {
  *   V_aa - V_bb, mean force -1/2 (dV_aa/dR + dV_bb/dR), transitions a -> g with
  *   amplitude -i V_ga dt/hbar and b -> g with +i V_bg dt/hbar.  The imaginary
  *   unit is carried as a per-walker count of quarter turns (weight
- *   m exp(-i phi) i^q).  Any N_s; the FP32-bulk precision takes the modes of
- *   the adiabatic representation (at most 32 for N_s <= 4, else 8).
- *   Trajectory spawning takes any N_s (FP32 bulk: up to 8 modes beyond two
- *   states).  The observables keep their layout: diabatic rho_ij (the
+ *   m exp(-i phi) i^q).  Any N_s and mode count (FP32 bulk for two states:
+ *   at most 32 modes).  Trajectory spawning takes either representation.  The
+ *   observables keep their layout: diabatic rho_ij (the
  *   walkers' own pairs) and adiabatic rho_ab (rotated at the walker's R by its
  *   eigenvectors, each with its largest-magnitude component positive). */
 #define QCL_REPR_ADIABATIC 0
@@ -194,8 +193,12 @@ qcl_status qcl_sample_initial(const qcl_model* model, const qcl_ensemble_desc* e
  * order), so that results do not depend on the launch shape and two calls give
  * the same bits as one.  FP64 ensembles launch one kernel per step; FP32-bulk
  * ensembles run a persistent kernel over the tiles with state held in
- * registers (models of 33..256 modes split each walker's modes over 2 or 4
- * warps, so their tiles hold 128 or 64 walkers). */
+ * registers (two-state models of 33..256 modes split each walker's modes over
+ * 2 or 4 warps, so their tiles hold 128 or 64 walkers).  N_s-state models
+ * keep R and P in registers or, with the same arithmetic and results, in the
+ * ensemble buffer, read twice per step (once for the diabatic representation):
+ * beyond the register limit (32 modes for N_s <= 4, 8 beyond) always, below it
+ * where that form measured faster (QCL_OPT_MODES_IN_MEMORY). */
 qcl_status qcl_propagate(const qcl_model* model, const qcl_ensemble_desc* ens, void* ens_buf,
                          size_t ens_bytes, int64_t step0, int64_t n_steps, double dt,
                          int32_t out_stride, void* obs_buf, size_t obs_bytes, int64_t n_out,
@@ -411,8 +414,8 @@ qcl_status qcl_autotune(qcl_model* model, int64_t probe_walkers, int64_t n_steps
                         qcl_launch_shape* best, void* stream);
 
 /* ---------------------------------------------------------------------------
- * Trajectory spawning (either representation; FP64 for any N_s, or FP32 bulk
- * for two-state models of at most 32 modes and N_s-state models of at most 8).
+ * Trajectory spawning (either representation; FP64 for any N_s, FP32 bulk for
+ * any N_s, two-state models of at most 32 modes).
  *
  * The scheme of the CPU code that the paper's GPU version replaces (Sec. II B:
  * there a new trajectory was started each time a transition test fired, so
@@ -577,9 +580,16 @@ qcl_status qcl_server_destroy(qcl_server* s);
  *   QCL_OPT_GRID_CAP  cap on the persistent grid (0: SMs x resident blocks);
  *                     results do not depend on it (fixed reduction tree)
  *   QCL_OPT_TIMING    1: record a CUDA event pair on the launching stream around
- *                     every persistent-kernel and FP64 step-kernel launch */
+ *                     every persistent-kernel and FP64 step-kernel launch
+ *   QCL_OPT_MODES_IN_MEMORY  where the FP32-bulk N_s-state kernels (N_s > 2)
+ *                     keep R and P: 0 (default) the faster form as measured
+ *                     for the model's N_s, mode count and representation; 1 in
+ *                     the ensemble buffer for every mode count; 2 in registers
+ *                     wherever a register form exists (up to 32 modes for
+ *                     N_s <= 4, 8 beyond).  Every choice gives the same bits. */
 #define QCL_OPT_GRID_CAP 1
 #define QCL_OPT_TIMING 2
+#define QCL_OPT_MODES_IN_MEMORY 3
 qcl_status qcl_set_option(int32_t key, int64_t value);
 
 /* Kernel launches made by the library since the last reset; resets the counter

@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 
 #include <cmath>
+#include <cstring>
 
 #include "qcl_common.cuh"
 
@@ -55,8 +56,9 @@ inline void make_sample32(const DevModel& h, const SampleParams& sp, Sample32& s
 }
 
 // The N_s-state FP32 sampler's inputs, converted to FP32 once on the host:
-// E (N_s x N_s), K_j (N_s x N_s each, j < n; n N_s^2 <= kSampleNK, which the
-// FP32-bulk mode limits guarantee) and the initial density.
+// E (N_s x N_s), K_j (N_s x N_s each, j < n, when n N_s^2 <= kSampleNK; larger
+// models are read from the model's FP64 K on the device and rounded to FP32
+// there, the same values) and the initial density.
 constexpr int kSampleNK = 512;
 struct SampleN32 {
   int64_t n_traj;
@@ -67,6 +69,7 @@ struct SampleN32 {
   float E[kMaxNS * kMaxNS];
   float rho[kMaxNS * kMaxNS];
   float K[kSampleNK];
+  const double* Kd;  // the model's K on the device, [n][N_s][N_s]
 };
 
 // FP32 per-mode coefficients of a two-state model for one time step dt.
@@ -111,9 +114,6 @@ struct BulkParams {
   float caa, cab, cbb;
 };
 
-// The model-dependent scalars of a bulk launch for time step dt (every caller
-// fills them here, so the single-request, packed and no-allocation routes see
-// the same values).
 // FP32 degeneracy test of the adiabatic two-state kernels: the coupling is set
 // to zero where r^2 < kDegR2_32 (2r = e_b - e_a below kDegTol32).
 constexpr float kDegTol32 = 1e-6f;
@@ -130,6 +130,9 @@ inline int bulk_kind(const DevModel& h) {
   return b0 * b0 >= kDegR2_32 ? 0 : 1;
 }
 
+// The model-dependent scalars of a bulk launch for time step dt (every caller
+// fills them here, so the single-request, packed and no-allocation routes see
+// the same values).
 inline void bulk_model_scalars(BulkParams& bp, const DevModel& h, double dt) {
   bp.kind = bulk_kind(h);
   bp.repr = h.repr;
@@ -157,15 +160,38 @@ inline void bulk_model_scalars(BulkParams& bp, const DevModel& h, double dt) {
   bp.cbb = (float)cbb;
 }
 
-// FP32 coefficients of an N_s-state model (N_s <= 8, n_modes <= 32): upper
-// triangles (row-major a <= b) of E and of each K_j.
+// FP32 coefficients of an N_s-state model (N_s <= 8): upper triangles
+// (row-major a <= b) of E and of each K_j, the per-mode ones for the first 32
+// modes.  The kernels that keep the modes in memory build their per-mode table
+// on the device from the model (dm) and dt, with the same roundings.
 struct CoefN {
   float hk[32];    // dt/2 * k_j
   float dtm[32];   // dt / M_j
   float minv[32];  // 1 / M_j
   float K[32][36];
   float E[36];
+  // the model on the device and dt, as 32-bit words (the struct keeps 4-byte
+  // alignment, so the kernels' parameter layout stays as it was)
+  uint32_t dm_w[2];
+  uint32_t dt_w[2];
+  int32_t modes_in_memory;  // 0: measured choice, 1: modes in memory, 2: in registers where a form exists
+  int32_t pad;
 };
+inline void coef_set_model(CoefN& c, const DevModel* dm, double dt) {
+  uint64_t a, d;
+  std::memcpy(&a, &dm, sizeof a);
+  std::memcpy(&d, &dt, sizeof d);
+  c.dm_w[0] = (uint32_t)a;
+  c.dm_w[1] = (uint32_t)(a >> 32);
+  c.dt_w[0] = (uint32_t)d;
+  c.dt_w[1] = (uint32_t)(d >> 32);
+}
+__device__ __forceinline__ const DevModel* coef_dm(const CoefN& c) {
+  return reinterpret_cast<const DevModel*>(((uint64_t)c.dm_w[1] << 32) | c.dm_w[0]);
+}
+__device__ __forceinline__ double coef_dt(const CoefN& c) {
+  return __hiloint2double((int)c.dt_w[1], (int)c.dt_w[0]);
+}
 
 // One request of a packed launch: a two-state model with at most 8 modes
 // advancing over its own steps [cs, ce) (device table entry).

@@ -1004,6 +1004,7 @@ __device__ __forceinline__ void sample_walkerN_f32(const SampleN32& sp, uint64_t
                                                    uint16_t& ab, float (&e)[NS],
                                                    float (&U)[NS][NS]) {
   const int n = sp.n;
+  const bool k_dev = n * NS * NS > kSampleNK;  // K past the parameter copy: from the model
   float W[NS][NS];
 #pragma unroll
   for (int a = 0; a < NS; ++a)
@@ -1024,10 +1025,14 @@ __device__ __forceinline__ void sample_walkerN_f32(const SampleN32& sp, uint64_t
     Rg[(int64_t)j * stride] = R;
     Pg[(int64_t)j * stride] = P;
     const float* Kj = sp.K + j * NS * NS;
+    const double* Kdj = sp.Kd + (size_t)j * NS * NS;
 #pragma unroll
     for (int a = 0; a < NS; ++a)
 #pragma unroll
-      for (int b = 0; b < NS; ++b) W[a][b] = __fmaf_rn(R, Kj[a * NS + b], W[a][b]);
+      for (int b = 0; b < NS; ++b) {
+        const float kv = k_dev ? (float)Kdj[a * NS + b] : Kj[a * NS + b];
+        W[a][b] = __fmaf_rn(R, kv, W[a][b]);
+      }
   }
   eigh_ns<float, NS>(W, nullptr, e, U, 12, 1e-13f);
   // the pair's density: U^T rho U in the adiabatic basis, rho itself in the
@@ -1139,6 +1144,58 @@ __host__ __device__ constexpr int tri(int a, int b) {
   return a <= b ? a * NS - a * (a - 1) / 2 + (b - a) : b * NS - b * (b - 1) / 2 + (a - b);
 }
 
+// ---------------------------------------------------------- modes in memory --
+// The FP32 kernels' form for any mode count: R and P stay in the ensemble
+// buffer and are read (and written back) mode by mode in each pass of a step;
+// the per-mode coefficients come from a table in shared memory, row j = the
+// upper triangle of K_j, dt/2 k_j, dt/M_j and 1/M_j (padded to whole float4s),
+// built from the FP64 model with the host's roundings (the CoefN values).
+template <int NS>
+struct ModeRow {
+  static constexpr int NTRI = NS * (NS + 1) / 2;
+  static constexpr int HK = NTRI, DTM = NTRI + 1, MINV = NTRI + 2;
+  static constexpr int CS = (NTRI + 3 + 3) / 4 * 4;
+  static size_t bytes(int n) { return (size_t)n * CS * sizeof(float); }
+};
+
+template <int NS>
+__device__ void fill_mode_table(float* mt, const DevModel* dm, double dt, int n) {
+  using MR = ModeRow<NS>;
+  for (int idx = threadIdx.x; idx < n * MR::CS; idx += blockDim.x) {
+    const int j = idx / MR::CS, c = idx - j * MR::CS;
+    float v = 0.0f;
+    if (c < MR::NTRI) {
+      int a = 0, rem = c;  // row a, column a + rem of the upper triangle
+      while (rem >= NS - a) {
+        rem -= NS - a;
+        ++a;
+      }
+      v = (float)dm->K[(size_t)j * NS * NS + a * NS + a + rem];
+    } else if (c == MR::HK) {
+      v = (float)(0.5 * dt * dm->k[j]);
+    } else if (c == MR::DTM) {
+      v = (float)(dt / dm->mass[j]);
+    } else if (c == MR::MINV) {
+      v = (float)(1.0 / dm->mass[j]);
+    }
+    mt[idx] = v;
+  }
+  __syncthreads();
+}
+
+template <int NS>
+__device__ __forceinline__ void mode_row(const float* mt, int j, float (&r)[ModeRow<NS>::CS]) {
+  const float4* p = reinterpret_cast<const float4*>(mt + j * ModeRow<NS>::CS);
+#pragma unroll
+  for (int q = 0; q < ModeRow<NS>::CS / 4; ++q) {
+    const float4 v = p[q];
+    r[4 * q] = v.x;
+    r[4 * q + 1] = v.y;
+    r[4 * q + 2] = v.z;
+    r[4 * q + 3] = v.w;
+  }
+}
+
 // WPT (1 or 2) tiles of 128 walkers per block, thread t holding walker t of
 // each: with WPT = 2 the two walkers are the lanes of float2 values and their
 // FP32 arithmetic runs as packed FP32x2 instructions (explicit round-to-nearest
@@ -1154,17 +1211,25 @@ template <int NS, int NPL, int WPT>
 __global__ void __launch_bounds__(128, (BulkNMinBlocks<NS, NPL, WPT>::value))
     k_bulkN(const BulkParams bp, const CoefN cf, void* buf, double* __restrict__ part) {
   static_assert(WPT == 1 || WPT == 2, "one or two walkers per thread");
+  // NPL = 0: the modes stay in memory (any mode count, one walker per thread)
+  constexpr bool MEM = NPL == 0;
+  constexpr int NR = MEM ? 1 : NPL;
+  static_assert(!MEM || WPT == 1, "modes in memory: one walker per thread");
+  using MR = ModeRow<NS>;
   using V = std::conditional_t<WPT == 2, float2, float>;
   constexpr int NN = NS * NS, NTRI = NS * (NS + 1) / 2;
   constexpr int NP = (4 * NN + 15) / 16;  // observation passes of 32 quantities
   constexpr int TW = 128;                 // walkers per tile
   __shared__ double red[2][4][32];
   __shared__ float obs_rows[TW * 33];
+  extern __shared__ float4 mode_tab4[];
+  float* const mtab = reinterpret_cast<float*>(mode_tab4);
   WN<float> ws = viewN<float>(buf, bp.n_traj, NS, bp.n, QCL_PREC_FP32_BULK);
   if (ws.hdr->step != bp.step0) {
     if (blockIdx.x == 0 && threadIdx.x == 0) atomicOr(&ws.hdr->flags, QCL_FLAG_STEP_MISMATCH);
     return;
   }
+  if constexpr (MEM) fill_mode_table<NS>(mtab, coef_dm(cf), coef_dt(cf), bp.n);
   const int64_t nt = bp.n_traj;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   unsigned int n_deg = 0;
@@ -1173,7 +1238,7 @@ __global__ void __launch_bounds__(128, (BulkNMinBlocks<NS, NPL, WPT>::value))
        tile0 += (int64_t)gridDim.x * WPT) {
     bool active[WPT];
     int64_t iw[WPT];
-    V R[NPL], P[NPL], U[NS][NS], e[NS];
+    V R[NR], P[NR], U[NS][NS], e[NS];
     PairV<V> m, ph;
     int mexp[WPT], al[WPT], be[WPT];
     uint64_t traj[WPT];
@@ -1258,14 +1323,17 @@ __global__ void __launch_bounds__(128, (BulkNMinBlocks<NS, NPL, WPT>::value))
     // the coupling part of dt/2 F_ab: g_j = sum_k K_jk Q_k with
     // Q = dt/2 * (1/2)(u_a u_a^T + u_b u_b^T) folded with the off-diagonal
     // factor 2 (ua, ub: columns al, be of U)
-    auto force = [&](const V (&ua)[NS], const V (&ub)[NS], V (&g)[NPL]) {
-      V Q[NTRI];
+    auto make_q = [&](const V (&ua)[NS], const V (&ub)[NS], V (&Q)[NTRI]) {
 #pragma unroll
       for (int a = 0; a < NS; ++a)
 #pragma unroll
         for (int b = a; b < NS; ++b)
           Q[tri<NS>(a, b)] = vmul(splat<V>((a == b ? 0.5f : 1.0f) * bp.hdt),
                                   vfma(ua[a], ua[b], vmul(ub[a], ub[b])));
+    };
+    auto force = [&](const V (&ua)[NS], const V (&ub)[NS], V (&g)[NR]) {
+      V Q[NTRI];
+      make_q(ua, ub, Q);
 #pragma unroll
       for (int j = 0; j < NPL; ++j) {
         V gj = splat<V>(0.0f);
@@ -1275,9 +1343,67 @@ __global__ void __launch_bounds__(128, (BulkNMinBlocks<NS, NPL, WPT>::value))
       }
     };
     // P += dt/2 F_ab(R) = P - dt/2 k R - g
-    auto kick = [&](const V (&g)[NPL]) {
+    auto kick = [&](const V (&g)[NR]) {
 #pragma unroll
       for (int j = 0; j < NPL; ++j) P[j] = vsub(vfma(splat<V>(-cf.hk[j]), R[j], P[j]), g[j]);
+    };
+    // Modes in memory, mode by mode with the register form's operations in its
+    // order.  Pass A: the first half kick with the force term of Q, the drift
+    // and the upper triangle of W(R_{n+1}); pass B: the second half kick with
+    // the force term of Q and the sum G = sum_j (P_j/M_j) K_j.
+    auto pass_a = [&](const V (&Q)[NTRI], V (&W)[NS][NS]) {
+      V t[NTRI];
+#pragma unroll
+      for (int k = 0; k < NTRI; ++k) t[k] = splat<V>(cf.E[k]);
+      const int64_t i = iw[0];
+#pragma unroll 2
+      for (int j = 0; j < bp.n; ++j) {
+        float kr[MR::CS];
+        mode_row<NS>(mtab, j, kr);
+        V r = splat<V>(0.0f), p = splat<V>(0.0f);
+        if (active[0]) {
+          ln(r, 0) = ws.R[(int64_t)j * nt + i];
+          ln(p, 0) = ws.P[(int64_t)j * nt + i];
+        }
+        V g = splat<V>(0.0f);
+#pragma unroll
+        for (int k = 0; k < NTRI; ++k) g = vfma(splat<V>(kr[k]), Q[k], g);
+        p = vsub(vfma(splat<V>(-kr[MR::HK]), r, p), g);
+        r = vfma(splat<V>(kr[MR::DTM]), p, r);
+#pragma unroll
+        for (int k = 0; k < NTRI; ++k) t[k] = vfma(r, splat<V>(kr[k]), t[k]);
+        if (active[0]) {
+          ws.R[(int64_t)j * nt + i] = ln(r, 0);
+          ws.P[(int64_t)j * nt + i] = ln(p, 0);
+        }
+      }
+#pragma unroll
+      for (int a = 0; a < NS; ++a)
+#pragma unroll
+        for (int b = 0; b < NS; ++b) W[a][b] = t[tri<NS>(a, b)];
+    };
+    auto pass_b = [&](const V (&Q)[NTRI], V (&t)[NTRI]) {
+#pragma unroll
+      for (int k = 0; k < NTRI; ++k) t[k] = splat<V>(0.0f);
+      const int64_t i = iw[0];
+#pragma unroll 2
+      for (int j = 0; j < bp.n; ++j) {
+        float kr[MR::CS];
+        mode_row<NS>(mtab, j, kr);
+        V r = splat<V>(0.0f), p = splat<V>(0.0f);
+        if (active[0]) {
+          ln(r, 0) = ws.R[(int64_t)j * nt + i];
+          ln(p, 0) = ws.P[(int64_t)j * nt + i];
+        }
+        V g = splat<V>(0.0f);
+#pragma unroll
+        for (int k = 0; k < NTRI; ++k) g = vfma(splat<V>(kr[k]), Q[k], g);
+        p = vsub(vfma(splat<V>(-kr[MR::HK]), r, p), g);
+        const V v = vmul(p, splat<V>(kr[MR::MINV]));
+#pragma unroll
+        for (int k = 0; k < NTRI; ++k) t[k] = vfma(v, splat<V>(kr[k]), t[k]);
+        if (active[0]) ws.P[(int64_t)j * nt + i] = ln(p, 0);
+      }
     };
     // observation of walker lane l into slot `slot` of tile tile0 + l
     auto observe_lane = [&](int l, int slot) {
@@ -1358,38 +1484,58 @@ __global__ void __launch_bounds__(128, (BulkNMinBlocks<NS, NPL, WPT>::value))
     for (int l = 0; l < WPT; ++l) wd[l] = philox_draw(bp.seed, blk, traj[l], kPurposeHop);
     // Carried from one step to the next while no walker of the thread hops:
     // the pair's columns ua, ub and energies ea, eb at R_{n+1}, their gap and the
-    // force term g, which the next step's first half kick (the same R, U and
-    // pair) would compute again bit for bit.  A hop, and the first step of a
-    // launch, compute them afresh.
-    V ua[NS], ub[NS], gk[NPL], ea, eb, de0;
+    // force term g (its Q with the modes in memory), which the next step's
+    // first half kick (the same R, U and pair) would compute again bit for
+    // bit.  A hop, and the first step of a launch, compute them afresh.
+    V ua[NS], ub[NS], gk[NR], Qc[NTRI], ea, eb, de0;
     bool cached = false;
     for (int it = 0; it < bp.len; ++it) {
       if (!cached) {
         de0 = gap_ab(ea, eb);
         columns(ua, ub);
-        force(ua, ub, gk);
+        if constexpr (MEM) make_q(ua, ub, Qc);
+        else force(ua, ub, gk);
       }
-      kick(gk);  // first half kick at R_n
-#pragma unroll
-      for (int j = 0; j < NPL; ++j) R[j] = vfma(splat<V>(cf.dtm[j]), P[j], R[j]);
-      {
+      V Gt[NTRI];  // (modes in memory: G's upper triangle from pass B)
+      if constexpr (MEM) {
         V W[NS][NS], Uref[NS][NS];
 #pragma unroll
         for (int a = 0; a < NS; ++a)
 #pragma unroll
           for (int b = 0; b < NS; ++b) Uref[a][b] = U[a][b];
-        build_w(W);
+        pass_a(Qc, W);  // first half kick at R_n, drift, W(R_{n+1})
         eigh_warm_fast<NS, V>(W, Uref, e, U);
+        columns(ua, ub);
+        make_q(ua, ub, Qc);
+        pass_b(Qc, Gt);  // second half kick at R_{n+1}, G
+      } else {
+        kick(gk);  // first half kick at R_n
+#pragma unroll
+        for (int j = 0; j < NPL; ++j) R[j] = vfma(splat<V>(cf.dtm[j]), P[j], R[j]);
+        {
+          V W[NS][NS], Uref[NS][NS];
+#pragma unroll
+          for (int a = 0; a < NS; ++a)
+#pragma unroll
+            for (int b = 0; b < NS; ++b) Uref[a][b] = U[a][b];
+          build_w(W);
+          eigh_warm_fast<NS, V>(W, Uref, e, U);
+        }
+        columns(ua, ub);  // (the new decomposition's columns)
+        force(ua, ub, gk);
+        kick(gk);  // second half kick at R_{n+1}
       }
-      columns(ua, ub);  // (the new decomposition's columns)
-      force(ua, ub, gk);
-      kick(gk);  // second half kick at R_{n+1}
       const V de1 = gap_ab(ea, eb);
       ph = df_add_v(ph, vmul(splat<V>(bp.hdt_hbar), vadd(de0, de1)));
       de0 = de1;
       // G = sum_j (P_j/M_j) K_j
       V G[NS][NS];
-      {
+      if constexpr (MEM) {
+#pragma unroll
+        for (int a = 0; a < NS; ++a)
+#pragma unroll
+          for (int b = 0; b < NS; ++b) G[a][b] = Gt[tri<NS>(a, b)];
+      } else {
         V t[NTRI];
 #pragma unroll
         for (int k = 0; k < NTRI; ++k) t[k] = splat<V>(0.0f);
@@ -1589,13 +1735,20 @@ __global__ void __launch_bounds__(128, (NPL > 8 || NS > 5) ? 2 : 4)
   constexpr int NP = (4 * NN + 15) / 16;
   constexpr int TW = 128;
   constexpr int NC = 2 * NS;
+  // NPL = 0: the modes stay in memory (any mode count)
+  constexpr bool MEM = NPL == 0;
+  constexpr int NR = MEM ? 1 : NPL;
+  using MR = ModeRow<NS>;
   __shared__ double red[2][4][32];
   __shared__ float obs_rows[TW * 33];
+  extern __shared__ float4 mode_tab4[];
+  float* const mtab = reinterpret_cast<float*>(mode_tab4);
   WN<float> ws = viewN<float>(buf, bp.n_traj, NS, bp.n, QCL_PREC_FP32_BULK);
   if (ws.hdr->step != bp.step0) {
     if (blockIdx.x == 0 && threadIdx.x == 0) atomicOr(&ws.hdr->flags, QCL_FLAG_STEP_MISMATCH);
     return;
   }
+  if constexpr (MEM) fill_mode_table<NS>(mtab, coef_dm(cf), coef_dt(cf), bp.n);
   const int64_t nt = bp.n_traj;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   int rb = 0;
@@ -1603,7 +1756,7 @@ __global__ void __launch_bounds__(128, (NPL > 8 || NS > 5) ? 2 : 4)
     const int64_t i = tile0 * TW + threadIdx.x;
     const bool active = i < nt;
     const int64_t ii = active ? i : 0;
-    float R[NPL], P[NPL];
+    float R[NR], P[NR];
 #pragma unroll
     for (int j = 0; j < NPL; ++j) {
       const bool on = active && j < bp.n;
@@ -1638,7 +1791,7 @@ __global__ void __launch_bounds__(128, (NPL > 8 || NS > 5) ? 2 : 4)
       return __fsub_rn(va, vb);
     };
     // the pair's force constants: hkd_j = dt/2 * 1/2 (K_j,aa + K_j,bb)
-    float hkd[NPL];
+    float hkd[NR];
     auto pair_force = [&]() {
 #pragma unroll
       for (int j = 0; j < NPL; ++j) {
@@ -1657,8 +1810,43 @@ __global__ void __launch_bounds__(128, (NPL > 8 || NS > 5) ? 2 : 4)
       for (int j = 0; j < NPL; ++j)
         P[j] = __fsub_rn(__fmaf_rn(-cf.hk[j], R[j], P[j]), hkd[j]);
     };
+    // Modes in memory: one pass per step, mode by mode with the register
+    // form's operations in its order.  The second half kick of a step is
+    // taken at the start of the next step's pass (the transition does not
+    // depend on the momenta here), with the pair it was due with (pa, pb),
+    // then the first half kick of the current pair, the drift and the upper
+    // triangle of W(R_{n+1}); a last pass ends the launch with the pending kick.
+    const float hh = 0.5f * bp.hdt;
+    auto pass_dia = [&](float (&t)[NTRI], bool pend, int pa, int pb, bool step) {
+#pragma unroll
+      for (int k = 0; k < NTRI; ++k) t[k] = cf.E[k];
+      const int dpa = tri<NS>(pa, pa), dpb = tri<NS>(pb, pb);
+      const int da = tri<NS>(al, al), db = tri<NS>(be, be);
+#pragma unroll 2
+      for (int j = 0; j < bp.n; ++j) {
+        const float* row = mtab + j * MR::CS;
+        float kr[MR::CS];
+        mode_row<NS>(mtab, j, kr);
+        float r = active ? ws.R[(int64_t)j * nt + i] : 0.0f;
+        float p = active ? ws.P[(int64_t)j * nt + i] : 0.0f;
+        if (pend) p = __fsub_rn(__fmaf_rn(-kr[MR::HK], r, p), __fmul_rn(hh, __fadd_rn(row[dpa], row[dpb])));
+        if (step) {
+          p = __fsub_rn(__fmaf_rn(-kr[MR::HK], r, p), __fmul_rn(hh, __fadd_rn(row[da], row[db])));
+          r = __fmaf_rn(kr[MR::DTM], p, r);
+        }
+#pragma unroll
+        for (int k = 0; k < NTRI; ++k) t[k] = __fmaf_rn(r, kr[k], t[k]);
+        if (active && (pend || step)) {
+          ws.R[(int64_t)j * nt + i] = r;
+          ws.P[(int64_t)j * nt + i] = p;
+        }
+      }
+    };
     float t[NTRI];
-    build_w(t);
+    bool pend = false;
+    int pa = al, pb = be;
+    if constexpr (MEM) pass_dia(t, false, al, be, false);
+    else build_w(t);
     pair_force();
     float w0 = diag_gap(t);  // hbar w_ab at R_n (times 1/hbar in hdt_hbar)
 
@@ -1728,11 +1916,18 @@ __global__ void __launch_bounds__(128, (NPL > 8 || NS > 5) ? 2 : 4)
     u4 wd = philox_draw(bp.seed, blk, traj, kPurposeHop);
     const float tmaxf = (float)bp.tmax;
     for (int it = 0; it < bp.len; ++it) {
-      kick();  // first half kick at R_n
+      if constexpr (MEM) {
+        pass_dia(t, pend, pa, pb, true);
+        pend = true;  // the second half kick at R_{n+1}, with this pair
+        pa = al;
+        pb = be;
+      } else {
+        kick();  // first half kick at R_n
 #pragma unroll
-      for (int j = 0; j < NPL; ++j) R[j] = __fmaf_rn(cf.dtm[j], P[j], R[j]);
-      build_w(t);
-      kick();  // second half kick at R_{n+1} (the diagonal force's coupling part is a constant)
+        for (int j = 0; j < NPL; ++j) R[j] = __fmaf_rn(cf.dtm[j], P[j], R[j]);
+        build_w(t);
+        kick();  // second half kick at R_{n+1} (the diagonal force's coupling part is a constant)
+      }
       const float w1 = diag_gap(t);
       ph = df_add(ph, __fmul_rn(bp.hdt_hbar, __fadd_rn(w0, w1)));
       // events at R_{n+1}: slots 0..NS-1 a -> g with c = W_ga dt / hbar (three
@@ -1814,6 +2009,9 @@ __global__ void __launch_bounds__(128, (NPL > 8 || NS > 5) ? 2 : 4)
         observe(slot++);
         to_out = bp.stride;
       }
+    }
+    if constexpr (MEM) {
+      if (pend) pass_dia(t, true, pa, pb, false);
     }
     if (active) {
 #pragma unroll
@@ -1920,6 +2118,12 @@ __global__ void __launch_bounds__(256) k_spawnN_step32(const BulkParams bp, cons
                                                        void* buf, int64_t cap, int64_t n0,
                                                        int64_t step) {
   constexpr int NTRI = NS * (NS + 1) / 2, NC = 2 * NS;
+  // NPL = 0: the modes stay in memory (any mode count)
+  constexpr bool MEM = NPL == 0;
+  constexpr int NR = MEM ? 1 : NPL;
+  using MR = ModeRow<NS>;
+  extern __shared__ float4 mode_tab4[];
+  float* const mtab = reinterpret_cast<float*>(mode_tab4);
   const SpawnLayout L = SpawnLayout::make(cap, bp.n, n0, QCL_PREC_FP32_BULK, NS);
   EnsHeader* hdr = (EnsHeader*)buf;
   const int src = (int)(step & 1);
@@ -1928,6 +2132,7 @@ __global__ void __launch_bounds__(256) k_spawnN_step32(const BulkParams bp, cons
     if (blockIdx.x == 0 && threadIdx.x == 0) atomicOr(&hdr->flags, QCL_FLAG_STEP_MISMATCH);
     return;
   }
+  if constexpr (MEM) fill_mode_table<NS>(mtab, coef_dm(cf), coef_dt(cf), bp.n);
   const bool dia = bp.repr == QCL_REPR_DIABATIC;
   const float tmaxf = (float)bp.tmax;
   const int64_t nvb = (n_live + 255) / 256;
@@ -1940,7 +2145,7 @@ __global__ void __launch_bounds__(256) k_spawnN_step32(const BulkParams bp, cons
     int flag = 0;
     {
       const SetN32 s = spawn_setN32(buf, L, src);
-      float R[NPL], P[NPL];
+      float R[NR], P[NR];
 #pragma unroll
       for (int j = 0; j < NPL; ++j) {
         const bool on = j < bp.n;
@@ -1964,7 +2169,7 @@ __global__ void __launch_bounds__(256) k_spawnN_step32(const BulkParams bp, cons
       bool deg = false;
       if (dia) {
         // diagonal force constants of the pair, W_aa - W_bb at R_n and R_{n+1}
-        float hkd[NPL];
+        float hkd[NR];
 #pragma unroll
         for (int j = 0; j < NPL; ++j) {
           float ka = cf.K[j][tri<NS>(0, 0)], kb = ka;
@@ -1987,15 +2192,46 @@ __global__ void __launch_bounds__(256) k_spawnN_step32(const BulkParams bp, cons
           return __fsub_rn(va, vb);
         };
         float t[NTRI];
-        build_w(t);
-        const float w0 = gap(t);
+        float w0;
+        if constexpr (MEM) {
+          // one pass: W(R_n), both half kicks, the drift and W(R_{n+1}) mode
+          // by mode (the register form's operations in its order)
+          const float hh = 0.5f * bp.hdt;
+          const int da = tri<NS>(al, al), db = tri<NS>(be, be);
+          float t0[NTRI];
 #pragma unroll
-        for (int j = 0; j < NPL; ++j) P[j] = __fsub_rn(__fmaf_rn(-cf.hk[j], R[j], P[j]), hkd[j]);
+          for (int k = 0; k < NTRI; ++k) t0[k] = t[k] = cf.E[k];
+#pragma unroll 2
+          for (int j = 0; j < bp.n; ++j) {
+            const float* row = mtab + j * MR::CS;
+            float kr[MR::CS];
+            mode_row<NS>(mtab, j, kr);
+            float r = s.R[(int64_t)j * cap + i], p = s.P[(int64_t)j * cap + i];
+            const float hd = __fmul_rn(hh, __fadd_rn(row[da], row[db]));
 #pragma unroll
-        for (int j = 0; j < NPL; ++j) R[j] = __fmaf_rn(cf.dtm[j], P[j], R[j]);
-        build_w(t);
+            for (int k = 0; k < NTRI; ++k) t0[k] = __fmaf_rn(r, kr[k], t0[k]);
+            p = __fsub_rn(__fmaf_rn(-kr[MR::HK], r, p), hd);
+            r = __fmaf_rn(kr[MR::DTM], p, r);
 #pragma unroll
-        for (int j = 0; j < NPL; ++j) P[j] = __fsub_rn(__fmaf_rn(-cf.hk[j], R[j], P[j]), hkd[j]);
+            for (int k = 0; k < NTRI; ++k) t[k] = __fmaf_rn(r, kr[k], t[k]);
+            p = __fsub_rn(__fmaf_rn(-kr[MR::HK], r, p), hd);
+            if (live) {
+              s.R[(int64_t)j * cap + i] = r;
+              s.P[(int64_t)j * cap + i] = p;
+            }
+          }
+          w0 = gap(t0);
+        } else {
+          build_w(t);
+          w0 = gap(t);
+#pragma unroll
+          for (int j = 0; j < NPL; ++j) P[j] = __fsub_rn(__fmaf_rn(-cf.hk[j], R[j], P[j]), hkd[j]);
+#pragma unroll
+          for (int j = 0; j < NPL; ++j) R[j] = __fmaf_rn(cf.dtm[j], P[j], R[j]);
+          build_w(t);
+#pragma unroll
+          for (int j = 0; j < NPL; ++j) P[j] = __fsub_rn(__fmaf_rn(-cf.hk[j], R[j], P[j]), hkd[j]);
+        }
         ph = df_add(ph, __fmul_rn(bp.hdt_hbar, __fadd_rn(w0, gap(t))));
 #pragma unroll
         for (int g = 0; g < NS; ++g) {
@@ -2019,17 +2255,20 @@ __global__ void __launch_bounds__(256) k_spawnN_step32(const BulkParams bp, cons
         }
         // P += dt/2 F_ab with the pair's columns ua, ub (the persistent
         // kernel's force term)
-        auto kick = [&](const float (&Uc)[NS][NS]) {
+        auto make_q = [&](const float (&Uc)[NS][NS], float (&Q)[NTRI]) {
           float ua[NS], ub[NS];
           column<float, NS>(Uc, al, ua);
           column<float, NS>(Uc, be, ub);
-          float Q[NTRI];
 #pragma unroll
           for (int a = 0; a < NS; ++a)
 #pragma unroll
             for (int b = a; b < NS; ++b)
               Q[tri<NS>(a, b)] = __fmul_rn((a == b ? 0.5f : 1.0f) * bp.hdt,
                                            __fmaf_rn(ua[a], ua[b], __fmul_rn(ub[a], ub[b])));
+        };
+        auto kick = [&](const float (&Uc)[NS][NS]) {
+          float Q[NTRI];
+          make_q(Uc, Q);
 #pragma unroll
           for (int j = 0; j < NPL; ++j) {
             float gj = 0.0f;
@@ -2039,33 +2278,80 @@ __global__ void __launch_bounds__(256) k_spawnN_step32(const BulkParams bp, cons
           }
         };
         const float de0 = __fsub_rn(pick<float, NS>(e, al), pick<float, NS>(e, be));
-        kick(U);
-#pragma unroll
-        for (int j = 0; j < NPL; ++j) R[j] = __fmaf_rn(cf.dtm[j], P[j], R[j]);
         float W[NS][NS], U1[NS][NS];
-        {
-          float t[NTRI];
-          build_w(t);
+        float G[NTRI];
+#pragma unroll
+        for (int k = 0; k < NTRI; ++k) G[k] = 0.0f;
+        if constexpr (MEM) {
+          // pass A: first half kick, drift, W(R_{n+1}); pass B: second half
+          // kick and G (the register form's operations in its order)
+          float Q[NTRI], t[NTRI];
+          make_q(U, Q);
+#pragma unroll
+          for (int k = 0; k < NTRI; ++k) t[k] = cf.E[k];
+#pragma unroll 2
+          for (int j = 0; j < bp.n; ++j) {
+            float kr[MR::CS];
+            mode_row<NS>(mtab, j, kr);
+            float r = s.R[(int64_t)j * cap + i], p = s.P[(int64_t)j * cap + i];
+            float g = 0.0f;
+#pragma unroll
+            for (int k = 0; k < NTRI; ++k) g = __fmaf_rn(kr[k], Q[k], g);
+            p = __fsub_rn(__fmaf_rn(-kr[MR::HK], r, p), g);
+            r = __fmaf_rn(kr[MR::DTM], p, r);
+#pragma unroll
+            for (int k = 0; k < NTRI; ++k) t[k] = __fmaf_rn(r, kr[k], t[k]);
+            if (live) {
+              s.R[(int64_t)j * cap + i] = r;
+              s.P[(int64_t)j * cap + i] = p;
+            }
+          }
 #pragma unroll
           for (int a = 0; a < NS; ++a)
 #pragma unroll
             for (int b = 0; b < NS; ++b) W[a][b] = t[tri<NS>(a, b)];
+          eigh_warm_fast<NS, float>(W, U, e, U1);
+          make_q(U1, Q);
+#pragma unroll 2
+          for (int j = 0; j < bp.n; ++j) {
+            float kr[MR::CS];
+            mode_row<NS>(mtab, j, kr);
+            const float r = s.R[(int64_t)j * cap + i];
+            float p = s.P[(int64_t)j * cap + i];
+            float g = 0.0f;
+#pragma unroll
+            for (int k = 0; k < NTRI; ++k) g = __fmaf_rn(kr[k], Q[k], g);
+            p = __fsub_rn(__fmaf_rn(-kr[MR::HK], r, p), g);
+            const float v = __fmul_rn(p, kr[MR::MINV]);
+#pragma unroll
+            for (int k = 0; k < NTRI; ++k) G[k] = __fmaf_rn(v, kr[k], G[k]);
+            if (live) s.P[(int64_t)j * cap + i] = p;
+          }
+        } else {
+          kick(U);
+#pragma unroll
+          for (int j = 0; j < NPL; ++j) R[j] = __fmaf_rn(cf.dtm[j], P[j], R[j]);
+          {
+            float t[NTRI];
+            build_w(t);
+#pragma unroll
+            for (int a = 0; a < NS; ++a)
+#pragma unroll
+              for (int b = 0; b < NS; ++b) W[a][b] = t[tri<NS>(a, b)];
+          }
+          eigh_warm_fast<NS, float>(W, U, e, U1);
+          kick(U1);
+#pragma unroll
+          for (int j = 0; j < NPL; ++j) {
+            const float v = __fmul_rn(P[j], cf.minv[j]);
+#pragma unroll
+            for (int k = 0; k < NTRI; ++k) G[k] = __fmaf_rn(v, cf.K[j][k], G[k]);
+          }
         }
-        eigh_warm_fast<NS, float>(W, U, e, U1);
-        kick(U1);
         const float ea = pick<float, NS>(e, al), eb = pick<float, NS>(e, be);
         ph = df_add(ph, __fmul_rn(bp.hdt_hbar, __fadd_rn(de0, __fsub_rn(ea, eb))));
         // event amplitudes: slots 0..NS-1 a -> nu with A = -dt (v.d)_{nu a},
         // slots NS..2NS-1 b -> nu with A = +dt (v.d)_{b nu}
-        float G[NTRI];
-#pragma unroll
-        for (int k = 0; k < NTRI; ++k) G[k] = 0.0f;
-#pragma unroll
-        for (int j = 0; j < NPL; ++j) {
-          const float v = __fmul_rn(P[j], cf.minv[j]);
-#pragma unroll
-          for (int k = 0; k < NTRI; ++k) G[k] = __fmaf_rn(v, cf.K[j][k], G[k]);
-        }
         float ua[NS], ub[NS], Gua[NS], Gub[NS];
         column<float, NS>(U1, al, ua);
         column<float, NS>(U1, be, ub);
@@ -2294,12 +2580,18 @@ __global__ void __launch_bounds__(128) k_spawnN_observe32(const BulkParams bp, c
         for (int a = 0; a < NS; ++a)
 #pragma unroll
           for (int b = 0; b < NS; ++b) W[a][b] = cf.E[tri<NS>(a, b)];
+        // (modes past the 32 of cf from the model's FP64 K, rounded alike)
         for (int m = 0; m < bp.n; ++m) {
           const float r = s.R[(int64_t)m * cap + j];
+          const double* Km = coef_dm(cf)->K + (size_t)m * NS * NS;
 #pragma unroll
           for (int a = 0; a < NS; ++a)
 #pragma unroll
-            for (int b = 0; b < NS; ++b) W[a][b] = __fmaf_rn(r, cf.K[m][tri<NS>(a, b)], W[a][b]);
+            for (int b = 0; b < NS; ++b) {
+              const float kv = m < 32 ? cf.K[m][tri<NS>(a, b)]
+                                      : (float)Km[a <= b ? a * NS + b : b * NS + a];
+              W[a][b] = __fmaf_rn(r, kv, W[a][b]);
+            }
         }
         eigh_ns<float, NS>(W, nullptr, e, U, 12, 1e-13f);
       } else {
@@ -2405,14 +2697,23 @@ struct NStateOps {
   template <int NPL>
   static void spawn_step32_npl(const BulkParams& bp, const CoefN& cf, void* buf, int64_t cap,
                                int64_t n0, int64_t step, cudaStream_t st) {
-    k_spawnN_step32<NS, NPL><<<spawn_grid(cap), 256, 0, st>>>(bp, cf, buf, cap, n0, step);
+    // (NPL = 0: the mode table in dynamic shared memory)
+    const size_t dyn = NPL == 0 ? ModeRow<NS>::bytes(bp.n) : 0;
+    static size_t dyn_set = 0;
+    if (dyn > dyn_set) {
+      cudaFuncSetAttribute(k_spawnN_step32<NS, NPL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)dyn);
+      dyn_set = dyn;
+    }
+    k_spawnN_step32<NS, NPL><<<spawn_grid(cap), 256, dyn, st>>>(bp, cf, buf, cap, n0, step);
   }
-  // one FP32 spawning step (step kernel, scan, scatter); at most 8 modes
+  // one FP32 spawning step (step kernel, scan, scatter): up to 8 modes in
+  // registers, beyond (or under the modes-in-memory option) in memory
   static int spawn_step32(const BulkParams& bp, const CoefN& cf, void* buf, int64_t cap,
                           int64_t n0, int64_t step0, int64_t step, cudaStream_t st) {
-    if (bp.n <= 4) spawn_step32_npl<4>(bp, cf, buf, cap, n0, step, st);
-    else if (bp.n <= 8) spawn_step32_npl<8>(bp, cf, buf, cap, n0, step, st);
-    else return 0;
+    if (cf.modes_in_memory == 1 || bp.n > 8) spawn_step32_npl<0>(bp, cf, buf, cap, n0, step, st);
+    else if (bp.n <= 4) spawn_step32_npl<4>(bp, cf, buf, cap, n0, step, st);
+    else spawn_step32_npl<8>(bp, cf, buf, cap, n0, step, st);
     launch_spawn_scan(buf, cap, bp.n, n0, QCL_PREC_FP32_BULK, NS, step0, step, st);
     k_spawnN_scatter32<NS><<<spawn_grid(cap), 256, 0, st>>>(buf, cap, bp.n, n0, step0, step,
                                                             bp.seed);
@@ -2436,34 +2737,39 @@ struct NStateOps {
   template <int NPL, int WPT = 1>
   static int bulk_npl(const BulkParams& bp, const CoefN& cf, void* buf, double* part,
                       int grid_cap, cudaStream_t st) {
-    // (occupancy cached per kernel: [0] adiabatic, [1] diabatic)
+    // (occupancy cached per kernel and table size: [0] adiabatic, [1] diabatic;
+    // NPL = 0: the mode table in dynamic shared memory)
     static int per_sm[2] = {-1, -1}, n_sm[2] = {0, 0};
+    static size_t dyn_at[2] = {0, 0};
+    const size_t dyn = NPL == 0 ? ModeRow<NS>::bytes(bp.n) : 0;
     if (bp.repr == QCL_REPR_DIABATIC)
-      return launch_persistent(k_bulkN_dia<NS, NPL>, per_sm[1], n_sm[1], bp, cf, buf, part,
-                               grid_cap, 1, st);
-    return launch_persistent(k_bulkN<NS, NPL, WPT>, per_sm[0], n_sm[0], bp, cf, buf, part,
-                             grid_cap, WPT, st);
+      return launch_persistent(k_bulkN_dia<NS, NPL>, per_sm[1], n_sm[1], dyn_at[1], bp, cf, buf,
+                               part, grid_cap, 1, dyn, st);
+    return launch_persistent(k_bulkN<NS, NPL, WPT>, per_sm[0], n_sm[0], dyn_at[0], bp, cf, buf,
+                             part, grid_cap, WPT, dyn, st);
   }
   // one persistent grid: the occupancy limit of resident blocks on every SM
   // (capped), at most one block per WPT tiles
   template <typename Fn>
-  static int launch_persistent(Fn fn, int& per_sm, int& n_sm, const BulkParams& bp,
+  static int launch_persistent(Fn fn, int& per_sm, int& n_sm, size_t& dyn_at, const BulkParams& bp,
                                const CoefN& cf, void* buf, double* part, int grid_cap, int WPT,
-                               cudaStream_t st) {
-    if (per_sm < 0) {
+                               size_t dyn, cudaStream_t st) {
+    if (per_sm < 0 || dyn != dyn_at) {
       int dev = 0;
       cudaGetDevice(&dev);
       cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
-      if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, 128, 0) != cudaSuccess ||
+      if (dyn > 0) cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
+      if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, 128, dyn) != cudaSuccess ||
           per_sm < 1)
         per_sm = 1;
+      dyn_at = dyn;
     }
     int64_t grid = (int64_t)per_sm * n_sm;
     if (grid_cap > 0 && grid > grid_cap) grid = grid_cap;
     const int64_t units = (bp.n_tiles + WPT - 1) / WPT;
     if (grid > units) grid = units;
     if (grid < 1) grid = 1;
-    fn<<<(unsigned)grid, 128, 0, st>>>(bp, cf, buf, part);
+    fn<<<(unsigned)grid, 128, dyn, st>>>(bp, cf, buf, part);
     return (int)grid;
   }
   // wpt: walkers per thread asked for.  The kernel takes one or two, but only
@@ -2473,11 +2779,26 @@ struct NStateOps {
   static int bulk(const BulkParams& bp, const CoefN& cf, void* buf, double* part, int grid_cap,
                   int wpt, cudaStream_t st) {
     (void)wpt;
-    // up to 8 modes for any N_s; up to 32 modes for N_s <= 4 (larger N_s x modes
-    // would not fit a walker in registers).  For N_s <= 5 models of at most 4 or
-    // 6 modes get their own instantiations, which skip the padding modes'
-    // arithmetic (the results are the same: padding modes have zero
-    // coefficients and stay at zero)
+    // Register forms exist up to 8 modes for any N_s and up to 32 modes for
+    // N_s <= 4 (larger N_s x modes would not fit a walker in registers); the
+    // modes-in-memory form takes any mode count with the same bits.  The
+    // automatic choice follows measured solve rates on GB300 (1e6 walkers,
+    // 200 steps, random LVC models): registers for N_s = 3 (except adiabatic
+    // models of 9-16 modes, where the 32-mode register form is 10-30 % slower)
+    // and for N_s = 4 up to 8 modes (20-30 % faster); the memory form beyond
+    // (N_s = 4 with 12-32 modes: 1.3-2.6x faster) and for N_s >= 5 at every
+    // mode count (1.0-2.2x, the register forms there run one or two blocks per
+    // SM).  Models of at most 4 or 6 modes get their own instantiations,
+    // which skip the padding modes' arithmetic (padding modes have zero
+    // coefficients and stay at zero).
+    const int reg_max = NS <= 4 ? 32 : 8;
+    bool mem;
+    if (cf.modes_in_memory == 1) mem = true;
+    else if (cf.modes_in_memory == 2) mem = bp.n > reg_max;
+    else if (NS == 3) mem = bp.n > 32 || (bp.repr != QCL_REPR_DIABATIC && bp.n > 8 && bp.n <= 16);
+    else if (NS == 4) mem = bp.n > 8;
+    else mem = true;
+    if (mem) return bulk_npl<0>(bp, cf, buf, part, grid_cap, st);
     if constexpr (NS <= 5) {
       if (bp.n <= 4) return bulk_npl<4>(bp, cf, buf, part, grid_cap, st);
       if (bp.n <= 6) return bulk_npl<6>(bp, cf, buf, part, grid_cap, st);

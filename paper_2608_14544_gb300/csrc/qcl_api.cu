@@ -22,6 +22,7 @@ namespace {
 thread_local std::string g_err;
 int64_t g_opt_grid_cap = 0;
 bool g_opt_timing = false;
+int g_opt_modes_mem = 0;
 std::mutex g_tmu;
 std::vector<std::pair<cudaEvent_t, cudaEvent_t>> g_events[2];
 
@@ -94,10 +95,8 @@ qcl_status check_ens(const qcl_model* m, const qcl_ensemble_desc* e) {
   if (e->n_traj > (int64_t)1 << 40) return fail(QCL_ERR_INVALID_ARG, "n_traj too large");
   if (e->precision != QCL_PREC_FP64 && e->precision != QCL_PREC_FP32_BULK)
     return fail(QCL_ERR_INVALID_ARG, "unknown precision %d", e->precision);
-  if (m->ns > 2 && e->precision == QCL_PREC_FP32_BULK && m->n > (m->ns <= 4 ? 32 : 8))
-    return fail(QCL_ERR_UNSUPPORTED, "FP32-bulk models with %d states support n_modes <= %d (got %d)", m->ns, m->ns <= 4 ? 32 : 8, m->n);
-  if (m->host.repr == QCL_REPR_DIABATIC && e->precision == QCL_PREC_FP32_BULK && m->n > 32)
-    return fail(QCL_ERR_UNSUPPORTED, "diabatic FP32-bulk models support n_modes <= 32 (got %d)", m->n);
+  if (m->ns == 2 && m->host.repr == QCL_REPR_DIABATIC && e->precision == QCL_PREC_FP32_BULK && m->n > 32)
+    return fail(QCL_ERR_UNSUPPORTED, "diabatic FP32-bulk two-state models support n_modes <= 32 (got %d)", m->n);
   return QCL_OK;
 }
 
@@ -126,6 +125,11 @@ qcl_status qcl_set_option(int32_t key, int64_t value) {
   }
   if (key == QCL_OPT_TIMING) {
     g_opt_timing = value != 0;
+    return ok();
+  }
+  if (key == QCL_OPT_MODES_IN_MEMORY) {
+    if (value < 0 || value > 2) return fail(QCL_ERR_INVALID_ARG, "modes-in-memory option takes 0, 1 or 2");
+    g_opt_modes_mem = (int)value;
     return ok();
   }
   return fail(QCL_ERR_INVALID_ARG, "unknown option %d", key);
@@ -332,23 +336,26 @@ void fill_coef2(const qcl_model* model, double dt, Coef2* cf) {
   }
 }
 
-// FP32 copies of an N_s-state model's E, K and the sampling inputs (the FP32-bulk
-// mode limits keep n N_s^2 within kSampleNK).
 // FP32 per-mode coefficients of an N_s-state model for one time step dt
-// (upper triangles of E and of each K_j).
+// (upper triangles of E and of each K_j; the per-mode arrays hold the first 32
+// modes, the kernels that keep the modes in memory build the whole table on
+// the device from the model pointer and dt stored here).
 void fill_coefN(const qcl_model* model, double dt, CoefN& cn) {
   const DevModel& h = model->host;
   const int ns = model->ns;
   auto tri = [ns](int a, int b) { return a * ns - a * (a - 1) / 2 + (b - a); };
   for (int a = 0; a < ns; ++a)
     for (int b = a; b < ns; ++b) cn.E[tri(a, b)] = (float)model->E[a * ns + b];
-  for (int j = 0; j < model->n; ++j) {
+  const int n_reg = model->n < 32 ? model->n : 32;
+  for (int j = 0; j < n_reg; ++j) {
     cn.hk[j] = (float)(0.5 * dt * h.k[j]);
     cn.dtm[j] = (float)(dt / h.mass[j]);
     cn.minv[j] = (float)(1.0 / h.mass[j]);
     for (int a = 0; a < ns; ++a)
       for (int b = a; b < ns; ++b) cn.K[j][tri(a, b)] = (float)model->K[(size_t)j * ns * ns + a * ns + b];
   }
+  coef_set_model(cn, model->dev, dt);
+  cn.modes_in_memory = g_opt_modes_mem;
 }
 
 void make_sampleN32(const qcl_model* model, const SampleParams& sp, SampleN32& s) {
@@ -373,6 +380,7 @@ void make_sampleN32(const qcl_model* model, const SampleParams& sp, SampleN32& s
   }
   const size_t nk = (size_t)n * ns * ns;
   for (size_t k = 0; k < (size_t)kSampleNK; ++k) s.K[k] = k < nk ? (float)model->K[k] : 0.0f;
+  s.Kd = model->host.K;
 }
 
 // Validates an initial condition and builds the sampling parameters.
@@ -427,10 +435,6 @@ qcl_status qcl_sample_initial(const qcl_model* model, const qcl_ensemble_desc* e
   if (ns > 2) {
     SampleN32* s32 = nullptr;
     if (ens->precision == QCL_PREC_FP32_BULK) {
-      if ((size_t)model->n * ns * ns > (size_t)kSampleNK) {
-        delete sp;
-        return fail(QCL_ERR_UNSUPPORTED, "FP32-bulk sampling takes n_modes * n_states^2 <= %d", kSampleNK);
-      }
       s32 = new (std::nothrow) SampleN32();
       if (!s32) {
         delete sp;
@@ -856,10 +860,8 @@ namespace {
 qcl_status check_spawn(const qcl_model* m, const qcl_ensemble_desc* e, int64_t capacity) {
   qcl_status st = check_ens(m, e);
   if (st) return st;
-  if (m->ns != 2 && e->precision == QCL_PREC_FP32_BULK && m->n > 8)
-    return fail(QCL_ERR_UNSUPPORTED, "FP32-bulk spawning of %d-state models takes at most 8 modes (got %d)", m->ns, m->n);
-  if (e->precision == QCL_PREC_FP32_BULK && m->n > 32)
-    return fail(QCL_ERR_UNSUPPORTED, "FP32-bulk spawning takes at most 32 modes (got %d)", m->n);
+  if (m->ns == 2 && e->precision == QCL_PREC_FP32_BULK && m->n > 32)
+    return fail(QCL_ERR_UNSUPPORTED, "FP32-bulk spawning of two-state models takes at most 32 modes (got %d)", m->n);
   if (e->n_traj >= ((int64_t)1 << 31)) return fail(QCL_ERR_INVALID_ARG, "n_traj must be below 2^31 for a spawning ensemble");
   if (capacity < e->n_traj || capacity > ((int64_t)1 << 36))
     return fail(QCL_ERR_INVALID_ARG, "capacity %lld outside [n_traj, 2^36]", (long long)capacity);

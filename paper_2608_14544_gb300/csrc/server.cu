@@ -605,8 +605,6 @@ qcl_status qcl_server_submit(qcl_server* s, const qcl_request_desc* r, int64_t* 
   const qcl_model_desc& m = *r->model;
   if (m.n_states < 2 || m.n_states > QCL_MAX_STATES || m.n_modes < 1 || m.n_modes > QCL_MAX_MODES)
     return fail(QCL_ERR_UNSUPPORTED, "model size outside the built range");
-  if (m.n_states > 2 && m.n_modes > (m.n_states <= 4 ? 32 : 8))
-    return fail(QCL_ERR_UNSUPPORTED, "too many modes for a %d-state FP32-bulk model", m.n_states);
   if (m.repr != QCL_REPR_ADIABATIC && m.repr != QCL_REPR_DIABATIC) return fail(QCL_ERR_INVALID_ARG, "unknown representation %d", m.repr);
   if (m.repr == QCL_REPR_DIABATIC && m.n_states == 2 && m.n_modes > 32)
     return fail(QCL_ERR_UNSUPPORTED, "the diabatic representation takes two-state FP32-bulk models of at most 32 modes");

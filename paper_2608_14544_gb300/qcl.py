@@ -23,6 +23,7 @@ PREC_FP64 = 0
 PREC_FP32_BULK = 1
 OPT_GRID_CAP = 1
 OPT_TIMING = 2
+OPT_MODES_IN_MEMORY = 3
 KERNEL_BULK, KERNEL_FP64_STEP = 0, 1
 FLAG_NONFINITE, FLAG_DEGENERATE, FLAG_STEP_MISMATCH = 1, 2, 4
 

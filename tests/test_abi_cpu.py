@@ -97,9 +97,16 @@ def test_model_validation_without_gpu(lib):
 
 
 def test_option_and_null_checks_without_gpu(lib):
+    from paper_2608_14544_gb300 import qcl
+
     assert lib.qcl_set_option(99, 0) == 1
     assert lib.qcl_set_option(1, -1) == 1
     assert lib.qcl_set_option(1, 0) == 0
+    # where the N_s-state FP32 kernels keep the modes: 0, 1 or 2
+    assert lib.qcl_set_option(qcl.OPT_MODES_IN_MEMORY, 3) == 1
+    assert lib.qcl_set_option(qcl.OPT_MODES_IN_MEMORY, -1) == 1
+    for v in (1, 2, 0):
+        assert lib.qcl_set_option(qcl.OPT_MODES_IN_MEMORY, v) == 0
     assert lib.qcl_launch_count(None, 0) == 1
     c = C.c_int64()
     assert lib.qcl_launch_count(C.byref(c), 0) == 0
