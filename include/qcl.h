@@ -100,8 +100,8 @@ typedef struct {
  *   V_aa - V_bb, mean force -1/2 (dV_aa/dR + dV_bb/dR), transitions a -> g with
  *   amplitude -i V_ga dt/hbar and b -> g with +i V_bg dt/hbar.  The imaginary
  *   unit is carried as a per-walker count of quarter turns (weight
- *   m exp(-i phi) i^q).  Any N_s and mode count (FP32 bulk for two states:
- *   at most 32 modes).  Trajectory spawning takes either representation.  The
+ *   m exp(-i phi) i^q).  Any N_s and mode count in both precisions.
+ *   Trajectory spawning takes either representation.  The
  *   observables keep their layout: diabatic rho_ij (the
  *   walkers' own pairs) and adiabatic rho_ab (rotated at the walker's R by its
  *   eigenvectors, each with its largest-magnitude component positive). */

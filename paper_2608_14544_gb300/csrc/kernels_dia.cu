@@ -1,10 +1,16 @@
 // kernels_dia.cu -- FP32-bulk persistent kernel of the diabatic representation
 // (two states, one thread per walker, up to 32 modes): the same tile body as
 // the adiabatic kernel with the diagonal mean force, the diabatic phase and
-// the quarter-turn transitions (bulk2.cuh, DIA = true).
+// the quarter-turn transitions (bulk2.cuh, DIA = true).  Models of 33..256
+// modes run the split form (kernels_split.cu).
 #include "bulk2.cuh"
 
 namespace qcl {
+
+// (kernels_split.cu)
+int launch_bulk2_split_dia(const BulkParams& bp, const Coef2& cf, void* buf, double* part,
+                           const LaunchShape& ls, cudaStream_t st);
+BulkFn bulk2_split_dia_fn(int n, int kind);
 
 template <int NPL, int KIND, int WPT>
 __global__ void __launch_bounds__(256, (WPT == 1 || NPL <= 4) ? 3 : 2)
@@ -52,7 +58,7 @@ int dispatch_dia(const BulkParams& bp, const Coef2& cf, void* buf, double* part,
   if (n <= 8) return run_dia<8, KIND>(bp, cf, buf, part, ls, st);
   if (n <= 16) return run_dia<16, KIND>(bp, cf, buf, part, ls, st);
   if (n <= 32) return run_dia<32, KIND>(bp, cf, buf, part, ls, st);
-  return 0;
+  return launch_bulk2_split_dia(bp, cf, buf, part, ls, st);
 }
 
 template <int KIND, int WPT>
@@ -69,6 +75,7 @@ BulkFn dia_fn_n(int n) {
 }  // namespace
 
 BulkFn bulk2_dia_fn(int n, int kind, int wpt) {
+  if (n > 32) return bulk2_split_dia_fn(n, kind);
   const bool two = wpt == 2 && n <= 8;
   return kind == 0 ? (two ? dia_fn_n<0, 2>(n) : dia_fn_n<0, 1>(n))
                    : (two ? dia_fn_n<1, 2>(n) : dia_fn_n<1, 1>(n));

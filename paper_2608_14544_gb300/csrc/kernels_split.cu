@@ -1,5 +1,5 @@
 // kernels_split.cu -- many-mode two-state models (33..256 modes) on the FP32
-// bulk path.  A walker's modes are split over L warps (warp role r holds modes
+// bulk path, in either representation.  A walker's modes are split over L warps (warp role r holds modes
 // r NPL .. r NPL + NPL - 1 of the same 32 walker slots); a tile is 256 / L
 // walkers.  Coefficient indices are warp-uniform: compile-time constant-bank
 // operands with one copy of the unrolled code per role, or, where those copies
@@ -313,6 +313,207 @@ __device__ __forceinline__ void split_tiles_v(const BulkParams& bp, const Coef2&
   }
 }
 
+// The diabatic representation (two states, 33..256 modes) on the same split:
+// the diagonal mean force is a constant of the pair, so both half kicks and
+// the drift run in one mode loop, and the transition (a -> 1 - a, b -> 1 - b
+// with amplitude -/+ i b(R_{n+1}) dt / hbar) needs only a(R_{n+1}) and
+// b(R_{n+1}): one exchange of those sums per step, no momentum sums.  The
+// scalar step is the one-thread-per-walker kernel's (dia_phase_and_transition);
+// role 0 keeps the weight's range checked every step (as in the adiabatic split
+// kernel) and observes.
+template <int NPL, int L, int KIND, int ROLE, int WPT, bool SH>
+__device__ __forceinline__ void split_tiles_dia(const BulkParams& bp, const Coef2& cf, W32& ws,
+                                                double* __restrict__ part, void* xbuf,
+                                                double (*red)[8][32], float* obs_rows,
+                                                const float4* scoef, int role_rt) {
+  using V = std::conditional_t<WPT == 2, float2, float>;
+  using U = typename Lanes<V>::U;
+  constexpr int BW = 256 / L;
+  constexpr int G = BW / 32;
+  const int role = SH ? role_rt : ROLE;
+  const int OFF = role * NPL;
+  auto coef = [&](int t) {
+    ModeCoef c;
+    if constexpr (SH) {
+      const float4 c0 = scoef[2 * (OFF + t)], c1 = scoef[2 * (OFF + t) + 1];
+      c = {c0.x, c0.y, c0.z, c0.w, c1.x, c1.y, c1.z};
+    } else {
+      c = {cf.hk[ROLE * NPL + t], cf.dtm[ROLE * NPL + t], cf.am[ROLE * NPL + t],
+           cf.bm[ROLE * NPL + t], cf.a[ROLE * NPL + t],  cf.b[ROLE * NPL + t],
+           cf.hs[ROLE * NPL + t]};
+    }
+    return c;
+  };
+  constexpr int NV = KIND == 1 ? 2 : 1;  // a R (, b R)
+  using X = XBuf<V, L, BW, NV>;
+  using XV = XVec<V, NV>;
+  X* const x = reinterpret_cast<X*>(xbuf);
+  const int64_t nt = bp.n_traj;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int grp = warp % G;
+  const int wslot = grp * 32 + lane;
+  const int bar_id = 1 + grp;
+  int rb = 0;
+  for (int64_t tile0 = (int64_t)blockIdx.x * WPT; tile0 < bp.n_tiles;
+       tile0 += (int64_t)gridDim.x * WPT) {
+    group_sync(bar_id, 32 * L);
+    WalkerV<NPL, V> w;
+    ScalV<V> z;
+    bool active[WPT];
+    PhiloxStream rng[WPT];
+    u4 wd[WPT];
+#pragma unroll
+    for (int k = 0; k < WPT; ++k) {
+      const int64_t i = (tile0 + k) * BW + wslot;
+      active[k] = i < nt;
+      const int64_t ii = active[k] ? i : 0;
+#pragma unroll
+      for (int t = 0; t < NPL; ++t) {
+        const bool on = active[k] && OFF + t < bp.n;
+        ln(w.R[t], k) = on ? ws.R[(int64_t)(OFF + t) * nt + ii] : 0.0f;
+        ln(w.P[t], k) = on ? ws.P[(int64_t)(OFF + t) * nt + ii] : 0.0f;
+      }
+      ln(z.m.hi, k) = active[k] ? ws.mh[ii] : 0.0f;
+      ln(z.m.lo, k) = active[k] ? ws.ml[ii] : 0.0f;
+      ln(z.mexp, k) = active[k] ? ws.me[ii] : 0;
+      ln(z.ph.hi, k) = active[k] ? ws.ph[ii] : 0.0f;
+      ln(z.ph.lo, k) = active[k] ? ws.pl[ii] : 0.0f;
+      const uint32_t ab = active[k] ? ws.ab[ii] : 0u;  // alpha | q << 4 | beta << 8
+      ln(z.sa, k) = sgn(ab & 0xf);
+      ln(z.sb, k) = sgn((ab >> 8) & 0xf);
+      ln(z.q, k) = (int)((ab >> 4) & 3u);
+      rng[k] = PhiloxStream(bp.seed, bp.traj_offset + (uint64_t)ii, kPurposeHop);
+    }
+    auto exchange = [&](X& xb, XV& v) {
+      xb.x[role][wslot] = v;
+      group_sync(bar_id, 32 * L);
+      v = xb.x[0][wslot];
+#pragma unroll
+      for (int r = 1; r < L; ++r) {
+        const XV o = xb.x[r][wslot];
+#pragma unroll
+        for (int c = 0; c < NV; ++c) v.v[c] = vadd(v.v[c], o.v[c]);
+      }
+    };
+    // a(R), b(R): b0 + b R stays b0 for the spin-boson form
+    auto sums = [&](X& xb, XV& v) {
+      exchange(xb, v);
+      z.A = vadd(splat<V>(bp.a0), v.v[0]);
+      z.B = (KIND == 1) ? vadd(splat<V>(bp.b0), v.v[NV - 1]) : splat<V>(bp.b0);
+    };
+    {
+      XV v;
+#pragma unroll
+      for (int c = 0; c < NV; ++c) v.v[c] = splat<V>(0.0f);
+#pragma unroll
+      for (int t = 0; t < NPL; ++t) {
+        const ModeCoef c = coef(t);
+        v.v[0] = vfma(splat<V>(c.a), w.R[t], v.v[0]);
+        if (KIND == 1) v.v[NV - 1] = vfma(splat<V>(c.b), w.R[t], v.v[NV - 1]);
+      }
+      sums(x[0], v);
+    }
+    auto observe = [&](int slot) {
+      if (role == 0) {
+#pragma unroll
+        for (int k = 0; k < WPT; ++k) {
+          Scal zk = lane_of(z, k);
+          observe_warp<true, false>(zk, active[k], obs_rows, wslot, grp * 32, lane,
+                                    red[WPT * rb + k][grp]);
+          set_lane(z, k, zk);
+        }
+      }
+      __syncthreads();
+      if (warp < WPT && tile0 + warp < bp.n_tiles) {
+        const double* r = &red[WPT * rb + warp][0][0];
+        double t0;
+        if (G == 1) t0 = r[lane];
+        else if (G == 2) t0 = r[lane] + r[32 + lane];
+        else t0 = (r[lane] + r[32 + lane]) + (r[64 + lane] + r[96 + lane]);
+        part[((int64_t)slot * bp.n_tiles + tile0 + warp) * 32 + lane] = t0;
+      }
+      rb ^= 1;
+    };
+
+    int slot = bp.obs_first;
+    if (bp.obs_first) observe(0);
+    int to_out = bp.to_out0;
+    uint32_t blk = bp.blk0;
+    int widx = bp.widx0;
+    int xsel = 0;
+#pragma unroll
+    for (int k = 0; k < WPT; ++k) wd[k] = rng[k].draw(blk);
+    for (int it = 0; it < bp.len; ++it) {
+      U word;
+#pragma unroll
+      for (int k = 0; k < WPT; ++k) ln(word, k) = pick_word(wd[k], widx);
+      const V hsab = vmul(splat<V>(bp.hdt * 0.5f), vadd(z.sa, z.sb));
+      XV v;
+#pragma unroll
+      for (int c = 0; c < NV; ++c) v.v[c] = splat<V>(0.0f);
+#pragma unroll
+      for (int t = 0; t < NPL; ++t) {
+        // half kick with the pair's diagonal force, drift, a and b at
+        // R_{n+1}, the second half kick (the same force)
+        const ModeCoef c = coef(t);
+        V p = vfma(splat<V>(-c.hk), w.R[t], w.P[t]);
+        if (KIND == 1) p = vadd(p, splat<V>(-c.hs));
+        p = vfma(hsab, splat<V>(c.a), p);
+        const V r = vfma(splat<V>(c.dtm), p, w.R[t]);
+        w.R[t] = r;
+        v.v[0] = vfma(splat<V>(c.a), r, v.v[0]);
+        if (KIND == 1) v.v[NV - 1] = vfma(splat<V>(c.b), r, v.v[NV - 1]);
+        p = vfma(splat<V>(-c.hk), r, p);
+        if (KIND == 1) p = vadd(p, splat<V>(-c.hs));
+        w.P[t] = vfma(hsab, splat<V>(c.a), p);
+      }
+      const V a_old = z.A;
+      sums(x[1 + xsel], v);
+      xsel ^= 1;
+      if (role == 0) dia_phase_and_transition<true>(z, a_old, z.B, word, bp);
+      else dia_phase_and_transition<false>(z, a_old, z.B, word, bp);
+      if (++widx == 4) {
+        widx = 0;
+        if (role == 0) block_end<false>(z);
+        ++blk;
+        if (it + 1 < bp.len) {
+#pragma unroll
+          for (int k = 0; k < WPT; ++k) wd[k] = rng[k].draw(blk);
+        }
+      }
+      if (--to_out == 0) {
+        observe(slot++);
+        to_out = bp.stride;
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < WPT; ++k) {
+      if (!active[k]) continue;
+      const int64_t i = (tile0 + k) * BW + wslot;
+#pragma unroll
+      for (int t = 0; t < NPL; ++t)
+        if (OFF + t < bp.n) {
+          ws.R[(int64_t)(OFF + t) * nt + i] = ln(w.R[t], k);
+          ws.P[(int64_t)(OFF + t) * nt + i] = ln(w.P[t], k);
+        }
+      if (role == 0) {
+        const float mh = ln(z.m.hi, k), ph = ln(z.ph.hi, k);
+        ws.mh[i] = mh;
+        ws.ml[i] = ln(z.m.lo, k);
+        ws.me[i] = ln(z.mexp, k);
+        ws.ph[i] = ph;
+        ws.pl[i] = ln(z.ph.lo, k);
+        ws.ab[i] = (uint16_t)((ln(z.sa, k) > 0.0f ? 1 : 0) | (ln(z.q, k) << 4) |
+                              ((ln(z.sb, k) > 0.0f ? 1 : 0) << 8));
+        if (!isfinite(mh) || !isfinite(ph)) {
+          atomicAdd(&ws.hdr->n_nonfinite, 1ull);
+          atomicOr(&ws.hdr->flags, QCL_FLAG_NONFINITE);
+        }
+      }
+    }
+  }
+}
+
 }  // namespace
 
 template <int NPL, int L, int KIND, int WPT, int MINB>
@@ -422,6 +623,89 @@ BulkFn bulk2_split_fn(int n, int kind, int wpt) {
   }
   if (n <= 128) return kind == 0 ? split_fn<32, 4, 0, 1>() : split_fn<32, 4, 1, 1>();
   if (n <= 256) return kind == 0 ? split_fn<64, 4, 0, 1>() : split_fn<64, 4, 1, 1>();
+  return nullptr;
+}
+
+// The diabatic split kernel (two states, 33..256 modes): split_tiles_dia over
+// the same roles, tiles and exchange buffers as k_bulk2_split2.
+template <int NPL, int L, int KIND, int WPT, int MINB>
+__global__ void __launch_bounds__(256, MINB)
+    k_bulk2_split_dia(const BulkParams bp, const Coef2 cf, void* buf, double* __restrict__ part) {
+  static_assert(L == 2 || L == 4, "two or four roles");
+  using V = std::conditional_t<WPT == 2, float2, float>;
+  constexpr int BW = 256 / L;
+  __shared__ __align__(16) XBuf<V, L, BW, KIND == 1 ? 2 : 1> xbuf[3];
+  __shared__ double red[2 * WPT][8][32];
+  __shared__ __align__(16) float obs_rows[BW * kObsRow];
+  W32 ws = view32(buf, bp.n_traj, 2, bp.n);
+  if (ws.hdr->step != bp.step0) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) atomicOr(&ws.hdr->flags, QCL_FLAG_STEP_MISMATCH);
+    return;
+  }
+  const int role = (threadIdx.x >> 5) / (BW / 32);
+  if constexpr (split_shared<NPL, L, KIND, WPT>()) {
+    __shared__ float4 scoef[2 * L * NPL];
+    for (int i = threadIdx.x; i < L * NPL; i += blockDim.x) {
+      scoef[2 * i] = make_float4(cf.hk[i], cf.dtm[i], cf.am[i], cf.bm[i]);
+      scoef[2 * i + 1] = make_float4(cf.a[i], cf.b[i], cf.hs[i], 0.0f);
+    }
+    __syncthreads();
+    split_tiles_dia<NPL, L, KIND, 0, WPT, true>(bp, cf, ws, part, xbuf, red, obs_rows, scoef,
+                                                role);
+  } else {
+    if (role == 0)
+      split_tiles_dia<NPL, L, KIND, 0, WPT, false>(bp, cf, ws, part, xbuf, red, obs_rows,
+                                                   nullptr, 0);
+    else if (role == 1)
+      split_tiles_dia<NPL, L, KIND, 1, WPT, false>(bp, cf, ws, part, xbuf, red, obs_rows,
+                                                   nullptr, 1);
+    else if (role == 2)
+      split_tiles_dia<NPL, L, KIND, 2 % L, WPT, false>(bp, cf, ws, part, xbuf, red, obs_rows,
+                                                       nullptr, 2);
+    else
+      split_tiles_dia<NPL, L, KIND, 3 % L, WPT, false>(bp, cf, ws, part, xbuf, red, obs_rows,
+                                                       nullptr, 3);
+  }
+}
+
+namespace {
+// (one walker per thread; two resident blocks per SM for the spin-boson form
+// with at most 32 modes per warp, as in the adiabatic split kernel: the
+// general form would spill at the 128 registers that takes)
+template <int NPL, int L, int KIND>
+BulkFn split_dia_fn() {
+  return k_bulk2_split_dia<NPL, L, KIND, 1, split_minb<NPL, KIND, 1>()>;
+}
+
+template <int NPL, int L, int KIND>
+int run_split_dia(const BulkParams& bp, const Coef2& cf, void* buf, double* part,
+                  const LaunchShape& ls, cudaStream_t st) {
+  static int per_sm = -1, n_sm = 0;
+  return run_bulk_kernel(split_dia_fn<NPL, L, KIND>(), per_sm, n_sm, bp, cf, buf, part, ls, 1, st);
+}
+
+// warps per walker must agree with bulk_lanes(n)
+template <int KIND>
+int dispatch_split_dia(const BulkParams& bp, const Coef2& cf, void* buf, double* part,
+                       const LaunchShape& ls, cudaStream_t st) {
+  const int n = bp.n;
+  if (n <= 64) return run_split_dia<32, 2, KIND>(bp, cf, buf, part, ls, st);
+  if (n <= 128) return run_split_dia<32, 4, KIND>(bp, cf, buf, part, ls, st);
+  if (n <= 256) return run_split_dia<64, 4, KIND>(bp, cf, buf, part, ls, st);
+  return 0;
+}
+}  // namespace
+
+int launch_bulk2_split_dia(const BulkParams& bp, const Coef2& cf, void* buf, double* part,
+                           const LaunchShape& ls, cudaStream_t st) {
+  return bp.kind == 0 ? dispatch_split_dia<0>(bp, cf, buf, part, ls, st)
+                      : dispatch_split_dia<1>(bp, cf, buf, part, ls, st);
+}
+
+BulkFn bulk2_split_dia_fn(int n, int kind) {
+  if (n <= 64) return kind == 0 ? split_dia_fn<32, 2, 0>() : split_dia_fn<32, 2, 1>();
+  if (n <= 128) return kind == 0 ? split_dia_fn<32, 4, 0>() : split_dia_fn<32, 4, 1>();
+  if (n <= 256) return kind == 0 ? split_dia_fn<64, 4, 0>() : split_dia_fn<64, 4, 1>();
   return nullptr;
 }
 

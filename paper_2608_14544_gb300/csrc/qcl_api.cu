@@ -95,8 +95,6 @@ qcl_status check_ens(const qcl_model* m, const qcl_ensemble_desc* e) {
   if (e->n_traj > (int64_t)1 << 40) return fail(QCL_ERR_INVALID_ARG, "n_traj too large");
   if (e->precision != QCL_PREC_FP64 && e->precision != QCL_PREC_FP32_BULK)
     return fail(QCL_ERR_INVALID_ARG, "unknown precision %d", e->precision);
-  if (m->ns == 2 && m->host.repr == QCL_REPR_DIABATIC && e->precision == QCL_PREC_FP32_BULK && m->n > 32)
-    return fail(QCL_ERR_UNSUPPORTED, "diabatic FP32-bulk two-state models support n_modes <= 32 (got %d)", m->n);
   return QCL_OK;
 }
 

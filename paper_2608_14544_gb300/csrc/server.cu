@@ -606,8 +606,6 @@ qcl_status qcl_server_submit(qcl_server* s, const qcl_request_desc* r, int64_t* 
   if (m.n_states < 2 || m.n_states > QCL_MAX_STATES || m.n_modes < 1 || m.n_modes > QCL_MAX_MODES)
     return fail(QCL_ERR_UNSUPPORTED, "model size outside the built range");
   if (m.repr != QCL_REPR_ADIABATIC && m.repr != QCL_REPR_DIABATIC) return fail(QCL_ERR_INVALID_ARG, "unknown representation %d", m.repr);
-  if (m.repr == QCL_REPR_DIABATIC && m.n_states == 2 && m.n_modes > 32)
-    return fail(QCL_ERR_UNSUPPORTED, "the diabatic representation takes two-state FP32-bulk models of at most 32 modes");
   if (!m.mass || !m.omega || !m.E || !m.K || !r->init->rho_el0 || !r->init->R0 || !r->init->P0)
     return fail(QCL_ERR_INVALID_ARG, "a request array is NULL");
   if (r->n_traj < 1 || r->n_steps < 1 || r->out_stride < 1 || !(r->dt > 0.0))
