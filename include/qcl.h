@@ -414,8 +414,8 @@ qcl_status qcl_autotune(qcl_model* model, int64_t probe_walkers, int64_t n_steps
                         qcl_launch_shape* best, void* stream);
 
 /* ---------------------------------------------------------------------------
- * Trajectory spawning (either representation; FP64 for any N_s, FP32 bulk for
- * any N_s, two-state models of at most 32 modes).
+ * Trajectory spawning (either representation, any N_s and mode count, FP64 or
+ * FP32 bulk).
  *
  * The scheme of the CPU code that the paper's GPU version replaces (Sec. II B:
  * there a new trajectory was started each time a transition test fired, so
@@ -582,11 +582,13 @@ qcl_status qcl_server_destroy(qcl_server* s);
  *   QCL_OPT_TIMING    1: record a CUDA event pair on the launching stream around
  *                     every persistent-kernel and FP64 step-kernel launch
  *   QCL_OPT_MODES_IN_MEMORY  where the FP32-bulk N_s-state kernels (N_s > 2)
- *                     keep R and P: 0 (default) the faster form as measured
- *                     for the model's N_s, mode count and representation; 1 in
- *                     the ensemble buffer for every mode count; 2 in registers
- *                     wherever a register form exists (up to 32 modes for
- *                     N_s <= 4, 8 beyond).  Every choice gives the same bits. */
+ *                     and the FP32 spawning steps keep R and P: 0 (default)
+ *                     the faster form as measured for the model's N_s, mode
+ *                     count and representation; 1 in the ensemble buffer for
+ *                     every mode count; 2 in registers wherever a register
+ *                     form exists (N_s-state: up to 32 modes for N_s <= 4, 8
+ *                     beyond; two-state spawning: up to 32).  Every choice
+ *                     gives the same bits. */
 #define QCL_OPT_GRID_CAP 1
 #define QCL_OPT_TIMING 2
 #define QCL_OPT_MODES_IN_MEMORY 3

@@ -27,4 +27,6 @@ qcl_status set_error(qcl_status st, const char* msg);
 qcl_status check_ensemble(const qcl_model* m, const qcl_ensemble_desc* e);
 // The process-wide QCL_OPT_GRID_CAP value.
 int64_t option_grid_cap();
+// The process-wide QCL_OPT_MODES_IN_MEMORY value (0, 1 or 2).
+int option_modes_in_memory();
 }  // namespace qcl

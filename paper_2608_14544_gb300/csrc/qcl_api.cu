@@ -107,6 +107,7 @@ qcl_status set_error(qcl_status st, const char* msg) {
 }
 qcl_status check_ensemble(const qcl_model* m, const qcl_ensemble_desc* e) { return check_ens(m, e); }
 int64_t option_grid_cap() { return g_opt_grid_cap; }
+int option_modes_in_memory() { return g_opt_modes_mem; }
 }  // namespace qcl
 
 extern "C" {
@@ -858,8 +859,6 @@ namespace {
 qcl_status check_spawn(const qcl_model* m, const qcl_ensemble_desc* e, int64_t capacity) {
   qcl_status st = check_ens(m, e);
   if (st) return st;
-  if (m->ns == 2 && e->precision == QCL_PREC_FP32_BULK && m->n > 32)
-    return fail(QCL_ERR_UNSUPPORTED, "FP32-bulk spawning of two-state models takes at most 32 modes (got %d)", m->n);
   if (e->n_traj >= ((int64_t)1 << 31)) return fail(QCL_ERR_INVALID_ARG, "n_traj must be below 2^31 for a spawning ensemble");
   if (capacity < e->n_traj || capacity > ((int64_t)1 << 36))
     return fail(QCL_ERR_INVALID_ARG, "capacity %lld outside [n_traj, 2^36]", (long long)capacity);

@@ -1,11 +1,12 @@
-// spawn32.cu -- trajectory spawning in FP32 bulk precision (two states, up to
-// 32 modes, either representation).  The same scheme and walker order as the
+// spawn32.cu -- trajectory spawning in FP32 bulk precision (two states, any
+// mode count, either representation).  The same scheme and walker order as the
 // FP64 spawning kernels (spawn.cu): one step per launch, a child inserted right
 // after its parent by the deterministic count / scan / scatter; the walker's
 // arithmetic is that of the FP32-bulk kernels (compensated phase and weight
 // pairs with a carried exponent), with the state read from and written to HBM
 // every step.  Family observation in FP64 from the walkers' FP32 contributions.
 #include "bulk2.cuh"
+#include "model.h"
 #include "reduce.cuh"
 
 namespace qcl {
@@ -83,10 +84,17 @@ __global__ void __launch_bounds__(256) k_spawn_sample32(const Sample32 sp, int64
 
 // One step of every live walker of set `src` (in place); children to the
 // per-parent staging, each block's child count to bsum.
+// NPL = 0: the modes stay in memory (any mode count), read and written back
+// mode by mode with the register form's operations in its order (the same
+// bits): one pass for the diabatic step, three for the adiabatic one (a(R_n),
+// b(R_n); first half kick, drift, a and b at R_{n+1}; second half kick and the
+// coupling sums).
 template <int NPL, int KIND, bool DIA>
 __global__ void __launch_bounds__(256) k_spawn_step32(const BulkParams bp, const Coef2 cf,
                                                       void* buf, int64_t cap, int64_t n0,
                                                       int64_t step) {
+  constexpr bool MEM = NPL == 0;
+  constexpr int NR = MEM ? 1 : NPL;
   const SpawnLayout L = SpawnLayout::make(cap, bp.n, n0, QCL_PREC_FP32_BULK);
   EnsHeader* hdr = (EnsHeader*)buf;
   const int src = (int)(step & 1);
@@ -103,7 +111,7 @@ __global__ void __launch_bounds__(256) k_spawn_step32(const BulkParams bp, const
     int flag = 0;
     if (i < n_live) {
       const Set32 s = set32(buf, L, src);
-      Walker<NPL> w;
+      Walker<NR> w;
   #pragma unroll
       for (int j = 0; j < NPL; ++j) {
         const bool on = j < bp.n;
@@ -120,6 +128,13 @@ __global__ void __launch_bounds__(256) k_spawn_step32(const BulkParams bp, const
       z.q = DIA ? (int)((ab >> 4) & 3u) : 0;
       z.A = bp.a0;
       z.B = bp.b0;
+      if constexpr (MEM) {
+        for (int j = 0; j < bp.n; ++j) {
+          const float r = s.R[(int64_t)j * cap + i];
+          z.A = __fmaf_rn(cf.a[j], r, z.A);
+          if (KIND == 1) z.B = __fmaf_rn(cf.b[j], r, z.B);
+        }
+      }
   #pragma unroll
       for (int j = 0; j < NPL; ++j) {
         z.A = __fmaf_rn(cf.a[j], w.R[j], z.A);
@@ -132,7 +147,57 @@ __global__ void __launch_bounds__(256) k_spawn_step32(const BulkParams bp, const
       Scal child;
       bool hop;
       const float hsab = bp.hdt * 0.5f * (z.sa + z.sb);
-      if (DIA) {
+      if constexpr (MEM) {
+        // P += dt/2 F with the pair's force (kick / kick_dia of one mode)
+        auto kick1 = [&](int j, float r, float p, float hu, float hv) {
+          p = __fmaf_rn(-cf.hk[j], r, p);
+          if (KIND == 1) p = __fadd_rn(p, -cf.hs[j]);
+          if (DIA) return __fmaf_rn(hsab, cf.a[j], p);
+          p = __fmaf_rn(hu, -cf.a[j], p);
+          if (KIND == 1) p = __fmaf_rn(hv, -cf.b[j], p);
+          return p;
+        };
+        if (DIA) {
+          const float a_old = z.A;
+          z.A = bp.a0;
+          if (KIND == 1) z.B = bp.b0;
+          for (int j = 0; j < bp.n; ++j) {
+            float r = s.R[(int64_t)j * cap + i], p = s.P[(int64_t)j * cap + i];
+            p = kick1(j, r, p, 0.0f, 0.0f);
+            r = __fmaf_rn(cf.dtm[j], p, r);
+            z.A = __fmaf_rn(cf.a[j], r, z.A);
+            if (KIND == 1) z.B = __fmaf_rn(cf.b[j], r, z.B);
+            s.R[(int64_t)j * cap + i] = r;
+            s.P[(int64_t)j * cap + i] = kick1(j, r, p, 0.0f, 0.0f);
+          }
+          hop = spawn_transition<KIND, true>(z, a_old, 0.0f, z.B, word, bp, deg, child);
+        } else {
+          const float hu = hsab * z.c2, hv = hsab * z.s2;
+          const float r_old = z.r;
+          z.A = bp.a0;
+          z.B = bp.b0;
+          for (int j = 0; j < bp.n; ++j) {
+            float r = s.R[(int64_t)j * cap + i], p = s.P[(int64_t)j * cap + i];
+            p = kick1(j, r, p, hu, hv);
+            r = __fmaf_rn(cf.dtm[j], p, r);
+            z.A = __fmaf_rn(cf.a[j], r, z.A);
+            if (KIND == 1) z.B = __fmaf_rn(cf.b[j], r, z.B);
+            s.R[(int64_t)j * cap + i] = r;
+            s.P[(int64_t)j * cap + i] = p;
+          }
+          closed_form(z);
+          const float hu2 = hsab * z.c2, hv2 = hsab * z.s2;
+          float Av = 0.0f, Bv = 0.0f;
+          for (int j = 0; j < bp.n; ++j) {
+            const float r = s.R[(int64_t)j * cap + i];
+            const float p = kick1(j, r, s.P[(int64_t)j * cap + i], hu2, hv2);
+            Av = __fmaf_rn(cf.am[j], p, Av);
+            if (KIND == 1) Bv = __fmaf_rn(cf.bm[j], p, Bv);
+            s.P[(int64_t)j * cap + i] = p;
+          }
+          hop = spawn_transition<KIND, false>(z, r_old, Av, Bv, word, bp, deg, child);
+        }
+      } else if (DIA) {
         kick_dia<NPL, KIND, Coef2>(w, cf, hsab);
   #pragma unroll
         for (int j = 0; j < NPL; ++j) w.R[j] = __fmaf_rn(cf.dtm[j], w.P[j], w.R[j]);
@@ -370,17 +435,19 @@ void run_step32(const BulkParams& bp, const Coef2& cf, void* buf, int64_t cap, i
   k_spawn_step32<NPL, KIND, DIA><<<spawn_grid(cap), 256, 0, st>>>(bp, cf, buf, cap, n0, step);
 }
 
+// in registers up to 32 modes, beyond that (or under QCL_OPT_MODES_IN_MEMORY = 1)
+// in memory
 template <int KIND, bool DIA>
 int dispatch_step32(const BulkParams& bp, const Coef2& cf, void* buf, int64_t cap, int64_t n0,
                     int64_t step, cudaStream_t st) {
   const int n = bp.n;
-  if (n <= 1) run_step32<1, KIND, DIA>(bp, cf, buf, cap, n0, step, st);
+  if (n > 32 || option_modes_in_memory() == 1) run_step32<0, KIND, DIA>(bp, cf, buf, cap, n0, step, st);
+  else if (n <= 1) run_step32<1, KIND, DIA>(bp, cf, buf, cap, n0, step, st);
   else if (n <= 2) run_step32<2, KIND, DIA>(bp, cf, buf, cap, n0, step, st);
   else if (n <= 4) run_step32<4, KIND, DIA>(bp, cf, buf, cap, n0, step, st);
   else if (n <= 8) run_step32<8, KIND, DIA>(bp, cf, buf, cap, n0, step, st);
   else if (n <= 16) run_step32<16, KIND, DIA>(bp, cf, buf, cap, n0, step, st);
-  else if (n <= 32) run_step32<32, KIND, DIA>(bp, cf, buf, cap, n0, step, st);
-  else return 0;
+  else run_step32<32, KIND, DIA>(bp, cf, buf, cap, n0, step, st);
   return 1;
 }
 

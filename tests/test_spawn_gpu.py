@@ -203,3 +203,54 @@ def test_fp32_spawn_overflow_sets_flag(q):
     run.propagate(300, cfg["dt"], 10)
     assert run.status()["flags"] & q.FLAG_SPAWN_OVERFLOW
     assert n0 <= run.n_live() <= n0 + 40
+
+
+@pytest.mark.parametrize("cfg_id,rep", [(2, "adiabatic"), (2, "diabatic"), (3, "adiabatic")])
+def test_fp32_spawn_modes_in_memory_bitwise_equals_registers(q, cfg_id, rep):
+    """The spawning step's form that keeps R and P in memory (taken beyond 32
+    modes, forced here by QCL_OPT_MODES_IN_MEMORY = 1) against the register
+    form: the same walkers, families and sums, bit for bit."""
+    cfg = _cfg(cfg_id, rep)
+    n0, cap = 2000, 400_000
+    outs = []
+    for mem in (0, 1):
+        q.set_option(q.OPT_MODES_IN_MEMORY, mem)
+        try:
+            run = q.SpawnRun(q.Model(cfg["model"]), n0, cap, 6, 16, precision=q.PREC_FP32_BULK)
+            run.sample(cfg["init"])
+            run.propagate(60, cfg["dt"], 10)
+            run.propagate(90, cfg["dt"], 10)
+        finally:
+            q.set_option(q.OPT_MODES_IN_MEMORY, 0)
+        outs.append((run.sums(), run.state(), run.n_live()))
+    assert outs[0][2] == outs[1][2] and outs[0][2] > n0
+    assert np.array_equal(outs[0][0], outs[1][0])
+    for key in outs[0][1]:
+        assert np.array_equal(outs[0][1][key], outs[1][1][key]), key
+
+
+@pytest.mark.parametrize("rep", ["adiabatic", "diabatic"])
+def test_fp32_spawn_many_modes_match_oracle(q, rep):
+    """FP32 spawning of a 40-mode two-state model (past the 32 modes held in
+    registers) against the oracle's FP64 spawning of the same walkers."""
+    model = wl.random_lvc2(40, seed=40, scale=0.1)
+    model["repr"] = rep
+    init = wl.sb_init(model, beta=2.0)
+    n0, steps, stride, dt = 3000, 150, 10, 0.01
+    cap = 200 * n0
+    run = q.SpawnRun(q.Model(model), n0, cap, 13, steps // stride + 1,
+                     precision=q.PREC_FP32_BULK)
+    run.sample(init)
+    run.propagate(steps, dt, stride)
+    assert run.status()["flags"] == 0
+    obs = run.observables()
+    om = oracle.OracleModel(model)
+    ref, n_live = oracle.run_spawn(om, oracle.OracleInit(om, init), 13, 0, n0, cap, dt, steps,
+                                   stride)
+    mean, se = oracle.finalize(ref, n0)
+    diff = np.abs(obs[:, :16] - mean)
+    se2 = np.hypot(se, obs[:, 16:32])
+    # (256 comparisons: 3.5 combined standard errors)
+    assert np.all(diff <= 3.5 * se2 + 1e-6), (diff / (se2 + 1e-300)).max()
+    assert abs(run.n_live() - n_live[-1]) <= max(5, 0.002 * n_live[-1])
+    assert run.n_live() > 1.1 * n0

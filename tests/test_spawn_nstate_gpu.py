@@ -195,7 +195,7 @@ def test_fp32_spawn_nstate_chunking_is_bitwise_invisible(q):
             assert np.array_equal(st[key], outs[0][1][key]), key
 
 
-def test_fp32_spawn_nstate_overflow_and_mode_limit(q):
+def test_fp32_spawn_nstate_overflow_sets_flag(q):
     model, init, dt = _case("diabatic")
     n0 = 300
     m = q.Model(model)
@@ -204,8 +204,3 @@ def test_fp32_spawn_nstate_overflow_and_mode_limit(q):
     run.propagate(200, dt, 10)
     assert run.status()["flags"] & q.FLAG_SPAWN_OVERFLOW
     assert n0 <= run.n_live() <= n0 + 30
-    # two-state models of more than 32 modes: FP64 spawning only
-    big = wl._model(np.diag([0.0, 0.4]), np.zeros((40, 2, 2)), np.ones(40), np.ones(40),
-                    name="lvc2-40")
-    with pytest.raises(q.QclError, match="at most 32 modes"):
-        q.SpawnRun(q.Model(big), 100, 1000, 1, 2, precision=q.PREC_FP32_BULK)
