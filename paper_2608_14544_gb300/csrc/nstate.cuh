@@ -385,4 +385,70 @@ __device__ __forceinline__ void eigh_warm_fast(const V (&W)[NS][NS], const V (&r
   }
 }
 
+// Decomposition from the identity for the FP32 observation of diabatic walkers
+// (the adiabatic block at the walker's R): the warm kernel's sweeps on W's
+// upper triangle with U starting as the identity.  Full sweeps until every
+// walker of the warp has |a_pq| <= 2^-12 |d| for every pair (at most eight),
+// then one small-angle sweep; eigenvalues ascending, each eigenvector's
+// largest-magnitude component positive (the convention of eigh_ns without a
+// reference).  Takes warp-wide votes: every lane of the warp calls it.
+template <int NS>
+__device__ __forceinline__ void eigh_cold_fast(const float (&W)[NS][NS], float (&e)[NS],
+                                               float (&U)[NS][NS]) {
+  float A[NS][NS];
+#pragma unroll
+  for (int a = 0; a < NS; ++a)
+#pragma unroll
+    for (int b = 0; b < NS; ++b) {
+      A[a][b] = W[a][b];
+      U[a][b] = a == b ? 1.0f : 0.0f;
+    }
+  float tm = 0.0f;
+#pragma unroll 1
+  for (int sweep = 0; sweep < 9; ++sweep) {
+    bool large = false;
+#pragma unroll
+    for (int p = 0; p < NS; ++p)
+#pragma unroll
+      for (int q = p + 1; q < NS; ++q)
+        large |= !(fabsf(A[p][q]) * 4096.0f <= fabsf(A[q][q] - A[p][p]));
+    if (!__any_sync(0xffffffffu, large)) {
+      jacobi_sweep_warm<NS, true, float>(A, U, tm);
+      break;
+    }
+    if (sweep == 8) break;
+    jacobi_sweep_warm<NS, false, float>(A, U, tm);
+  }
+#pragma unroll
+  for (int a = 0; a < NS; ++a) e[a] = A[a][a];
+#pragma unroll
+  for (int i = 1; i < NS; ++i)
+#pragma unroll
+    for (int j = i; j > 0; --j) {
+      const bool sw = e[j] < e[j - 1];
+      const float t0 = e[j], t1 = e[j - 1];
+      e[j] = sw ? t1 : t0;
+      e[j - 1] = sw ? t0 : t1;
+#pragma unroll
+      for (int k = 0; k < NS; ++k) {
+        const float u0 = U[k][j], u1 = U[k][j - 1];
+        U[k][j] = sw ? u1 : u0;
+        U[k][j - 1] = sw ? u0 : u1;
+      }
+    }
+#pragma unroll
+  for (int a = 0; a < NS; ++a) {
+    float vmax = fabsf(U[0][a]), v = U[0][a];
+#pragma unroll
+    for (int i = 1; i < NS; ++i) {
+      const bool g = fabsf(U[i][a]) > vmax;
+      vmax = g ? fabsf(U[i][a]) : vmax;
+      v = g ? U[i][a] : v;
+    }
+    const float sg = v < 0.0f ? -1.0f : 1.0f;
+#pragma unroll
+    for (int i = 0; i < NS; ++i) U[i][a] *= sg;
+  }
+}
+
 }  // namespace qcl

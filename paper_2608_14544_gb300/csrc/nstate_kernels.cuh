@@ -1873,7 +1873,7 @@ __global__ void __launch_bounds__(128, (NPL > 8 || NS > 5) ? 2 : 4)
       for (int a = 0; a < NS; ++a)
 #pragma unroll
         for (int b = 0; b < NS; ++b) W[a][b] = t[tri<NS>(a, b)];
-      eigh_ns<float, NS>(W, nullptr, e, U, 12, 1e-13f);
+      eigh_cold_fast<NS>(W, e, U);  // (every lane: warp votes)
       float* row = &obs_rows[threadIdx.x * 33];
       constexpr int kPassUnroll = NP <= 4 ? NP : 1;
 #pragma unroll kPassUnroll
