@@ -1216,6 +1216,7 @@ __global__ void __launch_bounds__(128, (BulkNMinBlocks<NS, NPL, WPT>::value))
   constexpr int NR = MEM ? 1 : NPL;
   static_assert(!MEM || WPT == 1, "modes in memory: one walker per thread");
   using MR = ModeRow<NS>;
+  constexpr int MU = NS <= 4 ? 4 : 2;  // mode-loop unrolling (loads in flight; registers)
   using V = std::conditional_t<WPT == 2, float2, float>;
   constexpr int NN = NS * NS, NTRI = NS * (NS + 1) / 2;
   constexpr int NP = (4 * NN + 15) / 16;  // observation passes of 32 quantities
@@ -1351,20 +1352,21 @@ __global__ void __launch_bounds__(128, (BulkNMinBlocks<NS, NPL, WPT>::value))
     // order.  Pass A: the first half kick with the force term of Q, the drift
     // and the upper triangle of W(R_{n+1}); pass B: the second half kick with
     // the force term of Q and the sum G = sum_j (P_j/M_j) K_j.
+    // (lanes past the ensemble load walker 0's values, take zeros as the
+    // register form does, and store nothing)
     auto pass_a = [&](const V (&Q)[NTRI], V (&W)[NS][NS]) {
       V t[NTRI];
 #pragma unroll
       for (int k = 0; k < NTRI; ++k) t[k] = splat<V>(cf.E[k]);
-      const int64_t i = iw[0];
-#pragma unroll 2
-      for (int j = 0; j < bp.n; ++j) {
+      float* Rj = ws.R + (active[0] ? iw[0] : 0);
+      float* Pj = ws.P + (active[0] ? iw[0] : 0);
+#pragma unroll MU
+      for (int j = 0; j < bp.n; ++j, Rj += nt, Pj += nt) {
         float kr[MR::CS];
         mode_row<NS>(mtab, j, kr);
         V r = splat<V>(0.0f), p = splat<V>(0.0f);
-        if (active[0]) {
-          ln(r, 0) = ws.R[(int64_t)j * nt + i];
-          ln(p, 0) = ws.P[(int64_t)j * nt + i];
-        }
+        ln(r, 0) = active[0] ? *Rj : 0.0f;
+        ln(p, 0) = active[0] ? *Pj : 0.0f;
         V g = splat<V>(0.0f);
 #pragma unroll
         for (int k = 0; k < NTRI; ++k) g = vfma(splat<V>(kr[k]), Q[k], g);
@@ -1373,8 +1375,8 @@ __global__ void __launch_bounds__(128, (BulkNMinBlocks<NS, NPL, WPT>::value))
 #pragma unroll
         for (int k = 0; k < NTRI; ++k) t[k] = vfma(r, splat<V>(kr[k]), t[k]);
         if (active[0]) {
-          ws.R[(int64_t)j * nt + i] = ln(r, 0);
-          ws.P[(int64_t)j * nt + i] = ln(p, 0);
+          *Rj = ln(r, 0);
+          *Pj = ln(p, 0);
         }
       }
 #pragma unroll
@@ -1385,16 +1387,15 @@ __global__ void __launch_bounds__(128, (BulkNMinBlocks<NS, NPL, WPT>::value))
     auto pass_b = [&](const V (&Q)[NTRI], V (&t)[NTRI]) {
 #pragma unroll
       for (int k = 0; k < NTRI; ++k) t[k] = splat<V>(0.0f);
-      const int64_t i = iw[0];
-#pragma unroll 2
-      for (int j = 0; j < bp.n; ++j) {
+      const float* Rj = ws.R + (active[0] ? iw[0] : 0);
+      float* Pj = ws.P + (active[0] ? iw[0] : 0);
+#pragma unroll MU
+      for (int j = 0; j < bp.n; ++j, Rj += nt, Pj += nt) {
         float kr[MR::CS];
         mode_row<NS>(mtab, j, kr);
         V r = splat<V>(0.0f), p = splat<V>(0.0f);
-        if (active[0]) {
-          ln(r, 0) = ws.R[(int64_t)j * nt + i];
-          ln(p, 0) = ws.P[(int64_t)j * nt + i];
-        }
+        ln(r, 0) = active[0] ? *Rj : 0.0f;
+        ln(p, 0) = active[0] ? *Pj : 0.0f;
         V g = splat<V>(0.0f);
 #pragma unroll
         for (int k = 0; k < NTRI; ++k) g = vfma(splat<V>(kr[k]), Q[k], g);
@@ -1402,7 +1403,7 @@ __global__ void __launch_bounds__(128, (BulkNMinBlocks<NS, NPL, WPT>::value))
         const V v = vmul(p, splat<V>(kr[MR::MINV]));
 #pragma unroll
         for (int k = 0; k < NTRI; ++k) t[k] = vfma(v, splat<V>(kr[k]), t[k]);
-        if (active[0]) ws.P[(int64_t)j * nt + i] = ln(p, 0);
+        if (active[0]) *Pj = ln(p, 0);
       }
     };
     // observation of walker lane l into slot `slot` of tile tile0 + l
@@ -1739,6 +1740,7 @@ __global__ void __launch_bounds__(128, (NPL > 8 || NS > 5) ? 2 : 4)
   constexpr bool MEM = NPL == 0;
   constexpr int NR = MEM ? 1 : NPL;
   using MR = ModeRow<NS>;
+  constexpr int MU = NS <= 4 ? 4 : 2;  // mode-loop unrolling (loads in flight; registers)
   __shared__ double red[2][4][32];
   __shared__ float obs_rows[TW * 33];
   extern __shared__ float4 mode_tab4[];
@@ -1822,13 +1824,16 @@ __global__ void __launch_bounds__(128, (NPL > 8 || NS > 5) ? 2 : 4)
       for (int k = 0; k < NTRI; ++k) t[k] = cf.E[k];
       const int dpa = tri<NS>(pa, pa), dpb = tri<NS>(pb, pb);
       const int da = tri<NS>(al, al), db = tri<NS>(be, be);
-#pragma unroll 2
-      for (int j = 0; j < bp.n; ++j) {
+      // (lanes past the ensemble take zeros, as in the register form)
+      float* Rj = ws.R + (active ? i : 0);
+      float* Pj = ws.P + (active ? i : 0);
+#pragma unroll MU
+      for (int j = 0; j < bp.n; ++j, Rj += nt, Pj += nt) {
         const float* row = mtab + j * MR::CS;
         float kr[MR::CS];
         mode_row<NS>(mtab, j, kr);
-        float r = active ? ws.R[(int64_t)j * nt + i] : 0.0f;
-        float p = active ? ws.P[(int64_t)j * nt + i] : 0.0f;
+        float r = active ? *Rj : 0.0f;
+        float p = active ? *Pj : 0.0f;
         if (pend) p = __fsub_rn(__fmaf_rn(-kr[MR::HK], r, p), __fmul_rn(hh, __fadd_rn(row[dpa], row[dpb])));
         if (step) {
           p = __fsub_rn(__fmaf_rn(-kr[MR::HK], r, p), __fmul_rn(hh, __fadd_rn(row[da], row[db])));
@@ -1837,8 +1842,8 @@ __global__ void __launch_bounds__(128, (NPL > 8 || NS > 5) ? 2 : 4)
 #pragma unroll
         for (int k = 0; k < NTRI; ++k) t[k] = __fmaf_rn(r, kr[k], t[k]);
         if (active && (pend || step)) {
-          ws.R[(int64_t)j * nt + i] = r;
-          ws.P[(int64_t)j * nt + i] = p;
+          *Rj = r;
+          *Pj = p;
         }
       }
     };
@@ -2698,12 +2703,15 @@ struct NStateOps {
   static void spawn_step32_npl(const BulkParams& bp, const CoefN& cf, void* buf, int64_t cap,
                                int64_t n0, int64_t step, cudaStream_t st) {
     // (NPL = 0: the mode table in dynamic shared memory)
-    const size_t dyn = NPL == 0 ? ModeRow<NS>::bytes(bp.n) : 0;
-    static size_t dyn_set = 0;
-    if (dyn > dyn_set) {
-      cudaFuncSetAttribute(k_spawnN_step32<NS, NPL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           (int)dyn);
-      dyn_set = dyn;
+    size_t dyn = 0;
+    if constexpr (NPL == 0) {
+      dyn = ModeRow<NS>::bytes(bp.n);
+      static size_t dyn_set = 0;
+      if (dyn > dyn_set) {
+        cudaFuncSetAttribute(k_spawnN_step32<NS, NPL>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
+        dyn_set = dyn;
+      }
     }
     k_spawnN_step32<NS, NPL><<<spawn_grid(cap), 256, dyn, st>>>(bp, cf, buf, cap, n0, step);
   }

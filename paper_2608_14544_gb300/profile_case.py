@@ -5,6 +5,7 @@ the measurements.
 
   python -m paper_2608_14544_gb300.profile_case --config 2 --n-traj 1048576 --steps 160
   python -m paper_2608_14544_gb300.profile_case --config 2 --served --repeat 2
+  python -m paper_2608_14544_gb300.profile_case --config lvc4 --modes 64 --n-traj 262144
 """
 from __future__ import annotations
 
@@ -26,6 +27,9 @@ def main():
                     help="> 0: a spawning ensemble with this many walker slots per initial walker")
     ap.add_argument("--served", action="store_true",
                     help="submit the solve to the request server (qcl_server_submit / wait)")
+    ap.add_argument("--modes", type=int, default=6, help="modes of the lvc4 model")
+    ap.add_argument("--modes-in-memory", type=int, default=0, choices=[0, 1, 2],
+                    help="QCL_OPT_MODES_IN_MEMORY (0: measured choice, 1: memory, 2: registers)")
     args = ap.parse_args()
 
     import torch
@@ -35,7 +39,8 @@ def main():
 
     build.build()
     torch.cuda.set_device(0)
-    cfg = wl.lvc4_config(1) if args.config == "lvc4" else wl.config(int(args.config))
+    qcl.set_option(qcl.OPT_MODES_IN_MEMORY, args.modes_in_memory)
+    cfg = wl.lvc4_config(1, args.modes) if args.config == "lvc4" else wl.config(int(args.config))
     cfg["model"]["repr"] = args.repr
     n = args.n_traj or cfg["n_traj"]
     steps = args.steps or cfg["n_steps"]

@@ -108,12 +108,16 @@ def vibronic_init(model):
 
 
 def random_lvc4(request_id: int, n_modes: int = 6):
+    """Random four-state LVC model: unit masses, frequencies ~ U(0.5, 2),
+    E = diag(0, 0.5, 1, 1.5), K_j with entries ~ U(0, 0.2) scaled by
+    sqrt(6 / n_modes) (the six-mode coupling strength for any mode count)."""
     rng = np.random.default_rng(request_id)
     omega = rng.uniform(0.5, 2.0, size=n_modes)
     E = np.diag([0.0, 0.5, 1.0, 1.5])
     K = np.zeros((n_modes, 4, 4))
+    scale = 1.0 if n_modes == 6 else math.sqrt(6.0 / n_modes)
     for j in range(n_modes):
-        a = rng.uniform(0.0, 0.2, size=(4, 4))
+        a = rng.uniform(0.0, 0.2, size=(4, 4)) * scale
         K[j] = np.triu(a) + np.triu(a, 1).T
     return _model(E, K, np.ones(n_modes), omega, name=f"random-lvc4-{request_id}")
 
@@ -155,8 +159,8 @@ def config(idx: int):
     raise ValueError(idx)
 
 
-def lvc4_config(request_id: int):
-    m = random_lvc4(request_id)
+def lvc4_config(request_id: int, n_modes: int = 6):
+    m = random_lvc4(request_id, n_modes)
     return dict(name="lvc4", model=m, init=sb_init(m), n_traj=10_000, dt=0.01, n_steps=1000,
                 out_stride=10, seed=request_id, precision="fp32")
 
