@@ -34,8 +34,15 @@ def _cases():
     c80 = copy.deepcopy(c3)
     c80["model"] = wl.random_lvc2(80, 5, 0.1)
     c80["init"] = wl.sb_init(c80["model"], beta=2.0)
+    c4d = copy.deepcopy(c4)
+    c4d["model"]["repr"] = "diabatic"
+    lvc40 = wl.lvc4_config(2, 40)
+    lvc40d = copy.deepcopy(lvc40)
+    lvc40d["model"]["repr"] = "diabatic"
     return [("sb3", c2), ("vib3", c3), ("sb3-diabatic", d2), ("lvc2-6mode", c6),
-            ("lvc4", wl.lvc4_config(2)), ("sb100-split", c4), ("lvc2-80mode-split", c80)]
+            ("lvc4", wl.lvc4_config(2)), ("sb100-split", c4), ("lvc2-80mode-split", c80),
+            ("sb100-diabatic-split", c4d), ("lvc4-40mode-in-memory", lvc40),
+            ("lvc4-40mode-diabatic-in-memory", lvc40d)]
 
 
 @pytest.mark.parametrize("name,cfg", _cases())
