@@ -635,6 +635,13 @@ def run_ours(args):
                                         peak_tflops),
                              workload="100-mode ohmic spin-boson (eps=Delta=1, xi=0.25, wc=5, "
                                       "beta=1)")
+    if args.sb100_walkers > 0:
+        c4d = copy.deepcopy(wl.config(4))
+        c4d["model"]["repr"] = "diabatic"
+        legs["sb100_diabatic"] = dict(
+            config_leg(qcl, torch, c4d, args.sb100_walkers, stream, peak_tflops, counted=False),
+            workload="the 100-mode model in the diabatic representation (the split kernel's "
+                     "diabatic form; no per-unit flop figure in the scope)")
     cd = copy.deepcopy(cfg)
     cd["model"]["repr"] = "diabatic"
     legs["diabatic"] = dict(config_leg(qcl, torch, cd, n, stream, peak_tflops),
@@ -650,6 +657,11 @@ def run_ours(args):
             config_leg(qcl, torch, c4d, args.nstate_walkers, stream, peak_tflops, counted=False),
             workload="the same model in the diabatic representation (no decomposition in the "
                      "step; no per-unit flop figure in the scope)")
+        c64 = wl.lvc4_config(1, 64)
+        legs["lvc4_64modes"] = dict(
+            config_leg(qcl, torch, c64, args.nstate_walkers, stream, peak_tflops, counted=False),
+            workload="random four-state 64-mode LVC model (R and P kept in the ensemble buffer "
+                     "by the modes-in-memory kernel), 1000 steps, outputs every 10")
     if args.spawn_walkers > 0:
         legs["spawning"] = spawning_leg(qcl, torch, wl.config(1), args.spawn_walkers, 400, 20)
         # (horizon, initial spawning walkers, slots per initial walker): the

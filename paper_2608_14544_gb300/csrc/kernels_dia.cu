@@ -10,7 +10,7 @@ namespace qcl {
 // (kernels_split.cu)
 int launch_bulk2_split_dia(const BulkParams& bp, const Coef2& cf, void* buf, double* part,
                            const LaunchShape& ls, cudaStream_t st);
-BulkFn bulk2_split_dia_fn(int n, int kind);
+BulkFn bulk2_split_dia_fn(int n, int kind, int wpt);
 
 template <int NPL, int KIND, int WPT>
 __global__ void __launch_bounds__(256, (WPT == 1 || NPL <= 4) ? 3 : 2)
@@ -75,7 +75,7 @@ BulkFn dia_fn_n(int n) {
 }  // namespace
 
 BulkFn bulk2_dia_fn(int n, int kind, int wpt) {
-  if (n > 32) return bulk2_split_dia_fn(n, kind);
+  if (n > 32) return bulk2_split_dia_fn(n, kind, wpt);
   const bool two = wpt == 2 && n <= 8;
   return kind == 0 ? (two ? dia_fn_n<0, 2>(n) : dia_fn_n<0, 1>(n))
                    : (two ? dia_fn_n<1, 2>(n) : dia_fn_n<1, 1>(n));

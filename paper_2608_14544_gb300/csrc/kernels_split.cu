@@ -669,19 +669,30 @@ __global__ void __launch_bounds__(256, MINB)
 }
 
 namespace {
-// (one walker per thread; two resident blocks per SM for the spin-boson form
-// with at most 32 modes per warp, as in the adiabatic split kernel: the
+// (two resident blocks per SM for the spin-boson form with at most 32 modes
+// per warp and one walker per thread, as in the adiabatic split kernel: the
 // general form would spill at the 128 registers that takes)
-template <int NPL, int L, int KIND>
+template <int NPL, int L, int KIND, int WPT>
 BulkFn split_dia_fn() {
-  return k_bulk2_split_dia<NPL, L, KIND, 1, split_minb<NPL, KIND, 1>()>;
+  return k_bulk2_split_dia<NPL, L, KIND, WPT, split_minb<NPL, KIND, WPT>()>;
 }
 
+// Two walkers per thread (packed FP32x2 lanes) where a warp holds at most 25
+// modes, as in the adiabatic split kernel; otherwise one.
 template <int NPL, int L, int KIND>
 int run_split_dia(const BulkParams& bp, const Coef2& cf, void* buf, double* part,
                   const LaunchShape& ls, cudaStream_t st) {
-  static int per_sm = -1, n_sm = 0;
-  return run_bulk_kernel(split_dia_fn<NPL, L, KIND>(), per_sm, n_sm, bp, cf, buf, part, ls, 1, st);
+  static int per_sm[2] = {-1, -1}, n_sm[2] = {0, 0};
+  if constexpr (NPL <= 25) {
+    int wpt = (ls.wpt > 0 ? ls.wpt : 2) >= 2 ? 2 : 1;
+    if (wpt == 2)
+      wpt = bulk_wpt(split_dia_fn<NPL, L, KIND, 2>(), per_sm[1], n_sm[1], bp.n_tiles, ls);
+    if (wpt == 2)
+      return run_bulk_kernel(split_dia_fn<NPL, L, KIND, 2>(), per_sm[1], n_sm[1], bp, cf, buf,
+                             part, ls, 2, st);
+  }
+  return run_bulk_kernel(split_dia_fn<NPL, L, KIND, 1>(), per_sm[0], n_sm[0], bp, cf, buf, part,
+                         ls, 1, st);
 }
 
 // warps per walker must agree with bulk_lanes(n)
@@ -690,6 +701,7 @@ int dispatch_split_dia(const BulkParams& bp, const Coef2& cf, void* buf, double*
                        const LaunchShape& ls, cudaStream_t st) {
   const int n = bp.n;
   if (n <= 64) return run_split_dia<32, 2, KIND>(bp, cf, buf, part, ls, st);
+  if (n <= 100) return run_split_dia<25, 4, KIND>(bp, cf, buf, part, ls, st);
   if (n <= 128) return run_split_dia<32, 4, KIND>(bp, cf, buf, part, ls, st);
   if (n <= 256) return run_split_dia<64, 4, KIND>(bp, cf, buf, part, ls, st);
   return 0;
@@ -702,10 +714,15 @@ int launch_bulk2_split_dia(const BulkParams& bp, const Coef2& cf, void* buf, dou
                       : dispatch_split_dia<1>(bp, cf, buf, part, ls, st);
 }
 
-BulkFn bulk2_split_dia_fn(int n, int kind) {
-  if (n <= 64) return kind == 0 ? split_dia_fn<32, 2, 0>() : split_dia_fn<32, 2, 1>();
-  if (n <= 128) return kind == 0 ? split_dia_fn<32, 4, 0>() : split_dia_fn<32, 4, 1>();
-  if (n <= 256) return kind == 0 ? split_dia_fn<64, 4, 0>() : split_dia_fn<64, 4, 1>();
+BulkFn bulk2_split_dia_fn(int n, int kind, int wpt) {
+  const bool two = wpt == 2 && n > 64 && n <= 100;
+  if (n <= 64) return kind == 0 ? split_dia_fn<32, 2, 0, 1>() : split_dia_fn<32, 2, 1, 1>();
+  if (n <= 100) {
+    if (kind == 0) return two ? split_dia_fn<25, 4, 0, 2>() : split_dia_fn<25, 4, 0, 1>();
+    return two ? split_dia_fn<25, 4, 1, 2>() : split_dia_fn<25, 4, 1, 1>();
+  }
+  if (n <= 128) return kind == 0 ? split_dia_fn<32, 4, 0, 1>() : split_dia_fn<32, 4, 1, 1>();
+  if (n <= 256) return kind == 0 ? split_dia_fn<64, 4, 0, 1>() : split_dia_fn<64, 4, 1, 1>();
   return nullptr;
 }
 

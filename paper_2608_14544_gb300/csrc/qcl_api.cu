@@ -772,8 +772,8 @@ qcl_status qcl_autotune(qcl_model* model, int64_t probe_walkers, int64_t n_steps
   const qcl_init_desc init{rho.data(), zero.data(), zero.data(), INFINITY, 1, 0};
   // candidates: walkers per thread, then blocks per SM up to the occupancy limit
   const bool dia = model->host.repr == QCL_REPR_DIABATIC;
-  const bool two_state_reg = ns == 2 && (dia ? n <= 32 : (n <= 8 || (n > 32 && n <= 256)));
-  const int wmax = (ns == 2 && (dia ? n <= 8 : max_wpt(n) == 2)) ? 2 : 1;
+  const bool two_state_reg = ns == 2 && (dia ? n <= 256 : (n <= 8 || (n > 32 && n <= 256)));
+  const int wmax = (ns == 2 && max_wpt(n) == 2) ? 2 : 1;
   const int keep_wpt = model->shape_wpt, keep_bps = model->shape_bps, keep_outs = model->shape_outs;
   const double keep_rate = model->shape_rate;
   cudaStream_t s = (cudaStream_t)stream;
