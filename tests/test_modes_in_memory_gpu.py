@@ -76,7 +76,8 @@ def test_modes_in_memory_bitwise_equals_registers(q, ns, n, rep):
 
 
 _MANY = [(3, 40, "adiabatic"), (3, 40, "diabatic"), (6, 12, "adiabatic"),
-         (8, 10, "diabatic"), (5, 64, "adiabatic")]
+         (8, 10, "diabatic"), (5, 64, "adiabatic"), (8, 40, "adiabatic"),
+         (4, 256, "diabatic")]
 
 
 @pytest.mark.parametrize("ns,n,rep", _MANY)
