@@ -1,5 +1,7 @@
 // nstate_kernels.cuh -- models with N_s = 3..8 electronic states: sampling,
-// the FP64 one-launch-per-step path and the FP32-bulk persistent kernel.
+// the FP64 one-launch-per-step path, the FP32-bulk persistent kernels (the
+// walker's modes in registers, or for any mode count in the ensemble buffer)
+// and trajectory spawning in both precisions.
 // The per-step algorithm is the two-state one with the closed form replaced by
 // a Jacobi decomposition carried along the trajectory (nstate.cuh):
 // velocity Verlet on the mean force -1/2 (F_a + F_b), trapezoid phase
@@ -2041,8 +2043,8 @@ __global__ void __launch_bounds__(128, (NPL > 8 || NS > 5) ? 2 : 4)
 
 // ------------------------------------------------------ FP32 spawning, N_s --
 // Trajectory spawning for N_s-state models in FP32 bulk precision (either
-// representation, up to 8 modes): one step per launch with the walker state in
-// HBM, the walker arithmetic of the FP32 N_s-state kernels (the carried
+// representation, any mode count: up to 8 modes in registers, beyond that in
+// memory): one step per launch with the walker state in HBM, the walker arithmetic of the FP32 N_s-state kernels (the carried
 // eigenvectors and eigenvalues warm-start each decomposition; the diabatic
 // step needs none), compensated FP32 weight and phase pairs with a carried
 // exponent.  A fired test stages a child (weight m A_e / p_hat_e, the event's
