@@ -104,3 +104,19 @@ def test_noalloc_rejects_walker_counts_beyond_the_static_scratch(q):
     with pytest.raises(q.QclError) as e:
         q.propagate_noalloc(m, fp64, buf64, 0, 10, cfg["dt"], 10, rows, n_out)
     assert e.value.status == 2 and "FP32-bulk" in q.last_error()
+
+
+def test_noalloc_diabatic_many_mode_matches_propagate(q):
+    """The diabatic representation of the 100-mode model (the split kernel's
+    diabatic form, 64-walker tiles) through the no-allocation call: the same
+    rows and walker states as qcl_propagate."""
+    import copy
+
+    cfg = copy.deepcopy(wl.config(4))
+    cfg["model"]["repr"] = "diabatic"
+    stride = cfg["out_stride"]
+    ref, ref_state = _reference_rows(q, cfg, 30_001, 7, (60, 40), stride)
+    got, got_state = _noalloc_rows(q, cfg, 30_001, 7, (60, 40), stride)
+    assert np.array_equal(got, ref)
+    for k in ref_state:
+        assert np.array_equal(got_state[k], ref_state[k]), k
