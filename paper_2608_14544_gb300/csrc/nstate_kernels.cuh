@@ -1354,31 +1354,64 @@ __global__ void __launch_bounds__(128, (BulkNMinBlocks<NS, NPL, WPT>::value))
     // order.  Pass A: the first half kick with the force term of Q, the drift
     // and the upper triangle of W(R_{n+1}); pass B: the second half kick with
     // the force term of Q and the sum G = sum_j (P_j/M_j) K_j.
-    // (lanes past the ensemble load walker 0's values, take zeros as the
-    // register form does, and store nothing)
+    // Each pass loads R and P of MU modes before computing them and stores them
+    // after, so that a batch's loads are not ordered behind the previous
+    // mode's stores (lanes past the ensemble load walker 0's values, take
+    // zeros as the register form does, and store nothing).
+    auto mode_a = [&](int jj, const V (&Q)[NTRI], V (&t)[NTRI], V& r, V& p) {
+      float kr[MR::CS];
+      mode_row<NS>(mtab, jj, kr);
+      V g = splat<V>(0.0f);
+#pragma unroll
+      for (int k = 0; k < NTRI; ++k) g = vfma(splat<V>(kr[k]), Q[k], g);
+      p = vsub(vfma(splat<V>(-kr[MR::HK]), r, p), g);
+      r = vfma(splat<V>(kr[MR::DTM]), p, r);
+#pragma unroll
+      for (int k = 0; k < NTRI; ++k) t[k] = vfma(r, splat<V>(kr[k]), t[k]);
+    };
+    auto mode_b = [&](int jj, const V (&Q)[NTRI], V (&t)[NTRI], V r, V& p) {
+      float kr[MR::CS];
+      mode_row<NS>(mtab, jj, kr);
+      V g = splat<V>(0.0f);
+#pragma unroll
+      for (int k = 0; k < NTRI; ++k) g = vfma(splat<V>(kr[k]), Q[k], g);
+      p = vsub(vfma(splat<V>(-kr[MR::HK]), r, p), g);
+      const V v = vmul(p, splat<V>(kr[MR::MINV]));
+#pragma unroll
+      for (int k = 0; k < NTRI; ++k) t[k] = vfma(v, splat<V>(kr[k]), t[k]);
+    };
     auto pass_a = [&](const V (&Q)[NTRI], V (&W)[NS][NS]) {
       V t[NTRI];
 #pragma unroll
       for (int k = 0; k < NTRI; ++k) t[k] = splat<V>(cf.E[k]);
-      float* Rj = ws.R + (active[0] ? iw[0] : 0);
-      float* Pj = ws.P + (active[0] ? iw[0] : 0);
-#pragma unroll MU
-      for (int j = 0; j < bp.n; ++j, Rj += nt, Pj += nt) {
-        float kr[MR::CS];
-        mode_row<NS>(mtab, j, kr);
-        V r = splat<V>(0.0f), p = splat<V>(0.0f);
-        ln(r, 0) = active[0] ? *Rj : 0.0f;
-        ln(p, 0) = active[0] ? *Pj : 0.0f;
-        V g = splat<V>(0.0f);
+      float* R0 = ws.R + (active[0] ? iw[0] : 0);
+      float* P0 = ws.P + (active[0] ? iw[0] : 0);
+      int j = 0;
+      for (; j + MU <= bp.n; j += MU, R0 += MU * nt, P0 += MU * nt) {
+        V rb[MU], pb[MU];
 #pragma unroll
-        for (int k = 0; k < NTRI; ++k) g = vfma(splat<V>(kr[k]), Q[k], g);
-        p = vsub(vfma(splat<V>(-kr[MR::HK]), r, p), g);
-        r = vfma(splat<V>(kr[MR::DTM]), p, r);
+        for (int u = 0; u < MU; ++u) {
+          ln(rb[u], 0) = active[0] ? R0[u * nt] : 0.0f;
+          ln(pb[u], 0) = active[0] ? P0[u * nt] : 0.0f;
+        }
 #pragma unroll
-        for (int k = 0; k < NTRI; ++k) t[k] = vfma(r, splat<V>(kr[k]), t[k]);
+        for (int u = 0; u < MU; ++u) mode_a(j + u, Q, t, rb[u], pb[u]);
         if (active[0]) {
-          *Rj = ln(r, 0);
-          *Pj = ln(p, 0);
+#pragma unroll
+          for (int u = 0; u < MU; ++u) {
+            R0[u * nt] = ln(rb[u], 0);
+            P0[u * nt] = ln(pb[u], 0);
+          }
+        }
+      }
+      for (; j < bp.n; ++j, R0 += nt, P0 += nt) {
+        V r, p;
+        ln(r, 0) = active[0] ? *R0 : 0.0f;
+        ln(p, 0) = active[0] ? *P0 : 0.0f;
+        mode_a(j, Q, t, r, p);
+        if (active[0]) {
+          *R0 = ln(r, 0);
+          *P0 = ln(p, 0);
         }
       }
 #pragma unroll
@@ -1389,23 +1422,29 @@ __global__ void __launch_bounds__(128, (BulkNMinBlocks<NS, NPL, WPT>::value))
     auto pass_b = [&](const V (&Q)[NTRI], V (&t)[NTRI]) {
 #pragma unroll
       for (int k = 0; k < NTRI; ++k) t[k] = splat<V>(0.0f);
-      const float* Rj = ws.R + (active[0] ? iw[0] : 0);
-      float* Pj = ws.P + (active[0] ? iw[0] : 0);
-#pragma unroll MU
-      for (int j = 0; j < bp.n; ++j, Rj += nt, Pj += nt) {
-        float kr[MR::CS];
-        mode_row<NS>(mtab, j, kr);
-        V r = splat<V>(0.0f), p = splat<V>(0.0f);
-        ln(r, 0) = active[0] ? *Rj : 0.0f;
-        ln(p, 0) = active[0] ? *Pj : 0.0f;
-        V g = splat<V>(0.0f);
+      const float* R0 = ws.R + (active[0] ? iw[0] : 0);
+      float* P0 = ws.P + (active[0] ? iw[0] : 0);
+      int j = 0;
+      for (; j + MU <= bp.n; j += MU, R0 += MU * nt, P0 += MU * nt) {
+        V rb[MU], pb[MU];
 #pragma unroll
-        for (int k = 0; k < NTRI; ++k) g = vfma(splat<V>(kr[k]), Q[k], g);
-        p = vsub(vfma(splat<V>(-kr[MR::HK]), r, p), g);
-        const V v = vmul(p, splat<V>(kr[MR::MINV]));
+        for (int u = 0; u < MU; ++u) {
+          ln(rb[u], 0) = active[0] ? R0[u * nt] : 0.0f;
+          ln(pb[u], 0) = active[0] ? P0[u * nt] : 0.0f;
+        }
 #pragma unroll
-        for (int k = 0; k < NTRI; ++k) t[k] = vfma(v, splat<V>(kr[k]), t[k]);
-        if (active[0]) *Pj = ln(p, 0);
+        for (int u = 0; u < MU; ++u) mode_b(j + u, Q, t, rb[u], pb[u]);
+        if (active[0]) {
+#pragma unroll
+          for (int u = 0; u < MU; ++u) P0[u * nt] = ln(pb[u], 0);
+        }
+      }
+      for (; j < bp.n; ++j, R0 += nt, P0 += nt) {
+        V r, p;
+        ln(r, 0) = active[0] ? *R0 : 0.0f;
+        ln(p, 0) = active[0] ? *P0 : 0.0f;
+        mode_b(j, Q, t, r, p);
+        if (active[0]) *P0 = ln(p, 0);
       }
     };
     // observation of walker lane l into slot `slot` of tile tile0 + l
@@ -1826,16 +1865,10 @@ __global__ void __launch_bounds__(128, (NPL > 8 || NS > 5) ? 2 : 4)
       for (int k = 0; k < NTRI; ++k) t[k] = cf.E[k];
       const int dpa = tri<NS>(pa, pa), dpb = tri<NS>(pb, pb);
       const int da = tri<NS>(al, al), db = tri<NS>(be, be);
-      // (lanes past the ensemble take zeros, as in the register form)
-      float* Rj = ws.R + (active ? i : 0);
-      float* Pj = ws.P + (active ? i : 0);
-#pragma unroll MU
-      for (int j = 0; j < bp.n; ++j, Rj += nt, Pj += nt) {
-        const float* row = mtab + j * MR::CS;
+      auto mode = [&](int jj, float& r, float& p) {
+        const float* row = mtab + jj * MR::CS;
         float kr[MR::CS];
-        mode_row<NS>(mtab, j, kr);
-        float r = active ? *Rj : 0.0f;
-        float p = active ? *Pj : 0.0f;
+        mode_row<NS>(mtab, jj, kr);
         if (pend) p = __fsub_rn(__fmaf_rn(-kr[MR::HK], r, p), __fmul_rn(hh, __fadd_rn(row[dpa], row[dpb])));
         if (step) {
           p = __fsub_rn(__fmaf_rn(-kr[MR::HK], r, p), __fmul_rn(hh, __fadd_rn(row[da], row[db])));
@@ -1843,9 +1876,36 @@ __global__ void __launch_bounds__(128, (NPL > 8 || NS > 5) ? 2 : 4)
         }
 #pragma unroll
         for (int k = 0; k < NTRI; ++k) t[k] = __fmaf_rn(r, kr[k], t[k]);
-        if (active && (pend || step)) {
-          *Rj = r;
-          *Pj = p;
+      };
+      // batches of MU modes: loads before the batch's arithmetic, stores after
+      // (lanes past the ensemble take zeros, as in the register form)
+      const bool store = active && (pend || step);
+      float* R0 = ws.R + (active ? i : 0);
+      float* P0 = ws.P + (active ? i : 0);
+      int j = 0;
+      for (; j + MU <= bp.n; j += MU, R0 += MU * nt, P0 += MU * nt) {
+        float rb[MU], pb[MU];
+#pragma unroll
+        for (int u = 0; u < MU; ++u) {
+          rb[u] = active ? R0[u * nt] : 0.0f;
+          pb[u] = active ? P0[u * nt] : 0.0f;
+        }
+#pragma unroll
+        for (int u = 0; u < MU; ++u) mode(j + u, rb[u], pb[u]);
+        if (store) {
+#pragma unroll
+          for (int u = 0; u < MU; ++u) {
+            R0[u * nt] = rb[u];
+            P0[u * nt] = pb[u];
+          }
+        }
+      }
+      for (; j < bp.n; ++j, R0 += nt, P0 += nt) {
+        float r = active ? *R0 : 0.0f, p = active ? *P0 : 0.0f;
+        mode(j, r, p);
+        if (store) {
+          *R0 = r;
+          *P0 = p;
         }
       }
     };
