@@ -8,6 +8,7 @@
 // (e_a - e_b)/hbar, and one transition among the 2 (N_s - 1) events of the
 // coupling term of Eq. 1.
 #pragma once
+#include <mutex>
 #include <type_traits>
 
 #include "kernels.h"
@@ -2768,7 +2769,9 @@ struct NStateOps {
     size_t dyn = 0;
     if constexpr (NPL == 0) {
       dyn = ModeRow<NS>::bytes(bp.n);
+      static std::mutex mu;
       static size_t dyn_set = 0;
+      std::lock_guard<std::mutex> lock(mu);
       if (dyn > dyn_set) {
         cudaFuncSetAttribute(k_spawnN_step32<NS, NPL>,
                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
@@ -2820,21 +2823,39 @@ struct NStateOps {
   }
   // one persistent grid: the occupancy limit of resident blocks on every SM
   // (capped), at most one block per WPT tiles
+  // (dyn > 0, the modes-in-memory kernels: the shared-memory limit only grows
+  // and the occupancy is computed for this call's table, under a lock, so
+  // that threads launching models of different mode counts do not race)
   template <typename Fn>
   static int launch_persistent(Fn fn, int& per_sm, int& n_sm, size_t& dyn_at, const BulkParams& bp,
                                const CoefN& cf, void* buf, double* part, int grid_cap, int WPT,
                                size_t dyn, cudaStream_t st) {
-    if (per_sm < 0 || dyn != dyn_at) {
+    int blocks = per_sm;
+    if (dyn > 0) {
+      static std::mutex mu;
+      std::lock_guard<std::mutex> lock(mu);
+      if (n_sm == 0) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
+      }
+      if (dyn > dyn_at) {
+        cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
+        dyn_at = dyn;
+      }
+      if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, fn, 128, dyn) != cudaSuccess ||
+          blocks < 1)
+        blocks = 1;
+    } else if (per_sm < 0) {
       int dev = 0;
       cudaGetDevice(&dev);
       cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
-      if (dyn > 0) cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
-      if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, 128, dyn) != cudaSuccess ||
-          per_sm < 1)
-        per_sm = 1;
-      dyn_at = dyn;
+      if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, fn, 128, 0) != cudaSuccess ||
+          blocks < 1)
+        blocks = 1;
+      per_sm = blocks;
     }
-    int64_t grid = (int64_t)per_sm * n_sm;
+    int64_t grid = (int64_t)blocks * n_sm;
     if (grid_cap > 0 && grid > grid_cap) grid = grid_cap;
     const int64_t units = (bp.n_tiles + WPT - 1) / WPT;
     if (grid > units) grid = units;
