@@ -328,9 +328,8 @@ void launch_spawnN_step(const DevModel* dm, int ns, void* buf, int64_t capacity,
                         int64_t step0, int64_t step, double dt, uint64_t seed, cudaStream_t st);
 void launch_spawnN_observe(const DevModel* dm, int ns, const void* buf, int64_t capacity, int n,
                            int64_t n0, int set, double* part, cudaStream_t st);
-// FP32-bulk spawning for N_s = 3..8 states (either representation, n <= 8
-// modes; kernels in nstate_kernels.cuh): sample, one step (0 if no kernel for
-// n), observation.
+// FP32-bulk spawning for N_s = 3..8 states (either representation, any mode
+// count; kernels in nstate_spawn32.cuh): sample, one step, observation.
 void launch_spawnN_sample32(int ns, const SampleN32& sp, int64_t capacity, void* buf,
                             cudaStream_t st);
 int launch_spawnN_step32(int ns, const BulkParams& bp, const CoefN& cf, void* buf,

@@ -1,5 +1,5 @@
 // spawn.cu -- trajectory spawning on the GPU (FP64, two states; N_s > 2 in
-// nstate_kernels.cuh, and the scan and family starts here serve both): the scheme of
+// nstate_f64.cuh, and the scan and family starts here serve both): the scheme of
 // the CPU code that the paper's GPU version replaces (Sec. II B).  Every step a
 // walker whose transition test fires keeps its pair and weight and spawns a
 // child at the event's target pair with weight m A_e / p_hat_e (no stay
