@@ -24,11 +24,26 @@ def _gauge_signs(U_or, U_np):
     return s
 
 
+def _random_lvc(ns, n, seed):
+    """Random N_s-state LVC model (levels 0.4 apart, weak off-diagonal E,
+    symmetric K_j with strength independent of the mode count)."""
+    rng = np.random.default_rng(seed)
+    omega = rng.uniform(0.6, 1.5, size=n)
+    E = np.diag(0.4 * np.arange(ns)) + 0.04 * (np.ones((ns, ns)) - np.eye(ns))
+    K = np.zeros((n, ns, ns))
+    for j in range(n):
+        a = rng.normal(size=(ns, ns)) * 0.12 * np.sqrt(6.0 / n)
+        K[j] = 0.5 * (a + a.T)
+    return wl._model(E, K, np.ones(n), omega, name=f"lvc{ns}x{n}")
+
+
 def _models():
     m2 = wl.config(2)["model"]
     m3 = wl.config(3)["model"]
     m4 = wl.random_lvc4(7)
-    return [m2, m3, m4]
+    # the mode counts and state counts the FP32 modes-in-memory kernels are
+    # compared at: four states with 40 modes, eight states with 12
+    return [m2, m3, m4, wl.random_lvc4(8, 40), _random_lvc(8, 12, 9)]
 
 
 def _random_R(model, rng):
