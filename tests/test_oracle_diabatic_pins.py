@@ -153,12 +153,26 @@ def test_diabatic_pure_dephasing_at_any_eps(eps):
     assert np.array_equal(st.m, s0.m) and np.all(st.q == 0)
 
 
-def test_diabatic_events_follow_the_off_diagonal_potential():
-    model = wl.random_lvc4(3)
+def _lvc8(n, seed):
+    rng = np.random.default_rng(seed)
+    E = np.diag(0.4 * np.arange(8)) + 0.04 * (np.ones((8, 8)) - np.eye(8))
+    K = np.zeros((n, 8, 8))
+    for j in range(n):
+        a = rng.normal(size=(8, 8)) * 0.12 * np.sqrt(6.0 / n)
+        K[j] = 0.5 * (a + a.T)
+    return wl._model(E, K, np.ones(n), rng.uniform(0.6, 1.5, size=n), name=f"lvc8x{n}")
+
+
+# (four states with 6 and 40 modes, eight states with 12: the sizes the FP32
+# kernels are compared at)
+@pytest.mark.parametrize("make", [lambda: wl.random_lvc4(3), lambda: wl.random_lvc4(3, 40),
+                                  lambda: _lvc8(12, 4)])
+def test_diabatic_events_follow_the_off_diagonal_potential(make):
+    model = make()
     model["repr"] = "diabatic"
     om = O.OracleModel(model)
     rng = np.random.default_rng(2)
-    dt, ns = 0.05, 4
+    dt, ns = 0.05, model["n_states"]
     for _ in range(20):
         R = rng.normal(size=model["n_modes"])
         W = model["E"] + np.einsum("j,jab->ab", R, model["K"])
