@@ -205,6 +205,11 @@ def version() -> str:
 
 
 def set_option(key: int, value: int):
+    """Process-wide option (include/qcl.h): OPT_GRID_CAP (cap on the persistent
+    grid, 0 = none), OPT_TIMING (1: CUDA events around the kernel launches),
+    OPT_MODES_IN_MEMORY (0: the measured choice between the register and
+    modes-in-memory kernels, 1: memory, 2: registers where a form exists).  No
+    option changes a bit of any result."""
     _check(load().qcl_set_option(key, value), "qcl_set_option")
 
 
